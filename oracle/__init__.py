@@ -1,0 +1,24 @@
+"""CPU oracle for batch-dynamic 4-node graphlet counting.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library path imports this package:
+only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may use it.  It shares no code with the CUDA library.
+
+* ``brute``  -- census of every 4-subset (n <= 40), the plain definition.
+* ``oracle`` -- plain single-threaded C (``gc_oracle.c``): literal and
+  degree-oriented static counts, batch normalisation and one literal step of
+  Algorithm 2 (FDGC).
+"""
+from . import brute  # noqa: F401
+from .oracle import (  # noqa: F401
+    GRAPHLETS,
+    SUMS,
+    OracleGraph,
+    build,
+    counts_from_sums,
+    fdgc_step,
+    normalize,
+    static_counts,
+    sums_literal,
+    sums_oriented,
+)

@@ -1,0 +1,61 @@
+"""Brute-force census of every 4-vertex subset (tiny graphs only, n <= 40).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+This is the plain definition of the counted quantity (Sec. 3, Problem 1, and
+Fig. 1): for each of the C(n, 4) vertex subsets S, classify the induced
+subgraph G[S] by its edge count and sorted degree sequence.  The six
+connected classes are the paper's graphlets g1..g6; the other five classes
+(empty, one edge, two adjacent edges, two disjoint edges, triangle plus an
+isolated vertex) are disconnected and only serve the check that all eleven
+classes together account for every one of the C(n, 4) subsets.
+"""
+from __future__ import annotations
+
+import itertools
+
+# (edge count, sorted degrees) -> class name
+_CLASSES = {
+    (0, (0, 0, 0, 0)): "empty",
+    (1, (0, 0, 1, 1)): "edge",
+    (2, (0, 1, 1, 2)): "wedge+isolated",
+    (2, (1, 1, 1, 1)): "two-edges",
+    (3, (0, 2, 2, 2)): "triangle+isolated",
+    (3, (1, 1, 2, 2)): "g1",   # 3-path
+    (3, (1, 1, 1, 3)): "g2",   # 3-star
+    (4, (2, 2, 2, 2)): "g3",   # 4-cycle
+    (4, (1, 2, 2, 3)): "g4",   # tailed triangle
+    (5, (2, 2, 3, 3)): "g5",   # diamond
+    (6, (3, 3, 3, 3)): "g6",   # 4-clique
+}
+CONNECTED = ("g1", "g2", "g3", "g4", "g5", "g6")
+ALL_CLASSES = tuple(sorted(set(_CLASSES.values())))
+
+
+def census(n: int, edges) -> dict[str, int]:
+    """Histogram of the 11 induced 4-vertex classes over all C(n,4) subsets."""
+    if n > 40:
+        raise ValueError("brute force is for n <= 40")
+    adj = [[False] * n for _ in range(n)]
+    for a, b in edges:
+        if a == b:
+            raise ValueError("self-loop")
+        adj[a][b] = adj[b][a] = True
+    hist = {c: 0 for c in ALL_CLASSES}
+    for s in itertools.combinations(range(n), 4):
+        deg = [0, 0, 0, 0]
+        k = 0
+        for i in range(4):
+            for j in range(i + 1, 4):
+                if adj[s[i]][s[j]]:
+                    k += 1
+                    deg[i] += 1
+                    deg[j] += 1
+        hist[_CLASSES[(k, tuple(sorted(deg)))]] += 1
+    return hist
+
+
+def graphlet_counts(n: int, edges) -> list[int]:
+    """[g1, g2, g3, g4, g5, g6] by brute force."""
+    h = census(n, edges)
+    return [h[c] for c in CONNECTED]

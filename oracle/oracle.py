@@ -1,0 +1,181 @@
+"""ctypes front end of the plain C oracle (``gc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Functions here take
+numpy CSR arrays (``row_ptr`` of n+1 offsets, ``col`` of int32 neighbours,
+rows sorted) and return Python ints, so expected values never pass through
+the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GRAPHLETS = ("3-path", "3-star", "4-cycle", "tailed-triangle", "diamond", "4-clique")
+SUMS = ("P", "S", "TT", "D", "K", "Q")
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (plain -O2, single-threaded)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            I64 = ctypes.c_int64
+            lib.or_sums_literal.argtypes = [I64, i64p, i32p, ctypes.c_int, i64p]
+            lib.or_sums_oriented.argtypes = [I64, i64p, i32p, i64p]
+            lib.or_counts_from_sums.argtypes = [i64p, i64p]
+            lib.or_counts_from_sums.restype = None
+            lib.or_normalize.argtypes = [I64, i64p, i32p, i32p, I64, i32p, I64, u64p, i64p, u64p, i64p, i64p]
+            lib.or_fdgc_step.argtypes = [I64, i64p, i32p, i32p, I64, i32p, I64, ctypes.c_int, ctypes.c_int,
+                                         u64p, i64p, i64p, i64p, i64p, i64p, i64p, i32p, i32p]
+            _lib = lib
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _csr(row_ptr, col):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    if c.size == 0:
+        c = np.zeros(1, dtype=np.int32)
+    return rp, c
+
+
+def _pairs(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1, 2))
+    buf = a if a.size else np.zeros((1, 2), dtype=np.int32)
+    return buf, a.shape[0]
+
+
+def sums_literal(row_ptr, col, with_ic4: bool = False) -> list[int]:
+    """[P, S, TT, D, K, Q] (+ induced 4-cycles if ``with_ic4``) by plain definitions."""
+    rp, c = _csr(row_ptr, col)
+    out = np.zeros(7, dtype=np.int64)
+    rc = _load().or_sums_literal(rp.size - 1, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32),
+                                 1 if with_ic4 else 0, _p(out, ctypes.c_int64))
+    if rc != 0:
+        raise RuntimeError(f"or_sums_literal failed ({rc})")
+    return [int(x) for x in (out if with_ic4 else out[:6])]
+
+
+def sums_oriented(row_ptr, col) -> list[int]:
+    """[P, S, TT, D, K, Q] by degree-oriented listing (large graphs)."""
+    rp, c = _csr(row_ptr, col)
+    out = np.zeros(6, dtype=np.int64)
+    rc = _load().or_sums_oriented(rp.size - 1, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32), _p(out, ctypes.c_int64))
+    if rc != 0:
+        raise RuntimeError(f"or_sums_oriented failed ({rc})")
+    return [int(x) for x in out]
+
+
+def counts_from_sums(sums) -> list[int]:
+    s = np.asarray(sums[:6], dtype=np.int64)
+    out = np.zeros(6, dtype=np.int64)
+    _load().or_counts_from_sums(_p(s, ctypes.c_int64), _p(out, ctypes.c_int64))
+    return [int(x) for x in out]
+
+
+def static_counts(row_ptr, col, variant: str = "oriented") -> list[int]:
+    """Induced graphlet counts [g1..g6] of a whole graph."""
+    s = sums_literal(row_ptr, col) if variant == "literal" else sums_oriented(row_ptr, col)
+    return counts_from_sums(s)
+
+
+def normalize(row_ptr, col, ins, dels):
+    """Normalised batch: (A keys, D keys, stats) or raises ValueError."""
+    rp, c = _csr(row_ptr, col)
+    ib, ni = _pairs(ins)
+    db, nd = _pairs(dels)
+    A = np.zeros(max(ni, 1), dtype=np.uint64)
+    D = np.zeros(max(nd, 1), dtype=np.uint64)
+    na = ctypes.c_int64(0)
+    ndd = ctypes.c_int64(0)
+    st = np.zeros(8, dtype=np.int64)
+    rc = _load().or_normalize(rp.size - 1, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32),
+                              _p(ib, ctypes.c_int32), ni, _p(db, ctypes.c_int32), nd,
+                              _p(A, ctypes.c_uint64), ctypes.byref(na), _p(D, ctypes.c_uint64), ctypes.byref(ndd),
+                              _p(st, ctypes.c_int64))
+    if rc == -1:
+        raise ValueError("invalid batch (self-loop or vertex out of range)")
+    if rc != 0:
+        raise RuntimeError(f"or_normalize failed ({rc})")
+    return A[: na.value].copy(), D[: ndd.value].copy(), [int(x) for x in st]
+
+
+def fdgc_step(row_ptr, col, ins, dels, F, hops: int = 3, variant: str = "oriented", want_region: bool = False):
+    """One step of Algorithm 2.  Returns a dict with the new F, C_a, C_b, the
+    sums of G_a and G_b, info and the committed CSR."""
+    rp, c = _csr(row_ptr, col)
+    n = rp.size - 1
+    ib, ni = _pairs(ins)
+    db, nd = _pairs(dels)
+    Fa = np.asarray([int(x) & 0xFFFFFFFFFFFFFFFF for x in F], dtype=np.uint64)
+    Ca = np.zeros(6, dtype=np.int64)
+    Cb = np.zeros(6, dtype=np.int64)
+    sa = np.zeros(6, dtype=np.int64)
+    sb = np.zeros(6, dtype=np.int64)
+    info = np.zeros(8, dtype=np.int64)
+    new_rp = np.zeros(n + 1, dtype=np.int64)
+    new_col = np.zeros(int(rp[-1]) + 2 * ni + 1, dtype=np.int32)
+    region = np.zeros(max(n, 1), dtype=np.int32)
+    rc = _load().or_fdgc_step(n, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32),
+                              _p(ib, ctypes.c_int32), ni, _p(db, ctypes.c_int32), nd,
+                              int(hops), 0 if variant == "literal" else 1,
+                              _p(Fa, ctypes.c_uint64), _p(Ca, ctypes.c_int64), _p(Cb, ctypes.c_int64),
+                              _p(sa, ctypes.c_int64), _p(sb, ctypes.c_int64), _p(info, ctypes.c_int64),
+                              _p(new_rp, ctypes.c_int64), _p(new_col, ctypes.c_int32),
+                              _p(region, ctypes.c_int32) if want_region else None)
+    if rc == -1:
+        raise ValueError("invalid batch (self-loop or vertex out of range)")
+    if rc != 0:
+        raise RuntimeError(f"or_fdgc_step failed ({rc})")
+    out = dict(F=[int(x) for x in Fa], Ca=[int(x) for x in Ca], Cb=[int(x) for x in Cb],
+               sums_a=[int(x) for x in sa], sums_b=[int(x) for x in sb],
+               n_ins=int(info[0]), n_del=int(info[1]), region_vertices=int(info[2]),
+               edges_a=int(info[3]), edges_b=int(info[4]), cancelled=int(info[5]),
+               noops=int(info[6]), repeats=int(info[7]),
+               row_ptr=new_rp, col=new_col[: int(new_rp[-1])].copy())
+    if want_region:
+        out["region"] = region[: int(info[2])].copy()
+    return out
+
+
+class OracleGraph:
+    """A graph under a stream of batches, maintained by the oracle alone."""
+
+    def __init__(self, row_ptr, col, variant: str = "oriented", hops: int = 3):
+        self.row_ptr = np.asarray(row_ptr, dtype=np.int64).copy()
+        self.col = np.asarray(col, dtype=np.int32).copy()
+        self.variant = variant
+        self.hops = hops
+        self.F = [x & 0xFFFFFFFFFFFFFFFF for x in static_counts(self.row_ptr, self.col, variant)]
+
+    def apply(self, ins, dels):
+        r = fdgc_step(self.row_ptr, self.col, ins, dels, self.F, self.hops, self.variant)
+        self.F = r["F"]
+        self.row_ptr, self.col = r["row_ptr"], r["col"]
+        return r

@@ -1,0 +1,363 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Nothing here runs CUDA.  Each test checks the oracle against something other
+than itself: hand-derived counts of named graphs, a brute-force census of
+every 4-subset, containment numbers enumerated from first principles, and the
+identities that Lemma 1 / Lemma 2 (Sec. 4.2, 4.3) guarantee for the dynamic
+update.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from synth import gen
+from gc_testutil import (bfs_region, csr_from_edges, edges_from_csr, load_closed_forms,
+                         random_graph, rows_of)
+
+CLOSED = load_closed_forms()
+
+
+# ---------------------------------------------------------------- static --
+
+@pytest.mark.parametrize("name,n,edges,expect", CLOSED, ids=[c[0] for c in CLOSED])
+def test_closed_form_graphs(name, n, edges, expect, oracle_lib):
+    rp, col = csr_from_edges(n, edges)
+    assert brute.graphlet_counts(n, edges) == expect
+    assert oracle.static_counts(rp, col, "literal") == expect
+    assert oracle.static_counts(rp, col, "oriented") == expect
+
+
+def test_complete_graph_family(oracle_lib):
+    for n in range(4, 11):
+        rp, col = csr_from_edges(n, itertools.combinations(range(n), 2))
+        assert oracle.static_counts(rp, col, "oriented") == [0, 0, 0, 0, 0, math.comb(n, 4)]
+        assert oracle.static_counts(rp, col, "literal") == [0, 0, 0, 0, 0, math.comb(n, 4)]
+
+
+def test_bipartite_and_cycle_families(oracle_lib):
+    for a in range(1, 6):
+        for b in range(1, 7):
+            n = a + b
+            rp, col = csr_from_edges(n, [(i, a + j) for i in range(a) for j in range(b)])
+            exp = [0, a * math.comb(b, 3) + b * math.comb(a, 3), math.comb(a, 2) * math.comb(b, 2), 0, 0, 0]
+            assert oracle.static_counts(rp, col, "oriented") == exp
+    for n in range(5, 12):
+        rp, col = csr_from_edges(n, [(i, (i + 1) % n) for i in range(n)])
+        assert oracle.static_counts(rp, col, "oriented") == [n, 0, 0, 0, 0, 0]
+        rp, col = csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+        assert oracle.static_counts(rp, col, "literal") == [n - 3, 0, 0, 0, 0, 0]
+
+
+def test_census_covers_every_subset():
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        n = int(rng.integers(4, 13))
+        h = brute.census(n, random_graph(rng, n, rng.random()))
+        assert sum(h.values()) == math.comb(n, 4)
+
+
+def _classify_edges(edge_subset):
+    deg = {}
+    for a, b in edge_subset:
+        deg[a] = deg.get(a, 0) + 1
+        deg[b] = deg.get(b, 0) + 1
+    return len(edge_subset), tuple(sorted(deg.get(v, 0) for v in range(4)))
+
+
+# representative of each connected graphlet on vertices 0..3
+_SHAPES = {
+    "g1": [(0, 1), (1, 2), (2, 3)],
+    "g2": [(0, 1), (0, 2), (0, 3)],
+    "g3": [(0, 1), (1, 2), (2, 3), (3, 0)],
+    "g4": [(0, 1), (1, 2), (2, 0), (2, 3)],
+    "g5": [(0, 1), (0, 2), (1, 2), (1, 3), (2, 3)],
+    "g6": [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)],
+}
+_PATTERN_SIG = {  # (edges, sorted degrees) of each non-induced pattern
+    "P": (3, (1, 1, 2, 2)), "S": (3, (1, 1, 1, 3)), "TT": (4, (1, 2, 2, 3)),
+    "D": (5, (2, 2, 3, 3)), "K": (6, (3, 3, 3, 3)), "Q": (4, (2, 2, 2, 2)),
+}
+
+
+def _containment():
+    """copies[pattern][graphlet]: edge subsets of the graphlet shaped like the pattern."""
+    out = {p: {} for p in _PATTERN_SIG}
+    for g, edges in _SHAPES.items():
+        for p, sig in _PATTERN_SIG.items():
+            c = 0
+            for r in range(len(edges) + 1):
+                for sub in itertools.combinations(edges, r):
+                    if _classify_edges(sub) == sig:
+                        c += 1
+            out[p][g] = c
+    return out
+
+
+def test_containment_matrix_by_enumeration():
+    c = _containment()
+    # spot values quoted in the oracle's header
+    assert [c["D"]["g6"], c["Q"]["g6"], c["TT"]["g6"], c["S"]["g6"], c["P"]["g6"]] == [6, 3, 12, 4, 12]
+    assert [c["Q"]["g5"], c["TT"]["g5"], c["S"]["g5"], c["P"]["g5"]] == [1, 4, 2, 6]
+    assert c["P"]["g3"] == 4 and c["S"]["g4"] == 1 and c["P"]["g4"] == 2
+
+
+def test_each_sum_matches_brute_force(oracle_lib):
+    """Every non-induced sum equals the census pushed through the enumerated
+    containment matrix, so a dropped or mis-signed term in any single sum fails."""
+    cont = _containment()
+    rng = np.random.default_rng(11)
+    for trial in range(150):
+        n = int(rng.integers(4, 15))
+        edges = random_graph(rng, n, float(rng.random()))
+        h = brute.census(n, edges)
+        expect = [sum(cont[p][g] * h[g] for g in _SHAPES) for p in ("P", "S", "TT", "D", "K", "Q")]
+        rp, col = csr_from_edges(n, edges)
+        lit = oracle.sums_literal(rp, col, with_ic4=True)
+        assert lit[:6] == expect, (trial, n)
+        assert lit[6] == h["g3"]  # PGD's per-edge induced 4-cycle rule
+        assert oracle.sums_oriented(rp, col) == expect, (trial, n)
+        assert oracle.counts_from_sums(expect) == [h[g] for g in brute.CONNECTED]
+
+
+def test_planted_hubs_and_cliques(oracle_lib):
+    """Dense cores plus a hub: exercises large t_uv and high-degree pivots."""
+    rng = np.random.default_rng(3)
+    for trial in range(30):
+        n = 30
+        edges = set(map(tuple, random_graph(rng, n, 0.08)))
+        core = rng.choice(n, size=7, replace=False)
+        edges |= {(min(a, b), max(a, b)) for a in core for b in core if a != b}
+        hub = int(rng.integers(0, n))
+        edges |= {(min(hub, v), max(hub, v)) for v in range(n) if v != hub and rng.random() < 0.7}
+        edges = sorted(edges)
+        rp, col = csr_from_edges(n, edges)
+        bf = brute.graphlet_counts(n, edges)
+        assert oracle.static_counts(rp, col, "literal") == bf
+        assert oracle.static_counts(rp, col, "oriented") == bf
+
+
+def test_variants_agree_on_workload_graphs(oracle_lib):
+    for name in ("c1", "c2"):
+        n, keys = gen.workload_graph(name)
+        rp, col = gen.csr_from_keys(n, keys)
+        assert oracle.sums_literal(rp, col) == oracle.sums_oriented(rp, col)
+
+
+def test_relabel_invariance(oracle_lib):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    base = oracle.static_counts(rp, col)
+    perm = np.random.default_rng(5).permutation(n)
+    edges = [(int(perm[a]), int(perm[b])) for a, b in edges_from_csr(rp, col)]
+    rp2, col2 = csr_from_edges(n, edges)
+    assert oracle.static_counts(rp2, col2) == base
+
+
+# --------------------------------------------------------------- dynamic --
+
+def _random_dirty_batch(rng, n, edges, k_ins, k_del):
+    """Pairs with repeats, reversed orientation, cancellations and no-ops."""
+    es = list(edges)
+    ins = [tuple(rng.choice(n, 2, replace=False)) for _ in range(k_ins)]
+    dels = [es[i] for i in rng.choice(len(es), min(k_del, len(es)), replace=False)] if es else []
+    dels += [tuple(rng.choice(n, 2, replace=False)) for _ in range(k_del // 3)]
+    if ins and rng.random() < 0.5:
+        dels.append(ins[0][::-1])          # cancelled pair
+    if dels and rng.random() < 0.5:
+        ins.append(dels[0])                # cancelled pair
+    if ins:
+        ins.append(ins[-1][::-1])          # repeat, reversed
+    ins = np.array(ins, dtype=np.int32).reshape(-1, 2)
+    dels = np.array(dels, dtype=np.int32).reshape(-1, 2)
+    return ins, dels
+
+
+def test_lemma2_on_random_graphs(oracle_lib):
+    """Algorithm 2: F + C_a - C_b equals the census of G \\ D u A (Lemma 2)."""
+    rng = np.random.default_rng(21)
+    for trial in range(120):
+        n = int(rng.integers(5, 16))
+        edges = random_graph(rng, n, float(rng.uniform(0.1, 0.7)))
+        rp, col = csr_from_edges(n, edges)
+        F0 = brute.graphlet_counts(n, edges)
+        ins, dels = _random_dirty_batch(rng, n, edges, int(rng.integers(0, 5)), int(rng.integers(0, 5)))
+        for variant in ("literal", "oriented"):
+            r = oracle.fdgc_step(rp, col, ins, dels, F0, 3, variant)
+            after = edges_from_csr(r["row_ptr"], r["col"])
+            assert r["F"] == brute.graphlet_counts(n, after), (trial, variant)
+        # the committed graph is G \ D u A after normalisation
+        A, D, _ = oracle.normalize(rp, col, ins, dels)
+        eset = {(a << 32) | b for a, b in edges}
+        expect = (eset - set(map(int, D))) | set(map(int, A))
+        assert {(a << 32) | b for a, b in after} == expect
+
+
+def test_lemma2_workload_c1(oracle_lib):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.random_batch(n, keys, 200, 200, 1, ins_weighting="uniform")
+    F0 = oracle.static_counts(rp, col, "literal")
+    r = oracle.fdgc_step(rp, col, ins, dels, F0, 3, "literal")
+    assert (r["n_ins"], r["n_del"]) == (200, 200)
+    assert r["F"] == oracle.static_counts(r["row_ptr"], r["col"], "literal")
+    assert [a - b for a, b in zip(r["Ca"], r["Cb"])] == [x - y for x, y in zip(r["F"], F0)]
+
+
+def test_lemma2_workload_c2_stream(oracle_lib):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    g = oracle.OracleGraph(rp, col)
+    for ins, dels in gen.batch_stream(n, keys, [1000, 10000, 1000], 0.5, 2):
+        g.apply(ins, dels)
+        assert g.F == oracle.static_counts(g.row_ptr, g.col)
+    # insert-only (IGC) stream
+    g = oracle.OracleGraph(rp, col)
+    for ins, dels in gen.batch_stream(n, keys, [1000, 10000], 1.0, 2):
+        assert len(dels) == 0
+        g.apply(ins, dels)
+        assert g.F == oracle.static_counts(g.row_ptr, g.col)
+
+
+def test_radius_two_suffices_and_one_does_not(oracle_lib):
+    """Any 4-subset holding a changed pair lies within 2 hops of its
+    endpoints, so k = 2 gives the same delta as the paper's k = 3; k = 1
+    misses subsets and must fail somewhere."""
+    rng = np.random.default_rng(31)
+    k1_wrong = 0
+    for trial in range(150):
+        n = int(rng.integers(6, 16))
+        edges = random_graph(rng, n, float(rng.uniform(0.1, 0.5)))
+        rp, col = csr_from_edges(n, edges)
+        F0 = oracle.static_counts(rp, col)
+        ins, dels = _random_dirty_batch(rng, n, edges, 2, 2)
+        r3 = oracle.fdgc_step(rp, col, ins, dels, F0, 3)
+        r2 = oracle.fdgc_step(rp, col, ins, dels, F0, 2)
+        r1 = oracle.fdgc_step(rp, col, ins, dels, F0, 1)
+        assert r2["F"] == r3["F"]
+        k1_wrong += r1["F"] != r3["F"]
+    assert k1_wrong > 0
+
+
+def test_region_is_the_same_in_G_and_G_union_A(oracle_lib):
+    """The walk starts from every endpoint, so an inserted edge joins two
+    vertices already at depth 0 and can never shorten a distance: the region
+    taken in G (Algorithm 2 as printed) equals the region taken in G u A."""
+    rng = np.random.default_rng(41)
+    for trial in range(60):
+        n = int(rng.integers(6, 30))
+        edges = random_graph(rng, n, float(rng.uniform(0.05, 0.3)))
+        rp, col = csr_from_edges(n, edges)
+        ins, dels = _random_dirty_batch(rng, n, edges, 3, 3)
+        r = oracle.fdgc_step(rp, col, ins, dels, [0] * 6, 3, want_region=True)
+        A, D, _ = oracle.normalize(rp, col, ins, dels)
+        src = [int(k >> 32) for k in list(A) + list(D)] + [int(k & 0xFFFFFFFF) for k in list(A) + list(D)]
+        expect = bfs_region(n, rows_of(rp, col), src, 3)
+        assert list(map(int, r["region"])) == expect
+
+
+def test_igc_is_fdgc_without_deletions(oracle_lib):
+    """Algorithm 1 built literally (G <- G + B first, W from the updated
+    graph, G_b = G_a \\ B) gives the same C_a and C_b as Algorithm 2 with
+    D empty."""
+    rng = np.random.default_rng(51)
+    for trial in range(60):
+        n = int(rng.integers(6, 20))
+        edges = random_graph(rng, n, float(rng.uniform(0.1, 0.4)))
+        rp, col = csr_from_edges(n, edges)
+        eset = set(edges)
+        cand = [(a, b) for a in range(n) for b in range(a + 1, n) if (a, b) not in eset]
+        if not cand:
+            continue
+        pick = rng.choice(len(cand), min(len(cand), int(rng.integers(1, 5))), replace=False)
+        B = [cand[i] for i in pick]
+        new_edges = sorted(eset | set(B))
+        rp1, col1 = csr_from_edges(n, new_edges)
+        W = bfs_region(n, rows_of(rp1, col1), [x for e in B for x in e], 3)
+        idx = {v: i for i, v in enumerate(W)}
+        ga = [(idx[a], idx[b]) for a, b in new_edges if a in idx and b in idx]
+        gb = [e for e in ga if (W[e[0]], W[e[1]]) not in set(B)]
+        Ca = oracle.static_counts(*csr_from_edges(len(W), ga))
+        Cb = oracle.static_counts(*csr_from_edges(len(W), gb))
+        r = oracle.fdgc_step(rp, col, np.array(B, dtype=np.int32), np.zeros((0, 2), np.int32), [0] * 6, 3)
+        assert (r["Ca"], r["Cb"]) == (Ca, Cb)
+
+
+def test_batch_then_inverse_restores_counts(oracle_lib):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    g = oracle.OracleGraph(rp, col)
+    F0 = list(g.F)
+    ins, dels = gen.random_batch(n, keys, 700, 300, 9)
+    g.apply(ins, dels)
+    assert g.F != F0
+    g.apply(dels, ins)
+    assert g.F == F0
+    assert np.array_equal(g.row_ptr, rp.astype(np.int64)) and np.array_equal(g.col, col)
+
+
+def test_split_batch_gives_same_counts(oracle_lib):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.random_batch(n, keys, 200, 200, 1, ins_weighting="uniform")
+    whole = oracle.OracleGraph(rp, col)
+    whole.apply(ins, dels)
+    parts = oracle.OracleGraph(rp, col)
+    parts.apply(ins[:77], dels[:150])
+    parts.apply(ins[77:], dels[150:])
+    assert whole.F == parts.F
+
+
+def test_normalisation_rules(oracle_lib):
+    # path 0-1-2-3 plus edge 0-2
+    rp, col = csr_from_edges(5, [(0, 1), (1, 2), (2, 3), (0, 2)])
+    ins = np.array([[3, 4], [4, 3], [1, 3], [0, 1], [2, 4]], dtype=np.int32)
+    dels = np.array([[2, 1], [1, 2], [0, 4], [3, 1]], dtype=np.int32)
+    A, D, st = oracle.normalize(rp, col, ins, dels)
+    # (3,4) repeated -> once; (1,3) also deleted -> cancelled; (0,1) exists -> no-op
+    assert sorted(int(k) for k in A) == [(2 << 32) | 4, (3 << 32) | 4]
+    # (1,2) repeated -> once; (0,4) missing -> no-op; (1,3) cancelled
+    assert [int(k) for k in D] == [(1 << 32) | 2]
+    assert st == [5, 4, 1, 1, 1, 1, 1, 0]
+    with pytest.raises(ValueError):
+        oracle.normalize(rp, col, np.array([[2, 2]], np.int32), np.zeros((0, 2), np.int32))
+    with pytest.raises(ValueError):
+        oracle.normalize(rp, col, np.zeros((0, 2), np.int32), np.array([[0, 5]], np.int32))
+
+
+def test_empty_and_all_noop_batches(oracle_lib):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    e = np.zeros((0, 2), np.int32)
+    r = oracle.fdgc_step(rp, col, e, e, F0)
+    assert r["F"] == F0 and r["region_vertices"] == 0 and r["Ca"] == [0] * 6
+    existing = np.array(edges_from_csr(rp, col)[:10], dtype=np.int32)
+    r = oracle.fdgc_step(rp, col, existing, np.array([[0, 1999]] if 1999 not in col[rp[0]:rp[1]] else [], np.int32).reshape(-1, 2), F0)
+    assert r["F"] == F0 and r["region_vertices"] == 0 and r["noops"] >= 10
+
+
+def test_stored_workload_values(oracle_lib):
+    """``golden/workloads.json`` (written by ``golden/make_golden.py`` from the
+    oracle alone) still matches a fresh oracle run, and is self-consistent
+    with Lemma 2."""
+    import json
+    import os
+
+    from gc_testutil import GOLDEN_DIR
+
+    with open(os.path.join(GOLDEN_DIR, "workloads.json")) as f:
+        gold = json.load(f)
+    c1 = gold["c1"]
+    assert [a - b for a, b in zip(c1["Ca"], c1["Cb"])] == [x - y for x, y in zip(c1["after"], c1["static"])]
+    assert oracle.counts_from_sums(c1["sums_a"]) == c1["Ca"]
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    assert oracle.static_counts(rp, col) == c1["static"]
+    ins, dels = gen.random_batch(n, keys, 200, 200, 1, ins_weighting="uniform")
+    r = oracle.fdgc_step(rp, col, ins, dels, c1["static"], 3)
+    assert r["F"] == c1["after"] and r["Ca"] == c1["Ca"] and r["Cb"] == c1["Cb"]
+    assert oracle.static_counts(r["row_ptr"], r["col"], "literal") == c1["after"]
