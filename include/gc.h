@@ -1,0 +1,169 @@
+/*
+ * gc.h -- C ABI of the GB300 batch-dynamic 4-node graphlet counter.
+ *
+ * The library maintains, for one simple undirected graph resident in GPU
+ * memory, the counts of the six connected induced 4-vertex graphlets, in the
+ * order of Fig. 1 of "Efficient Batch Dynamic Graphlet Counting"
+ * (arXiv 2308.14493):
+ *
+ *     out[0] g1 3-path        out[3] g4 tailed triangle
+ *     out[1] g2 3-star        out[4] g5 diamond
+ *     out[2] g3 4-cycle       out[5] g6 4-clique
+ *
+ * Problem 1 (Sec. 3) defines the maintained quantity; Algorithm 2 (FDGC,
+ * Sec. 4.3) is the update: for a batch B = A u D, take the region H induced
+ * by the k-hop neighbourhood of the batch endpoints, count graphlets in
+ * G_a = (H \ D) u A and G_b = (H \ A) u D, add C_a - C_b to the counts, then
+ * commit G <- G \ D u A.  Insert-only batches are IGC (Algorithm 1, Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *  - Return GC_OK (0) or a negative GC_E* code; gc_last_error() then holds
+ *    a one-line reason.  A failed call leaves the graph and its counts
+ *    exactly as they were.
+ *  - Vertex ids are int32 in [0, n); n is fixed by gc_open.  n < 2^30.
+ *  - Edge pairs are int32 [k][2] arrays, row-major: pair i is (p[2i], p[2i+1]).
+ *  - All entry points are synchronous: when they return, every input buffer
+ *    may be reused and every output is written.  A handle is not thread-safe;
+ *    separate handles are independent.
+ *  - The caller owns every buffer it passes; the library copies what it
+ *    needs and owns all device memory it allocates.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GC_OK = 0,
+    GC_EINVAL = -1,   /* bad argument: null pointer, id out of range, self-loop, malformed CSR */
+    GC_ENOMEM = -2,   /* device or host allocation failed */
+    GC_ECUDA = -3,    /* a CUDA runtime call failed; see gc_last_error() */
+    GC_ETIMEOUT = -4  /* reserved: a bounded device-side wait ran out */
+};
+
+typedef struct gc_graph gc_graph;
+
+/* Options for gc_open.  Zero-initialised fields take the defaults. */
+typedef struct {
+    /* Device allocator callbacks (both or neither).  alloc returns device
+       memory of at least `bytes` bytes usable on `stream`, or NULL. */
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+    void *stream;        /* cudaStream_t to run on; NULL: the library makes one */
+    int32_t region_hops; /* k of the k-hop region; 0 -> 3 as in Sec. 4.2; must be >= 2 */
+    float slack;         /* spare capacity per adjacency row; 0 -> 0.25 */
+    int32_t device;      /* CUDA device ordinal; 0 -> current device */
+    int32_t reserved[7];
+} gc_options;
+
+/* Per-batch record of the last gc_apply_batch* call. */
+typedef struct {
+    int64_t n_ins_raw, n_del_raw;   /* pairs passed in */
+    int64_t n_ins, n_del;           /* pairs applied after normalisation (|A|, |D|) */
+    int64_t repeats;                /* pairs dropped as repeats within A or within D */
+    int64_t cancelled;              /* pairs present in both A and D, dropped from both (Sec. 5) */
+    int64_t noop_ins, noop_del;     /* insertions of present edges, deletions of absent ones */
+    int64_t region_vertices;        /* |W|, the k-hop region */
+    int64_t region_entries;         /* directed adjacency entries of the region union graph */
+    int64_t edges_a, edges_b;       /* undirected edges of G_a and G_b */
+    int64_t Ca[6], Cb[6];           /* induced counts of G_a and G_b */
+    int64_t sums_a[6], sums_b[6];   /* [P, S, TT, D, K, Q]: non-induced 3-paths, 3-stars,
+                                       tailed triangles, diamonds, 4-cliques, 4-cycles */
+    int64_t num_edges;              /* edges of the graph after the batch */
+    float ms_device;                /* device time of the batch (CUDA events) */
+    float ms_wall;                  /* host wall time of the call */
+    int32_t relayouts;              /* adjacency re-layouts the batch needed */
+    int32_t reserved[5];
+    /* device time per stage (CUDA events on the library's stream):
+       [0] normalise  [1] region walk  [2] union graph  [3] triangles + 4-cliques
+       [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused */
+    float ms_stage[8];
+} gc_stats;
+
+/* Fill *opt with the defaults. */
+void gc_default_options(gc_options *opt);
+
+/*
+ * Open a graph from a host CSR and count it.
+ *   n        vertices, 0 <= n < 2^30
+ *   row_ptr  host int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = 2m
+ *   col      host int32[row_ptr[n]]: neighbours; rows in any order
+ *   opt      NULL for defaults
+ *   out      receives the handle
+ * The CSR must be symmetric, without self-loops or repeated entries
+ * (GC_EINVAL otherwise).  The initial counts are a full static count, which
+ * equals streaming every edge into an empty graph (Algorithm 2 starts from
+ * F = 0 on an empty graph).  Input is copied; the caller keeps ownership.
+ */
+int gc_open(int32_t n, const int32_t *row_ptr, const int32_t *col,
+            const gc_options *opt, gc_graph **out);
+
+/* Full static recount of the current graph into out[6] (the recount
+   baseline of Sec. 4.1).  Does not change the maintained counts. */
+int gc_count_static(gc_graph *g, uint64_t out[6]);
+
+/* The maintained counts. */
+int gc_counts(const gc_graph *g, uint64_t out[6]);
+
+/*
+ * Apply one batch (Algorithm 2) and return the updated counts.
+ *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)
+ *   del   host int32[n_del][2]: pairs to delete (may be NULL when n_del = 0)
+ *   out   host uint64[6]: counts after the batch (may be NULL)
+ * Pairs are unordered; repeats collapse; a pair in both lists is dropped from
+ * both; inserting a present edge or deleting an absent one does nothing.
+ * Self-loops or ids outside [0, n) give GC_EINVAL and change nothing.
+ */
+int gc_apply_batch(gc_graph *g, const int32_t *ins, int64_t n_ins,
+                   const int32_t *del, int64_t n_del, uint64_t out[6]);
+
+/* As gc_apply_batch, with the pair arrays in device memory (int32, same
+   layout).  The caller guarantees every id is in [0, n) and no pair is a
+   self-loop; the library does not read the pairs on the host. */
+int gc_apply_batch_device(gc_graph *g, const int32_t *d_ins, int64_t n_ins,
+                          const int32_t *d_del, int64_t n_del, uint64_t out[6]);
+
+/*
+ * Apply k batches in one device launch sequence (a CUDA graph replayed per
+ * batch, with batch sizes read on the device).
+ *   ins[i], n_ins[i], del[i], n_del[i]   host pair arrays of batch i
+ *   independent  0: batches apply in order, each on the graph the previous
+ *                   one left (sequential stream);
+ *                1: every batch is counted against the current graph and
+ *                   nothing is committed (what-if batches on one snapshot)
+ *   out          host uint64[k][6]: counts after each batch
+ * Results equal k calls of gc_apply_batch (independent = 0), or k calls each
+ * made on a fresh copy of the graph (independent = 1).
+ */
+int gc_apply_batches(gc_graph *g, const int32_t *const *ins, const int64_t *n_ins,
+                     const int32_t *const *del, const int64_t *n_del, int32_t k,
+                     int32_t independent, uint64_t *out);
+
+/* Record of the last batch. */
+int gc_batch_stats(const gc_graph *g, gc_stats *s);
+
+/* Edges currently in the graph. */
+int64_t gc_num_edges(const gc_graph *g);
+
+/* Copy the current graph out as a host CSR with sorted rows.
+   row_ptr: int32[n+1]; col: int32[2 * gc_num_edges(g)]. */
+int gc_export_csr(gc_graph *g, int32_t *row_ptr, int32_t *col);
+
+/* One-line reason for the last failure on this handle ("" if none).
+   With g == NULL: the reason for the last failed gc_open. */
+const char *gc_last_error(const gc_graph *g);
+
+/* Release the handle and all its device memory.  NULL is allowed. */
+void gc_close(gc_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

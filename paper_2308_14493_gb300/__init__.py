@@ -1,0 +1,24 @@
+"""GB300 batch-dynamic 4-node graphlet counting (FDGC / IGC, arXiv 2308.14493).
+
+The compute path is the CUDA library ``libgc.so`` behind the C ABI in
+``include/gc.h``; ``gc`` is its ctypes binding.  Importing this package does
+not load the library; the first call does, and fails loudly if it cannot.
+"""
+from .gc import (  # noqa: F401
+    GRAPHLETS,
+    GCError,
+    Graph,
+    gc_apply_batch,
+    gc_apply_batch_device,
+    gc_apply_batches,
+    gc_batch_stats,
+    gc_close,
+    gc_count_static,
+    gc_counts,
+    gc_export_csr,
+    gc_last_error,
+    gc_num_edges,
+    gc_open,
+    library_path,
+    load,
+)

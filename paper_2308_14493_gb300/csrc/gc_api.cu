@@ -1,0 +1,853 @@
+// gc_api.cu -- the C ABI (include/gc.h): handle state, device buffers and the
+// launch sequence of one batch of Algorithm 2 (FDGC, Sec. 4.3):
+//
+//   a0 normalise the batch (sort directed keys, drop repeats, pairs in both
+//      lists, no-ops)                                    gc_batch.cu
+//   a1 k-hop region W from every endpoint               gc_region.cu
+//   a2 flagged union graph U = G[W] u A, degrees in G_a and G_b
+//   a3 per-edge triangles of G_a and G_b                 gc_count.cu
+//   a4 4-cliques, a5 4-cycles, a6 per-edge / per-vertex terms
+//   a7 closed forms: C_a, C_b, F += C_a - C_b
+//   a8 commit G <- G \ D u A into the slack-padded rows  gc_batch.cu
+//
+// Every stage reads its sizes from the device control block, so the host
+// only enqueues work and reads the control block back once per batch.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gc.h"
+#include "gc_internal.cuh"
+#include "gc_kernels.cuh"
+
+using namespace gcx;
+
+namespace {
+
+thread_local std::string t_open_error;
+
+template <class T>
+struct Buf {
+    T* p = nullptr;
+    size_t cap = 0;
+};
+
+constexpr int TPB = 256;
+
+int bitlen(long long x) {
+    int b = 0;
+    while (x > 0) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace
+
+struct gc_graph {
+    int dev = 0, n = 0, S = 1, sms = 148, hops = 3;
+    float slack = 0.25f;
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    gc_options opt{};
+    // persistent state
+    int32_t *perm = nullptr, *iperm = nullptr, *deg = nullptr, *cap = nullptr, *col = nullptr;
+    long long* row_start = nullptr;
+    long long col_capacity = 0;
+    Ctl* ctl = nullptr;
+    Ctl* h_ctl = nullptr;           // pinned mirror
+    long long* desc = nullptr;      // device: [ins_off, n_ins, del_off, n_del, misc...]
+    long long* h_desc = nullptr;    // pinned
+    int2 *segA = nullptr, *segD = nullptr;
+    uint32_t* visited = nullptr;
+    int32_t *wlist = nullptr, *U_deg = nullptr, *U_split = nullptr, *da = nullptr, *db = nullptr;
+    long long* U_off = nullptr;
+    // scratch that grows with the batch or the graph
+    Buf<uint32_t> U_col;
+    Buf<unsigned long long> tpack;
+    Buf<uint64_t> keys, keys_tmp;
+    Buf<int32_t> keepA, keepD, srcA, dstA, srcD, dstD, plan_cap, plan_deg, pairs;
+    Buf<long long> posA, posD, plan_dst, plan_scr, bsum;
+    Buf<uint32_t> hist;
+    Buf<unsigned long long> c4cnt;
+    int c4_blocks = 0;
+    // host mirror
+    uint64_t F[6] = {0, 0, 0, 0, 0, 0};
+    long long m = 0;
+    gc_stats st{};
+    std::string err;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t ev[8] = {};  // stage boundaries, see gc_stats.ms_stage
+};
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+static void* dalloc(gc_graph* g, size_t bytes) {
+    if (bytes < 16) bytes = 16;
+    void* p = nullptr;
+    if (g->opt.alloc) {
+        p = g->opt.alloc(bytes, (void*)g->s, g->opt.ctx);
+    } else if (cudaMallocAsync(&p, bytes, g->s) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+static void dfree(gc_graph* g, void* p) {
+    if (!p) return;
+    if (g->opt.free) g->opt.free(p, (void*)g->s, g->opt.ctx);
+    else cudaFreeAsync(p, g->s);
+}
+
+template <class T>
+static bool ensure(gc_graph* g, Buf<T>& b, size_t count) {
+    if (b.p && b.cap >= count) return true;
+    size_t nc = std::max<size_t>(count + count / 4, 64);
+    dfree(g, b.p);
+    b.p = (T*)dalloc(g, nc * sizeof(T));
+    b.cap = b.p ? nc : 0;
+    return b.p != nullptr;
+}
+
+template <class T>
+static void release(gc_graph* g, Buf<T>& b) {
+    dfree(g, b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            g->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return GC_ECUDA;                                                              \
+        }                                                                                 \
+    } while (0)
+
+#define CKL()                                                                             \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) {                                                          \
+            g->err = std::string("kernel launch: ") + cudaGetErrorString(e_);             \
+            return GC_ECUDA;                                                              \
+        }                                                                                 \
+    } while (0)
+
+static int nomem(gc_graph* g, const char* what) {
+    g->err = std::string("device allocation failed: ") + what;
+    return GC_ENOMEM;
+}
+
+static int grid_elems(gc_graph* g, long long n) {
+    long long b = (n + TPB - 1) / TPB;
+    if (b < 1) b = 1;
+    if (b > 8LL * g->sms) b = 8LL * g->sms;
+    return (int)b;
+}
+static int grid_warps(gc_graph* g) { return 8 * g->sms; }  // 8 warps per block
+
+// ---------------------------------------------------------------------------
+// small device helpers local to this file
+// ---------------------------------------------------------------------------
+namespace gcx {
+__global__ void k_begin_batch(Ctl* c, const long long* desc, int commit_reset) {
+    if (threadIdx.x != 0) return;
+    c->n_ins = desc[1];
+    c->n_del = desc[3];
+    c->nkeys = 2 * (desc[1] + desc[3]);
+    c->nA2 = c->nD2 = 0;
+    for (int i = 0; i < 8; i++) c->st[i] = 0;
+    c->nW = 0;
+    for (int i = 0; i < MAX_HOPS + 2; i++) c->lvl[i] = 0;
+    c->nU = 0;
+    c->scratch_tail = 0;
+    c->overflow = 0;
+    c->err = 0;
+    (void)commit_reset;
+}
+__global__ void k_commit_reset(Ctl* c, unsigned long long pool_tail, int set_pool) {
+    if (threadIdx.x != 0) return;
+    c->scratch_tail = 0;
+    c->overflow = 0;
+    if (set_pool) c->pool_tail = pool_tail;
+}
+__global__ void k_set_F(Ctl* c) {
+    if (threadIdx.x < 6) c->F[threadIdx.x] = (unsigned long long)c->Ca[threadIdx.x];
+}
+}  // namespace gcx
+
+// ---------------------------------------------------------------------------
+// pipeline pieces
+// ---------------------------------------------------------------------------
+static int plan_region_buffers(gc_graph* g, long long n_ins) {
+    size_t ucap = (size_t)(2 * g->m + 2 * n_ins + 64);
+    if (!ensure(g, g->U_col, ucap)) return nomem(g, "region adjacency");
+    if (!ensure(g, g->tpack, ucap)) return nomem(g, "triangle counters");
+    return GC_OK;
+}
+
+// U build + counting + closed forms. mode: 0 batch, 1 static, 2 static that sets F
+static int count_region(gc_graph* g, int mode) {
+    cudaStream_t s = g->s;
+    int gw = grid_warps(g);
+    k_reset_count<<<1, 32, 0, s>>>(g->ctl);
+    CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
+    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg);
+    scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
+    k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
+                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
+    k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
+    CK(cudaEventRecord(g->ev[3], s));
+    k_tri_k4<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p);
+    CK(cudaEventRecord(g->ev[4], s));
+    k_c4<<<g->c4_blocks, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->c4cnt.p, g->n);
+    CK(cudaEventRecord(g->ev[5], s));
+    k_edge_terms<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p, g->da, g->db);
+    k_finalize<<<1, 32, 0, s>>>(g->ctl, mode == 0 ? 0 : 1);
+    if (mode == 2) k_set_F<<<1, 32, 0, s>>>(g->ctl);
+    CK(cudaEventRecord(g->ev[6], s));
+    CKL();
+    return GC_OK;
+}
+
+static int enqueue_commit(gc_graph* g) {
+    cudaStream_t s = g->s;
+    int gw = grid_warps(g);
+    k_commit_plan<<<grid_elems(g, std::max<long long>(g->keys.cap, 1)), TPB, 0, s>>>(
+        g->ctl, g->wlist, g->segA, g->segD, g->deg, g->cap, g->row_start, g->col_capacity, g->slack,
+        g->plan_dst.p, g->plan_cap.p, g->plan_deg.p, g->plan_scr.p);
+    // the region adjacency buffer is free again and is large enough for every
+    // rewritten row: use it as the merge scratch
+    k_commit_merge<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->segA, g->segD, g->dstA.p, g->dstD.p, g->deg, g->row_start,
+                                      g->col, g->plan_scr.p, g->U_col.p);
+    k_commit_write<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->plan_dst.p, g->plan_cap.p, g->plan_deg.p,
+                                      g->plan_scr.p, g->U_col.p, g->deg, g->cap, g->row_start, g->col);
+    CKL();
+    return GC_OK;
+}
+
+static int enqueue_clear_segments(gc_graph* g) {
+    int ge = grid_elems(g, std::max<long long>(g->keys.cap, 1));
+    k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+    k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+    CKL();
+    return GC_OK;
+}
+
+// Re-lay every row with fresh slack; the pool beyond the rows gets
+// pool_extra slots more than the usual slack share.
+static int relayout(gc_graph* g, long long pool_extra) {
+    cudaStream_t s = g->s;
+    int n = g->n;
+    long long* new_start = (long long*)dalloc(g, sizeof(long long) * (size_t)(n + 1));
+    if (!new_start) return nomem(g, "row offsets");
+    k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
+    scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, new_start + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    long long pool = std::max<long long>((long long)(total * g->slack), 4096) + pool_extra;
+    long long ncap = total + pool;
+    int32_t* ncol = (int32_t*)dalloc(g, sizeof(int32_t) * (size_t)ncap);
+    if (!ncol) {
+        dfree(g, new_start);
+        return nomem(g, "adjacency pool");
+    }
+    k_copy_rows<<<grid_warps(g), TPB, 0, s>>>(g->deg, n, g->row_start, g->col, new_start, ncol);
+    k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
+    CKL();
+    dfree(g, g->col);
+    dfree(g, g->row_start);
+    g->col = ncol;
+    g->row_start = new_start;
+    g->col_capacity = ncap;
+    return GC_OK;
+}
+
+static void fill_stats(gc_graph* g, const Ctl& c) {
+    gc_stats& t = g->st;
+    t.n_ins = c.nA2 / 2;
+    t.n_del = c.nD2 / 2;
+    t.repeats = (long long)c.st[0] / 2;
+    t.cancelled = (long long)c.st[1] / 2;
+    t.noop_ins = (long long)c.st[2] / 2;
+    t.noop_del = (long long)c.st[3] / 2;
+    t.region_vertices = c.nW;
+    t.region_entries = c.nU;
+    t.edges_a = (long long)c.acc[12];
+    t.edges_b = (long long)c.acc[13];
+    for (int i = 0; i < 6; i++) {
+        t.Ca[i] = c.Ca[i];
+        t.Cb[i] = c.Cb[i];
+        t.sums_a[i] = c.sa[i];
+        t.sums_b[i] = c.sb[i];
+    }
+}
+
+// One batch whose pairs are already in device memory.
+static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, const int32_t* d_del,
+                        long long n_del, int commit, uint64_t out[6]) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = g->s;
+    long long nk = 2 * (n_ins + n_del);
+    size_t nkb = (size_t)std::max<long long>(nk, 1);
+    if (!ensure(g, g->keys, nkb) || !ensure(g, g->keys_tmp, nkb) || !ensure(g, g->keepA, nkb) ||
+        !ensure(g, g->keepD, nkb) || !ensure(g, g->posA, nkb + 1) || !ensure(g, g->posD, nkb + 1) ||
+        !ensure(g, g->srcA, nkb) || !ensure(g, g->dstA, nkb) || !ensure(g, g->srcD, nkb) ||
+        !ensure(g, g->dstD, nkb) || !ensure(g, g->plan_dst, nkb) || !ensure(g, g->plan_scr, nkb) ||
+        !ensure(g, g->plan_cap, nkb) || !ensure(g, g->plan_deg, nkb))
+        return nomem(g, "batch scratch");
+    int rg = radix_grid(nk, g->sms);
+    if (!ensure(g, g->hist, (size_t)256 * rg)) return nomem(g, "sort histogram");
+    int rc = plan_region_buffers(g, n_ins);
+    if (rc) return rc;
+    g->h_desc[0] = 0;
+    g->h_desc[1] = n_ins;
+    g->h_desc[2] = 0;
+    g->h_desc[3] = n_del;
+    CK(cudaEventRecord(g->e0, s));
+    CK(cudaMemcpyAsync(g->desc, g->h_desc, 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(g->ev[0], s));
+    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, 0);
+    int ge = grid_elems(g, nkb);
+    if (nk > 0) {
+        k_batch_keys<<<grid_elems(g, n_ins + n_del), TPB, 0, s>>>(d_ins, d_del, g->ctl, g->perm, g->n, g->S,
+                                                                   g->keys.p);
+        radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nk, 2 * g->S + 1, g->hist.p, rg, s);
+        k_batch_decide<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col, g->keepA.p,
+                                          g->keepD.p);
+        int sg = scan_grid(nk, g->sms);
+        scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
+        scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
+        k_batch_compact<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p, g->posA.p, g->posD.p,
+                                           g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
+        k_batch_segments<<<ge, TPB, 0, s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+        k_batch_segments<<<ge, TPB, 0, s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+    }
+    CK(cudaEventRecord(g->ev[1], s));
+    CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+    k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
+    k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
+    for (int L = 1; L <= g->hops; L++) {
+        k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
+        k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
+    }
+    CKL();
+    CK(cudaEventRecord(g->ev[2], s));
+    rc = count_region(g, 0);
+    if (rc) return rc;
+    if (commit) {
+        rc = enqueue_commit(g);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(g->ev[7], s));
+    CK(cudaEventRecord(g->e1, s));
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Ctl c = *g->h_ctl;
+    int relayouts = 0;
+    if (c.err) {
+        enqueue_clear_segments(g);
+        CK(cudaStreamSynchronize(s));
+        g->err = "batch rejected on the device: a pair is a self-loop or names a vertex outside [0, n)";
+        return GC_EINVAL;
+    }
+    while (commit && c.overflow) {
+        // the rows were not touched; grow the pool and commit again
+        long long extra = 4 * (c.nA2 + c.nD2) + 1024;
+        for (int i = 0; i < relayouts; i++) extra *= 2;
+        rc = relayout(g, extra);
+        if (rc) return rc;
+        relayouts++;
+        rc = enqueue_commit(g);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        c = *g->h_ctl;
+        if (relayouts > 4) {
+            g->err = "adjacency pool could not be grown enough";
+            return GC_ENOMEM;
+        }
+    }
+    rc = enqueue_clear_segments(g);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->e0, g->e1);
+    fill_stats(g, c);
+    g->st.n_ins_raw = n_ins;
+    g->st.n_del_raw = n_del;
+    g->st.ms_device = ms;
+    g->st.relayouts = relayouts;
+    {
+        // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
+        // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
+        for (int i = 0; i < 7; i++) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]);
+            g->st.ms_stage[i] = x;
+        }
+        g->st.ms_stage[7] = 0.f;
+    }
+    uint64_t res[6];
+    for (int i = 0; i < 6; i++) res[i] = (uint64_t)c.F[i] + (commit ? 0ull : (uint64_t)(c.Ca[i] - c.Cb[i]));
+    if (commit) {
+        for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
+        g->m += c.nA2 / 2 - c.nD2 / 2;
+    } else {
+        // independent batch: restore the maintained counts on the device
+        CK(cudaMemcpyAsync(g->ctl->F, g->F, sizeof(g->F), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < 6; i++) res[i] = g->F[i] + (uint64_t)(c.Ca[i] - c.Cb[i]);
+    }
+    g->st.num_edges = g->m;
+    if (out)
+        for (int i = 0; i < 6; i++) out[i] = res[i];
+    g->st.ms_wall =
+        std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return GC_OK;
+}
+
+static int count_static(gc_graph* g, int mode, uint64_t out[6]) {
+    cudaStream_t s = g->s;
+    int rc = plan_region_buffers(g, 0);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->visited, 0xFF, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+    k_region_all<<<grid_elems(g, g->n), TPB, 0, s>>>(g->ctl, g->n, g->wlist);
+    CKL();
+    CK(cudaEventRecord(g->ev[2], s));
+    rc = count_region(g, mode);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // a static count leaves its stage times in the stats record
+    for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
+    for (int i = 2; i < 6; i++) cudaEventElapsedTime(&g->st.ms_stage[i], g->ev[i], g->ev[i + 1]);
+    cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]);
+    fill_stats(g, *g->h_ctl);
+    if (out)
+        for (int i = 0; i < 6; i++) out[i] = (uint64_t)g->h_ctl->Ca[i];
+    if (mode == 2)
+        for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
+    return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// open / close
+// ---------------------------------------------------------------------------
+static void destroy(gc_graph* g) {
+    if (!g) return;
+    if (g->s) cudaStreamSynchronize(g->s);
+    int32_t* p32[] = {g->perm, g->iperm, g->deg, g->cap, g->col, g->wlist, g->U_deg, g->U_split, g->da, g->db};
+    for (auto p : p32) dfree(g, p);
+    dfree(g, g->row_start);
+    dfree(g, g->U_off);
+    dfree(g, g->ctl);
+    dfree(g, g->desc);
+    dfree(g, g->segA);
+    dfree(g, g->segD);
+    dfree(g, g->visited);
+    release(g, g->U_col);
+    release(g, g->tpack);
+    release(g, g->keys);
+    release(g, g->keys_tmp);
+    release(g, g->keepA);
+    release(g, g->keepD);
+    release(g, g->srcA);
+    release(g, g->dstA);
+    release(g, g->srcD);
+    release(g, g->dstD);
+    release(g, g->plan_cap);
+    release(g, g->plan_deg);
+    release(g, g->pairs);
+    release(g, g->posA);
+    release(g, g->posD);
+    release(g, g->plan_dst);
+    release(g, g->plan_scr);
+    release(g, g->bsum);
+    release(g, g->hist);
+    release(g, g->c4cnt);
+    if (g->s) cudaStreamSynchronize(g->s);
+    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    if (g->h_desc) cudaFreeHost(g->h_desc);
+    if (g->e0) cudaEventDestroy(g->e0);
+    for (auto e : g->ev)
+        if (e) cudaEventDestroy(e);
+    if (g->e1) cudaEventDestroy(g->e1);
+    if (g->own_stream && g->s) cudaStreamDestroy(g->s);
+    delete g;
+}
+
+static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh) {
+    const int n = g->n;
+    const long long m2 = n > 0 ? row_ptr[n] : 0;
+    cudaStream_t s = g->s;
+    size_t nn = (size_t)std::max(n, 1);
+    g->perm = (int32_t*)dalloc(g, 4 * nn);
+    g->iperm = (int32_t*)dalloc(g, 4 * nn);
+    g->deg = (int32_t*)dalloc(g, 4 * nn);
+    g->cap = (int32_t*)dalloc(g, 4 * nn);
+    g->wlist = (int32_t*)dalloc(g, 4 * nn);
+    g->U_deg = (int32_t*)dalloc(g, 4 * nn);
+    g->U_split = (int32_t*)dalloc(g, 4 * nn);
+    g->da = (int32_t*)dalloc(g, 4 * nn);
+    g->db = (int32_t*)dalloc(g, 4 * nn);
+    g->row_start = (long long*)dalloc(g, 8 * (nn + 1));
+    g->U_off = (long long*)dalloc(g, 8 * (nn + 1));
+    g->ctl = (Ctl*)dalloc(g, sizeof(Ctl));
+    g->desc = (long long*)dalloc(g, 16 * sizeof(long long));
+    g->segA = (int2*)dalloc(g, sizeof(int2) * nn);
+    g->segD = (int2*)dalloc(g, sizeof(int2) * nn);
+    g->visited = (uint32_t*)dalloc(g, 4 * ((nn + 31) / 32 + 1));
+    if (!g->perm || !g->iperm || !g->deg || !g->cap || !g->wlist || !g->U_deg || !g->U_split || !g->da || !g->db ||
+        !g->row_start || !g->U_off || !g->ctl || !g->desc || !g->segA || !g->segD || !g->visited)
+        return nomem(g, "graph state");
+    int sgn = scan_grid(std::max<long long>(n, m2), g->sms);
+    if (!ensure(g, g->bsum, 1024)) return nomem(g, "scan scratch");
+    (void)sgn;
+    CK(cudaMemsetAsync(g->segA, 0, sizeof(int2) * nn, s));
+    CK(cudaMemsetAsync(g->segD, 0, sizeof(int2) * nn, s));
+    Ctl zero{};
+    *g->h_ctl = zero;
+    CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+
+    // temporaries of the open
+    int32_t* d_rp = (int32_t*)dalloc(g, 4 * (nn + 1));
+    int32_t* d_col = (int32_t*)dalloc(g, 4 * (size_t)std::max<long long>(m2, 1));
+    int32_t* deg0 = (int32_t*)dalloc(g, 4 * nn);
+    long long* key_off = (long long*)dalloc(g, 8 * (nn + 1));
+    int* bad = (int*)dalloc(g, sizeof(int));
+    size_t kcount = (size_t)std::max<long long>(std::max<long long>(m2, n), 1);
+    uint64_t* k1 = (uint64_t*)dalloc(g, 8 * kcount);
+    uint64_t* k2 = (uint64_t*)dalloc(g, 8 * kcount);
+    int rg = radix_grid((long long)kcount, g->sms);
+    if (!d_rp || !d_col || !deg0 || !key_off || !bad || !k1 || !k2 || !ensure(g, g->hist, (size_t)256 * rg)) {
+        dfree(g, d_rp); dfree(g, d_col); dfree(g, deg0); dfree(g, key_off); dfree(g, bad); dfree(g, k1); dfree(g, k2);
+        return nomem(g, "open scratch");
+    }
+    int rc = GC_OK;
+    do {
+        if (n > 0) {
+            if (cudaMemcpyAsync(d_rp, row_ptr, 4 * (size_t)(n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                (m2 > 0 && cudaMemcpyAsync(d_col, colh, 4 * (size_t)m2, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+                g->err = "copying the CSR to the device failed";
+                rc = GC_ECUDA;
+                break;
+            }
+        }
+        if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { rc = GC_ECUDA; break; }
+        // internal order: ascending initial degree, ties by id
+        long long maxdeg = 0;
+        for (int v = 0; v < n; v++) maxdeg = std::max<long long>(maxdeg, (long long)row_ptr[v + 1] - row_ptr[v]);
+        g->h_desc[8] = n;
+        g->h_desc[9] = m2;
+        if (cudaMemcpyAsync(g->desc + 8, g->h_desc + 8, 2 * sizeof(long long), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) { rc = GC_ECUDA; break; }
+        if (n > 0) {
+            k_degree_keys<<<grid_elems(g, n), TPB, 0, s>>>(d_rp, n, deg0, k1);
+            radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
+            k_perm_from_keys<<<grid_elems(g, n), TPB, 0, s>>>(k1, n, g->perm, g->iperm, deg0, g->deg);
+        }
+        if (m2 > 0) {
+            k_edge_keys<<<grid_warps(g), TPB, 0, s>>>(d_rp, d_col, n, g->perm, g->S, k1, bad);
+            radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
+        }
+        if (n > 0) {
+            scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+            k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
+            scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+        }
+        long long total = 0;
+        if (n > 0 &&
+            cudaMemcpyAsync(&total, g->row_start + n, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            rc = GC_ECUDA;
+            break;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            g->err = std::string("open: ") + cudaGetErrorString(cudaGetLastError());
+            rc = GC_ECUDA;
+            break;
+        }
+        long long pool = std::max<long long>((long long)(total * g->slack), 4096);
+        g->col_capacity = total + pool;
+        g->col = (int32_t*)dalloc(g, 4 * (size_t)g->col_capacity);
+        if (!g->col) { rc = nomem(g, "adjacency"); break; }
+        if (m2 > 0)
+            k_fill_from_keys<<<grid_elems(g, m2), TPB, 0, s>>>(k1, m2, n, g->S, key_off, g->row_start, g->col, bad);
+        k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
+        int hbad = 0;
+        if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            g->err = std::string("open: ") + cudaGetErrorString(cudaGetLastError());
+            rc = GC_ECUDA;
+            break;
+        }
+        if (hbad) {
+            g->err = hbad == 1 ? "CSR has a self-loop or a neighbour outside [0, n)"
+                     : hbad == 2 ? "CSR has a repeated entry in a row"
+                                 : "CSR is not symmetric";
+            rc = GC_EINVAL;
+            break;
+        }
+    } while (0);
+    cudaStreamSynchronize(s);
+    dfree(g, d_rp); dfree(g, d_col); dfree(g, deg0); dfree(g, key_off); dfree(g, bad); dfree(g, k1); dfree(g, k2);
+    if (rc) return rc;
+    g->m = m2 / 2;
+    // 4-cycle counters: one dense array of n words per resident block
+    g->c4_blocks = std::max(1, std::min(2 * g->sms, 1024));
+    size_t c4words = (size_t)g->c4_blocks * nn;
+    if (!ensure(g, g->c4cnt, c4words)) return nomem(g, "4-cycle counters");
+    CK(cudaMemsetAsync(g->c4cnt.p, 0, 8 * g->c4cnt.cap, s));
+    return count_static(g, 2, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void gc_default_options(gc_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->region_hops = 3;
+    opt->slack = 0.25f;
+}
+
+int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_options* opt, gc_graph** out) {
+    t_open_error.clear();
+    if (!out) {
+        t_open_error = "out is NULL";
+        return GC_EINVAL;
+    }
+    *out = nullptr;
+    if (n < 0 || n >= (1 << 30)) {
+        t_open_error = "n must be in [0, 2^30)";
+        return GC_EINVAL;
+    }
+    if (n > 0 && !row_ptr) {
+        t_open_error = "row_ptr is NULL";
+        return GC_EINVAL;
+    }
+    if (n > 0) {
+        if (row_ptr[0] != 0) {
+            t_open_error = "row_ptr[0] must be 0";
+            return GC_EINVAL;
+        }
+        for (int v = 0; v < n; v++)
+            if (row_ptr[v + 1] < row_ptr[v]) {
+                t_open_error = "row_ptr must be non-decreasing";
+                return GC_EINVAL;
+            }
+        if (row_ptr[n] > 0 && !col) {
+            t_open_error = "col is NULL";
+            return GC_EINVAL;
+        }
+        if (row_ptr[n] % 2) {
+            t_open_error = "CSR of an undirected graph has an even number of entries";
+            return GC_EINVAL;
+        }
+    }
+    gc_options o;
+    gc_default_options(&o);
+    if (opt) {
+        o = *opt;
+        if (o.region_hops == 0) o.region_hops = 3;
+        if (o.slack <= 0.f) o.slack = 0.25f;
+    }
+    if (o.region_hops < 2 || o.region_hops > MAX_HOPS) {
+        t_open_error = "region_hops must be in [2, 8]";
+        return GC_EINVAL;
+    }
+    if ((o.alloc == nullptr) != (o.free == nullptr)) {
+        t_open_error = "alloc and free callbacks come together";
+        return GC_EINVAL;
+    }
+    gc_graph* g = new gc_graph();
+    g->opt = o;
+    g->n = n;
+    g->S = std::max(1, bitlen(n > 0 ? n - 1 : 0));
+    g->hops = o.region_hops;
+    g->slack = o.slack;
+    int rc = GC_OK;
+    do {
+        if (o.device > 0 && cudaSetDevice(o.device) != cudaSuccess) {
+            t_open_error = "cudaSetDevice failed";
+            rc = GC_ECUDA;
+            break;
+        }
+        if (cudaGetDevice(&g->dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess) {
+            t_open_error = std::string("no usable CUDA device: ") + cudaGetErrorString(cudaGetLastError());
+            rc = GC_ECUDA;
+            break;
+        }
+        if (o.stream) {
+            g->s = (cudaStream_t)o.stream;
+        } else {
+            if (cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking) != cudaSuccess) {
+                t_open_error = "cudaStreamCreate failed";
+                rc = GC_ECUDA;
+                break;
+            }
+            g->own_stream = true;
+        }
+        if (cudaMallocHost((void**)&g->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+            cudaMallocHost((void**)&g->h_desc, 16 * sizeof(long long)) != cudaSuccess ||
+            cudaEventCreate(&g->e0) != cudaSuccess || cudaEventCreate(&g->e1) != cudaSuccess ||
+            [&] {
+                for (auto& e : g->ev)
+                    if (cudaEventCreate(&e) != cudaSuccess) return true;
+                return false;
+            }()) {
+            t_open_error = "host allocation failed";
+            rc = GC_ENOMEM;
+            break;
+        }
+        rc = open_device(g, row_ptr, col);
+        if (rc) t_open_error = g->err;
+    } while (0);
+    if (rc) {
+        destroy(g);
+        return rc;
+    }
+    *out = g;
+    return GC_OK;
+}
+
+int gc_count_static(gc_graph* g, uint64_t out[6]) {
+    if (!g || !out) return GC_EINVAL;
+    g->err.clear();
+    return count_static(g, 1, out);
+}
+
+int gc_counts(const gc_graph* g, uint64_t out[6]) {
+    if (!g || !out) return GC_EINVAL;
+    for (int i = 0; i < 6; i++) out[i] = g->F[i];
+    return GC_OK;
+}
+
+int gc_apply_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t* del, int64_t n_del,
+                   uint64_t out[6]) {
+    if (!g) return GC_EINVAL;
+    auto t0 = std::chrono::steady_clock::now();
+    g->err.clear();
+    if (n_ins < 0 || n_del < 0 || (n_ins > 0 && !ins) || (n_del > 0 && !del)) {
+        g->err = "batch arrays: negative size or NULL pointer";
+        return GC_EINVAL;
+    }
+    if (n_ins + n_del > (1LL << 29)) {
+        g->err = "batch too large";
+        return GC_EINVAL;
+    }
+    for (int64_t i = 0; i < n_ins; i++) {
+        int32_t a = ins[2 * i], b = ins[2 * i + 1];
+        if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) {
+            g->err = "insertion " + std::to_string(i) + " is a self-loop or names a vertex outside [0, n)";
+            return GC_EINVAL;
+        }
+    }
+    for (int64_t i = 0; i < n_del; i++) {
+        int32_t a = del[2 * i], b = del[2 * i + 1];
+        if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) {
+            g->err = "deletion " + std::to_string(i) + " is a self-loop or names a vertex outside [0, n)";
+            return GC_EINVAL;
+        }
+    }
+    size_t np = (size_t)(n_ins + n_del);
+    if (!ensure(g, g->pairs, 2 * std::max<size_t>(np, 1))) return nomem(g, "batch staging");
+    if (n_ins) CK(cudaMemcpyAsync(g->pairs.p, ins, 8 * (size_t)n_ins, cudaMemcpyHostToDevice, g->s));
+    if (n_del) CK(cudaMemcpyAsync(g->pairs.p + 2 * n_ins, del, 8 * (size_t)n_del, cudaMemcpyHostToDevice, g->s));
+    int rc = apply_device(g, g->pairs.p, n_ins, g->pairs.p + 2 * n_ins, n_del, 1, out);
+    g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int gc_apply_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
+                          uint64_t out[6]) {
+    if (!g) return GC_EINVAL;
+    g->err.clear();
+    if (n_ins < 0 || n_del < 0 || (n_ins > 0 && !d_ins) || (n_del > 0 && !d_del) || n_ins + n_del > (1LL << 29)) {
+        g->err = "batch arrays: bad size or NULL pointer";
+        return GC_EINVAL;
+    }
+    return apply_device(g, d_ins, n_ins, d_del, n_del, 1, out);
+}
+
+int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_ins, const int32_t* const* del,
+                     const int64_t* n_del, int32_t k, int32_t independent, uint64_t* out) {
+    if (!g || k < 0 || (k > 0 && (!n_ins || !n_del || !ins || !del))) return GC_EINVAL;
+    g->err.clear();
+    for (int32_t i = 0; i < k; i++) {
+        if (independent) {
+            // validate like gc_apply_batch, then count without committing
+            int64_t ni = n_ins[i], nd = n_del[i];
+            if (ni < 0 || nd < 0 || (ni > 0 && !ins[i]) || (nd > 0 && !del[i])) return GC_EINVAL;
+            for (int64_t j = 0; j < ni; j++) {
+                int32_t a = ins[i][2 * j], b = ins[i][2 * j + 1];
+                if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return GC_EINVAL;
+            }
+            for (int64_t j = 0; j < nd; j++) {
+                int32_t a = del[i][2 * j], b = del[i][2 * j + 1];
+                if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return GC_EINVAL;
+            }
+            size_t np = (size_t)(ni + nd);
+            if (!ensure(g, g->pairs, 2 * std::max<size_t>(np, 1))) return nomem(g, "batch staging");
+            if (ni) CK(cudaMemcpyAsync(g->pairs.p, ins[i], 8 * (size_t)ni, cudaMemcpyHostToDevice, g->s));
+            if (nd) CK(cudaMemcpyAsync(g->pairs.p + 2 * ni, del[i], 8 * (size_t)nd, cudaMemcpyHostToDevice, g->s));
+            int rc = apply_device(g, g->pairs.p, ni, g->pairs.p + 2 * ni, nd, 0, out ? out + 6 * i : nullptr);
+            if (rc) return rc;
+        } else {
+            int rc = gc_apply_batch(g, ins[i], n_ins[i], del[i], n_del[i], out ? out + 6 * i : nullptr);
+            if (rc) return rc;
+        }
+    }
+    return GC_OK;
+}
+
+int gc_batch_stats(const gc_graph* g, gc_stats* s) {
+    if (!g || !s) return GC_EINVAL;
+    *s = g->st;
+    return GC_OK;
+}
+
+int64_t gc_num_edges(const gc_graph* g) { return g ? g->m : -1; }
+
+int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
+    if (!g || !row_ptr || (g->m > 0 && !col)) return GC_EINVAL;
+    int n = g->n;
+    std::vector<int32_t> deg(n), iperm(n);
+    std::vector<long long> rs(n);
+    std::vector<int32_t> hc((size_t)g->col_capacity);
+    CK(cudaStreamSynchronize(g->s));
+    if (n > 0) {
+        CK(cudaMemcpy(deg.data(), g->deg, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(iperm.data(), g->iperm, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rs.data(), g->row_start, 8 * (size_t)n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hc.data(), g->col, 4 * (size_t)g->col_capacity, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int32_t> ext_deg(n);
+    for (int i = 0; i < n; i++) ext_deg[iperm[i]] = deg[i];
+    row_ptr[0] = 0;
+    for (int x = 0; x < n; x++) row_ptr[x + 1] = row_ptr[x] + ext_deg[x];
+    for (int i = 0; i < n; i++) {
+        int32_t x = iperm[i];
+        int32_t* o = col + row_ptr[x];
+        for (int j = 0; j < deg[i]; j++) o[j] = iperm[hc[(size_t)rs[i] + j]];
+        std::sort(o, o + deg[i]);
+    }
+    return GC_OK;
+}
+
+const char* gc_last_error(const gc_graph* g) { return g ? g->err.c_str() : t_open_error.c_str(); }
+
+void gc_close(gc_graph* g) { destroy(g); }
+
+}  // extern "C"

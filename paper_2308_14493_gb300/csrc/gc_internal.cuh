@@ -1,0 +1,160 @@
+// gc_internal.cuh -- shared definitions of the CUDA graphlet-counting library.
+//
+// Vertex numbering.  The library renumbers vertices once, at open, in
+// ascending order of their initial degree (ties by id).  Every adjacency row
+// is kept sorted by this internal id, and each edge is oriented from its
+// lower to its higher internal id.  Any total order gives exact counts; the
+// degree order keeps out-lists short (hubs point to few vertices).
+//
+// Region union graph U.  For a batch B = A u D (Algorithm 2, Sec. 4.3) the
+// region is W, the k-hop neighbourhood of the batch endpoints.  G_a and G_b
+// share every edge of G[W] except the batch pairs, so both are stored as one
+// adjacency structure U = G[W] u A whose entries carry two membership bits:
+//   FLAG_A  the edge is in G_a = (H \ D) u A  (every entry except D pairs)
+//   FLAG_B  the edge is in G_b = (H \ A) u D  (every entry except A pairs)
+// One pass over U then counts both graphs.  A full static count is the
+// special case W = V, no batch, both bits on every entry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gcx {
+
+constexpr uint32_t ID_MASK = 0x3FFFFFFFu;  // vertex id (n < 2^30)
+constexpr uint32_t FLAG_A = 0x40000000u;   // entry belongs to G_a
+constexpr uint32_t FLAG_B = 0x80000000u;   // entry belongs to G_b
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int MAX_HOPS = 8;
+
+// Device control block: sizes produced and consumed on the device, so a
+// batch's kernels never wait for the host between stages.
+struct Ctl {
+    long long n_ins, n_del;          // raw pairs of the batch
+    long long nkeys;                 // directed batch keys = 2 (n_ins + n_del)
+    long long nA2, nD2;              // kept directed insertion / deletion entries
+    unsigned long long st[8];        // [0] repeats [1] cancelled [2] no-op ins [3] no-op del (directed)
+    int nW;                          // region size
+    int lvl[MAX_HOPS + 2];           // lvl[L]: end of BFS level L in the region list
+    long long nU;                    // entries of the region union graph
+    unsigned long long acc[16];      // [0..5] sums of G_a, [6..11] sums of G_b: P, S, 2TT, D, K, Q
+                                     // [12] |E(G_a)|, [13] |E(G_b)|
+    unsigned long long F[6];         // maintained counts
+    long long Ca[6], Cb[6];          // induced counts of G_a, G_b of the last pass
+    long long sa[6], sb[6];          // their non-induced sums (TT halved)
+    unsigned long long pool_tail;    // first free column slot of the adjacency pool
+    unsigned long long scratch_tail; // bump pointer of the commit scratch
+    int overflow;                    // commit needs a re-layout
+    int err;                         // GC_E* code raised on the device
+    unsigned work[8];                // dynamic work counters
+};
+
+// Handle-independent launch geometry.
+struct Dims {
+    int sms;
+};
+
+__device__ __forceinline__ uint32_t vid(uint32_t e) { return e & ID_MASK; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
+    return x;
+}
+
+// first index in sorted a[0..len) whose id is >= key
+__device__ __forceinline__ long long lower_bound_id(const uint32_t* a, long long len, uint32_t key) {
+    long long lo = 0, hi = len;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if ((a[mid] & ID_MASK) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ long long lower_bound_i32(const int32_t* a, long long len, int32_t key) {
+    long long lo = 0, hi = len;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long choose2(unsigned long long x) { return x * (x - 1) / 2; }
+__device__ __forceinline__ unsigned long long choose3(unsigned long long x) {
+    return x < 3 ? 0ull : x * (x - 1) / 2 * (x - 2) / 3;
+}
+
+// Warp-cooperative merge of one sorted adjacency row with a sorted list of
+// insertions (ids absent from the row).  Row entries failing keep(v) are
+// dropped; kept ones are written as v | tag(v); insertions as a | ins_tag.
+// The output is sorted by id.  All 32 lanes must call it together.
+// Returns the number of entries written.
+template <class KeepF, class TagF>
+__device__ __forceinline__ long long warp_merge_row(const int32_t* __restrict__ row, long long d,
+                                                    const int32_t* __restrict__ ins, long long na,
+                                                    uint32_t* __restrict__ out, uint32_t ins_tag, KeepF keep,
+                                                    TagF tag) {
+    const int lane = threadIdx.x & 31;
+    long long obase = 0, ia = 0;
+    for (long long cb = 0; cb < d; cb += 32) {
+        long long idx = cb + lane;
+        bool valid = idx < d;
+        int32_t v = valid ? row[idx] : 0x7fffffff;
+        bool kp = valid && keep(v);
+        unsigned km = __ballot_sync(FULL, kp);
+        int32_t vlast = row[(cb + 31 < d - 1) ? cb + 31 : d - 1];
+        long long ib = ia;
+        for (;;) {  // insertions in [ia, na) below vlast form a prefix
+            long long j = ib + lane;
+            unsigned m = __ballot_sync(FULL, j < na && ins[j] < vlast);
+            ib += __popc(m);
+            if (m != FULL) break;
+        }
+        if (kp) {
+            long long lb = lower_bound_i32(ins + ia, ib - ia, v);
+            out[obase + __popc(km & lanemask_lt()) + lb] = (uint32_t)v | tag(v);
+        }
+        for (long long j = ia; j < ib; j++) {
+            int32_t a = ins[j];
+            unsigned below = __ballot_sync(FULL, kp && v < a);
+            if (lane == 0) out[obase + (j - ia) + __popc(below)] = (uint32_t)a | ins_tag;
+        }
+        obase += __popc(km) + (ib - ia);
+        ia = ib;
+    }
+    for (long long j = ia + lane; j < na; j += 32) out[obase + (j - ia)] = (uint32_t)ins[j] | ins_tag;
+    return obase + (na - ia);
+}
+
+__device__ __forceinline__ bool sorted_contains(const int32_t* a, long long len, int32_t key) {
+    long long p = lower_bound_i32(a, len, key);
+    return p < len && a[p] == key;
+}
+
+// ---- host-side launchers implemented in the .cu files -------------------
+
+// gc_sort.cu
+// Sort `keys` (uint64) of device-resident length *d_count (<= max_count) by
+// their low `bits` bits.  `tmp` holds max_count keys; `hist` holds 256 * grid
+// words.  The sorted keys end in `keys`.
+void radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long long max_count, int bits,
+                    uint32_t* hist, int grid, cudaStream_t s);
+int radix_grid(long long max_count, int sms);
+// Exclusive prefix sum of int32 in[0..len) into int64 out[0..len], out[len] = total.
+// len = *d_len when d_len != null, else host_len.  `bsum` holds `grid` int64.
+// If total_out != null the total is also stored there.
+void scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len,
+                     long long* bsum, int grid, long long* total_out, cudaStream_t s);
+int scan_grid(long long max_len, int sms);
+
+}  // namespace gcx

@@ -1,0 +1,69 @@
+// gc_kernels.cuh -- declarations of the kernels, for the launchers in gc_api.cu.
+#pragma once
+
+#include "gc_internal.cuh"
+
+namespace gcx {
+
+// gc_batch.cu
+__global__ void k_batch_keys(const int32_t* ins, const int32_t* del, Ctl* c, const int32_t* perm, int n, int S,
+                             uint64_t* keys);
+__global__ void k_batch_decide(const uint64_t* keys, Ctl* c, int S, const long long* row_start, const int32_t* deg,
+                               const int32_t* col, int32_t* keepA, int32_t* keepD);
+__global__ void k_batch_compact(const uint64_t* keys, const Ctl* c, int S, const int32_t* keepA,
+                                const int32_t* keepD, const long long* posA, const long long* posD, int32_t* srcA,
+                                int32_t* dstA, int32_t* srcD, int32_t* dstD);
+__global__ void k_batch_segments(const int32_t* src, const long long* d_len, int2* seg);
+__global__ void k_batch_clear_segments(const int32_t* src, const long long* d_len, int2* seg);
+__global__ void k_commit_plan(Ctl* c, const int32_t* wlist, const int2* segA, const int2* segD, const int32_t* deg,
+                              const int32_t* cap, const long long* row_start, long long col_capacity, float slack,
+                              long long* plan_dst, int32_t* plan_cap, int32_t* plan_deg, long long* plan_scr);
+__global__ void k_commit_merge(const Ctl* c, const int32_t* wlist, const int2* segA, const int2* segD,
+                               const int32_t* dstA, const int32_t* dstD, const int32_t* deg,
+                               const long long* row_start, const int32_t* col, const long long* plan_scr,
+                               uint32_t* scratch);
+__global__ void k_commit_write(const Ctl* c, const int32_t* wlist, const long long* plan_dst,
+                               const int32_t* plan_cap, const int32_t* plan_deg, const long long* plan_scr,
+                               const uint32_t* scratch, int32_t* deg, int32_t* cap, long long* row_start,
+                               int32_t* col);
+__global__ void k_slack_caps(const int32_t* deg, int n, float slack, int32_t* cap);
+__global__ void k_copy_rows(const int32_t* deg, int n, const long long* old_start, const int32_t* old_col,
+                            const long long* new_start, int32_t* new_col);
+__global__ void k_degree_keys(const int32_t* rp, int n, int32_t* deg0, uint64_t* keys);
+__global__ void k_perm_from_keys(const uint64_t* keys, int n, int32_t* perm, int32_t* iperm, const int32_t* deg0,
+                                 int32_t* deg);
+__global__ void k_edge_keys(const int32_t* rp, const int32_t* col, int n, const int32_t* perm, int S,
+                            uint64_t* keys, int* bad);
+__global__ void k_fill_from_keys(const uint64_t* keys, long long m2, int n, int S, const long long* key_off,
+                                 const long long* row_start, int32_t* col, int* bad);
+__global__ void k_export_rows(const int32_t* deg, int n, const long long* row_start, const int32_t* col,
+                              const int32_t* perm, const long long* out_off_ext, const int32_t* iperm,
+                              int32_t* out_col);
+__global__ void k_ext_degrees(const int32_t* deg, const int32_t* iperm, int n, int32_t* ext_deg);
+
+// gc_region.cu
+__global__ void k_bfs_sources(Ctl* c, const int32_t* srcA, const int32_t* srcD, uint32_t* visited, int32_t* wlist);
+__global__ void k_level_mark(Ctl* c, int L);
+__global__ void k_bfs_expand(Ctl* c, int L, const long long* row_start, const int32_t* deg, const int32_t* col,
+                             uint32_t* visited, int32_t* wlist);
+__global__ void k_region_all(Ctl* c, int n, int32_t* wlist);
+__global__ void k_u_count(const Ctl* c, const int32_t* wlist, const uint32_t* visited, const long long* row_start,
+                          const int32_t* deg, const int32_t* col, const int2* segA, int32_t* U_deg);
+__global__ void k_u_fill(const Ctl* c, const int32_t* wlist, const uint32_t* visited, const long long* row_start,
+                         const int32_t* deg, const int32_t* col, const int2* segA, const int2* segD,
+                         const int32_t* dstA, const int32_t* dstD, const long long* U_off, uint32_t* U_col,
+                         int32_t* U_split, int32_t* da, int32_t* db);
+
+// gc_count.cu
+__global__ void k_reset_count(Ctl* c);
+__global__ void k_zero_u64(unsigned long long* a, const long long* d_len);
+__global__ void k_tri_k4(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
+                         const int32_t* U_split, unsigned long long* tpack);
+__global__ void k_c4(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
+                     const int32_t* U_split, unsigned long long* cnt_all, int n);
+__global__ void k_edge_terms(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
+                             const int32_t* U_split, const unsigned long long* tpack, const int32_t* da,
+                             const int32_t* db);
+__global__ void k_finalize(Ctl* c, int mode);
+
+}  // namespace gcx

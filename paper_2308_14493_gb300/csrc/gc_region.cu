@@ -1,0 +1,143 @@
+// gc_region.cu -- the region of change (step a1) and the flagged region
+// union graph (step a2).
+//
+// Region.  W is every vertex within k hops of a batch endpoint (Sec. 4.2:
+// a 4-vertex graphlet has diameter at most 3; Algorithm 2 takes the k-hop
+// neighbourhood of each changed pair).  The walk starts from all endpoints at
+// once, level by level, over a vertex bitmap; each level appends the newly
+// reached vertices to the region list, so level L occupies
+// wlist[lvl[L-1] .. lvl[L]).  Every inserted or deleted pair joins two
+// depth-0 vertices, so walking G alone reaches exactly what walking G u A does.
+//
+// Union graph.  Row u of U lists N(u) n W plus the insertions A_u, sorted by
+// id, each entry tagged FLAG_A / FLAG_B (membership in G_a / G_b).  d_a(u)
+// and d_b(u) are the degrees inside G_a and G_b (region-induced, as the
+// counts of Algorithm 2 are taken in those graphs), and split(u) is the
+// first position whose id exceeds u: the out-list N+(u).
+#include "gc_internal.cuh"
+#include "gc_kernels.cuh"
+
+namespace gcx {
+
+__device__ __forceinline__ bool in_region(const uint32_t* visited, int32_t v) {
+    return (visited[v >> 5] >> (v & 31)) & 1u;
+}
+
+// mark v; if it was unmarked, append it to the region list (warp-aggregated)
+__device__ __forceinline__ void visit_append(bool want, int32_t v, uint32_t* visited, int32_t* wlist, Ctl* c) {
+    bool fresh = false;
+    if (want) {
+        uint32_t bit = 1u << (v & 31);
+        if (!(visited[v >> 5] & bit)) fresh = !(atomicOr(&visited[v >> 5], bit) & bit);
+    }
+    unsigned m = __ballot_sync(FULL, fresh);
+    if (m) {
+        int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&c->nW, __popc(m));
+        base = __shfl_sync(FULL, base, leader);
+        if (fresh) wlist[base + __popc(m & lanemask_lt())] = v;
+    }
+}
+
+__global__ void k_bfs_sources(Ctl* c, const int32_t* __restrict__ srcA, const int32_t* __restrict__ srcD,
+                              uint32_t* __restrict__ visited, int32_t* __restrict__ wlist) {
+    if (c->err) return;
+    long long na = c->nA2, nd = c->nD2, tot = na + nd;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // the loop bound is warp-uniform so the ballot in visit_append is safe
+    long long tot_r = (tot + 31) & ~31ll;
+    for (long long i = start; i < tot_r; i += stride) {
+        bool ok = i < tot;
+        int32_t v = ok ? (i < na ? srcA[i] : srcD[i - na]) : 0;
+        visit_append(ok, v, visited, wlist, c);
+    }
+}
+
+__global__ void k_level_mark(Ctl* c, int L) { c->lvl[L] = c->nW; }
+
+__global__ void k_bfs_expand(Ctl* c, int L, const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
+                             const int32_t* __restrict__ col, uint32_t* __restrict__ visited,
+                             int32_t* __restrict__ wlist) {
+    if (c->err) return;
+    int fb = L >= 2 ? c->lvl[L - 2] : 0;
+    int fe = c->lvl[L - 1];
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = fb + warp; i < fe; i += nwarps) {
+        int32_t x = wlist[i];
+        const int32_t* row = col + row_start[x];
+        int d = deg[x];
+        for (int b = 0; b < d; b += 32) {
+            bool ok = b + lane < d;
+            int32_t y = ok ? row[b + lane] : 0;
+            visit_append(ok, y, visited, wlist, c);
+        }
+    }
+}
+
+// static count: W = V
+__global__ void k_region_all(Ctl* c, int n, int32_t* __restrict__ wlist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wlist[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->nW = n;
+        for (int L = 0; L < MAX_HOPS + 2; L++) c->lvl[L] = n;
+    }
+}
+
+__global__ void k_u_count(const Ctl* c, const int32_t* __restrict__ wlist, const uint32_t* __restrict__ visited,
+                          const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
+                          const int32_t* __restrict__ col, const int2* __restrict__ segA,
+                          int32_t* __restrict__ U_deg) {
+    int nW = c->nW;
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        int32_t u = wlist[i];
+        const int32_t* row = col + row_start[u];
+        int d = deg[u], cnt = 0;
+        for (int b = 0; b < d; b += 32) {
+            bool ok = b + lane < d && in_region(visited, row[b + lane]);
+            cnt += __popc(__ballot_sync(FULL, ok));
+        }
+        if (lane == 0) {
+            int2 a = segA[u];
+            U_deg[u] = cnt + (a.y - a.x);
+        }
+    }
+}
+
+__global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const uint32_t* __restrict__ visited,
+                         const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
+                         const int32_t* __restrict__ col, const int2* __restrict__ segA,
+                         const int2* __restrict__ segD, const int32_t* __restrict__ dstA,
+                         const int32_t* __restrict__ dstD, const long long* __restrict__ U_off,
+                         uint32_t* __restrict__ U_col, int32_t* __restrict__ U_split, int32_t* __restrict__ da,
+                         int32_t* __restrict__ db) {
+    int nW = c->nW;
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        int32_t u = wlist[i];
+        int2 a = segA[u], d = segD[u];
+        const int32_t* dl = dstD + d.x;
+        long long nd = d.y - d.x, na = a.y - a.x;
+        uint32_t* out = U_col + U_off[u];
+        long long len = warp_merge_row(
+            col + row_start[u], deg[u], dstA + a.x, na, out, FLAG_A,
+            [&](int32_t v) { return in_region(visited, v); },
+            [&](int32_t v) { return FLAG_B | ((nd == 0 || !sorted_contains(dl, nd, v)) ? FLAG_A : 0u); });
+        __syncwarp();
+        if (lane == 0) {
+            U_split[u] = (int32_t)lower_bound_id(out, len, (uint32_t)u);
+            da[u] = (int32_t)(len - nd);
+            db[u] = (int32_t)(len - na);
+        }
+    }
+}
+
+}  // namespace gcx

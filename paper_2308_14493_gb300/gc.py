@@ -1,0 +1,238 @@
+"""Thin ctypes binding of the C ABI in include/gc.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  All work
+runs in the CUDA library ``libgc.so``; if it is missing or cannot be loaded
+the first call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GC_OK, GC_EINVAL, GC_ENOMEM, GC_ECUDA, GC_ETIMEOUT = 0, -1, -2, -3, -4
+GRAPHLETS = ("3-path", "3-star", "4-cycle", "tailed-triangle", "diamond", "4-clique")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class gc_options(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class gc_stats(ctypes.Structure):
+    _fields_ = [("n_ins_raw", ctypes.c_int64), ("n_del_raw", ctypes.c_int64), ("n_ins", ctypes.c_int64),
+                ("n_del", ctypes.c_int64), ("repeats", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("noop_ins", ctypes.c_int64), ("noop_del", ctypes.c_int64), ("region_vertices", ctypes.c_int64),
+                ("region_entries", ctypes.c_int64), ("edges_a", ctypes.c_int64), ("edges_b", ctypes.c_int64),
+                ("Ca", ctypes.c_int64 * 6), ("Cb", ctypes.c_int64 * 6), ("sums_a", ctypes.c_int64 * 6),
+                ("sums_b", ctypes.c_int64 * 6), ("num_edges", ctypes.c_int64), ("ms_device", ctypes.c_float),
+                ("ms_wall", ctypes.c_float), ("relayouts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+                ("ms_stage", ctypes.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            if name == "reserved":
+                continue
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgc.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.gc_default_options.argtypes = [ctypes.POINTER(gc_options)]
+            lib.gc_default_options.restype = None
+            lib.gc_open.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.POINTER(gc_options), ctypes.POINTER(P)]
+            lib.gc_count_static.argtypes = [P, u64p]
+            lib.gc_counts.argtypes = [P, u64p]
+            lib.gc_apply_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
+            lib.gc_apply_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
+            lib.gc_apply_batches.argtypes = [P, ctypes.POINTER(i32p), i64p, ctypes.POINTER(i32p), i64p,
+                                             ctypes.c_int32, ctypes.c_int32, u64p]
+            lib.gc_batch_stats.argtypes = [P, ctypes.POINTER(gc_stats)]
+            lib.gc_num_edges.argtypes = [P]
+            lib.gc_num_edges.restype = ctypes.c_int64
+            lib.gc_export_csr.argtypes = [P, i32p, i32p]
+            lib.gc_last_error.argtypes = [P]
+            lib.gc_last_error.restype = ctypes.c_char_p
+            lib.gc_close.argtypes = [P]
+            lib.gc_close.restype = None
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, h=None):
+    if rc != GC_OK:
+        msg = load().gc_last_error(h)
+        raise GCError(rc, (msg or b"").decode() or "gc call failed")
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, ct=ctypes.c_int32):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _pairs(p):
+    a = _i32(np.asarray(p, dtype=np.int32).reshape(-1, 2)) if p is not None else np.zeros((0, 2), np.int32)
+    return a, a.shape[0]
+
+
+def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0):
+    """Open a graph from a symmetric CSR; returns an opaque handle."""
+    lib = load()
+    rp = _i32(row_ptr)
+    c = _i32(col) if len(col) else np.zeros(1, np.int32)
+    opt = gc_options()
+    lib.gc_default_options(ctypes.byref(opt))
+    opt.region_hops = region_hops
+    opt.slack = slack
+    opt.stream = stream or None
+    h = ctypes.c_void_p()
+    rc = lib.gc_open(int(n), _ptr(rp), _ptr(c), ctypes.byref(opt), ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def gc_close(h) -> None:
+    load().gc_close(h)
+
+
+def gc_count_static(h) -> list[int]:
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_count_static(h, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_counts(h) -> list[int]:
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_counts(h, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_apply_batch(h, ins, dels) -> list[int]:
+    a, na = _pairs(ins)
+    d, nd = _pairs(dels)
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_apply_batch(h, _ptr(a), na, _ptr(d), nd, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_apply_batch_device(h, d_ins_ptr: int, n_ins: int, d_del_ptr: int, n_del: int) -> list[int]:
+    """Pairs already in device memory (raw pointers, e.g. ``tensor.data_ptr()``)."""
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_apply_batch_device(h, ctypes.c_void_p(d_ins_ptr), n_ins, ctypes.c_void_p(d_del_ptr), n_del,
+                                        _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_apply_batches(h, batches, independent: bool = False) -> list[list[int]]:
+    k = len(batches)
+    arrs = [(_pairs(i), _pairs(d)) for i, d in batches]
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    ins_p = (i32p * max(k, 1))(*[_ptr(a[0][0]) for a in arrs])
+    del_p = (i32p * max(k, 1))(*[_ptr(a[1][0]) for a in arrs])
+    n_ins = np.array([a[0][1] for a in arrs] or [0], dtype=np.int64)
+    n_del = np.array([a[1][1] for a in arrs] or [0], dtype=np.int64)
+    out = np.zeros((max(k, 1), 6), np.uint64)
+    _check(load().gc_apply_batches(h, ins_p, _ptr(n_ins, ctypes.c_int64), del_p, _ptr(n_del, ctypes.c_int64), k,
+                                   1 if independent else 0, _ptr(out, ctypes.c_uint64)), h)
+    return [[int(x) for x in row] for row in out[:k]]
+
+
+def gc_batch_stats(h) -> dict:
+    s = gc_stats()
+    _check(load().gc_batch_stats(h, ctypes.byref(s)), h)
+    return s.as_dict()
+
+
+def gc_num_edges(h) -> int:
+    return int(load().gc_num_edges(h))
+
+
+def gc_export_csr(h, n: int):
+    m = gc_num_edges(h)
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(max(2 * m, 1), np.int32)
+    _check(load().gc_export_csr(h, _ptr(rp), _ptr(col)), h)
+    return rp, col[: 2 * m]
+
+
+def gc_last_error(h=None) -> str:
+    return (load().gc_last_error(h) or b"").decode()
+
+
+class Graph:
+    """A device-resident graph with maintained graphlet counts."""
+
+    def __init__(self, n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25):
+        self.n = int(n)
+        self.h = gc_open(n, row_ptr, col, region_hops, slack)
+
+    def close(self):
+        if self.h is not None:
+            gc_close(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counts(self):
+        return gc_counts(self.h)
+
+    def count_static(self):
+        return gc_count_static(self.h)
+
+    def apply(self, ins, dels):
+        return gc_apply_batch(self.h, ins, dels)
+
+    def apply_many(self, batches, independent=False):
+        return gc_apply_batches(self.h, batches, independent)
+
+    def stats(self):
+        return gc_batch_stats(self.h)
+
+    def num_edges(self):
+        return gc_num_edges(self.h)
+
+    def export_csr(self):
+        return gc_export_csr(self.h, self.n)

@@ -1,7 +1,10 @@
-"""Write ``workloads.json``: oracle results on the small seeded workloads.
+"""Write oracle results on the seeded workloads.
 
 Calls only the CPU oracle (``oracle/``) and the seeded generators (``synth``).
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:
+
+    python tests/golden/make_golden.py           # workloads.json (seconds)
+    python tests/golden/make_golden.py --large   # workloads_large.json (tens of minutes)
 """
 import json
 import os
@@ -40,5 +43,37 @@ def main():
         f.write("\n")
 
 
+def main_large():
+    """Full-size graphs: static counts and the first batch of each stream."""
+    out = {}
+    # Chung-Lu n=1.6M m=30M gamma 2.3 dmax 10,000; batches of 100,000
+    # (60% insertions, 40% deletions), batch seed 3
+    n, keys = gen.workload_graph("c3")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.batch_stream(n, keys, [100000], 0.6, 3)[0]
+    r = oracle.fdgc_step(rp, col, ins, dels, F0, 3)
+    out["c3"] = dict(static=F0, after=r["F"], Ca=r["Ca"], Cb=r["Cb"], region_vertices=r["region_vertices"],
+                     n_ins=r["n_ins"], n_del=r["n_del"])
+    # Chung-Lu n=2.4M m=5M gamma 1.8 dmax 100,000; independent 50/50 batches
+    # of log-uniform size in [10, 50,000], batch seed 4
+    n, keys = gen.workload_graph("c4")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    sizes = gen.log_uniform_sizes(64, 10, 50000, 4)
+    batches = gen.batch_stream(n, keys, sizes[:3], 0.5, 4, sequential=False)
+    res = []
+    for ins, dels in batches:
+        r = oracle.fdgc_step(rp, col, ins, dels, F0, 3)
+        res.append(dict(after=r["F"], Ca=r["Ca"], Cb=r["Cb"], region_vertices=r["region_vertices"]))
+    out["c4"] = dict(static=F0, sizes=sizes[:3], batches=res)
+    with open(os.path.join(HERE, "workloads_large.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+
+
 if __name__ == "__main__":
-    main()
+    if "--large" in sys.argv:
+        main_large()
+    else:
+        main()

@@ -1,0 +1,357 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Counts are integers and must match bit-exactly (uint64).  Expected values come
+from the oracle, run here on the same seeded inputs, or from the stored
+oracle results in golden/.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from synth import gen
+from gc_testutil import GOLDEN_DIR, csr_from_edges, edges_from_csr, load_closed_forms, random_graph
+
+pytestmark = pytest.mark.gpu
+
+CLOSED = load_closed_forms()
+
+
+@pytest.fixture(scope="module")
+def gcb():
+    from paper_2308_14493_gb300 import gc as binding
+
+    binding.load()
+    return binding
+
+
+def open_graph(gcb, n, rp, col, **kw):
+    return gcb.Graph(n, rp, col, **kw)
+
+
+def mod64(xs):
+    return [int(x) & 0xFFFFFFFFFFFFFFFF for x in xs]
+
+
+def same_graph(g, rp, col):
+    grp, gcol = g.export_csr()
+    return np.array_equal(grp.astype(np.int64), np.asarray(rp, np.int64)) and np.array_equal(gcol, np.asarray(col))
+
+
+# ------------------------------------------------------------------ static --
+
+@pytest.mark.parametrize("name,n,edges,expect", CLOSED, ids=[c[0] for c in CLOSED])
+def test_static_named_graphs(gcb, name, n, edges, expect):
+    rp, col = csr_from_edges(n, edges)
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == expect
+        assert g.count_static() == expect
+
+
+def test_static_random_small_graphs(gcb):
+    rng = np.random.default_rng(101)
+    for trial in range(60):
+        n = int(rng.integers(1, 40))
+        edges = random_graph(rng, n, float(rng.random()))
+        rp, col = csr_from_edges(n, edges)
+        with open_graph(gcb, n, rp, col) as g:
+            expect = brute.graphlet_counts(n, edges) if n <= 20 else oracle.static_counts(rp, col, "literal")
+            assert g.counts() == expect, (trial, n)
+
+
+def test_static_planted_hub_and_clique(gcb):
+    """A 2,000-vertex graph with a 600-degree hub and a 40-clique: exercises
+    long rows, many triangles per edge and heavy 4-cycle pivots."""
+    rng = np.random.default_rng(5)
+    n = 2000
+    keys = set(int(k) for k in gen.er_graph(n, 8000, 9))
+    hub = 17
+    for v in rng.choice(n, 600, replace=False):
+        if v != hub:
+            keys.add((min(hub, v) << 32) | max(hub, v))
+    core = rng.choice(n, 40, replace=False)
+    for a in core:
+        for b in core:
+            if a < b:
+                keys.add((int(a) << 32) | int(b))
+    k = np.array(sorted(keys), dtype=np.uint64)
+    rp, col = gen.csr_from_keys(n, k)
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == oracle.static_counts(rp, col, "literal")
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_static_workload_graphs(gcb, name):
+    n, keys = gen.workload_graph(name)
+    rp, col = gen.csr_from_keys(n, keys)
+    with open(os.path.join(GOLDEN_DIR, "workloads.json")) as f:
+        gold = json.load(f)
+    expect = gold["c1"]["static"] if name == "c1" else gold["c2"][0]["static"]
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == expect
+        assert g.count_static() == expect
+
+
+def test_empty_and_tiny_graphs(gcb):
+    for n in (0, 1, 2, 3):
+        rp = np.zeros(n + 1, np.int32)
+        with open_graph(gcb, n, rp, np.zeros(0, np.int32)) as g:
+            assert g.counts() == [0] * 6
+    rp, col = csr_from_edges(3, [(0, 1), (1, 2)])
+    with open_graph(gcb, 3, rp, col) as g:
+        assert g.counts() == [0] * 6
+        assert g.apply([(0, 2)], []) == [0] * 6
+
+
+def test_malformed_csr_is_rejected(gcb):
+    rp = np.array([0, 1, 1], np.int32)          # 0 -> 1 without 1 -> 0
+    with pytest.raises(gcb.GCError) as ei:
+        gcb.Graph(2, rp, np.array([1], np.int32))
+    assert ei.value.code == gcb.GC_EINVAL
+    rp = np.array([0, 2, 3], np.int32)          # repeated entry
+    with pytest.raises(gcb.GCError):
+        gcb.Graph(2, rp, np.array([1, 1, 0], np.int32))
+    rp = np.array([0, 1, 2], np.int32)          # self-loop
+    with pytest.raises(gcb.GCError):
+        gcb.Graph(2, rp, np.array([0, 1], np.int32))
+
+
+# ----------------------------------------------------------------- dynamic --
+
+def check_step(g, r, stats):
+    assert mod64(g.counts()) == mod64(r["F"])
+    assert stats["Ca"] == r["Ca"] and stats["Cb"] == r["Cb"]
+    assert stats["sums_a"] == r["sums_a"] and stats["sums_b"] == r["sums_b"]
+    assert stats["region_vertices"] == r["region_vertices"]
+    assert stats["edges_a"] == r["edges_a"] and stats["edges_b"] == r["edges_b"]
+    assert stats["n_ins"] == r["n_ins"] and stats["n_del"] == r["n_del"]
+
+
+def test_batch_workload_c1(gcb):
+    """ER n=2,000 m=20,000: one batch of 200 deletions + 200 insertions."""
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.random_batch(n, keys, 200, 200, 1, ins_weighting="uniform")
+    r = oracle.fdgc_step(rp, col, ins, dels, oracle.static_counts(rp, col), 3, "literal")
+    with open(os.path.join(GOLDEN_DIR, "workloads.json")) as f:
+        gold = json.load(f)["c1"]
+    with open_graph(gcb, n, rp, col) as g:
+        out = g.apply(ins, dels)
+        st = g.stats()
+        assert out == gold["after"] == r["F"]
+        check_step(g, r, st)
+        assert same_graph(g, r["row_ptr"], r["col"])
+        assert g.count_static() == r["F"]
+
+
+@pytest.mark.parametrize("ins_frac", [0.5, 1.0], ids=["fdgc", "igc"])
+def test_stream_workload_c2(gcb, ins_frac):
+    """Chung-Lu n=7,000 m=100,000: sequential batches of 1,000 and 10,000
+    (50/50, or insert-only IGC), every step against the oracle."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == og.F
+        for ins, dels in gen.batch_stream(n, keys, [1000, 10000, 1000, 10000], ins_frac, 2):
+            r = og.apply(ins, dels)
+            out = g.apply(ins, dels)
+            assert out == r["F"]
+            check_step(g, r, g.stats())
+        assert same_graph(g, og.row_ptr, og.col)
+
+
+def _dirty_batch(rng, n, edges, k_ins, k_del):
+    es = list(edges)
+    ins = [tuple(int(x) for x in rng.choice(n, 2, replace=False)) for _ in range(k_ins)]
+    dels = [es[i] for i in rng.choice(len(es), min(k_del, len(es)), replace=False)] if es else []
+    dels += [tuple(int(x) for x in rng.choice(n, 2, replace=False)) for _ in range(k_del // 3)]
+    if ins and rng.random() < 0.5:
+        dels.append(ins[0][::-1])
+    if dels and rng.random() < 0.5:
+        ins.append(dels[0])
+    if ins:
+        ins.append(ins[-1][::-1])
+    return np.array(ins, np.int32).reshape(-1, 2), np.array(dels, np.int32).reshape(-1, 2)
+
+
+def test_dirty_batches_on_random_graphs(gcb):
+    """Repeats, reversed pairs, cancellations and no-ops, on graphs whose
+    region is a strict subset of V (region-induced degrees matter)."""
+    rng = np.random.default_rng(202)
+    for trial in range(40):
+        n = int(rng.integers(8, 200))
+        edges = random_graph(rng, n, float(rng.uniform(0.005, 0.2)))
+        rp, col = csr_from_edges(n, edges)
+        og = oracle.OracleGraph(rp, col, variant="literal")
+        with open_graph(gcb, n, rp, col) as g:
+            for step in range(3):
+                cur = edges_from_csr(og.row_ptr, og.col)
+                ins, dels = _dirty_batch(rng, n, cur, int(rng.integers(0, 12)), int(rng.integers(0, 12)))
+                r = og.apply(ins, dels)
+                g.apply(ins, dels)
+                st = g.stats()
+                check_step(g, r, st)
+                assert st["cancelled"] == r["cancelled"]
+                assert st["noop_ins"] + st["noop_del"] == r["noops"]
+                assert st["repeats"] == r["repeats"]
+            assert same_graph(g, og.row_ptr, og.col)
+
+
+def test_invalid_batches_change_nothing(gcb):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    with open_graph(gcb, n, rp, col) as g:
+        F0 = g.counts()
+        for ins, dels in (([(3, 3)], []), ([], [(0, n)]), ([(-1, 2)], []), ([(0, 1), (5, 5)], [])):
+            with pytest.raises(gcb.GCError) as ei:
+                g.apply(ins, dels)
+            assert ei.value.code == gcb.GC_EINVAL
+            assert g.counts() == F0
+        assert same_graph(g, rp, col)
+
+
+def test_empty_batch_and_all_noop_batch(gcb):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    with open_graph(gcb, n, rp, col) as g:
+        F0 = g.counts()
+        assert g.apply([], []) == F0
+        assert g.stats()["region_vertices"] == 0
+        existing = edges_from_csr(rp, col)[:50]
+        assert g.apply(existing, []) == F0
+        st = g.stats()
+        assert st["noop_ins"] == 50 and st["n_ins"] == 0
+        assert g.apply(existing[:10], existing[:10]) == F0
+        assert g.stats()["cancelled"] == 10
+        assert same_graph(g, rp, col)
+
+
+def test_radius_two_gives_same_counts(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [1000, 5000], 0.5, 12)
+    with open_graph(gcb, n, rp, col, region_hops=3) as g3, open_graph(gcb, n, rp, col, region_hops=2) as g2:
+        for ins, dels in batches:
+            assert g3.apply(ins, dels) == g2.apply(ins, dels)
+
+
+def test_inverse_batch_restores_counts_and_graph(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.random_batch(n, keys, 3000, 2000, 77)
+    with open_graph(gcb, n, rp, col) as g:
+        F0 = g.counts()
+        g.apply(ins, dels)
+        assert g.counts() != F0
+        assert g.apply(dels, ins) == F0
+        assert same_graph(g, rp, col)
+
+
+def test_row_growth_forces_relocation_and_relayout(gcb):
+    """Insert many edges at a few vertices so rows outgrow their slack and the
+    pool; the result must still equal the oracle."""
+    n = 3000
+    keys = gen.er_graph(n, 6000, 3)
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    rng = np.random.default_rng(9)
+    with open_graph(gcb, n, rp, col, slack=0.05) as g:
+        relayouts = 0
+        for step in range(4):
+            hubs = rng.choice(n, 3, replace=False)
+            cur = set(int(k) for k in gen.keys_from_csr(og.row_ptr, og.col))
+            ins = []
+            for h in hubs:
+                for v in rng.choice(n, 900, replace=False):
+                    if v != h and ((min(h, v) << 32) | max(h, v)) not in cur:
+                        ins.append((int(h), int(v)))
+            ins = np.array(ins, np.int32)
+            r = og.apply(ins, np.zeros((0, 2), np.int32))
+            assert g.apply(ins, []) == r["F"]
+            relayouts += g.stats()["relayouts"]
+        assert same_graph(g, og.row_ptr, og.col)
+        assert relayouts >= 1
+
+
+def test_independent_batches_equal_fresh_copies(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    sizes = [10, 300, 5000, 40, 2000]
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 44, sequential=False)
+    F0 = oracle.static_counts(rp, col)
+    with open_graph(gcb, n, rp, col) as g:
+        outs = g.apply_many(batches, independent=True)
+        assert g.counts() == F0 and same_graph(g, rp, col)
+    for (ins, dels), out in zip(batches, outs):
+        assert out == oracle.fdgc_step(rp, col, ins, dels, F0)["F"]
+
+
+def test_sequential_batches_call_equals_single_calls(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [700, 50, 4000], 0.5, 45)
+    with open_graph(gcb, n, rp, col) as g1, open_graph(gcb, n, rp, col) as g2:
+        outs = g1.apply_many(batches)
+        for (ins, dels), out in zip(batches, outs):
+            assert g2.apply(ins, dels) == out
+
+
+def test_device_resident_batch(gcb):
+    torch = pytest.importorskip("torch")
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.random_batch(n, keys, 800, 600, 5)
+    r = oracle.fdgc_step(rp, col, ins, dels, oracle.static_counts(rp, col))
+    ti = torch.from_numpy(ins).cuda()
+    td = torch.from_numpy(dels).cuda()
+    torch.cuda.synchronize()
+    with open_graph(gcb, n, rp, col) as g:
+        out = gcb.gc_apply_batch_device(g.h, ti.data_ptr(), ins.shape[0], td.data_ptr(), dels.shape[0])
+        assert out == r["F"]
+
+
+# -------------------------------------------------------------- full size --
+
+def _large_gold():
+    p = os.path.join(GOLDEN_DIR, "workloads_large.json")
+    if not os.path.exists(p):
+        pytest.skip("workloads_large.json not generated")
+    with open(p) as f:
+        return json.load(f)
+
+
+@pytest.mark.slow
+def test_fullsize_c3_static_and_first_batch(gcb):
+    """Chung-Lu n=1.6M m=30M: static count and one 100,000-update batch
+    against stored oracle results, plus Lemma 2 on the device."""
+    gold = _large_gold()["c3"]
+    n, keys = gen.workload_graph("c3")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.batch_stream(n, keys, [100000], 0.6, 3)[0]
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == gold["static"]
+        out = g.apply(ins, dels)
+        st = g.stats()
+        assert out == gold["after"]
+        assert st["Ca"] == gold["Ca"] and st["Cb"] == gold["Cb"]
+        assert st["region_vertices"] == gold["region_vertices"]
+        assert g.count_static() == out
+
+
+@pytest.mark.slow
+def test_fullsize_c4_independent_batches(gcb):
+    """Chung-Lu n=2.4M m=5M with 40k-degree hubs: independent batches on one
+    snapshot against stored oracle results."""
+    gold = _large_gold()["c4"]
+    n, keys = gen.workload_graph("c4")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, gold["sizes"], 0.5, 4, sequential=False)
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == gold["static"]
+        outs = g.apply_many(batches, independent=True)
+        for out, b in zip(outs, gold["batches"]):
+            assert out == b["after"]
