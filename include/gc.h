@@ -84,6 +84,11 @@ typedef struct {
        [0] normalise  [1] region walk  [2] union graph  [3] triangles + 4-cliques
        [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused */
     float ms_stage[8];
+    /* work of the counting pass, for roofline accounting */
+    int64_t work_triangles;         /* sum over union-graph out-edges u->v of |N+(u)| + |N+(v)| */
+    int64_t work_wedges;            /* wedges u-v-w (v, w below u) walked for the 4-cycles */
+    int32_t launches;               /* kernels the call launched */
+    int32_t reserved2[3];
 } gc_stats;
 
 /* Fill *opt with the defaults. */

@@ -82,6 +82,7 @@ struct gc_graph {
     std::string err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEvent_t ev[8] = {};  // stage boundaries, see gc_stats.ms_stage
+    int launches = 0;        // kernels launched by the current call
 };
 
 // ---------------------------------------------------------------------------
@@ -197,19 +198,27 @@ static int plan_region_buffers(gc_graph* g, long long n_ins) {
 static int count_region(gc_graph* g, int mode) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
+    g->launches++;
     k_reset_count<<<1, 32, 0, s>>>(g->ctl);
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
+    g->launches++;
     k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg);
-    scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
+    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
+    g->launches++;
     k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
                                 g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
+    g->launches++;
     k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
     CK(cudaEventRecord(g->ev[3], s));
+    g->launches++;
     k_tri_k4<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p);
     CK(cudaEventRecord(g->ev[4], s));
+    g->launches++;
     k_c4<<<g->c4_blocks, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->c4cnt.p, g->n);
     CK(cudaEventRecord(g->ev[5], s));
+    g->launches++;
     k_edge_terms<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p, g->da, g->db);
+    g->launches++;
     k_finalize<<<1, 32, 0, s>>>(g->ctl, mode == 0 ? 0 : 1);
     if (mode == 2) k_set_F<<<1, 32, 0, s>>>(g->ctl);
     CK(cudaEventRecord(g->ev[6], s));
@@ -220,13 +229,16 @@ static int count_region(gc_graph* g, int mode) {
 static int enqueue_commit(gc_graph* g) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
+    g->launches++;
     k_commit_plan<<<grid_elems(g, std::max<long long>(g->keys.cap, 1)), TPB, 0, s>>>(
         g->ctl, g->wlist, g->segA, g->segD, g->deg, g->cap, g->row_start, g->col_capacity, g->slack,
         g->plan_dst.p, g->plan_cap.p, g->plan_deg.p, g->plan_scr.p);
     // the region adjacency buffer is free again and is large enough for every
     // rewritten row: use it as the merge scratch
+    g->launches++;
     k_commit_merge<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->segA, g->segD, g->dstA.p, g->dstD.p, g->deg, g->row_start,
                                       g->col, g->plan_scr.p, g->U_col.p);
+    g->launches++;
     k_commit_write<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->plan_dst.p, g->plan_cap.p, g->plan_deg.p,
                                       g->plan_scr.p, g->U_col.p, g->deg, g->cap, g->row_start, g->col);
     CKL();
@@ -235,7 +247,9 @@ static int enqueue_commit(gc_graph* g) {
 
 static int enqueue_clear_segments(gc_graph* g) {
     int ge = grid_elems(g, std::max<long long>(g->keys.cap, 1));
+    g->launches++;
     k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+    g->launches++;
     k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
     CKL();
     return GC_OK;
@@ -248,8 +262,9 @@ static int relayout(gc_graph* g, long long pool_extra) {
     int n = g->n;
     long long* new_start = (long long*)dalloc(g, sizeof(long long) * (size_t)(n + 1));
     if (!new_start) return nomem(g, "row offsets");
+    g->launches++;
     k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
-    scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+    g->launches += scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
     long long total = 0;
     CK(cudaMemcpyAsync(&total, new_start + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -260,7 +275,9 @@ static int relayout(gc_graph* g, long long pool_extra) {
         dfree(g, new_start);
         return nomem(g, "adjacency pool");
     }
+    g->launches++;
     k_copy_rows<<<grid_warps(g), TPB, 0, s>>>(g->deg, n, g->row_start, g->col, new_start, ncol);
+    g->launches++;
     k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
     CKL();
     dfree(g, g->col);
@@ -283,6 +300,8 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
     t.region_entries = c.nU;
     t.edges_a = (long long)c.acc[12];
     t.edges_b = (long long)c.acc[13];
+    t.work_triangles = (long long)c.acc[14];
+    t.work_wedges = (long long)c.acc[15];
     for (int i = 0; i < 6; i++) {
         t.Ca[i] = c.Ca[i];
         t.Cb[i] = c.Cb[i];
@@ -308,6 +327,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     if (!ensure(g, g->hist, (size_t)256 * rg)) return nomem(g, "sort histogram");
     int rc = plan_region_buffers(g, n_ins);
     if (rc) return rc;
+    g->launches = 0;
     g->h_desc[0] = 0;
     g->h_desc[1] = n_ins;
     g->h_desc[2] = 0;
@@ -315,28 +335,38 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     CK(cudaEventRecord(g->e0, s));
     CK(cudaMemcpyAsync(g->desc, g->h_desc, 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(g->ev[0], s));
+    g->launches++;
     k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, 0);
     int ge = grid_elems(g, nkb);
     if (nk > 0) {
+        g->launches++;
         k_batch_keys<<<grid_elems(g, n_ins + n_del), TPB, 0, s>>>(d_ins, d_del, g->ctl, g->perm, g->n, g->S,
                                                                    g->keys.p);
-        radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nk, 2 * g->S + 1, g->hist.p, rg, s);
+        g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nk, 2 * g->S + 1, g->hist.p, rg, s);
+        g->launches++;
         k_batch_decide<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col, g->keepA.p,
                                           g->keepD.p);
         int sg = scan_grid(nk, g->sms);
-        scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
-        scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
+        g->launches += scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
+        g->launches += scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
+        g->launches++;
         k_batch_compact<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p, g->posA.p, g->posD.p,
                                            g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
+        g->launches++;
         k_batch_segments<<<ge, TPB, 0, s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+        g->launches++;
         k_batch_segments<<<ge, TPB, 0, s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
     }
     CK(cudaEventRecord(g->ev[1], s));
     CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+    g->launches++;
     k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
+    g->launches++;
     k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
     for (int L = 1; L <= g->hops; L++) {
+        g->launches++;
         k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
+        g->launches++;
         k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
     }
     CKL();
@@ -386,6 +416,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     g->st.n_del_raw = n_del;
     g->st.ms_device = ms;
     g->st.relayouts = relayouts;
+    g->st.launches = g->launches;
     {
         // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
         // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
@@ -420,6 +451,7 @@ static int count_static(gc_graph* g, int mode, uint64_t out[6]) {
     int rc = plan_region_buffers(g, 0);
     if (rc) return rc;
     CK(cudaMemsetAsync(g->visited, 0xFF, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+    g->launches++;
     k_region_all<<<grid_elems(g, g->n), TPB, 0, s>>>(g->ctl, g->n, g->wlist);
     CKL();
     CK(cudaEventRecord(g->ev[2], s));
@@ -551,18 +583,22 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
         if (cudaMemcpyAsync(g->desc + 8, g->h_desc + 8, 2 * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) { rc = GC_ECUDA; break; }
         if (n > 0) {
+            g->launches++;
             k_degree_keys<<<grid_elems(g, n), TPB, 0, s>>>(d_rp, n, deg0, k1);
-            radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
+            g->launches += radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
+            g->launches++;
             k_perm_from_keys<<<grid_elems(g, n), TPB, 0, s>>>(k1, n, g->perm, g->iperm, deg0, g->deg);
         }
         if (m2 > 0) {
+            g->launches++;
             k_edge_keys<<<grid_warps(g), TPB, 0, s>>>(d_rp, d_col, n, g->perm, g->S, k1, bad);
-            radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
+            g->launches += radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
         }
         if (n > 0) {
-            scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+            g->launches += scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+            g->launches++;
             k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
-            scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+            g->launches += scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
         }
         long long total = 0;
         if (n > 0 &&
@@ -580,7 +616,9 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
         g->col = (int32_t*)dalloc(g, 4 * (size_t)g->col_capacity);
         if (!g->col) { rc = nomem(g, "adjacency"); break; }
         if (m2 > 0)
+            g->launches++;
             k_fill_from_keys<<<grid_elems(g, m2), TPB, 0, s>>>(k1, m2, n, g->S, key_off, g->row_start, g->col, bad);
+        g->launches++;
         k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
         int hbad = 0;
         if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_c4(Ctl* c, const int32_t* __restrict__ 
     unsigned long long* cnt = cnt_all + (size_t)blockIdx.x * n;
     int nW = c->nW;
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    unsigned long long qa = 0, qb = 0;
+    unsigned long long qa = 0, qb = 0, wedges = 0;
     for (;;) {
         if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[0], 1u);
         __syncthreads();
@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_c4(Ctl* c, const int32_t* __restrict__ 
                 uint32_t v = vid(fv);
                 long long vb = U_off[v];
                 long long lenv = lower_bound_id(U_col + vb, U_off[v + 1] - vb, (uint32_t)u);
+                if (pass == 0 && lane == 0) wedges += (unsigned long long)lenv;
                 for (long long q = lane; q < lenv; q += 32) {
                     uint32_t fw = U_col[vb + q];
                     uint32_t w = vid(fw);
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(256) k_c4(Ctl* c, const int32_t* __restrict__ 
     }
     qa = warp_sum_u64(qa);
     qb = warp_sum_u64(qb);
+    if (lane == 0 && wedges) atomicAdd(&c->acc[15], wedges);
     if (lane == 0) {
         s_q[0][warp] = qa;
         s_q[1][warp] = qb;
@@ -185,7 +187,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long P[2] = {0, 0}, S[2] = {0, 0}, T[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0};
+    unsigned long long P[2] = {0, 0}, S[2] = {0, 0}, T[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0}, work = 0;
     for (int wi = warp; wi < nW; wi += nwarps) {
         int32_t u = wlist[wi];
         long long dau = da[u], dbu = db[u];
@@ -198,6 +200,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
             uint32_t fe = U_col[e];
             uint32_t v = vid(fe);
             unsigned long long t = tpack[e];
+            work += (unsigned long long)((oe - ob) + (U_off[v + 1] - U_off[v] - U_split[v]));
             if (fe & FLAG_A) {
                 long long dv = da[v], tt = (long long)(t >> 32);
                 P[0] += (unsigned long long)((dau - 1) * (dv - 1) - tt);
@@ -232,6 +235,8 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
             if (E[g]) atomicAdd(&c->acc[12 + g], E[g]);
         }
     }
+    work = warp_sum_u64(work);
+    if (lane == 0 && work) atomicAdd(&c->acc[14], work);
 }
 
 // mode 0: batch (F += C_a - C_b unless the batch was rejected); 1: static

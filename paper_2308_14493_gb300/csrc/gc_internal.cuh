@@ -38,7 +38,7 @@ struct Ctl {
     int lvl[MAX_HOPS + 2];           // lvl[L]: end of BFS level L in the region list
     long long nU;                    // entries of the region union graph
     unsigned long long acc[16];      // [0..5] sums of G_a, [6..11] sums of G_b: P, S, 2TT, D, K, Q
-                                     // [12] |E(G_a)|, [13] |E(G_b)|
+                                     // [12] |E(G_a)|, [13] |E(G_b)|, [14] triangle work, [15] wedges
     unsigned long long F[6];         // maintained counts
     long long Ca[6], Cb[6];          // induced counts of G_a, G_b of the last pass
     long long sa[6], sb[6];          // their non-induced sums (TT halved)
@@ -147,14 +147,15 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, long long len,
 // Sort `keys` (uint64) of device-resident length *d_count (<= max_count) by
 // their low `bits` bits.  `tmp` holds max_count keys; `hist` holds 256 * grid
 // words.  The sorted keys end in `keys`.
-void radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long long max_count, int bits,
-                    uint32_t* hist, int grid, cudaStream_t s);
+// Returns the number of kernels launched.
+int radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long long max_count, int bits,
+                   uint32_t* hist, int grid, cudaStream_t s);
 int radix_grid(long long max_count, int sms);
 // Exclusive prefix sum of int32 in[0..len) into int64 out[0..len], out[len] = total.
 // len = *d_len when d_len != null, else host_len.  `bsum` holds `grid` int64.
 // If total_out != null the total is also stored there.
-void scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len,
-                     long long* bsum, int grid, long long* total_out, cudaStream_t s);
+int scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len,
+                    long long* bsum, int grid, long long* total_out, cudaStream_t s);
 int scan_grid(long long max_len, int sms);
 
 }  // namespace gcx

@@ -188,9 +188,10 @@ int radix_grid(long long max_count, int sms) {
     return (int)g;
 }
 
-void radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long long max_count, int bits,
-                    uint32_t* hist, int grid, cudaStream_t s) {
+int radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long long max_count, int bits,
+                   uint32_t* hist, int grid, cudaStream_t s) {
     int passes = (bits + 7) / 8;
+    int launches = 3 * passes;
     uint64_t* a = keys;
     uint64_t* b = tmp;
     for (int p = 0; p < passes; p++) {
@@ -207,7 +208,9 @@ void radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, lon
         if (g < 1) g = 1;
         if (g > 2048) g = 2048;
         k_copy_u64<<<g, 256, 0, s>>>(a, keys, d_count);
+        launches++;
     }
+    return launches;
 }
 
 int scan_grid(long long max_len, int sms) {
@@ -218,11 +221,12 @@ int scan_grid(long long max_len, int sms) {
     return (int)g;
 }
 
-void scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len, long long* bsum,
-                     int grid, long long* total_out, cudaStream_t s) {
+int scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len, long long* bsum,
+                    int grid, long long* total_out, cudaStream_t s) {
     k_scan_partials<<<grid, SC_BLOCK, 0, s>>>(in, d_len, host_len, bsum);
     k_scan_top<<<1, 1024, 0, s>>>(bsum, grid);
     k_scan_apply<<<grid, SC_BLOCK, 0, s>>>(in, out, d_len, host_len, bsum, total_out);
+    return 3;
 }
 
 }  // namespace gcx

@@ -41,12 +41,13 @@ class gc_stats(ctypes.Structure):
                 ("Ca", ctypes.c_int64 * 6), ("Cb", ctypes.c_int64 * 6), ("sums_a", ctypes.c_int64 * 6),
                 ("sums_b", ctypes.c_int64 * 6), ("num_edges", ctypes.c_int64), ("ms_device", ctypes.c_float),
                 ("ms_wall", ctypes.c_float), ("relayouts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
-                ("ms_stage", ctypes.c_float * 8)]
+                ("ms_stage", ctypes.c_float * 8), ("work_triangles", ctypes.c_int64),
+                ("work_wedges", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved2", ctypes.c_int32 * 3)]
 
     def as_dict(self) -> dict:
         out = {}
         for name, _ in self._fields_:
-            if name == "reserved":
+            if name.startswith("reserved"):
                 continue
             v = getattr(self, name)
             out[name] = list(v) if hasattr(v, "__len__") else v
