@@ -160,6 +160,39 @@ int64_t gc_num_edges(const gc_graph *g);
    row_ptr: int32[n+1]; col: int32[2 * gc_num_edges(g)]. */
 int gc_export_csr(gc_graph *g, int32_t *row_ptr, int32_t *col);
 
+/*
+ * Static count that allocates nothing.  The paper has no counterpart; this
+ * entry point exists for callers that must not allocate device memory when
+ * they ask for a count: a service whose device memory is all reserved up
+ * front by another allocator, a latency-critical loop that cannot afford the
+ * device-wide synchronisation and delay of cudaMalloc, or a plug-in inside a
+ * host process that forbids device allocations after start-up.
+ *
+ * It computes the same six counts as gc_count_static, for a graph the caller
+ * already holds in device memory, using only a fixed scratch array compiled
+ * into this library (about 9 MB, held on every GPU that loads the library
+ * until the process exits).  It calls no cudaMalloc, cudaFree or any other
+ * allocating routine.
+ *   n          vertices, 1 <= n <= GC_NOALLOC_MAX_VERTICES (n = 0 gives zeros)
+ *   d_row_ptr  device int32[n+1], d_row_ptr[0] = 0, d_row_ptr[n] = nnz
+ *   d_col      device int32[nnz]: a symmetric simple graph, every row sorted
+ *              ascending, nnz <= GC_NOALLOC_MAX_ENTRIES
+ *   stream     cudaStream_t to run on (NULL: the default stream)
+ *   out        host uint64[6]: the counts, in the order of gc_count_static
+ * Returns GC_EINVAL for sizes beyond the limits (before any device work) or
+ * for a CSR that fails the checks, GC_ECUDA if a CUDA call fails.  The call
+ * is synchronous.  The first call on each device, made with that device
+ * current, looks up the scratch array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the one
+ * scratch array and leaves its contents behind (each call clears what must
+ * start at zero); calls that overlap on the GPU, from different streams or
+ * host threads, race and must be serialised by the caller.
+ */
+#define GC_NOALLOC_MAX_VERTICES 16384
+#define GC_NOALLOC_MAX_ENTRIES 524288
+int gc_count_static_noalloc(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col, int64_t nnz,
+                            void *stream, uint64_t out[6]);
+
 /* One-line reason for the last failure on this handle ("" if none).
    With g == NULL: the reason for the last failed gc_open. */
 const char *gc_last_error(const gc_graph *g);

@@ -14,6 +14,7 @@ from .gc import (  # noqa: F401
     gc_batch_stats,
     gc_close,
     gc_count_static,
+    gc_count_static_noalloc,
     gc_counts,
     gc_export_csr,
     gc_last_error,

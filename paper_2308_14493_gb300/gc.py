@@ -86,6 +86,7 @@ def load():
             lib.gc_last_error.restype = ctypes.c_char_p
             lib.gc_close.argtypes = [P]
             lib.gc_close.restype = None
+            lib.gc_count_static_noalloc.argtypes = [ctypes.c_int32, P, P, ctypes.c_int64, P, u64p]
             _lib = lib
     return _lib
 
@@ -187,6 +188,26 @@ def gc_export_csr(h, n: int):
     col = np.zeros(max(2 * m, 1), np.int32)
     _check(load().gc_export_csr(h, _ptr(rp), _ptr(col)), h)
     return rp, col[: 2 * m]
+
+
+GC_NOALLOC_MAX_VERTICES = 16384
+GC_NOALLOC_MAX_ENTRIES = 524288
+
+
+def gc_count_static_noalloc(n: int, d_row_ptr: int, d_col: int, nnz: int, stream: int = 0) -> list[int]:
+    """Static count without any device allocation, for callers that must not
+    allocate (memory reserved up front by another allocator, latency-critical
+    loops, hosts that forbid allocations after start-up).  The CSR is already
+    in device memory: raw pointers (e.g. ``tensor.data_ptr()``) to int32
+    row offsets and sorted, symmetric rows.  Limited to
+    GC_NOALLOC_MAX_VERTICES vertices and GC_NOALLOC_MAX_ENTRIES entries."""
+    out = np.zeros(6, np.uint64)
+    rc = load().gc_count_static_noalloc(int(n), ctypes.c_void_p(d_row_ptr), ctypes.c_void_p(d_col), int(nnz),
+                                        ctypes.c_void_p(stream or None), _ptr(out, ctypes.c_uint64))
+    if rc != GC_OK:
+        raise GCError(rc, "gc_count_static_noalloc failed (sizes beyond the fixed scratch, "
+                          "a CSR that is not symmetric, simple and sorted, or a CUDA error)")
+    return [int(x) for x in out]
 
 
 def gc_last_error(h=None) -> str:
