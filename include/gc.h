@@ -59,7 +59,8 @@ typedef struct {
     int32_t region_hops; /* k of the k-hop region; 0 -> 3 as in Sec. 4.2; must be >= 2 */
     float slack;         /* spare capacity per adjacency row; 0 -> 0.25 */
     int32_t device;      /* CUDA device ordinal; 0 -> current device */
-    int32_t reserved[7];
+    int32_t dense_cluster; /* CTAs per cluster of the heavy 4-cycle kernel: 0 auto, 8 or 16 */
+    int32_t reserved[6];
 } gc_options;
 
 /* Per-batch record of the last gc_apply_batch* call. */

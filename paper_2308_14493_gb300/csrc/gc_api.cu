@@ -73,8 +73,12 @@ struct gc_graph {
     Buf<int32_t> keepA, keepD, srcA, dstA, srcD, dstD, plan_cap, plan_deg, pairs;
     Buf<long long> posA, posD, plan_dst, plan_scr, bsum;
     Buf<uint32_t> hist;
-    Buf<unsigned long long> c4cnt;
-    int c4_blocks = 0;
+    Buf<unsigned long long> dense;      // counter arrays of the heaviest 4-cycle pivots (per cluster)
+    Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
+    int cta_groups = 0;
+    int dense_clusters = 0;
+    int dense_cluster_size = 8;
+    int32_t* bins = nullptr;        // NBINS * n work lists of the counting pass
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
     long long m = 0;
@@ -209,18 +213,29 @@ static int count_region(gc_graph* g, int mode) {
                                 g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
     g->launches++;
     k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
-    CK(cudaEventRecord(g->ev[3], s));
-    g->launches++;
-    k_tri_k4<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p);
-    CK(cudaEventRecord(g->ev[4], s));
-    g->launches++;
-    k_c4<<<g->c4_blocks, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->c4cnt.p, g->n);
-    CK(cudaEventRecord(g->ev[5], s));
-    g->launches++;
-    k_edge_terms<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p, g->da, g->db);
-    g->launches++;
-    k_finalize<<<1, 32, 0, s>>>(g->ctl, mode == 0 ? 0 : 1);
-    if (mode == 2) k_set_F<<<1, 32, 0, s>>>(g->ctl);
+    CountArgs ca;
+    ca.ctl = g->ctl;
+    ca.wlist = g->wlist;
+    ca.U_off = g->U_off;
+    ca.U_col = g->U_col.p;
+    ca.U_split = g->U_split;
+    ca.da = g->da;
+    ca.db = g->db;
+    ca.tpack = g->tpack.p;
+    ca.bins = g->bins;
+    ca.dense = g->dense.p;
+    ca.n_alloc = std::max(g->n, 1);
+    ca.dense_clusters = g->dense_clusters;
+    ca.dense_cluster_size = g->dense_cluster_size;
+    ca.cta_tables = g->cta_tables.p;
+    ca.cta_table_words = 2 * C4_T3;
+    ca.cta_groups = g->cta_groups;
+    ca.sms = g->sms;
+    g->launches += enqueue_counting(ca, s, g->ev[3], g->ev[4], g->ev[5], mode == 0 ? 0 : 1);
+    if (mode == 2) {
+        g->launches++;
+        k_set_F<<<1, 32, 0, s>>>(g->ctl);
+    }
     CK(cudaEventRecord(g->ev[6], s));
     CKL();
     return GC_OK;
@@ -505,7 +520,9 @@ static void destroy(gc_graph* g) {
     release(g, g->plan_scr);
     release(g, g->bsum);
     release(g, g->hist);
-    release(g, g->c4cnt);
+    release(g, g->dense);
+    release(g, g->cta_tables);
+    dfree(g, g->bins);
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_desc) cudaFreeHost(g->h_desc);
@@ -639,11 +656,16 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     dfree(g, d_rp); dfree(g, d_col); dfree(g, deg0); dfree(g, key_off); dfree(g, bad); dfree(g, k1); dfree(g, k2);
     if (rc) return rc;
     g->m = m2 / 2;
-    // 4-cycle counters: one dense array of n words per resident block
-    g->c4_blocks = std::max(1, std::min(2 * g->sms, 1024));
-    size_t c4words = (size_t)g->c4_blocks * nn;
-    if (!ensure(g, g->c4cnt, c4words)) return nomem(g, "4-cycle counters");
-    CK(cudaMemsetAsync(g->c4cnt.p, 0, 8 * g->c4cnt.cap, s));
+    // counting pass: work lists, and one dense counter array per cluster of
+    // the heavy 4-cycle kernel (kept zero between pivots)
+    count_setup_attributes();
+    g->bins = (int32_t*)dalloc(g, sizeof(int32_t) * (size_t)NBINS * nn);
+    g->dense_clusters = dense_cluster_plan(g->opt.dense_cluster, g->sms, &g->dense_cluster_size);
+    if (!g->bins || !ensure(g, g->dense, (size_t)g->dense_clusters * (nn + 1))) return nomem(g, "counting work lists");
+    CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
+    g->cta_groups = g->sms;
+    if (!ensure(g, g->cta_tables, (size_t)g->cta_groups * 2 * C4_T3)) return nomem(g, "4-cycle hash tables");
+    CK(cudaMemsetAsync(g->cta_tables.p, 0, 8 * g->cta_tables.cap, s));
     return count_static(g, 2, nullptr);
 }
 

@@ -14,17 +14,39 @@
 //   g2 = S-g4-2g5-4K, g1 = P-2g4-4g3-6g5-12K.
 //
 // Orientation: an edge points from its lower to its higher internal id.
-//  * each triangle u<v<w is listed once, from edge u->v, as w in N+(u) n N+(v),
-//    and credited to its three edges (one 64-bit atomic each: G_a count in the
-//    high word, G_b count in the low word);
-//  * each 4-clique u<v<w<x is counted once, from triangle (u,v,w), as
-//    x in N+(u) n N+(v) n N+(w);
-//  * each 4-cycle is counted once at its highest vertex u: for every w < u,
-//    c_w = #{v in N(u) n N(w), v < u}, and the cycle count is sum_w C(c_w,2).
+//
+// Triangles and 4-cliques, root-centred.  For a root u with out-list
+// X = N+(u) (k entries), every v = X[q] is probed: each entry y of N+(v)
+// that is also in X (binary search in shared memory) closes the triangle
+// (u, v, y), listed exactly once (u < v < y).  It sets bit p = pos(y) of the
+// local row q, and credits its three edges: (u,v) and (u,y) in a per-root
+// shared-memory accumulator, (v,y) by one 64-bit atomic.  The rows are the
+// adjacency of N+(u) as bitmasks, so the 4-cliques through u are
+// sum over bits p of row q of popcount(row_q & row_p).  G_a and G_b get one
+// row set each.  Roots are binned by k: a warp (k <= 32), a block
+// (k <= TRI_KM), or per-edge merging (larger k).
+//
+// 4-cycles, pivot-centred.  Each 4-cycle is counted once at its highest
+// vertex u: for every w < u, c_w = #{v in N(u) n N(w): v < u}, and the
+// pivot contributes sum_w C(c_w, 2).  Counters are incremented one wedge
+// u-v-w at a time and the increment returns the old value c, so the pivot's
+// sum is accumulated on the fly as sum of old values (C(c+1,2) - C(c,2) = c);
+// no reduction pass is needed.  Pivots are binned by the wedge bound
+// w~ = sum of the degrees of the lower neighbours: registers (w~ <= 32, equal
+// endpoints grouped by __match_any_sync), a per-warp or per-block hash table
+// in shared memory, or, for the heavy pivots, a cluster of CTAs sharing one
+// dense counter array in global memory.
+//
 // An edge set counts for G_a (G_b) only if all its entries carry FLAG_A
 // (FLAG_B), so one walk serves both graphs.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "gc_internal.cuh"
 #include "gc_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gcx {
 
@@ -32,6 +54,8 @@ __global__ void k_reset_count(Ctl* c) {
     int t = threadIdx.x;
     if (t < 16) c->acc[t] = 0;
     if (t < 8) c->work[t] = 0;
+    if (t < 8) c->nbin[t] = 0;
+    if (t == 0) c->maxdeg = 0;
 }
 
 __global__ void k_zero_u64(unsigned long long* __restrict__ a, const long long* d_len) {
@@ -44,18 +68,274 @@ __device__ __forceinline__ unsigned long long flag_inc(uint32_t f) {
     return ((f & FLAG_A) ? (1ull << 32) : 0ull) | ((f & FLAG_B) ? 1ull : 0ull);
 }
 
-// One warp per region vertex u; each lane takes one out-edge u->v and merges
-// N+(u) (after v) with N+(v).
-__global__ void k_tri_k4(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
-                         const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
-                         unsigned long long* __restrict__ tpack) {
-    int nW = c->nW;
-    int lane = threadIdx.x & 31;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int nwarps = (gridDim.x * blockDim.x) >> 5;
+__device__ __forceinline__ void acc_add(Ctl* c, int slot, unsigned long long x) {
+    x = warp_sum_u64(x);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c->acc[slot], x);
+}
+
+// index of id y in the sorted entries s[0..k), or -1
+__device__ __forceinline__ int find_pos(const uint32_t* s, int k, uint32_t y) {
+    int lo = 0, hi = k;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (vid(s[mid]) < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < k && vid(s[lo]) == y) ? lo : -1;
+}
+
+// largest q in [0, k) with pre[q] <= t (pre[0] = 0 <= t < pre[k])
+__device__ __forceinline__ int find_seg(const int* pre, int k, int t) {
+    int lo = 0, hi = k;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (pre[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---- binning ---------------------------------------------------------------
+
+__global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                      const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                      int32_t* __restrict__ bins, int n, long long t3) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nW_r = ((long long)nW + 31) & ~31ll;
+    int dmax = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nW_r; i += stride) {
+        bool valid = i < nW;
+        int tb = -1, cb = -1;
+        int32_t u = valid ? wlist[i] : 0;
+        if (valid) {
+            long long rb = U_off[u], re = U_off[u + 1];
+            int split = U_split[u];
+            int k = (int)(re - rb) - split;
+            dmax = max(dmax, (int)(re - rb));
+            if (k >= 2) tb = k <= 32 ? BIN_TRI_WARP : (k <= TRI_KM ? BIN_TRI_BLOCK : BIN_TRI_MERGE);
+            if (split >= 2) {
+                long long wt = 0;
+                for (int j = 0; j < split; j++) {
+                    uint32_t v = vid(U_col[rb + j]);
+                    wt += U_off[v + 1] - U_off[v];
+                }
+                // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
+                cb = wt <= 32                        ? BIN_C4_REG
+                     : wt <= C4_T1                   ? BIN_C4_WARP
+                     : wt <= C4_T2                   ? BIN_C4_BLOCK
+                     : (wt <= t3 && split < 65536)   ? BIN_C4_CTA
+                                                     : BIN_C4_DENSE;
+            }
+        }
+#pragma unroll 1
+        for (int b = 0; b < NBINS; b++) {
+            bool mine = valid && (tb == b || cb == b);
+            unsigned m = __ballot_sync(FULL, mine);
+            if (m) {
+                int leader = __ffs(m) - 1, base = 0;
+                if (lane == leader) base = atomicAdd(&c->nbin[b], __popc(m));
+                base = __shfl_sync(FULL, base, leader);
+                if (mine) bins[(size_t)b * n + base + __popc(m & lanemask_lt())] = u;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_down_sync(FULL, dmax, o));
+    if (lane == 0 && dmax) atomicMax(&c->maxdeg, dmax);
+}
+
+// ---- triangles and 4-cliques -------------------------------------------------
+
+constexpr int TW = 8;  // warps per block of the warp-per-root kernel
+
+__global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __restrict__ list,
+                                                     const long long* __restrict__ U_off,
+                                                     const uint32_t* __restrict__ U_col,
+                                                     const int32_t* __restrict__ U_split,
+                                                     unsigned long long* __restrict__ tpack) {
+    __shared__ uint32_t sX[TW][32];
+    __shared__ long long sNb[TW][32];
+    __shared__ int sPre[TW][33];
+    __shared__ uint32_t sRA[TW][32], sRB[TW][32];
+    __shared__ unsigned long long sTq[TW][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cnt = c->nbin[BIN_TRI_WARP];
     unsigned long long ka = 0, kb = 0;
-    for (int wi = warp; wi < nW; wi += nwarps) {
-        int32_t u = wlist[wi];
+    for (int i = blockIdx.x * TW + w; i < cnt; i += gridDim.x * TW) {
+        int32_t u = list[i];
+        long long rb = U_off[u] + U_split[u];
+        int k = (int)(U_off[u + 1] - rb);
+        uint32_t x = lane < k ? U_col[rb + lane] : 0u;
+        uint32_t xmax = vid(__shfl_sync(FULL, x, k - 1));
+        int cq = 0;
+        long long nb = 0;
+        if (lane < k) {
+            uint32_t v = vid(x);
+            nb = U_off[v] + U_split[v];
+            cq = (int)lower_bound_id(U_col + nb, U_off[v + 1] - nb, xmax + 1);
+        }
+        int inc = cq;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        sX[w][lane] = x;
+        sNb[w][lane] = nb;
+        sPre[w][lane + 1] = inc;
+        if (lane == 0) sPre[w][0] = 0;
+        sRA[w][lane] = 0;
+        sRB[w][lane] = 0;
+        sTq[w][lane] = 0;
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            int q = find_seg(sPre[w], k, t);
+            long long slot = sNb[w][q] + (t - sPre[w][q]);
+            uint32_t e = U_col[slot];
+            int p = find_pos(sX[w], k, vid(e));
+            if (p < 0) continue;
+            uint32_t f = sX[w][q] & sX[w][p] & e;
+            unsigned long long iv = flag_inc(f);
+            if (!iv) continue;
+            if (f & FLAG_A) atomicOr(&sRA[w][q], 1u << p);
+            if (f & FLAG_B) atomicOr(&sRB[w][q], 1u << p);
+            atomicAdd(&sTq[w][q], iv);
+            atomicAdd(&sTq[w][p], iv);
+            atomicAdd(&tpack[slot], iv);
+        }
+        __syncwarp();
+        if (lane < k) {
+            uint32_t ra = sRA[w][lane], rbm = sRB[w][lane];
+            for (uint32_t m = ra; m; m &= m - 1) ka += __popc(ra & sRA[w][__ffs(m) - 1]);
+            for (uint32_t m = rbm; m; m &= m - 1) kb += __popc(rbm & sRB[w][__ffs(m) - 1]);
+            unsigned long long tq = sTq[w][lane];
+            if (tq) atomicAdd(&tpack[rb + lane], tq);
+        }
+        __syncwarp();
+    }
+    acc_add(c, 4, ka);
+    acc_add(c, 10, kb);
+}
+
+constexpr int TB_WORDS = TRI_KM / 32;
+constexpr size_t tri_block_smem() {
+    return (size_t)TRI_KM * 4 + (size_t)TRI_KM * 8 + (size_t)(TRI_KM + 8) * 4 + 2ull * TRI_KM * TB_WORDS * 4 +
+           (size_t)TRI_KM * 8;
+}
+size_t tri_block_smem_bytes() { return tri_block_smem(); }
+
+__global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __restrict__ list,
+                                                  const long long* __restrict__ U_off,
+                                                  const uint32_t* __restrict__ U_col,
+                                                  const int32_t* __restrict__ U_split,
+                                                  unsigned long long* __restrict__ tpack) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long* sNb = (long long*)smem;
+    unsigned long long* sTq = (unsigned long long*)(smem + (size_t)TRI_KM * 8);
+    uint32_t* sX = (uint32_t*)(smem + (size_t)TRI_KM * 16);
+    int* sPre = (int*)(smem + (size_t)TRI_KM * 20);
+    uint32_t* sRA = (uint32_t*)(smem + (size_t)TRI_KM * 24 + 32);
+    uint32_t* sRB = sRA + TRI_KM * TB_WORDS;
+    __shared__ int s_idx;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cnt = c->nbin[BIN_TRI_BLOCK];
+    unsigned long long ka = 0, kb = 0;
+    for (;;) {
+        if (tid == 0) s_idx = (int)atomicAdd(&c->work[1], 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= cnt) break;
+        int32_t u = list[idx];
+        long long rb = U_off[u] + U_split[u];
+        const int k = (int)(U_off[u + 1] - rb);
+        const int W = (k + 31) >> 5;
+        const uint32_t xmax = vid(U_col[rb + k - 1]);
+        for (int t = tid; t < k; t += blockDim.x) {
+            uint32_t x = U_col[rb + t];
+            uint32_t v = vid(x);
+            long long nb = U_off[v] + U_split[v];
+            sX[t] = x;
+            sNb[t] = nb;
+            sPre[t + 1] = (int)lower_bound_id(U_col + nb, U_off[v + 1] - nb, xmax + 1);
+            sTq[t] = 0;
+        }
+        for (int t = tid; t < k * W; t += blockDim.x) {
+            sRA[t] = 0;
+            sRB[t] = 0;
+        }
+        __syncthreads();
+        if (warp == 0) {  // inclusive scan of sPre[1..k]
+            int carry = 0;
+            for (int b = 0; b < k; b += 32) {
+                int x = b + lane < k ? sPre[b + lane + 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (b + lane < k) sPre[b + lane + 1] = x + carry;
+                carry += __shfl_sync(FULL, x, 31);
+            }
+            if (lane == 0) sPre[0] = 0;
+        }
+        __syncthreads();
+        const int total = sPre[k];
+        for (int t = tid; t < total; t += blockDim.x) {
+            int q = find_seg(sPre, k, t);
+            long long slot = sNb[q] + (t - sPre[q]);
+            uint32_t e = U_col[slot];
+            int p = find_pos(sX, k, vid(e));
+            if (p < 0) continue;
+            uint32_t f = sX[q] & sX[p] & e;
+            unsigned long long iv = flag_inc(f);
+            if (!iv) continue;
+            if (f & FLAG_A) atomicOr(&sRA[q * W + (p >> 5)], 1u << (p & 31));
+            if (f & FLAG_B) atomicOr(&sRB[q * W + (p >> 5)], 1u << (p & 31));
+            atomicAdd(&sTq[q], iv);
+            atomicAdd(&sTq[p], iv);
+            atomicAdd(&tpack[slot], iv);
+        }
+        __syncthreads();
+        for (int q = tid; q < k; q += blockDim.x) {
+            const uint32_t* ra = sRA + q * W;
+            const uint32_t* rbm = sRB + q * W;
+            for (int i = 0; i < W; i++) {
+                for (uint32_t m = ra[i]; m; m &= m - 1) {
+                    int p = i * 32 + __ffs(m) - 1;
+                    const uint32_t* rp = sRA + p * W;
+                    for (int i2 = p >> 5; i2 < W; i2++) ka += __popc(ra[i2] & rp[i2]);
+                }
+                for (uint32_t m = rbm[i]; m; m &= m - 1) {
+                    int p = i * 32 + __ffs(m) - 1;
+                    const uint32_t* rp = sRB + p * W;
+                    for (int i2 = p >> 5; i2 < W; i2++) kb += __popc(rbm[i2] & rp[i2]);
+                }
+            }
+            unsigned long long tq = sTq[q];
+            if (tq) atomicAdd(&tpack[rb + q], tq);
+        }
+        __syncthreads();
+    }
+    acc_add(c, 4, ka);
+    acc_add(c, 10, kb);
+}
+
+// Roots with very long out-lists: one warp per root, one lane per out-edge
+// u->v merging N+(u) (after v) with N+(v); 4-cliques by a three-way merge.
+__global__ void k_tri_merge(Ctl* c, const int32_t* __restrict__ list, const long long* __restrict__ U_off,
+                            const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                            unsigned long long* __restrict__ tpack) {
+    const int cnt = c->nbin[BIN_TRI_MERGE];
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long ka = 0, kb = 0;
+    for (int wi = warp; wi < cnt; wi += nwarps) {
+        int32_t u = list[wi];
         long long ob = U_off[u] + U_split[u], oe = U_off[u + 1];
         for (long long e = ob + lane; e < oe; e += 32) {
             uint32_t fe = U_col[e];
@@ -76,7 +356,6 @@ __global__ void k_tri_k4(Ctl* c, const int32_t* __restrict__ wlist, const long l
                         atomicAdd(&tpack[e], inc);
                         atomicAdd(&tpack[i], inc);
                         atomicAdd(&tpack[j], inc);
-                        // 4-cliques through triangle (u, v, x): z in N+(u) n N+(v) n N+(x)
                         long long wb = U_off[x] + U_split[x], we = U_off[x + 1];
                         long long p = i + 1, q = j + 1, r = wb;
                         while (p < oe && q < ve && r < we) {
@@ -103,81 +382,518 @@ __global__ void k_tri_k4(Ctl* c, const int32_t* __restrict__ wlist, const long l
             }
         }
     }
-    ka = warp_sum_u64(ka);
-    kb = warp_sum_u64(kb);
-    if (lane == 0 && (ka | kb)) {
-        atomicAdd(&c->acc[4], ka);
-        atomicAdd(&c->acc[10], kb);
+    acc_add(c, 4, ka);
+    acc_add(c, 10, kb);
+}
+
+// ---- 4-cycles ----------------------------------------------------------------
+
+constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+
+// packed counter: G_a count in the high 16 bits, G_b count in the low 16
+__device__ __forceinline__ uint32_t flag_inc16(uint32_t f) {
+    return ((f & FLAG_A) ? 0x10000u : 0u) | ((f & FLAG_B) ? 1u : 0u);
+}
+
+// open-addressing insert; returns the counter's old value
+__device__ __forceinline__ uint32_t hash_add(uint32_t* keys, uint32_t* cnts, int shift, uint32_t mask, uint32_t w,
+                                             uint32_t inc) {
+    uint32_t h = (w * 0x9E3779B1u) >> shift;
+    for (;;) {
+        uint32_t k = keys[h];
+        if (k == w) return atomicAdd(&cnts[h], inc);
+        if (k == EMPTY_KEY) {
+            uint32_t prev = atomicCAS(&keys[h], EMPTY_KEY, w);
+            if (prev == EMPTY_KEY || prev == w) return atomicAdd(&cnts[h], inc);
+        }
+        h = (h + 1) & mask;
     }
 }
 
-// One block per pivot u (dynamic queue).  Each block owns a dense counter
-// array cnt[0..n) in global memory, zero between pivots: pass 1 adds the
-// wedges u-v-w (v < u, w < u), pass 2 walks the same wedges and takes each
-// counter with an exchange, so every w is summed once and left at zero.
-__global__ void __launch_bounds__(256) k_c4(Ctl* c, const int32_t* __restrict__ wlist,
-                                            const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
-                                            const int32_t* __restrict__ U_split,
-                                            unsigned long long* __restrict__ cnt_all, int n) {
+__device__ __forceinline__ int log2_table(long long wt, int lo_log, int hi_log) {
+    int lg = lo_log;
+    while (lg < hi_log && (1ll << lg) < 2 * wt) lg++;
+    return lg;
+}
+
+// w~ <= 32: every wedge endpoint in one lane; equal endpoints are grouped
+// with __match_any_sync and each group adds C(c, 2).
+__global__ void __launch_bounds__(256) k_c4_reg(Ctl* c, const int32_t* __restrict__ list,
+                                               const long long* __restrict__ U_off,
+                                               const uint32_t* __restrict__ U_col,
+                                               const int32_t* __restrict__ U_split) {
+    __shared__ long long sVb[8][32];
+    __shared__ uint32_t sFv[8][32];
+    __shared__ int sPre[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cnt = c->nbin[BIN_C4_REG];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    for (int i = blockIdx.x * 8 + w; i < cnt; i += gridDim.x * 8) {
+        int32_t u = list[i];
+        long long rb = U_off[u];
+        int nlow = U_split[u];  // 2..32 here
+        int dv = 0;
+        if (lane < nlow) {
+            uint32_t fv = U_col[rb + lane];
+            uint32_t v = vid(fv);
+            long long vb = U_off[v];
+            dv = (int)(U_off[v + 1] - vb);
+            sVb[w][lane] = vb;
+            sFv[w][lane] = fv;
+        }
+        int inc = dv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);  // <= 32
+        sPre[w][lane + 1] = inc;
+        if (lane == 0) sPre[w][0] = 0;
+        __syncwarp();
+        bool ok = false;
+        uint32_t wv = 0, fl = 0;
+        if (lane < total) {
+            int j = find_seg(sPre[w], nlow, lane);
+            uint32_t e = U_col[sVb[w][j] + (lane - sPre[w][j])];
+            wv = vid(e);
+            ok = wv < (uint32_t)u;
+            fl = sFv[w][j] & e & (FLAG_A | FLAG_B);
+        }
+        unsigned okm = __ballot_sync(FULL, ok);
+        if (lane == 0) wedges += __popc(okm);
+        bool valid = ok && fl;
+        unsigned peers = __match_any_sync(FULL, valid ? wv : (0x80000000u | (uint32_t)lane));
+        unsigned ba = __ballot_sync(FULL, valid && (fl & FLAG_A));
+        unsigned bb = __ballot_sync(FULL, valid && (fl & FLAG_B));
+        if (valid && lane == __ffs(peers) - 1) {
+            qa += choose2(__popc(peers & ba));
+            qb += choose2(__popc(peers & bb));
+        }
+        __syncwarp();
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
+
+// Walk the wedges u-v-w of pivot u for the lower neighbours v = N(u)[j],
+// j = j0, j0 + step, ...; calls fn(w, flags) for each w < u.  Warp-uniform.
+template <class Fn>
+__device__ __forceinline__ void walk_wedges(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
+                                            int32_t u, long long rb, int nlow, int j0, int step, Fn fn) {
+    const int lane = threadIdx.x & 31;
+    for (int j = j0; j < nlow; j += step) {
+        uint32_t fv = U_col[rb + j];
+        uint32_t v = vid(fv);
+        long long vb = U_off[v];
+        int dv = (int)(U_off[v + 1] - vb);
+        for (int b = 0; b < dv; b += 32) {
+            int q = b + lane;
+            uint32_t e = q < dv ? U_col[vb + q] : 0xFFFFFFFFu;
+            uint32_t wv = vid(e);
+            bool ok = q < dv && wv < (uint32_t)u;
+            if (ok) fn(wv, fv & e & (FLAG_A | FLAG_B));
+            if (__ballot_sync(FULL, q < dv && wv >= (uint32_t)u)) break;  // rows are sorted
+        }
+    }
+}
+
+constexpr int C4W_WARPS = 4;
+constexpr int C4W_SLOTS = 2 * C4_T1;
+
+__global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_t* __restrict__ list,
+                                                          const long long* __restrict__ U_off,
+                                                          const uint32_t* __restrict__ U_col,
+                                                          const int32_t* __restrict__ U_split) {
+    __shared__ uint32_t sKey[C4W_WARPS][C4W_SLOTS];
+    __shared__ uint32_t sCnt[C4W_WARPS][C4W_SLOTS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cnt = c->nbin[BIN_C4_WARP];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    uint32_t* keys = sKey[w];
+    uint32_t* cnts = sCnt[w];
+    for (int i = blockIdx.x * C4W_WARPS + w; i < cnt; i += gridDim.x * C4W_WARPS) {
+        int32_t u = list[i];
+        long long rb = U_off[u];
+        int nlow = U_split[u];
+        long long wt = 0;
+        for (int j = lane; j < nlow; j += 32) {
+            uint32_t v = vid(U_col[rb + j]);
+            wt += U_off[v + 1] - U_off[v];
+        }
+        wt = (long long)warp_sum_u64((unsigned long long)wt);
+        wt = __shfl_sync(FULL, wt, 0);
+        const int lg = log2_table(wt, 5, 10);
+        const uint32_t mask = (1u << lg) - 1;
+        const int shift = 32 - lg;
+        for (int s = lane; s <= (int)mask; s += 32) {
+            keys[s] = EMPTY_KEY;
+            cnts[s] = 0;
+        }
+        __syncwarp();
+        walk_wedges(U_off, U_col, u, rb, nlow, 0, 1, [&](uint32_t wv, uint32_t fl) {
+            wedges++;
+            if (!fl) return;
+            uint32_t old = hash_add(keys, cnts, shift, mask, wv, flag_inc16(fl));
+            if (fl & FLAG_A) qa += old >> 16;
+            if (fl & FLAG_B) qb += old & 0xFFFFu;
+        });
+        __syncwarp();
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
+
+constexpr int C4B_SLOTS = 2 * C4_T2;
+size_t c4_block_smem_bytes() { return (size_t)C4B_SLOTS * 8; }
+
+__global__ void __launch_bounds__(256) k_c4_block(Ctl* c, const int32_t* __restrict__ list,
+                                                 const long long* __restrict__ U_off,
+                                                 const uint32_t* __restrict__ U_col,
+                                                 const int32_t* __restrict__ U_split) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* keys = (uint32_t*)smem;
+    uint32_t* cnts = keys + C4B_SLOTS;
     __shared__ int s_idx;
-    __shared__ unsigned long long s_q[2][8];
-    unsigned long long* cnt = cnt_all + (size_t)blockIdx.x * n;
-    int nW = c->nW;
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    __shared__ long long s_wt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int cnt = c->nbin[BIN_C4_BLOCK];
     unsigned long long qa = 0, qb = 0, wedges = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[0], 1u);
+        if (tid == 0) {
+            s_idx = (int)atomicAdd(&c->work[2], 1u);
+            s_wt = 0;
+        }
         __syncthreads();
-        int idx = s_idx;
+        const int idx = s_idx;
+        if (idx >= cnt) break;
+        int32_t u = list[idx];
+        long long rb = U_off[u];
+        int nlow = U_split[u];
+        long long wt = 0;
+        for (int j = tid; j < nlow; j += blockDim.x) {
+            uint32_t v = vid(U_col[rb + j]);
+            wt += U_off[v + 1] - U_off[v];
+        }
+        wt = (long long)warp_sum_u64((unsigned long long)wt);
+        if (lane == 0) atomicAdd((unsigned long long*)&s_wt, (unsigned long long)wt);
         __syncthreads();
-        if (idx >= nW) break;
-        int32_t u = wlist[idx];
-        long long rb = U_off[u], nlow = U_split[u];
+        const int lg = log2_table(s_wt, 6, 14);
+        const uint32_t mask = (1u << lg) - 1;
+        const int shift = 32 - lg;
+        for (int s = tid; s <= (int)mask; s += blockDim.x) {
+            keys[s] = EMPTY_KEY;
+            cnts[s] = 0;
+        }
+        __syncthreads();
+        walk_wedges(U_off, U_col, u, rb, nlow, warp, nwarps, [&](uint32_t wv, uint32_t fl) {
+            wedges++;
+            if (!fl) return;
+            uint32_t old = hash_add(keys, cnts, shift, mask, wv, flag_inc16(fl));
+            if (fl & FLAG_A) qa += old >> 16;
+            if (fl & FLAG_B) qb += old & 0xFFFFu;
+        });
+        __syncthreads();
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
+
+// Prefix sums of the row lengths of lower neighbours rb[s0 .. s0+ns) of a
+// pivot, so a pivot's wedges can be split evenly over many threads: wedge i
+// of the segment lies in row j = find_seg(pre, ns, i) at offset i - pre[j].
+// Every thread of the block calls it; ends with __syncthreads().
+__device__ __forceinline__ void wedge_segment_prefix(const long long* __restrict__ U_off,
+                                                     const uint32_t* __restrict__ U_col, long long rb, int s0, int ns,
+                                                     int* pre, long long* vbs, uint32_t* fvs, int* wtot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int j = tid; j < ns; j += blockDim.x) {
+        uint32_t fv = U_col[rb + s0 + j];
+        uint32_t v = vid(fv);
+        long long vb = U_off[v];
+        vbs[j] = vb;
+        fvs[j] = fv;
+        pre[j + 1] = (int)(U_off[v + 1] - vb);
+    }
+    __syncthreads();
+    // two-level scan: each warp scans a contiguous slice, then the slice totals
+    const int per = (ns + nwarps - 1) / nwarps;
+    const int b0 = warp * per, b1 = min(ns, b0 + per);
+    int carry = 0;
+    for (int b = b0; b < b1; b += 32) {
+        int x = b + lane < b1 ? pre[b + lane + 1] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b + lane < b1) pre[b + lane + 1] = x + carry;
+        carry += __shfl_sync(FULL, x, 31);
+    }
+    __shared__ int s_part[33];
+    if (lane == 0) s_part[warp + 1] = carry;
+    __syncthreads();
+    if (tid == 0) {
+        s_part[0] = 0;
+        for (int w = 1; w <= nwarps; w++) s_part[w] += s_part[w - 1];
+        pre[0] = 0;
+        *wtot = s_part[nwarps];
+    }
+    __syncthreads();
+    for (int j = b0 + lane; j < b1; j += 32) pre[j + 1] += s_part[warp];
+    __syncthreads();
+}
+
+constexpr int C4D_SEG = 2048;  // lower neighbours per prefix segment
+constexpr int C4D_UNROLL = 4;
+
+template <bool CLUSTER>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (CLUSTER) {
+        __threadfence();
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Heavy pivots, dense counter array in global memory (16/16-bit packed
+// counts while every degree is below 2^16, else 32/32 in 64-bit words).
+// CLUSTER = true: a cluster of CTAs takes one pivot at a time and shares one
+// array (the heaviest pivots); CLUSTER = false: one CTA per pivot with its
+// own array (the medium ones).  The pivot's wedges are numbered through
+// per-segment prefix sums and dealt in warp-contiguous chunks to every
+// thread of the group (coalesced, balanced even when one lower neighbour has
+// a very long row).  After the increments a group barrier; then the array is
+// cleared, by a vectorised fill of the whole array when the pivot touched a
+// large part of it, else by walking the same wedges again; then another
+// barrier.
+template <bool CLUSTER>
+__global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, const int32_t* __restrict__ list,
+                                                                const long long* __restrict__ U_off,
+                                                                const uint32_t* __restrict__ U_col,
+                                                                const int32_t* __restrict__ U_split,
+                                                                unsigned long long* __restrict__ arrays, int n) {
+    int rank = 0, ncta = 1;
+    if constexpr (CLUSTER) {
+        cg::cluster_group cl = cg::this_cluster();
+        rank = (int)cl.block_rank();
+        ncta = (int)cl.num_blocks();
+    }
+    const int gid = blockIdx.x / ncta;
+    // per-group arrays start on 16-byte boundaries (vectorised clearing)
+    unsigned long long* a64 = arrays + (size_t)gid * (size_t)(((long long)n + 1) & ~1ll);
+    uint32_t* a32 = (uint32_t*)a64;
+    const bool wide = c->maxdeg >= 65536;
+    __shared__ int s_idx, s_tot;
+    __shared__ int s_pre[C4D_SEG + 1];
+    __shared__ long long s_vb[C4D_SEG];
+    __shared__ uint32_t s_fv[C4D_SEG];
+    const long long T = (long long)ncta * blockDim.x;
+    const long long g = (long long)rank * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = rank * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    const int NW = ncta * (int)(blockDim.x >> 5);
+    const int bin = CLUSTER ? BIN_C4_DENSE : BIN_C4_CTA;
+    const int cnt = c->nbin[bin];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    for (;;) {
+        int idx;
+        if constexpr (CLUSTER) {
+            cg::cluster_group cl = cg::this_cluster();
+            if (rank == 0 && threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[3], 1u);
+            cl.sync();
+            idx = *cl.map_shared_rank(&s_idx, 0);
+            cl.sync();
+        } else {
+            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[4], 1u);
+            __syncthreads();
+            idx = s_idx;
+            __syncthreads();
+        }
+        if (idx >= cnt) break;
+        const int32_t u = list[idx];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        long long wall = 0;  // wedge entries of the pivot (all rows, any id)
         for (int pass = 0; pass < 2; pass++) {
-            for (long long k = warp; k < nlow; k += nwarps) {
-                uint32_t fv = U_col[rb + k];
-                uint32_t v = vid(fv);
-                long long vb = U_off[v];
-                long long lenv = lower_bound_id(U_col + vb, U_off[v + 1] - vb, (uint32_t)u);
-                if (pass == 0 && lane == 0) wedges += (unsigned long long)lenv;
-                for (long long q = lane; q < lenv; q += 32) {
-                    uint32_t fw = U_col[vb + q];
-                    uint32_t w = vid(fw);
-                    if (pass == 0) {
-                        unsigned long long inc = flag_inc(fv & fw);
-                        if (inc) atomicAdd(&cnt[w], inc);
-                    } else {
-                        unsigned long long cw = atomicExch(&cnt[w], 0ull);
-                        if (cw) {
-                            qa += choose2(cw >> 32);
-                            qb += choose2(cw & 0xFFFFFFFFull);
+            // pass 0: increments; pass 1: clear by walking (only for small pivots)
+            if (pass == 1) {
+                group_sync<CLUSTER>();
+                if (wall * 8 > n) {
+                    const long long words = wide ? (long long)n : ((long long)n + 1) / 2;  // 64-bit words
+                    uint4* a4 = (uint4*)a64;
+                    const long long n16 = words / 2;
+                    for (long long i = g; i < n16; i += T) a4[i] = make_uint4(0, 0, 0, 0);
+                    if ((words & 1) && g == 0) a64[words - 1] = 0ull;
+                    break;
+                }
+            }
+            for (int s0 = 0; s0 < nlow; s0 += C4D_SEG) {
+                const int ns = min(C4D_SEG, nlow - s0);
+                // a single-segment pivot keeps its prefix for the clearing walk
+                if (pass == 0 || nlow > C4D_SEG)
+                    wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
+                const long long total = s_tot;
+                if (pass == 0) wall += total;
+                // each warp takes C4D_UNROLL consecutive chunks of 32 wedges;
+                // a lane finds its row by stepping forward from the chunk's
+                // first row (rows average tens of entries, so a step or two)
+                const long long wstep = (long long)NW * 32 * C4D_UNROLL;
+                for (long long base = (long long)gwarp * 32 * C4D_UNROLL; base < total; base += wstep) {
+                    uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
+                    int j = find_seg(s_pre, ns, (int)base);
+#pragma unroll
+                    for (int r = 0; r < C4D_UNROLL; r++) {
+                        long long i = base + r * 32 + lane;
+                        e[r] = 0xFFFFFFFFu;
+                        f[r] = 0;
+                        if (i < total) {
+                            while (j + 1 < ns && s_pre[j + 1] <= i) j++;
+                            e[r] = U_col[s_vb[j] + (i - s_pre[j])];
+                            f[r] = s_fv[j];
                         }
                     }
+#pragma unroll
+                    for (int r = 0; r < C4D_UNROLL; r++) {
+                        uint32_t wv = vid(e[r]);
+                        if (wv >= (uint32_t)u) continue;
+                        uint32_t fl = f[r] & e[r] & (FLAG_A | FLAG_B);
+                        if (pass == 0) wedges++;
+                        if (!fl) continue;
+                        if (pass == 1) {
+                            if (wide) a64[wv] = 0ull;
+                            else a32[wv] = 0u;
+                        } else if (wide) {
+                            unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
+                            if (fl & FLAG_A) qa += old >> 32;
+                            if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
+                        } else {
+                            uint32_t old = atomicAdd(&a32[wv], flag_inc16(fl));
+                            if (fl & FLAG_A) qa += old >> 16;
+                            if (fl & FLAG_B) qb += old & 0xFFFFu;
+                        }
+                    }
+                }
+                __syncthreads();  // the next segment reuses the shared arrays
+            }
+        }
+        group_sync<CLUSTER>();
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
+
+// Open-addressing insert into a table in global memory.  A slot holds
+// (w + 1) << 32 | packed counts, 0 = empty; counts stay below 2^16 because a
+// pivot of this tier has fewer than 2^16 lower neighbours.  Returns the
+// packed counts before the increment.
+__device__ __forceinline__ uint32_t ghash_add(unsigned long long* tab, int shift, uint32_t mask, uint32_t w,
+                                              uint32_t inc) {
+    uint32_t h = (w * 0x9E3779B1u) >> shift;
+    const unsigned long long key = (unsigned long long)(w + 1) << 32;
+    for (;;) {
+        unsigned long long cur = __ldcg(&tab[h]);  // from L2: slots change only by atomics
+        if (cur == 0ull) {
+            cur = atomicCAS(&tab[h], 0ull, key | inc);
+            if (cur == 0ull) return 0u;
+        }
+        if ((cur & 0xFFFFFFFF00000000ull) == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
+        h = (h + 1) & mask;
+    }
+}
+
+// Medium pivots (C4_T2 < w~ <= t3): one CTA per pivot with its own hash
+// table in global memory, sized to the pivot (twice the next power of two of
+// w~), so the tables of all CTAs stay small enough for L2.  The wedges are
+// dealt in warp-contiguous chunks as in the dense kernel; the used part of
+// the table is cleared by a vectorised fill after the pivot.
+__global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const int32_t* __restrict__ list,
+                                                             const long long* __restrict__ U_off,
+                                                             const uint32_t* __restrict__ U_col,
+                                                             const int32_t* __restrict__ U_split,
+                                                             unsigned long long* __restrict__ tables,
+                                                             long long table_words) {
+    unsigned long long* tab = tables + (size_t)blockIdx.x * (size_t)table_words;
+    __shared__ int s_idx, s_tot;
+    __shared__ unsigned long long s_wt;
+    __shared__ int s_pre[C4D_SEG + 1];
+    __shared__ long long s_vb[C4D_SEG];
+    __shared__ uint32_t s_fv[C4D_SEG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
+    const int cnt = c->nbin[BIN_C4_CTA];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    for (;;) {
+        if (tid == 0) {
+            s_idx = (int)atomicAdd(&c->work[4], 1u);
+            s_wt = 0;
+        }
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= cnt) break;
+        const int32_t u = list[idx];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        unsigned long long wt = 0;
+        for (int j = tid; j < nlow; j += blockDim.x) {
+            uint32_t v = vid(U_col[rb + j]);
+            wt += (unsigned long long)(U_off[v + 1] - U_off[v]);
+        }
+        wt = warp_sum_u64(wt);
+        if (lane == 0 && wt) atomicAdd(&s_wt, wt);
+        __syncthreads();
+        int lg = 6;
+        while ((1ll << lg) < 2 * (long long)s_wt && (1ll << lg) < table_words) lg++;
+        const uint32_t mask = (1u << lg) - 1;
+        const int shift = 32 - lg;
+        for (int s0 = 0; s0 < nlow; s0 += C4D_SEG) {
+            const int ns = min(C4D_SEG, nlow - s0);
+            wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
+            const long long total = s_tot;
+            const long long wstep = (long long)NW * 32 * C4D_UNROLL;
+            for (long long base = (long long)warp * 32 * C4D_UNROLL; base < total; base += wstep) {
+                uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
+                int j = find_seg(s_pre, ns, (int)base);
+#pragma unroll
+                for (int r = 0; r < C4D_UNROLL; r++) {
+                    long long i = base + r * 32 + lane;
+                    e[r] = 0xFFFFFFFFu;
+                    f[r] = 0;
+                    if (i < total) {
+                        while (j + 1 < ns && s_pre[j + 1] <= i) j++;
+                        e[r] = U_col[s_vb[j] + (i - s_pre[j])];
+                        f[r] = s_fv[j];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < C4D_UNROLL; r++) {
+                    uint32_t wv = vid(e[r]);
+                    if (wv >= (uint32_t)u) continue;
+                    wedges++;
+                    uint32_t fl = f[r] & e[r] & (FLAG_A | FLAG_B);
+                    if (!fl) continue;
+                    uint32_t old = ghash_add(tab, shift, mask, wv, flag_inc16(fl));
+                    if (fl & FLAG_A) qa += old >> 16;
+                    if (fl & FLAG_B) qb += old & 0xFFFFu;
                 }
             }
             __syncthreads();
         }
+        // clear the used part of the table
+        uint4* t4 = (uint4*)tab;
+        for (long long i = tid; i < (1ll << lg) / 2; i += blockDim.x) t4[i] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
     }
-    qa = warp_sum_u64(qa);
-    qb = warp_sum_u64(qb);
-    if (lane == 0 && wedges) atomicAdd(&c->acc[15], wedges);
-    if (lane == 0) {
-        s_q[0][warp] = qa;
-        s_q[1][warp] = qb;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long ta = 0, tb = 0;
-        for (int w = 0; w < nwarps; w++) {
-            ta += s_q[0][w];
-            tb += s_q[1][w];
-        }
-        if (ta | tb) {
-            atomicAdd(&c->acc[5], ta);
-            atomicAdd(&c->acc[11], tb);
-        }
-    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
 }
+
+// ---- per-edge terms and closed forms ----------------------------------------
 
 __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                              const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
@@ -259,6 +975,94 @@ __global__ void k_finalize(Ctl* c, int mode) {
     }
     if (mode == 0 && c->err == 0)
         for (int i = 0; i < 6; i++) c->F[i] += (unsigned long long)(c->Ca[i] - c->Cb[i]);
+}
+
+}  // namespace gcx
+
+// ---- launch sequence of one counting pass -------------------------------------
+
+namespace gcx {
+
+void count_setup_attributes() {
+    cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_block_smem_bytes());
+    cudaFuncSetAttribute(k_c4_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_block_smem_bytes());
+    cudaFuncSetAttribute(k_c4_dense_t<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+int dense_cluster_plan(int want, int sms, int* size_out) {
+    int sizes[2] = {16, 8};
+    for (int i = 0; i < 2; i++) {
+        int cs = sizes[i];
+        if (want && want != cs) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs * std::max(1, sms / cs));
+        cfg.blockDim = dim3(C4_DENSE_THREADS);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, k_c4_dense_t<true>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            active = 0;
+        }
+        if (active > 0) {
+            *size_out = cs;
+            return std::min(active, std::max(1, sms / cs));
+        }
+    }
+    *size_out = 8;
+    return std::max(1, sms / 8);
+}
+
+int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_c4, cudaEvent_t ev_end,
+                     int mode) {
+    const int sms = a.sms;
+    int nl = 0;
+    auto lists = [&](int b) { return a.bins + (size_t)b * a.n_alloc; };
+    long long nw = a.n_alloc > 0 ? a.n_alloc : 1;
+    int gb = (int)std::min<long long>((nw + 255) / 256, 8LL * sms);
+    k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.bins, a.n_alloc,
+                             a.cta_table_words / 2);
+    nl++;
+    if (ev_tri) cudaEventRecord(ev_tri, s);
+    k_tri_warp<<<4 * sms, TW * 32, 0, s>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
+    k_tri_block<<<2 * sms, 256, tri_block_smem_bytes(), s>>>(a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col,
+                                                              a.U_split, a.tpack);
+    k_tri_merge<<<sms, 256, 0, s>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
+    nl += 3;
+    if (ev_c4) cudaEventRecord(ev_c4, s);
+    k_c4_reg<<<4 * sms, 256, 0, s>>>(a.ctl, lists(BIN_C4_REG), a.U_off, a.U_col, a.U_split);
+    k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, s>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split);
+    k_c4_block<<<sms, 256, c4_block_smem_bytes(), s>>>(a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col, a.U_split);
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.dense_cluster_size * a.dense_clusters);
+        cfg.blockDim = dim3(C4_DENSE_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = a.dense_cluster_size;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_c4_dense_t<true>, a.ctl, (const int32_t*)lists(BIN_C4_DENSE),
+                           (const long long*)a.U_off, (const uint32_t*)a.U_col, (const int32_t*)a.U_split, a.dense,
+                           a.n_alloc);
+    }
+    k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
+                                                        a.cta_tables, a.cta_table_words);
+    nl += 5;
+    if (ev_end) cudaEventRecord(ev_end, s);
+    k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
+    k_finalize<<<1, 32, 0, s>>>(a.ctl, mode);
+    nl += 2;
+    return nl;
 }
 
 }  // namespace gcx

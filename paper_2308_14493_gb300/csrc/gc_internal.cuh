@@ -47,7 +47,30 @@ struct Ctl {
     int overflow;                    // commit needs a re-layout
     int err;                         // GC_E* code raised on the device
     unsigned work[8];                // dynamic work counters
+    int nbin[8];                     // sizes of the work bins (see gc_count.cu)
+    int maxdeg;                      // largest union-graph degree in the region
 };
+
+// Work bins of the counting pass: region bins[b * n ...] holds the vertices
+// of bin b.  Triangle roots by out-degree k; 4-cycle pivots by the wedge
+// bound w~ = sum of the degrees of the lower neighbours.
+enum {
+    BIN_TRI_WARP = 0,   // 2 <= k <= 32        warp per root
+    BIN_TRI_BLOCK = 1,  // 32 < k <= TRI_KM     block per root
+    BIN_TRI_MERGE = 2,  // k > TRI_KM           merge per out-edge
+    BIN_C4_REG = 3,     // w~ <= 32             registers (match)
+    BIN_C4_WARP = 4,    // w~ <= C4_T1          warp hash in shared memory
+    BIN_C4_BLOCK = 5,   // w~ <= C4_T2          block hash in shared memory
+    BIN_C4_DENSE = 6,   // w~ > C4_T3           cluster, shared dense counter array
+    BIN_C4_CTA = 7,     // C4_T2 < w~ <= C4_T3  CTA, own hash table in global memory
+    NBINS = 8
+};
+constexpr int TRI_KM = 512;
+constexpr int C4_T1 = 512;
+constexpr int C4_T2 = 8192;
+constexpr long long C4_T3 = 262144;
+constexpr int C4_CLUSTER = 8;       // CTAs per cluster of the dense 4-cycle kernel
+constexpr int C4_DENSE_THREADS = 1024;
 
 // Handle-independent launch geometry.
 struct Dims {

@@ -57,13 +57,41 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* wlist, const uint32_t* vis
 // gc_count.cu
 __global__ void k_reset_count(Ctl* c);
 __global__ void k_zero_u64(unsigned long long* a, const long long* d_len);
-__global__ void k_tri_k4(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
-                         const int32_t* U_split, unsigned long long* tpack);
-__global__ void k_c4(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
-                     const int32_t* U_split, unsigned long long* cnt_all, int n);
 __global__ void k_edge_terms(Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
                              const int32_t* U_split, const unsigned long long* tpack, const int32_t* da,
                              const int32_t* db);
 __global__ void k_finalize(Ctl* c, int mode);
+
+// Device buffers of one counting pass over a region union graph.
+struct CountArgs {
+    Ctl* ctl;
+    const int32_t* wlist;          // region vertices (c->nW of them)
+    const long long* U_off;        // n_alloc + 1
+    const uint32_t* U_col;         // flagged entries
+    const int32_t* U_split;        // start of the out-list per vertex
+    const int32_t* da;             // degree in G_a
+    const int32_t* db;             // degree in G_b
+    unsigned long long* tpack;     // per-entry triangle counters, zeroed
+    int32_t* bins;                 // NBINS * n_alloc
+    unsigned long long* dense;     // dense_clusters * (n_alloc + 1) zeroed words
+    int n_alloc;                   // vertex id bound
+    int dense_clusters;            // clusters of the heavy 4-cycle kernel
+    int dense_cluster_size;        // CTAs per such cluster (8 or 16)
+    unsigned long long* cta_tables; // cta_groups * cta_table_words zeroed words
+    long long cta_table_words;      // power of two; pivots up to half of it use the hash tier
+    int cta_groups;                 // CTAs of the medium 4-cycle kernel (one table each)
+    int sms;
+};
+// Dynamic shared-memory limits of the counting kernels (once per device).
+void count_setup_attributes();
+// Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
+// 16 if the device can co-schedule it, else 8) and the number of clusters.
+int dense_cluster_plan(int want, int sms, int* size_out);
+// Enqueue the counting kernels (binning, triangles / 4-cliques, 4-cycles,
+// edge terms, closed forms with k_finalize(mode)); events, when given, are
+// recorded before the triangle, 4-cycle and edge-term stages.  Returns the
+// number of kernels launched.
+int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_c4, cudaEvent_t ev_end,
+                     int mode);
 
 }  // namespace gcx

@@ -30,7 +30,9 @@ namespace {
 
 constexpr int NA_MAX_N = GC_NOALLOC_MAX_VERTICES;      // vertices
 constexpr long long NA_MAX_E = GC_NOALLOC_MAX_ENTRIES;  // directed adjacency entries (2m)
-constexpr int NA_C4_BLOCKS = 16;                        // blocks of the 4-cycle kernel
+constexpr int NA_DENSE_CLUSTERS = 2;                   // clusters of the heaviest 4-cycle pivots
+constexpr int NA_CTA_GROUPS = 4;                       // CTAs of the medium 4-cycle pivots
+constexpr long long NA_TABLE_WORDS = 1 << 15;          // hash table words per such CTA
 constexpr int NA_TPB = 256;
 
 // byte offsets of the pieces inside the scratch array
@@ -43,14 +45,17 @@ constexpr size_t OFF_DB = al(OFF_DA + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_WL = al(OFF_DB + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_UCOL = al(OFF_WL + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_TPACK = al(OFF_UCOL + 4 * (size_t)NA_MAX_E);
-constexpr size_t OFF_C4 = al(OFF_TPACK + 8 * (size_t)NA_MAX_E);
-constexpr size_t OFF_ERR = al(OFF_C4 + 8 * (size_t)NA_MAX_N * NA_C4_BLOCKS);
+constexpr size_t OFF_BINS = al(OFF_TPACK + 8 * (size_t)NA_MAX_E);
+constexpr size_t OFF_DENSE = al(OFF_BINS + 4 * (size_t)NA_MAX_N * NBINS);
+constexpr size_t OFF_CTA = al(OFF_DENSE + 8 * (size_t)NA_MAX_N * NA_DENSE_CLUSTERS);
+constexpr size_t OFF_ERR = al(OFF_CTA + 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS);
 constexpr size_t SCRATCH_BYTES = al(OFF_ERR + 16);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 std::mutex g_mu;
 void* g_base[128] = {};  // device address of the scratch array, per device ordinal
+int g_sms[128] = {};     // multiprocessors per device
 
 // Checks the caller's CSR (sorted rows, ids in range, no self-loops,
 // symmetric) and builds the flagged union-graph view the counting kernels read:
@@ -141,15 +146,20 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return GC_ECUDA;
     void* base = nullptr;
+    int sms = 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_base[dev]) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return GC_ECUDA;
+            if (cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return GC_ECUDA;
+            count_setup_attributes();
             g_base[dev] = p;
         }
         base = g_base[dev];
+        sms = g_sms[dev];
     }
     unsigned char* b = (unsigned char*)base;
     Ctl* ctl = (Ctl*)(b + OFF_CTL);
@@ -160,7 +170,9 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     int32_t* wlist = (int32_t*)(b + OFF_WL);
     uint32_t* U_col = (uint32_t*)(b + OFF_UCOL);
     unsigned long long* tpack = (unsigned long long*)(b + OFF_TPACK);
-    unsigned long long* c4 = (unsigned long long*)(b + OFF_C4);
+    int32_t* bins = (int32_t*)(b + OFF_BINS);
+    unsigned long long* dense = (unsigned long long*)(b + OFF_DENSE);
+    unsigned long long* cta_tables = (unsigned long long*)(b + OFF_CTA);
     int* bad = (int*)(b + OFF_ERR);
     cudaStream_t s = (cudaStream_t)stream;
     int nn = n > 0 ? n : 1;
@@ -171,7 +183,9 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     // 4-cycle counters (an interrupted earlier call may have left them dirty)
     k_na_reset<<<1, 32, 0, s>>>(ctl, bad);
     cudaMemsetAsync(tpack, 0, 8 * (size_t)std::max<long long>(nnz, 1), s);
-    cudaMemsetAsync(c4, 0, 8 * (size_t)nn * NA_C4_BLOCKS, s);
+    // per-cluster counter arrays are laid out with an even word stride
+    cudaMemsetAsync(dense, 0, 8 * (size_t)((nn + 1) & ~1) * NA_DENSE_CLUSTERS, s);
+    cudaMemsetAsync(cta_tables, 0, 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS, s);
     k_reset_count<<<1, 32, 0, s>>>(ctl);
     k_na_build<<<grid, NA_TPB, 0, s>>>(d_row_ptr, d_col, n, nnz, ctl, U_off, U_col, U_split, da, db, wlist, bad);
     k_na_fill<<<grid, NA_TPB, 0, s>>>(d_row_ptr, d_col, n, nnz, U_col, bad);
@@ -183,11 +197,25 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return GC_ECUDA;
     if (hbad) return GC_EINVAL;
-    int gw = 64;
-    k_tri_k4<<<gw, NA_TPB, 0, s>>>(ctl, wlist, U_off, U_col, U_split, tpack);
-    k_c4<<<NA_C4_BLOCKS, NA_TPB, 0, s>>>(ctl, wlist, U_off, U_col, U_split, c4, nn);
-    k_edge_terms<<<gw, NA_TPB, 0, s>>>(ctl, wlist, U_off, U_col, U_split, tpack, da, db);
-    k_finalize<<<1, 32, 0, s>>>(ctl, 1);
+    CountArgs ca;
+    ca.ctl = ctl;
+    ca.wlist = wlist;
+    ca.U_off = U_off;
+    ca.U_col = U_col;
+    ca.U_split = U_split;
+    ca.da = da;
+    ca.db = db;
+    ca.tpack = tpack;
+    ca.bins = bins;
+    ca.dense = dense;
+    ca.n_alloc = nn;
+    ca.dense_clusters = NA_DENSE_CLUSTERS;
+    ca.dense_cluster_size = 8;
+    ca.cta_tables = cta_tables;
+    ca.cta_table_words = NA_TABLE_WORDS;
+    ca.cta_groups = NA_CTA_GROUPS;
+    ca.sms = sms;
+    enqueue_counting(ca, s, nullptr, nullptr, nullptr, 1);
     long long Ca[6];
     cudaMemcpyAsync(Ca, ctl->Ca, sizeof(Ca), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);

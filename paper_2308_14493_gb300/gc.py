@@ -30,7 +30,7 @@ class GCError(RuntimeError):
 class gc_options(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class gc_stats(ctypes.Structure):
