@@ -151,7 +151,21 @@ int gc_apply_batches(gc_graph *g, const int32_t *const *ins, const int64_t *n_in
                      const int32_t *const *del, const int64_t *n_del, int32_t k,
                      int32_t independent, uint64_t *out);
 
-/* Record of the last batch. */
+/*
+ * As gc_apply_batches, with every pair already in device memory.
+ *   d_pairs   device int32 pairs [.][2]
+ *   batches   host int64[k][4]: for batch i, {ins_off, n_ins, del_off, n_del}
+ *             -- its insertions are pairs d_pairs[ins_off .. ins_off+n_ins),
+ *             its deletions d_pairs[del_off .. del_off+n_del)
+ *   out       host uint64[k][6]
+ * The caller guarantees every id is in [0, n) and no pair is a self-loop
+ * (a batch that breaks this is not applied and the call returns GC_EINVAL).
+ */
+int gc_apply_batches_device(gc_graph *g, const int32_t *d_pairs, const int64_t *batches, int32_t k,
+                            int32_t independent, uint64_t *out);
+
+/* Record of the last batch (of a batched call: its last batch, with the
+   run's device time in ms_device and its total launches). */
 int gc_batch_stats(const gc_graph *g, gc_stats *s);
 
 /* Edges currently in the graph. */

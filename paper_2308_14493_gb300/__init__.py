@@ -11,6 +11,7 @@ from .gc import (  # noqa: F401
     gc_apply_batch,
     gc_apply_batch_device,
     gc_apply_batches,
+    gc_apply_batches_device,
     gc_batch_stats,
     gc_close,
     gc_count_static,

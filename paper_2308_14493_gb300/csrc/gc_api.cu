@@ -11,7 +11,10 @@
 //   a8 commit G <- G \ D u A into the slack-padded rows  gc_batch.cu
 //
 // Every stage reads its sizes from the device control block, so the host
-// only enqueues work and reads the control block back once per batch.
+// only enqueues work.  The plain form enqueues one batch and reads the
+// control block back once.  The batched form captures the same sequence once
+// in a CUDA graph that takes its batch from a device-side cursor, and replays
+// it for every batch of a run without host round trips.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -59,9 +62,10 @@ struct gc_graph {
     long long* row_start = nullptr;
     long long col_capacity = 0;
     Ctl* ctl = nullptr;
-    Ctl* h_ctl = nullptr;           // pinned mirror
-    long long* desc = nullptr;      // device: [ins_off, n_ins, del_off, n_del, misc...]
-    long long* h_desc = nullptr;    // pinned
+    Ctl* h_ctl = nullptr;            // pinned mirror
+    long long* desc = nullptr;       // device run descriptor: [pair bases, then 4 words per batch]
+    long long* h_desc = nullptr;     // pinned staging of the descriptor
+    long long desc_cap = 0;          // words of desc / h_desc
     int2 *segA = nullptr, *segD = nullptr;
     uint32_t* visited = nullptr;
     int32_t *wlist = nullptr, *U_deg = nullptr, *U_split = nullptr, *da = nullptr, *db = nullptr;
@@ -73,12 +77,20 @@ struct gc_graph {
     Buf<int32_t> keepA, keepD, srcA, dstA, srcD, dstD, plan_cap, plan_deg, pairs;
     Buf<long long> posA, posD, plan_dst, plan_scr, bsum;
     Buf<uint32_t> hist;
-    Buf<unsigned long long> dense;      // counter arrays of the heaviest 4-cycle pivots (per cluster)
-    Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
-    int cta_groups = 0;
+    Buf<unsigned long long> out_dev;     // per-batch results of a batched run
+    Buf<unsigned long long> dense;       // counter arrays of the heaviest 4-cycle pivots (per cluster)
     int dense_clusters = 0;
     int dense_cluster_size = 8;
-    int32_t* bins = nullptr;        // NBINS * n work lists of the counting pass
+    Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
+    int cta_groups = 0;
+    int32_t* bins = nullptr;             // NBINS * n work lists of the counting pass
+    // captured batch graph and the shape it was captured for
+    cudaGraphExec_t gexec = nullptr;
+    long long g_nk = -1;
+    int g_commit = -1;
+    unsigned long long g_gen = 0;
+    int g_launches = 0;                  // kernels in one replay
+    unsigned long long buf_gen = 1;      // bumped whenever a buffer moves
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
     long long m = 0;
@@ -117,6 +129,7 @@ static bool ensure(gc_graph* g, Buf<T>& b, size_t count) {
     dfree(g, b.p);
     b.p = (T*)dalloc(g, nc * sizeof(T));
     b.cap = b.p ? nc : 0;
+    g->buf_gen++;
     return b.p != nullptr;
 }
 
@@ -162,57 +175,149 @@ static int grid_warps(gc_graph* g) { return 8 * g->sms; }  // 8 warps per block
 // small device helpers local to this file
 // ---------------------------------------------------------------------------
 namespace gcx {
-__global__ void k_begin_batch(Ctl* c, const long long* desc, int commit_reset) {
+
+// desc: [0] insertion pair base, [1] deletion pair base, then per batch
+// [ins_off, n_ins, del_off, n_del].  The batch index is the run cursor when
+// use_cursor is set, else 0.  A halted run (a commit waiting for pool space)
+// makes every later batch empty and inactive.
+struct BatchArg {
+    const int32_t* ins;
+    const int32_t* del;
+    long long n_ins, n_del;
+};
+
+__global__ void k_begin_batch(Ctl* c, const long long* desc, int use_cursor, BatchArg a) {
     if (threadIdx.x != 0) return;
-    c->n_ins = desc[1];
-    c->n_del = desc[3];
-    c->nkeys = 2 * (desc[1] + desc[3]);
+    const bool run = c->halt == 0;
+    c->active = run ? 1 : 0;
+    if (use_cursor) {
+        // the descriptor is rewritten by host copies between runs: read it
+        // from L2, never through the read-only cache path
+        const long long* b = desc + 2 + 4 * (long long)c->cur;
+        c->pairs_ins = (const int32_t*)__ldcg(desc);
+        c->pairs_del = (const int32_t*)__ldcg(desc + 1);
+        c->ins_off = run ? __ldcg(b) : 0;
+        c->n_ins = run ? __ldcg(b + 1) : 0;
+        c->del_off = run ? __ldcg(b + 2) : 0;
+        c->n_del = run ? __ldcg(b + 3) : 0;
+    } else {
+        c->pairs_ins = a.ins;
+        c->pairs_del = a.del;
+        c->ins_off = 0;
+        c->del_off = 0;
+        c->n_ins = run ? a.n_ins : 0;
+        c->n_del = run ? a.n_del : 0;
+    }
+    c->nkeys = 2 * (c->n_ins + c->n_del);
     c->nA2 = c->nD2 = 0;
-    for (int i = 0; i < 8; i++) c->st[i] = 0;
+    for (int k = 0; k < 8; k++) c->st[k] = 0;
     c->nW = 0;
-    for (int i = 0; i < MAX_HOPS + 2; i++) c->lvl[i] = 0;
+    for (int k = 0; k < MAX_HOPS + 2; k++) c->lvl[k] = 0;
     c->nU = 0;
     c->scratch_tail = 0;
     c->overflow = 0;
     c->err = 0;
-    (void)commit_reset;
 }
+
+// result of the current batch to out[cur], advance the cursor
+__global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit) {
+    if (threadIdx.x != 0 || !c->active) return;
+    for (int k = 0; k < 6; k++) out[6 * (long long)c->cur + k] = c->last_out[k];
+    if (commit && !c->err) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
+    c->cur++;
+}
+
+__global__ void k_run_reset(Ctl* c) {
+    if (threadIdx.x != 0) return;
+    c->cur = 0;
+    c->halt = 0;
+    c->m_delta = 0;
+}
+
+// restore the kept-entry counts of the batch whose commit is pending
+__global__ void k_resume_pending(Ctl* c) {
+    if (threadIdx.x != 0) return;
+    c->nA2 = c->pend_nA2;
+    c->nD2 = c->pend_nD2;
+    c->lvl[0] = c->pend_ns;
+    c->active = 1;
+    c->err = 0;
+}
+
+__global__ void k_halt_clear(Ctl* c) {
+    if (threadIdx.x == 0) c->halt = 0;
+}
+
 __global__ void k_commit_reset(Ctl* c, unsigned long long pool_tail, int set_pool) {
     if (threadIdx.x != 0) return;
     c->scratch_tail = 0;
     c->overflow = 0;
     if (set_pool) c->pool_tail = pool_tail;
 }
+
 __global__ void k_set_F(Ctl* c) {
     if (threadIdx.x < 6) c->F[threadIdx.x] = (unsigned long long)c->Ca[threadIdx.x];
 }
+
+__global__ void k_mark_active(Ctl* c) {
+    if (threadIdx.x == 0) c->active = 1;
+}
+
 }  // namespace gcx
 
 // ---------------------------------------------------------------------------
 // pipeline pieces
 // ---------------------------------------------------------------------------
-static int plan_region_buffers(gc_graph* g, long long n_ins) {
-    size_t ucap = (size_t)(2 * g->m + 2 * n_ins + 64);
+static int plan_region_buffers(gc_graph* g, long long max_edges, long long n_ins) {
+    size_t ucap = (size_t)(2 * max_edges + 2 * n_ins + 64);
     if (!ensure(g, g->U_col, ucap)) return nomem(g, "region adjacency");
     if (!ensure(g, g->tpack, ucap)) return nomem(g, "triangle counters");
     return GC_OK;
 }
 
-// U build + counting + closed forms. mode: 0 batch, 1 static, 2 static that sets F
-static int count_region(gc_graph* g, int mode) {
+static int plan_batch_buffers(gc_graph* g, long long nk) {
+    size_t nkb = (size_t)std::max<long long>(nk, 1);
+    if (!ensure(g, g->keys, nkb) || !ensure(g, g->keys_tmp, nkb) || !ensure(g, g->keepA, nkb) ||
+        !ensure(g, g->keepD, nkb) || !ensure(g, g->posA, nkb + 1) || !ensure(g, g->posD, nkb + 1) ||
+        !ensure(g, g->srcA, nkb) || !ensure(g, g->dstA, nkb) || !ensure(g, g->srcD, nkb) ||
+        !ensure(g, g->dstD, nkb) || !ensure(g, g->plan_dst, nkb) || !ensure(g, g->plan_scr, nkb) ||
+        !ensure(g, g->plan_cap, nkb) || !ensure(g, g->plan_deg, nkb))
+        return nomem(g, "batch scratch");
+    if (!ensure(g, g->hist, (size_t)256 * radix_grid(nk, g->sms))) return nomem(g, "sort histogram");
+    return GC_OK;
+}
+
+static int ensure_desc(gc_graph* g, long long words) {
+    if (g->desc && g->desc_cap >= words) return GC_OK;
+    long long nc = std::max<long long>(words + words / 4, 64);
+    if (g->h_desc) cudaFreeHost(g->h_desc);
+    dfree(g, g->desc);
+    g->h_desc = nullptr;
+    g->desc = (long long*)dalloc(g, sizeof(long long) * (size_t)nc);
+    g->buf_gen++;
+    if (!g->desc || cudaMallocHost((void**)&g->h_desc, sizeof(long long) * (size_t)nc) != cudaSuccess) {
+        g->desc_cap = 0;
+        return nomem(g, "batch descriptor");
+    }
+    g->desc_cap = nc;
+    return GC_OK;
+}
+
+// U build + counting + closed forms.
+//   fin: k_finalize mode (0 committed batch, 1 static, 2 independent batch)
+//   set_F: a static count that initialises F; timed: record stage events
+static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
-    g->launches++;
     k_reset_count<<<1, 32, 0, s>>>(g->ctl);
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
-    g->launches++;
     k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg);
+    g->launches += 2;
     g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
-    g->launches++;
     k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
                                 g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
-    g->launches++;
     k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
+    g->launches += 2;
     CountArgs ca;
     ca.ctl = g->ctl;
     ca.wlist = g->wlist;
@@ -231,12 +336,13 @@ static int count_region(gc_graph* g, int mode) {
     ca.cta_table_words = 2 * C4_T3;
     ca.cta_groups = g->cta_groups;
     ca.sms = g->sms;
-    g->launches += enqueue_counting(ca, s, g->ev[3], g->ev[4], g->ev[5], mode == 0 ? 0 : 1);
-    if (mode == 2) {
-        g->launches++;
+    g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
+                                    timed ? g->ev[5] : nullptr, fin);
+    if (set_F) {
         k_set_F<<<1, 32, 0, s>>>(g->ctl);
+        g->launches++;
     }
-    CK(cudaEventRecord(g->ev[6], s));
+    if (timed) CK(cudaEventRecord(g->ev[6], s));
     CKL();
     return GC_OK;
 }
@@ -244,28 +350,91 @@ static int count_region(gc_graph* g, int mode) {
 static int enqueue_commit(gc_graph* g) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
-    g->launches++;
     k_commit_plan<<<grid_elems(g, std::max<long long>(g->keys.cap, 1)), TPB, 0, s>>>(
         g->ctl, g->wlist, g->segA, g->segD, g->deg, g->cap, g->row_start, g->col_capacity, g->slack,
         g->plan_dst.p, g->plan_cap.p, g->plan_deg.p, g->plan_scr.p);
     // the region adjacency buffer is free again and is large enough for every
     // rewritten row: use it as the merge scratch
-    g->launches++;
     k_commit_merge<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->segA, g->segD, g->dstA.p, g->dstD.p, g->deg, g->row_start,
                                       g->col, g->plan_scr.p, g->U_col.p);
-    g->launches++;
     k_commit_write<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->plan_dst.p, g->plan_cap.p, g->plan_deg.p,
                                       g->plan_scr.p, g->U_col.p, g->deg, g->cap, g->row_start, g->col);
+    g->launches += 3;
     CKL();
     return GC_OK;
 }
 
-static int enqueue_clear_segments(gc_graph* g) {
+static int enqueue_segments(gc_graph* g, bool clear) {
     int ge = grid_elems(g, std::max<long long>(g->keys.cap, 1));
+    if (clear) {
+        k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+        k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+    } else {
+        k_batch_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
+        k_batch_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+    }
+    g->launches += 2;
+    CKL();
+    return GC_OK;
+}
+
+// One batch of Algorithm 2, all stages, on g->s.  Grids are sized for batches
+// of up to max_nk directed keys; the actual sizes are read on the device.
+//   use_cursor: take the batch from the run cursor (batched form)
+//   commit:     apply G <- G \ D u A (else an independent what-if batch)
+//   timed:      record the stage events (not while capturing)
+static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool commit, bool timed,
+                         BatchArg arg = BatchArg{nullptr, nullptr, 0, 0}) {
+    cudaStream_t s = g->s;
+    if (timed) CK(cudaEventRecord(g->ev[0], s));
+    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, use_cursor ? 1 : 0, arg);
     g->launches++;
-    k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
-    g->launches++;
-    k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+    const long long nkb = std::max<long long>(max_nk, 1);
+    const int ge = grid_elems(g, nkb);
+    if (max_nk > 0) {
+        k_batch_keys<<<grid_elems(g, nkb / 2), TPB, 0, s>>>(g->ctl, g->perm, g->n, g->S, g->keys.p);
+        g->launches++;
+        g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nkb, 2 * g->S + 1, g->hist.p,
+                                      radix_grid(nkb, g->sms), s);
+        k_batch_decide<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col, g->keepA.p,
+                                          g->keepD.p);
+        g->launches++;
+        int sg = scan_grid(nkb, g->sms);
+        g->launches += scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
+        g->launches += scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
+        k_batch_compact<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p, g->posA.p, g->posD.p,
+                                           g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
+        g->launches++;
+        int rc = enqueue_segments(g, false);
+        if (rc) return rc;
+    }
+    if (timed) CK(cudaEventRecord(g->ev[1], s));
+    CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+    k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
+    k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
+    g->launches += 2;
+    for (int L = 1; L <= g->hops; L++) {
+        k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
+        k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
+        g->launches += 2;
+    }
+    CKL();
+    if (timed) CK(cudaEventRecord(g->ev[2], s));
+    int rc = count_region(g, commit ? 0 : 2, false, timed);
+    if (rc) return rc;
+    if (commit) {
+        rc = enqueue_commit(g);
+        if (rc) return rc;
+    }
+    if (timed) CK(cudaEventRecord(g->ev[7], s));
+    if (max_nk > 0) {
+        rc = enqueue_segments(g, true);
+        if (rc) return rc;
+    }
+    if (use_cursor) {
+        k_end_batch<<<1, 32, 0, s>>>(g->ctl, g->out_dev.p, commit ? 1 : 0);
+        g->launches++;
+    }
     CKL();
     return GC_OK;
 }
@@ -277,9 +446,8 @@ static int relayout(gc_graph* g, long long pool_extra) {
     int n = g->n;
     long long* new_start = (long long*)dalloc(g, sizeof(long long) * (size_t)(n + 1));
     if (!new_start) return nomem(g, "row offsets");
-    g->launches++;
     k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
-    g->launches += scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+    scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
     long long total = 0;
     CK(cudaMemcpyAsync(&total, new_start + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -290,9 +458,7 @@ static int relayout(gc_graph* g, long long pool_extra) {
         dfree(g, new_start);
         return nomem(g, "adjacency pool");
     }
-    g->launches++;
     k_copy_rows<<<grid_warps(g), TPB, 0, s>>>(g->deg, n, g->row_start, g->col, new_start, ncol);
-    g->launches++;
     k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
     CKL();
     dfree(g, g->col);
@@ -300,7 +466,46 @@ static int relayout(gc_graph* g, long long pool_extra) {
     g->col = ncol;
     g->row_start = new_start;
     g->col_capacity = ncap;
+    g->buf_gen++;  // captured graphs hold the old adjacency pointers
     return GC_OK;
+}
+
+static int read_ctl(gc_graph* g) {
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->s));
+    CK(cudaStreamSynchronize(g->s));
+    return GC_OK;
+}
+
+// A commit ran out of pool space: the rows are untouched.  Grow the pool and
+// commit the pending batch again (its kept entries are still in scratch).
+static int finish_pending_commit(gc_graph* g, int* relayouts) {
+    for (int tries = 0;; tries++) {
+        const Ctl& c = *g->h_ctl;
+        long long extra = 4 * (c.pend_nA2 + c.pend_nD2) + 1024;
+        for (int i = 0; i < tries; i++) extra *= 2;
+        int rc = relayout(g, extra);
+        if (rc) return rc;
+        (*relayouts)++;
+        k_resume_pending<<<1, 32, 0, g->s>>>(g->ctl);
+        k_halt_clear<<<1, 32, 0, g->s>>>(g->ctl);
+        CKL();
+        rc = enqueue_segments(g, false);
+        if (rc) return rc;
+        rc = enqueue_commit(g);
+        if (rc) return rc;
+        rc = read_ctl(g);
+        if (rc) return rc;
+        if (!g->h_ctl->overflow) break;
+        if (tries >= 4) {
+            g->err = "adjacency pool could not be grown enough";
+            return GC_ENOMEM;
+        }
+    }
+    int rc = enqueue_segments(g, true);
+    if (rc) return rc;
+    k_halt_clear<<<1, 32, 0, g->s>>>(g->ctl);
+    CKL();
+    return read_ctl(g);
 }
 
 static void fill_stats(gc_graph* g, const Ctl& c) {
@@ -325,105 +530,33 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
     }
 }
 
-// One batch whose pairs are already in device memory.
+// One batch whose pairs are already in device memory (plain form).
 static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, const int32_t* d_del,
                         long long n_del, int commit, uint64_t out[6]) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = g->s;
     long long nk = 2 * (n_ins + n_del);
-    size_t nkb = (size_t)std::max<long long>(nk, 1);
-    if (!ensure(g, g->keys, nkb) || !ensure(g, g->keys_tmp, nkb) || !ensure(g, g->keepA, nkb) ||
-        !ensure(g, g->keepD, nkb) || !ensure(g, g->posA, nkb + 1) || !ensure(g, g->posD, nkb + 1) ||
-        !ensure(g, g->srcA, nkb) || !ensure(g, g->dstA, nkb) || !ensure(g, g->srcD, nkb) ||
-        !ensure(g, g->dstD, nkb) || !ensure(g, g->plan_dst, nkb) || !ensure(g, g->plan_scr, nkb) ||
-        !ensure(g, g->plan_cap, nkb) || !ensure(g, g->plan_deg, nkb))
-        return nomem(g, "batch scratch");
-    int rg = radix_grid(nk, g->sms);
-    if (!ensure(g, g->hist, (size_t)256 * rg)) return nomem(g, "sort histogram");
-    int rc = plan_region_buffers(g, n_ins);
+    int rc = plan_batch_buffers(g, nk);
+    if (rc) return rc;
+    rc = plan_region_buffers(g, g->m, n_ins);
     if (rc) return rc;
     g->launches = 0;
-    g->h_desc[0] = 0;
-    g->h_desc[1] = n_ins;
-    g->h_desc[2] = 0;
-    g->h_desc[3] = n_del;
     CK(cudaEventRecord(g->e0, s));
-    CK(cudaMemcpyAsync(g->desc, g->h_desc, 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
-    CK(cudaEventRecord(g->ev[0], s));
-    g->launches++;
-    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, 0);
-    int ge = grid_elems(g, nkb);
-    if (nk > 0) {
-        g->launches++;
-        k_batch_keys<<<grid_elems(g, n_ins + n_del), TPB, 0, s>>>(d_ins, d_del, g->ctl, g->perm, g->n, g->S,
-                                                                   g->keys.p);
-        g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nk, 2 * g->S + 1, g->hist.p, rg, s);
-        g->launches++;
-        k_batch_decide<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col, g->keepA.p,
-                                          g->keepD.p);
-        int sg = scan_grid(nk, g->sms);
-        g->launches += scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
-        g->launches += scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
-        g->launches++;
-        k_batch_compact<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p, g->posA.p, g->posD.p,
-                                           g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
-        g->launches++;
-        k_batch_segments<<<ge, TPB, 0, s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
-        g->launches++;
-        k_batch_segments<<<ge, TPB, 0, s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
-    }
-    CK(cudaEventRecord(g->ev[1], s));
-    CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
-    g->launches++;
-    k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
-    g->launches++;
-    k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
-    for (int L = 1; L <= g->hops; L++) {
-        g->launches++;
-        k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
-        g->launches++;
-        k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
-    }
-    CKL();
-    CK(cudaEventRecord(g->ev[2], s));
-    rc = count_region(g, 0);
+    rc = enqueue_batch(g, nk, false, commit != 0, true, BatchArg{d_ins, d_del, n_ins, n_del});
     if (rc) return rc;
-    if (commit) {
-        rc = enqueue_commit(g);
-        if (rc) return rc;
-    }
-    CK(cudaEventRecord(g->ev[7], s));
     CK(cudaEventRecord(g->e1, s));
-    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    Ctl c = *g->h_ctl;
+    rc = read_ctl(g);
+    if (rc) return rc;
     int relayouts = 0;
-    if (c.err) {
-        enqueue_clear_segments(g);
-        CK(cudaStreamSynchronize(s));
+    if (g->h_ctl->err) {
         g->err = "batch rejected on the device: a pair is a self-loop or names a vertex outside [0, n)";
         return GC_EINVAL;
     }
-    while (commit && c.overflow) {
-        // the rows were not touched; grow the pool and commit again
-        long long extra = 4 * (c.nA2 + c.nD2) + 1024;
-        for (int i = 0; i < relayouts; i++) extra *= 2;
-        rc = relayout(g, extra);
+    if (commit && g->h_ctl->overflow) {
+        rc = finish_pending_commit(g, &relayouts);
         if (rc) return rc;
-        relayouts++;
-        rc = enqueue_commit(g);
-        if (rc) return rc;
-        CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        c = *g->h_ctl;
-        if (relayouts > 4) {
-            g->err = "adjacency pool could not be grown enough";
-            return GC_ENOMEM;
-        }
     }
-    rc = enqueue_clear_segments(g);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(s));
+    Ctl c = *g->h_ctl;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, g->e0, g->e1);
     fill_stats(g, c);
@@ -432,57 +565,174 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     g->st.ms_device = ms;
     g->st.relayouts = relayouts;
     g->st.launches = g->launches;
-    {
-        // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
-        // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
-        for (int i = 0; i < 7; i++) {
-            float x = 0.f;
-            cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]);
-            g->st.ms_stage[i] = x;
-        }
-        g->st.ms_stage[7] = 0.f;
+    // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
+    // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
+    for (int i = 0; i < 7; i++) {
+        float x = 0.f;
+        cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]);
+        g->st.ms_stage[i] = x;
     }
-    uint64_t res[6];
-    for (int i = 0; i < 6; i++) res[i] = (uint64_t)c.F[i] + (commit ? 0ull : (uint64_t)(c.Ca[i] - c.Cb[i]));
+    g->st.ms_stage[7] = 0.f;
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
         g->m += c.nA2 / 2 - c.nD2 / 2;
-    } else {
-        // independent batch: restore the maintained counts on the device
-        CK(cudaMemcpyAsync(g->ctl->F, g->F, sizeof(g->F), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-        for (int i = 0; i < 6; i++) res[i] = g->F[i] + (uint64_t)(c.Ca[i] - c.Cb[i]);
     }
     g->st.num_edges = g->m;
     if (out)
-        for (int i = 0; i < 6; i++) out[i] = res[i];
-    g->st.ms_wall =
-        std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (int i = 0; i < 6; i++) out[i] = c.last_out[i];
+    g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return GC_OK;
 }
 
-static int count_static(gc_graph* g, int mode, uint64_t out[6]) {
+// Batched form: k batches whose pairs are in device memory, described by
+// h_batches[k][4] = {ins_off, n_ins, del_off, n_del} (in pairs, relative to
+// d_ins / d_del).  One captured graph per batch shape, replayed k times.
+static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t* d_del, const long long* h_batches,
+                                int k, int independent, uint64_t* out) {
+    auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = g->s;
-    int rc = plan_region_buffers(g, 0);
+    const bool commit = !independent;
+    long long max_nk = 0, max_ins = 0, sum_ins = 0, raw_ins = 0, raw_del = 0;
+    for (int i = 0; i < k; i++) {
+        long long ni = h_batches[4 * i + 1], nd = h_batches[4 * i + 3];
+        max_nk = std::max(max_nk, 2 * (ni + nd));
+        max_ins = std::max(max_ins, ni);
+        sum_ins += ni;
+        raw_ins = ni;
+        raw_del = nd;
+    }
+    // grids are sized by powers of two of the largest batch, so runs of
+    // similar shape share one captured graph
+    long long shape_nk = 1;
+    while (shape_nk < max_nk) shape_nk <<= 1;
+    int rc = plan_batch_buffers(g, shape_nk);
     if (rc) return rc;
+    rc = plan_region_buffers(g, g->m + (commit ? sum_ins : max_ins), max_ins);
+    if (rc) return rc;
+    rc = ensure_desc(g, 2 + 4LL * k);
+    if (rc) return rc;
+    if (!ensure(g, g->out_dev, (size_t)6 * std::max(k, 1))) return nomem(g, "batch results");
+    g->h_desc[0] = (long long)d_ins;
+    g->h_desc[1] = (long long)d_del;
+    std::memcpy(g->h_desc + 2, h_batches, sizeof(long long) * 4 * (size_t)k);
+    CK(cudaMemcpyAsync(g->desc, g->h_desc, sizeof(long long) * (2 + 4 * (size_t)k), cudaMemcpyHostToDevice, s));
+    k_run_reset<<<1, 32, 0, s>>>(g->ctl);
+    CKL();
+    // (re)capture the per-batch graph when its shape or any buffer changed
+    if (!g->gexec || g->g_nk != shape_nk || g->g_commit != (int)commit || g->g_gen != g->buf_gen) {
+        if (g->gexec) {
+            cudaGraphExecDestroy(g->gexec);
+            g->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int lsave = g->launches;
+        g->launches = 0;
+        rc = enqueue_batch(g, shape_nk, true, commit, false);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        g->g_launches = g->launches;
+        g->launches = lsave;
+        if (rc) return rc;
+        if (ce != cudaSuccess) {
+            g->err = std::string("graph capture: ") + cudaGetErrorString(ce);
+            return GC_ECUDA;
+        }
+        ce = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            g->gexec = nullptr;
+            g->err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+            return GC_ECUDA;
+        }
+        g->g_nk = shape_nk;
+        g->g_commit = (int)commit;
+        g->g_gen = g->buf_gen;
+    }
+    CK(cudaEventRecord(g->e0, s));
+    int relayouts = 0, done = 0;
+    while (done < k) {
+        for (int i = done; i < k; i++) CK(cudaGraphLaunch(g->gexec, s));
+        rc = read_ctl(g);
+        if (rc) return rc;
+        done = g->h_ctl->cur;
+        if (g->h_ctl->halt) {
+            // batch done-1 is counted but its commit waits for pool space
+            rc = finish_pending_commit(g, &relayouts);
+            if (rc) return rc;
+            if (g->gexec && g->g_gen != g->buf_gen) {
+                // the adjacency moved: capture again for the remaining batches
+                cudaGraphExecDestroy(g->gexec);
+                g->gexec = nullptr;
+                cudaGraph_t graph = nullptr;
+                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                int lsave = g->launches;
+                rc = enqueue_batch(g, shape_nk, true, commit, false);
+                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                g->launches = lsave;
+                if (rc) return rc;
+                if (ce != cudaSuccess || cudaGraphInstantiate(&g->gexec, graph, 0) != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    g->gexec = nullptr;
+                    g->err = "graph capture after re-layout failed";
+                    return GC_ECUDA;
+                }
+                cudaGraphDestroy(graph);
+                g->g_gen = g->buf_gen;
+            }
+        }
+    }
+    CK(cudaEventRecord(g->e1, s));
+    std::vector<unsigned long long> res((size_t)6 * std::max(k, 1));
+    CK(cudaMemcpyAsync(res.data(), g->out_dev.p, sizeof(unsigned long long) * 6 * (size_t)k, cudaMemcpyDeviceToHost,
+                       s));
+    rc = read_ctl(g);
+    if (rc) return rc;
+    const Ctl& c = *g->h_ctl;
+    if (commit) {
+        for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
+        g->m += c.m_delta;
+    }
+    if (out)
+        for (long long i = 0; i < 6LL * k; i++) out[i] = (uint64_t)res[(size_t)i];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->e0, g->e1);
+    fill_stats(g, c);
+    g->st.n_ins_raw = raw_ins;
+    g->st.n_del_raw = raw_del;
+    g->st.ms_device = ms;
+    g->st.relayouts = relayouts;
+    g->st.launches = g->g_launches * k;
+    for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
+    g->st.num_edges = g->m;
+    g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return GC_OK;
+}
+
+static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
+    cudaStream_t s = g->s;
+    int rc = plan_region_buffers(g, g->m, 0);
+    if (rc) return rc;
+    g->launches = 0;
     CK(cudaMemsetAsync(g->visited, 0xFF, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
-    g->launches++;
     k_region_all<<<grid_elems(g, g->n), TPB, 0, s>>>(g->ctl, g->n, g->wlist);
+    k_mark_active<<<1, 32, 0, s>>>(g->ctl);
+    g->launches += 2;
     CKL();
     CK(cudaEventRecord(g->ev[2], s));
-    rc = count_region(g, mode);
+    rc = count_region(g, 1, set_F, true);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    rc = read_ctl(g);
+    if (rc) return rc;
+    if (out)
+        for (int i = 0; i < 6; i++) out[i] = (uint64_t)g->h_ctl->Ca[i];
+    if (set_F)
+        for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
     // a static count leaves its stage times in the stats record
     for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
     for (int i = 2; i < 6; i++) cudaEventElapsedTime(&g->st.ms_stage[i], g->ev[i], g->ev[i + 1]);
     cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]);
     fill_stats(g, *g->h_ctl);
-    if (out)
-        for (int i = 0; i < 6; i++) out[i] = (uint64_t)g->h_ctl->Ca[i];
-    if (mode == 2)
-        for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
+    g->st.launches = g->launches;
     return GC_OK;
 }
 
@@ -492,6 +742,7 @@ static int count_static(gc_graph* g, int mode, uint64_t out[6]) {
 static void destroy(gc_graph* g) {
     if (!g) return;
     if (g->s) cudaStreamSynchronize(g->s);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
     int32_t* p32[] = {g->perm, g->iperm, g->deg, g->cap, g->col, g->wlist, g->U_deg, g->U_split, g->da, g->db};
     for (auto p : p32) dfree(g, p);
     dfree(g, g->row_start);
@@ -520,6 +771,7 @@ static void destroy(gc_graph* g) {
     release(g, g->plan_scr);
     release(g, g->bsum);
     release(g, g->hist);
+    release(g, g->out_dev);
     release(g, g->dense);
     release(g, g->cta_tables);
     dfree(g, g->bins);
@@ -551,16 +803,14 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     g->row_start = (long long*)dalloc(g, 8 * (nn + 1));
     g->U_off = (long long*)dalloc(g, 8 * (nn + 1));
     g->ctl = (Ctl*)dalloc(g, sizeof(Ctl));
-    g->desc = (long long*)dalloc(g, 16 * sizeof(long long));
     g->segA = (int2*)dalloc(g, sizeof(int2) * nn);
     g->segD = (int2*)dalloc(g, sizeof(int2) * nn);
     g->visited = (uint32_t*)dalloc(g, 4 * ((nn + 31) / 32 + 1));
     if (!g->perm || !g->iperm || !g->deg || !g->cap || !g->wlist || !g->U_deg || !g->U_split || !g->da || !g->db ||
-        !g->row_start || !g->U_off || !g->ctl || !g->desc || !g->segA || !g->segD || !g->visited)
+        !g->row_start || !g->U_off || !g->ctl || !g->segA || !g->segD || !g->visited)
         return nomem(g, "graph state");
-    int sgn = scan_grid(std::max<long long>(n, m2), g->sms);
+    if (ensure_desc(g, 16)) return GC_ENOMEM;
     if (!ensure(g, g->bsum, 1024)) return nomem(g, "scan scratch");
-    (void)sgn;
     CK(cudaMemsetAsync(g->segA, 0, sizeof(int2) * nn, s));
     CK(cudaMemsetAsync(g->segD, 0, sizeof(int2) * nn, s));
     Ctl zero{};
@@ -600,22 +850,18 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
         if (cudaMemcpyAsync(g->desc + 8, g->h_desc + 8, 2 * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) { rc = GC_ECUDA; break; }
         if (n > 0) {
-            g->launches++;
             k_degree_keys<<<grid_elems(g, n), TPB, 0, s>>>(d_rp, n, deg0, k1);
-            g->launches += radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
-            g->launches++;
+            radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
             k_perm_from_keys<<<grid_elems(g, n), TPB, 0, s>>>(k1, n, g->perm, g->iperm, deg0, g->deg);
         }
         if (m2 > 0) {
-            g->launches++;
             k_edge_keys<<<grid_warps(g), TPB, 0, s>>>(d_rp, d_col, n, g->perm, g->S, k1, bad);
-            g->launches += radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
+            radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
         }
         if (n > 0) {
-            g->launches += scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
-            g->launches++;
+            scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
             k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
-            g->launches += scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
+            scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
         }
         long long total = 0;
         if (n > 0 &&
@@ -631,11 +877,12 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
         long long pool = std::max<long long>((long long)(total * g->slack), 4096);
         g->col_capacity = total + pool;
         g->col = (int32_t*)dalloc(g, 4 * (size_t)g->col_capacity);
-        if (!g->col) { rc = nomem(g, "adjacency"); break; }
+        if (!g->col) {
+            rc = nomem(g, "adjacency");
+            break;
+        }
         if (m2 > 0)
-            g->launches++;
             k_fill_from_keys<<<grid_elems(g, m2), TPB, 0, s>>>(k1, m2, n, g->S, key_off, g->row_start, g->col, bad);
-        g->launches++;
         k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
         int hbad = 0;
         if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -656,8 +903,9 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     dfree(g, d_rp); dfree(g, d_col); dfree(g, deg0); dfree(g, key_off); dfree(g, bad); dfree(g, k1); dfree(g, k2);
     if (rc) return rc;
     g->m = m2 / 2;
-    // counting pass: work lists, and one dense counter array per cluster of
-    // the heavy 4-cycle kernel (kept zero between pivots)
+    // counting pass: work lists, one dense counter array per cluster of the
+    // heaviest 4-cycle pivots and one hash table per CTA of the medium ones
+    // (all kept zero between pivots)
     count_setup_attributes();
     g->bins = (int32_t*)dalloc(g, sizeof(int32_t) * (size_t)NBINS * nn);
     g->dense_clusters = dense_cluster_plan(g->opt.dense_cluster, g->sms, &g->dense_cluster_size);
@@ -666,7 +914,20 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     g->cta_groups = g->sms;
     if (!ensure(g, g->cta_tables, (size_t)g->cta_groups * 2 * C4_T3)) return nomem(g, "4-cycle hash tables");
     CK(cudaMemsetAsync(g->cta_tables.p, 0, 8 * g->cta_tables.cap, s));
-    return count_static(g, 2, nullptr);
+    return count_static(g, true, nullptr);
+}
+
+// host-side checks of a batch's pairs
+static int check_pairs(gc_graph* g, const int32_t* p, int64_t k, const char* what) {
+    for (int64_t i = 0; i < k; i++) {
+        int32_t a = p[2 * i], b = p[2 * i + 1];
+        if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) {
+            g->err = std::string(what) + " " + std::to_string(i) +
+                     " is a self-loop or names a vertex outside [0, n)";
+            return GC_EINVAL;
+        }
+    }
+    return GC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -730,6 +991,10 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
         t_open_error = "alloc and free callbacks come together";
         return GC_EINVAL;
     }
+    if (o.dense_cluster != 0 && o.dense_cluster != 8 && o.dense_cluster != 16) {
+        t_open_error = "dense_cluster must be 0, 8 or 16";
+        return GC_EINVAL;
+    }
     gc_graph* g = new gc_graph();
     g->opt = o;
     g->n = n;
@@ -760,7 +1025,6 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
             g->own_stream = true;
         }
         if (cudaMallocHost((void**)&g->h_ctl, sizeof(Ctl)) != cudaSuccess ||
-            cudaMallocHost((void**)&g->h_desc, 16 * sizeof(long long)) != cudaSuccess ||
             cudaEventCreate(&g->e0) != cudaSuccess || cudaEventCreate(&g->e1) != cudaSuccess ||
             [&] {
                 for (auto& e : g->ev)
@@ -785,7 +1049,7 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
 int gc_count_static(gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;
     g->err.clear();
-    return count_static(g, 1, out);
+    return count_static(g, false, out);
 }
 
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
@@ -807,25 +1071,15 @@ int gc_apply_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t
         g->err = "batch too large";
         return GC_EINVAL;
     }
-    for (int64_t i = 0; i < n_ins; i++) {
-        int32_t a = ins[2 * i], b = ins[2 * i + 1];
-        if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) {
-            g->err = "insertion " + std::to_string(i) + " is a self-loop or names a vertex outside [0, n)";
-            return GC_EINVAL;
-        }
-    }
-    for (int64_t i = 0; i < n_del; i++) {
-        int32_t a = del[2 * i], b = del[2 * i + 1];
-        if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) {
-            g->err = "deletion " + std::to_string(i) + " is a self-loop or names a vertex outside [0, n)";
-            return GC_EINVAL;
-        }
-    }
+    int rc = check_pairs(g, ins, n_ins, "insertion");
+    if (rc) return rc;
+    rc = check_pairs(g, del, n_del, "deletion");
+    if (rc) return rc;
     size_t np = (size_t)(n_ins + n_del);
     if (!ensure(g, g->pairs, 2 * std::max<size_t>(np, 1))) return nomem(g, "batch staging");
     if (n_ins) CK(cudaMemcpyAsync(g->pairs.p, ins, 8 * (size_t)n_ins, cudaMemcpyHostToDevice, g->s));
     if (n_del) CK(cudaMemcpyAsync(g->pairs.p + 2 * n_ins, del, 8 * (size_t)n_del, cudaMemcpyHostToDevice, g->s));
-    int rc = apply_device(g, g->pairs.p, n_ins, g->pairs.p + 2 * n_ins, n_del, 1, out);
+    rc = apply_device(g, g->pairs.p, n_ins, g->pairs.p + 2 * n_ins, n_del, 1, out);
     g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return rc;
 }
@@ -845,31 +1099,53 @@ int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_in
                      const int64_t* n_del, int32_t k, int32_t independent, uint64_t* out) {
     if (!g || k < 0 || (k > 0 && (!n_ins || !n_del || !ins || !del))) return GC_EINVAL;
     g->err.clear();
+    if (k == 0) return GC_OK;
+    long long tot = 0;
     for (int32_t i = 0; i < k; i++) {
-        if (independent) {
-            // validate like gc_apply_batch, then count without committing
-            int64_t ni = n_ins[i], nd = n_del[i];
-            if (ni < 0 || nd < 0 || (ni > 0 && !ins[i]) || (nd > 0 && !del[i])) return GC_EINVAL;
-            for (int64_t j = 0; j < ni; j++) {
-                int32_t a = ins[i][2 * j], b = ins[i][2 * j + 1];
-                if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return GC_EINVAL;
-            }
-            for (int64_t j = 0; j < nd; j++) {
-                int32_t a = del[i][2 * j], b = del[i][2 * j + 1];
-                if (a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return GC_EINVAL;
-            }
-            size_t np = (size_t)(ni + nd);
-            if (!ensure(g, g->pairs, 2 * std::max<size_t>(np, 1))) return nomem(g, "batch staging");
-            if (ni) CK(cudaMemcpyAsync(g->pairs.p, ins[i], 8 * (size_t)ni, cudaMemcpyHostToDevice, g->s));
-            if (nd) CK(cudaMemcpyAsync(g->pairs.p + 2 * ni, del[i], 8 * (size_t)nd, cudaMemcpyHostToDevice, g->s));
-            int rc = apply_device(g, g->pairs.p, ni, g->pairs.p + 2 * ni, nd, 0, out ? out + 6 * i : nullptr);
-            if (rc) return rc;
-        } else {
-            int rc = gc_apply_batch(g, ins[i], n_ins[i], del[i], n_del[i], out ? out + 6 * i : nullptr);
-            if (rc) return rc;
+        if (n_ins[i] < 0 || n_del[i] < 0 || (n_ins[i] > 0 && !ins[i]) || (n_del[i] > 0 && !del[i])) {
+            g->err = "batch arrays: negative size or NULL pointer";
+            return GC_EINVAL;
+        }
+        if (n_ins[i] + n_del[i] > (1LL << 29)) {
+            g->err = "batch too large";
+            return GC_EINVAL;
+        }
+        int rc = check_pairs(g, ins[i], n_ins[i], "insertion");
+        if (rc) return rc;
+        rc = check_pairs(g, del[i], n_del[i], "deletion");
+        if (rc) return rc;
+        tot += n_ins[i] + n_del[i];
+    }
+    // all batches in one upload: insertions then deletions of each batch
+    if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(tot, 1))) return nomem(g, "batch staging");
+    std::vector<long long> d((size_t)4 * k);
+    long long off = 0;
+    for (int32_t i = 0; i < k; i++) {
+        if (n_ins[i]) CK(cudaMemcpyAsync(g->pairs.p + 2 * off, ins[i], 8 * (size_t)n_ins[i], cudaMemcpyHostToDevice, g->s));
+        d[4 * i] = off;
+        d[4 * i + 1] = n_ins[i];
+        off += n_ins[i];
+        if (n_del[i]) CK(cudaMemcpyAsync(g->pairs.p + 2 * off, del[i], 8 * (size_t)n_del[i], cudaMemcpyHostToDevice, g->s));
+        d[4 * i + 2] = off;
+        d[4 * i + 3] = n_del[i];
+        off += n_del[i];
+    }
+    return apply_batches_device(g, g->pairs.p, g->pairs.p, d.data(), k, independent, out);
+}
+
+int gc_apply_batches_device(gc_graph* g, const int32_t* d_pairs, const int64_t* batches, int32_t k,
+                            int32_t independent, uint64_t* out) {
+    if (!g || k < 0 || (k > 0 && (!d_pairs || !batches))) return GC_EINVAL;
+    g->err.clear();
+    if (k == 0) return GC_OK;
+    for (int32_t i = 0; i < k; i++) {
+        const int64_t* b = batches + 4 * (size_t)i;
+        if (b[0] < 0 || b[1] < 0 || b[2] < 0 || b[3] < 0 || b[1] + b[3] > (1LL << 29)) {
+            g->err = "batch descriptor: negative offset or size, or batch too large";
+            return GC_EINVAL;
         }
     }
-    return GC_OK;
+    return apply_batches_device(g, d_pairs, d_pairs, (const long long*)batches, k, independent, out);
 }
 
 int gc_batch_stats(const gc_graph* g, gc_stats* s) {

@@ -15,9 +15,10 @@
 
 namespace gcx {
 
-__global__ void k_batch_keys(const int32_t* __restrict__ ins, const int32_t* __restrict__ del, Ctl* c,
-                             const int32_t* __restrict__ perm, int n, int S, uint64_t* __restrict__ keys) {
+__global__ void k_batch_keys(Ctl* c, const int32_t* __restrict__ perm, int n, int S, uint64_t* __restrict__ keys) {
     long long ni = c->n_ins, nd = c->n_del, tot = ni + nd;
+    const int32_t* ins = c->pairs_ins + 2 * c->ins_off;
+    const int32_t* del = c->pairs_del + 2 * c->del_off;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
         const int32_t* p = i < ni ? ins + 2 * i : del + 2 * (i - ni);
@@ -139,7 +140,14 @@ __global__ void k_commit_plan(Ctl* c, const int32_t* __restrict__ wlist, const i
             if (extra < 4) extra = 4;
             int ncap = nd + extra;
             unsigned long long at = atomicAdd(&c->pool_tail, (unsigned long long)ncap);
-            if (at + (unsigned long long)ncap > (unsigned long long)col_capacity) atomicExch(&c->overflow, 1);
+            if (at + (unsigned long long)ncap > (unsigned long long)col_capacity && atomicExch(&c->overflow, 1) == 0) {
+                // no row is written; later batches of a run wait until the
+                // host has grown the pool and finished this commit
+                c->halt = 1;
+                c->pend_ns = ns;
+                c->pend_nA2 = c->nA2;
+                c->pend_nD2 = c->nD2;
+            }
             plan_dst[i] = (long long)at;
             plan_cap[i] = ncap;
         } else {

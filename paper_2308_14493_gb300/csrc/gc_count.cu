@@ -973,8 +973,14 @@ __global__ void k_finalize(Ctl* c, int mode) {
         C[0] = g1; C[1] = g2; C[2] = g3; C[3] = g4; C[4] = g5; C[5] = g6;
         sm[0] = P; sm[1] = S; sm[2] = TT; sm[3] = D; sm[4] = K; sm[5] = Q;
     }
-    if (mode == 0 && c->err == 0)
-        for (int i = 0; i < 6; i++) c->F[i] += (unsigned long long)(c->Ca[i] - c->Cb[i]);
+    // mode 0: committed batch, F += C_a - C_b; mode 2: independent batch,
+    // the result is F + C_a - C_b and F stays; mode 1: static count
+    const bool ok = c->err == 0 && c->active;
+    for (int i = 0; i < 6; i++) {
+        unsigned long long d = (unsigned long long)(c->Ca[i] - c->Cb[i]);
+        if (mode == 0 && ok) c->F[i] += d;
+        c->last_out[i] = mode == 2 ? c->F[i] + d : c->F[i];
+    }
 }
 
 }  // namespace gcx

@@ -49,6 +49,17 @@ struct Ctl {
     unsigned work[8];                // dynamic work counters
     int nbin[8];                     // sizes of the work bins (see gc_count.cu)
     int maxdeg;                      // largest union-graph degree in the region
+    // batch source and sequencing (a captured batch graph reads these)
+    const int32_t* pairs_ins;        // base of the insertion pairs
+    const int32_t* pairs_del;        // base of the deletion pairs
+    long long ins_off, del_off;      // offsets (in pairs) of the current batch
+    int cur;                         // index of the current batch in a run
+    int active;                      // the current batch runs (no commit is pending)
+    int halt;                        // a commit ran out of pool space; later batches wait
+    int pend_ns;                     // endpoints of the batch whose commit is pending
+    long long pend_nA2, pend_nD2;    // its kept directed insertion / deletion entries
+    long long m_delta;               // net edges committed during a run
+    unsigned long long last_out[6];  // counts after the current batch
 };
 
 // Work bins of the counting pass: region bins[b * n ...] holds the vertices

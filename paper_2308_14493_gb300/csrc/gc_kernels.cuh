@@ -6,8 +6,7 @@
 namespace gcx {
 
 // gc_batch.cu
-__global__ void k_batch_keys(const int32_t* ins, const int32_t* del, Ctl* c, const int32_t* perm, int n, int S,
-                             uint64_t* keys);
+__global__ void k_batch_keys(Ctl* c, const int32_t* perm, int n, int S, uint64_t* keys);
 __global__ void k_batch_decide(const uint64_t* keys, Ctl* c, int S, const long long* row_start, const int32_t* deg,
                                const int32_t* col, int32_t* keepA, int32_t* keepD);
 __global__ void k_batch_compact(const uint64_t* keys, const Ctl* c, int S, const int32_t* keepA,

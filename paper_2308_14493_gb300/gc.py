@@ -78,6 +78,7 @@ def load():
             lib.gc_apply_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
             lib.gc_apply_batches.argtypes = [P, ctypes.POINTER(i32p), i64p, ctypes.POINTER(i32p), i64p,
                                              ctypes.c_int32, ctypes.c_int32, u64p]
+            lib.gc_apply_batches_device.argtypes = [P, P, i64p, ctypes.c_int32, ctypes.c_int32, u64p]
             lib.gc_batch_stats.argtypes = [P, ctypes.POINTER(gc_stats)]
             lib.gc_num_edges.argtypes = [P]
             lib.gc_num_edges.restype = ctypes.c_int64
@@ -169,6 +170,17 @@ def gc_apply_batches(h, batches, independent: bool = False) -> list[list[int]]:
     out = np.zeros((max(k, 1), 6), np.uint64)
     _check(load().gc_apply_batches(h, ins_p, _ptr(n_ins, ctypes.c_int64), del_p, _ptr(n_del, ctypes.c_int64), k,
                                    1 if independent else 0, _ptr(out, ctypes.c_uint64)), h)
+    return [[int(x) for x in row] for row in out[:k]]
+
+
+def gc_apply_batches_device(h, d_pairs_ptr: int, batches, independent: bool = False) -> list[list[int]]:
+    """Batches whose pairs are in device memory: ``batches`` is a [k][4] array of
+    (ins_off, n_ins, del_off, n_del) in pairs relative to ``d_pairs_ptr``."""
+    b = np.ascontiguousarray(np.asarray(batches, dtype=np.int64).reshape(-1, 4))
+    k = b.shape[0]
+    out = np.zeros((max(k, 1), 6), np.uint64)
+    _check(load().gc_apply_batches_device(h, ctypes.c_void_p(d_pairs_ptr), _ptr(b, ctypes.c_int64), k,
+                                          1 if independent else 0, _ptr(out, ctypes.c_uint64)), h)
     return [[int(x) for x in row] for row in out[:k]]
 
 

@@ -355,3 +355,86 @@ def test_fullsize_c4_independent_batches(gcb):
         outs = g.apply_many(batches, independent=True)
         for out, b in zip(outs, gold["batches"]):
             assert out == b["after"]
+
+
+# ----------------------------------------------------------- batched form --
+
+def test_batched_run_that_outgrows_the_pool(gcb):
+    """A captured multi-batch run whose commits outgrow the adjacency pool
+    mid-run (the run pauses, the pool grows, the run resumes) still matches
+    the oracle batch by batch."""
+    n = 3000
+    keys = gen.er_graph(n, 6000, 3)
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    rng = np.random.default_rng(19)
+    batches, expect = [], []
+    for step in range(5):
+        hubs = rng.choice(n, 3, replace=False)
+        cur = set(int(k) for k in gen.keys_from_csr(og.row_ptr, og.col))
+        ins = []
+        for h in hubs:
+            for v in rng.choice(n, 900, replace=False):
+                kk = (min(h, v) << 32) | max(h, v)
+                if v != h and kk not in cur:
+                    cur.add(kk)
+                    ins.append((int(h), int(v)))
+        edges = edges_from_csr(og.row_ptr, og.col)
+        dels = np.array([edges[i] for i in rng.choice(len(edges), 50, replace=False)], np.int32)
+        ins = np.array(ins, np.int32)
+        batches.append((ins, dels))
+        expect.append(og.apply(ins, dels)["F"])
+    with open_graph(gcb, n, rp, col, slack=0.05) as g:
+        outs = g.apply_many(batches)
+        assert outs == expect
+        assert g.stats()["relayouts"] >= 1
+        assert same_graph(g, og.row_ptr, og.col)
+        assert g.count_static() == expect[-1]
+
+
+def test_device_batched_api_equals_plain(gcb):
+    torch = pytest.importorskip("torch")
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [1000, 10, 5000, 300], 0.5, 71)
+    pairs, desc, off = [], [], 0
+    for ins, dels in batches:
+        desc.append((off, len(ins), off + len(ins), len(dels)))
+        pairs += [ins, dels]
+        off += len(ins) + len(dels)
+    d_pairs = torch.from_numpy(np.ascontiguousarray(np.concatenate(pairs).astype(np.int32))).cuda()
+    torch.cuda.synchronize()
+    with open_graph(gcb, n, rp, col) as g1, open_graph(gcb, n, rp, col) as g2:
+        plain = [g1.apply(i, d) for i, d in batches]
+        got = gcb.gc_apply_batches_device(g2.h, d_pairs.data_ptr(), desc)
+        assert got == plain
+        assert g2.counts() == g1.counts() and g2.num_edges() == g1.num_edges()
+    with open_graph(gcb, n, rp, col) as g3:
+        ind = gcb.gc_apply_batches_device(g3.h, d_pairs.data_ptr(), desc, independent=True)
+        F0 = g3.counts()
+    for (ins, dels), out in zip(batches, ind):
+        assert out == oracle.fdgc_step(rp, col, ins, dels, F0)["F"]
+
+
+def test_batched_runs_reuse_and_recapture(gcb):
+    """Runs of different shapes on one handle (the captured graph is reused or
+    captured again) agree with the plain form."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    runs = [gen.batch_stream(n, keys, sizes, 0.5, 80 + i)
+            for i, sizes in enumerate([[200, 200], [150, 180], [20000], [5, 6, 7]])]
+    with open_graph(gcb, n, rp, col) as gb, open_graph(gcb, n, rp, col) as gp:
+        for run in runs:
+            assert gb.apply_many(run) == [gp.apply(i, d) for i, d in run]
+            assert gb.counts() == gp.counts()
+
+
+def test_batched_invalid_pair_changes_nothing(gcb):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    with open_graph(gcb, n, rp, col) as g:
+        F0 = g.counts()
+        ok = gen.random_batch(n, keys, 10, 10, 3)
+        with pytest.raises(gcb.GCError):
+            g.apply_many([ok, ([(1, 1)], [])])
+        assert g.counts() == F0 and same_graph(g, rp, col)
