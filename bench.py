@@ -53,7 +53,10 @@ BENCH = {
                desc="Erdos-Renyi n=2,000 m=20,000; 400-update batches, 50% ins / 50% del"),
 }
 STAGES = ["normalise", "region", "union_graph", "triangles_k4", "four_cycles", "terms_closed_forms", "commit"]
-KERNEL_OF_STAGE = {3: "k_tri_k4", 4: "k_c4"}
+KERNEL_OF_STAGE = {3: "k_tri_warp + k_tri_block + k_tri_merge (triangles, 4-cliques)",
+                   4: "k_c4_reg + k_c4_warp + k_c4_block + k_c4_dense + k_c4_hash (4-cycles)"}
+WORKLOADS_DESC_C4 = ("Chung-Lu n=2.4M m=5M gamma=1.8 dmax=100,000; 64 independent batches, sizes log-uniform "
+                     "10..50,000, 50% ins / 50% del")
 
 
 def parse():
@@ -62,9 +65,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gc", "reference"], default="gc")
-    ap.add_argument("--workload", choices=sorted(BENCH), default="c2")
+    ap.add_argument("--workload", choices=sorted(BENCH) + ["c5"], default="c2",
+                    help="c5: the serving workload (8 resident graphs, request loop)")
+    ap.add_argument("--requests", type=int, default=96, help="c5: requests per phase")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary blocks")
     ap.add_argument("--no-large", action="store_true", help="skip the 1.6M/30M graph block")
+    ap.add_argument("--slots", type=int, default=4, help="c5: server slots")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     return ap.parse_args()
 
@@ -261,16 +267,85 @@ def roofline(recs, peak, peak_kind):
             "stage_ms": dict(zip(STAGES, [round(x, 4) for x in sm]))}
 
 
-def run_batched(gcb, n, rp, col, batches, warmup):
-    """Batched form: all batches in one C-ABI call (host wall clock)."""
-    g = gcb.Graph(n, rp, col)
-    g.apply_many(batches[:warmup])
-    t0 = time.perf_counter()
-    g.apply_many(batches[warmup:])
-    dt = time.perf_counter() - t0
-    edges = sum(len(i) + len(d) for i, d in batches[warmup:])
-    g.close()
-    return dict(value=edges / dt, seconds=dt, note="host wall clock around one gc_apply_batches call")
+def pack_batches(batches):
+    """All pairs of a run in one int32 array + the [k][4] descriptor
+    (ins_off, n_ins, del_off, n_del) of gc_apply_batches_device."""
+    chunks, desc, off = [], [], 0
+    for ins, dels in batches:
+        ins = np.asarray(ins, np.int32).reshape(-1, 2)
+        dels = np.asarray(dels, np.int32).reshape(-1, 2)
+        desc.append((off, ins.shape[0], off + ins.shape[0], dels.shape[0]))
+        chunks += [ins, dels]
+        off += ins.shape[0] + dels.shape[0]
+    pairs = np.concatenate(chunks) if chunks else np.zeros((1, 2), np.int32)
+    return np.ascontiguousarray(pairs), np.asarray(desc, np.int64).reshape(-1, 4)
+
+
+def run_batched(gcb, torch, n, rp, col, batches, warmup, stream, flush, independent=False):
+    """Batched form: the timed batches in ONE gc_apply_batches_device call
+    (one captured CUDA graph replayed per batch, sizes read on the device),
+    pairs resident in HBM.  Device time = CUDA events on the library's stream
+    around the call; L2 is flushed before the call, not between the batches
+    inside it.  Returns (seconds, raw updates, outputs, launches)."""
+    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    pairs, desc = pack_batches(batches)
+    dp = torch.from_numpy(pairs).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        if warmup:
+            gcb.gc_apply_batches_device(h, dp.data_ptr(), desc[:warmup], independent)
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = gcb.gc_apply_batches_device(h, dp.data_ptr(), desc[warmup:], independent)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    st = gcb.gc_batch_stats(h)
+    gcb.gc_close(h)
+    raw = int(desc[warmup:, 1].sum() + desc[warmup:, 3].sum())
+    return e0.elapsed_time(e1) / 1e3, raw, outs, st["launches"]
+
+
+def run_what_if(gcb, torch, n, rp, col, batches, stream, flush):
+    """Plain form of independent batches: one gc_count_batch_device call per
+    batch against the same snapshot, L2 flushed between calls."""
+    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    dev = [(torch.from_numpy(np.ascontiguousarray(i)).cuda(), torch.from_numpy(np.ascontiguousarray(d)).cuda())
+           for i, d in batches]
+    torch.cuda.synchronize()
+    ms, outs, edges, launches = [], [], 0, 0
+    with torch.cuda.stream(stream):
+        for ti, td in dev:
+            if flush is not None:
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs.append(gcb.gc_count_batch_device(h, ti.data_ptr(), ti.shape[0], td.data_ptr(), td.shape[0]))
+            e1.record(stream)
+            st = gcb.gc_batch_stats(h)
+            edges += st["n_ins"] + st["n_del"]
+            launches += st["launches"]
+            ms.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ms]
+    gcb.gc_close(h)
+    return ms, outs, edges, launches
+
+
+def plain_vs_batched(gcb, torch, n, rp, col, batches, W, stream, flush):
+    """Both forms on the same sequential stream (each from a fresh open)."""
+    recs, _, _ = run_plain(gcb, torch, n, rp, col, batches, W, len(batches) - W, stream, flush)
+    sp = summarize(recs)
+    secs, raw, outs, launches = run_batched(gcb, torch, n, rp, col, batches, W, stream, flush)
+    normalised = sp["edges"]
+    return {"plain": {"value": sp["value"], "ms_per_batch": sp["ms_per_step"], "p50_ms": sp["p50_ms"],
+                      "p99_ms": sp["p99_ms"], "launches_per_batch": sp["launches"] / max(len(recs), 1)},
+            "batched": {"value": normalised / secs, "ms_per_batch": 1e3 * secs / max(len(recs), 1),
+                        "launches_per_batch": launches / max(len(recs), 1)},
+            "batched_over_plain": (normalised / secs) / sp["value"],
+            "counts_equal": outs == [r["out"] for r in recs],
+            "normalised_equals_raw": normalised == raw}
 
 
 def cpu_oracle_sample(rp, col, batches, budget_s):
@@ -289,6 +364,26 @@ def cpu_oracle_sample(rp, col, batches, budget_s):
         if secs >= budget_s:
             break
     return edges, secs, done, t_static
+
+
+def c4_block(gcb, torch, stream, flush, peak, peak_kind):
+    """64 independent batches (sizes log-uniform in 10..50,000, 50/50,
+    degree-weighted endpoints) against one snapshot of the Chung-Lu
+    n=2.4M m=5M graph: plain (one what-if call per batch) vs batched (one
+    call, one captured graph replayed per batch)."""
+    n, keys = gen.workload_graph("c4")
+    rp, col = gen.csr_from_keys(n, keys)
+    sizes = gen.log_uniform_sizes(64, 10, 50000, 4)
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 4, sequential=False)
+    ms, outs_p, edges, launches_p = run_what_if(gcb, torch, n, rp, col, batches, stream, flush)
+    secs, raw, outs_b, launches_b = run_batched(gcb, torch, n, rp, col, batches, 0, stream, flush, independent=True)
+    tot = sum(ms) / 1e3
+    return {"workload": WORKLOADS_DESC_C4, "batches": len(batches), "updates": raw,
+            "plain": {"value": edges / tot, "p50_ms": pct(ms, 0.5), "p99_ms": pct(ms, 0.99),
+                      "launches": launches_p},
+            "batched": {"value": edges / secs, "ms_total": 1e3 * secs, "launches": launches_b},
+            "batched_over_plain": tot / secs, "counts_equal": outs_p == outs_b,
+            "normalised_equals_raw": edges == raw}
 
 
 def gpu_arm(args):
@@ -339,29 +434,41 @@ def gpu_arm(args):
                    "api": "gc_apply_batch (host pinned pairs in, 6 uint64 counts out)"}
     if not args.no_secondary and rank == 0:
         sec = {}
-        try:
-            sec["batched_10k"] = run_batched(gcb, n, rp, col, batches, W)
-        except Exception as e:  # pragma: no cover - reported, not hidden
-            sec["batched_10k"] = {"error": str(e)}
-        for tag, frac, size in (("fdgc_1k", spec["ins_frac"], 1000), ("igc_10k", 1.0, 10000), ("igc_1k", 1.0, 1000)):
-            if args.workload != "c2":
-                break
-            _, _, _, _, b2 = make_batches(spec, W + K, rank, ins_frac=frac, size=size)
-            r2, _, _ = run_plain(gcb, torch, n, rp, col, b2, W, K, stream, flush)
-            s2 = summarize(r2)
-            sec[tag] = {"value": s2["value"], "p50_ms": s2["p50_ms"], "p99_ms": s2["p99_ms"]}
+        if args.workload == "c2":
+            pvb = {}
+            for tag, frac, size in (("fdgc_10k", spec["ins_frac"], 10000), ("fdgc_1k", spec["ins_frac"], 1000),
+                                    ("igc_10k", 1.0, 10000), ("igc_1k", 1.0, 1000)):
+                try:
+                    if tag == "fdgc_10k":
+                        b2 = batches
+                    else:
+                        _, _, _, _, b2 = make_batches(spec, W + K, rank, ins_frac=frac, size=size)
+                    pvb[tag] = plain_vs_batched(gcb, torch, n, rp, col, b2, W, stream, flush)
+                except Exception as e:  # pragma: no cover - reported, not hidden
+                    pvb[tag] = {"error": str(e)}
+            sec["c2_plain_vs_batched"] = pvb
+        if not args.no_large:
+            try:
+                sec["c4_independent"] = c4_block(gcb, torch, stream, flush, peak, peak_kind)
+            except Exception as e:  # pragma: no cover
+                sec["c4_independent"] = {"error": str(e)}
         if not args.no_large and args.workload != "c3":
             try:
                 sp3 = BENCH["c3"]
                 n3, _, rp3, col3, b3 = make_batches(sp3, 1 + 3)
                 r3, st_ms3, st3 = run_plain(gcb, torch, n3, rp3, col3, b3, 1, 3, stream, None)
                 s3 = summarize(r3)
-                sec["c3_plain"] = {"workload": sp3["desc"], "value": s3["value"], "ms_per_step": s3["ms_per_step"],
-                                   "p99_ms": s3["p99_ms"], "static_recount_ms": st_ms3,
-                                   "roofline": roofline(r3, peak, peak_kind),
-                                   "l2": "inputs larger than L2 (union graph 240 MB)"}
+                secs3, raw3, outs3, _ = run_batched(gcb, torch, n3, rp3, col3, b3, 1, stream, None)
+                sec["c3"] = {"workload": sp3["desc"], "plain": {"value": s3["value"], "ms_per_batch": s3["ms_per_step"],
+                                                                 "p99_ms": s3["p99_ms"]},
+                             "batched": {"value": s3["edges"] / secs3, "ms_per_batch": 1e3 * secs3 / 3},
+                             "counts_equal": outs3 == [r["out"] for r in r3],
+                             "static_recount_ms": st_ms3,
+                             "static_recount_stage_ms": dict(zip(STAGES, [round(x, 4) for x in st3["ms_stage"]])),
+                             "roofline": roofline(r3, peak, peak_kind),
+                             "l2": "inputs larger than L2 (union graph 240 MB)"}
             except Exception as e:  # pragma: no cover
-                sec["c3_plain"] = {"error": str(e)}
+                sec["c3"] = {"error": str(e)}
         line["secondary"] = sec
     if rank == 0 and world == 1:
         edges, secs, done, t_static = cpu_oracle_sample(rp, col, batches, args.cpu_seconds)
@@ -376,12 +483,119 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ serving arm --
+
+def c5_requests(graphs, count, seed):
+    """Requests of the serving workload: sizes log-uniform in 100..100,000,
+    70% insertions, routed uniformly over the graphs; each batch drawn
+    against its graph's initial edge set (later no-ops are normalised away)."""
+    sizes = gen.log_uniform_sizes(count, 100, 100000, seed)
+    route = (gen.uniform01(seed + 1, 0, count) * len(graphs)).astype(np.int64)
+    per = {gi: [s for s, r in zip(sizes, route) if r == gi] for gi in range(len(graphs))}
+    made = {gi: (gen.batch_stream(graphs[gi][0], graphs[gi][1], per[gi], 0.7, seed + 10 + gi, sequential=False)
+                 if per[gi] else []) for gi in per}
+    cur = {gi: 0 for gi in per}
+    out = []
+    for r in route:
+        gi = int(r)
+        out.append((gi,) + tuple(made[gi][cur[gi]]))
+        cur[gi] += 1
+    return out
+
+
+def serve_arm(args):
+    """Serving workload: 8 resident Chung-Lu graphs (n 100k..4.8M, m 1M..69M,
+    gamma 2.0..2.4).  Three phases on the same resident graphs:
+      plain     requests one at a time through gc_apply_batch (closed loop)
+      saturated the same number of requests all queued at once on the server
+      poisson   Poisson arrivals at 0.8x the plain request rate (latency)
+    value = updated edges/s of the saturated served phase."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2308_14493_gb300 import gc as gcb
+
+    gcb.load()
+    params = gen.c5_graph_params()
+    t0 = time.perf_counter()
+    graphs = [gen.workload_graph(p) for p in params]
+    t_gen = time.perf_counter() - t0
+    R = args.requests
+    reqs = c5_requests(graphs, 3 * R, 5)
+    handles = [gcb.Graph(n, *gen.csr_from_keys(n, keys)) for n, keys in graphs]
+    torch.cuda.synchronize()
+
+    # warm-up: one small batch per graph
+    for gi, h in enumerate(handles):
+        n, keys = graphs[gi]
+        h.apply(*gen.random_batch(n, keys, 5, 5, 900 + gi))
+
+    with ClockSampler(0) as clk:
+        # plain
+        lat, ups = [], 0
+        t = time.perf_counter()
+        for gi, ins, dels in reqs[:R]:
+            a = time.perf_counter()
+            handles[gi].apply(ins, dels)
+            lat.append(1e3 * (time.perf_counter() - a))
+            st = handles[gi].stats()
+            ups += st["n_ins"] + st["n_del"]
+        plain_s = time.perf_counter() - t
+        plain = {"value": ups / plain_s, "requests_per_s": R / plain_s, "p50_ms": pct(lat, 0.5),
+                 "p99_ms": pct(lat, 0.99)}
+
+        def served(batch, rate):
+            with gcb.Server(handles, slots=args.slots) as srv:
+                tickets, rng = [], np.random.default_rng(100)
+                start = time.perf_counter()
+                due = 0.0
+                for gi, ins, dels in batch:
+                    if rate:
+                        due += rng.exponential(1.0 / rate)
+                        wait = start + due - time.perf_counter()
+                        if wait > 0:
+                            time.sleep(wait)
+                    tickets.append(srv.submit(gi, ins, dels))
+                res = [srv.wait(tk) for tk in tickets]
+                peak, trims = srv.counters()
+            bad = [r for r in res if r["status"] != 0]
+            lat = [r["t_done_ms"] - r["t_submit_ms"] for r in res]
+            span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) / 1e3
+            ups = sum(r["n_ins"] + r["n_del"] for r in res)
+            return {"value": ups / span, "requests_per_s": len(res) / span, "p50_ms": pct(lat, 0.5),
+                    "p99_ms": pct(lat, 0.99), "peak_in_flight": peak, "trims": trims, "failed": len(bad),
+                    "device_ms_sum": sum(r["ms_device"] for r in res), "span_s": span}
+
+        sat = served(reqs[R:2 * R], 0.0)
+        poi = served(reqs[2 * R:], 0.8 * plain["requests_per_s"])
+    line = {
+        "metric": METRIC, "value": sat["value"], "unit": UNIT, "n_gpus": 1, "steps": R, "warmup": len(handles),
+        "ms_per_step": 1e3 * sat["span_s"] / R, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serving: 8 resident Chung-Lu graphs, n 100k..4.8M, m 1M..69M (log-spaced), "
+                               "gamma 2.0..2.4, dmax sqrt(2m); requests log-uniform 100..100,000 updates, 70% ins, "
+                               "uniform routing", "slots": args.slots,
+                   "l2": "graphs of 1M..69M edges; the larger ones exceed L2"},
+        "plain": plain, "served_saturated": sat, "served_poisson_0.8x": poi,
+        "served_over_plain": sat["value"] / plain["value"],
+        "generation_s": t_gen, "clocks": clk.summary(),
+    }
+    for h in handles:
+        h.close()
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- reference arm --
 
 def reference_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "c5":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the default workload; "
+                                                              "on the 1M..69M-edge serving graphs it exceeds the "
+                                                              "few-minute bound of a bench run"}), flush=True)
         return
     import oracle
 
@@ -414,6 +628,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "c5":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

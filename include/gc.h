@@ -136,6 +136,19 @@ int gc_apply_batch_device(gc_graph *g, const int32_t *d_ins, int64_t n_ins,
                           const int32_t *d_del, int64_t n_del, uint64_t out[6]);
 
 /*
+ * Count one batch against the current graph without applying it: out
+ * receives the counts of G (+) B, the graph and the maintained counts stay as
+ * they were.  The same Algorithm 2 step as gc_apply_batch, minus the commit
+ * (a what-if query; k of these on one graph give the independent mode of
+ * gc_apply_batches).  Arguments, batch semantics and errors as for
+ * gc_apply_batch / gc_apply_batch_device.
+ */
+int gc_count_batch(gc_graph *g, const int32_t *ins, int64_t n_ins,
+                   const int32_t *del, int64_t n_del, uint64_t out[6]);
+int gc_count_batch_device(gc_graph *g, const int32_t *d_ins, int64_t n_ins,
+                          const int32_t *d_del, int64_t n_del, uint64_t out[6]);
+
+/*
  * Apply k batches in one device launch sequence (a CUDA graph replayed per
  * batch, with batch sizes read on the device).
  *   ins[i], n_ins[i], del[i], n_del[i]   host pair arrays of batch i
@@ -207,6 +220,82 @@ int gc_export_csr(gc_graph *g, int32_t *row_ptr, int32_t *col);
 #define GC_NOALLOC_MAX_ENTRIES 524288
 int gc_count_static_noalloc(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col, int64_t nnz,
                             void *stream, uint64_t out[6]);
+
+/* Device memory.  gc_device_bytes: bytes the handle holds now (graph,
+   counting state and scratch).  gc_batch_bytes: bytes a batch of n_ins
+   insertions and n_del deletions may add to that (scratch growth, plus a
+   re-layout of the adjacency if the pool may not take the insertions); an
+   upper estimate made on the host, without device work.  gc_trim: release
+   the scratch that the next batch re-creates on demand (synchronous).
+   -1 / GC_EINVAL for a NULL handle or negative sizes. */
+int64_t gc_device_bytes(const gc_graph *g);
+int64_t gc_batch_bytes(const gc_graph *g, int64_t n_ins, int64_t n_del);
+int gc_trim(gc_graph *g);
+
+/*
+ * Serving: a request loop over several resident graphs.  The paper has no
+ * serving layer; this is the deployment form of Algorithm 2 for streams of
+ * update batches that arrive for many graphs at once.
+ *
+ * The server takes graphs opened with gc_open (it does not own them; the
+ * caller closes them after gc_server_close and does not use them while they
+ * are served).  Requests are batches for one graph; they apply in submission
+ * order per graph, each with the semantics of gc_apply_batch.  `slots`
+ * worker threads run requests of different graphs at the same time, each on
+ * its graph's stream, so their device work overlaps (continuous batching: a
+ * request is admitted when a slot is free and its graph idle).  Admission by
+ * memory: a request starts only if the device bytes held by all served graphs
+ * plus the predicted growth (gc_batch_bytes) of every running request and of
+ * this one stay within the budget; when they do not, the scratch of idle
+ * graphs is released (gc_trim) first, and if that is not enough the request
+ * waits for running ones.  A request that cannot fit even alone runs alone.
+ * Requests are admitted oldest first among graphs that are idle.
+ */
+typedef struct gc_server gc_server;
+
+typedef struct {
+    int32_t slots;            /* requests in flight at once; 0 -> 4 */
+    int32_t reserved0;
+    int64_t hbm_budget_bytes; /* 0 -> bytes held by the graphs at open + 90% of the free device memory */
+    int64_t reserved[6];
+} gc_server_options;
+
+typedef struct {
+    int64_t ticket;
+    int32_t graph;          /* index into the graphs passed to gc_server_open */
+    int32_t status;         /* GC_OK or the GC_E* code of the batch */
+    uint64_t counts[6];     /* counts of the graph after the batch */
+    int64_t n_ins, n_del;   /* pairs applied after normalisation */
+    int64_t region_vertices;
+    float ms_device;        /* device time of the batch */
+    int32_t relayouts;
+    double t_submit_ms;     /* host clock, ms since gc_server_open */
+    double t_admit_ms;
+    double t_done_ms;
+    int64_t bytes_predicted; /* admission estimate of the batch */
+} gc_result;
+
+int gc_server_open(gc_graph *const *graphs, int32_t n_graphs, const gc_server_options *opt, gc_server **out);
+
+/* Queue a batch for graph `graph`; the pairs are copied, the call returns at
+   once with a ticket.  GC_EINVAL for a bad graph index, NULL arrays with
+   non-zero sizes, or a closed server. */
+int gc_server_submit(gc_server *s, int32_t graph, const int32_t *ins, int64_t n_ins,
+                     const int32_t *del, int64_t n_del, int64_t *ticket);
+
+/* Block until the request is done and return its record (once per ticket;
+   GC_EINVAL for an unknown ticket).  The batch's own error, if any, is in
+   r->status; the call itself returns GC_OK. */
+int gc_server_wait(gc_server *s, int64_t ticket, gc_result *r);
+
+/* Block until every submitted request is done. */
+int gc_server_drain(gc_server *s);
+
+/* Peak number of requests that were running at once, and trims made. */
+int gc_server_counters(const gc_server *s, int64_t *peak_inflight, int64_t *trims);
+
+/* Finish every queued request, stop the workers, free the server (not the graphs). */
+void gc_server_close(gc_server *s);
 
 /* One-line reason for the last failure on this handle ("" if none).
    With g == NULL: the reason for the last failed gc_open. */

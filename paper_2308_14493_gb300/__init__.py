@@ -8,14 +8,26 @@ from .gc import (  # noqa: F401
     GRAPHLETS,
     GCError,
     Graph,
+    Server,
     gc_apply_batch,
     gc_apply_batch_device,
     gc_apply_batches,
     gc_apply_batches_device,
     gc_batch_stats,
     gc_close,
+    gc_count_batch,
+    gc_count_batch_device,
     gc_count_static,
     gc_count_static_noalloc,
+    gc_device_bytes,
+    gc_batch_bytes,
+    gc_trim,
+    gc_server_open,
+    gc_server_submit,
+    gc_server_wait,
+    gc_server_drain,
+    gc_server_counters,
+    gc_server_close,
     gc_counts,
     gc_export_csr,
     gc_last_error,

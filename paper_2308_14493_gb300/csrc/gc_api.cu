@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gc.h"
@@ -99,6 +100,9 @@ struct gc_graph {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEvent_t ev[8] = {};  // stage boundaries, see gc_stats.ms_stage
     int launches = 0;        // kernels launched by the current call
+    // device bytes held, for admission control
+    std::unordered_map<void*, size_t> held;
+    long long bytes_held = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -113,11 +117,20 @@ static void* dalloc(gc_graph* g, size_t bytes) {
         cudaGetLastError();
         p = nullptr;
     }
+    if (p) {
+        g->held[p] = bytes;
+        g->bytes_held += (long long)bytes;
+    }
     return p;
 }
 
 static void dfree(gc_graph* g, void* p) {
     if (!p) return;
+    auto it = g->held.find(p);
+    if (it != g->held.end()) {
+        g->bytes_held -= (long long)it->second;
+        g->held.erase(it);
+    }
     if (g->opt.free) g->opt.free(p, (void*)g->s, g->opt.ctx);
     else cudaFreeAsync(p, g->s);
 }
@@ -285,6 +298,66 @@ static int plan_batch_buffers(gc_graph* g, long long nk) {
         return nomem(g, "batch scratch");
     if (!ensure(g, g->hist, (size_t)256 * radix_grid(nk, g->sms))) return nomem(g, "sort histogram");
     return GC_OK;
+}
+
+// Bytes that ensure(b, count) would add.
+template <class T>
+static long long grow_bytes(const Buf<T>& b, size_t count) {
+    if (b.p && b.cap >= count) return 0;
+    size_t nc = std::max<size_t>(count + count / 4, 64);
+    return (long long)(nc * sizeof(T)) - (long long)(b.cap * sizeof(T));
+}
+
+// Device bytes a batch of n_ins + n_del pairs would add to what the handle
+// holds: its scratch growth, plus a re-layout of the adjacency when the
+// pool's free space at the end of the last batch may not take the insertions.
+static long long predict_batch_bytes(const gc_graph* g, long long n_ins, long long n_del) {
+    const size_t nk = (size_t)std::max<long long>(2 * (n_ins + n_del), 1);
+    long long b = grow_bytes(g->keys, nk) + grow_bytes(g->keys_tmp, nk) + grow_bytes(g->keepA, nk) +
+                  grow_bytes(g->keepD, nk) + grow_bytes(g->posA, nk + 1) + grow_bytes(g->posD, nk + 1) +
+                  grow_bytes(g->srcA, nk) + grow_bytes(g->dstA, nk) + grow_bytes(g->srcD, nk) +
+                  grow_bytes(g->dstD, nk) + grow_bytes(g->plan_dst, nk) + grow_bytes(g->plan_scr, nk) +
+                  grow_bytes(g->plan_cap, nk) + grow_bytes(g->plan_deg, nk) +
+                  grow_bytes(g->hist, (size_t)256 * radix_grid((long long)nk, g->sms)) +
+                  grow_bytes(g->pairs, nk);
+    const size_t ucap = (size_t)(2 * g->m + 4 * n_ins + 64);
+    b += grow_bytes(g->U_col, ucap) + grow_bytes(g->tpack, ucap);
+    const long long pool_free = g->col_capacity - (long long)g->h_ctl->pool_tail;
+    if (n_ins > 0 && pool_free < 8 * n_ins) {
+        // new rows with fresh slack and a new pool, while the old ones live
+        const double rows = (double)(2 * (g->m + n_ins)) * (1.0 + 2.0 * g->slack) + 8.0 * n_ins + 4096;
+        b += (long long)(4.0 * rows) + 8LL * (g->n + 1);
+    }
+    return b;
+}
+
+// Free the scratch that the next batch re-creates on demand.
+static void trim_scratch(gc_graph* g) {
+    if (g->s) cudaStreamSynchronize(g->s);
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    release(g, g->U_col);
+    release(g, g->tpack);
+    release(g, g->keys);
+    release(g, g->keys_tmp);
+    release(g, g->keepA);
+    release(g, g->keepD);
+    release(g, g->srcA);
+    release(g, g->dstA);
+    release(g, g->srcD);
+    release(g, g->dstD);
+    release(g, g->plan_cap);
+    release(g, g->plan_deg);
+    release(g, g->pairs);
+    release(g, g->posA);
+    release(g, g->posD);
+    release(g, g->plan_dst);
+    release(g, g->plan_scr);
+    release(g, g->out_dev);
+    g->buf_gen++;
+    if (g->s) cudaStreamSynchronize(g->s);
 }
 
 static int ensure_desc(gc_graph* g, long long words) {
@@ -933,6 +1006,14 @@ static int check_pairs(gc_graph* g, const int32_t* p, int64_t k, const char* wha
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// Make the handle's device current for the calling thread (a thread other
+// than the one that opened the handle starts on device 0).
+static bool on_device(gc_graph* g) {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return false;
+    return d == g->dev || cudaSetDevice(g->dev) == cudaSuccess;
+}
+
 extern "C" {
 
 void gc_default_options(gc_options* opt) {
@@ -1048,6 +1129,10 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
 
 int gc_count_static(gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     g->err.clear();
     return count_static(g, false, out);
 }
@@ -1058,9 +1143,13 @@ int gc_counts(const gc_graph* g, uint64_t out[6]) {
     return GC_OK;
 }
 
-int gc_apply_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t* del, int64_t n_del,
-                   uint64_t out[6]) {
+static int batch_host(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t* del, int64_t n_del, int commit,
+                      uint64_t out[6]) {
     if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     auto t0 = std::chrono::steady_clock::now();
     g->err.clear();
     if (n_ins < 0 || n_del < 0 || (n_ins > 0 && !ins) || (n_del > 0 && !del)) {
@@ -1079,25 +1168,53 @@ int gc_apply_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t
     if (!ensure(g, g->pairs, 2 * std::max<size_t>(np, 1))) return nomem(g, "batch staging");
     if (n_ins) CK(cudaMemcpyAsync(g->pairs.p, ins, 8 * (size_t)n_ins, cudaMemcpyHostToDevice, g->s));
     if (n_del) CK(cudaMemcpyAsync(g->pairs.p + 2 * n_ins, del, 8 * (size_t)n_del, cudaMemcpyHostToDevice, g->s));
-    rc = apply_device(g, g->pairs.p, n_ins, g->pairs.p + 2 * n_ins, n_del, 1, out);
+    rc = apply_device(g, g->pairs.p, n_ins, g->pairs.p + 2 * n_ins, n_del, commit, out);
     g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return rc;
 }
 
-int gc_apply_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
-                          uint64_t out[6]) {
+int gc_apply_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t* del, int64_t n_del,
+                   uint64_t out[6]) {
+    return batch_host(g, ins, n_ins, del, n_del, 1, out);
+}
+
+int gc_count_batch(gc_graph* g, const int32_t* ins, int64_t n_ins, const int32_t* del, int64_t n_del,
+                   uint64_t out[6]) {
+    return batch_host(g, ins, n_ins, del, n_del, 0, out);
+}
+
+static int batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
+                        int commit, uint64_t out[6]) {
     if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     g->err.clear();
     if (n_ins < 0 || n_del < 0 || (n_ins > 0 && !d_ins) || (n_del > 0 && !d_del) || n_ins + n_del > (1LL << 29)) {
         g->err = "batch arrays: bad size or NULL pointer";
         return GC_EINVAL;
     }
-    return apply_device(g, d_ins, n_ins, d_del, n_del, 1, out);
+    return apply_device(g, d_ins, n_ins, d_del, n_del, commit, out);
+}
+
+int gc_apply_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
+                          uint64_t out[6]) {
+    return batch_device(g, d_ins, n_ins, d_del, n_del, 1, out);
+}
+
+int gc_count_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
+                          uint64_t out[6]) {
+    return batch_device(g, d_ins, n_ins, d_del, n_del, 0, out);
 }
 
 int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_ins, const int32_t* const* del,
                      const int64_t* n_del, int32_t k, int32_t independent, uint64_t* out) {
     if (!g || k < 0 || (k > 0 && (!n_ins || !n_del || !ins || !del))) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     g->err.clear();
     if (k == 0) return GC_OK;
     long long tot = 0;
@@ -1136,6 +1253,10 @@ int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_in
 int gc_apply_batches_device(gc_graph* g, const int32_t* d_pairs, const int64_t* batches, int32_t k,
                             int32_t independent, uint64_t* out) {
     if (!g || k < 0 || (k > 0 && (!d_pairs || !batches))) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     g->err.clear();
     if (k == 0) return GC_OK;
     for (int32_t i = 0; i < k; i++) {
@@ -1158,6 +1279,10 @@ int64_t gc_num_edges(const gc_graph* g) { return g ? g->m : -1; }
 
 int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
     if (!g || !row_ptr || (g->m > 0 && !col)) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
     int n = g->n;
     std::vector<int32_t> deg(n), iperm(n);
     std::vector<long long> rs(n);
@@ -1182,8 +1307,28 @@ int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
     return GC_OK;
 }
 
+int64_t gc_device_bytes(const gc_graph* g) { return g ? g->bytes_held : -1; }
+
+int64_t gc_batch_bytes(const gc_graph* g, int64_t n_ins, int64_t n_del) {
+    if (!g || n_ins < 0 || n_del < 0) return -1;
+    return predict_batch_bytes(g, n_ins, n_del);
+}
+
+int gc_trim(gc_graph* g) {
+    if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    trim_scratch(g);
+    return GC_OK;
+}
+
 const char* gc_last_error(const gc_graph* g) { return g ? g->err.c_str() : t_open_error.c_str(); }
 
-void gc_close(gc_graph* g) { destroy(g); }
+void gc_close(gc_graph* g) {
+    if (g) on_device(g);
+    destroy(g);
+}
 
 }  // extern "C"

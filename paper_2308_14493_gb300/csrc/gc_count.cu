@@ -111,23 +111,44 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
         int32_t u = valid ? wlist[i] : 0;
         if (valid) {
             long long rb = U_off[u], re = U_off[u + 1];
-            int split = U_split[u];
-            int k = (int)(re - rb) - split;
+            int k = (int)(re - rb) - U_split[u];
             dmax = max(dmax, (int)(re - rb));
             if (k >= 2) tb = k <= 32 ? BIN_TRI_WARP : (k <= TRI_KM ? BIN_TRI_BLOCK : BIN_TRI_MERGE);
-            if (split >= 2) {
-                long long wt = 0;
-                for (int j = 0; j < split; j++) {
-                    uint32_t v = vid(U_col[rb + j]);
-                    wt += U_off[v + 1] - U_off[v];
-                }
-                // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
-                cb = wt <= 32                        ? BIN_C4_REG
-                     : wt <= C4_T1                   ? BIN_C4_WARP
-                     : wt <= C4_T2                   ? BIN_C4_BLOCK
-                     : (wt <= t3 && split < 65536)   ? BIN_C4_CTA
-                                                     : BIN_C4_DENSE;
+        }
+        // wedge bound w~ = sum of the row lengths of the lower neighbours:
+        // short lists by their own thread, long ones (hubs) by the whole warp
+        const int split = valid ? U_split[u] : 0;
+        long long wt = 0;
+        if (split >= 2 && split <= 64) {
+            const long long rb = U_off[u];
+            for (int j = 0; j < split; j++) {
+                uint32_t v = vid(U_col[rb + j]);
+                wt += U_off[v + 1] - U_off[v];
             }
+        }
+        unsigned big = __ballot_sync(FULL, split > 64);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t uu = __shfl_sync(FULL, u, src);
+            const int sp = __shfl_sync(FULL, split, src);
+            const long long rb = U_off[uu];
+            long long part = 0;
+            for (int j = lane; j < sp; j += 32) {
+                uint32_t v = vid(U_col[rb + j]);
+                part += U_off[v + 1] - U_off[v];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+            if (lane == src) wt = part;
+        }
+        if (split >= 2) {
+            // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
+            cb = wt <= 32                        ? BIN_C4_REG
+                 : wt <= C4_T1                   ? BIN_C4_WARP
+                 : wt <= C4_T2                   ? BIN_C4_BLOCK
+                 : (wt <= t3 && split < 65536)   ? BIN_C4_CTA
+                                                 : BIN_C4_DENSE;
         }
 #pragma unroll 1
         for (int b = 0; b < NBINS; b++) {

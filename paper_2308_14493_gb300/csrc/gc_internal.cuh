@@ -79,7 +79,7 @@ enum {
 constexpr int TRI_KM = 512;
 constexpr int C4_T1 = 512;
 constexpr int C4_T2 = 8192;
-constexpr long long C4_T3 = 262144;
+constexpr long long C4_T3 = 32768;
 constexpr int C4_CLUSTER = 8;       // CTAs per cluster of the dense 4-cycle kernel
 constexpr int C4_DENSE_THREADS = 1024;
 

@@ -54,6 +54,24 @@ class gc_stats(ctypes.Structure):
         return out
 
 
+class gc_server_options(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
+class gc_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("graph", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("counts", ctypes.c_uint64 * 6), ("n_ins", ctypes.c_int64), ("n_del", ctypes.c_int64),
+                ("region_vertices", ctypes.c_int64), ("ms_device", ctypes.c_float), ("relayouts", ctypes.c_int32),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("bytes_predicted", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["counts"] = [int(x) for x in self.counts]
+        return d
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -76,6 +94,8 @@ def load():
             lib.gc_counts.argtypes = [P, u64p]
             lib.gc_apply_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
             lib.gc_apply_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
+            lib.gc_count_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
+            lib.gc_count_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
             lib.gc_apply_batches.argtypes = [P, ctypes.POINTER(i32p), i64p, ctypes.POINTER(i32p), i64p,
                                              ctypes.c_int32, ctypes.c_int32, u64p]
             lib.gc_apply_batches_device.argtypes = [P, P, i64p, ctypes.c_int32, ctypes.c_int32, u64p]
@@ -88,6 +108,19 @@ def load():
             lib.gc_close.argtypes = [P]
             lib.gc_close.restype = None
             lib.gc_count_static_noalloc.argtypes = [ctypes.c_int32, P, P, ctypes.c_int64, P, u64p]
+            lib.gc_device_bytes.argtypes = [P]
+            lib.gc_device_bytes.restype = ctypes.c_int64
+            lib.gc_batch_bytes.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+            lib.gc_batch_bytes.restype = ctypes.c_int64
+            lib.gc_trim.argtypes = [P]
+            lib.gc_server_open.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(gc_server_options),
+                                           ctypes.POINTER(P)]
+            lib.gc_server_submit.argtypes = [P, ctypes.c_int32, i32p, ctypes.c_int64, i32p, ctypes.c_int64, i64p]
+            lib.gc_server_wait.argtypes = [P, ctypes.c_int64, ctypes.POINTER(gc_result)]
+            lib.gc_server_drain.argtypes = [P]
+            lib.gc_server_counters.argtypes = [P, i64p, i64p]
+            lib.gc_server_close.argtypes = [P]
+            lib.gc_server_close.restype = None
             _lib = lib
     return _lib
 
@@ -159,6 +192,22 @@ def gc_apply_batch_device(h, d_ins_ptr: int, n_ins: int, d_del_ptr: int, n_del: 
     return [int(x) for x in out]
 
 
+def gc_count_batch(h, ins, dels) -> list[int]:
+    """Counts of G (+) B without applying the batch (what-if)."""
+    a, na = _pairs(ins)
+    d, nd = _pairs(dels)
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_count_batch(h, _ptr(a), na, _ptr(d), nd, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_count_batch_device(h, d_ins_ptr: int, n_ins: int, d_del_ptr: int, n_del: int) -> list[int]:
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_count_batch_device(h, ctypes.c_void_p(d_ins_ptr), n_ins, ctypes.c_void_p(d_del_ptr), n_del,
+                                        _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
 def gc_apply_batches(h, batches, independent: bool = False) -> list[list[int]]:
     k = len(batches)
     arrs = [(_pairs(i), _pairs(d)) for i, d in batches]
@@ -222,6 +271,94 @@ def gc_count_static_noalloc(n: int, d_row_ptr: int, d_col: int, nnz: int, stream
     return [int(x) for x in out]
 
 
+def gc_device_bytes(h) -> int:
+    return int(load().gc_device_bytes(h))
+
+
+def gc_batch_bytes(h, n_ins: int, n_del: int) -> int:
+    return int(load().gc_batch_bytes(h, int(n_ins), int(n_del)))
+
+
+def gc_trim(h) -> None:
+    _check(load().gc_trim(h), h)
+
+
+def gc_server_open(handles, slots: int = 4, hbm_budget_bytes: int = 0):
+    lib = load()
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    o = gc_server_options()
+    o.slots = slots
+    o.hbm_budget_bytes = hbm_budget_bytes
+    s = ctypes.c_void_p()
+    rc = lib.gc_server_open(arr, len(handles), ctypes.byref(o), ctypes.byref(s))
+    if rc != GC_OK:
+        raise GCError(rc, "gc_server_open failed")
+    return s
+
+
+def gc_server_submit(s, graph: int, ins, dels) -> int:
+    a, na = _pairs(ins)
+    d, nd = _pairs(dels)
+    t = ctypes.c_int64()
+    rc = load().gc_server_submit(s, int(graph), _ptr(a), na, _ptr(d), nd, ctypes.byref(t))
+    if rc != GC_OK:
+        raise GCError(rc, "gc_server_submit failed")
+    return int(t.value)
+
+
+def gc_server_wait(s, ticket: int) -> dict:
+    r = gc_result()
+    rc = load().gc_server_wait(s, int(ticket), ctypes.byref(r))
+    if rc != GC_OK:
+        raise GCError(rc, "gc_server_wait: unknown ticket")
+    return r.as_dict()
+
+
+def gc_server_drain(s) -> None:
+    load().gc_server_drain(s)
+
+
+def gc_server_counters(s) -> tuple[int, int]:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    load().gc_server_counters(s, ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
+
+
+def gc_server_close(s) -> None:
+    load().gc_server_close(s)
+
+
+class Server:
+    """Request loop over resident graphs (``Graph`` objects, not owned)."""
+
+    def __init__(self, graphs, slots: int = 4, hbm_budget_bytes: int = 0):
+        self.graphs = list(graphs)
+        self.s = gc_server_open([g.h for g in self.graphs], slots, hbm_budget_bytes)
+
+    def submit(self, graph: int, ins, dels) -> int:
+        return gc_server_submit(self.s, graph, ins, dels)
+
+    def wait(self, ticket: int) -> dict:
+        return gc_server_wait(self.s, ticket)
+
+    def drain(self):
+        gc_server_drain(self.s)
+
+    def counters(self):
+        return gc_server_counters(self.s)
+
+    def close(self):
+        if self.s is not None:
+            gc_server_close(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def gc_last_error(h=None) -> str:
     return (load().gc_last_error(h) or b"").decode()
 
@@ -259,6 +396,9 @@ class Graph:
     def apply(self, ins, dels):
         return gc_apply_batch(self.h, ins, dels)
 
+    def count_batch(self, ins, dels):
+        return gc_count_batch(self.h, ins, dels)
+
     def apply_many(self, batches, independent=False):
         return gc_apply_batches(self.h, batches, independent)
 
@@ -270,3 +410,9 @@ class Graph:
 
     def export_csr(self):
         return gc_export_csr(self.h, self.n)
+
+    def device_bytes(self):
+        return gc_device_bytes(self.h)
+
+    def trim(self):
+        gc_trim(self.h)

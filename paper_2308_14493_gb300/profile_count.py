@@ -1,0 +1,57 @@
+"""Static count of a seeded Chung-Lu graph, repeated, for kernel profiling.
+
+    python -m paper_2308_14493_gb300.profile_count --n 800000 --m 15000000 \\
+        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000]
+
+Opens the graph (one static count), then runs ``reps`` more static counts
+(or, with ``--batch``, ``reps`` sequential batches of that many updates, 60%
+insertions) and prints the per-stage device times of each call.  Used as the
+command under ncu; it runs the library exactly as a user would.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import gen  # noqa: E402
+
+from . import gc as gcb  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=800000)
+    ap.add_argument("--m", type=int, default=15000000)
+    ap.add_argument("--gamma", type=float, default=2.3)
+    ap.add_argument("--dmax", type=float, default=10000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=0)
+    a = ap.parse_args()
+    keys = gen.chung_lu_graph(a.n, a.m, a.gamma, a.dmax, a.seed)
+    rp, col = gen.csr_from_keys(a.n, keys)
+    with gcb.Graph(a.n, rp, col) as g:
+        print(json.dumps({"open": g.stats()["ms_stage"]}), flush=True)
+        if a.batch:
+            for ins, dels in gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1):
+                g.apply(ins, dels)
+                st = g.stats()
+                print(json.dumps({"batch_ms": st["ms_device"], "stage_ms": st["ms_stage"],
+                                  "region_vertices": st["region_vertices"]}), flush=True)
+        else:
+            for _ in range(a.reps):
+                g.count_static()
+                st = g.stats()
+                print(json.dumps({"static_ms": st["ms_device"], "stage_ms": st["ms_stage"],
+                                  "work_triangles": st["work_triangles"], "work_wedges": st["work_wedges"]}),
+                      flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -290,6 +290,22 @@ def test_independent_batches_equal_fresh_copies(gcb):
         assert out == oracle.fdgc_step(rp, col, ins, dels, F0)["F"]
 
 
+def test_count_batch_is_a_what_if_query(gcb):
+    """gc_count_batch returns the counts of G (+) B and leaves the graph and
+    the maintained counts untouched; its stats carry C_a and C_b."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    with open_graph(gcb, n, rp, col) as g:
+        for seed, (ni, nd) in enumerate([(700, 300), (0, 900), (1200, 0), (1, 1)]):
+            ins, dels = gen.random_batch(n, keys, ni, nd, 60 + seed)
+            r = oracle.fdgc_step(rp, col, ins, dels, F0)
+            assert g.count_batch(ins, dels) == r["F"]
+            st = g.stats()
+            assert mod64(st["Ca"]) == mod64(r["Ca"]) and mod64(st["Cb"]) == mod64(r["Cb"])
+            assert g.counts() == F0 and same_graph(g, rp, col)
+
+
 def test_sequential_batches_call_equals_single_calls(gcb):
     n, keys = gen.workload_graph("c2")
     rp, col = gen.csr_from_keys(n, keys)
