@@ -60,7 +60,11 @@ typedef struct {
     float slack;         /* spare capacity per adjacency row; 0 -> 0.25 */
     int32_t device;      /* CUDA device ordinal; 0 -> current device */
     int32_t dense_cluster; /* CTAs per cluster of the heavy 4-cycle kernel: 0 auto, 8 or 16 */
-    int32_t reserved[6];
+    int32_t chunk_threshold; /* wedge bound above which a 4-cycle pivot is counted in shared memory
+                                over id-range chunks; <= 0: never (the cluster kernel takes them) */
+    int32_t chunk_stage;     /* wedge records staged per CTA by that kernel: 0 -> min(2^21, 2m + 1024),
+                                at least 1024; larger pivots take more walks */
+    int32_t reserved[4];
 } gc_options;
 
 /* Per-batch record of the last gc_apply_batch* call. */
@@ -220,6 +224,39 @@ int gc_export_csr(gc_graph *g, int32_t *row_ptr, int32_t *col);
 #define GC_NOALLOC_MAX_ENTRIES 524288
 int gc_count_static_noalloc(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col, int64_t nnz,
                             void *stream, uint64_t out[6]);
+
+/*
+ * Bin boundaries of the counting pass.  Triangle roots are binned by their
+ * out-degree k, 4-cycle pivots by the wedge bound w~ (sum of the degrees of
+ * their lower neighbours); each field is the upper bound of one kernel's bin,
+ * clamped to the capacity that kernel was compiled for (in brackets).  The
+ * bins change only the speed, never the counts.
+ */
+typedef struct {
+    int32_t tri_warp_max;   /* warp per root                    [32]    */
+    int32_t tri_block_max;  /* block per root, merge beyond     [512]   */
+    int32_t c4_reg_max;     /* registers                        [32]    */
+    int32_t c4_warp_max;    /* warp hash in shared memory       [512]   */
+    int32_t c4_block_max;   /* block hash in shared memory      [8192]  */
+    int32_t reserved0;
+    int64_t c4_cta_max;     /* per-CTA hash table in L2         [32768] */
+    int64_t c4_chunk_min;   /* above this: shared-memory counters over id-range chunks;
+                               otherwise a CTA cluster on a dense array in L2; 0 = never */
+    int64_t reserved[4];
+} gc_tuning;
+
+int gc_get_tuning(const gc_graph *g, gc_tuning *t);
+int gc_set_tuning(gc_graph *g, const gc_tuning *t);
+
+/*
+ * Pick the bin boundaries for this graph by measurement: static counts of
+ * the current graph under a set of candidate boundaries (coordinate descent
+ * from the current ones, each candidate timed `reps` times with CUDA events,
+ * the minimum kept).  The fastest set is installed and returned in *best
+ * (may be NULL); *best_ms (may be NULL) receives its time.  Counts are
+ * checked equal across all candidates (GC_ECUDA if not).
+ */
+int gc_autotune(gc_graph *g, int32_t reps, gc_tuning *best, float *best_ms);
 
 /* Device memory.  gc_device_bytes: bytes the handle holds now (graph,
    counting state and scratch).  gc_batch_bytes: bytes a batch of n_ins

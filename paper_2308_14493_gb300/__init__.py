@@ -20,6 +20,9 @@ from .gc import (  # noqa: F401
     gc_count_static,
     gc_count_static_noalloc,
     gc_device_bytes,
+    gc_get_tuning,
+    gc_set_tuning,
+    gc_autotune,
     gc_batch_bytes,
     gc_trim,
     gc_server_open,

@@ -71,6 +71,7 @@ struct gc_graph {
     uint32_t* visited = nullptr;
     int32_t *wlist = nullptr, *U_deg = nullptr, *U_split = nullptr, *da = nullptr, *db = nullptr;
     long long* U_off = nullptr;
+    long long* U_wt = nullptr;           // wedge bound per 4-cycle pivot
     // scratch that grows with the batch or the graph
     Buf<uint32_t> U_col;
     Buf<unsigned long long> tpack;
@@ -84,6 +85,9 @@ struct gc_graph {
     int dense_cluster_size = 8;
     Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
     int cta_groups = 0;
+    Buf<uint32_t> chunk_stages;          // staging of the chunked 4-cycle kernel (per CTA)
+    long long stage_cap = 0;
+    Tuning tune = default_tuning();     // bin boundaries of the counting pass
     int32_t* bins = nullptr;             // NBINS * n work lists of the counting pass
     // captured batch graph and the shape it was captured for
     cudaGraphExec_t gexec = nullptr;
@@ -397,6 +401,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     ca.U_off = g->U_off;
     ca.U_col = g->U_col.p;
     ca.U_split = g->U_split;
+    ca.U_wt = g->U_wt;
     ca.da = g->da;
     ca.db = g->db;
     ca.tpack = g->tpack.p;
@@ -408,6 +413,9 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     ca.cta_tables = g->cta_tables.p;
     ca.cta_table_words = 2 * C4_T3;
     ca.cta_groups = g->cta_groups;
+    ca.chunk_stages = g->chunk_stages.p;
+    ca.stage_cap = g->stage_cap;
+    ca.tune = g->tune;
     ca.sms = g->sms;
     g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
                                     timed ? g->ev[5] : nullptr, fin);
@@ -820,6 +828,7 @@ static void destroy(gc_graph* g) {
     for (auto p : p32) dfree(g, p);
     dfree(g, g->row_start);
     dfree(g, g->U_off);
+    dfree(g, g->U_wt);
     dfree(g, g->ctl);
     dfree(g, g->desc);
     dfree(g, g->segA);
@@ -847,6 +856,7 @@ static void destroy(gc_graph* g) {
     release(g, g->out_dev);
     release(g, g->dense);
     release(g, g->cta_tables);
+    release(g, g->chunk_stages);
     dfree(g, g->bins);
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -875,12 +885,13 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     g->db = (int32_t*)dalloc(g, 4 * nn);
     g->row_start = (long long*)dalloc(g, 8 * (nn + 1));
     g->U_off = (long long*)dalloc(g, 8 * (nn + 1));
+    g->U_wt = (long long*)dalloc(g, 8 * nn);
     g->ctl = (Ctl*)dalloc(g, sizeof(Ctl));
     g->segA = (int2*)dalloc(g, sizeof(int2) * nn);
     g->segD = (int2*)dalloc(g, sizeof(int2) * nn);
     g->visited = (uint32_t*)dalloc(g, 4 * ((nn + 31) / 32 + 1));
     if (!g->perm || !g->iperm || !g->deg || !g->cap || !g->wlist || !g->U_deg || !g->U_split || !g->da || !g->db ||
-        !g->row_start || !g->U_off || !g->ctl || !g->segA || !g->segD || !g->visited)
+        !g->row_start || !g->U_off || !g->U_wt || !g->ctl || !g->segA || !g->segD || !g->visited)
         return nomem(g, "graph state");
     if (ensure_desc(g, 16)) return GC_ENOMEM;
     if (!ensure(g, g->bsum, 1024)) return nomem(g, "scan scratch");
@@ -986,6 +997,11 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
     g->cta_groups = g->sms;
     if (!ensure(g, g->cta_tables, (size_t)g->cta_groups * 2 * C4_T3)) return nomem(g, "4-cycle hash tables");
+    // staging of the chunked 4-cycle kernel: a pivot's wedge records, up to
+    // 2^21 per CTA (larger pivots take several walks)
+    g->stage_cap = g->opt.chunk_stage > 0 ? std::max<long long>(g->opt.chunk_stage, 1024)
+                                          : std::min<long long>(1ll << 21, std::max<long long>(2 * m2 + 1024, 1 << 16));
+    if (!ensure(g, g->chunk_stages, (size_t)g->sms * (size_t)g->stage_cap)) return nomem(g, "4-cycle staging");
     CK(cudaMemsetAsync(g->cta_tables.p, 0, 8 * g->cta_tables.cap, s));
     return count_static(g, true, nullptr);
 }
@@ -1080,6 +1096,7 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
     g->opt = o;
     g->n = n;
     g->S = std::max(1, bitlen(n > 0 ? n - 1 : 0));
+    if (o.chunk_threshold > 0) g->tune.c4_chunk_min = o.chunk_threshold;
     g->hops = o.region_hops;
     g->slack = o.slack;
     int rc = GC_OK;
@@ -1304,6 +1321,136 @@ int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
         for (int j = 0; j < deg[i]; j++) o[j] = iperm[hc[(size_t)rs[i] + j]];
         std::sort(o, o + deg[i]);
     }
+    return GC_OK;
+}
+
+static void tuning_to_abi(const Tuning& t, gc_tuning* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->tri_warp_max = t.tri_warp_max;
+    o->tri_block_max = t.tri_block_max;
+    o->c4_reg_max = t.c4_reg_max;
+    o->c4_warp_max = t.c4_warp_max;
+    o->c4_block_max = t.c4_block_max;
+    o->c4_cta_max = t.c4_cta_max;
+    o->c4_chunk_min = t.c4_chunk_min >= NEVER ? 0 : t.c4_chunk_min;
+}
+
+int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
+    if (!g || !t) return GC_EINVAL;
+    tuning_to_abi(g->tune, t);
+    return GC_OK;
+}
+
+int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
+    if (!g || !t) return GC_EINVAL;
+    if (t->tri_warp_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
+        t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0) {
+        g->err = "tuning: every bound must be positive (c4_chunk_min may be 0)";
+        return GC_EINVAL;
+    }
+    Tuning n;
+    n.tri_warp_max = t->tri_warp_max;
+    n.tri_block_max = t->tri_block_max;
+    n.c4_reg_max = t->c4_reg_max;
+    n.c4_warp_max = t->c4_warp_max;
+    n.c4_block_max = t->c4_block_max;
+    n.c4_cta_max = t->c4_cta_max;
+    n.c4_chunk_min = t->c4_chunk_min == 0 ? NEVER : t->c4_chunk_min;
+    g->tune = n;
+    return GC_OK;
+}
+
+// Best of `reps` static counts under the current tuning.
+static int time_static(gc_graph* g, int reps, float* ms, uint64_t out[6]) {
+    float best = 1e30f;
+    for (int r = 0; r < reps; r++) {
+        int rc = count_static(g, false, out);
+        if (rc) return rc;
+        best = std::min(best, g->st.ms_device);
+    }
+    *ms = best;
+    return GC_OK;
+}
+
+int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
+    if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    g->err.clear();
+    if (reps <= 0) reps = 2;
+    Tuning cur = g->tune;
+    uint64_t ref[6], got[6];
+    float cur_ms = 0.f;
+    int rc = time_static(g, reps, &cur_ms, ref);
+    if (rc) return rc;
+    // candidate values per boundary; coordinate descent, at most two sweeps
+    const long long cand[7][4] = {
+        {16, 32, -1, -1},                 // tri_warp_max
+        {128, 256, 512, -1},              // tri_block_max
+        {16, 32, -1, -1},                 // c4_reg_max
+        {128, 512, -1, -1},               // c4_warp_max
+        {2048, 8192, -1, -1},             // c4_block_max
+        {8192, 16384, 32768, -1},         // c4_cta_max (8192: tier unused)
+        {NEVER, 262144, 1048576, 4194304} // c4_chunk_min
+    };
+    auto field = [](Tuning& t, int i) -> long long {
+        switch (i) {
+            case 0: return t.tri_warp_max;
+            case 1: return t.tri_block_max;
+            case 2: return t.c4_reg_max;
+            case 3: return t.c4_warp_max;
+            case 4: return t.c4_block_max;
+            case 5: return t.c4_cta_max;
+            default: return t.c4_chunk_min;
+        }
+    };
+    auto set = [](Tuning& t, int i, long long v) {
+        switch (i) {
+            case 0: t.tri_warp_max = (int)v; break;
+            case 1: t.tri_block_max = (int)v; break;
+            case 2: t.c4_reg_max = (int)v; break;
+            case 3: t.c4_warp_max = (int)v; break;
+            case 4: t.c4_block_max = (int)v; break;
+            case 5: t.c4_cta_max = v; break;
+            default: t.c4_chunk_min = v; break;
+        }
+    };
+    const bool chunk_ok = g->chunk_stages.p && (long long)g->n <= c4_chunk_max_ids();
+    for (int sweep = 0; sweep < 2; sweep++) {
+        bool moved = false;
+        for (int i = 0; i < 7; i++) {
+            if (i == 6 && !chunk_ok) continue;
+            for (int k = 0; k < 4; k++) {
+                const long long v = cand[i][k];
+                if (v < 0 || v == field(cur, i)) continue;
+                Tuning t = cur;
+                set(t, i, v);
+                g->tune = t;
+                float ms = 0.f;
+                rc = time_static(g, reps, &ms, got);
+                if (rc) {
+                    g->tune = cur;
+                    return rc;
+                }
+                if (std::memcmp(got, ref, sizeof(ref)) != 0) {
+                    g->tune = cur;
+                    g->err = "autotune: counts differ between bin boundaries";
+                    return GC_ECUDA;
+                }
+                if (ms < 0.97f * cur_ms) {
+                    cur = t;
+                    cur_ms = ms;
+                    moved = true;
+                }
+            }
+        }
+        if (!moved) break;
+    }
+    g->tune = cur;
+    if (best) tuning_to_abi(cur, best);
+    if (best_ms) *best_ms = cur_ms;
     return GC_OK;
 }
 

@@ -54,7 +54,7 @@ __global__ void k_reset_count(Ctl* c) {
     int t = threadIdx.x;
     if (t < 16) c->acc[t] = 0;
     if (t < 8) c->work[t] = 0;
-    if (t < 8) c->nbin[t] = 0;
+    if (t < NBINS) c->nbin[t] = 0;
     if (t == 0) c->maxdeg = 0;
 }
 
@@ -73,17 +73,6 @@ __device__ __forceinline__ void acc_add(Ctl* c, int slot, unsigned long long x) 
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c->acc[slot], x);
 }
 
-// index of id y in the sorted entries s[0..k), or -1
-__device__ __forceinline__ int find_pos(const uint32_t* s, int k, uint32_t y) {
-    int lo = 0, hi = k;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (vid(s[mid]) < y) lo = mid + 1;
-        else hi = mid;
-    }
-    return (lo < k && vid(s[lo]) == y) ? lo : -1;
-}
-
 // largest q in [0, k) with pre[q] <= t (pre[0] = 0 <= t < pre[k])
 __device__ __forceinline__ int find_seg(const int* pre, int k, int t) {
     int lo = 0, hi = k;
@@ -97,58 +86,63 @@ __device__ __forceinline__ int find_seg(const int* pre, int k, int t) {
 
 // ---- binning ---------------------------------------------------------------
 
+// Wedge bound of every 4-cycle pivot: w~(u) = sum of the union-graph degrees
+// of its lower neighbours.  A warp per vertex (hubs with tens of thousands
+// of lower neighbours spread over the grid like everyone else).
+__global__ void k_wedge_bound(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                              const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                              long long* __restrict__ U_wt) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const int32_t u = wlist[i];
+        const int sp = U_split[u];
+        long long part = 0;
+        if (sp >= 2) {
+            const long long rb = U_off[u];
+#pragma unroll 4
+            for (int j = lane; j < sp; j += 32) {
+                const uint32_t v = vid(U_col[rb + j]);
+                part += U_off[v + 1] - U_off[v];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        }
+        if (lane == 0) U_wt[u] = part;
+    }
+}
+
+// Work bins: triangle roots by out-degree, 4-cycle pivots by w~.
 __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
-                      const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
-                      int32_t* __restrict__ bins, int n, long long t3) {
+                      const int32_t* __restrict__ U_split, const long long* __restrict__ U_wt,
+                      int32_t* __restrict__ bins, int n, Tuning t) {
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long nW_r = ((long long)nW + 31) & ~31ll;
     int dmax = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nW_r; i += stride) {
-        bool valid = i < nW;
+        const bool valid = i < nW;
         int tb = -1, cb = -1;
-        int32_t u = valid ? wlist[i] : 0;
+        const int32_t u = valid ? wlist[i] : 0;
         if (valid) {
-            long long rb = U_off[u], re = U_off[u + 1];
-            int k = (int)(re - rb) - U_split[u];
+            const long long rb = U_off[u], re = U_off[u + 1];
+            const int split = U_split[u];
+            const int k = (int)(re - rb) - split;
             dmax = max(dmax, (int)(re - rb));
-            if (k >= 2) tb = k <= 32 ? BIN_TRI_WARP : (k <= TRI_KM ? BIN_TRI_BLOCK : BIN_TRI_MERGE);
-        }
-        // wedge bound w~ = sum of the row lengths of the lower neighbours:
-        // short lists by their own thread, long ones (hubs) by the whole warp
-        const int split = valid ? U_split[u] : 0;
-        long long wt = 0;
-        if (split >= 2 && split <= 64) {
-            const long long rb = U_off[u];
-            for (int j = 0; j < split; j++) {
-                uint32_t v = vid(U_col[rb + j]);
-                wt += U_off[v + 1] - U_off[v];
+            if (k >= 2) tb = k <= t.tri_warp_max ? BIN_TRI_WARP : (k <= t.tri_block_max ? BIN_TRI_BLOCK : BIN_TRI_MERGE);
+            if (split >= 2) {
+                const long long wt = U_wt[u];
+                // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
+                cb = wt <= t.c4_reg_max                         ? BIN_C4_REG
+                     : wt <= t.c4_warp_max                      ? BIN_C4_WARP
+                     : wt <= t.c4_block_max                     ? BIN_C4_BLOCK
+                     : (wt <= t.c4_cta_max && split < 65536)    ? BIN_C4_CTA
+                     : wt > t.c4_chunk_min                      ? BIN_C4_CHUNK
+                                                                : BIN_C4_DENSE;
             }
-        }
-        unsigned big = __ballot_sync(FULL, split > 64);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const int32_t uu = __shfl_sync(FULL, u, src);
-            const int sp = __shfl_sync(FULL, split, src);
-            const long long rb = U_off[uu];
-            long long part = 0;
-            for (int j = lane; j < sp; j += 32) {
-                uint32_t v = vid(U_col[rb + j]);
-                part += U_off[v + 1] - U_off[v];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-            if (lane == src) wt = part;
-        }
-        if (split >= 2) {
-            // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
-            cb = wt <= 32                        ? BIN_C4_REG
-                 : wt <= C4_T1                   ? BIN_C4_WARP
-                 : wt <= C4_T2                   ? BIN_C4_BLOCK
-                 : (wt <= t3 && split < 65536)   ? BIN_C4_CTA
-                                                 : BIN_C4_DENSE;
         }
 #pragma unroll 1
         for (int b = 0; b < NBINS; b++) {
@@ -169,6 +163,17 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
 
 // ---- triangles and 4-cliques -------------------------------------------------
 
+// Position of id y in the out-list through the shared hash table, or -1.
+__device__ __forceinline__ int hash_pos(const uint32_t* hk, const uint16_t* hp, int shift, uint32_t mask, uint32_t y) {
+    uint32_t h = (y * 0x9E3779B1u) >> shift;
+    for (;;) {
+        const uint32_t key = hk[h];
+        if (key == y) return hp[h];
+        if (key == 0xFFFFFFFFu) return -1;
+        h = (h + 1) & mask;
+    }
+}
+
 constexpr int TW = 8;  // warps per block of the warp-per-root kernel
 
 __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __restrict__ list,
@@ -181,6 +186,8 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
     __shared__ int sPre[TW][33];
     __shared__ uint32_t sRA[TW][32], sRB[TW][32];
     __shared__ unsigned long long sTq[TW][32];
+    __shared__ uint32_t sHk[TW][64];
+    __shared__ uint16_t sHp[TW][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cnt = c->nbin[BIN_TRI_WARP];
     unsigned long long ka = 0, kb = 0;
@@ -211,12 +218,22 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
         sRA[w][lane] = 0;
         sRB[w][lane] = 0;
         sTq[w][lane] = 0;
+        sHk[w][lane] = 0xFFFFFFFFu;
+        sHk[w][lane + 32] = 0xFFFFFFFFu;
         __syncwarp();
+        if (lane < k) {  // id -> position, 64 slots for at most 32 distinct ids
+            const uint32_t y = vid(x);
+            uint32_t h = (y * 0x9E3779B1u) >> 26;
+            while (atomicCAS(&sHk[w][h], 0xFFFFFFFFu, y) != 0xFFFFFFFFu) h = (h + 1) & 63u;
+            sHp[w][h] = (uint16_t)lane;
+        }
+        __syncwarp();
+        int q = 0;
         for (int t = lane; t < total; t += 32) {
-            int q = find_seg(sPre[w], k, t);
+            while (q + 1 < k && sPre[w][q + 1] <= t) q++;
             long long slot = sNb[w][q] + (t - sPre[w][q]);
             uint32_t e = U_col[slot];
-            int p = find_pos(sX[w], k, vid(e));
+            int p = hash_pos(sHk[w], sHp[w], 26, 63u, vid(e));
             if (p < 0) continue;
             uint32_t f = sX[w][q] & sX[w][p] & e;
             unsigned long long iv = flag_inc(f);
@@ -242,12 +259,17 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
 }
 
 constexpr int TB_WORDS = TRI_KM / 32;
+constexpr int TB_HASH = 2 * TRI_KM;  // id -> position table of the out-list
 constexpr size_t tri_block_smem() {
     return (size_t)TRI_KM * 4 + (size_t)TRI_KM * 8 + (size_t)(TRI_KM + 8) * 4 + 2ull * TRI_KM * TB_WORDS * 4 +
-           (size_t)TRI_KM * 8;
+           (size_t)TRI_KM * 8 + (size_t)TB_HASH * 4 + (size_t)TB_HASH * 2;
 }
 size_t tri_block_smem_bytes() { return tri_block_smem(); }
 
+// Roots with 32 < k <= TRI_KM: one block per root.  The out-list X is held
+// in shared memory with an id -> position hash table; the candidates (every
+// entry of N+(v) up to max X, for v in X) are dealt in warp-contiguous runs
+// of 32, so a lane finds its row by stepping from the run's first row.
 __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __restrict__ list,
                                                   const long long* __restrict__ U_off,
                                                   const uint32_t* __restrict__ U_col,
@@ -260,8 +282,10 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
     int* sPre = (int*)(smem + (size_t)TRI_KM * 20);
     uint32_t* sRA = (uint32_t*)(smem + (size_t)TRI_KM * 24 + 32);
     uint32_t* sRB = sRA + TRI_KM * TB_WORDS;
+    uint32_t* sHk = sRB + TRI_KM * TB_WORDS;
+    uint16_t* sHp = (uint16_t*)(sHk + TB_HASH);
     __shared__ int s_idx;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
     const int cnt = c->nbin[BIN_TRI_BLOCK];
     unsigned long long ka = 0, kb = 0;
     for (;;) {
@@ -274,7 +298,12 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
         long long rb = U_off[u] + U_split[u];
         const int k = (int)(U_off[u + 1] - rb);
         const int W = (k + 31) >> 5;
+        int lg = 6;
+        while ((1 << lg) < 2 * k) lg++;
+        const uint32_t hmask = (1u << lg) - 1;
+        const int hshift = 32 - lg;
         const uint32_t xmax = vid(U_col[rb + k - 1]);
+        for (int t = tid; t < (1 << lg); t += blockDim.x) sHk[t] = 0xFFFFFFFFu;
         for (int t = tid; t < k; t += blockDim.x) {
             uint32_t x = U_col[rb + t];
             uint32_t v = vid(x);
@@ -289,6 +318,12 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
             sRB[t] = 0;
         }
         __syncthreads();
+        for (int t = tid; t < k; t += blockDim.x) {  // ids of an out-list are distinct
+            const uint32_t y = vid(sX[t]);
+            uint32_t h = (y * 0x9E3779B1u) >> hshift;
+            while (atomicCAS(&sHk[h], 0xFFFFFFFFu, y) != 0xFFFFFFFFu) h = (h + 1) & hmask;
+            sHp[h] = (uint16_t)t;
+        }
         if (warp == 0) {  // inclusive scan of sPre[1..k]
             int carry = 0;
             for (int b = 0; b < k; b += 32) {
@@ -305,20 +340,26 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
         }
         __syncthreads();
         const int total = sPre[k];
-        for (int t = tid; t < total; t += blockDim.x) {
-            int q = find_seg(sPre, k, t);
-            long long slot = sNb[q] + (t - sPre[q]);
-            uint32_t e = U_col[slot];
-            int p = find_pos(sX, k, vid(e));
-            if (p < 0) continue;
-            uint32_t f = sX[q] & sX[p] & e;
-            unsigned long long iv = flag_inc(f);
-            if (!iv) continue;
-            if (f & FLAG_A) atomicOr(&sRA[q * W + (p >> 5)], 1u << (p & 31));
-            if (f & FLAG_B) atomicOr(&sRB[q * W + (p >> 5)], 1u << (p & 31));
-            atomicAdd(&sTq[q], iv);
-            atomicAdd(&sTq[p], iv);
-            atomicAdd(&tpack[slot], iv);
+        for (int base = warp * 32; base < total; base += NW * 32) {
+            const int t = base + lane;
+            int q = find_seg(sPre, k, base);
+            if (t < total) {
+                while (q + 1 < k && sPre[q + 1] <= t) q++;
+                const long long slot = sNb[q] + (t - sPre[q]);
+                const uint32_t e = U_col[slot];
+                const int p = hash_pos(sHk, sHp, hshift, hmask, vid(e));
+                if (p >= 0) {
+                    const uint32_t f = sX[q] & sX[p] & e;
+                    const unsigned long long iv = flag_inc(f);
+                    if (iv) {
+                        if (f & FLAG_A) atomicOr(&sRA[q * W + (p >> 5)], 1u << (p & 31));
+                        if (f & FLAG_B) atomicOr(&sRB[q * W + (p >> 5)], 1u << (p & 31));
+                        atomicAdd(&sTq[q], iv);
+                        atomicAdd(&sTq[p], iv);
+                        atomicAdd(&tpack[slot], iv);
+                    }
+                }
+            }
         }
         __syncthreads();
         for (int q = tid; q < k; q += blockDim.x) {
@@ -809,6 +850,275 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
     acc_add(c, 15, wedges);
 }
 
+// Heavy pivots, counters in shared memory.  Shared-memory atomics are about
+// twenty times faster than L2 or distributed-shared-memory atomics, but a
+// pivot's endpoints w range over [0, u), far more ids than shared memory
+// holds.  So the id range is cut into chunks of R ids (R counters fill the
+// shared array) and each chunk is counted on its own:
+//   A1  walk the pivot's wedges once, histogram of their chunks
+//   A2  walk again, scatter each wedge record (w | its G_a / G_b flags) into
+//       a staging area grouped by chunk (runs of equal chunks in a warp take
+//       one atomic)
+//   B   per chunk: one increment per record on the shared counters (the old
+//       value gives the C(c, 2) sum as in the other 4-cycle kernels), then
+//       clear the counters
+// When the pivot's records exceed the staging area, the chunks are taken in
+// groups that fit, one A2 walk per group; a single chunk larger than the
+// staging area is counted directly during its own walk.  Counters are packed
+// 16/16 bits (a/b) while every degree is below 2^16, else 32/32 in 64 bits
+// (half as many ids per chunk).
+constexpr int CH_SEG = 1024;       // lower neighbours per prefix segment
+constexpr int CH_MAXB = 2048;      // chunks per pivot (n <= CH_MAXB * CH_R64)
+constexpr int CH_BYTES = 196608;   // counter bytes
+constexpr int CH_R32 = CH_BYTES / 4;
+constexpr int CH_R64 = CH_BYTES / 8;
+constexpr int CH_UNROLL = 4;
+
+size_t c4_chunk_smem_bytes() {
+    return (size_t)CH_BYTES + sizeof(int) * (CH_MAXB + 1) + sizeof(int) * (CH_SEG + 1) + sizeof(long long) * CH_SEG +
+           sizeof(uint32_t) * CH_SEG;
+}
+
+long long c4_chunk_max_ids() { return (long long)CH_MAXB * CH_R64; }
+
+// Walk every wedge u-v-w (v lower neighbour of u, w < u) of the pivot;
+// fn(w, flags, valid) is called by all 32 lanes of a warp together.
+template <class Fn>
+__device__ __forceinline__ void chunk_walk(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
+                                           long long rb, int nlow, uint32_t u, int* s_pre, long long* s_vb,
+                                           uint32_t* s_fv, int* s_tot, Fn fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    for (int s0 = 0; s0 < nlow; s0 += CH_SEG) {
+        const int ns = min(CH_SEG, nlow - s0);
+        wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, s_tot);
+        const long long total = *s_tot;
+        const long long wstep = (long long)NW * 32 * CH_UNROLL;
+        for (long long base = (long long)warp * 32 * CH_UNROLL; base < total; base += wstep) {
+            uint32_t e[CH_UNROLL], f[CH_UNROLL];
+            int j = find_seg(s_pre, ns, (int)base);
+#pragma unroll
+            for (int r = 0; r < CH_UNROLL; r++) {
+                long long i = base + r * 32 + lane;
+                e[r] = 0xFFFFFFFFu;
+                f[r] = 0;
+                if (i < total) {
+                    while (j + 1 < ns && s_pre[j + 1] <= i) j++;
+                    e[r] = U_col[s_vb[j] + (i - s_pre[j])];
+                    f[r] = s_fv[j];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < CH_UNROLL; r++) {
+                const uint32_t w = vid(e[r]);
+                fn(w, f[r] & e[r] & (FLAG_A | FLAG_B), w < u);
+            }
+        }
+        __syncthreads();  // the next segment reuses the prefix arrays
+    }
+}
+
+// Runs of equal keys among the 32 lanes (consecutive lanes): head lane of
+// each run, its length, and for every lane the head of its run.
+struct Runs {
+    bool head;
+    int len;
+    int myhead;
+};
+__device__ __forceinline__ Runs lane_runs(int key, int lane) {
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    Runs r;
+    r.head = lane == 0 || key != prev;
+    const unsigned heads = __ballot_sync(FULL, r.head);
+    const unsigned le = (2u << lane) - 1u;  // lanes <= lane (all lanes for lane 31)
+    const unsigned after = heads & ~le;
+    r.len = (after ? __ffs(after) - 1 : 32) - lane;
+    r.myhead = 31 - __clz(heads & le);
+    return r;
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void chunk_count_pivot(Ctl* c, const long long* __restrict__ U_off,
+                                                  const uint32_t* __restrict__ U_col, int32_t u, long long rb,
+                                                  int nlow, uint32_t* __restrict__ stage, long long stage_cap,
+                                                  unsigned char* smem, unsigned long long& qa,
+                                                  unsigned long long& qb, unsigned long long& wedges) {
+    constexpr int R = WIDE ? CH_R64 : CH_R32;
+    uint32_t* cnt32 = (uint32_t*)smem;
+    unsigned long long* cnt64 = (unsigned long long*)smem;
+    int* pos = (int*)(smem + CH_BYTES);
+    int* s_pre = pos + CH_MAXB + 1;
+    long long* s_vb = (long long*)(s_pre + CH_SEG + 1);
+    uint32_t* s_fv = (uint32_t*)(s_vb + CH_SEG);
+    __shared__ int s_tot;
+    __shared__ int s_g1;
+    __shared__ long long s_grec;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nch = (int)(((long long)u + R - 1) / R);
+
+    auto count_one = [&](uint32_t w, uint32_t fl, uint32_t base_id) {
+        if (WIDE) {
+            const unsigned long long inc = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
+            const unsigned long long old = atomicAdd(&cnt64[w - base_id], inc);
+            if (fl & FLAG_A) qa += old >> 32;
+            if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
+        } else {
+            const uint32_t old = atomicAdd(&cnt32[w - base_id], flag_inc16(fl));
+            if (fl & FLAG_A) qa += old >> 16;
+            if (fl & FLAG_B) qb += old & 0xFFFFu;
+        }
+    };
+    auto clear_all = [&]() {
+        uint4* c4 = (uint4*)smem;
+        for (int i = tid; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
+    };
+
+    if (nch <= 2) {
+        // few chunks: count each during its own walk, no staging
+        for (int b = 0; b < nch; b++) {
+            const uint32_t base_id = (uint32_t)b * R;
+            chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
+                       [&](uint32_t w, uint32_t fl, bool lt) {
+                           if (lt && b == 0) wedges++;
+                           if (lt && fl && (nch == 1 || (int)(w / R) == b)) count_one(w, fl, base_id);
+                       });
+            // clear the ids this chunk can hold (16-byte granules)
+            const long long ids = min((long long)R, (long long)u - base_id);
+            const long long granules = (ids * (WIDE ? 8 : 4) + 15) / 16;
+            uint4* c4 = (uint4*)smem;
+            for (long long i = tid; i < granules; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+        }
+        return;
+    }
+
+    // A1: histogram of the chunks (and the work counter)
+    for (int b = tid; b < nch; b += blockDim.x) pos[b] = 0;
+    __syncthreads();
+    chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
+               [&](uint32_t w, uint32_t fl, bool lt) {
+                   if (lt) wedges++;
+                   const int key = (lt && fl) ? (int)(w / R) : -1;
+                   const Runs r = lane_runs(key, lane);
+                   if (r.head && key >= 0) atomicAdd(&pos[key], r.len);
+               });
+    // groups of chunks whose records fit the staging area
+    int g0 = 0;
+    while (g0 < nch) {
+        if (tid == 0) {
+            long long sum = 0;
+            int g1 = g0;
+            while (g1 < nch && sum + pos[g1] <= stage_cap) sum += pos[g1++];
+            if (g1 == g0) {
+                sum = pos[g0];
+                g1 = g0 + 1;  // one chunk beyond the staging area: counted directly
+            }
+            s_g1 = g1;
+            s_grec = sum;
+        }
+        __syncthreads();
+        const int g1 = s_g1;
+        const long long grec = s_grec;
+        if (grec == 0) {
+            g0 = g1;
+            __syncthreads();
+            continue;
+        }
+        if (grec > stage_cap) {
+            // direct: one chunk, counted during its own walk
+            const uint32_t base_id = (uint32_t)g0 * R;
+            chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
+                       [&](uint32_t w, uint32_t fl, bool lt) {
+                           if (lt && fl && (int)(w / R) == g0) count_one(w, fl, base_id);
+                       });
+            clear_all();
+            __syncthreads();
+            g0 = g1;
+            continue;
+        }
+        // exclusive offsets of the group's chunks, then A2 scatters into them
+        const int nk = g1 - g0;
+        __syncthreads();
+        if (tid == 0) {
+            int run = 0;
+            for (int b = g0; b < g1; b++) {
+                const int x = pos[b];
+                pos[b] = run;
+                run += x;
+            }
+        }
+        __syncthreads();
+        chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
+                   [&](uint32_t w, uint32_t fl, bool lt) {
+                       const int b = (lt && fl) ? (int)(w / R) : -1;
+                       const int key = (b >= g0 && b < g1) ? b : -1;
+                       const Runs r = lane_runs(key, lane);
+                       int at = 0;
+                       if (r.head && key >= 0) at = atomicAdd(&pos[key], r.len);
+                       at = __shfl_sync(FULL, at, r.myhead);
+                       if (key >= 0) stage[at + (lane - r.myhead)] = w | fl;
+                   });
+        // B: after A2, pos[b] is the end of chunk b and the start of chunk b+1
+        for (int k = 0; k < nk; k++) {
+            const int b = g0 + k;
+            const int st = k == 0 ? 0 : pos[b - 1];
+            const int en = pos[b];
+            if (en == st) continue;
+            const uint32_t base_id = (uint32_t)b * R;
+            for (int i = st + tid; i < en; i += blockDim.x) {
+                const uint32_t rec = __ldcg(&stage[i]);
+                count_one(vid(rec), rec & (FLAG_A | FLAG_B), base_id);
+            }
+            __syncthreads();
+            if ((long long)(en - st) * 16 > R) {
+                clear_all();
+            } else {
+                for (int i = st + tid; i < en; i += blockDim.x) {
+                    const uint32_t w = vid(__ldcg(&stage[i]));
+                    if (WIDE) cnt64[w - base_id] = 0ull;
+                    else cnt32[w - base_id] = 0u;
+                }
+            }
+            __syncthreads();
+        }
+        // the histogram of later groups is still in pos[g1 ..]
+        g0 = g1;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_chunk(Ctl* c, const int32_t* __restrict__ list,
+                                                              const long long* __restrict__ U_off,
+                                                              const uint32_t* __restrict__ U_col,
+                                                              const int32_t* __restrict__ U_split,
+                                                              uint32_t* __restrict__ stages, long long stage_cap) {
+    extern __shared__ __align__(16) unsigned char ch_smem[];
+    __shared__ int s_idx;
+    uint32_t* stage = stages + (size_t)blockIdx.x * (size_t)stage_cap;
+    const bool wide = c->maxdeg >= 65536;
+    const int cnt = c->nbin[BIN_C4_CHUNK];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    // counters start at zero and every chunk leaves them at zero
+    {
+        uint4* c4 = (uint4*)ch_smem;
+        for (int i = threadIdx.x; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[5], 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= cnt) break;
+        const int32_t u = list[idx];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        if (wide) chunk_count_pivot<true>(c, U_off, U_col, u, rb, nlow, stage, stage_cap, ch_smem, qa, qb, wedges);
+        else chunk_count_pivot<false>(c, U_off, U_col, u, rb, nlow, stage, stage_cap, ch_smem, qa, qb, wedges);
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
+
 // Open-addressing insert into a table in global memory.  A slot holds
 // (w + 1) << 32 | packed counts, 0 = empty; counts stay below 2^16 because a
 // pivot of this tier has fewer than 2^16 lower neighbours.  Returns the
@@ -1014,6 +1324,7 @@ void count_setup_attributes() {
     cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_block_smem_bytes());
     cudaFuncSetAttribute(k_c4_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_block_smem_bytes());
     cudaFuncSetAttribute(k_c4_dense_t<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_c4_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_chunk_smem_bytes());
 }
 
 int dense_cluster_plan(int want, int sms, int* size_out) {
@@ -1045,6 +1356,21 @@ int dense_cluster_plan(int want, int sms, int* size_out) {
     return std::max(1, sms / 8);
 }
 
+// The caller's bin boundaries, clamped to what the kernels and the scratch
+// of this pass can take.
+Tuning effective_tuning(const CountArgs& a) {
+    Tuning t = a.tune;
+    t.tri_warp_max = std::max(1, std::min(t.tri_warp_max, 32));
+    t.tri_block_max = std::max(t.tri_warp_max, std::min(t.tri_block_max, TRI_KM));
+    t.c4_reg_max = std::max(1, std::min(t.c4_reg_max, 32));
+    t.c4_warp_max = std::max(t.c4_reg_max, std::min(t.c4_warp_max, C4_T1));
+    t.c4_block_max = std::max(t.c4_warp_max, std::min(t.c4_block_max, C4_T2));
+    t.c4_cta_max = std::max<long long>(t.c4_block_max, std::min<long long>(t.c4_cta_max, a.cta_table_words / 2));
+    if (!a.chunk_stages || a.n_alloc > c4_chunk_max_ids() || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
+    t.c4_chunk_min = std::max<long long>(t.c4_chunk_min, t.c4_cta_max);
+    return t;
+}
+
 int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_c4, cudaEvent_t ev_end,
                      int mode) {
     const int sms = a.sms;
@@ -1052,9 +1378,10 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     auto lists = [&](int b) { return a.bins + (size_t)b * a.n_alloc; };
     long long nw = a.n_alloc > 0 ? a.n_alloc : 1;
     int gb = (int)std::min<long long>((nw + 255) / 256, 8LL * sms);
-    k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.bins, a.n_alloc,
-                             a.cta_table_words / 2);
-    nl++;
+    const Tuning t = effective_tuning(a);
+    k_wedge_bound<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
+    k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
+    nl += 2;
     if (ev_tri) cudaEventRecord(ev_tri, s);
     k_tri_warp<<<4 * sms, TW * 32, 0, s>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
     k_tri_block<<<2 * sms, 256, tri_block_smem_bytes(), s>>>(a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col,
@@ -1085,6 +1412,11 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
                                                         a.cta_tables, a.cta_table_words);
     nl += 5;
+    if (t.c4_chunk_min < NEVER) {
+        k_c4_chunk<<<sms, C4_DENSE_THREADS, c4_chunk_smem_bytes(), s>>>(
+            a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col, a.U_split, a.chunk_stages, a.stage_cap);
+        nl++;
+    }
     if (ev_end) cudaEventRecord(ev_end, s);
     k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
     k_finalize<<<1, 32, 0, s>>>(a.ctl, mode);

@@ -27,6 +27,23 @@ constexpr uint32_t FLAG_B = 0x80000000u;   // entry belongs to G_b
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int MAX_HOPS = 8;
 
+// Work bins of the counting pass: region bins[b * n ...] holds the vertices
+// of bin b.  Triangle roots by out-degree k; 4-cycle pivots by the wedge
+// bound w~ = sum of the degrees of the lower neighbours.
+enum {
+    // (default boundaries; the Tuning below moves them at run time)
+    BIN_TRI_WARP = 0,   // 2 <= k <= 32                   warp per root
+    BIN_TRI_BLOCK = 1,  // 32 < k <= TRI_KM                block per root
+    BIN_TRI_MERGE = 2,  // k > TRI_KM                      merge per out-edge
+    BIN_C4_REG = 3,     // w~ <= 32                        registers (match)
+    BIN_C4_WARP = 4,    // w~ <= C4_T1                     warp hash in shared memory
+    BIN_C4_BLOCK = 5,   // w~ <= C4_T2                     block hash in shared memory
+    BIN_C4_DENSE = 6,   // C4_T3 < w~ <= c4_chunk_min      cluster, shared dense counter array
+    BIN_C4_CTA = 7,     // C4_T2 < w~ <= C4_T3             CTA, own hash table in global memory
+    BIN_C4_CHUNK = 8,   // w~ > c4_chunk_min (off)         CTA, shared-memory counters over id-range chunks
+    NBINS = 9
+};
+
 // Device control block: sizes produced and consumed on the device, so a
 // batch's kernels never wait for the host between stages.
 struct Ctl {
@@ -47,7 +64,7 @@ struct Ctl {
     int overflow;                    // commit needs a re-layout
     int err;                         // GC_E* code raised on the device
     unsigned work[8];                // dynamic work counters
-    int nbin[8];                     // sizes of the work bins (see gc_count.cu)
+    int nbin[NBINS];                 // sizes of the work bins (see gc_count.cu)
     int maxdeg;                      // largest union-graph degree in the region
     // batch source and sequencing (a captured batch graph reads these)
     const int32_t* pairs_ins;        // base of the insertion pairs
@@ -62,25 +79,26 @@ struct Ctl {
     unsigned long long last_out[6];  // counts after the current batch
 };
 
-// Work bins of the counting pass: region bins[b * n ...] holds the vertices
-// of bin b.  Triangle roots by out-degree k; 4-cycle pivots by the wedge
-// bound w~ = sum of the degrees of the lower neighbours.
-enum {
-    BIN_TRI_WARP = 0,   // 2 <= k <= 32        warp per root
-    BIN_TRI_BLOCK = 1,  // 32 < k <= TRI_KM     block per root
-    BIN_TRI_MERGE = 2,  // k > TRI_KM           merge per out-edge
-    BIN_C4_REG = 3,     // w~ <= 32             registers (match)
-    BIN_C4_WARP = 4,    // w~ <= C4_T1          warp hash in shared memory
-    BIN_C4_BLOCK = 5,   // w~ <= C4_T2          block hash in shared memory
-    BIN_C4_DENSE = 6,   // w~ > C4_T3           cluster, shared dense counter array
-    BIN_C4_CTA = 7,     // C4_T2 < w~ <= C4_T3  CTA, own hash table in global memory
-    NBINS = 8
-};
 constexpr int TRI_KM = 512;
 constexpr int C4_T1 = 512;
 constexpr int C4_T2 = 8192;
 constexpr long long C4_T3 = 32768;
 constexpr int C4_CLUSTER = 8;       // CTAs per cluster of the dense 4-cycle kernel
+
+// Bin boundaries of the counting pass (upper bounds of each tier; each at
+// most the capacity its kernel was compiled for).  Chosen per graph by the
+// autotuner or set by the caller.
+struct Tuning {
+    int tri_warp_max;        // out-degree k: warp kernel up to this (<= 32)
+    int tri_block_max;       // block kernel up to this (<= TRI_KM), merge beyond
+    int c4_reg_max;          // wedge bound w~: registers up to this (<= 32)
+    int c4_warp_max;         // warp hash (<= C4_T1)
+    int c4_block_max;        // block hash (<= C4_T2)
+    long long c4_cta_max;    // global hash tables (<= half the table words)
+    long long c4_chunk_min;  // chunked shared-memory kernel above this (else cluster kernel)
+};
+constexpr long long NEVER = 1ll << 62;
+inline Tuning default_tuning() { return Tuning{32, TRI_KM, 32, C4_T1, C4_T2, C4_T3, NEVER}; }
 constexpr int C4_DENSE_THREADS = 1024;
 
 // Handle-independent launch geometry.

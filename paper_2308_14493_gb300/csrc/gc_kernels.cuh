@@ -68,6 +68,7 @@ struct CountArgs {
     const long long* U_off;        // n_alloc + 1
     const uint32_t* U_col;         // flagged entries
     const int32_t* U_split;        // start of the out-list per vertex
+    long long* U_wt;               // n_alloc: wedge bound per pivot (written by the pass)
     const int32_t* da;             // degree in G_a
     const int32_t* db;             // degree in G_b
     unsigned long long* tpack;     // per-entry triangle counters, zeroed
@@ -79,10 +80,16 @@ struct CountArgs {
     unsigned long long* cta_tables; // cta_groups * cta_table_words zeroed words
     long long cta_table_words;      // power of two; pivots up to half of it use the hash tier
     int cta_groups;                 // CTAs of the medium 4-cycle kernel (one table each)
+    uint32_t* chunk_stages;         // sms * stage_cap records of the chunked 4-cycle kernel
+    long long stage_cap;            // records per CTA
+    Tuning tune;                    // bin boundaries (clamped to the capacities)
     int sms;
 };
+Tuning effective_tuning(const CountArgs& a);
 // Dynamic shared-memory limits of the counting kernels (once per device).
 void count_setup_attributes();
+size_t c4_chunk_smem_bytes();
+long long c4_chunk_max_ids();   // the chunked 4-cycle kernel handles vertex ids below this
 // Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
 // 16 if the device can co-schedule it, else 8) and the number of clusters.
 int dense_cluster_plan(int want, int sms, int* size_out);

@@ -39,7 +39,8 @@ constexpr int NA_TPB = 256;
 constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t OFF_CTL = 0;
 constexpr size_t OFF_UOFF = al(OFF_CTL + sizeof(Ctl));
-constexpr size_t OFF_SPLIT = al(OFF_UOFF + 8 * (size_t)(NA_MAX_N + 1));
+constexpr size_t OFF_WT = al(OFF_UOFF + 8 * (size_t)(NA_MAX_N + 1));
+constexpr size_t OFF_SPLIT = al(OFF_WT + 8 * (size_t)NA_MAX_N);
 constexpr size_t OFF_DA = al(OFF_SPLIT + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_DB = al(OFF_DA + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_WL = al(OFF_DB + 4 * (size_t)NA_MAX_N);
@@ -165,6 +166,7 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     Ctl* ctl = (Ctl*)(b + OFF_CTL);
     long long* U_off = (long long*)(b + OFF_UOFF);
     int32_t* U_split = (int32_t*)(b + OFF_SPLIT);
+    long long* U_wt = (long long*)(b + OFF_WT);
     int32_t* da = (int32_t*)(b + OFF_DA);
     int32_t* db = (int32_t*)(b + OFF_DB);
     int32_t* wlist = (int32_t*)(b + OFF_WL);
@@ -203,6 +205,7 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     ca.U_off = U_off;
     ca.U_col = U_col;
     ca.U_split = U_split;
+    ca.U_wt = U_wt;
     ca.da = da;
     ca.db = db;
     ca.tpack = tpack;
@@ -213,6 +216,9 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     ca.dense_cluster_size = 8;
     ca.cta_tables = cta_tables;
     ca.cta_table_words = NA_TABLE_WORDS;
+    ca.chunk_stages = nullptr;  // no chunked 4-cycle tier in the fixed scratch
+    ca.stage_cap = 0;
+    ca.tune = default_tuning();
     ca.cta_groups = NA_CTA_GROUPS;
     ca.sms = sms;
     enqueue_counting(ca, s, nullptr, nullptr, nullptr, 1);

@@ -180,10 +180,12 @@ __global__ void __launch_bounds__(SC_BLOCK) k_scan_apply(const int32_t* __restri
 
 }  // namespace
 
+// One block per 1024 keys (four tiles: short serial scatter loops for the
+// small sorts of a batch), at most two per SM.
 int radix_grid(long long max_count, int sms) {
-    long long g = (max_count + 4095) / 4096;
+    long long g = (max_count + 1023) / 1024;
     if (g < 1) g = 1;
-    if (g > 4L * sms) g = 4L * sms;
+    if (g > 2L * sms) g = 2L * sms;
     if (g > 1024) g = 1024;
     return (int)g;
 }

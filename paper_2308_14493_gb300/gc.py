@@ -30,7 +30,8 @@ class GCError(RuntimeError):
 class gc_options(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
-                ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("chunk_threshold", ctypes.c_int32),
+                ("chunk_stage", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class gc_stats(ctypes.Structure):
@@ -52,6 +53,15 @@ class gc_stats(ctypes.Structure):
             v = getattr(self, name)
             out[name] = list(v) if hasattr(v, "__len__") else v
         return out
+
+
+class gc_tuning(ctypes.Structure):
+    _fields_ = [("tri_warp_max", ctypes.c_int32), ("tri_block_max", ctypes.c_int32), ("c4_reg_max", ctypes.c_int32),
+                ("c4_warp_max", ctypes.c_int32), ("c4_block_max", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("c4_cta_max", ctypes.c_int64), ("c4_chunk_min", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if not name.startswith("reserved")}
 
 
 class gc_server_options(ctypes.Structure):
@@ -108,6 +118,9 @@ def load():
             lib.gc_close.argtypes = [P]
             lib.gc_close.restype = None
             lib.gc_count_static_noalloc.argtypes = [ctypes.c_int32, P, P, ctypes.c_int64, P, u64p]
+            lib.gc_get_tuning.argtypes = [P, ctypes.POINTER(gc_tuning)]
+            lib.gc_set_tuning.argtypes = [P, ctypes.POINTER(gc_tuning)]
+            lib.gc_autotune.argtypes = [P, ctypes.c_int32, ctypes.POINTER(gc_tuning), ctypes.POINTER(ctypes.c_float)]
             lib.gc_device_bytes.argtypes = [P]
             lib.gc_device_bytes.restype = ctypes.c_int64
             lib.gc_batch_bytes.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
@@ -144,7 +157,8 @@ def _pairs(p):
     return a, a.shape[0]
 
 
-def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0):
+def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0,
+            chunk_threshold: int = 0, dense_cluster: int = 0, chunk_stage: int = 0):
     """Open a graph from a symmetric CSR; returns an opaque handle."""
     lib = load()
     rp = _i32(row_ptr)
@@ -154,6 +168,9 @@ def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, str
     opt.region_hops = region_hops
     opt.slack = slack
     opt.stream = stream or None
+    opt.chunk_threshold = chunk_threshold
+    opt.dense_cluster = dense_cluster
+    opt.chunk_stage = chunk_stage
     h = ctypes.c_void_p()
     rc = lib.gc_open(int(n), _ptr(rp), _ptr(c), ctypes.byref(opt), ctypes.byref(h))
     _check(rc, None)
@@ -271,6 +288,27 @@ def gc_count_static_noalloc(n: int, d_row_ptr: int, d_col: int, nnz: int, stream
     return [int(x) for x in out]
 
 
+def gc_get_tuning(h) -> dict:
+    t = gc_tuning()
+    _check(load().gc_get_tuning(h, ctypes.byref(t)), h)
+    return t.as_dict()
+
+
+def gc_set_tuning(h, **bounds) -> None:
+    t = gc_tuning()
+    _check(load().gc_get_tuning(h, ctypes.byref(t)), h)
+    for k, v in bounds.items():
+        setattr(t, k, int(v))
+    _check(load().gc_set_tuning(h, ctypes.byref(t)), h)
+
+
+def gc_autotune(h, reps: int = 2) -> tuple[dict, float]:
+    t = gc_tuning()
+    ms = ctypes.c_float()
+    _check(load().gc_autotune(h, int(reps), ctypes.byref(t), ctypes.byref(ms)), h)
+    return t.as_dict(), float(ms.value)
+
+
 def gc_device_bytes(h) -> int:
     return int(load().gc_device_bytes(h))
 
@@ -366,9 +404,9 @@ def gc_last_error(h=None) -> str:
 class Graph:
     """A device-resident graph with maintained graphlet counts."""
 
-    def __init__(self, n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25):
+    def __init__(self, n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, **opts):
         self.n = int(n)
-        self.h = gc_open(n, row_ptr, col, region_hops, slack)
+        self.h = gc_open(n, row_ptr, col, region_hops, slack, **opts)
 
     def close(self):
         if self.h is not None:
@@ -413,6 +451,15 @@ class Graph:
 
     def device_bytes(self):
         return gc_device_bytes(self.h)
+
+    def tuning(self):
+        return gc_get_tuning(self.h)
+
+    def set_tuning(self, **bounds):
+        gc_set_tuning(self.h, **bounds)
+
+    def autotune(self, reps: int = 2):
+        return gc_autotune(self.h, reps)
 
     def trim(self):
         gc_trim(self.h)

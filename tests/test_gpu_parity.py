@@ -83,6 +83,105 @@ def test_static_planted_hub_and_clique(gcb):
         assert g.counts() == oracle.static_counts(rp, col, "literal")
 
 
+def _bipartite_hub_graph():
+    """A pivot with 90,000 wedges onto 300 endpoints: hub h (350 neighbours:
+    300 'a' vertices and 50 leaves), each 'a' joined to the same 300 'b'
+    vertices, plus a sparse background."""
+    n = 3000
+    keys = set(int(k) for k in gen.er_graph(n, 3000, 21))
+    h, A, B, L = 0, range(1, 301), range(301, 601), range(601, 651)
+    for a in A:
+        keys.add((h << 32) | a)
+        for b in B:
+            keys.add((a << 32) | b)
+    for x in L:
+        keys.add((h << 32) | x)
+    k = np.array(sorted(keys), dtype=np.uint64)
+    return n, k
+
+
+CHUNK_CASES = [
+    ("c2", dict(chunk_threshold=64)),
+    ("c2", dict(chunk_threshold=64, chunk_stage=1024)),
+    ("hub", dict(chunk_threshold=64)),
+    ("hub", dict(chunk_threshold=64, chunk_stage=4096)),
+    ("wide_ids", dict(chunk_threshold=64, chunk_stage=4096)),
+    ("wide_ids", dict(chunk_threshold=4096)),
+]
+
+
+def _chunk_graph(name):
+    if name == "c2":
+        return gen.workload_graph("c2")
+    if name == "hub":
+        return _bipartite_hub_graph()
+    # 120,000 ids: the chunked kernel's id range spans three chunks
+    return 120000, gen.chung_lu_graph(120000, 400000, 2.1, 3000.0, 22)
+
+
+@pytest.mark.parametrize("name,opts", CHUNK_CASES, ids=[f"{c[0]}-{'-'.join(map(str, c[1].values()))}"
+                                                        for c in CHUNK_CASES])
+def test_chunked_four_cycle_tier(gcb, name, opts):
+    """4-cycle pivots counted in shared memory over id-range chunks: with the
+    tier forced on most pivots, and with a staging area small enough to need
+    several chunk groups and single chunks counted during their own walk;
+    static counts and a batch equal the oracle."""
+    n, keys = _chunk_graph(name)
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.random_batch(n, keys, 300, 200, 23)
+    r = oracle.fdgc_step(rp, col, ins, dels, F0)
+    with open_graph(gcb, n, rp, col, **opts) as g:
+        assert g.counts() == F0
+        assert g.count_static() == F0
+        assert g.apply(ins, dels) == r["F"]
+        st = g.stats()
+        assert mod64(st["sums_a"]) == mod64(r["sums_a"]) and mod64(st["sums_b"]) == mod64(r["sums_b"])
+
+
+TUNINGS = {
+    "tri_all_merge": dict(tri_warp_max=1, tri_block_max=1),
+    "tri_all_block": dict(tri_warp_max=1, tri_block_max=512),
+    "tri_small_block": dict(tri_warp_max=8, tri_block_max=40),
+    "c4_warp_hash": dict(c4_reg_max=1, c4_warp_max=512, c4_block_max=512, c4_cta_max=512),
+    "c4_block_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=8192, c4_cta_max=8192),
+    "c4_cta_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=32768),
+    "c4_all_cluster": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=0),
+    "c4_all_chunk": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=1),
+}
+
+
+@pytest.mark.parametrize("tname", sorted(TUNINGS))
+@pytest.mark.parametrize("gname", ["c2", "hub"])
+def test_every_kernel_tier_alone(gcb, gname, tname):
+    """Bin boundaries move work between kernels, never change counts: with
+    each tier forced to take (almost) every root or pivot, the static count
+    and a batch equal the oracle."""
+    n, keys = _chunk_graph(gname)
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.random_batch(n, keys, 250, 250, 31)
+    r = oracle.fdgc_step(rp, col, ins, dels, F0)
+    with open_graph(gcb, n, rp, col) as g:
+        g.set_tuning(**TUNINGS[tname])
+        assert g.count_static() == F0
+        assert g.apply(ins, dels) == r["F"]
+        assert mod64(g.stats()["Ca"]) == mod64(r["Ca"])
+
+
+def test_autotune_keeps_counts(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.random_batch(n, keys, 500, 500, 32)
+    r = oracle.fdgc_step(rp, col, ins, dels, F0)
+    with open_graph(gcb, n, rp, col) as g:
+        best, ms = g.autotune(reps=1)
+        assert ms > 0 and best == g.tuning()
+        assert g.count_static() == F0
+        assert g.apply(ins, dels) == r["F"]
+
+
 @pytest.mark.parametrize("name", ["c1", "c2"])
 def test_static_workload_graphs(gcb, name):
     n, keys = gen.workload_graph(name)
