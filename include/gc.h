@@ -62,9 +62,7 @@ typedef struct {
     int32_t dense_cluster; /* CTAs per cluster of the heavy 4-cycle kernel: 0 auto, 8 or 16 */
     int32_t chunk_threshold; /* wedge bound above which a 4-cycle pivot is counted in shared memory
                                 over id-range chunks; <= 0: never (the cluster kernel takes them) */
-    int32_t chunk_stage;     /* wedge records staged per CTA by that kernel: 0 -> min(2^21, 2m + 1024),
-                                at least 1024; larger pivots take more walks */
-    int32_t reserved[4];
+    int32_t reserved[5];
 } gc_options;
 
 /* Per-batch record of the last gc_apply_batch* call. */

@@ -85,8 +85,7 @@ struct gc_graph {
     int dense_cluster_size = 8;
     Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
     int cta_groups = 0;
-    Buf<uint32_t> chunk_stages;          // staging of the chunked 4-cycle kernel (per CTA)
-    long long stage_cap = 0;
+    Buf<int32_t> chunk_table;            // run bounds of the chunked 4-cycle kernel
     Tuning tune = default_tuning();     // bin boundaries of the counting pass
     int32_t* bins = nullptr;             // NBINS * n work lists of the counting pass
     // captured batch graph and the shape it was captured for
@@ -364,6 +363,15 @@ static void trim_scratch(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
 }
 
+// Run bounds of the chunked 4-cycle kernel: one int per vertex and id-range
+// chunk, allocated when a tuning first enables that tier (never for vertex
+// counts whose table would be too large: the tier then stays off).
+static bool ensure_chunk_table(gc_graph* g) {
+    const long long te = c4_chunk_table_entries(std::max(g->n, 1));
+    if (te <= 0) return true;
+    return ensure(g, g->chunk_table, (size_t)te);
+}
+
 static int ensure_desc(gc_graph* g, long long words) {
     if (g->desc && g->desc_cap >= words) return GC_OK;
     long long nc = std::max<long long>(words + words / 4, 64);
@@ -413,8 +421,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     ca.cta_tables = g->cta_tables.p;
     ca.cta_table_words = 2 * C4_T3;
     ca.cta_groups = g->cta_groups;
-    ca.chunk_stages = g->chunk_stages.p;
-    ca.stage_cap = g->stage_cap;
+    ca.chunk_table = g->chunk_table.p;
     ca.tune = g->tune;
     ca.sms = g->sms;
     g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
@@ -856,7 +863,7 @@ static void destroy(gc_graph* g) {
     release(g, g->out_dev);
     release(g, g->dense);
     release(g, g->cta_tables);
-    release(g, g->chunk_stages);
+    release(g, g->chunk_table);
     dfree(g, g->bins);
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -997,11 +1004,7 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
     g->cta_groups = g->sms;
     if (!ensure(g, g->cta_tables, (size_t)g->cta_groups * 2 * C4_T3)) return nomem(g, "4-cycle hash tables");
-    // staging of the chunked 4-cycle kernel: a pivot's wedge records, up to
-    // 2^21 per CTA (larger pivots take several walks)
-    g->stage_cap = g->opt.chunk_stage > 0 ? std::max<long long>(g->opt.chunk_stage, 1024)
-                                          : std::min<long long>(1ll << 21, std::max<long long>(2 * m2 + 1024, 1 << 16));
-    if (!ensure(g, g->chunk_stages, (size_t)g->sms * (size_t)g->stage_cap)) return nomem(g, "4-cycle staging");
+    if (g->tune.c4_chunk_min < NEVER && !ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     CK(cudaMemsetAsync(g->cta_tables.p, 0, 8 * g->cta_tables.cap, s));
     return count_static(g, true, nullptr);
 }
@@ -1356,6 +1359,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     n.c4_block_max = t->c4_block_max;
     n.c4_cta_max = t->c4_cta_max;
     n.c4_chunk_min = t->c4_chunk_min == 0 ? NEVER : t->c4_chunk_min;
+    if (n.c4_chunk_min < NEVER && !ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     g->tune = n;
     return GC_OK;
 }
@@ -1386,14 +1390,17 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     int rc = time_static(g, reps, &cur_ms, ref);
     if (rc) return rc;
     // candidate values per boundary; coordinate descent, at most two sweeps
-    const long long cand[7][4] = {
-        {16, 32, -1, -1},                 // tri_warp_max
-        {128, 256, 512, -1},              // tri_block_max
-        {16, 32, -1, -1},                 // c4_reg_max
-        {128, 512, -1, -1},               // c4_warp_max
-        {2048, 8192, -1, -1},             // c4_block_max
-        {8192, 16384, 32768, -1},         // c4_cta_max (8192: tier unused)
-        {NEVER, 262144, 1048576, 4194304} // c4_chunk_min
+    // (a bound below the tier beneath it empties the tier; the chunked
+    // kernel only takes pivots above c4_cta_max, so lowering that one after
+    // c4_chunk_min opens the chunked tier to medium pivots)
+    const long long cand[7][6] = {
+        {16, 32, -1, -1, -1, -1},                          // tri_warp_max
+        {128, 256, 512, -1, -1, -1},                       // tri_block_max
+        {16, 32, -1, -1, -1, -1},                          // c4_reg_max
+        {128, 512, -1, -1, -1, -1},                        // c4_warp_max
+        {512, 2048, 8192, -1, -1, -1},                     // c4_block_max
+        {2048, 8192, 16384, 32768, -1, -1},                // c4_cta_max
+        {NEVER, 2048, 8192, 32768, 262144, 1048576}        // c4_chunk_min
     };
     auto field = [](Tuning& t, int i) -> long long {
         switch (i) {
@@ -1417,12 +1424,12 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
             default: t.c4_chunk_min = v; break;
         }
     };
-    const bool chunk_ok = g->chunk_stages.p && (long long)g->n <= c4_chunk_max_ids();
-    for (int sweep = 0; sweep < 2; sweep++) {
+    const bool chunk_ok = c4_chunk_table_entries(std::max(g->n, 1)) > 0 && ensure_chunk_table(g);
+    for (int sweep = 0; sweep < 3; sweep++) {
         bool moved = false;
-        for (int i = 0; i < 7; i++) {
+        for (int i = 6; i >= 0; i--) {
             if (i == 6 && !chunk_ok) continue;
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < 6; k++) {
                 const long long v = cand[i][k];
                 if (v < 0 || v == field(cur, i)) continue;
                 Tuning t = cur;

@@ -73,6 +73,18 @@ __device__ __forceinline__ void acc_add(Ctl* c, int slot, unsigned long long x) 
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c->acc[slot], x);
 }
 
+// index of id y in the sorted entries s[0..k), or -1 (the first probes of
+// all lanes hit the same entries, which shared memory broadcasts)
+__device__ __forceinline__ int find_pos(const uint32_t* s, int k, uint32_t y) {
+    int lo = 0, hi = k;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (vid(s[mid]) < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < k && vid(s[lo]) == y) ? lo : -1;
+}
+
 // largest q in [0, k) with pre[q] <= t (pre[0] = 0 <= t < pre[k])
 __device__ __forceinline__ int find_seg(const int* pre, int k, int t) {
     int lo = 0, hi = k;
@@ -163,17 +175,6 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
 
 // ---- triangles and 4-cliques -------------------------------------------------
 
-// Position of id y in the out-list through the shared hash table, or -1.
-__device__ __forceinline__ int hash_pos(const uint32_t* hk, const uint16_t* hp, int shift, uint32_t mask, uint32_t y) {
-    uint32_t h = (y * 0x9E3779B1u) >> shift;
-    for (;;) {
-        const uint32_t key = hk[h];
-        if (key == y) return hp[h];
-        if (key == 0xFFFFFFFFu) return -1;
-        h = (h + 1) & mask;
-    }
-}
-
 constexpr int TW = 8;  // warps per block of the warp-per-root kernel
 
 __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __restrict__ list,
@@ -186,8 +187,6 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
     __shared__ int sPre[TW][33];
     __shared__ uint32_t sRA[TW][32], sRB[TW][32];
     __shared__ unsigned long long sTq[TW][32];
-    __shared__ uint32_t sHk[TW][64];
-    __shared__ uint16_t sHp[TW][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cnt = c->nbin[BIN_TRI_WARP];
     unsigned long long ka = 0, kb = 0;
@@ -218,22 +217,13 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
         sRA[w][lane] = 0;
         sRB[w][lane] = 0;
         sTq[w][lane] = 0;
-        sHk[w][lane] = 0xFFFFFFFFu;
-        sHk[w][lane + 32] = 0xFFFFFFFFu;
-        __syncwarp();
-        if (lane < k) {  // id -> position, 64 slots for at most 32 distinct ids
-            const uint32_t y = vid(x);
-            uint32_t h = (y * 0x9E3779B1u) >> 26;
-            while (atomicCAS(&sHk[w][h], 0xFFFFFFFFu, y) != 0xFFFFFFFFu) h = (h + 1) & 63u;
-            sHp[w][h] = (uint16_t)lane;
-        }
         __syncwarp();
         int q = 0;
         for (int t = lane; t < total; t += 32) {
             while (q + 1 < k && sPre[w][q + 1] <= t) q++;
             long long slot = sNb[w][q] + (t - sPre[w][q]);
             uint32_t e = U_col[slot];
-            int p = hash_pos(sHk[w], sHp[w], 26, 63u, vid(e));
+            int p = find_pos(sX[w], k, vid(e));
             if (p < 0) continue;
             uint32_t f = sX[w][q] & sX[w][p] & e;
             unsigned long long iv = flag_inc(f);
@@ -259,17 +249,16 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
 }
 
 constexpr int TB_WORDS = TRI_KM / 32;
-constexpr int TB_HASH = 2 * TRI_KM;  // id -> position table of the out-list
 constexpr size_t tri_block_smem() {
     return (size_t)TRI_KM * 4 + (size_t)TRI_KM * 8 + (size_t)(TRI_KM + 8) * 4 + 2ull * TRI_KM * TB_WORDS * 4 +
-           (size_t)TRI_KM * 8 + (size_t)TB_HASH * 4 + (size_t)TB_HASH * 2;
+           (size_t)TRI_KM * 8;
 }
 size_t tri_block_smem_bytes() { return tri_block_smem(); }
 
 // Roots with 32 < k <= TRI_KM: one block per root.  The out-list X is held
-// in shared memory with an id -> position hash table; the candidates (every
-// entry of N+(v) up to max X, for v in X) are dealt in warp-contiguous runs
-// of 32, so a lane finds its row by stepping from the run's first row.
+// in shared memory; the candidates (every entry of N+(v) up to max X, for v
+// in X) are dealt in warp-contiguous runs of 32, so a lane finds its row by
+// stepping from the run's first row, and its position in X by binary search.
 __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __restrict__ list,
                                                   const long long* __restrict__ U_off,
                                                   const uint32_t* __restrict__ U_col,
@@ -282,8 +271,6 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
     int* sPre = (int*)(smem + (size_t)TRI_KM * 20);
     uint32_t* sRA = (uint32_t*)(smem + (size_t)TRI_KM * 24 + 32);
     uint32_t* sRB = sRA + TRI_KM * TB_WORDS;
-    uint32_t* sHk = sRB + TRI_KM * TB_WORDS;
-    uint16_t* sHp = (uint16_t*)(sHk + TB_HASH);
     __shared__ int s_idx;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
     const int cnt = c->nbin[BIN_TRI_BLOCK];
@@ -298,12 +285,7 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
         long long rb = U_off[u] + U_split[u];
         const int k = (int)(U_off[u + 1] - rb);
         const int W = (k + 31) >> 5;
-        int lg = 6;
-        while ((1 << lg) < 2 * k) lg++;
-        const uint32_t hmask = (1u << lg) - 1;
-        const int hshift = 32 - lg;
         const uint32_t xmax = vid(U_col[rb + k - 1]);
-        for (int t = tid; t < (1 << lg); t += blockDim.x) sHk[t] = 0xFFFFFFFFu;
         for (int t = tid; t < k; t += blockDim.x) {
             uint32_t x = U_col[rb + t];
             uint32_t v = vid(x);
@@ -318,12 +300,6 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
             sRB[t] = 0;
         }
         __syncthreads();
-        for (int t = tid; t < k; t += blockDim.x) {  // ids of an out-list are distinct
-            const uint32_t y = vid(sX[t]);
-            uint32_t h = (y * 0x9E3779B1u) >> hshift;
-            while (atomicCAS(&sHk[h], 0xFFFFFFFFu, y) != 0xFFFFFFFFu) h = (h + 1) & hmask;
-            sHp[h] = (uint16_t)t;
-        }
         if (warp == 0) {  // inclusive scan of sPre[1..k]
             int carry = 0;
             for (int b = 0; b < k; b += 32) {
@@ -347,7 +323,7 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
                 while (q + 1 < k && sPre[q + 1] <= t) q++;
                 const long long slot = sNb[q] + (t - sPre[q]);
                 const uint32_t e = U_col[slot];
-                const int p = hash_pos(sHk, sHp, hshift, hmask, vid(e));
+                const int p = find_pos(sX, k, vid(e));
                 if (p >= 0) {
                     const uint32_t f = sX[q] & sX[p] & e;
                     const unsigned long long iv = flag_inc(f);
@@ -853,255 +829,127 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
 // Heavy pivots, counters in shared memory.  Shared-memory atomics are about
 // twenty times faster than L2 or distributed-shared-memory atomics, but a
 // pivot's endpoints w range over [0, u), far more ids than shared memory
-// holds.  So the id range is cut into chunks of R ids (R counters fill the
-// shared array) and each chunk is counted on its own:
-//   A1  walk the pivot's wedges once, histogram of their chunks
-//   A2  walk again, scatter each wedge record (w | its G_a / G_b flags) into
-//       a staging area grouped by chunk (runs of equal chunks in a warp take
-//       one atomic)
-//   B   per chunk: one increment per record on the shared counters (the old
-//       value gives the C(c, 2) sum as in the other 4-cycle kernels), then
-//       clear the counters
-// When the pivot's records exceed the staging area, the chunks are taken in
-// groups that fit, one A2 walk per group; a single chunk larger than the
-// staging area is counted directly during its own walk.  Counters are packed
-// 16/16 bits (a/b) while every degree is below 2^16, else 32/32 in 64 bits
-// (half as many ids per chunk).
-constexpr int CH_SEG = 1024;       // lower neighbours per prefix segment
-constexpr int CH_MAXB = 2048;      // chunks per pivot (n <= CH_MAXB * CH_R64)
-constexpr int CH_BYTES = 196608;   // counter bytes
-constexpr int CH_R32 = CH_BYTES / 4;
-constexpr int CH_R64 = CH_BYTES / 8;
-constexpr int CH_UNROLL = 4;
+// holds.  So the id range is cut into chunks of CH_R ids (one chunk of
+// counters fills the shared array) and the pivot is counted chunk by chunk.
+// Every adjacency row is sorted, so the entries of row v inside chunk b are
+// one contiguous run [T[v][b], T[v][b+1]); the table T of these bounds is
+// built once per counting pass (k_chunk_bounds, one read of U).  For each
+// chunk, every warp takes lower neighbours 32 at a time, lays their runs
+// end to end (a warp prefix sum) and walks them with all lanes, one shared
+// atomic per wedge (the old value gives the C(c, 2) sum as in the other
+// 4-cycle kernels); then the counters are cleared.  Counters are packed
+// 16/16 bits (G_a / G_b) while every degree is below 2^16; with larger
+// degrees they are 32/32 bits in 64-bit words and each chunk is walked twice,
+// one half of its ids at a time.
+constexpr int CH_BYTES = 196608;        // counter bytes
+constexpr int CH_R = CH_BYTES / 4;      // ids per chunk (49,152)
+constexpr int CH_THREADS = 1024;
+constexpr long long CH_TABLE_MAX = 2ll << 30;  // table entries the library will allocate
 
-size_t c4_chunk_smem_bytes() {
-    return (size_t)CH_BYTES + sizeof(int) * (CH_MAXB + 1) + sizeof(int) * (CH_SEG + 1) + sizeof(long long) * CH_SEG +
-           sizeof(uint32_t) * CH_SEG;
+size_t c4_chunk_smem_bytes() { return (size_t)CH_BYTES + (CH_THREADS / 32) * 32 * (4 + 8 + 4); }
+int c4_chunk_width(long long n) { return (int)((n + CH_R - 1) / CH_R) + 1; }
+long long c4_chunk_table_entries(long long n) {
+    const long long e = n * (long long)c4_chunk_width(n);
+    return e <= CH_TABLE_MAX ? e : -1;
 }
 
-long long c4_chunk_max_ids() { return (long long)CH_MAXB * CH_R64; }
-
-// Walk every wedge u-v-w (v lower neighbour of u, w < u) of the pivot;
-// fn(w, flags, valid) is called by all 32 lanes of a warp together.
-template <class Fn>
-__device__ __forceinline__ void chunk_walk(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
-                                           long long rb, int nlow, uint32_t u, int* s_pre, long long* s_vb,
-                                           uint32_t* s_fv, int* s_tot, Fn fn) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    for (int s0 = 0; s0 < nlow; s0 += CH_SEG) {
-        const int ns = min(CH_SEG, nlow - s0);
-        wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, s_tot);
-        const long long total = *s_tot;
-        const long long wstep = (long long)NW * 32 * CH_UNROLL;
-        for (long long base = (long long)warp * 32 * CH_UNROLL; base < total; base += wstep) {
-            uint32_t e[CH_UNROLL], f[CH_UNROLL];
-            int j = find_seg(s_pre, ns, (int)base);
-#pragma unroll
-            for (int r = 0; r < CH_UNROLL; r++) {
-                long long i = base + r * 32 + lane;
-                e[r] = 0xFFFFFFFFu;
-                f[r] = 0;
-                if (i < total) {
-                    while (j + 1 < ns && s_pre[j + 1] <= i) j++;
-                    e[r] = U_col[s_vb[j] + (i - s_pre[j])];
-                    f[r] = s_fv[j];
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < CH_UNROLL; r++) {
-                const uint32_t w = vid(e[r]);
-                fn(w, f[r] & e[r] & (FLAG_A | FLAG_B), w < u);
-            }
+// T[v][b] = first position in row v whose id is >= b * CH_R, b = 0 .. TW-1.
+// A warp per row: a position starts chunk b when the ids before and at it
+// straddle b * CH_R; chunks after the last entry start at the row's end.
+__global__ void k_chunk_bounds(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                               const uint32_t* __restrict__ U_col, int32_t* __restrict__ T, int TW) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const int32_t v = wlist[i];
+        const long long rb = U_off[v];
+        const int d = (int)(U_off[v + 1] - rb);
+        int32_t* t = T + (size_t)v * TW;
+        for (int p = lane; p < d; p += 32) {
+            const int cb = (int)(vid(U_col[rb + p]) / CH_R);
+            const int ca = p == 0 ? -1 : (int)(vid(U_col[rb + p - 1]) / CH_R);
+            for (int b = ca + 1; b <= cb; b++) t[b] = p;
         }
-        __syncthreads();  // the next segment reuses the prefix arrays
+        const int last = d == 0 ? -1 : (int)(vid(U_col[rb + d - 1]) / CH_R);
+        for (int b = last + 1 + lane; b < TW; b += 32) t[b] = d;
     }
-}
-
-// Runs of equal keys among the 32 lanes (consecutive lanes): head lane of
-// each run, its length, and for every lane the head of its run.
-struct Runs {
-    bool head;
-    int len;
-    int myhead;
-};
-__device__ __forceinline__ Runs lane_runs(int key, int lane) {
-    const int prev = __shfl_up_sync(FULL, key, 1);
-    Runs r;
-    r.head = lane == 0 || key != prev;
-    const unsigned heads = __ballot_sync(FULL, r.head);
-    const unsigned le = (2u << lane) - 1u;  // lanes <= lane (all lanes for lane 31)
-    const unsigned after = heads & ~le;
-    r.len = (after ? __ffs(after) - 1 : 32) - lane;
-    r.myhead = 31 - __clz(heads & le);
-    return r;
 }
 
 template <bool WIDE>
-__device__ __forceinline__ void chunk_count_pivot(Ctl* c, const long long* __restrict__ U_off,
-                                                  const uint32_t* __restrict__ U_col, int32_t u, long long rb,
-                                                  int nlow, uint32_t* __restrict__ stage, long long stage_cap,
-                                                  unsigned char* smem, unsigned long long& qa,
-                                                  unsigned long long& qb, unsigned long long& wedges) {
-    constexpr int R = WIDE ? CH_R64 : CH_R32;
+__device__ __forceinline__ void chunk_pass(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
+                                           const int32_t* __restrict__ T, int TW, int32_t u, long long rb, int nlow,
+                                           int b, uint32_t lo_id, uint32_t hi_id, unsigned char* smem,
+                                           int* w_pre, long long* w_vb, uint32_t* w_fv, unsigned long long& qa,
+                                           unsigned long long& qb, unsigned long long& wedges, bool count_wedges) {
     uint32_t* cnt32 = (uint32_t*)smem;
     unsigned long long* cnt64 = (unsigned long long*)smem;
-    int* pos = (int*)(smem + CH_BYTES);
-    int* s_pre = pos + CH_MAXB + 1;
-    long long* s_vb = (long long*)(s_pre + CH_SEG + 1);
-    uint32_t* s_fv = (uint32_t*)(s_vb + CH_SEG);
-    __shared__ int s_tot;
-    __shared__ int s_g1;
-    __shared__ long long s_grec;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int nch = (int)(((long long)u + R - 1) / R);
-
-    auto count_one = [&](uint32_t w, uint32_t fl, uint32_t base_id) {
-        if (WIDE) {
-            const unsigned long long inc = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
-            const unsigned long long old = atomicAdd(&cnt64[w - base_id], inc);
-            if (fl & FLAG_A) qa += old >> 32;
-            if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
-        } else {
-            const uint32_t old = atomicAdd(&cnt32[w - base_id], flag_inc16(fl));
-            if (fl & FLAG_A) qa += old >> 16;
-            if (fl & FLAG_B) qb += old & 0xFFFFu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    int* pre = w_pre + warp * 32;
+    long long* vbs = w_vb + warp * 32;
+    uint32_t* fvs = w_fv + warp * 32;
+    for (int j0 = warp * 32; j0 < nlow; j0 += NW * 32) {
+        const int j = j0 + lane;
+        int len = 0;
+        if (j < nlow) {
+            const uint32_t fv = U_col[rb + j];
+            const uint32_t v = vid(fv);
+            const int32_t* t = T + (size_t)v * TW + b;
+            const int lo = t[0];
+            len = t[1] - lo;
+            vbs[lane] = U_off[v] + lo;
+            fvs[lane] = fv;
         }
-    };
-    auto clear_all = [&]() {
-        uint4* c4 = (uint4*)smem;
-        for (int i = tid; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
-    };
-
-    if (nch <= 2) {
-        // few chunks: count each during its own walk, no staging
-        for (int b = 0; b < nch; b++) {
-            const uint32_t base_id = (uint32_t)b * R;
-            chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
-                       [&](uint32_t w, uint32_t fl, bool lt) {
-                           if (lt && b == 0) wedges++;
-                           if (lt && fl && (nch == 1 || (int)(w / R) == b)) count_one(w, fl, base_id);
-                       });
-            // clear the ids this chunk can hold (16-byte granules)
-            const long long ids = min((long long)R, (long long)u - base_id);
-            const long long granules = (ids * (WIDE ? 8 : 4) + 15) / 16;
-            uint4* c4 = (uint4*)smem;
-            for (long long i = tid; i < granules; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
-            __syncthreads();
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
         }
-        return;
-    }
-
-    // A1: histogram of the chunks (and the work counter)
-    for (int b = tid; b < nch; b += blockDim.x) pos[b] = 0;
-    __syncthreads();
-    chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
-               [&](uint32_t w, uint32_t fl, bool lt) {
-                   if (lt) wedges++;
-                   const int key = (lt && fl) ? (int)(w / R) : -1;
-                   const Runs r = lane_runs(key, lane);
-                   if (r.head && key >= 0) atomicAdd(&pos[key], r.len);
-               });
-    // groups of chunks whose records fit the staging area
-    int g0 = 0;
-    while (g0 < nch) {
-        if (tid == 0) {
-            long long sum = 0;
-            int g1 = g0;
-            while (g1 < nch && sum + pos[g1] <= stage_cap) sum += pos[g1++];
-            if (g1 == g0) {
-                sum = pos[g0];
-                g1 = g0 + 1;  // one chunk beyond the staging area: counted directly
-            }
-            s_g1 = g1;
-            s_grec = sum;
-        }
-        __syncthreads();
-        const int g1 = s_g1;
-        const long long grec = s_grec;
-        if (grec == 0) {
-            g0 = g1;
-            __syncthreads();
-            continue;
-        }
-        if (grec > stage_cap) {
-            // direct: one chunk, counted during its own walk
-            const uint32_t base_id = (uint32_t)g0 * R;
-            chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
-                       [&](uint32_t w, uint32_t fl, bool lt) {
-                           if (lt && fl && (int)(w / R) == g0) count_one(w, fl, base_id);
-                       });
-            clear_all();
-            __syncthreads();
-            g0 = g1;
-            continue;
-        }
-        // exclusive offsets of the group's chunks, then A2 scatters into them
-        const int nk = g1 - g0;
-        __syncthreads();
-        if (tid == 0) {
-            int run = 0;
-            for (int b = g0; b < g1; b++) {
-                const int x = pos[b];
-                pos[b] = run;
-                run += x;
-            }
-        }
-        __syncthreads();
-        chunk_walk(U_off, U_col, rb, nlow, (uint32_t)u, s_pre, s_vb, s_fv, &s_tot,
-                   [&](uint32_t w, uint32_t fl, bool lt) {
-                       const int b = (lt && fl) ? (int)(w / R) : -1;
-                       const int key = (b >= g0 && b < g1) ? b : -1;
-                       const Runs r = lane_runs(key, lane);
-                       int at = 0;
-                       if (r.head && key >= 0) at = atomicAdd(&pos[key], r.len);
-                       at = __shfl_sync(FULL, at, r.myhead);
-                       if (key >= 0) stage[at + (lane - r.myhead)] = w | fl;
-                   });
-        // B: after A2, pos[b] is the end of chunk b and the start of chunk b+1
-        for (int k = 0; k < nk; k++) {
-            const int b = g0 + k;
-            const int st = k == 0 ? 0 : pos[b - 1];
-            const int en = pos[b];
-            if (en == st) continue;
-            const uint32_t base_id = (uint32_t)b * R;
-            for (int i = st + tid; i < en; i += blockDim.x) {
-                const uint32_t rec = __ldcg(&stage[i]);
-                count_one(vid(rec), rec & (FLAG_A | FLAG_B), base_id);
-            }
-            __syncthreads();
-            if ((long long)(en - st) * 16 > R) {
-                clear_all();
+        pre[lane] = inc - len;  // exclusive
+        const int total = __shfl_sync(FULL, inc, 31);
+        __syncwarp();
+        int r = 0;
+        for (int t = lane; t < total; t += 32) {
+            while (r < 31 && pre[r + 1] <= t) r++;
+            const uint32_t e = U_col[vbs[r] + (t - pre[r])];
+            const uint32_t w = vid(e);
+            if (w >= (uint32_t)u) continue;  // the pivot's own chunk holds ids above it too
+            if (count_wedges) wedges++;
+            if (w < lo_id || w >= hi_id) continue;
+            const uint32_t fl = fvs[r] & e & (FLAG_A | FLAG_B);
+            if (!fl) continue;
+            if (WIDE) {
+                const unsigned long long inc2 = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
+                const unsigned long long old = atomicAdd(&cnt64[w - lo_id], inc2);
+                if (fl & FLAG_A) qa += old >> 32;
+                if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
             } else {
-                for (int i = st + tid; i < en; i += blockDim.x) {
-                    const uint32_t w = vid(__ldcg(&stage[i]));
-                    if (WIDE) cnt64[w - base_id] = 0ull;
-                    else cnt32[w - base_id] = 0u;
-                }
+                const uint32_t old = atomicAdd(&cnt32[w - lo_id], flag_inc16(fl));
+                if (fl & FLAG_A) qa += old >> 16;
+                if (fl & FLAG_B) qb += old & 0xFFFFu;
             }
-            __syncthreads();
         }
-        // the histogram of later groups is still in pos[g1 ..]
-        g0 = g1;
-        __syncthreads();
+        __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_chunk(Ctl* c, const int32_t* __restrict__ list,
-                                                              const long long* __restrict__ U_off,
-                                                              const uint32_t* __restrict__ U_col,
-                                                              const int32_t* __restrict__ U_split,
-                                                              uint32_t* __restrict__ stages, long long stage_cap) {
+__global__ void __launch_bounds__(CH_THREADS, 1) k_c4_chunk(Ctl* c, const int32_t* __restrict__ list,
+                                                        const long long* __restrict__ U_off,
+                                                        const uint32_t* __restrict__ U_col,
+                                                        const int32_t* __restrict__ U_split,
+                                                        const int32_t* __restrict__ T, int TW) {
     extern __shared__ __align__(16) unsigned char ch_smem[];
+    int* w_pre = (int*)(ch_smem + CH_BYTES);
+    long long* w_vb = (long long*)(w_pre + CH_THREADS);
+    uint32_t* w_fv = (uint32_t*)(w_vb + CH_THREADS);
     __shared__ int s_idx;
-    uint32_t* stage = stages + (size_t)blockIdx.x * (size_t)stage_cap;
     const bool wide = c->maxdeg >= 65536;
     const int cnt = c->nbin[BIN_C4_CHUNK];
     unsigned long long qa = 0, qb = 0, wedges = 0;
-    // counters start at zero and every chunk leaves them at zero
-    {
-        uint4* c4 = (uint4*)ch_smem;
-        for (int i = threadIdx.x; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
-    }
+    uint4* c4 = (uint4*)ch_smem;
+    for (int i = threadIdx.x; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
     for (;;) {
         if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[5], 1u);
         __syncthreads();
@@ -1111,8 +959,25 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_chunk(Ctl* c, const 
         const int32_t u = list[idx];
         const long long rb = U_off[u];
         const int nlow = U_split[u];
-        if (wide) chunk_count_pivot<true>(c, U_off, U_col, u, rb, nlow, stage, stage_cap, ch_smem, qa, qb, wedges);
-        else chunk_count_pivot<false>(c, U_off, U_col, u, rb, nlow, stage, stage_cap, ch_smem, qa, qb, wedges);
+        const int nch = (int)(((long long)u + CH_R - 1) / CH_R);
+        for (int b = 0; b < nch; b++) {
+            const int halves = wide ? 2 : 1;
+            for (int h = 0; h < halves; h++) {
+                const uint32_t span = wide ? CH_R / 2 : CH_R;
+                const uint32_t lo_id = (uint32_t)b * CH_R + h * span;
+                const uint32_t hi_id = min(lo_id + span, (uint32_t)u);
+                if (lo_id >= hi_id) continue;
+                if (wide) chunk_pass<true>(U_off, U_col, T, TW, u, rb, nlow, b, lo_id, hi_id, ch_smem, w_pre, w_vb,
+                                           w_fv, qa, qb, wedges, h == 0);
+                else chunk_pass<false>(U_off, U_col, T, TW, u, rb, nlow, b, lo_id, hi_id, ch_smem, w_pre, w_vb,
+                                       w_fv, qa, qb, wedges, true);
+                __syncthreads();
+                // clear the counters this chunk used (16-byte granules)
+                const long long granules = ((long long)(hi_id - lo_id) * (wide ? 8 : 4) + 15) / 16;
+                for (long long i = threadIdx.x; i < granules; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
+                __syncthreads();
+            }
+        }
     }
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
@@ -1366,7 +1231,7 @@ Tuning effective_tuning(const CountArgs& a) {
     t.c4_warp_max = std::max(t.c4_reg_max, std::min(t.c4_warp_max, C4_T1));
     t.c4_block_max = std::max(t.c4_warp_max, std::min(t.c4_block_max, C4_T2));
     t.c4_cta_max = std::max<long long>(t.c4_block_max, std::min<long long>(t.c4_cta_max, a.cta_table_words / 2));
-    if (!a.chunk_stages || a.n_alloc > c4_chunk_max_ids() || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
+    if (!a.chunk_table || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
     t.c4_chunk_min = std::max<long long>(t.c4_chunk_min, t.c4_cta_max);
     return t;
 }
@@ -1413,9 +1278,11 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                                                         a.cta_tables, a.cta_table_words);
     nl += 5;
     if (t.c4_chunk_min < NEVER) {
-        k_c4_chunk<<<sms, C4_DENSE_THREADS, c4_chunk_smem_bytes(), s>>>(
-            a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col, a.U_split, a.chunk_stages, a.stage_cap);
-        nl++;
+        const int TW = c4_chunk_width(a.n_alloc);
+        k_chunk_bounds<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.chunk_table, TW);
+        k_c4_chunk<<<sms, CH_THREADS, c4_chunk_smem_bytes(), s>>>(a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col,
+                                                                   a.U_split, a.chunk_table, TW);
+        nl += 2;
     }
     if (ev_end) cudaEventRecord(ev_end, s);
     k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);

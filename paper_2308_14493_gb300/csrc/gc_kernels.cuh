@@ -80,8 +80,7 @@ struct CountArgs {
     unsigned long long* cta_tables; // cta_groups * cta_table_words zeroed words
     long long cta_table_words;      // power of two; pivots up to half of it use the hash tier
     int cta_groups;                 // CTAs of the medium 4-cycle kernel (one table each)
-    uint32_t* chunk_stages;         // sms * stage_cap records of the chunked 4-cycle kernel
-    long long stage_cap;            // records per CTA
+    int32_t* chunk_table;           // n_alloc * c4_chunk_width(n_alloc) run bounds of the chunked 4-cycle kernel
     Tuning tune;                    // bin boundaries (clamped to the capacities)
     int sms;
 };
@@ -89,7 +88,8 @@ Tuning effective_tuning(const CountArgs& a);
 // Dynamic shared-memory limits of the counting kernels (once per device).
 void count_setup_attributes();
 size_t c4_chunk_smem_bytes();
-long long c4_chunk_max_ids();   // the chunked 4-cycle kernel handles vertex ids below this
+int c4_chunk_width(long long n);                 // id-range chunks + 1
+long long c4_chunk_table_entries(long long n);   // entries of the run-bound table, -1 if too large
 // Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
 // 16 if the device can co-schedule it, else 8) and the number of clusters.
 int dense_cluster_plan(int want, int sms, int* size_out);

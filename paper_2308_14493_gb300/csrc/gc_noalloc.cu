@@ -216,8 +216,7 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     ca.dense_cluster_size = 8;
     ca.cta_tables = cta_tables;
     ca.cta_table_words = NA_TABLE_WORDS;
-    ca.chunk_stages = nullptr;  // no chunked 4-cycle tier in the fixed scratch
-    ca.stage_cap = 0;
+    ca.chunk_table = nullptr;  // no chunked 4-cycle tier in the fixed scratch
     ca.tune = default_tuning();
     ca.cta_groups = NA_CTA_GROUPS;
     ca.sms = sms;

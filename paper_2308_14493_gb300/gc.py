@@ -31,7 +31,7 @@ class gc_options(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
                 ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("chunk_threshold", ctypes.c_int32),
-                ("chunk_stage", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class gc_stats(ctypes.Structure):
@@ -158,7 +158,7 @@ def _pairs(p):
 
 
 def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0,
-            chunk_threshold: int = 0, dense_cluster: int = 0, chunk_stage: int = 0):
+            chunk_threshold: int = 0, dense_cluster: int = 0):
     """Open a graph from a symmetric CSR; returns an opaque handle."""
     lib = load()
     rp = _i32(row_ptr)
@@ -170,7 +170,6 @@ def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, str
     opt.stream = stream or None
     opt.chunk_threshold = chunk_threshold
     opt.dense_cluster = dense_cluster
-    opt.chunk_stage = chunk_stage
     h = ctypes.c_void_p()
     rc = lib.gc_open(int(n), _ptr(rp), _ptr(c), ctypes.byref(opt), ctypes.byref(h))
     _check(rc, None)

@@ -33,11 +33,17 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="pick the bin boundaries first")
+    ap.add_argument("--chunk-threshold", type=int, default=0,
+                    help="wedge bound above which 4-cycle pivots use the chunked shared-memory kernel")
     a = ap.parse_args()
     keys = gen.chung_lu_graph(a.n, a.m, a.gamma, a.dmax, a.seed)
     rp, col = gen.csr_from_keys(a.n, keys)
-    with gcb.Graph(a.n, rp, col) as g:
+    with gcb.Graph(a.n, rp, col, chunk_threshold=a.chunk_threshold) as g:
         print(json.dumps({"open": g.stats()["ms_stage"]}), flush=True)
+        if a.autotune:
+            best, ms = g.autotune(reps=2)
+            print(json.dumps({"autotune_ms": ms, "tuning": best}), flush=True)
         if a.batch:
             for ins, dels in gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1):
                 g.apply(ins, dels)

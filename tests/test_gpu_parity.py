@@ -102,10 +102,8 @@ def _bipartite_hub_graph():
 
 CHUNK_CASES = [
     ("c2", dict(chunk_threshold=64)),
-    ("c2", dict(chunk_threshold=64, chunk_stage=1024)),
     ("hub", dict(chunk_threshold=64)),
-    ("hub", dict(chunk_threshold=64, chunk_stage=4096)),
-    ("wide_ids", dict(chunk_threshold=64, chunk_stage=4096)),
+    ("wide_ids", dict(chunk_threshold=64)),
     ("wide_ids", dict(chunk_threshold=4096)),
 ]
 
@@ -122,10 +120,9 @@ def _chunk_graph(name):
 @pytest.mark.parametrize("name,opts", CHUNK_CASES, ids=[f"{c[0]}-{'-'.join(map(str, c[1].values()))}"
                                                         for c in CHUNK_CASES])
 def test_chunked_four_cycle_tier(gcb, name, opts):
-    """4-cycle pivots counted in shared memory over id-range chunks: with the
-    tier forced on most pivots, and with a staging area small enough to need
-    several chunk groups and single chunks counted during their own walk;
-    static counts and a batch equal the oracle."""
+    """4-cycle pivots counted in shared memory over id-range chunks (three
+    chunks on the 120,000-vertex graph), with the tier taking every pivot
+    above the hash tiers; static counts and a batch equal the oracle."""
     n, keys = _chunk_graph(name)
     rp, col = gen.csr_from_keys(n, keys)
     F0 = oracle.static_counts(rp, col)
