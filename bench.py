@@ -281,13 +281,15 @@ def pack_batches(batches):
     return np.ascontiguousarray(pairs), np.asarray(desc, np.int64).reshape(-1, 4)
 
 
-def run_batched(gcb, torch, n, rp, col, batches, warmup, stream, flush, independent=False):
+def run_batched(gcb, torch, n, rp, col, batches, warmup, stream, flush, independent=False, tuning=None):
     """Batched form: the timed batches in ONE gc_apply_batches_device call
     (one captured CUDA graph replayed per batch, sizes read on the device),
     pairs resident in HBM.  Device time = CUDA events on the library's stream
     around the call; L2 is flushed before the call, not between the batches
     inside it.  Returns (seconds, raw updates, outputs, launches)."""
     h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    if tuning:
+        gcb.gc_set_tuning(h, **tuning)
     pairs, desc = pack_batches(batches)
     dp = torch.from_numpy(pairs).cuda()
     torch.cuda.synchronize()
@@ -307,10 +309,12 @@ def run_batched(gcb, torch, n, rp, col, batches, warmup, stream, flush, independ
     return e0.elapsed_time(e1) / 1e3, raw, outs, st["launches"]
 
 
-def run_what_if(gcb, torch, n, rp, col, batches, stream, flush):
+def run_what_if(gcb, torch, n, rp, col, batches, stream, flush, tuning=None):
     """Plain form of independent batches: one gc_count_batch_device call per
     batch against the same snapshot, L2 flushed between calls."""
     h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    if tuning:
+        gcb.gc_set_tuning(h, **tuning)
     dev = [(torch.from_numpy(np.ascontiguousarray(i)).cuda(), torch.from_numpy(np.ascontiguousarray(d)).cuda())
            for i, d in batches]
     torch.cuda.synchronize()
@@ -375,15 +379,24 @@ def c4_block(gcb, torch, stream, flush, peak, peak_kind):
     rp, col = gen.csr_from_keys(n, keys)
     sizes = gen.log_uniform_sizes(64, 10, 50000, 4)
     batches = gen.batch_stream(n, keys, sizes, 0.5, 4, sequential=False)
-    ms, outs_p, edges, launches_p = run_what_if(gcb, torch, n, rp, col, batches, stream, flush)
-    secs, raw, outs_b, launches_b = run_batched(gcb, torch, n, rp, col, batches, 0, stream, flush, independent=True)
+    # bin boundaries picked once for this graph by the autotuner (static
+    # counts under candidate boundaries), then used by both forms
+    t0 = time.perf_counter()
+    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    tuning, tuned_ms = gcb.gc_autotune(h, 2)
+    gcb.gc_close(h)
+    t_tune = time.perf_counter() - t0
+    ms, outs_p, edges, launches_p = run_what_if(gcb, torch, n, rp, col, batches, stream, flush, tuning)
+    secs, raw, outs_b, launches_b = run_batched(gcb, torch, n, rp, col, batches, 0, stream, flush, independent=True,
+                                                tuning=tuning)
     tot = sum(ms) / 1e3
     return {"workload": WORKLOADS_DESC_C4, "batches": len(batches), "updates": raw,
             "plain": {"value": edges / tot, "p50_ms": pct(ms, 0.5), "p99_ms": pct(ms, 0.99),
                       "launches": launches_p},
             "batched": {"value": edges / secs, "ms_total": 1e3 * secs, "launches": launches_b},
             "batched_over_plain": tot / secs, "counts_equal": outs_p == outs_b,
-            "normalised_equals_raw": edges == raw}
+            "normalised_equals_raw": edges == raw,
+            "autotune": {"tuning": tuning, "static_count_ms": tuned_ms, "seconds_with_open": t_tune}}
 
 
 def gpu_arm(args):
@@ -523,6 +536,9 @@ def serve_arm(args):
     R = args.requests
     reqs = c5_requests(graphs, 3 * R, 5)
     handles = [gcb.Graph(n, *gen.csr_from_keys(n, keys)) for n, keys in graphs]
+    t0 = time.perf_counter()
+    tunings = [h.autotune(reps=1)[0] for h in handles]
+    t_tune = time.perf_counter() - t0
     torch.cuda.synchronize()
 
     # warm-up: one small batch per graph
@@ -578,7 +594,8 @@ def serve_arm(args):
                    "l2": "graphs of 1M..69M edges; the larger ones exceed L2"},
         "plain": plain, "served_saturated": sat, "served_poisson_0.8x": poi,
         "served_over_plain": sat["value"] / plain["value"],
-        "generation_s": t_gen, "clocks": clk.summary(),
+        "generation_s": t_gen, "autotune_s": t_tune,
+        "autotuned_chunk_tier": sum(1 for t in tunings if t["c4_chunk_min"]), "clocks": clk.summary(),
     }
     for h in handles:
         h.close()

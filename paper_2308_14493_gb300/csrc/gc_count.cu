@@ -844,6 +844,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
 constexpr int CH_BYTES = 196608;        // counter bytes
 constexpr int CH_R = CH_BYTES / 4;      // ids per chunk (49,152)
 constexpr int CH_THREADS = 1024;
+constexpr int CH_UNROLL = 4;
 constexpr long long CH_TABLE_MAX = 2ll << 30;  // table entries the library will allocate
 
 size_t c4_chunk_smem_bytes() { return (size_t)CH_BYTES + (CH_THREADS / 32) * 32 * (4 + 8 + 4); }
@@ -911,24 +912,38 @@ __device__ __forceinline__ void chunk_pass(const long long* __restrict__ U_off, 
         const int total = __shfl_sync(FULL, inc, 31);
         __syncwarp();
         int r = 0;
-        for (int t = lane; t < total; t += 32) {
-            while (r < 31 && pre[r + 1] <= t) r++;
-            const uint32_t e = U_col[vbs[r] + (t - pre[r])];
-            const uint32_t w = vid(e);
-            if (w >= (uint32_t)u) continue;  // the pivot's own chunk holds ids above it too
-            if (count_wedges) wedges++;
-            if (w < lo_id || w >= hi_id) continue;
-            const uint32_t fl = fvs[r] & e & (FLAG_A | FLAG_B);
-            if (!fl) continue;
-            if (WIDE) {
-                const unsigned long long inc2 = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
-                const unsigned long long old = atomicAdd(&cnt64[w - lo_id], inc2);
-                if (fl & FLAG_A) qa += old >> 32;
-                if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
-            } else {
-                const uint32_t old = atomicAdd(&cnt32[w - lo_id], flag_inc16(fl));
-                if (fl & FLAG_A) qa += old >> 16;
-                if (fl & FLAG_B) qb += old & 0xFFFFu;
+        for (int t0 = 0; t0 < total; t0 += 32 * CH_UNROLL) {
+            uint32_t ev[CH_UNROLL], fr[CH_UNROLL];
+#pragma unroll
+            for (int k = 0; k < CH_UNROLL; k++) {  // independent loads in flight
+                const int t = t0 + k * 32 + lane;
+                ev[k] = 0xFFFFFFFFu;
+                fr[k] = 0;
+                if (t < total) {
+                    while (r < 31 && pre[r + 1] <= t) r++;
+                    ev[k] = U_col[vbs[r] + (t - pre[r])];
+                    fr[k] = fvs[r];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CH_UNROLL; k++) {
+                const uint32_t e = ev[k];
+                const uint32_t w = vid(e);
+                if (w >= (uint32_t)u) continue;  // the pivot's own chunk holds ids above it too
+                if (count_wedges) wedges++;
+                if (w < lo_id || w >= hi_id) continue;
+                const uint32_t fl = fr[k] & e & (FLAG_A | FLAG_B);
+                if (!fl) continue;
+                if (WIDE) {
+                    const unsigned long long inc2 = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
+                    const unsigned long long old = atomicAdd(&cnt64[w - lo_id], inc2);
+                    if (fl & FLAG_A) qa += old >> 32;
+                    if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
+                } else {
+                    const uint32_t old = atomicAdd(&cnt32[w - lo_id], flag_inc16(fl));
+                    if (fl & FLAG_A) qa += old >> 16;
+                    if (fl & FLAG_B) qb += old & 0xFFFFu;
+                }
             }
         }
         __syncwarp();
