@@ -498,12 +498,15 @@ def gpu_arm(args):
 
 # ------------------------------------------------------------ serving arm --
 
-def c5_requests(graphs, count, seed):
+def c5_requests(graphs, count, seed, pair_seed=None):
     """Requests of the serving workload: sizes log-uniform in 100..100,000,
     70% insertions, routed uniformly over the graphs; each batch drawn
-    against its graph's initial edge set (later no-ops are normalised away)."""
+    against its graph's initial edge set (later no-ops are normalised away).
+    Sizes and routing come from `seed`, the pairs from `pair_seed`, so
+    phases with one `seed` carry the same work."""
     sizes = gen.log_uniform_sizes(count, 100, 100000, seed)
     route = (gen.uniform01(seed + 1, 0, count) * len(graphs)).astype(np.int64)
+    seed = seed if pair_seed is None else pair_seed
     per = {gi: [s for s, r in zip(sizes, route) if r == gi] for gi in range(len(graphs))}
     made = {gi: (gen.batch_stream(graphs[gi][0], graphs[gi][1], per[gi], 0.7, seed + 10 + gi, sequential=False)
                  if per[gi] else []) for gi in per}
@@ -534,7 +537,8 @@ def serve_arm(args):
     graphs = [gen.workload_graph(p) for p in params]
     t_gen = time.perf_counter() - t0
     R = args.requests
-    reqs = c5_requests(graphs, 3 * R, 5)
+    # three phases with the same request sizes and routing, fresh pairs each
+    reqs = c5_requests(graphs, R, 5, 50) + c5_requests(graphs, R, 5, 60) + c5_requests(graphs, R, 5, 70)
     handles = [gcb.Graph(n, *gen.csr_from_keys(n, keys)) for n, keys in graphs]
     t0 = time.perf_counter()
     tunings = [h.autotune(reps=1)[0] for h in handles]
