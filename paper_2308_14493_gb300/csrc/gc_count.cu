@@ -714,6 +714,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                                                                 const long long* __restrict__ U_off,
                                                                 const uint32_t* __restrict__ U_col,
                                                                 const int32_t* __restrict__ U_split,
+                                                                const long long* __restrict__ U_wt,
                                                                 unsigned long long* __restrict__ arrays, int n) {
     int rank = 0, ncta = 1;
     if constexpr (CLUSTER) {
@@ -756,11 +757,46 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
         const int32_t u = list[idx];
         const long long rb = U_off[u];
         const int nlow = U_split[u];
+        // A pivot with many wedges for its id range (w~ > u / 8) increments
+        // without taking old values (an L2 reduction costs a quarter of an
+        // atomic that returns), then sweeps the counters of [0, u) once,
+        // coalesced: each c_w gives C(c_w, 2) and is cleared.  Smaller
+        // pivots take old values and clear by walking their wedges again.
+        const bool sweep = U_wt[u] * 8 > (long long)u;
         long long wall = 0;  // wedge entries of the pivot (all rows, any id)
         for (int pass = 0; pass < 2; pass++) {
-            // pass 0: increments; pass 1: clear by walking (only for small pivots)
+            // pass 0: increments; pass 1: sweep, or clear by walking
             if (pass == 1) {
                 group_sync<CLUSTER>();
+                if (sweep) {
+                    if (wide) {
+                        for (long long w = g; w < u; w += T) {
+                            const unsigned long long x = __ldcg(&a64[w]);
+                            if (x) {
+                                qa += choose2(x >> 32);
+                                qb += choose2(x & 0xFFFFFFFFull);
+                                a64[w] = 0ull;
+                            }
+                        }
+                    } else {
+                        // four 16/16 counters per 16-byte load; the array starts 16-byte aligned
+                        const long long q4 = ((long long)u + 3) / 4;
+                        uint4* a4 = (uint4*)a32;
+                        for (long long i = g; i < q4; i += T) {
+                            const uint4 x = __ldcg(&a4[i]);
+                            if (x.x | x.y | x.z | x.w) {
+                                const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                                for (int k = 0; k < 4; k++) {
+                                    qa += choose2(xs[k] >> 16);
+                                    qb += choose2(xs[k] & 0xFFFFu);
+                                }
+                                a4[i] = make_uint4(0, 0, 0, 0);
+                            }
+                        }
+                    }
+                    break;
+                }
                 if (wall * 8 > n) {
                     const long long words = wide ? (long long)n : ((long long)n + 1) / 2;  // 64-bit words
                     uint4* a4 = (uint4*)a64;
@@ -805,6 +841,9 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                         if (pass == 1) {
                             if (wide) a64[wv] = 0ull;
                             else a32[wv] = 0u;
+                        } else if (sweep) {
+                            if (wide) atomicAdd(&a64[wv], flag_inc(fl));
+                            else atomicAdd(&a32[wv], flag_inc16(fl));
                         } else if (wide) {
                             unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
                             if (fl & FLAG_A) qa += old >> 32;
@@ -1286,8 +1325,8 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaLaunchKernelEx(&cfg, k_c4_dense_t<true>, a.ctl, (const int32_t*)lists(BIN_C4_DENSE),
-                           (const long long*)a.U_off, (const uint32_t*)a.U_col, (const int32_t*)a.U_split, a.dense,
-                           a.n_alloc);
+                           (const long long*)a.U_off, (const uint32_t*)a.U_col, (const int32_t*)a.U_split,
+                           (const long long*)a.U_wt, a.dense, a.n_alloc);
     }
     k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
                                                         a.cta_tables, a.cta_table_words);
