@@ -232,11 +232,11 @@ int gc_count_static_noalloc(int32_t n, const int32_t *d_row_ptr, const int32_t *
  */
 typedef struct {
     int32_t tri_warp_max;   /* warp per root                    [32]    */
+    int32_t tri_small_max;  /* block per root, short out-lists  [128]   */
     int32_t tri_block_max;  /* block per root, merge beyond     [512]   */
     int32_t c4_reg_max;     /* registers                        [32]    */
     int32_t c4_warp_max;    /* warp hash in shared memory       [512]   */
     int32_t c4_block_max;   /* block hash in shared memory      [8192]  */
-    int32_t reserved0;
     int64_t c4_cta_max;     /* per-CTA hash table in L2         [32768] */
     int64_t c4_chunk_min;   /* above this: shared-memory counters over id-range chunks;
                                otherwise a CTA cluster on a dense array in L2; 0 = never */

@@ -1330,6 +1330,7 @@ int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
 static void tuning_to_abi(const Tuning& t, gc_tuning* o) {
     std::memset(o, 0, sizeof(*o));
     o->tri_warp_max = t.tri_warp_max;
+    o->tri_small_max = t.tri_small_max;
     o->tri_block_max = t.tri_block_max;
     o->c4_reg_max = t.c4_reg_max;
     o->c4_warp_max = t.c4_warp_max;
@@ -1346,13 +1347,14 @@ int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
 
 int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
-    if (t->tri_warp_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
+    if (t->tri_warp_max < 1 || t->tri_small_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
         t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0) {
         g->err = "tuning: every bound must be positive (c4_chunk_min may be 0)";
         return GC_EINVAL;
     }
     Tuning n;
     n.tri_warp_max = t->tri_warp_max;
+    n.tri_small_max = t->tri_small_max;
     n.tri_block_max = t->tri_block_max;
     n.c4_reg_max = t->c4_reg_max;
     n.c4_warp_max = t->c4_warp_max;
@@ -1389,13 +1391,14 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     float cur_ms = 0.f;
     int rc = time_static(g, reps, &cur_ms, ref);
     if (rc) return rc;
-    // candidate values per boundary; coordinate descent, at most two sweeps
+    // candidate values per boundary; coordinate descent, at most three sweeps
     // (a bound below the tier beneath it empties the tier; the chunked
     // kernel only takes pivots above c4_cta_max, so lowering that one after
     // c4_chunk_min opens the chunked tier to medium pivots)
-    const long long cand[7][6] = {
+    const long long cand[8][6] = {
         {16, 32, -1, -1, -1, -1},                          // tri_warp_max
-        {128, 256, 512, -1, -1, -1},                       // tri_block_max
+        {64, 128, -1, -1, -1, -1},                         // tri_small_max
+        {256, 512, -1, -1, -1, -1},                        // tri_block_max
         {16, 32, -1, -1, -1, -1},                          // c4_reg_max
         {128, 512, -1, -1, -1, -1},                        // c4_warp_max
         {512, 2048, 8192, -1, -1, -1},                     // c4_block_max
@@ -1405,30 +1408,32 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     auto field = [](Tuning& t, int i) -> long long {
         switch (i) {
             case 0: return t.tri_warp_max;
-            case 1: return t.tri_block_max;
-            case 2: return t.c4_reg_max;
-            case 3: return t.c4_warp_max;
-            case 4: return t.c4_block_max;
-            case 5: return t.c4_cta_max;
+            case 1: return t.tri_small_max;
+            case 2: return t.tri_block_max;
+            case 3: return t.c4_reg_max;
+            case 4: return t.c4_warp_max;
+            case 5: return t.c4_block_max;
+            case 6: return t.c4_cta_max;
             default: return t.c4_chunk_min;
         }
     };
     auto set = [](Tuning& t, int i, long long v) {
         switch (i) {
             case 0: t.tri_warp_max = (int)v; break;
-            case 1: t.tri_block_max = (int)v; break;
-            case 2: t.c4_reg_max = (int)v; break;
-            case 3: t.c4_warp_max = (int)v; break;
-            case 4: t.c4_block_max = (int)v; break;
-            case 5: t.c4_cta_max = v; break;
+            case 1: t.tri_small_max = (int)v; break;
+            case 2: t.tri_block_max = (int)v; break;
+            case 3: t.c4_reg_max = (int)v; break;
+            case 4: t.c4_warp_max = (int)v; break;
+            case 5: t.c4_block_max = (int)v; break;
+            case 6: t.c4_cta_max = v; break;
             default: t.c4_chunk_min = v; break;
         }
     };
     const bool chunk_ok = c4_chunk_table_entries(std::max(g->n, 1)) > 0 && ensure_chunk_table(g);
     for (int sweep = 0; sweep < 3; sweep++) {
         bool moved = false;
-        for (int i = 6; i >= 0; i--) {
-            if (i == 6 && !chunk_ok) continue;
+        for (int i = 7; i >= 0; i--) {
+            if (i == 7 && !chunk_ok) continue;
             for (int k = 0; k < 6; k++) {
                 const long long v = cand[i][k];
                 if (v < 0 || v == field(cur, i)) continue;

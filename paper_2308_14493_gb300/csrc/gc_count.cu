@@ -144,7 +144,11 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
             const int split = U_split[u];
             const int k = (int)(re - rb) - split;
             dmax = max(dmax, (int)(re - rb));
-            if (k >= 2) tb = k <= t.tri_warp_max ? BIN_TRI_WARP : (k <= t.tri_block_max ? BIN_TRI_BLOCK : BIN_TRI_MERGE);
+            if (k >= 2)
+                tb = k <= t.tri_warp_max    ? BIN_TRI_WARP
+                     : k <= t.tri_small_max ? BIN_TRI_SMALL
+                     : k <= t.tri_block_max ? BIN_TRI_BLOCK
+                                            : BIN_TRI_MERGE;
             if (split >= 2) {
                 const long long wt = U_wt[u];
                 // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
@@ -248,17 +252,20 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
     acc_add(c, 10, kb);
 }
 
-constexpr int TB_WORDS = TRI_KM / 32;
+// Shared memory of the block kernel for out-lists of up to KM entries.
+template <int KM>
 constexpr size_t tri_block_smem() {
-    return (size_t)TRI_KM * 4 + (size_t)TRI_KM * 8 + (size_t)(TRI_KM + 8) * 4 + 2ull * TRI_KM * TB_WORDS * 4 +
-           (size_t)TRI_KM * 8;
+    return (size_t)KM * 4 + (size_t)KM * 8 + (size_t)(KM + 8) * 4 + 2ull * KM * (KM / 32) * 4 + (size_t)KM * 8;
 }
-size_t tri_block_smem_bytes() { return tri_block_smem(); }
+size_t tri_block_smem_bytes() { return tri_block_smem<TRI_KM>(); }
 
-// Roots with 32 < k <= TRI_KM: one block per root.  The out-list X is held
+// Roots with 32 < k <= KM: one block per root.  The out-list X is held
 // in shared memory; the candidates (every entry of N+(v) up to max X, for v
 // in X) are dealt in warp-contiguous runs of 32, so a lane finds its row by
 // stepping from the run's first row, and its position in X by binary search.
+// Two instances: KM = TRI_KS for the many short lists (small shared
+// footprint, many blocks per SM) and KM = TRI_KM for the long ones.
+template <int KM, int BIN, int WORK>
 __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __restrict__ list,
                                                   const long long* __restrict__ U_off,
                                                   const uint32_t* __restrict__ U_col,
@@ -266,17 +273,17 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
                                                   unsigned long long* __restrict__ tpack) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long* sNb = (long long*)smem;
-    unsigned long long* sTq = (unsigned long long*)(smem + (size_t)TRI_KM * 8);
-    uint32_t* sX = (uint32_t*)(smem + (size_t)TRI_KM * 16);
-    int* sPre = (int*)(smem + (size_t)TRI_KM * 20);
-    uint32_t* sRA = (uint32_t*)(smem + (size_t)TRI_KM * 24 + 32);
-    uint32_t* sRB = sRA + TRI_KM * TB_WORDS;
+    unsigned long long* sTq = (unsigned long long*)(smem + (size_t)KM * 8);
+    uint32_t* sX = (uint32_t*)(smem + (size_t)KM * 16);
+    int* sPre = (int*)(smem + (size_t)KM * 20);
+    uint32_t* sRA = (uint32_t*)(smem + (size_t)KM * 24 + 32);
+    uint32_t* sRB = sRA + KM * (KM / 32);
     __shared__ int s_idx;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
-    const int cnt = c->nbin[BIN_TRI_BLOCK];
+    const int cnt = c->nbin[BIN];
     unsigned long long ka = 0, kb = 0;
     for (;;) {
-        if (tid == 0) s_idx = (int)atomicAdd(&c->work[1], 1u);
+        if (tid == 0) s_idx = (int)atomicAdd(&c->work[WORK], 1u);
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
@@ -1240,14 +1247,21 @@ __global__ void k_finalize(Ctl* c, int mode) {
 namespace gcx {
 
 void count_setup_attributes() {
-    cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_block_smem_bytes());
+    cudaFuncSetAttribute(k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tri_block_smem<TRI_KM>());
+    cudaFuncSetAttribute(k_tri_block<TRI_KS, BIN_TRI_SMALL, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tri_block_smem<TRI_KS>());
     cudaFuncSetAttribute(k_c4_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_block_smem_bytes());
     cudaFuncSetAttribute(k_c4_dense_t<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_c4_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_chunk_smem_bytes());
 }
 
+// Cluster size of the heavy 4-cycle kernel: the one that keeps the most
+// CTAs resident (8-CTA clusters fill all 152 SMs of a GB300, 16-CTA ones
+// only 112), unless the caller asks for a size.
 int dense_cluster_plan(int want, int sms, int* size_out) {
-    int sizes[2] = {16, 8};
+    int best_size = 8, best_active = 0;
+    const int sizes[2] = {8, 16};
     for (int i = 0; i < 2; i++) {
         int cs = sizes[i];
         if (want && want != cs) continue;
@@ -1266,13 +1280,14 @@ int dense_cluster_plan(int want, int sms, int* size_out) {
             cudaGetLastError();
             active = 0;
         }
-        if (active > 0) {
-            *size_out = cs;
-            return std::min(active, std::max(1, sms / cs));
+        active = std::min(active, std::max(1, sms / cs));
+        if (active * cs > best_active * best_size) {
+            best_size = cs;
+            best_active = active;
         }
     }
-    *size_out = 8;
-    return std::max(1, sms / 8);
+    *size_out = best_size;
+    return best_active > 0 ? best_active : std::max(1, sms / best_size);
 }
 
 // The caller's bin boundaries, clamped to what the kernels and the scratch
@@ -1280,7 +1295,8 @@ int dense_cluster_plan(int want, int sms, int* size_out) {
 Tuning effective_tuning(const CountArgs& a) {
     Tuning t = a.tune;
     t.tri_warp_max = std::max(1, std::min(t.tri_warp_max, 32));
-    t.tri_block_max = std::max(t.tri_warp_max, std::min(t.tri_block_max, TRI_KM));
+    t.tri_small_max = std::max(t.tri_warp_max, std::min(t.tri_small_max, TRI_KS));
+    t.tri_block_max = std::max(t.tri_small_max, std::min(t.tri_block_max, TRI_KM));
     t.c4_reg_max = std::max(1, std::min(t.c4_reg_max, 32));
     t.c4_warp_max = std::max(t.c4_reg_max, std::min(t.c4_warp_max, C4_T1));
     t.c4_block_max = std::max(t.c4_warp_max, std::min(t.c4_block_max, C4_T2));
@@ -1303,8 +1319,10 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     nl += 2;
     if (ev_tri) cudaEventRecord(ev_tri, s);
     k_tri_warp<<<4 * sms, TW * 32, 0, s>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_block<<<2 * sms, 256, tri_block_smem_bytes(), s>>>(a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col,
-                                                              a.U_split, a.tpack);
+    k_tri_block<TRI_KS, BIN_TRI_SMALL, 6><<<8 * sms, 256, tri_block_smem<TRI_KS>(), s>>>(
+        a.ctl, lists(BIN_TRI_SMALL), a.U_off, a.U_col, a.U_split, a.tpack);
+    k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1><<<2 * sms, 256, tri_block_smem<TRI_KM>(), s>>>(
+        a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col, a.U_split, a.tpack);
     k_tri_merge<<<sms, 256, 0, s>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
     nl += 3;
     if (ev_c4) cudaEventRecord(ev_c4, s);

@@ -33,7 +33,7 @@ constexpr int MAX_HOPS = 8;
 enum {
     // (default boundaries; the Tuning below moves them at run time)
     BIN_TRI_WARP = 0,   // 2 <= k <= 32                   warp per root
-    BIN_TRI_BLOCK = 1,  // 32 < k <= TRI_KM                block per root
+    BIN_TRI_BLOCK = 1,  // TRI_KS < k <= TRI_KM            block per root
     BIN_TRI_MERGE = 2,  // k > TRI_KM                      merge per out-edge
     BIN_C4_REG = 3,     // w~ <= 32                        registers (match)
     BIN_C4_WARP = 4,    // w~ <= C4_T1                     warp hash in shared memory
@@ -41,7 +41,8 @@ enum {
     BIN_C4_DENSE = 6,   // C4_T3 < w~ <= c4_chunk_min      cluster, shared dense counter array
     BIN_C4_CTA = 7,     // C4_T2 < w~ <= C4_T3             CTA, own hash table in global memory
     BIN_C4_CHUNK = 8,   // w~ > c4_chunk_min (off)         CTA, shared-memory counters over id-range chunks
-    NBINS = 9
+    BIN_TRI_SMALL = 9,  // 32 < k <= TRI_KS                block per root, small shared footprint
+    NBINS = 10
 };
 
 // Device control block: sizes produced and consumed on the device, so a
@@ -80,6 +81,7 @@ struct Ctl {
 };
 
 constexpr int TRI_KM = 512;
+constexpr int TRI_KS = 128;
 constexpr int C4_T1 = 512;
 constexpr int C4_T2 = 8192;
 constexpr long long C4_T3 = 32768;
@@ -90,6 +92,7 @@ constexpr int C4_CLUSTER = 8;       // CTAs per cluster of the dense 4-cycle ker
 // autotuner or set by the caller.
 struct Tuning {
     int tri_warp_max;        // out-degree k: warp kernel up to this (<= 32)
+    int tri_small_max;       // small-footprint block kernel up to this (<= TRI_KS)
     int tri_block_max;       // block kernel up to this (<= TRI_KM), merge beyond
     int c4_reg_max;          // wedge bound w~: registers up to this (<= 32)
     int c4_warp_max;         // warp hash (<= C4_T1)
@@ -98,7 +101,7 @@ struct Tuning {
     long long c4_chunk_min;  // chunked shared-memory kernel above this (else cluster kernel)
 };
 constexpr long long NEVER = 1ll << 62;
-inline Tuning default_tuning() { return Tuning{32, TRI_KM, 32, C4_T1, C4_T2, C4_T3, NEVER}; }
+inline Tuning default_tuning() { return Tuning{32, TRI_KS, TRI_KM, 32, C4_T1, C4_T2, C4_T3, NEVER}; }
 constexpr int C4_DENSE_THREADS = 1024;
 
 // Handle-independent launch geometry.

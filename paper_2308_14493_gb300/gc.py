@@ -56,8 +56,8 @@ class gc_stats(ctypes.Structure):
 
 
 class gc_tuning(ctypes.Structure):
-    _fields_ = [("tri_warp_max", ctypes.c_int32), ("tri_block_max", ctypes.c_int32), ("c4_reg_max", ctypes.c_int32),
-                ("c4_warp_max", ctypes.c_int32), ("c4_block_max", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    _fields_ = [("tri_warp_max", ctypes.c_int32), ("tri_small_max", ctypes.c_int32), ("tri_block_max", ctypes.c_int32),
+                ("c4_reg_max", ctypes.c_int32), ("c4_warp_max", ctypes.c_int32), ("c4_block_max", ctypes.c_int32),
                 ("c4_cta_max", ctypes.c_int64), ("c4_chunk_min", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
 
     def as_dict(self) -> dict:

@@ -137,9 +137,10 @@ def test_chunked_four_cycle_tier(gcb, name, opts):
 
 
 TUNINGS = {
-    "tri_all_merge": dict(tri_warp_max=1, tri_block_max=1),
-    "tri_all_block": dict(tri_warp_max=1, tri_block_max=512),
-    "tri_small_block": dict(tri_warp_max=8, tri_block_max=40),
+    "tri_all_merge": dict(tri_warp_max=1, tri_small_max=1, tri_block_max=1),
+    "tri_all_block": dict(tri_warp_max=1, tri_small_max=1, tri_block_max=512),
+    "tri_all_small_block": dict(tri_warp_max=1, tri_small_max=128, tri_block_max=128),
+    "tri_small_block": dict(tri_warp_max=8, tri_small_max=20, tri_block_max=40),
     "c4_warp_hash": dict(c4_reg_max=1, c4_warp_max=512, c4_block_max=512, c4_cta_max=512),
     "c4_block_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=8192, c4_cta_max=8192),
     "c4_cta_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=32768),
