@@ -695,6 +695,15 @@ __device__ __forceinline__ void wedge_segment_prefix(const long long* __restrict
 constexpr int C4D_SEG = 2048;  // lower neighbours per prefix segment
 constexpr int C4D_UNROLL = 4;
 
+// Reductions in L2 that return nothing (the compiler may otherwise merge
+// them with the returning atomics of the other path).
+__device__ __forceinline__ void red_add_u32(uint32_t* p, uint32_t v) {
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <bool CLUSTER>
 __device__ __forceinline__ void group_sync() {
     if constexpr (CLUSTER) {
@@ -849,8 +858,8 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                             if (wide) a64[wv] = 0ull;
                             else a32[wv] = 0u;
                         } else if (sweep) {
-                            if (wide) atomicAdd(&a64[wv], flag_inc(fl));
-                            else atomicAdd(&a32[wv], flag_inc16(fl));
+                            if (wide) red_add_u64(&a64[wv], flag_inc(fl));
+                            else red_add_u32(&a32[wv], flag_inc16(fl));
                         } else if (wide) {
                             unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
                             if (fl & FLAG_A) qa += old >> 32;

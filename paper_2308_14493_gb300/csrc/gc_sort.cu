@@ -35,27 +35,39 @@ __global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const uint64_t* __restrict
     hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// In-place exclusive scan of a[0..len) by one block of 1024 threads.
+// In-place exclusive scan of a[0..len) by one block of 1024 threads: each
+// thread sums a contiguous slice, the 1024 slice sums are scanned with warp
+// shuffles (two levels), then each thread rewrites its slice.
 __global__ void __launch_bounds__(1024) k_scan_u32_one_block(uint32_t* a, int len) {
-    __shared__ uint32_t part[1024];
-    int t = threadIdx.x;
-    int per = (len + 1023) / 1024;
-    int beg = t * per, end = min(beg + per, len);
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (len + 1023) / 1024;
+    const int beg = t * per, end = min(beg + per, len);
     uint32_t s = 0;
     for (int i = beg; i < end; i++) s += a[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    uint32_t x = s;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
     }
-    uint32_t run = part[t] - s;
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
     for (int i = beg; i < end; i++) {
-        uint32_t x = a[i];
+        const uint32_t v = a[i];
         a[i] = run;
-        run += x;
+        run += v;
     }
 }
 
