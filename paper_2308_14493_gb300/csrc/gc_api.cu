@@ -94,6 +94,12 @@ struct gc_graph {
     int g_commit = -1;
     unsigned long long g_gen = 0;
     int g_launches = 0;                  // kernels in one replay
+    // the same for the plain form: one batch per call, stage events recorded
+    cudaGraphExec_t pexec = nullptr;
+    long long p_nk = -1;
+    int p_commit = -1;
+    unsigned long long p_gen = 0;
+    int p_launches = 0;
     unsigned long long buf_gen = 1;      // bumped whenever a buffer moves
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
@@ -315,14 +321,16 @@ static long long grow_bytes(const Buf<T>& b, size_t count) {
 // holds: its scratch growth, plus a re-layout of the adjacency when the
 // pool's free space at the end of the last batch may not take the insertions.
 static long long predict_batch_bytes(const gc_graph* g, long long n_ins, long long n_del) {
-    const size_t nk = (size_t)std::max<long long>(2 * (n_ins + n_del), 1);
+    // batch scratch is sized for the captured shape: the next power of two of the keys
+    size_t nk = 1;
+    while (nk < (size_t)std::max<long long>(2 * (n_ins + n_del), 1)) nk <<= 1;
     long long b = grow_bytes(g->keys, nk) + grow_bytes(g->keys_tmp, nk) + grow_bytes(g->keepA, nk) +
                   grow_bytes(g->keepD, nk) + grow_bytes(g->posA, nk + 1) + grow_bytes(g->posD, nk + 1) +
                   grow_bytes(g->srcA, nk) + grow_bytes(g->dstA, nk) + grow_bytes(g->srcD, nk) +
                   grow_bytes(g->dstD, nk) + grow_bytes(g->plan_dst, nk) + grow_bytes(g->plan_scr, nk) +
                   grow_bytes(g->plan_cap, nk) + grow_bytes(g->plan_deg, nk) +
                   grow_bytes(g->hist, (size_t)256 * radix_grid((long long)nk, g->sms)) +
-                  grow_bytes(g->pairs, nk);
+                  grow_bytes(g->pairs, nk) + grow_bytes(g->out_dev, 6);
     const size_t ucap = (size_t)(2 * g->m + 4 * n_ins + 64);
     b += grow_bytes(g->U_col, ucap) + grow_bytes(g->tpack, ucap);
     const long long pool_free = g->col_capacity - (long long)g->h_ctl->pool_tail;
@@ -340,6 +348,10 @@ static void trim_scratch(gc_graph* g) {
     if (g->gexec) {
         cudaGraphExecDestroy(g->gexec);
         g->gexec = nullptr;
+    }
+    if (g->pexec) {
+        cudaGraphExecDestroy(g->pexec);
+        g->pexec = nullptr;
     }
     release(g, g->U_col);
     release(g, g->tpack);
@@ -430,7 +442,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
         k_set_F<<<1, 32, 0, s>>>(g->ctl);
         g->launches++;
     }
-    if (timed) CK(cudaEventRecord(g->ev[6], s));
+    if (timed) CK(record_stage(g->ev[6], s));
     CKL();
     return GC_OK;
 }
@@ -474,7 +486,7 @@ static int enqueue_segments(gc_graph* g, bool clear) {
 static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool commit, bool timed,
                          BatchArg arg = BatchArg{nullptr, nullptr, 0, 0}) {
     cudaStream_t s = g->s;
-    if (timed) CK(cudaEventRecord(g->ev[0], s));
+    if (timed) CK(record_stage(g->ev[0], s));
     k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, use_cursor ? 1 : 0, arg);
     g->launches++;
     const long long nkb = std::max<long long>(max_nk, 1);
@@ -496,7 +508,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool co
         int rc = enqueue_segments(g, false);
         if (rc) return rc;
     }
-    if (timed) CK(cudaEventRecord(g->ev[1], s));
+    if (timed) CK(record_stage(g->ev[1], s));
     CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
     k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
     k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
@@ -507,14 +519,14 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool co
         g->launches += 2;
     }
     CKL();
-    if (timed) CK(cudaEventRecord(g->ev[2], s));
+    if (timed) CK(record_stage(g->ev[2], s));
     int rc = count_region(g, commit ? 0 : 2, false, timed);
     if (rc) return rc;
     if (commit) {
         rc = enqueue_commit(g);
         if (rc) return rc;
     }
-    if (timed) CK(cudaEventRecord(g->ev[7], s));
+    if (timed) CK(record_stage(g->ev[7], s));
     if (max_nk > 0) {
         rc = enqueue_segments(g, true);
         if (rc) return rc;
@@ -618,20 +630,78 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
     }
 }
 
-// One batch whose pairs are already in device memory (plain form).
+// Capture the per-batch launch sequence (batch from the run cursor) into
+// *exec; timed: with the stage events as event-record nodes.
+static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool timed, cudaGraphExec_t* exec,
+                         int* launches) {
+    cudaStream_t s = g->s;
+    if (*exec) {
+        cudaGraphExecDestroy(*exec);
+        *exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int lsave = g->launches;
+    g->launches = 0;
+    int rc = enqueue_batch(g, shape_nk, true, commit, timed);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    *launches = g->launches;
+    g->launches = lsave;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) {
+        g->err = std::string("graph capture: ") + cudaGetErrorString(ce);
+        return GC_ECUDA;
+    }
+    ce = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        *exec = nullptr;
+        g->err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+        return GC_ECUDA;
+    }
+    return GC_OK;
+}
+
+// One batch whose pairs are already in device memory (plain form): the
+// batch's launch sequence is captured once per batch shape (grids sized for
+// the next power of two of its keys) with its stage events, then replayed
+// with the batch described on the device.
 static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, const int32_t* d_del,
                         long long n_del, int commit, uint64_t out[6]) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = g->s;
-    long long nk = 2 * (n_ins + n_del);
-    int rc = plan_batch_buffers(g, nk);
+    const long long nk = 2 * (n_ins + n_del);
+    long long shape_nk = 1;
+    while (shape_nk < nk) shape_nk <<= 1;
+    int rc = plan_batch_buffers(g, shape_nk);
     if (rc) return rc;
     rc = plan_region_buffers(g, g->m, n_ins);
     if (rc) return rc;
-    g->launches = 0;
-    CK(cudaEventRecord(g->e0, s));
-    rc = enqueue_batch(g, nk, false, commit != 0, true, BatchArg{d_ins, d_del, n_ins, n_del});
+    rc = ensure_desc(g, 6);
     if (rc) return rc;
+    if (!ensure(g, g->out_dev, 6)) return nomem(g, "batch results");
+    if (!g->pexec || g->p_nk != shape_nk || g->p_commit != commit || g->p_gen != g->buf_gen) {
+        rc = capture_batch(g, shape_nk, commit != 0, true, &g->pexec, &g->p_launches);
+        if (rc) return rc;
+        g->p_nk = shape_nk;
+        g->p_commit = commit;
+        g->p_gen = g->buf_gen;
+    }
+    g->h_desc[0] = (long long)d_ins;
+    g->h_desc[1] = (long long)d_del;
+    g->h_desc[2] = 0;
+    g->h_desc[3] = n_ins;
+    g->h_desc[4] = 0;
+    g->h_desc[5] = n_del;
+    CK(cudaMemcpyAsync(g->desc, g->h_desc, 6 * sizeof(long long), cudaMemcpyHostToDevice, s));
+    k_run_reset<<<1, 32, 0, s>>>(g->ctl);
+    CKL();
+    g->launches = g->p_launches + 1;
+    CK(cudaEventRecord(g->e0, s));
+    CK(cudaGraphLaunch(g->pexec, s));
     CK(cudaEventRecord(g->e1, s));
     rc = read_ctl(g);
     if (rc) return rc;
@@ -657,7 +727,10 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
     for (int i = 0; i < 7; i++) {
         float x = 0.f;
-        cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]);
+        if (cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]) != cudaSuccess) {
+            cudaGetLastError();  // a stage the batch skipped; not an error of the batch
+            x = 0.f;
+        }
         g->st.ms_stage[i] = x;
     }
     g->st.ms_stage[7] = 0.f;
@@ -817,8 +890,9 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
         for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
     // a static count leaves its stage times in the stats record
     for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
-    for (int i = 2; i < 6; i++) cudaEventElapsedTime(&g->st.ms_stage[i], g->ev[i], g->ev[i + 1]);
-    cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]);
+    for (int i = 2; i < 6; i++)
+        if (cudaEventElapsedTime(&g->st.ms_stage[i], g->ev[i], g->ev[i + 1]) != cudaSuccess) cudaGetLastError();
+    if (cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]) != cudaSuccess) cudaGetLastError();
     fill_stats(g, *g->h_ctl);
     g->st.launches = g->launches;
     return GC_OK;
@@ -831,6 +905,7 @@ static void destroy(gc_graph* g) {
     if (!g) return;
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->pexec) cudaGraphExecDestroy(g->pexec);
     int32_t* p32[] = {g->perm, g->iperm, g->deg, g->cap, g->col, g->wlist, g->U_deg, g->U_split, g->da, g->db};
     for (auto p : p32) dfree(g, p);
     dfree(g, g->row_start);

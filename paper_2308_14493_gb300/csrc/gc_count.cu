@@ -1326,7 +1326,7 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     k_wedge_bound<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
     k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
     nl += 2;
-    if (ev_tri) cudaEventRecord(ev_tri, s);
+    if (ev_tri) record_stage(ev_tri, s);
     k_tri_warp<<<4 * sms, TW * 32, 0, s>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
     k_tri_block<TRI_KS, BIN_TRI_SMALL, 6><<<8 * sms, 256, tri_block_smem<TRI_KS>(), s>>>(
         a.ctl, lists(BIN_TRI_SMALL), a.U_off, a.U_col, a.U_split, a.tpack);
@@ -1334,7 +1334,7 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
         a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col, a.U_split, a.tpack);
     k_tri_merge<<<sms, 256, 0, s>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
     nl += 3;
-    if (ev_c4) cudaEventRecord(ev_c4, s);
+    if (ev_c4) record_stage(ev_c4, s);
     k_c4_reg<<<4 * sms, 256, 0, s>>>(a.ctl, lists(BIN_C4_REG), a.U_off, a.U_col, a.U_split);
     k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, s>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split);
     k_c4_block<<<sms, 256, c4_block_smem_bytes(), s>>>(a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col, a.U_split);
@@ -1365,7 +1365,7 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                                                                    a.U_split, a.chunk_table, TW);
         nl += 2;
     }
-    if (ev_end) cudaEventRecord(ev_end, s);
+    if (ev_end) record_stage(ev_end, s);
     k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
     k_finalize<<<1, 32, 0, s>>>(a.ctl, mode);
     nl += 2;

@@ -109,6 +109,17 @@ struct Dims {
     int sms;
 };
 
+// Stage-boundary event: inside a stream capture it becomes an event-record
+// node that records at every replay (a plain record there would only order
+// the capture); outside a capture an ordinary record.
+inline cudaError_t record_stage(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(s, &st);
+    if (r != cudaSuccess) return r;
+    return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
 __device__ __forceinline__ uint32_t vid(uint32_t e) { return e & ID_MASK; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
