@@ -766,7 +766,20 @@ static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t
     // similar shape share one captured graph
     long long shape_nk = 1;
     while (shape_nk < max_nk) shape_nk <<= 1;
-    int rc = plan_batch_buffers(g, shape_nk);
+    int rc = GC_OK;
+    int relayouts = 0;
+    if (commit && sum_ins > 0) {
+        // room for the whole run's insertions and the rows they relocate, so
+        // the replays are not halted by a full pool mid-run
+        const long long need = 8 * sum_ins;
+        const long long pool_free = g->col_capacity - (long long)g->h_ctl->pool_tail;
+        if (pool_free < need) {
+            rc = relayout(g, need);
+            if (rc) return rc;
+            relayouts++;
+        }
+    }
+    rc = plan_batch_buffers(g, shape_nk);
     if (rc) return rc;
     rc = plan_region_buffers(g, g->m + (commit ? sum_ins : max_ins), max_ins);
     if (rc) return rc;
@@ -810,7 +823,7 @@ static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t
         g->g_gen = g->buf_gen;
     }
     CK(cudaEventRecord(g->e0, s));
-    int relayouts = 0, done = 0;
+    int done = 0;
     while (done < k) {
         for (int i = done; i < k; i++) CK(cudaGraphLaunch(g->gexec, s));
         rc = read_ctl(g);

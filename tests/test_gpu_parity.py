@@ -505,6 +505,46 @@ def test_batched_run_that_outgrows_the_pool(gcb):
         assert g.count_static() == expect[-1]
 
 
+def test_batched_run_that_relocates_hub_rows_repeatedly(gcb):
+    """Few insertions into many nearly full hub rows: every batch relocates
+    whole rows, more than the pool grown ahead of the run can take, so the
+    run halts and resumes mid-way; results still match the oracle."""
+    n = 3000
+    rng = np.random.default_rng(29)
+    keys = set(int(k) for k in gen.er_graph(n, 3000, 28))
+    hubs = list(range(20))
+    for h in hubs:
+        for v in rng.choice(np.arange(20, n), 500, replace=False):
+            keys.add((h << 32) | int(v))
+    keys = np.array(sorted(keys), dtype=np.uint64)
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    batches, expect = [], []
+    for step in range(6):
+        cur = set(int(k) for k in gen.keys_from_csr(og.row_ptr, og.col))
+        ins = []
+        for h in hubs:
+            added = 0
+            for v in rng.permutation(np.arange(20, n)):
+                kk = (h << 32) | int(v)
+                if kk not in cur:
+                    cur.add(kk)
+                    ins.append((h, int(v)))
+                    added += 1
+                    if added == 30:
+                        break
+        edges = edges_from_csr(og.row_ptr, og.col)
+        dels = np.array([edges[i] for i in rng.choice(len(edges), 20, replace=False)], np.int32)
+        ins = np.array(ins, np.int32)
+        batches.append((ins, dels))
+        expect.append(og.apply(ins, dels)["F"])
+    with open_graph(gcb, n, rp, col, slack=0.05) as g:
+        outs = g.apply_many(batches)
+        assert outs == expect
+        assert g.stats()["relayouts"] >= 2
+        assert same_graph(g, og.row_ptr, og.col)
+
+
 def test_device_batched_api_equals_plain(gcb):
     torch = pytest.importorskip("torch")
     n, keys = gen.workload_graph("c2")
