@@ -83,9 +83,11 @@ typedef struct {
     float ms_wall;                  /* host wall time of the call */
     int32_t relayouts;              /* adjacency re-layouts the batch needed */
     int32_t reserved[5];
-    /* device time per stage (CUDA events on the library's stream):
+    /* device time per stage (CUDA events):
        [0] normalise  [1] region walk  [2] union graph  [3] triangles + 4-cliques
-       [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused */
+       [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused
+       Stages 3 and 4 run side by side: each is timed from the start of the
+       counting pass to its own end. */
     float ms_stage[8];
     /* work of the counting pass, for roofline accounting */
     int64_t work_triangles;         /* sum over union-graph out-edges u->v of |N+(u)| + |N+(v)| */

@@ -108,6 +108,8 @@ struct gc_graph {
     std::string err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEvent_t ev[8] = {};  // stage boundaries, see gc_stats.ms_stage
+    cudaStream_t aux[3] = {};   // side streams of the counting pass
+    cudaEvent_t fork = nullptr, join[3] = {};
     int launches = 0;        // kernels launched by the current call
     // device bytes held, for admission control
     std::unordered_map<void*, size_t> held;
@@ -436,6 +438,11 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     ca.chunk_table = g->chunk_table.p;
     ca.tune = g->tune;
     ca.sms = g->sms;
+    for (int i = 0; i < 3; i++) {
+        ca.aux[i] = g->aux[i];
+        ca.join[i] = g->join[i];
+    }
+    ca.fork = g->fork;
     g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
                                     timed ? g->ev[5] : nullptr, fin);
     if (set_F) {
@@ -608,6 +615,27 @@ static int finish_pending_commit(gc_graph* g, int* relayouts) {
     return read_ctl(g);
 }
 
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, a, b) != cudaSuccess) {
+        cudaGetLastError();  // a stage the call did not run; not an error of the call
+        x = 0.f;
+    }
+    return x;
+}
+
+// Stage times of gc_stats.ms_stage from the boundary events ev[lo .. hi].
+// The triangle stage (ev3 -> ev4) and the 4-cycle stage (ev3 -> ev5) run
+// side by side from the same fork; the edge terms start after both.
+static void stage_times(gc_graph* g, int lo, int hi) {
+    for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
+    for (int i = lo; i < hi; i++) {
+        if (i == 4) g->st.ms_stage[4] = elapsed(g->ev[3], g->ev[5]);
+        else if (i == 5) g->st.ms_stage[5] = std::min(elapsed(g->ev[4], g->ev[6]), elapsed(g->ev[5], g->ev[6]));
+        else g->st.ms_stage[i] = elapsed(g->ev[i], g->ev[i + 1]);
+    }
+}
+
 static void fill_stats(gc_graph* g, const Ctl& c) {
     gc_stats& t = g->st;
     t.n_ins = c.nA2 / 2;
@@ -725,15 +753,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     g->st.launches = g->launches;
     // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
     // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
-    for (int i = 0; i < 7; i++) {
-        float x = 0.f;
-        if (cudaEventElapsedTime(&x, g->ev[i], g->ev[i + 1]) != cudaSuccess) {
-            cudaGetLastError();  // a stage the batch skipped; not an error of the batch
-            x = 0.f;
-        }
-        g->st.ms_stage[i] = x;
-    }
-    g->st.ms_stage[7] = 0.f;
+    stage_times(g, 0, 7);
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
         g->m += c.nA2 / 2 - c.nD2 / 2;
@@ -902,9 +922,7 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
     if (set_F)
         for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
     // a static count leaves its stage times in the stats record
-    for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
-    for (int i = 2; i < 6; i++)
-        if (cudaEventElapsedTime(&g->st.ms_stage[i], g->ev[i], g->ev[i + 1]) != cudaSuccess) cudaGetLastError();
+    stage_times(g, 2, 6);
     if (cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]) != cudaSuccess) cudaGetLastError();
     fill_stats(g, *g->h_ctl);
     g->st.launches = g->launches;
@@ -960,6 +978,11 @@ static void destroy(gc_graph* g) {
     for (auto e : g->ev)
         if (e) cudaEventDestroy(e);
     if (g->e1) cudaEventDestroy(g->e1);
+    for (int i = 0; i < 3; i++) {
+        if (g->aux[i]) cudaStreamDestroy(g->aux[i]);
+        if (g->join[i]) cudaEventDestroy(g->join[i]);
+    }
+    if (g->fork) cudaEventDestroy(g->fork);
     if (g->own_stream && g->s) cudaStreamDestroy(g->s);
     delete g;
 }
@@ -1222,6 +1245,17 @@ int gc_open(int32_t n, const int32_t* row_ptr, const int32_t* col, const gc_opti
             }()) {
             t_open_error = "host allocation failed";
             rc = GC_ENOMEM;
+            break;
+        }
+        // side streams of the counting pass (they inherit nothing from the
+        // caller's stream: every use is fenced by events on it)
+        bool aux_ok = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 3 && aux_ok; i++)
+            aux_ok = cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!aux_ok) {
+            t_open_error = "cudaStreamCreate failed";
+            rc = GC_ECUDA;
             break;
         }
         rc = open_device(g, row_ptr, col);

@@ -1326,24 +1326,36 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     k_wedge_bound<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
     k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
     nl += 2;
+    // The triangle kernels and the 4-cycle tiers are independent: with
+    // auxiliary streams they run side by side (a fork after the binning, a
+    // join before the edge terms), which fills the GPU when each tier alone
+    // has little work.  ev_tri marks the fork, ev_c4 the end of the triangle
+    // branch, ev_end the end of the 4-cycle branches.
+    const bool par = a.aux[0] && a.aux[1] && a.aux[2];
+    cudaStream_t sT = par ? a.aux[0] : s, sC1 = par ? a.aux[1] : s, sC2 = par ? a.aux[2] : s;
     if (ev_tri) record_stage(ev_tri, s);
-    k_tri_warp<<<4 * sms, TW * 32, 0, s>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_block<TRI_KS, BIN_TRI_SMALL, 6><<<8 * sms, 256, tri_block_smem<TRI_KS>(), s>>>(
+    if (par) {
+        cudaEventRecord(a.fork, s);
+        for (int i = 0; i < 3; i++) cudaStreamWaitEvent(a.aux[i], a.fork, 0);
+    }
+    k_tri_warp<<<4 * sms, TW * 32, 0, sT>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
+    k_tri_block<TRI_KS, BIN_TRI_SMALL, 6><<<8 * sms, 256, tri_block_smem<TRI_KS>(), sT>>>(
         a.ctl, lists(BIN_TRI_SMALL), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1><<<2 * sms, 256, tri_block_smem<TRI_KM>(), s>>>(
+    k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1><<<2 * sms, 256, tri_block_smem<TRI_KM>(), sT>>>(
         a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_merge<<<sms, 256, 0, s>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
-    nl += 3;
-    if (ev_c4) record_stage(ev_c4, s);
-    k_c4_reg<<<4 * sms, 256, 0, s>>>(a.ctl, lists(BIN_C4_REG), a.U_off, a.U_col, a.U_split);
-    k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, s>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split);
-    k_c4_block<<<sms, 256, c4_block_smem_bytes(), s>>>(a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col, a.U_split);
+    k_tri_merge<<<sms, 256, 0, sT>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
+    nl += 4;
+    if (ev_c4) record_stage(ev_c4, sT);
+    k_c4_reg<<<4 * sms, 256, 0, sC1>>>(a.ctl, lists(BIN_C4_REG), a.U_off, a.U_col, a.U_split);
+    k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, sC1>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split);
+    k_c4_block<<<sms, 256, c4_block_smem_bytes(), sC1>>>(a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col,
+                                                         a.U_split);
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.dense_cluster_size * a.dense_clusters);
         cfg.blockDim = dim3(C4_DENSE_THREADS);
         cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
+        cfg.stream = sC2;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = a.dense_cluster_size;
@@ -1355,17 +1367,27 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                            (const long long*)a.U_off, (const uint32_t*)a.U_col, (const int32_t*)a.U_split,
                            (const long long*)a.U_wt, a.dense, a.n_alloc);
     }
+    if (t.c4_chunk_min < NEVER) {
+        const int TW = c4_chunk_width(a.n_alloc);
+        k_chunk_bounds<<<8 * sms, 256, 0, sC2>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.chunk_table, TW);
+        k_c4_chunk<<<sms, CH_THREADS, c4_chunk_smem_bytes(), sC2>>>(a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col,
+                                                                    a.U_split, a.chunk_table, TW);
+        nl += 2;
+    }
     k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
                                                         a.cta_tables, a.cta_table_words);
     nl += 5;
-    if (t.c4_chunk_min < NEVER) {
-        const int TW = c4_chunk_width(a.n_alloc);
-        k_chunk_bounds<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.chunk_table, TW);
-        k_c4_chunk<<<sms, CH_THREADS, c4_chunk_smem_bytes(), s>>>(a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col,
-                                                                   a.U_split, a.chunk_table, TW);
-        nl += 2;
+    if (par) {
+        cudaEventRecord(a.join[1], sC1);
+        cudaEventRecord(a.join[2], sC2);
+        cudaStreamWaitEvent(s, a.join[1], 0);
+        cudaStreamWaitEvent(s, a.join[2], 0);
     }
     if (ev_end) record_stage(ev_end, s);
+    if (par) {
+        cudaEventRecord(a.join[0], sT);
+        cudaStreamWaitEvent(s, a.join[0], 0);
+    }
     k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
     k_finalize<<<1, 32, 0, s>>>(a.ctl, mode);
     nl += 2;

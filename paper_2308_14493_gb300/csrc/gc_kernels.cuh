@@ -83,6 +83,9 @@ struct CountArgs {
     int32_t* chunk_table;           // n_alloc * c4_chunk_width(n_alloc) run bounds of the chunked 4-cycle kernel
     Tuning tune;                    // bin boundaries (clamped to the capacities)
     int sms;
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // side streams of the counting pass (or none)
+    cudaEvent_t fork = nullptr;     // fork / join events for them (timing disabled)
+    cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
 };
 Tuning effective_tuning(const CountArgs& a);
 // Dynamic shared-memory limits of the counting kernels (once per device).
