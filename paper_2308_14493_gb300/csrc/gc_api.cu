@@ -578,7 +578,7 @@ static int relayout(gc_graph* g, long long pool_extra) {
 }
 
 static int read_ctl(gc_graph* g) {
-    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->s));
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, offsetof(Ctl, accs), cudaMemcpyDeviceToHost, g->s));
     CK(cudaStreamSynchronize(g->s));
     return GC_OK;
 }

@@ -53,6 +53,7 @@ namespace gcx {
 __global__ void k_reset_count(Ctl* c) {
     int t = threadIdx.x;
     if (t < 16) c->acc[t] = 0;
+    for (int i = t; i < 16 * ACC_STRIPES; i += blockDim.x) (&c->accs[0][0])[i] = 0;
     if (t < 8) c->work[t] = 0;
     if (t < NBINS) c->nbin[t] = 0;
     if (t == 0) c->maxdeg = 0;
@@ -68,9 +69,17 @@ __device__ __forceinline__ unsigned long long flag_inc(uint32_t f) {
     return ((f & FLAG_A) ? (1ull << 32) : 0ull) | ((f & FLAG_B) ? 1ull : 0ull);
 }
 
+// Add a warp's sum to accumulator `slot`: one atomic per warp, on one of
+// ACC_STRIPES copies chosen by the warp (thousands of warps adding to one
+// address would queue at a single L2 slice); k_finalize sums the copies.
+__device__ __forceinline__ void acc_add_warp(Ctl* c, int slot, unsigned long long x) {
+    if ((threadIdx.x & 31) == 0 && x) {
+        const int stripe = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (ACC_STRIPES - 1));
+        atomicAdd(&c->accs[slot][stripe], x);
+    }
+}
 __device__ __forceinline__ void acc_add(Ctl* c, int slot, unsigned long long x) {
-    x = warp_sum_u64(x);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c->acc[slot], x);
+    acc_add_warp(c, slot, warp_sum_u64(x));
 }
 
 // index of id y in the sorted entries s[0..k), or -1 (the first probes of
@@ -1207,22 +1216,27 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
         D[g] = warp_sum_u64(D[g]);
         E[g] = warp_sum_u64(E[g]);
     }
-    if (lane == 0) {
-        for (int g = 0; g < 2; g++) {
-            int o = 6 * g;
-            if (P[g]) atomicAdd(&c->acc[o + 0], P[g]);
-            if (S[g]) atomicAdd(&c->acc[o + 1], S[g]);
-            if (T[g]) atomicAdd(&c->acc[o + 2], T[g]);
-            if (D[g]) atomicAdd(&c->acc[o + 3], D[g]);
-            if (E[g]) atomicAdd(&c->acc[12 + g], E[g]);
-        }
+    for (int g = 0; g < 2; g++) {
+        const int o = 6 * g;
+        acc_add_warp(c, o + 0, P[g]);
+        acc_add_warp(c, o + 1, S[g]);
+        acc_add_warp(c, o + 2, T[g]);
+        acc_add_warp(c, o + 3, D[g]);
+        acc_add_warp(c, 12 + g, E[g]);
     }
-    work = warp_sum_u64(work);
-    if (lane == 0 && work) atomicAdd(&c->acc[14], work);
+    acc_add(c, 14, work);
 }
 
 // mode 0: batch (F += C_a - C_b unless the batch was rejected); 1: static
 __global__ void k_finalize(Ctl* c, int mode) {
+    // fold the striped accumulators (one warp: lane i sums slot i's copies
+    // and slot i + 16's if any)
+    if (blockIdx.x == 0 && threadIdx.x < 16) {
+        unsigned long long x = 0;
+        for (int k = 0; k < ACC_STRIPES; k++) x += c->accs[threadIdx.x][k];
+        c->acc[threadIdx.x] += x;
+    }
+    __syncwarp();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int g = 0; g < 2; g++) {
         const unsigned long long* s = c->acc + 6 * g;

@@ -45,6 +45,8 @@ enum {
     NBINS = 10
 };
 
+constexpr int ACC_STRIPES = 32;  // copies of each accumulator (spreads the atomics of many warps)
+
 // Device control block: sizes produced and consumed on the device, so a
 // batch's kernels never wait for the host between stages.
 struct Ctl {
@@ -78,6 +80,8 @@ struct Ctl {
     long long pend_nA2, pend_nD2;    // its kept directed insertion / deletion entries
     long long m_delta;               // net edges committed during a run
     unsigned long long last_out[6];  // counts after the current batch
+    // (device-only tail: the host mirror copies the block up to here)
+    unsigned long long accs[16][ACC_STRIPES];  // acc, striped: kernels add here, k_finalize sums
 };
 
 constexpr int TRI_KM = 512;
