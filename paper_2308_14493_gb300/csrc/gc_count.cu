@@ -658,7 +658,8 @@ __global__ void __launch_bounds__(256) k_c4_block(Ctl* c, const int32_t* __restr
 
 // Prefix sums of the row lengths of lower neighbours rb[s0 .. s0+ns) of a
 // pivot, so a pivot's wedges can be split evenly over many threads: wedge i
-// of the segment lies in row j = find_seg(pre, ns, i) at offset i - pre[j].
+// of the segment lies in row j = find_seg(pre, ns, i), at U_col[vbs[j] + i]
+// (vbs holds each row's start minus its prefix).
 // Every thread of the block calls it; ends with __syncthreads().
 __device__ __forceinline__ void wedge_segment_prefix(const long long* __restrict__ U_off,
                                                      const uint32_t* __restrict__ U_col, long long rb, int s0, int ns,
@@ -698,6 +699,9 @@ __device__ __forceinline__ void wedge_segment_prefix(const long long* __restrict
     }
     __syncthreads();
     for (int j = b0 + lane; j < b1; j += 32) pre[j + 1] += s_part[warp];
+    __syncthreads();
+    // rebase: wedge i of row j is U_col[vbs[j] + i]
+    for (int j = tid; j < ns; j += blockDim.x) vbs[j] -= pre[j];
     __syncthreads();
 }
 
@@ -836,23 +840,23 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                 // a single-segment pivot keeps its prefix for the clearing walk
                 if (pass == 0 || nlow > C4D_SEG)
                     wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
-                const long long total = s_tot;
+                const int total = s_tot;
                 if (pass == 0) wall += total;
                 // each warp takes C4D_UNROLL consecutive chunks of 32 wedges;
                 // a lane finds its row by stepping forward from the chunk's
                 // first row (rows average tens of entries, so a step or two)
-                const long long wstep = (long long)NW * 32 * C4D_UNROLL;
-                for (long long base = (long long)gwarp * 32 * C4D_UNROLL; base < total; base += wstep) {
+                const int wstep = NW * 32 * C4D_UNROLL;
+                for (int base = gwarp * 32 * C4D_UNROLL; base < total; base += wstep) {
                     uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
                     int j = find_seg(s_pre, ns, (int)base);
 #pragma unroll
                     for (int r = 0; r < C4D_UNROLL; r++) {
-                        long long i = base + r * 32 + lane;
+                        const int i = base + r * 32 + lane;
                         e[r] = 0xFFFFFFFFu;
                         f[r] = 0;
                         if (i < total) {
                             while (j + 1 < ns && s_pre[j + 1] <= i) j++;
-                            e[r] = U_col[s_vb[j] + (i - s_pre[j])];
+                            e[r] = U_col[s_vb[j] + i];
                             f[r] = s_fv[j];
                         }
                     }
@@ -1128,19 +1132,19 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
         for (int s0 = 0; s0 < nlow; s0 += C4D_SEG) {
             const int ns = min(C4D_SEG, nlow - s0);
             wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
-            const long long total = s_tot;
-            const long long wstep = (long long)NW * 32 * C4D_UNROLL;
-            for (long long base = (long long)warp * 32 * C4D_UNROLL; base < total; base += wstep) {
+            const int total = s_tot;
+            const int wstep = NW * 32 * C4D_UNROLL;
+            for (int base = warp * 32 * C4D_UNROLL; base < total; base += wstep) {
                 uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
                 int j = find_seg(s_pre, ns, (int)base);
 #pragma unroll
                 for (int r = 0; r < C4D_UNROLL; r++) {
-                    long long i = base + r * 32 + lane;
+                    const int i = base + r * 32 + lane;
                     e[r] = 0xFFFFFFFFu;
                     f[r] = 0;
                     if (i < total) {
                         while (j + 1 < ns && s_pre[j + 1] <= i) j++;
-                        e[r] = U_col[s_vb[j] + (i - s_pre[j])];
+                        e[r] = U_col[s_vb[j] + i];
                         f[r] = s_fv[j];
                     }
                 }
