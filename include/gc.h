@@ -240,9 +240,11 @@ typedef struct {
     int32_t c4_warp_max;    /* warp hash in shared memory       [512]   */
     int32_t c4_block_max;   /* block hash in shared memory      [8192]  */
     int64_t c4_cta_max;     /* per-CTA hash table in L2         [32768] */
-    int64_t c4_chunk_min;   /* above this: shared-memory counters over id-range chunks;
-                               otherwise a CTA cluster on a dense array in L2; 0 = never */
-    int64_t reserved[4];
+    int64_t c4_chunk_min;   /* above this and up to c4_chunk_max: shared-memory counters over
+                               id-range chunks; other pivots above c4_cta_max: a CTA cluster on a
+                               dense array in L2; 0 = never */
+    int64_t c4_chunk_max;   /* 0 = no upper bound */
+    int64_t reserved[3];
 } gc_tuning;
 
 int gc_get_tuning(const gc_graph *g, gc_tuning *t);

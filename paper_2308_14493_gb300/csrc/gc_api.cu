@@ -1459,6 +1459,7 @@ static void tuning_to_abi(const Tuning& t, gc_tuning* o) {
     o->c4_block_max = t.c4_block_max;
     o->c4_cta_max = t.c4_cta_max;
     o->c4_chunk_min = t.c4_chunk_min >= NEVER ? 0 : t.c4_chunk_min;
+    o->c4_chunk_max = t.c4_chunk_max >= NEVER ? 0 : t.c4_chunk_max;
 }
 
 int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
@@ -1470,7 +1471,7 @@ int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
 int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
     if (t->tri_warp_max < 1 || t->tri_small_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
-        t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0) {
+        t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0 || t->c4_chunk_max < 0) {
         g->err = "tuning: every bound must be positive (c4_chunk_min may be 0)";
         return GC_EINVAL;
     }
@@ -1483,6 +1484,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     n.c4_block_max = t->c4_block_max;
     n.c4_cta_max = t->c4_cta_max;
     n.c4_chunk_min = t->c4_chunk_min == 0 ? NEVER : t->c4_chunk_min;
+    n.c4_chunk_max = t->c4_chunk_max == 0 ? NEVER : t->c4_chunk_max;
     if (n.c4_chunk_min < NEVER && !ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     g->tune = n;
     return GC_OK;
@@ -1517,7 +1519,7 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     // (a bound below the tier beneath it empties the tier; the chunked
     // kernel only takes pivots above c4_cta_max, so lowering that one after
     // c4_chunk_min opens the chunked tier to medium pivots)
-    const long long cand[8][6] = {
+    const long long cand[9][6] = {
         {16, 32, -1, -1, -1, -1},                          // tri_warp_max
         {64, 128, -1, -1, -1, -1},                         // tri_small_max
         {256, 512, -1, -1, -1, -1},                        // tri_block_max
@@ -1525,7 +1527,8 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
         {128, 512, -1, -1, -1, -1},                        // c4_warp_max
         {512, 2048, 8192, -1, -1, -1},                     // c4_block_max
         {2048, 8192, 16384, 32768, -1, -1},                // c4_cta_max
-        {NEVER, 2048, 8192, 32768, 262144, 1048576}        // c4_chunk_min
+        {NEVER, 2048, 8192, 32768, 262144, 1048576},       // c4_chunk_min
+        {NEVER, 131072, 524288, 2097152, -1, -1}            // c4_chunk_max
     };
     auto field = [](Tuning& t, int i) -> long long {
         switch (i) {
@@ -1536,7 +1539,8 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
             case 4: return t.c4_warp_max;
             case 5: return t.c4_block_max;
             case 6: return t.c4_cta_max;
-            default: return t.c4_chunk_min;
+            case 7: return t.c4_chunk_min;
+            default: return t.c4_chunk_max;
         }
     };
     auto set = [](Tuning& t, int i, long long v) {
@@ -1548,14 +1552,15 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
             case 4: t.c4_warp_max = (int)v; break;
             case 5: t.c4_block_max = (int)v; break;
             case 6: t.c4_cta_max = v; break;
-            default: t.c4_chunk_min = v; break;
+            case 7: t.c4_chunk_min = v; break;
+            default: t.c4_chunk_max = v; break;
         }
     };
     const bool chunk_ok = c4_chunk_table_entries(std::max(g->n, 1)) > 0 && ensure_chunk_table(g);
     for (int sweep = 0; sweep < 3; sweep++) {
         bool moved = false;
-        for (int i = 7; i >= 0; i--) {
-            if (i == 7 && !chunk_ok) continue;
+        for (int i = 8; i >= 0; i--) {
+            if (i >= 7 && !chunk_ok) continue;
             for (int k = 0; k < 6; k++) {
                 const long long v = cand[i][k];
                 if (v < 0 || v == field(cur, i)) continue;

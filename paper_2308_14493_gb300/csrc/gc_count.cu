@@ -165,7 +165,7 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
                      : wt <= t.c4_warp_max                      ? BIN_C4_WARP
                      : wt <= t.c4_block_max                     ? BIN_C4_BLOCK
                      : (wt <= t.c4_cta_max && split < 65536)    ? BIN_C4_CTA
-                     : wt > t.c4_chunk_min                      ? BIN_C4_CHUNK
+                     : (wt > t.c4_chunk_min && wt <= t.c4_chunk_max) ? BIN_C4_CHUNK
                                                                 : BIN_C4_DENSE;
             }
         }
@@ -1330,6 +1330,8 @@ Tuning effective_tuning(const CountArgs& a) {
     t.c4_cta_max = std::max<long long>(t.c4_block_max, std::min<long long>(t.c4_cta_max, a.cta_table_words / 2));
     if (!a.chunk_table || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
     t.c4_chunk_min = std::max<long long>(t.c4_chunk_min, t.c4_cta_max);
+    if (t.c4_chunk_max <= 0) t.c4_chunk_max = NEVER;
+    if (t.c4_chunk_max <= t.c4_chunk_min) t.c4_chunk_min = NEVER;  // empty chunked bin
     return t;
 }
 

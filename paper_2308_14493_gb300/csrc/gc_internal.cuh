@@ -102,10 +102,11 @@ struct Tuning {
     int c4_warp_max;         // warp hash (<= C4_T1)
     int c4_block_max;        // block hash (<= C4_T2)
     long long c4_cta_max;    // global hash tables (<= half the table words)
-    long long c4_chunk_min;  // chunked shared-memory kernel above this (else cluster kernel)
+    long long c4_chunk_min;  // chunked shared-memory kernel above this ...
+    long long c4_chunk_max;  // ... and up to this (the cluster kernel takes the rest)
 };
 constexpr long long NEVER = 1ll << 62;
-inline Tuning default_tuning() { return Tuning{32, TRI_KS, TRI_KM, 32, C4_T1, C4_T2, C4_T3, NEVER}; }
+inline Tuning default_tuning() { return Tuning{32, TRI_KS, TRI_KM, 32, C4_T1, C4_T2, C4_T3, NEVER, NEVER}; }
 constexpr int C4_DENSE_THREADS = 1024;
 
 // Handle-independent launch geometry.

@@ -146,6 +146,8 @@ TUNINGS = {
     "c4_cta_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=32768),
     "c4_all_cluster": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=0),
     "c4_all_chunk": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=1),
+    "c4_chunk_then_cluster": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=1,
+                                  c4_chunk_max=2000),
 }
 
 
