@@ -201,37 +201,22 @@ static int grid_warps(gc_graph* g) { return 8 * g->sms; }  // 8 warps per block
 namespace gcx {
 
 // desc: [0] insertion pair base, [1] deletion pair base, then per batch
-// [ins_off, n_ins, del_off, n_del].  The batch index is the run cursor when
-// use_cursor is set, else 0.  A halted run (a commit waiting for pool space)
-// makes every later batch empty and inactive.
-struct BatchArg {
-    const int32_t* ins;
-    const int32_t* del;
-    long long n_ins, n_del;
-};
-
-__global__ void k_begin_batch(Ctl* c, const long long* desc, int use_cursor, BatchArg a) {
+// [ins_off, n_ins, del_off, n_del]; the batch is the one at the run cursor.
+// A halted run (a commit waiting for pool space) makes every later batch
+// empty and inactive.
+__global__ void k_begin_batch(Ctl* c, const long long* desc) {
     if (threadIdx.x != 0) return;
     const bool run = c->halt == 0;
     c->active = run ? 1 : 0;
-    if (use_cursor) {
-        // the descriptor is rewritten by host copies between runs: read it
-        // from L2, never through the read-only cache path
-        const long long* b = desc + 2 + 4 * (long long)c->cur;
-        c->pairs_ins = (const int32_t*)__ldcg(desc);
-        c->pairs_del = (const int32_t*)__ldcg(desc + 1);
-        c->ins_off = run ? __ldcg(b) : 0;
-        c->n_ins = run ? __ldcg(b + 1) : 0;
-        c->del_off = run ? __ldcg(b + 2) : 0;
-        c->n_del = run ? __ldcg(b + 3) : 0;
-    } else {
-        c->pairs_ins = a.ins;
-        c->pairs_del = a.del;
-        c->ins_off = 0;
-        c->del_off = 0;
-        c->n_ins = run ? a.n_ins : 0;
-        c->n_del = run ? a.n_del : 0;
-    }
+    // the descriptor is rewritten by host copies between calls: read it
+    // from L2, never through the read-only cache path
+    const long long* b = desc + 2 + 4 * (long long)c->cur;
+    c->pairs_ins = (const int32_t*)__ldcg(desc);
+    c->pairs_del = (const int32_t*)__ldcg(desc + 1);
+    c->ins_off = run ? __ldcg(b) : 0;
+    c->n_ins = run ? __ldcg(b + 1) : 0;
+    c->del_off = run ? __ldcg(b + 2) : 0;
+    c->n_del = run ? __ldcg(b + 3) : 0;
     c->nkeys = 2 * (c->n_ins + c->n_del);
     c->nA2 = c->nD2 = 0;
     for (int k = 0; k < 8; k++) c->st[k] = 0;
@@ -485,16 +470,16 @@ static int enqueue_segments(gc_graph* g, bool clear) {
     return GC_OK;
 }
 
-// One batch of Algorithm 2, all stages, on g->s.  Grids are sized for batches
-// of up to max_nk directed keys; the actual sizes are read on the device.
-//   use_cursor: take the batch from the run cursor (batched form)
+// One batch of Algorithm 2, all stages, on g->s, taken from the run cursor
+// of the device descriptor (captured once per batch shape, replayed per
+// batch).  Grids are sized for batches of up to max_nk directed keys; the
+// actual sizes are read on the device.
 //   commit:     apply G <- G \ D u A (else an independent what-if batch)
-//   timed:      record the stage events (not while capturing)
-static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool commit, bool timed,
-                         BatchArg arg = BatchArg{nullptr, nullptr, 0, 0}) {
+//   timed:      record the stage events (event-record nodes in the graph)
+static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
-    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc, use_cursor ? 1 : 0, arg);
+    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc);
     g->launches++;
     const long long nkb = std::max<long long>(max_nk, 1);
     const int ge = grid_elems(g, nkb);
@@ -538,10 +523,8 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool use_cursor, bool co
         rc = enqueue_segments(g, true);
         if (rc) return rc;
     }
-    if (use_cursor) {
-        k_end_batch<<<1, 32, 0, s>>>(g->ctl, g->out_dev.p, commit ? 1 : 0);
-        g->launches++;
-    }
+    k_end_batch<<<1, 32, 0, s>>>(g->ctl, g->out_dev.p, commit ? 1 : 0);
+    g->launches++;
     CKL();
     return GC_OK;
 }
@@ -671,7 +654,7 @@ static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool time
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const int lsave = g->launches;
     g->launches = 0;
-    int rc = enqueue_batch(g, shape_nk, true, commit, timed);
+    int rc = enqueue_batch(g, shape_nk, commit, timed);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     *launches = g->launches;
     g->launches = lsave;
@@ -814,30 +797,8 @@ static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t
     CKL();
     // (re)capture the per-batch graph when its shape or any buffer changed
     if (!g->gexec || g->g_nk != shape_nk || g->g_commit != (int)commit || g->g_gen != g->buf_gen) {
-        if (g->gexec) {
-            cudaGraphExecDestroy(g->gexec);
-            g->gexec = nullptr;
-        }
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        int lsave = g->launches;
-        g->launches = 0;
-        rc = enqueue_batch(g, shape_nk, true, commit, false);
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        g->g_launches = g->launches;
-        g->launches = lsave;
+        rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches);
         if (rc) return rc;
-        if (ce != cudaSuccess) {
-            g->err = std::string("graph capture: ") + cudaGetErrorString(ce);
-            return GC_ECUDA;
-        }
-        ce = cudaGraphInstantiate(&g->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) {
-            g->gexec = nullptr;
-            g->err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
-            return GC_ECUDA;
-        }
         g->g_nk = shape_nk;
         g->g_commit = (int)commit;
         g->g_gen = g->buf_gen;
@@ -853,24 +814,10 @@ static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t
             // batch done-1 is counted but its commit waits for pool space
             rc = finish_pending_commit(g, &relayouts);
             if (rc) return rc;
-            if (g->gexec && g->g_gen != g->buf_gen) {
+            if (g->g_gen != g->buf_gen) {
                 // the adjacency moved: capture again for the remaining batches
-                cudaGraphExecDestroy(g->gexec);
-                g->gexec = nullptr;
-                cudaGraph_t graph = nullptr;
-                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                int lsave = g->launches;
-                rc = enqueue_batch(g, shape_nk, true, commit, false);
-                cudaError_t ce = cudaStreamEndCapture(s, &graph);
-                g->launches = lsave;
+                rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches);
                 if (rc) return rc;
-                if (ce != cudaSuccess || cudaGraphInstantiate(&g->gexec, graph, 0) != cudaSuccess) {
-                    if (graph) cudaGraphDestroy(graph);
-                    g->gexec = nullptr;
-                    g->err = "graph capture after re-layout failed";
-                    return GC_ECUDA;
-                }
-                cudaGraphDestroy(graph);
                 g->g_gen = g->buf_gen;
             }
         }

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_
 constexpr int C4B_SLOTS = 2 * C4_T2;
 size_t c4_block_smem_bytes() { return (size_t)C4B_SLOTS * 8; }
 
-__global__ void __launch_bounds__(256) k_c4_block(Ctl* c, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, 4) k_c4_block(Ctl* c, const int32_t* __restrict__ list,
                                                  const long long* __restrict__ U_off,
                                                  const uint32_t* __restrict__ U_col,
                                                  const int32_t* __restrict__ U_split) {
@@ -730,14 +730,16 @@ __device__ __forceinline__ void group_sync() {
 // Heavy pivots, dense counter array in global memory (16/16-bit packed
 // counts while every degree is below 2^16, else 32/32 in 64-bit words).
 // CLUSTER = true: a cluster of CTAs takes one pivot at a time and shares one
-// array (the heaviest pivots); CLUSTER = false: one CTA per pivot with its
-// own array (the medium ones).  The pivot's wedges are numbered through
-// per-segment prefix sums and dealt in warp-contiguous chunks to every
-// thread of the group (coalesced, balanced even when one lower neighbour has
-// a very long row).  After the increments a group barrier; then the array is
-// cleared, by a vectorised fill of the whole array when the pivot touched a
-// large part of it, else by walking the same wedges again; then another
-// barrier.
+// array (the instance launched); CLUSTER = false: one CTA per pivot with its
+// own array.  The pivot's wedges are numbered through per-segment prefix
+// sums and dealt in warp-contiguous chunks to every thread of the group
+// (coalesced, balanced even when one lower neighbour has a very long row).
+// Two ways through a pivot, each ending with group barriers:
+//   w~ > u / 8 (many wedges for its id range): increments by L2 reductions,
+//     then one coalesced sweep of the counters of [0, u) that adds C(c_w, 2)
+//     and clears them;
+//   otherwise: increments that return the old value (summed on the fly),
+//     then the same wedges walked again to clear what they touched.
 template <bool CLUSTER>
 __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, const int32_t* __restrict__ list,
                                                                 const long long* __restrict__ U_off,
@@ -792,7 +794,6 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
         // coalesced: each c_w gives C(c_w, 2) and is cleared.  Smaller
         // pivots take old values and clear by walking their wedges again.
         const bool sweep = U_wt[u] * 8 > (long long)u;
-        long long wall = 0;  // wedge entries of the pivot (all rows, any id)
         for (int pass = 0; pass < 2; pass++) {
             // pass 0: increments; pass 1: sweep, or clear by walking
             if (pass == 1) {
@@ -826,14 +827,6 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                     }
                     break;
                 }
-                if (wall * 8 > n) {
-                    const long long words = wide ? (long long)n : ((long long)n + 1) / 2;  // 64-bit words
-                    uint4* a4 = (uint4*)a64;
-                    const long long n16 = words / 2;
-                    for (long long i = g; i < n16; i += T) a4[i] = make_uint4(0, 0, 0, 0);
-                    if ((words & 1) && g == 0) a64[words - 1] = 0ull;
-                    break;
-                }
             }
             for (int s0 = 0; s0 < nlow; s0 += C4D_SEG) {
                 const int ns = min(C4D_SEG, nlow - s0);
@@ -841,7 +834,6 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                 if (pass == 0 || nlow > C4D_SEG)
                     wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
                 const int total = s_tot;
-                if (pass == 0) wall += total;
                 // each warp takes C4D_UNROLL consecutive chunks of 32 wedges;
                 // a lane finds its row by stepping forward from the chunk's
                 // first row (rows average tens of entries, so a step or two)
