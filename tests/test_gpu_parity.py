@@ -182,6 +182,31 @@ def test_autotune_keeps_counts(gcb):
         assert g.apply(ins, dels) == r["F"]
 
 
+def _two_big_hubs():
+    """Two hubs sharing 66,000 neighbours (degrees above 2^16, so one pair
+    has 66,000 common neighbours) over a sparse background: the 4-cycle
+    counters must switch to 32-bit halves."""
+    n = 70000
+    keys = set(int(k) for k in gen.er_graph(n, 40000, 41))
+    for h in (0, 1):
+        for v in range(2, 66002):
+            keys.add((h << 32) | v)
+    return n, np.array(sorted(keys), dtype=np.uint64)
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(chunk_threshold=1)], ids=["cluster", "chunked"])
+def test_hubs_beyond_16_bit_counts(gcb, opts):
+    n, keys = _two_big_hubs()
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.random_batch(n, keys, 300, 300, 42)
+    r = oracle.fdgc_step(rp, col, ins, dels, F0)
+    with open_graph(gcb, n, rp, col, **opts) as g:
+        assert g.counts() == F0
+        assert g.apply(ins, dels) == r["F"]
+        assert mod64(g.stats()["sums_a"]) == mod64(r["sums_a"])
+
+
 @pytest.mark.parametrize("name", ["c1", "c2"])
 def test_static_workload_graphs(gcb, name):
     n, keys = gen.workload_graph(name)
