@@ -841,15 +841,28 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                 for (int base = gwarp * 32 * C4D_UNROLL; base < total; base += wstep) {
                     uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
                     int j = find_seg(s_pre, ns, (int)base);
+                    const int end = min(total, base + 32 * C4D_UNROLL);
+                    if (j + 1 >= ns || s_pre[j + 1] >= end) {
+                        // the whole chunk lies in one row: its base and flags are uniform
+                        const long long vb = s_vb[j];
+                        const uint32_t fv = s_fv[j];
 #pragma unroll
-                    for (int r = 0; r < C4D_UNROLL; r++) {
-                        const int i = base + r * 32 + lane;
-                        e[r] = 0xFFFFFFFFu;
-                        f[r] = 0;
-                        if (i < total) {
-                            while (j + 1 < ns && s_pre[j + 1] <= i) j++;
-                            e[r] = U_col[s_vb[j] + i];
-                            f[r] = s_fv[j];
+                        for (int r = 0; r < C4D_UNROLL; r++) {
+                            const int i = base + r * 32 + lane;
+                            e[r] = i < total ? U_col[vb + i] : 0xFFFFFFFFu;
+                            f[r] = fv;
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < C4D_UNROLL; r++) {
+                            const int i = base + r * 32 + lane;
+                            e[r] = 0xFFFFFFFFu;
+                            f[r] = 0;
+                            if (i < total) {
+                                while (j + 1 < ns && s_pre[j + 1] <= i) j++;
+                                e[r] = U_col[s_vb[j] + i];
+                                f[r] = s_fv[j];
+                            }
                         }
                     }
 #pragma unroll
@@ -1129,15 +1142,27 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
             for (int base = warp * 32 * C4D_UNROLL; base < total; base += wstep) {
                 uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
                 int j = find_seg(s_pre, ns, (int)base);
+                const int end = min(total, base + 32 * C4D_UNROLL);
+                if (j + 1 >= ns || s_pre[j + 1] >= end) {
+                    const long long vb = s_vb[j];
+                    const uint32_t fv = s_fv[j];
 #pragma unroll
-                for (int r = 0; r < C4D_UNROLL; r++) {
-                    const int i = base + r * 32 + lane;
-                    e[r] = 0xFFFFFFFFu;
-                    f[r] = 0;
-                    if (i < total) {
-                        while (j + 1 < ns && s_pre[j + 1] <= i) j++;
-                        e[r] = U_col[s_vb[j] + i];
-                        f[r] = s_fv[j];
+                    for (int r = 0; r < C4D_UNROLL; r++) {
+                        const int i = base + r * 32 + lane;
+                        e[r] = i < total ? U_col[vb + i] : 0xFFFFFFFFu;
+                        f[r] = fv;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < C4D_UNROLL; r++) {
+                        const int i = base + r * 32 + lane;
+                        e[r] = 0xFFFFFFFFu;
+                        f[r] = 0;
+                        if (i < total) {
+                            while (j + 1 < ns && s_pre[j + 1] <= i) j++;
+                            e[r] = U_col[s_vb[j] + i];
+                            f[r] = s_fv[j];
+                        }
                     }
                 }
 #pragma unroll
