@@ -94,6 +94,8 @@ typedef struct {
     int64_t work_wedges;            /* wedges u-v-w (v, w below u) walked for the 4-cycles */
     int32_t launches;               /* kernels the call launched */
     int32_t reserved2[3];
+    int64_t C3a[2], C3b[2];         /* 3-vertex counts of G_a and G_b: [0] induced 2-paths
+                                       (open wedges), [1] triangles */
 } gc_stats;
 
 /* Fill *opt with the defaults. */
@@ -121,6 +123,13 @@ int gc_count_static(gc_graph *g, uint64_t out[6]);
 /* The maintained counts. */
 int gc_counts(const gc_graph *g, uint64_t out[6]);
 
+/* The maintained 3-vertex graphlet counts, a by-product of the same per-edge
+   triangle counts and degrees (Sec. 3 notes PGD yields them too):
+   out[0] induced 2-paths (open wedges) = sum_v C(d_v, 2) - 3 triangles,
+   out[1] triangles.  They follow every batch exactly as the 4-vertex
+   counts do (F3 += C3_a - C3_b). */
+int gc_counts3(const gc_graph *g, uint64_t out[2]);
+
 /*
  * Apply one batch (Algorithm 2) and return the updated counts.
  *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)
@@ -132,6 +141,16 @@ int gc_counts(const gc_graph *g, uint64_t out[6]);
  */
 int gc_apply_batch(gc_graph *g, const int32_t *ins, int64_t n_ins,
                    const int32_t *del, int64_t n_del, uint64_t out[6]);
+
+/*
+ * Delete vertices (Sec. 3 models a vertex deletion as the deletion of its
+ * edges): every edge incident to ids[0..k) is deleted in one batch, applied
+ * as gc_apply_batch would; the vertices stay, isolated (n is fixed at open:
+ * a vertex to be inserted later is opened as an isolated id and gains its
+ * edges by gc_apply_batch).  Ids outside [0, n) give GC_EINVAL and change
+ * nothing; repeated ids are allowed.  out: counts after the deletion.
+ */
+int gc_delete_vertices(gc_graph *g, const int32_t *ids, int64_t k, uint64_t out[6]);
 
 /* As gc_apply_batch, with the pair arrays in device memory (int32, same
    layout).  The caller guarantees every id is in [0, n) and no pair is a

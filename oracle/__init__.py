@@ -4,10 +4,11 @@ TEST INFRASTRUCTURE ONLY.  Nothing in the library path imports this package:
 only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may use it.  It shares no code with the CUDA library.
 
-* ``brute``  -- census of every 4-subset (n <= 40), the plain definition.
+* ``brute``  -- census of every 4-subset (n <= 40) and every 3-subset
+  (n <= 60), the plain definitions.
 * ``oracle`` -- plain single-threaded C (``gc_oracle.c``): literal and
-  degree-oriented static counts, batch normalisation and one literal step of
-  Algorithm 2 (FDGC).
+  degree-oriented static counts, the 3-vertex counts, batch normalisation and
+  one literal step of Algorithm 2 (FDGC).
 """
 from . import brute  # noqa: F401
 from .oracle import (  # noqa: F401
@@ -19,6 +20,7 @@ from .oracle import (  # noqa: F401
     fdgc_step,
     normalize,
     static_counts,
+    static_counts3,
     sums_literal,
     sums_oriented,
 )

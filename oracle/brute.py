@@ -59,3 +59,24 @@ def graphlet_counts(n: int, edges) -> list[int]:
     """[g1, g2, g3, g4, g5, g6] by brute force."""
     h = census(n, edges)
     return [h[c] for c in CONNECTED]
+
+
+def census3(n: int, edges) -> dict[str, int]:
+    """Histogram of the induced 3-vertex classes over all C(n,3) subsets:
+    'empty', 'edge', 'path' (2 edges, the open wedge), 'triangle'."""
+    if n > 60:
+        raise ValueError("brute force is for n <= 60")
+    adj = [[False] * n for _ in range(n)]
+    for a, b in edges:
+        adj[a][b] = adj[b][a] = True
+    names = ("empty", "edge", "path", "triangle")
+    hist = {k: 0 for k in names}
+    for a, b, c in itertools.combinations(range(n), 3):
+        hist[names[adj[a][b] + adj[a][c] + adj[b][c]]] += 1
+    return hist
+
+
+def graphlet3_counts(n: int, edges) -> list[int]:
+    """[induced 2-paths, triangles] by the census."""
+    h = census3(n, edges)
+    return [h["path"], h["triangle"]]

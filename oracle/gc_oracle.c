@@ -99,6 +99,33 @@ void or_counts_from_sums(const int64_t *s, int64_t *c) {
 /* count by PGD's per-edge rule (only when with_ic4 != 0, else -1):          */
 /*   IC4 = 1/4 sum_{uv in E} #{(w,x): w in N(u)\N[v], x in N(v)\N[u], wx in E} */
 /* ------------------------------------------------------------------------ */
+/* 3-vertex graphlets (the by-product of PGD's per-edge triangle counts and
+ * degrees, Sec. 3): out[0] induced 2-paths, out[1] triangles.
+ * Triangles: every edge u < v adds |N(u) n N(v)| (a merge of the two sorted
+ * rows); each triangle is seen from its three edges.  2-paths: every vertex
+ * centres C(d, 2) pairs of its edges, of which the closed ones are the
+ * triangle corners (three per triangle). */
+int or_counts3(int64_t n, const int64_t *rp, const int32_t *col, int64_t *out) {
+    ograph g = {n, rp, col};
+    int64_t wedges = 0, tsum = 0;
+    for (int64_t u = 0; u < n; u++) {
+        wedges += choose2(deg_of(&g, u));
+        for (int64_t i = g.rp[u]; i < g.rp[u + 1]; i++) {
+            int64_t v = g.col[i];
+            if (v <= u) continue;
+            int64_t a = g.rp[u], b = g.rp[v];
+            while (a < g.rp[u + 1] && b < g.rp[v + 1]) {
+                if (g.col[a] < g.col[b]) a++;
+                else if (g.col[a] > g.col[b]) b++;
+                else { tsum++; a++; b++; }
+            }
+        }
+    }
+    out[0] = wedges - tsum;
+    out[1] = tsum / 3;
+    return 0;
+}
+
 int or_sums_literal(int64_t n, const int64_t *rp, const int32_t *col, int with_ic4, int64_t *out) {
     ograph g = {n, rp, col};
     int64_t P = 0, S = 0, TT2 = 0, D = 0, K6 = 0, Q2 = 0, IC4x4 = 0;

@@ -44,6 +44,7 @@ def _load():
             I64 = ctypes.c_int64
             lib.or_sums_literal.argtypes = [I64, i64p, i32p, ctypes.c_int, i64p]
             lib.or_sums_oriented.argtypes = [I64, i64p, i32p, i64p]
+            lib.or_counts3.argtypes = [I64, i64p, i32p, i64p]
             lib.or_counts_from_sums.argtypes = [i64p, i64p]
             lib.or_counts_from_sums.restype = None
             lib.or_normalize.argtypes = [I64, i64p, i32p, i32p, I64, i32p, I64, u64p, i64p, u64p, i64p, i64p]
@@ -103,6 +104,17 @@ def static_counts(row_ptr, col, variant: str = "oriented") -> list[int]:
     """Induced graphlet counts [g1..g6] of a whole graph."""
     s = sums_literal(row_ptr, col) if variant == "literal" else sums_oriented(row_ptr, col)
     return counts_from_sums(s)
+
+
+def static_counts3(row_ptr, col) -> list[int]:
+    """Induced 3-vertex counts [2-paths, triangles] of a whole graph (the
+    by-product of the per-edge triangle counts and degrees, Sec. 3)."""
+    rp, c = _csr(row_ptr, col)
+    n = rp.size - 1
+    out = np.zeros(2, np.int64)
+    if _load().or_counts3(n, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32), _p(out, ctypes.c_int64)) != 0:
+        raise RuntimeError("or_counts3 failed")
+    return [int(x) for x in out]
 
 
 def normalize(row_ptr, col, ins, dels):

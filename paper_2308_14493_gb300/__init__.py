@@ -17,6 +17,7 @@ from .gc import (  # noqa: F401
     gc_close,
     gc_count_batch,
     gc_count_batch_device,
+    gc_delete_vertices,
     gc_count_static,
     gc_count_static_noalloc,
     gc_device_bytes,
@@ -32,6 +33,7 @@ from .gc import (  # noqa: F401
     gc_server_counters,
     gc_server_close,
     gc_counts,
+    gc_counts3,
     gc_export_csr,
     gc_last_error,
     gc_num_edges,

@@ -80,6 +80,8 @@ struct gc_graph {
     Buf<long long> posA, posD, plan_dst, plan_scr, bsum;
     Buf<uint32_t> hist;
     Buf<unsigned long long> out_dev;     // per-batch results of a batched run
+    Buf<int32_t> vids, vdeg;             // vertex deletion: ids and their degrees
+    Buf<long long> voff;                 // vertex deletion: pair offsets
     Buf<unsigned long long> dense;       // counter arrays of the heaviest 4-cycle pivots (per cluster)
     int dense_clusters = 0;
     int dense_cluster_size = 8;
@@ -103,6 +105,7 @@ struct gc_graph {
     unsigned long long buf_gen = 1;      // bumped whenever a buffer moves
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
+    uint64_t F3[2] = {0, 0};  // maintained 3-vertex counts: induced 2-paths, triangles
     long long m = 0;
     gc_stats st{};
     std::string err;
@@ -264,8 +267,36 @@ __global__ void k_commit_reset(Ctl* c, unsigned long long pool_tail, int set_poo
     if (set_pool) c->pool_tail = pool_tail;
 }
 
+// Vertex deletion as an edge batch: the degrees of the listed vertices, then
+// every incident edge as an (external id) pair.
+__global__ void k_vertex_degrees(const int32_t* __restrict__ ids, long long k, const int32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ deg, int32_t* __restrict__ vdeg) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k; i += (long long)gridDim.x * blockDim.x)
+        vdeg[i] = deg[perm[ids[i]]];
+}
+__global__ void k_vertex_pairs(const int32_t* __restrict__ ids, long long k, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ iperm, const long long* __restrict__ row_start,
+                               const int32_t* __restrict__ deg, const int32_t* __restrict__ col,
+                               const long long* __restrict__ off, int32_t* __restrict__ pairs) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < k; i += nwarps) {
+        const int32_t v = ids[i];
+        const int32_t iv = perm[v];
+        const long long rb = row_start[iv];
+        const int d = deg[iv];
+        int32_t* o = pairs + 2 * off[i];
+        for (int j = lane; j < d; j += 32) {
+            o[2 * j] = v;
+            o[2 * j + 1] = iperm[col[rb + j]];
+        }
+    }
+}
+
 __global__ void k_set_F(Ctl* c) {
     if (threadIdx.x < 6) c->F[threadIdx.x] = (unsigned long long)c->Ca[threadIdx.x];
+    if (threadIdx.x < 2) c->F3[threadIdx.x] = (unsigned long long)c->C3a[threadIdx.x];
 }
 
 __global__ void k_mark_active(Ctl* c) {
@@ -639,6 +670,10 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
         t.sums_a[i] = c.sa[i];
         t.sums_b[i] = c.sb[i];
     }
+    for (int i = 0; i < 2; i++) {
+        t.C3a[i] = c.C3a[i];
+        t.C3b[i] = c.C3b[i];
+    }
 }
 
 // Capture the per-batch launch sequence (batch from the run cursor) into
@@ -739,6 +774,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     stage_times(g, 0, 7);
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
+        for (int i = 0; i < 2; i++) g->F3[i] = c.F3[i];
         g->m += c.nA2 / 2 - c.nD2 / 2;
     }
     g->st.num_edges = g->m;
@@ -831,6 +867,7 @@ static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t
     const Ctl& c = *g->h_ctl;
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
+        for (int i = 0; i < 2; i++) g->F3[i] = c.F3[i];
         g->m += c.m_delta;
     }
     if (out)
@@ -868,6 +905,7 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
         for (int i = 0; i < 6; i++) out[i] = (uint64_t)g->h_ctl->Ca[i];
     if (set_F)
         for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
+        for (int i = 0; i < 2; i++) g->F3[i] = (uint64_t)g->h_ctl->C3a[i];
     // a static count leaves its stage times in the stats record
     stage_times(g, 2, 6);
     if (cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]) != cudaSuccess) cudaGetLastError();
@@ -914,6 +952,9 @@ static void destroy(gc_graph* g) {
     release(g, g->bsum);
     release(g, g->hist);
     release(g, g->out_dev);
+    release(g, g->vids);
+    release(g, g->vdeg);
+    release(g, g->voff);
     release(g, g->dense);
     release(g, g->cta_tables);
     release(g, g->chunk_table);
@@ -1226,6 +1267,13 @@ int gc_count_static(gc_graph* g, uint64_t out[6]) {
     return count_static(g, false, out);
 }
 
+int gc_counts3(const gc_graph* g, uint64_t out[2]) {
+    if (!g || !out) return GC_EINVAL;
+    out[0] = g->F3[0];
+    out[1] = g->F3[1];
+    return GC_OK;
+}
+
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;
     for (int i = 0; i < 6; i++) out[i] = g->F[i];
@@ -1295,6 +1343,45 @@ int gc_apply_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, cons
 int gc_count_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, const int32_t* d_del, int64_t n_del,
                           uint64_t out[6]) {
     return batch_device(g, d_ins, n_ins, d_del, n_del, 0, out);
+}
+
+int gc_delete_vertices(gc_graph* g, const int32_t* ids, int64_t k, uint64_t out[6]) {
+    if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    g->err.clear();
+    if (k < 0 || (k > 0 && !ids)) {
+        g->err = "vertex list: negative size or NULL pointer";
+        return GC_EINVAL;
+    }
+    for (int64_t i = 0; i < k; i++)
+        if (ids[i] < 0 || ids[i] >= g->n) {
+            g->err = "vertex id outside [0, n)";
+            return GC_EINVAL;
+        }
+    cudaStream_t s = g->s;
+    const size_t kk = (size_t)std::max<int64_t>(k, 1);
+    if (!ensure(g, g->vids, kk) || !ensure(g, g->vdeg, kk) || !ensure(g, g->voff, kk + 1))
+        return nomem(g, "vertex list");
+    long long total = 0;
+    if (k > 0) {
+        CK(cudaMemcpyAsync(g->vids.p, ids, 4 * (size_t)k, cudaMemcpyHostToDevice, s));
+        k_vertex_degrees<<<grid_elems(g, k), TPB, 0, s>>>(g->vids.p, k, g->perm, g->deg, g->vdeg.p);
+        CKL();
+        scan_i32_to_i64(g->vdeg.p, g->voff.p, nullptr, k, g->bsum.p, scan_grid(k, g->sms), nullptr, s);
+        CK(cudaMemcpyAsync(&total, g->voff.p + k, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(total, 1))) return nomem(g, "vertex edges");
+    if (total > 0) {
+        k_vertex_pairs<<<grid_warps(g), TPB, 0, s>>>(g->vids.p, k, g->perm, g->iperm, g->row_start, g->deg, g->col,
+                                                     g->voff.p, g->pairs.p);
+        CKL();
+    }
+    // an edge between two listed vertices appears twice; normalisation collapses it
+    return apply_device(g, g->pairs.p, 0, g->pairs.p, total, 1, out);
 }
 
 int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_ins, const int32_t* const* del,

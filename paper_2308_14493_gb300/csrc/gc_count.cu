@@ -52,8 +52,8 @@ namespace gcx {
 
 __global__ void k_reset_count(Ctl* c) {
     int t = threadIdx.x;
-    if (t < 16) c->acc[t] = 0;
-    for (int i = t; i < 16 * ACC_STRIPES; i += blockDim.x) (&c->accs[0][0])[i] = 0;
+    if (t < NACC) c->acc[t] = 0;
+    for (int i = t; i < NACC * ACC_STRIPES; i += blockDim.x) (&c->accs[0][0])[i] = 0;
     if (t < 8) c->work[t] = 0;
     if (t < NBINS) c->nbin[t] = 0;
     if (t == 0) c->maxdeg = 0;
@@ -1200,12 +1200,15 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long P[2] = {0, 0}, S[2] = {0, 0}, T[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0}, work = 0;
+    unsigned long long T3[2] = {0, 0}, W2[2] = {0, 0};  // sum of t_e; sum of C(d, 2)
     for (int wi = warp; wi < nW; wi += nwarps) {
         int32_t u = wlist[wi];
         long long dau = da[u], dbu = db[u];
         if (lane == 0) {
             S[0] += choose3((unsigned long long)dau);
             S[1] += choose3((unsigned long long)dbu);
+            W2[0] += choose2((unsigned long long)dau);
+            W2[1] += choose2((unsigned long long)dbu);
         }
         long long ob = U_off[u] + U_split[u], oe = U_off[u + 1];
         for (long long e = ob + lane; e < oe; e += 32) {
@@ -1218,6 +1221,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
                 P[0] += (unsigned long long)((dau - 1) * (dv - 1) - tt);
                 T[0] += (unsigned long long)(tt * (dau + dv - 4));
                 D[0] += choose2((unsigned long long)tt);
+                T3[0] += (unsigned long long)tt;
                 E[0] += 1;
             }
             if (fe & FLAG_B) {
@@ -1225,6 +1229,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
                 P[1] += (unsigned long long)((dbu - 1) * (dv - 1) - tt);
                 T[1] += (unsigned long long)(tt * (dbu + dv - 4));
                 D[1] += choose2((unsigned long long)tt);
+                T3[1] += (unsigned long long)tt;
                 E[1] += 1;
             }
         }
@@ -1233,6 +1238,8 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
     for (int g = 0; g < 2; g++) {
         P[g] = warp_sum_u64(P[g]);
         S[g] = warp_sum_u64(S[g]);
+        T3[g] = warp_sum_u64(T3[g]);
+        W2[g] = warp_sum_u64(W2[g]);
         T[g] = warp_sum_u64(T[g]);
         D[g] = warp_sum_u64(D[g]);
         E[g] = warp_sum_u64(E[g]);
@@ -1244,6 +1251,8 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
         acc_add_warp(c, o + 2, T[g]);
         acc_add_warp(c, o + 3, D[g]);
         acc_add_warp(c, 12 + g, E[g]);
+        acc_add_warp(c, 16 + g, T3[g]);
+        acc_add_warp(c, 18 + g, W2[g]);
     }
     acc_add(c, 14, work);
 }
@@ -1252,7 +1261,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
 __global__ void k_finalize(Ctl* c, int mode) {
     // fold the striped accumulators (one warp: lane i sums slot i's copies
     // and slot i + 16's if any)
-    if (blockIdx.x == 0 && threadIdx.x < 16) {
+    if (blockIdx.x == 0 && threadIdx.x < NACC) {
         unsigned long long x = 0;
         for (int k = 0; k < ACC_STRIPES; k++) x += c->accs[threadIdx.x][k];
         c->acc[threadIdx.x] += x;
@@ -1281,6 +1290,19 @@ __global__ void k_finalize(Ctl* c, int mode) {
         unsigned long long d = (unsigned long long)(c->Ca[i] - c->Cb[i]);
         if (mode == 0 && ok) c->F[i] += d;
         c->last_out[i] = mode == 2 ? c->F[i] + d : c->F[i];
+    }
+    // 3-vertex graphlets from the same sums: triangles = (sum t_e) / 3,
+    // induced 2-paths = sum C(d, 2) - 3 triangles
+    for (int g = 0; g < 2; g++) {
+        long long* C3 = g == 0 ? c->C3a : c->C3b;
+        const unsigned long long t3 = c->acc[16 + g], w2 = c->acc[18 + g];
+        C3[0] = (long long)(w2 - t3);
+        C3[1] = (long long)(t3 / 3);
+    }
+    for (int i = 0; i < 2; i++) {
+        unsigned long long d = (unsigned long long)(c->C3a[i] - c->C3b[i]);
+        if (mode == 0 && ok) c->F3[i] += d;
+        c->last_out3[i] = mode == 2 ? c->F3[i] + d : c->F3[i];
     }
 }
 

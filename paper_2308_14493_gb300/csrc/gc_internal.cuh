@@ -46,6 +46,7 @@ enum {
 };
 
 constexpr int ACC_STRIPES = 32;  // copies of each accumulator (spreads the atomics of many warps)
+constexpr int NACC = 20;         // accumulator slots (see Ctl::acc)
 
 // Device control block: sizes produced and consumed on the device, so a
 // batch's kernels never wait for the host between stages.
@@ -57,8 +58,10 @@ struct Ctl {
     int nW;                          // region size
     int lvl[MAX_HOPS + 2];           // lvl[L]: end of BFS level L in the region list
     long long nU;                    // entries of the region union graph
-    unsigned long long acc[16];      // [0..5] sums of G_a, [6..11] sums of G_b: P, S, 2TT, D, K, Q
+    unsigned long long acc[NACC];    // [0..5] sums of G_a, [6..11] sums of G_b: P, S, 2TT, D, K, Q
                                      // [12] |E(G_a)|, [13] |E(G_b)|, [14] triangle work, [15] wedges
+                                     // [16] sum of t_e in G_a (3 triangles), [17] in G_b,
+                                     // [18] sum C(d,2) in G_a (2-paths), [19] in G_b
     unsigned long long F[6];         // maintained counts
     long long Ca[6], Cb[6];          // induced counts of G_a, G_b of the last pass
     long long sa[6], sb[6];          // their non-induced sums (TT halved)
@@ -80,8 +83,12 @@ struct Ctl {
     long long pend_nA2, pend_nD2;    // its kept directed insertion / deletion entries
     long long m_delta;               // net edges committed during a run
     unsigned long long last_out[6];  // counts after the current batch
+    // 3-vertex graphlets, [0] induced 2-path (open wedge), [1] triangle
+    unsigned long long F3[2];        // maintained
+    long long C3a[2], C3b[2];        // of G_a, G_b of the last pass
+    unsigned long long last_out3[2]; // after the current batch
     // (device-only tail: the host mirror copies the block up to here)
-    unsigned long long accs[16][ACC_STRIPES];  // acc, striped: kernels add here, k_finalize sums
+    unsigned long long accs[NACC][ACC_STRIPES];  // acc, striped: kernels add here, k_finalize sums
 };
 
 constexpr int TRI_KM = 512;

@@ -43,7 +43,8 @@ class gc_stats(ctypes.Structure):
                 ("sums_b", ctypes.c_int64 * 6), ("num_edges", ctypes.c_int64), ("ms_device", ctypes.c_float),
                 ("ms_wall", ctypes.c_float), ("relayouts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
                 ("ms_stage", ctypes.c_float * 8), ("work_triangles", ctypes.c_int64),
-                ("work_wedges", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved2", ctypes.c_int32 * 3)]
+                ("work_wedges", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved2", ctypes.c_int32 * 3),
+                ("C3a", ctypes.c_int64 * 2), ("C3b", ctypes.c_int64 * 2)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -103,6 +104,8 @@ def load():
             lib.gc_open.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.POINTER(gc_options), ctypes.POINTER(P)]
             lib.gc_count_static.argtypes = [P, u64p]
             lib.gc_counts.argtypes = [P, u64p]
+            lib.gc_counts3.argtypes = [P, u64p]
+            lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
             lib.gc_apply_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
             lib.gc_apply_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
             lib.gc_count_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
@@ -190,6 +193,22 @@ def gc_count_static(h) -> list[int]:
 def gc_counts(h) -> list[int]:
     out = np.zeros(6, np.uint64)
     _check(load().gc_counts(h, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_counts3(h) -> list[int]:
+    """Maintained 3-vertex counts: [induced 2-paths, triangles]."""
+    out = np.zeros(2, np.uint64)
+    _check(load().gc_counts3(h, _ptr(out, ctypes.c_uint64)), h)
+    return [int(x) for x in out]
+
+
+def gc_delete_vertices(h, ids) -> list[int]:
+    """Delete every edge of the given vertices (one batch); counts after."""
+    a = _i32(np.asarray(ids, dtype=np.int32).reshape(-1)) if ids is not None else np.zeros(0, np.int32)
+    buf = a if a.size else np.zeros(1, np.int32)
+    out = np.zeros(6, np.uint64)
+    _check(load().gc_delete_vertices(h, _ptr(buf), a.size, _ptr(out, ctypes.c_uint64)), h)
     return [int(x) for x in out]
 
 
@@ -428,6 +447,9 @@ class Graph:
     def counts(self):
         return gc_counts(self.h)
 
+    def counts3(self):
+        return gc_counts3(self.h)
+
     def count_static(self):
         return gc_count_static(self.h)
 
@@ -436,6 +458,9 @@ class Graph:
 
     def count_batch(self, ins, dels):
         return gc_count_batch(self.h, ins, dels)
+
+    def delete_vertices(self, ids):
+        return gc_delete_vertices(self.h, ids)
 
     def apply_many(self, batches, independent=False):
         return gc_apply_batches(self.h, batches, independent)

@@ -430,6 +430,60 @@ def test_count_batch_is_a_what_if_query(gcb):
             assert g.counts() == F0 and same_graph(g, rp, col)
 
 
+def test_three_vertex_counts_follow_every_batch(gcb):
+    """The maintained [2-paths, triangles] equal the oracle's static 3-vertex
+    counts of the graph after each batch, in the plain and batched forms and
+    for what-if batches (which leave them unchanged)."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [1500, 40, 3000, 700], 0.5, 71)
+    og = oracle.OracleGraph(rp, col)
+    expect = []
+    for ins, dels in batches:
+        og.apply(ins, dels)
+        expect.append(oracle.static_counts3(og.row_ptr, og.col))
+    base3 = oracle.static_counts3(rp, col)
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts3() == base3
+        g.count_static()
+        assert mod64(g.stats()["C3a"]) == base3
+        g.count_batch(*batches[0])
+        assert g.counts3() == base3
+        for (ins, dels), e3 in zip(batches, expect):
+            g.apply(ins, dels)
+            assert g.counts3() == e3
+    with open_graph(gcb, n, rp, col) as g:
+        g.apply_many(batches)
+        assert g.counts3() == expect[-1]
+
+
+def test_delete_vertices(gcb):
+    """Deleting vertices deletes their edges in one batch (adjacent listed
+    vertices, repeats and a hub included); the counts equal the oracle's on
+    the graph without those edges, and a re-inserted edge counts again."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    deg = np.diff(rp)
+    hub = int(np.argmax(deg))
+    a = int(col[rp[hub]])  # a neighbour of the hub: an edge between two listed vertices
+    ids = [hub, a, 17, 17, 4000]
+    drop = set(ids)
+    kept = [(u, v) for u, v in edges_from_csr(rp, col) if u not in drop and v not in drop]
+    rp2, col2 = csr_from_edges(n, kept)
+    with open_graph(gcb, n, rp, col) as g:
+        out = g.delete_vertices(ids)
+        assert out == oracle.static_counts(rp2, col2) == g.counts()
+        assert same_graph(g, rp2, col2)
+        assert g.counts3() == oracle.static_counts3(rp2, col2)
+        assert g.delete_vertices([]) == out
+        with pytest.raises(gcb.GCError):
+            g.delete_vertices([n])
+        assert g.counts() == out
+        back = [(hub, a)]
+        rp3, col3 = csr_from_edges(n, kept + back)
+        assert g.apply(np.array(back, np.int32), None) == oracle.static_counts(rp3, col3)
+
+
 def test_sequential_batches_call_equals_single_calls(gcb):
     n, keys = gen.workload_graph("c2")
     rp, col = gen.csr_from_keys(n, keys)

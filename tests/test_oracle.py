@@ -361,3 +361,55 @@ def test_stored_workload_values(oracle_lib):
     r = oracle.fdgc_step(rp, col, ins, dels, c1["static"], 3)
     assert r["F"] == c1["after"] and r["Ca"] == c1["Ca"] and r["Cb"] == c1["Cb"]
     assert oracle.static_counts(r["row_ptr"], r["col"], "literal") == c1["after"]
+
+
+# ------------------------------------------------------- 3-vertex graphlets --
+
+def test_counts3_closed_forms(oracle_lib):
+    """[induced 2-paths, triangles]: K_n has C(n,3) triangles and no open
+    path; the star K_1,s has C(s,2) open paths; P_n has n - 2; C_n (n >= 4)
+    has n; K_a,b has a C(b,2) + b C(a,2)."""
+    def kn(n):
+        return n, [(a, b) for a in range(n) for b in range(a + 1, n)]
+
+    cases = []
+    for n in (3, 4, 7):
+        cases.append((kn(n), [0, math.comb(n, 3)]))
+    for s in (3, 6):
+        cases.append(((s + 1, [(0, i) for i in range(1, s + 1)]), [math.comb(s, 2), 0]))
+    for n in (3, 6):
+        cases.append(((n, [(i, i + 1) for i in range(n - 1)]), [n - 2, 0]))
+    for n in (4, 9):
+        cases.append(((n, [(i, (i + 1) % n) for i in range(n)]), [n, 0]))
+    for a, b in ((2, 3), (3, 4)):
+        edges = [(i, a + j) for i in range(a) for j in range(b)]
+        cases.append(((a + b, edges), [a * math.comb(b, 2) + b * math.comb(a, 2), 0]))
+    for (n, edges), expect in cases:
+        rp, col = csr_from_edges(n, edges)
+        assert oracle.static_counts3(rp, col) == expect
+        assert brute.graphlet3_counts(n, edges) == expect
+
+
+def test_counts3_match_census_on_random_graphs(oracle_lib):
+    rng = np.random.default_rng(33)
+    for _ in range(80):
+        n = int(rng.integers(3, 20))
+        edges = random_graph(rng, n, float(rng.uniform(0.1, 0.8)))
+        rp, col = csr_from_edges(n, edges)
+        h = brute.census3(n, edges)
+        assert sum(h.values()) == math.comb(n, 3)
+        assert oracle.static_counts3(rp, col) == [h["path"], h["triangle"]]
+
+
+def test_counts3_triangles_agree_with_the_four_vertex_sums(oracle_lib):
+    """Triangles from the 3-vertex count equal a third of the sum of t_e that
+    the 4-vertex sums use: TT = 1/2 sum t_e (d_u + d_v - 4) on a graph whose
+    every edge has d_u + d_v = 6 gives TT = sum t_e = 3 triangles (the
+    3-regular graphs K_4 and the prism)."""
+    k4 = (4, [(a, b) for a in range(4) for b in range(a + 1, 4)])
+    prism = (6, [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3), (1, 4), (2, 5)])
+    for n, edges in (k4, prism):
+        rp, col = csr_from_edges(n, edges)
+        tri = oracle.static_counts3(rp, col)[1]
+        TT = oracle.sums_literal(rp, col)[2]
+        assert TT == 3 * tri
