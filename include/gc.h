@@ -145,12 +145,23 @@ int gc_apply_batch(gc_graph *g, const int32_t *ins, int64_t n_ins,
 /*
  * Delete vertices (Sec. 3 models a vertex deletion as the deletion of its
  * edges): every edge incident to ids[0..k) is deleted in one batch, applied
- * as gc_apply_batch would; the vertices stay, isolated (n is fixed at open:
- * a vertex to be inserted later is opened as an isolated id and gains its
- * edges by gc_apply_batch).  Ids outside [0, n) give GC_EINVAL and change
+ * as gc_apply_batch would; the vertices stay, isolated (a vertex is
+ * inserted by gc_add_vertices and gains its edges by gc_apply_batch).  Ids
+ * outside [0, n) give GC_EINVAL and change
  * nothing; repeated ids are allowed.  out: counts after the deletion.
  */
 int gc_delete_vertices(gc_graph *g, const int32_t *ids, int64_t k, uint64_t out[6]);
+
+/*
+ * Add k isolated vertices; their ids are [n, n + k) with n the count before
+ * the call (*first_id receives n; first_id may be NULL).  The counts do not
+ * change (an isolated vertex is in no connected graphlet); later batches may
+ * use the new ids.  GC_EINVAL if n + k would reach 2^30.
+ */
+int gc_add_vertices(gc_graph *g, int64_t k, int32_t *first_id);
+
+/* Vertices of the graph (n). */
+int32_t gc_num_vertices(const gc_graph *g);
 
 /* As gc_apply_batch, with the pair arrays in device memory (int32, same
    layout).  The caller guarantees every id is in [0, n) and no pair is a

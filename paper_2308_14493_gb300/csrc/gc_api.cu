@@ -294,6 +294,20 @@ __global__ void k_vertex_pairs(const int32_t* __restrict__ ids, long long k, con
     }
 }
 
+// New vertices ids [n0, n1): internal id = external id, no edges (a zero
+// capacity row: the first insertion moves it to the pool).
+__global__ void k_init_new_vertices(int32_t* perm, int32_t* iperm, int32_t* deg, int32_t* cap, long long* row_start,
+                                    int n0, int n1) {
+    for (long long i = n0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n1;
+         i += (long long)gridDim.x * blockDim.x) {
+        perm[i] = (int32_t)i;
+        iperm[i] = (int32_t)i;
+        deg[i] = 0;
+        cap[i] = 0;
+        row_start[i] = 0;
+    }
+}
+
 __global__ void k_set_F(Ctl* c) {
     if (threadIdx.x < 6) c->F[threadIdx.x] = (unsigned long long)c->Ca[threadIdx.x];
     if (threadIdx.x < 2) c->F3[threadIdx.x] = (unsigned long long)c->C3a[threadIdx.x];
@@ -1344,6 +1358,77 @@ int gc_count_batch_device(gc_graph* g, const int32_t* d_ins, int64_t n_ins, cons
                           uint64_t out[6]) {
     return batch_device(g, d_ins, n_ins, d_del, n_del, 0, out);
 }
+
+// Append k isolated vertices: the per-vertex state is copied into arrays of
+// the new size (scratch is re-made), the id width of the batch keys follows
+// n, and every captured batch graph is dropped.
+static int grow_vertices(gc_graph* g, long long k) {
+    cudaStream_t s = g->s;
+    const int n0 = g->n, n1 = (int)(n0 + k);
+    const size_t nn = (size_t)std::max(n1, 1), old_nn = (size_t)std::max(n0, 1);
+    auto grow = [&](void** p, size_t elem, size_t count_new, size_t count_old, bool keep) -> bool {
+        void* q = dalloc(g, elem * count_new);
+        if (!q) return false;
+        if (keep && n0 > 0) {
+            if (cudaMemcpyAsync(q, *p, elem * count_old, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return false;
+        }
+        dfree(g, *p);
+        *p = q;
+        return true;
+    };
+    bool ok = grow((void**)&g->perm, 4, nn, old_nn, true) && grow((void**)&g->iperm, 4, nn, old_nn, true) &&
+              grow((void**)&g->deg, 4, nn, old_nn, true) && grow((void**)&g->cap, 4, nn, old_nn, true) &&
+              grow((void**)&g->row_start, 8, nn + 1, old_nn, true) && grow((void**)&g->wlist, 4, nn, 0, false) &&
+              grow((void**)&g->U_deg, 4, nn, 0, false) && grow((void**)&g->U_split, 4, nn, 0, false) &&
+              grow((void**)&g->da, 4, nn, 0, false) && grow((void**)&g->db, 4, nn, 0, false) &&
+              grow((void**)&g->U_off, 8, nn + 1, 0, false) && grow((void**)&g->U_wt, 8, nn, 0, false) &&
+              grow((void**)&g->segA, sizeof(int2), nn, 0, false) && grow((void**)&g->segD, sizeof(int2), nn, 0, false) &&
+              grow((void**)&g->visited, 4, (nn + 31) / 32 + 1, 0, false) &&
+              grow((void**)&g->bins, 4, (size_t)NBINS * nn, 0, false);
+    if (!ok) return nomem(g, "vertex arrays");
+    CK(cudaMemsetAsync(g->segA, 0, sizeof(int2) * nn, s));
+    CK(cudaMemsetAsync(g->segD, 0, sizeof(int2) * nn, s));
+    k_init_new_vertices<<<grid_elems(g, k), TPB, 0, s>>>(g->perm, g->iperm, g->deg, g->cap, g->row_start, n0, n1);
+    CKL();
+    release(g, g->dense);
+    if (!ensure(g, g->dense, (size_t)g->dense_clusters * (nn + 1))) return nomem(g, "4-cycle counter arrays");
+    CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
+    g->n = n1;
+    g->S = std::max(1, bitlen(n1 > 0 ? n1 - 1 : 0));
+    if (g->chunk_table.p) {
+        release(g, g->chunk_table);
+        if (!ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
+    }
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    if (g->pexec) {
+        cudaGraphExecDestroy(g->pexec);
+        g->pexec = nullptr;
+    }
+    g->buf_gen++;
+    CK(cudaStreamSynchronize(s));
+    return GC_OK;
+}
+
+int gc_add_vertices(gc_graph* g, int64_t k, int32_t* first_id) {
+    if (!g) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    g->err.clear();
+    if (k < 0 || (long long)g->n + k >= (1ll << 30)) {
+        g->err = "vertex count: negative, or n would reach 2^30";
+        return GC_EINVAL;
+    }
+    if (first_id) *first_id = g->n;
+    if (k == 0) return GC_OK;
+    return grow_vertices(g, k);
+}
+
+int32_t gc_num_vertices(const gc_graph* g) { return g ? g->n : -1; }
 
 int gc_delete_vertices(gc_graph* g, const int32_t* ids, int64_t k, uint64_t out[6]) {
     if (!g) return GC_EINVAL;

@@ -106,6 +106,9 @@ def load():
             lib.gc_counts.argtypes = [P, u64p]
             lib.gc_counts3.argtypes = [P, u64p]
             lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
+            lib.gc_add_vertices.argtypes = [P, ctypes.c_int64, i32p]
+            lib.gc_num_vertices.argtypes = [P]
+            lib.gc_num_vertices.restype = ctypes.c_int32
             lib.gc_apply_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
             lib.gc_apply_batch_device.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, u64p]
             lib.gc_count_batch.argtypes = [P, i32p, ctypes.c_int64, i32p, ctypes.c_int64, u64p]
@@ -210,6 +213,17 @@ def gc_delete_vertices(h, ids) -> list[int]:
     out = np.zeros(6, np.uint64)
     _check(load().gc_delete_vertices(h, _ptr(buf), a.size, _ptr(out, ctypes.c_uint64)), h)
     return [int(x) for x in out]
+
+
+def gc_add_vertices(h, k: int) -> int:
+    """Append k isolated vertices; returns the first new id."""
+    first = ctypes.c_int32()
+    _check(load().gc_add_vertices(h, int(k), ctypes.byref(first)), h)
+    return int(first.value)
+
+
+def gc_num_vertices(h) -> int:
+    return int(load().gc_num_vertices(h))
 
 
 def gc_apply_batch(h, ins, dels) -> list[int]:
@@ -461,6 +475,11 @@ class Graph:
 
     def delete_vertices(self, ids):
         return gc_delete_vertices(self.h, ids)
+
+    def add_vertices(self, k: int) -> int:
+        first = gc_add_vertices(self.h, k)
+        self.n = gc_num_vertices(self.h)
+        return first
 
     def apply_many(self, batches, independent=False):
         return gc_apply_batches(self.h, batches, independent)

@@ -484,6 +484,39 @@ def test_delete_vertices(gcb):
         assert g.apply(np.array(back, np.int32), None) == oracle.static_counts(rp3, col3)
 
 
+def test_add_vertices_then_connect_them(gcb):
+    """New vertices start isolated (counts unchanged) and then take part in
+    batches like any other: edges among themselves, to old vertices and to
+    the hub; plain and batched forms, against the oracle on the grown graph."""
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    rng = np.random.default_rng(81)
+    with open_graph(gcb, n, rp, col) as g:
+        first = g.add_vertices(300)
+        assert first == n and g.n == n + 300
+        assert g.counts() == F0
+        n2 = n + 300
+        new = np.arange(n, n2)
+        ins = [(int(a), int(b)) for a, b in zip(new[:-1], new[1:])]                 # a path of new vertices
+        ins += [(int(v), int(rng.integers(0, n))) for v in new]                     # each to an old vertex
+        ins += [(int(v), 0) for v in new[:50]]                                      # many to one old vertex
+        ins = np.array(sorted({(min(a, b), max(a, b)) for a, b in ins if a != b}), np.int32)
+        none = np.zeros((0, 2), np.int32)
+        og = oracle.OracleGraph(*csr_from_edges(n2, edges_from_csr(rp, col)))
+        r1 = og.apply(ins[:400], none)
+        assert g.apply(ins[:400], none) == r1["F"]
+        dels = np.array(edges_from_csr(og.row_ptr, og.col)[:30], np.int32)
+        r2 = og.apply(ins[400:], dels)
+        last = np.array([(int(new[0]), int(new[1]))], np.int32)
+        r3 = og.apply(none, last)
+        assert g.apply_many([(ins[400:], dels), (none, last)]) == [r2["F"], r3["F"]]
+        assert same_graph(g, og.row_ptr, og.col)
+        assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+        with pytest.raises(gcb.GCError):
+            g.apply(np.array([[0, n2]], np.int32), none)
+
+
 def test_sequential_batches_call_equals_single_calls(gcb):
     n, keys = gen.workload_graph("c2")
     rp, col = gen.csr_from_keys(n, keys)
