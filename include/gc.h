@@ -62,7 +62,12 @@ typedef struct {
     int32_t dense_cluster; /* CTAs per cluster of the heavy 4-cycle kernel: 0 auto, 8 or 16 */
     int32_t chunk_threshold; /* wedge bound above which a 4-cycle pivot is counted in shared memory
                                 over id-range chunks; <= 0: never (the cluster kernel takes them) */
-    int32_t reserved[5];
+    int32_t local_max_pairs; /* batches of at most this many pairs (as passed) to gc_apply_batch,
+                                gc_count_batch and their _device forms take the edge-local delta:
+                                the same counts from only the terms a batch can change (edges at
+                                its endpoints, 4-cliques and 4-cycles through its pairs) instead
+                                of a region recount.  0: never */
+    int32_t reserved[4];
 } gc_options;
 
 /* Per-batch record of the last gc_apply_batch* call. */
@@ -82,7 +87,12 @@ typedef struct {
     float ms_device;                /* device time of the batch (CUDA events) */
     float ms_wall;                  /* host wall time of the call */
     int32_t relayouts;              /* adjacency re-layouts the batch needed */
-    int32_t reserved[5];
+    int32_t path;                   /* 0: region recount (Algorithm 2); 1: edge-local delta, for
+                                       which region_vertices is |V_X| (the endpoints),
+                                       region_entries their union-row entries, Ca / sums_a the
+                                       six induced / non-induced deltas and Cb / sums_b zero,
+                                       C3a the 3-vertex deltas, work_triangles the probes */
+    int32_t reserved[4];
     /* device time per stage (CUDA events):
        [0] normalise  [1] region walk  [2] union graph  [3] triangles + 4-cliques
        [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused

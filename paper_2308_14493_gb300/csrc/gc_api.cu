@@ -102,6 +102,17 @@ struct gc_graph {
     int p_commit = -1;
     unsigned long long p_gen = 0;
     int p_launches = 0;
+    // the same for the edge-local form of the plain path
+    cudaGraphExec_t lexec = nullptr;
+    long long l_nk = -1;
+    int l_commit = -1;
+    unsigned long long l_gen = 0;
+    int l_launches = 0;
+    // scratch of the edge-local path (entries each; offsets one more)
+    Buf<int32_t> l_cost, l_own, l_pcost, l_ccnt, l_kcost, l_tpair;
+    Buf<long long> l_pre, l_ppre, l_cpre, l_kpre;
+    Buf<unsigned long long> l_rec;
+    long long l_cap = 0;
     unsigned long long buf_gen = 1;      // bumped whenever a buffer moves
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
@@ -229,13 +240,18 @@ __global__ void k_begin_batch(Ctl* c, const long long* desc) {
     c->scratch_tail = 0;
     c->overflow = 0;
     c->err = 0;
+    c->lovf = 0;
+    c->l_np = 0;
+    c->l_need = 0;
+    for (int k = 0; k < 4; k++) c->l_len[k] = 0;
+    for (int k = 0; k < 5; k++) c->l_tot[k] = 0;
 }
 
 // result of the current batch to out[cur], advance the cursor
 __global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit) {
     if (threadIdx.x != 0 || !c->active) return;
     for (int k = 0; k < 6; k++) out[6 * (long long)c->cur + k] = c->last_out[k];
-    if (commit && !c->err) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
+    if (commit && !c->err && !c->lovf) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
     c->cur++;
 }
 
@@ -374,6 +390,39 @@ static long long predict_batch_bytes(const gc_graph* g, long long n_ins, long lo
     return b;
 }
 
+static void release_local(gc_graph* g) {
+    release(g, g->l_cost);
+    release(g, g->l_own);
+    release(g, g->l_pcost);
+    release(g, g->l_ccnt);
+    release(g, g->l_kcost);
+    release(g, g->l_tpair);
+    release(g, g->l_pre);
+    release(g, g->l_ppre);
+    release(g, g->l_cpre);
+    release(g, g->l_kpre);
+    release(g, g->l_rec);
+    g->l_cap = 0;
+}
+
+// Scratch of the edge-local path for `cap` entries per array.
+static int ensure_local(gc_graph* g, long long cap) {
+    if (g->l_cap >= cap) return GC_OK;
+    const size_t c = (size_t)cap;
+    if (!ensure(g, g->l_cost, c) || !ensure(g, g->l_own, c) || !ensure(g, g->l_pcost, c) ||
+        !ensure(g, g->l_ccnt, c) || !ensure(g, g->l_kcost, c) || !ensure(g, g->l_tpair, c) ||
+        !ensure(g, g->l_pre, c + 1) || !ensure(g, g->l_ppre, c + 1) || !ensure(g, g->l_cpre, c + 1) ||
+        !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c))
+        return nomem(g, "edge-local scratch");
+    // ensure() may round up; the usable capacity is the smallest array's
+    size_t m = std::min({g->l_cost.cap, g->l_own.cap, g->l_pcost.cap, g->l_ccnt.cap, g->l_kcost.cap,
+                         g->l_tpair.cap, g->l_rec.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
+                         g->l_kpre.cap - 1});
+    g->l_cap = (long long)m;
+    g->buf_gen++;  // captured graphs hold the old pointers
+    return GC_OK;
+}
+
 // Free the scratch that the next batch re-creates on demand.
 static void trim_scratch(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
@@ -385,6 +434,11 @@ static void trim_scratch(gc_graph* g) {
         cudaGraphExecDestroy(g->pexec);
         g->pexec = nullptr;
     }
+    if (g->lexec) {
+        cudaGraphExecDestroy(g->lexec);
+        g->lexec = nullptr;
+    }
+    release_local(g);
     release(g, g->U_col);
     release(g, g->tpack);
     release(g, g->keys);
@@ -440,11 +494,11 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     int gw = grid_warps(g);
     k_reset_count<<<1, 32, 0, s>>>(g->ctl);
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
-    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg);
+    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg, 0);
     g->launches += 2;
     g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
     k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
-                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
+                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 0);
     k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     CountArgs ca;
@@ -479,6 +533,57 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
         k_set_F<<<1, 32, 0, s>>>(g->ctl);
         g->launches++;
     }
+    if (timed) CK(record_stage(g->ev[6], s));
+    CKL();
+    return GC_OK;
+}
+
+// Edge-local delta: union rows of the batch endpoints V_X (full rows), then
+// the local terms, 4-cliques and 4-cycles and their closed forms.
+static int count_local(gc_graph* g, int commit, bool timed) {
+    cudaStream_t s = g->s;
+    int gw = grid_warps(g);
+    k_reset_count<<<1, 32, 0, s>>>(g->ctl);
+    CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
+    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg, 1);
+    g->launches += 2;
+    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
+    k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
+                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 1);
+    k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
+    g->launches += 2;
+    LocalArgs la;
+    la.ctl = g->ctl;
+    la.wlist = g->wlist;
+    la.visited = g->visited;
+    la.U_off = g->U_off;
+    la.U_col = g->U_col.p;
+    la.row_start = g->row_start;
+    la.deg = g->deg;
+    la.col = g->col;
+    la.da = g->da;
+    la.db = g->db;
+    la.tpack = g->tpack.p;
+    la.srcA = g->srcA.p;
+    la.dstA = g->dstA.p;
+    la.srcD = g->srcD.p;
+    la.dstD = g->dstD.p;
+    la.cost = g->l_cost.p;
+    la.own = g->l_own.p;
+    la.pcost = g->l_pcost.p;
+    la.ccnt = g->l_ccnt.p;
+    la.kcost = g->l_kcost.p;
+    la.tpair = g->l_tpair.p;
+    la.pre = g->l_pre.p;
+    la.ppre = g->l_ppre.p;
+    la.cpre = g->l_cpre.p;
+    la.kpre = g->l_kpre.p;
+    la.rec = g->l_rec.p;
+    la.bsum = g->bsum.p;
+    la.cap = g->l_cap;
+    la.sms = g->sms;
+    g->launches += enqueue_local(la, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
+                                 timed ? g->ev[5] : nullptr, commit);
     if (timed) CK(record_stage(g->ev[6], s));
     CKL();
     return GC_OK;
@@ -521,7 +626,8 @@ static int enqueue_segments(gc_graph* g, bool clear) {
 // actual sizes are read on the device.
 //   commit:     apply G <- G \ D u A (else an independent what-if batch)
 //   timed:      record the stage events (event-record nodes in the graph)
-static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed) {
+//   local:      the edge-local delta instead of the region recount
+static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed, bool local = false) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
     k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc);
@@ -550,14 +656,14 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed)
     k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
     k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
     g->launches += 2;
-    for (int L = 1; L <= g->hops; L++) {
+    for (int L = 1; L <= (local ? 0 : g->hops); L++) {
         k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
         k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
         g->launches += 2;
     }
     CKL();
     if (timed) CK(record_stage(g->ev[2], s));
-    int rc = count_region(g, commit ? 0 : 2, false, timed);
+    int rc = local ? count_local(g, commit ? 1 : 0, timed) : count_region(g, commit ? 0 : 2, false, timed);
     if (rc) return rc;
     if (commit) {
         rc = enqueue_commit(g);
@@ -693,7 +799,7 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
 // Capture the per-batch launch sequence (batch from the run cursor) into
 // *exec; timed: with the stage events as event-record nodes.
 static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool timed, cudaGraphExec_t* exec,
-                         int* launches) {
+                         int* launches, bool local = false) {
     cudaStream_t s = g->s;
     if (*exec) {
         cudaGraphExecDestroy(*exec);
@@ -703,7 +809,7 @@ static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool time
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const int lsave = g->launches;
     g->launches = 0;
-    int rc = enqueue_batch(g, shape_nk, commit, timed);
+    int rc = enqueue_batch(g, shape_nk, commit, timed, local);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     *launches = g->launches;
     g->launches = lsave;
@@ -743,33 +849,57 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     rc = ensure_desc(g, 6);
     if (rc) return rc;
     if (!ensure(g, g->out_dev, 6)) return nomem(g, "batch results");
-    if (!g->pexec || g->p_nk != shape_nk || g->p_commit != commit || g->p_gen != g->buf_gen) {
-        rc = capture_batch(g, shape_nk, commit != 0, true, &g->pexec, &g->p_launches);
+    // small batches may take the edge-local delta (same counts, work
+    // proportional to the rows the batch touches instead of a region)
+    bool local = g->opt.local_max_pairs > 0 && n_ins + n_del <= (long long)g->opt.local_max_pairs;
+    for (int attempt = 0;; attempt++) {
+        if (local) {
+            rc = ensure_local(g, std::max<long long>(g->l_cap, 1LL << 20));
+            if (rc) return rc;
+        }
+        cudaGraphExec_t* ex = local ? &g->lexec : &g->pexec;
+        long long* ex_nk = local ? &g->l_nk : &g->p_nk;
+        int* ex_commit = local ? &g->l_commit : &g->p_commit;
+        unsigned long long* ex_gen = local ? &g->l_gen : &g->p_gen;
+        int* ex_launches = local ? &g->l_launches : &g->p_launches;
+        if (!*ex || *ex_nk != shape_nk || *ex_commit != commit || *ex_gen != g->buf_gen) {
+            rc = capture_batch(g, shape_nk, commit != 0, true, ex, ex_launches, local);
+            if (rc) return rc;
+            *ex_nk = shape_nk;
+            *ex_commit = commit;
+            *ex_gen = g->buf_gen;
+        }
+        g->h_desc[0] = (long long)d_ins;
+        g->h_desc[1] = (long long)d_del;
+        g->h_desc[2] = 0;
+        g->h_desc[3] = n_ins;
+        g->h_desc[4] = 0;
+        g->h_desc[5] = n_del;
+        CK(cudaMemcpyAsync(g->desc, g->h_desc, 6 * sizeof(long long), cudaMemcpyHostToDevice, s));
+        k_run_reset<<<1, 32, 0, s>>>(g->ctl);
+        CKL();
+        g->launches = *ex_launches + 1;
+        CK(cudaEventRecord(g->e0, s));
+        CK(cudaGraphLaunch(*ex, s));
+        CK(cudaEventRecord(g->e1, s));
+        rc = read_ctl(g);
         if (rc) return rc;
-        g->p_nk = shape_nk;
-        g->p_commit = commit;
-        g->p_gen = g->buf_gen;
+        if (g->h_ctl->err) {
+            g->err = "batch rejected on the device: a pair is a self-loop or names a vertex outside [0, n)";
+            return GC_EINVAL;
+        }
+        if (!(local && g->h_ctl->lovf)) break;
+        // the local scratch was too small and nothing was applied: grow it
+        // once to what the batch needed, else take the region path
+        if (attempt == 0) {
+            long long need = g->h_ctl->l_need;
+            rc = ensure_local(g, need + need / 4 + 1024);
+            if (rc) return rc;
+        } else {
+            local = false;
+        }
     }
-    g->h_desc[0] = (long long)d_ins;
-    g->h_desc[1] = (long long)d_del;
-    g->h_desc[2] = 0;
-    g->h_desc[3] = n_ins;
-    g->h_desc[4] = 0;
-    g->h_desc[5] = n_del;
-    CK(cudaMemcpyAsync(g->desc, g->h_desc, 6 * sizeof(long long), cudaMemcpyHostToDevice, s));
-    k_run_reset<<<1, 32, 0, s>>>(g->ctl);
-    CKL();
-    g->launches = g->p_launches + 1;
-    CK(cudaEventRecord(g->e0, s));
-    CK(cudaGraphLaunch(g->pexec, s));
-    CK(cudaEventRecord(g->e1, s));
-    rc = read_ctl(g);
-    if (rc) return rc;
     int relayouts = 0;
-    if (g->h_ctl->err) {
-        g->err = "batch rejected on the device: a pair is a self-loop or names a vertex outside [0, n)";
-        return GC_EINVAL;
-    }
     if (commit && g->h_ctl->overflow) {
         rc = finish_pending_commit(g, &relayouts);
         if (rc) return rc;
@@ -785,7 +915,13 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     g->st.launches = g->launches;
     // [0] normalise: ev0->ev1, [1] region: ev1->ev2, [2] union graph: ev2->ev3,
     // [3] triangles: ev3->ev4, [4] 4-cycles: ev4->ev5, [5] terms: ev5->ev6, [6] commit: ev6->ev7
-    stage_times(g, 0, 7);
+    // (the edge-local path runs its stages one after the other)
+    if (local) {
+        for (int i = 0; i < 8; i++) g->st.ms_stage[i] = i < 7 ? elapsed(g->ev[i], g->ev[i + 1]) : 0.f;
+    } else {
+        stage_times(g, 0, 7);
+    }
+    g->st.path = local ? 1 : 0;
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
         for (int i = 0; i < 2; i++) g->F3[i] = c.F3[i];
@@ -936,6 +1072,8 @@ static void destroy(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->pexec) cudaGraphExecDestroy(g->pexec);
+    if (g->lexec) cudaGraphExecDestroy(g->lexec);
+    release_local(g);
     int32_t* p32[] = {g->perm, g->iperm, g->deg, g->cap, g->col, g->wlist, g->U_deg, g->U_split, g->da, g->db};
     for (auto p : p32) dfree(g, p);
     dfree(g, g->row_start);
@@ -1406,6 +1544,10 @@ static int grow_vertices(gc_graph* g, long long k) {
     if (g->pexec) {
         cudaGraphExecDestroy(g->pexec);
         g->pexec = nullptr;
+    }
+    if (g->lexec) {
+        cudaGraphExecDestroy(g->lexec);
+        g->lexec = nullptr;
     }
     g->buf_gen++;
     CK(cudaStreamSynchronize(s));

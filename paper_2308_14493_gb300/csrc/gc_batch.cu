@@ -127,7 +127,7 @@ __global__ void k_commit_plan(Ctl* c, const int32_t* __restrict__ wlist, const i
                               long long col_capacity, float slack, long long* __restrict__ plan_dst,
                               int32_t* __restrict__ plan_cap, int32_t* __restrict__ plan_deg,
                               long long* __restrict__ plan_scr) {
-    if (c->err) return;
+    if (c->err || c->lovf) return;
     int ns = c->lvl[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
         int32_t u = wlist[i];
@@ -162,7 +162,7 @@ __global__ void k_commit_merge(const Ctl* c, const int32_t* __restrict__ wlist, 
                                const int32_t* __restrict__ dstD, const int32_t* __restrict__ deg,
                                const long long* __restrict__ row_start, const int32_t* __restrict__ col,
                                const long long* __restrict__ plan_scr, uint32_t* __restrict__ scratch) {
-    if (c->err || c->overflow) return;
+    if (c->err || c->overflow || c->lovf) return;
     int ns = c->lvl[0];
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -182,7 +182,7 @@ __global__ void k_commit_write(const Ctl* c, const int32_t* __restrict__ wlist, 
                                const long long* __restrict__ plan_scr, const uint32_t* __restrict__ scratch,
                                int32_t* __restrict__ deg, int32_t* __restrict__ cap,
                                long long* __restrict__ row_start, int32_t* __restrict__ col) {
-    if (c->err || c->overflow) return;
+    if (c->err || c->overflow || c->lovf) return;
     int ns = c->lvl[0];
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;

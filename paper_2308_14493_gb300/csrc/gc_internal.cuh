@@ -87,6 +87,14 @@ struct Ctl {
     unsigned long long F3[2];        // maintained
     long long C3a[2], C3b[2];        // of G_a, G_b of the last pass
     unsigned long long last_out3[2]; // after the current batch
+    // edge-local path (gc_local.cu)
+    int lovf;                        // a local scratch array was too small: nothing applied
+    long long l_np;                  // changed-pair slots (kept directed entries)
+    long long l_len[4];              // lengths of its scans: [0] union entries [1] pair slots
+                                     // [2] common-neighbour records [3] 4-cycle tasks (0: skip)
+    long long l_tot[5];              // totals: [0] triangle probes [1] records [2] 4-clique probes
+                                     // [3] 4-cycle tasks [4] 4-cycle probes
+    long long l_need;                // entries the largest local array needed
     // (device-only tail: the host mirror copies the block up to here)
     unsigned long long accs[NACC][ACC_STRIPES];  // acc, striped: kernels add here, k_finalize sums
 };

@@ -46,12 +46,13 @@ __global__ void k_level_mark(Ctl* c, int L);
 __global__ void k_bfs_expand(Ctl* c, int L, const long long* row_start, const int32_t* deg, const int32_t* col,
                              uint32_t* visited, int32_t* wlist);
 __global__ void k_region_all(Ctl* c, int n, int32_t* wlist);
+// all = 1: every entry of each row (the edge-local path), else N(u) n W
 __global__ void k_u_count(const Ctl* c, const int32_t* wlist, const uint32_t* visited, const long long* row_start,
-                          const int32_t* deg, const int32_t* col, const int2* segA, int32_t* U_deg);
+                          const int32_t* deg, const int32_t* col, const int2* segA, int32_t* U_deg, int all);
 __global__ void k_u_fill(const Ctl* c, const int32_t* wlist, const uint32_t* visited, const long long* row_start,
                          const int32_t* deg, const int32_t* col, const int2* segA, const int2* segD,
                          const int32_t* dstA, const int32_t* dstD, const long long* U_off, uint32_t* U_col,
-                         int32_t* U_split, int32_t* da, int32_t* db);
+                         int32_t* U_split, int32_t* da, int32_t* db, int all);
 
 // gc_count.cu
 __global__ void k_reset_count(Ctl* c);
@@ -96,6 +97,35 @@ long long c4_chunk_table_entries(long long n);   // entries of the run-bound tab
 // Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
 // 16 if the device can co-schedule it, else 8) and the number of clusters.
 int dense_cluster_plan(int want, int sms, int* size_out);
+// Device buffers of the edge-local path (gc_local.cu).  V_X = wlist[0 ..
+// lvl[0]), marked in `visited`; its union rows in U_off / U_col, degrees in
+// G_a / G_b in da / db.  The scratch arrays hold `cap` entries (the offset
+// arrays cap + 1); a batch that needs more sets Ctl::lovf and l_need.
+struct LocalArgs {
+    Ctl* ctl;
+    const int32_t* wlist;
+    const uint32_t* visited;
+    const long long* U_off;
+    const uint32_t* U_col;
+    const long long* row_start;
+    const int32_t* deg;
+    const int32_t* col;
+    const int32_t* da;
+    const int32_t* db;
+    unsigned long long* tpack;     // per-entry triangle counters, zeroed
+    const int32_t *srcA, *dstA, *srcD, *dstD;  // kept directed entries of the batch
+    int32_t *cost, *own, *pcost, *ccnt, *kcost, *tpair;
+    long long *pre, *ppre, *cpre, *kpre;
+    unsigned long long* rec;
+    long long* bsum;               // 1024 words
+    long long cap;
+    int sms;
+};
+// Enqueue the edge-local delta (after the union rows of V_X); events mark
+// the triangle stage, the 4-clique / 4-cycle stage and the closed forms.
+int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,
+                  int commit);
+
 // Enqueue the counting kernels (binning, triangles / 4-cliques, 4-cycles,
 // edge terms, closed forms with k_finalize(mode)); events, when given, are
 // recorded before the triangle, 4-cycle and edge-term stages.  Returns the

@@ -1,0 +1,631 @@
+// gc_local.cu -- the edge-local delta: the change of the maintained counts
+// from the terms a batch can change, without recounting a region.  An
+// alternative to steps a1..a7 for small batches; the normalisation (a0) and
+// the commit (a8) are shared with the region path.
+//
+// Why it is exact.  F(G_a) - F(G_b) is the image under the containment
+// inversion (Sec. 3, PGD's closed forms) of the difference of the
+// non-induced sums N = (P, S, TT, D, K, Q) of G_a and G_b (Lemma 2 takes the
+// same difference over a region).  Let X be the changed pairs of the batch
+// after normalisation and V_X their endpoints.
+//  * S and sum C(d,2) add a function of each vertex degree: only vertices of
+//    V_X change degree.
+//  * P, TT, D and sum t add, per edge uw, a function of d_u, d_w and
+//    t_uw = |N(u) n N(w)|.  A triangle uwz whose t changes holds a changed
+//    pair, whose endpoints are two of u, w, z, so one of u, w is in V_X; so
+//    every term that changes belongs to an edge with an endpoint in V_X.
+//  * K and Q count subgraphs (4-cliques, 4-cycles): the copies that differ
+//    between G_a and G_b are those holding a changed pair.  A copy in G_a
+//    (G_b) is counted once, at the smallest inserted (deleted) pair it holds,
+//    pairs ordered by the key (min id, max id).
+// Everything else is equal in G_a and G_b and cancels.  So the path sums the
+// a- and b-side terms of exactly those edges, vertices and subgraphs, and
+// k_finalize_local turns their differences into the six induced deltas.
+//
+// Work is a list of probes: each intersection of two sorted rows iterates
+// the shorter one and binary-searches the longer.  The probes of all rows
+// are numbered through prefix sums (an exclusive scan of per-task counts)
+// and dealt one per thread, so hub rows spread over the whole grid.
+//
+// Rows.  A vertex of V_X reads its union row from U (N(u) u A_u, entries
+// flagged FLAG_A / FLAG_B as in the region path, built over the full row).
+// Any other vertex is untouched by the batch and reads its adjacency row
+// directly (in both graphs: both flags implied).
+#include "gc_internal.cuh"
+#include "gc_kernels.cuh"
+
+namespace gcx {
+
+namespace {
+
+constexpr uint32_t AB = FLAG_A | FLAG_B;
+
+struct Row {
+    const uint32_t* p;
+    int len;
+    uint32_t orf;  // flags implied for every entry (plain adjacency rows)
+};
+
+__device__ __forceinline__ bool in_x(const uint32_t* __restrict__ visited, uint32_t v) {
+    return (visited[v >> 5] >> (v & 31)) & 1u;
+}
+
+struct LocalView {
+    const uint32_t* visited;
+    const long long* U_off;
+    const uint32_t* U_col;
+    const long long* row_start;
+    const int32_t* deg;
+    const int32_t* col;
+
+    __device__ __forceinline__ Row row(uint32_t y) const {
+        if (in_x(visited, y)) {
+            const long long b = U_off[y];
+            return Row{U_col + b, (int)(U_off[y + 1] - b), 0u};
+        }
+        return Row{(const uint32_t*)(col + row_start[y]), deg[y], AB};
+    }
+    __device__ __forceinline__ Row urow(uint32_t y) const {  // y in V_X
+        const long long b = U_off[y];
+        return Row{U_col + b, (int)(U_off[y + 1] - b), 0u};
+    }
+};
+
+__device__ __forceinline__ uint32_t flags_at(const Row& r, int i) { return (r.p[i] | r.orf) & AB; }
+
+// first position in r[lo, len) whose id is >= z
+__device__ __forceinline__ int row_lower(const Row& r, int lo, uint32_t z) {
+    int hi = r.len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (vid(r.p[mid]) < z) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// position of id z in r[lo, len), or -1
+__device__ __forceinline__ int row_find(const Row& r, int lo, uint32_t z) {
+    const int p = row_lower(r, lo, z);
+    return (p < r.len && vid(r.p[p]) == z) ? p : -1;
+}
+
+// last i in [0, n) with pre[i] <= t (pre non-decreasing, pre[0] = 0 <= t < pre[n])
+__device__ __forceinline__ long long locate(const long long* __restrict__ pre, long long n, long long t) {
+    long long lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (pre[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long pkey(uint32_t a, uint32_t b) {
+    return a < b ? ((unsigned long long)a << 32) | b : ((unsigned long long)b << 32) | a;
+}
+
+// Changed pair slot i of the batch: kept insertion entries first, then kept
+// deletions (both directions are listed; the slot with src < dst stands for
+// the pair).  x = the graph the pair belongs to (FLAG_A inserted, FLAG_B
+// deleted).
+struct Pair {
+    uint32_t a, b, x;
+};
+__device__ __forceinline__ Pair pair_at(const Ctl* c, const int32_t* __restrict__ srcA,
+                                        const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                                        const int32_t* __restrict__ dstD, long long i) {
+    if (i < c->nA2) return Pair{(uint32_t)srcA[i], (uint32_t)dstA[i], FLAG_A};
+    const long long j = i - c->nA2;
+    return Pair{(uint32_t)srcD[j], (uint32_t)dstD[j], FLAG_B};
+}
+
+// For the 4-cycles through a pair, the neighbours of the endpoint with the
+// longer union row are walked and the other row is probed.
+__device__ __forceinline__ void c4_orient(const LocalView& V, const Pair& p, uint32_t* v, uint32_t* u) {
+    const int la = (int)(V.U_off[p.a + 1] - V.U_off[p.a]);
+    const int lb = (int)(V.U_off[p.b + 1] - V.U_off[p.b]);
+    const bool a_long = la > lb || (la == lb && p.a > p.b);
+    *v = a_long ? p.a : p.b;
+    *u = a_long ? p.b : p.a;
+}
+
+__device__ __forceinline__ void acc_warp(Ctl* c, int slot, unsigned long long x) {
+    x = warp_sum_u64(x);
+    if ((threadIdx.x & 31) == 0 && x) {
+        const int stripe = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (ACC_STRIPES - 1));
+        atomicAdd(&c->accs[slot][stripe], x);
+    }
+}
+
+// packed common-neighbour record of a changed pair (u, v): id z, the flags of
+// uz and vz (bit 0 FLAG_A, bit 1 FLAG_B), and whether z is in both rows
+constexpr int T_FU = 32, T_FV = 34;
+constexpr unsigned long long T_VALID = 1ull << 36;
+__device__ __forceinline__ uint32_t t_flags(unsigned long long r, int at) {
+    return (uint32_t)((r >> at) & 3ull) << 30;
+}
+
+}  // namespace
+
+// ---- scratch bounds ---------------------------------------------------------
+
+// After the union rows: the entry and pair-slot scans run only if their
+// arrays fit.
+__global__ void k_loc_check_rows(Ctl* c, long long cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long np = c->nA2 + c->nD2;
+    c->l_np = np;
+    bool ovf = c->nU > cap || np > cap;
+    if (ovf) {
+        c->lovf = 1;
+        c->l_need = max(c->l_need, max(c->nU, np));
+    }
+    const bool run = !c->err && !c->lovf;
+    c->l_len[0] = run ? c->nU : 0;
+    c->l_len[1] = run ? np : 0;
+}
+
+// After the pair scans: common-neighbour records and 4-cycle tasks.
+__global__ void k_loc_check_pairs(Ctl* c, long long cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool ovf = c->l_tot[1] > cap || c->l_tot[3] > cap;
+    if (ovf) {
+        c->lovf = 1;
+        c->l_need = max(c->l_need, max(c->l_tot[1], c->l_tot[3]));
+    }
+    const bool run = !c->err && !c->lovf;
+    c->l_len[2] = run ? c->l_tot[1] : 0;
+    c->l_len[3] = run ? c->l_tot[3] : 0;
+    if (!run) {
+        c->l_len[0] = c->l_len[1] = 0;
+        c->l_tot[0] = c->l_tot[2] = c->l_tot[4] = 0;
+    }
+}
+
+// ---- triangles per edge with an endpoint in V_X -----------------------------
+
+// Probes of edge (u, w) for u in V_X: the shorter of the two rows.  An edge
+// with both endpoints in V_X is taken from its lower endpoint only.
+__global__ void k_loc_tri_cost(const Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
+                               int32_t* __restrict__ cost, int32_t* __restrict__ own) {
+    if (c->l_len[0] == 0) return;
+    const int nX = c->lvl[0];
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nX; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        const Row ru = V.urow(u);
+        const long long base = V.U_off[u];
+        for (int j = lane; j < ru.len; j += 32) {
+            const uint32_t w = vid(ru.p[j]);
+            int k = 0;
+            if (!(in_x(V.visited, w) && w < u)) k = min(ru.len, V.row(w).len);
+            cost[base + j] = k;
+            own[base + j] = (int32_t)u;
+        }
+    }
+}
+
+// One probe per thread: t_e for G_a and G_b packed into tpack[e] (high 32
+// bits G_a, low 32 G_b).
+__global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict__ pre,
+                          const int32_t* __restrict__ own, unsigned long long* __restrict__ tpack) {
+    const long long n = c->l_len[0];
+    if (n == 0) return;
+    const long long tot = pre[n];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long e = locate(pre, n, t);
+        const int k = (int)(t - pre[e]);
+        const uint32_t u = (uint32_t)own[e];
+        const Row ru = V.urow(u);
+        const uint32_t w = vid(V.U_col[e]);
+        const Row rw = V.row(w);
+        uint32_t f;
+        if (ru.len <= rw.len) {
+            const uint32_t z = ru.p[k];
+            const int q = row_find(rw, 0, vid(z));
+            f = q < 0 ? 0u : (z & flags_at(rw, q));
+        } else {
+            const uint32_t z = rw.p[k] | rw.orf;
+            const int q = row_find(ru, 0, vid(z));
+            f = q < 0 ? 0u : (z & flags_at(ru, q));
+        }
+        f &= AB;
+        if (f) atomicAdd(&tpack[e], ((f & FLAG_A) ? (1ull << 32) : 0ull) | ((f & FLAG_B) ? 1ull : 0ull));
+    }
+}
+
+// ---- per-edge and per-vertex terms --------------------------------------------
+
+// The a- and b-side terms of every edge with an endpoint in V_X and of every
+// vertex of V_X, into the accumulator slots of the region path.
+__global__ void k_loc_terms(Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
+                            const unsigned long long* __restrict__ tpack, const int32_t* __restrict__ da,
+                            const int32_t* __restrict__ db) {
+    const int nX = c->l_len[0] ? c->lvl[0] : 0;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long P[2] = {0, 0}, S[2] = {0, 0}, T[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0};
+    unsigned long long T3[2] = {0, 0}, W2[2] = {0, 0};
+    for (int i = warp; i < nX; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        const long long dau = da[u], dbu = db[u];
+        if (lane == 0) {
+            S[0] += choose3((unsigned long long)dau);
+            S[1] += choose3((unsigned long long)dbu);
+            W2[0] += choose2((unsigned long long)dau);
+            W2[1] += choose2((unsigned long long)dbu);
+        }
+        const Row ru = V.urow(u);
+        const long long base = V.U_off[u];
+        for (int j = lane; j < ru.len; j += 32) {
+            const uint32_t fe = ru.p[j];
+            const uint32_t w = vid(fe);
+            const bool wx = in_x(V.visited, w);
+            if (wx && w < u) continue;
+            const unsigned long long t = tpack[base + j];
+            if (fe & FLAG_A) {
+                const long long dw = wx ? da[w] : V.deg[w], tt = (long long)(t >> 32);
+                P[0] += (unsigned long long)((dau - 1) * (dw - 1) - tt);
+                T[0] += (unsigned long long)(tt * (dau + dw - 4));
+                D[0] += choose2((unsigned long long)tt);
+                T3[0] += (unsigned long long)tt;
+                E[0] += 1;
+            }
+            if (fe & FLAG_B) {
+                const long long dw = wx ? db[w] : V.deg[w], tt = (long long)(t & 0xFFFFFFFFull);
+                P[1] += (unsigned long long)((dbu - 1) * (dw - 1) - tt);
+                T[1] += (unsigned long long)(tt * (dbu + dw - 4));
+                D[1] += choose2((unsigned long long)tt);
+                T3[1] += (unsigned long long)tt;
+                E[1] += 1;
+            }
+        }
+    }
+    for (int g = 0; g < 2; g++) {
+        const int o = 6 * g;
+        acc_warp(c, o + 0, P[g]);
+        acc_warp(c, o + 1, S[g]);
+        acc_warp(c, o + 2, T[g]);
+        acc_warp(c, o + 3, D[g]);
+        acc_warp(c, 12 + g, E[g]);
+        acc_warp(c, 16 + g, T3[g]);
+        acc_warp(c, 18 + g, W2[g]);
+    }
+}
+
+// ---- changed pairs: common neighbours and 4-cycle tasks -----------------------
+
+// Per pair slot: probes of its common-neighbour list (shorter row) and the
+// number of 4-cycle tasks (one per entry of the walked row).
+__global__ void k_loc_pair_cost(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                                const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                                const int32_t* __restrict__ dstD, int32_t* __restrict__ pcost,
+                                int32_t* __restrict__ ccnt) {
+    const long long np = c->l_len[1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+        int k = 0, m = 0;
+        if (p.a < p.b) {
+            const int la = (int)(V.U_off[p.a + 1] - V.U_off[p.a]);
+            const int lb = (int)(V.U_off[p.b + 1] - V.U_off[p.b]);
+            k = min(la, lb);
+            m = max(la, lb);
+        }
+        pcost[i] = k;
+        ccnt[i] = m;
+    }
+}
+
+// Common neighbours of each changed pair (u, v) = (a, b): one record per
+// entry of the shorter row, in id order; valid when the id is in both rows.
+__global__ void k_loc_common(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                             const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                             const int32_t* __restrict__ dstD, const long long* __restrict__ ppre,
+                             unsigned long long* __restrict__ rec) {
+    const long long np = c->l_len[1];
+    const long long tot = c->l_len[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = locate(ppre, np, t);
+        const int k = (int)(t - ppre[i]);
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+        const Row ra = V.urow(p.a), rb = V.urow(p.b);
+        uint32_t z, fa, fb;
+        int q;
+        if (ra.len <= rb.len) {
+            z = vid(ra.p[k]);
+            fa = flags_at(ra, k);
+            q = row_find(rb, 0, z);
+            fb = q < 0 ? 0u : flags_at(rb, q);
+        } else {
+            z = vid(rb.p[k]);
+            fb = flags_at(rb, k);
+            q = row_find(ra, 0, z);
+            fa = q < 0 ? 0u : flags_at(ra, q);
+        }
+        unsigned long long r = z;
+        if (q >= 0)
+            r |= ((unsigned long long)(fa >> 30) << T_FU) | ((unsigned long long)(fb >> 30) << T_FV) | T_VALID;
+        rec[t] = r;
+    }
+}
+
+// ---- 4-cliques holding a changed pair -------------------------------------------
+
+// For a common neighbour w of pair (u, v) in the pair's graph x, the
+// 4-cliques {u, v, w, z} with z > w: probes of the shorter of the pair's
+// remaining records and w's row beyond w.
+__global__ void k_loc_k4_cost(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                              const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                              const int32_t* __restrict__ dstD, const long long* __restrict__ ppre,
+                              const unsigned long long* __restrict__ rec, int32_t* __restrict__ kcost) {
+    const long long np = c->l_len[1];
+    const long long tot = c->l_len[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = rec[t];
+        int k = 0;
+        if (r & T_VALID) {
+            const long long i = locate(ppre, np, t);
+            const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+            if (t_flags(r, T_FU) & t_flags(r, T_FV) & p.x) {
+                const uint32_t w = (uint32_t)(r & 0xFFFFFFFFull);
+                const Row rw = V.row(w);
+                const int lr = rw.len - row_lower(rw, 0, w + 1);
+                const long long lt = ppre[i + 1] - t - 1;
+                k = (int)min((long long)lr, lt);
+            }
+        }
+        kcost[t] = k;
+    }
+}
+
+__global__ void k_loc_k4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, const int32_t* __restrict__ dstA,
+                         const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
+                         const long long* __restrict__ ppre, const unsigned long long* __restrict__ rec,
+                         const long long* __restrict__ kpre) {
+    const long long np = c->l_len[1];
+    const long long n = c->l_len[2];
+    const long long tot = n ? kpre[n] : 0;
+    unsigned long long ka = 0, kb = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < tot;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long t = locate(kpre, n, s);
+        const int k = (int)(s - kpre[t]);
+        const long long i = locate(ppre, np, t);
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+        const unsigned long long rw_rec = rec[t];
+        const uint32_t w = (uint32_t)(rw_rec & 0xFFFFFFFFull);
+        const Row rw = V.row(w);
+        const int pos = row_lower(rw, 0, w + 1);
+        const long long lt = ppre[i + 1] - t - 1;
+        const int lr = rw.len - pos;
+        uint32_t z, fuz = 0, fvz = 0, fwz = 0;
+        bool ok = false;
+        if (lt <= (long long)lr) {
+            const unsigned long long rz = rec[t + 1 + k];
+            z = (uint32_t)(rz & 0xFFFFFFFFull);
+            if (rz & T_VALID) {
+                const int q = row_find(rw, pos, z);
+                if (q >= 0) {
+                    ok = true;
+                    fuz = t_flags(rz, T_FU);
+                    fvz = t_flags(rz, T_FV);
+                    fwz = flags_at(rw, q);
+                }
+            }
+        } else {
+            z = vid(rw.p[pos + k]);
+            fwz = flags_at(rw, pos + k);
+            // binary search of z among the pair's records after t (sorted by id)
+            long long lo = t + 1, hi = ppre[i + 1];
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if ((uint32_t)(rec[mid] & 0xFFFFFFFFull) < z) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < ppre[i + 1]) {
+                const unsigned long long rz = rec[lo];
+                if ((uint32_t)(rz & 0xFFFFFFFFull) == z && (rz & T_VALID)) {
+                    ok = true;
+                    fuz = t_flags(rz, T_FU);
+                    fvz = t_flags(rz, T_FV);
+                }
+            }
+        }
+        if (!ok) continue;
+        const uint32_t x = p.x;
+        const uint32_t fuw = t_flags(rw_rec, T_FU), fvw = t_flags(rw_rec, T_FV);
+        if (!(fuw & fvw & fuz & fvz & fwz & x)) continue;
+        // counted at the smallest changed pair of graph x in the clique
+        const unsigned long long kp = pkey(p.a, p.b);
+        const uint32_t ids[5][2] = {{p.a, w}, {p.b, w}, {p.a, z}, {p.b, z}, {w, z}};
+        const uint32_t fl[5] = {fuw, fvw, fuz, fvz, fwz};
+        bool mine = true;
+#pragma unroll
+        for (int q = 0; q < 5; q++)
+            if (fl[q] == x && pkey(ids[q][0], ids[q][1]) < kp) mine = false;
+        if (!mine) continue;
+        if (x == FLAG_A) ka++;
+        else kb++;
+    }
+    acc_warp(c, 4, ka);
+    acc_warp(c, 10, kb);
+}
+
+// ---- 4-cycles holding a changed pair ----------------------------------------------
+
+// One task per entry w of the walked endpoint v's row; its probes: the
+// shorter of w's row and the other endpoint u's row.
+__global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                               const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                               const int32_t* __restrict__ dstD, const long long* __restrict__ cpre,
+                               int32_t* __restrict__ tpair, int32_t* __restrict__ tent,
+                               int32_t* __restrict__ tcost) {
+    const long long np = c->l_len[1];
+    if (c->l_len[3] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < np; i += nwarps) {
+        const long long b0 = cpre[i], m = cpre[i + 1] - b0;
+        if (m == 0) continue;
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+        uint32_t v, u;
+        c4_orient(V, p, &v, &u);
+        const Row rv = V.urow(v);
+        const int lu = (int)(V.U_off[u + 1] - V.U_off[u]);
+        for (int j = lane; j < rv.len; j += 32) {
+            const uint32_t e = rv.p[j];
+            const uint32_t w = vid(e);
+            int k = 0;
+            if (w != u && (e & p.x)) k = min(V.row(w).len, lu);
+            tpair[b0 + j] = (int32_t)i;
+            tent[b0 + j] = j;
+            tcost[b0 + j] = k;
+        }
+    }
+}
+
+__global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, const int32_t* __restrict__ dstA,
+                         const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
+                         const int32_t* __restrict__ tpair, const int32_t* __restrict__ tent,
+                         const long long* __restrict__ tpre) {
+    const long long n = c->l_len[3];
+    const long long tot = n ? tpre[n] : 0;
+    unsigned long long qa = 0, qb = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < tot;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long tau = locate(tpre, n, s);
+        const int k = (int)(s - tpre[tau]);
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, tpair[tau]);
+        uint32_t v, u;
+        c4_orient(V, p, &v, &u);
+        const Row rv = V.urow(v), ru = V.urow(u);
+        const uint32_t ev = rv.p[tent[tau]];
+        const uint32_t w = vid(ev), fvw = ev & AB;
+        const Row rw = V.row(w);
+        uint32_t z, fuz, fwz;
+        if (rw.len <= ru.len) {
+            z = vid(rw.p[k]);
+            fwz = flags_at(rw, k);
+            const int q = row_find(ru, 0, z);
+            if (q < 0) continue;
+            fuz = flags_at(ru, q);
+        } else {
+            z = vid(ru.p[k]);
+            fuz = flags_at(ru, k);
+            const int q = row_find(rw, 0, z);
+            if (q < 0) continue;
+            fwz = flags_at(rw, q);
+        }
+        const uint32_t x = p.x;
+        if (z == v || !(fvw & fuz & fwz & x)) continue;
+        // the cycle u-v-w-z-u, counted at its smallest changed pair of graph x
+        const unsigned long long kp = pkey(p.a, p.b);
+        if ((fvw == x && pkey(v, w) < kp) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp))
+            continue;
+        if (x == FLAG_A) qa++;
+        else qb++;
+    }
+    acc_warp(c, 5, qa);
+    acc_warp(c, 11, qb);
+}
+
+// ---- closed forms on the differences -------------------------------------------------
+
+// commit = 1: F += delta (the batch is applied); 0: the result is F + delta
+// and F stays.  Nothing changes after a scratch overflow (the host re-runs
+// the batch).  Ca holds the six induced deltas and sa the non-induced ones
+// (Cb, sb zero).
+__global__ void k_finalize_local(Ctl* c, int commit) {
+    if (blockIdx.x == 0 && threadIdx.x < NACC) {
+        unsigned long long x = 0;
+        for (int k = 0; k < ACC_STRIPES; k++) x += c->accs[threadIdx.x][k];
+        c->acc[threadIdx.x] += x;
+    }
+    __syncwarp();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long* a = c->acc;
+    const long long P = (long long)(a[0] - a[6]), S = (long long)(a[1] - a[7]);
+    const long long TT = (long long)(a[2] - a[8]) / 2;  // both full sums are even
+    const long long D = (long long)(a[3] - a[9]), K = (long long)(a[4] - a[10]), Q = (long long)(a[5] - a[11]);
+    const long long g6 = K;
+    const long long g5 = D - 6 * K;
+    const long long g3 = Q - g5 - 3 * K;
+    const long long g4 = TT - 4 * g5 - 12 * K;
+    const long long g2 = S - g4 - 2 * g5 - 4 * K;
+    const long long g1 = P - 2 * g4 - 4 * g3 - 6 * g5 - 12 * K;
+    const long long d[6] = {g1, g2, g3, g4, g5, g6};
+    const long long s[6] = {P, S, TT, D, K, Q};
+    const long long t3 = (long long)(a[16] - a[17]);  // 3 x change of triangles
+    const long long d3[2] = {(long long)(a[18] - a[19]) - t3, t3 / 3};
+    const bool ok = c->err == 0 && c->active && c->lovf == 0;
+    for (int i = 0; i < 6; i++) {
+        c->Ca[i] = d[i];
+        c->Cb[i] = 0;
+        c->sa[i] = s[i];
+        c->sb[i] = 0;
+        if (commit && ok) c->F[i] += (unsigned long long)d[i];
+        c->last_out[i] = commit ? c->F[i] : c->F[i] + (unsigned long long)d[i];
+    }
+    for (int i = 0; i < 2; i++) {
+        c->C3a[i] = d3[i];
+        c->C3b[i] = 0;
+        if (commit && ok) c->F3[i] += (unsigned long long)d3[i];
+        c->last_out3[i] = commit ? c->F3[i] : c->F3[i] + (unsigned long long)d3[i];
+    }
+    c->acc[14] = (unsigned long long)(c->l_tot[0] + c->l_tot[2] + c->l_tot[4]);  // probes
+    c->acc[15] = 0;
+}
+
+// ---- launch sequence ---------------------------------------------------------------
+
+int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,
+                  int commit) {
+    const int sms = a.sms;
+    const int gw = 8 * sms, tpb = 256;
+    const int sg = scan_grid(a.cap, sms);
+    LocalView V{a.visited, a.U_off, a.U_col, a.row_start, a.deg, a.col};
+    int nl = 0;
+    k_loc_check_rows<<<1, 32, 0, s>>>(a.ctl, a.cap);
+    nl++;
+    if (ev_tri) record_stage(ev_tri, s);
+    // triangles of the edges at V_X, then their terms
+    k_loc_tri_cost<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.cost, a.own);
+    nl++;
+    nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
+    k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
+    k_loc_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.tpack, a.da, a.db);
+    nl += 2;
+    if (ev_sub) record_stage(ev_sub, s);
+    // changed pairs: common neighbours (4-cliques) and 4-cycle tasks
+    k_loc_pair_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt);
+    nl++;
+    nl += scan_i32_to_i64(a.pcost, a.ppre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[1], s);
+    nl += scan_i32_to_i64(a.ccnt, a.cpre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[3], s);
+    k_loc_check_pairs<<<1, 32, 0, s>>>(a.ctl, a.cap);
+    k_loc_common<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec);
+    k_loc_k4_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kcost);
+    nl += 3;
+    nl += scan_i32_to_i64(a.kcost, a.kpre, &a.ctl->l_len[2], 0, a.bsum, sg, &a.ctl->l_tot[2], s);
+    k_loc_k4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kpre);
+    // the triangle probe offsets are free again: the 4-cycle tasks reuse them
+    k_loc_c4_tasks<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.cpre, a.tpair, a.own, a.cost);
+    nl += 2;
+    nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
+    k_loc_c4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.tpair, a.own, a.pre);
+    nl++;
+    if (ev_fin) record_stage(ev_fin, s);
+    k_finalize_local<<<1, 32, 0, s>>>(a.ctl, commit);
+    nl++;
+    return nl;
+}
+
+}  // namespace gcx

@@ -90,7 +90,7 @@ __global__ void k_region_all(Ctl* c, int n, int32_t* __restrict__ wlist) {
 __global__ void k_u_count(const Ctl* c, const int32_t* __restrict__ wlist, const uint32_t* __restrict__ visited,
                           const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
                           const int32_t* __restrict__ col, const int2* __restrict__ segA,
-                          int32_t* __restrict__ U_deg) {
+                          int32_t* __restrict__ U_deg, int all) {
     int nW = c->nW;
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -100,7 +100,7 @@ __global__ void k_u_count(const Ctl* c, const int32_t* __restrict__ wlist, const
         const int32_t* row = col + row_start[u];
         int d = deg[u], cnt = 0;
         for (int b = 0; b < d; b += 32) {
-            bool ok = b + lane < d && in_region(visited, row[b + lane]);
+            bool ok = b + lane < d && (all || in_region(visited, row[b + lane]));
             cnt += __popc(__ballot_sync(FULL, ok));
         }
         if (lane == 0) {
@@ -116,7 +116,7 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const 
                          const int2* __restrict__ segD, const int32_t* __restrict__ dstA,
                          const int32_t* __restrict__ dstD, const long long* __restrict__ U_off,
                          uint32_t* __restrict__ U_col, int32_t* __restrict__ U_split, int32_t* __restrict__ da,
-                         int32_t* __restrict__ db) {
+                         int32_t* __restrict__ db, int all) {
     int nW = c->nW;
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -129,7 +129,7 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const 
         uint32_t* out = U_col + U_off[u];
         long long len = warp_merge_row(
             col + row_start[u], deg[u], dstA + a.x, na, out, FLAG_A,
-            [&](int32_t v) { return in_region(visited, v); },
+            [&](int32_t v) { return all || in_region(visited, v); },
             [&](int32_t v) { return FLAG_B | ((nd == 0 || !sorted_contains(dl, nd, v)) ? FLAG_A : 0u); });
         __syncwarp();
         if (lane == 0) {

@@ -31,7 +31,7 @@ class gc_options(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
                 ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("chunk_threshold", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("local_max_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class gc_stats(ctypes.Structure):
@@ -41,7 +41,8 @@ class gc_stats(ctypes.Structure):
                 ("region_entries", ctypes.c_int64), ("edges_a", ctypes.c_int64), ("edges_b", ctypes.c_int64),
                 ("Ca", ctypes.c_int64 * 6), ("Cb", ctypes.c_int64 * 6), ("sums_a", ctypes.c_int64 * 6),
                 ("sums_b", ctypes.c_int64 * 6), ("num_edges", ctypes.c_int64), ("ms_device", ctypes.c_float),
-                ("ms_wall", ctypes.c_float), ("relayouts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+                ("ms_wall", ctypes.c_float), ("relayouts", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4),
                 ("ms_stage", ctypes.c_float * 8), ("work_triangles", ctypes.c_int64),
                 ("work_wedges", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved2", ctypes.c_int32 * 3),
                 ("C3a", ctypes.c_int64 * 2), ("C3b", ctypes.c_int64 * 2)]
@@ -165,7 +166,7 @@ def _pairs(p):
 
 
 def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0,
-            chunk_threshold: int = 0, dense_cluster: int = 0):
+            chunk_threshold: int = 0, dense_cluster: int = 0, local_max_pairs: int = 0):
     """Open a graph from a symmetric CSR; returns an opaque handle."""
     lib = load()
     rp = _i32(row_ptr)
@@ -177,6 +178,7 @@ def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, str
     opt.stream = stream or None
     opt.chunk_threshold = chunk_threshold
     opt.dense_cluster = dense_cluster
+    opt.local_max_pairs = local_max_pairs
     h = ctypes.c_void_p()
     rc = lib.gc_open(int(n), _ptr(rp), _ptr(c), ctypes.byref(opt), ctypes.byref(h))
     _check(rc, None)

@@ -1,0 +1,169 @@
+"""Parity of the edge-local delta (gc_options.local_max_pairs) with the oracle.
+
+Small batches on graphs with hubs, cliques and dense cores, dirty batches
+(repeats, cancellations, no-ops), what-if batches, and a batch whose rows
+outgrow the first local scratch.  Every result must equal the oracle's
+Algorithm 2 step bit-exactly; the path actually taken is read back from the
+batch record (stats['path'] == 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import gen
+from gc_testutil import csr_from_edges, edges_from_csr, random_graph
+
+pytestmark = pytest.mark.gpu
+
+ALWAYS = 1 << 30  # local_max_pairs: every batch takes the edge-local path
+NONE = np.zeros((0, 2), np.int32)
+
+
+@pytest.fixture(scope="module")
+def gcb():
+    from paper_2308_14493_gb300 import gc as binding
+
+    binding.load()
+    return binding
+
+
+def mod64(xs):
+    return [int(x) & 0xFFFFFFFFFFFFFFFF for x in xs]
+
+
+def _dirty_batch(rng, n, edges, k_ins, k_del):
+    es = list(edges)
+    ins = [tuple(int(x) for x in rng.choice(n, 2, replace=False)) for _ in range(k_ins)]
+    dels = [es[i] for i in rng.choice(len(es), min(k_del, len(es)), replace=False)] if es else []
+    dels += [tuple(int(x) for x in rng.choice(n, 2, replace=False)) for _ in range(k_del // 3)]
+    if ins and rng.random() < 0.5:
+        dels.append(ins[0][::-1])
+    if dels and rng.random() < 0.5:
+        ins.append(dels[0])
+    if ins:
+        ins.append(ins[-1][::-1])
+    return np.array(ins, np.int32).reshape(-1, 2), np.array(dels, np.int32).reshape(-1, 2)
+
+
+def _step(g, og, ins, dels):
+    r = og.apply(ins, dels)
+    out = g.apply(ins, dels)
+    st = g.stats()
+    assert st["path"] == 1
+    assert out == mod64(r["F"])
+    # the local record holds the deltas: C_a - C_b of the region recount
+    assert st["Ca"] == [a - b for a, b in zip(r["Ca"], r["Cb"])]
+    assert st["Cb"] == [0] * 6
+    assert st["n_ins"] == r["n_ins"] and st["n_del"] == r["n_del"]
+    return r
+
+
+def test_local_dirty_batches_on_random_graphs(gcb):
+    rng = np.random.default_rng(404)
+    for trial in range(30):
+        n = int(rng.integers(6, 120))
+        edges = random_graph(rng, n, float(rng.uniform(0.02, 0.6)))
+        rp, col = csr_from_edges(n, edges)
+        og = oracle.OracleGraph(rp, col, variant="literal")
+        with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+            for step in range(4):
+                cur = edges_from_csr(og.row_ptr, og.col)
+                ins, dels = _dirty_batch(rng, n, cur, int(rng.integers(0, 15)), int(rng.integers(0, 15)))
+                _step(g, og, ins, dels)
+                assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+            grp, gcol = g.export_csr()
+            assert np.array_equal(grp.astype(np.int64), og.row_ptr) and np.array_equal(gcol, og.col)
+
+
+def test_local_batches_inside_cliques(gcb):
+    """Many pairs of one batch inside the same 4-cliques and 4-cycles: each
+    such subgraph must be counted once (at its smallest changed pair)."""
+    rng = np.random.default_rng(7)
+    n = 40
+    full = [(a, b) for a in range(14) for b in range(a + 1, 14)]           # K_14 core
+    ring = [(i, i + 1) for i in range(14, n - 1)] + [(13, 14), (0, n - 1)]  # and a path around it
+    for trial in range(6):
+        drop = [full[i] for i in rng.choice(len(full), size=25, replace=False)]
+        base = sorted(set(full + ring) - set(drop))
+        rp, col = csr_from_edges(n, base)
+        og = oracle.OracleGraph(rp, col, variant="literal")
+        with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+            _step(g, og, np.array(drop, np.int32), NONE)                     # insert them all back
+            dels = [full[i] for i in rng.choice(len(full), size=30, replace=False)]
+            _step(g, og, NONE, np.array(dels, np.int32))                     # delete 30 clique edges
+            mix_i = [e for e in drop[:10]]
+            mix_d = [e for e in full if e not in dels][:10]
+            _step(g, og, np.array(mix_i, np.int32), np.array(mix_d, np.int32))
+
+
+def test_local_and_region_paths_agree_on_c2(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    sizes = [1, 2, 5, 10, 30, 100, 300, 1000]
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 31)
+    with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as gl, gcb.Graph(n, rp, col) as gr:
+        for ins, dels in batches:
+            r = _step(gl, og, ins, dels)
+            assert gr.apply(ins, dels) == mod64(r["F"])
+            assert gr.stats()["path"] == 0
+        assert gl.counts3() == gr.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+
+
+def test_local_threshold_picks_the_path(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=64) as g:
+        for size, path in ((64, 1), (65, 0), (3, 1)):
+            ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), size - size // 2, size // 2, size)
+            r = og.apply(ins, dels)
+            assert g.apply(ins, dels) == mod64(r["F"])
+            assert g.stats()["path"] == path
+
+
+def test_local_what_if_batches_leave_the_graph(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+        for seed in range(5):
+            ins, dels = gen.random_batch(n, keys, 20, 20, 100 + seed)
+            r = oracle.fdgc_step(rp, col, ins, dels, F0, 3)
+            assert g.count_batch(ins, dels) == mod64(r["F"])
+            assert g.stats()["path"] == 1
+            assert g.counts() == mod64(F0)
+        assert g.count_static() == mod64(F0)
+
+
+def test_local_empty_and_noop_batches(gcb):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+        F0 = g.counts()
+        assert g.apply([], []) == F0
+        existing = edges_from_csr(rp, col)[:20]
+        assert g.apply(existing, []) == F0
+        assert g.apply(existing[:5], existing[:5]) == F0
+        with pytest.raises(gcb.GCError):
+            g.apply([(0, n)], [])
+        assert g.counts() == F0
+
+
+def test_local_scratch_grows_for_a_hub(gcb):
+    """A hub of 1.3M neighbours: the union rows of a batch at the hub exceed
+    the first local scratch (2^20 entries); the batch is re-run with larger
+    scratch and still matches the oracle."""
+    L = 1_300_000
+    n = L + 1
+    hub = L
+    rng = np.random.default_rng(3)
+    edges = [(i, hub) for i in range(L)] + [(i, i + 1) for i in range(0, L - 1, 2)]
+    rp, col = csr_from_edges(n, edges)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+        assert g.counts() == mod64(og.F)
+        ins = [(int(a), int(b)) for a, b in rng.integers(0, L, size=(6, 2)) if a != b]
+        dels = [(0, hub), (5, hub), (2, 3)]
+        _step(g, og, np.array(ins, np.int32), np.array(dels, np.int32))
+        assert g.stats()["region_entries"] > (1 << 20)
