@@ -373,6 +373,59 @@ def cpu_oracle_sample(rp, col, batches, budget_s):
     return edges, secs, done, t_static
 
 
+def paper_regime(gcb, torch, n, keys, rp, col, stream, flush, static_ms):
+    """The paper's batch sizes (10 and 100 updates, Figs. 2-4; insert-only IGC
+    and fully dynamic FDGC with p = 0.7) and 1,000, on the n=1.6M m=30M graph:
+    the edge-local delta against the region recount of Algorithm 2, both
+    through gc_apply_batch_device on their own handle (the two graphs take
+    the same batches and stay equal), and against one full static recount."""
+    hl = gcb.gc_open(n, rp, col, stream=stream.cuda_stream, local_max_pairs=1 << 30)
+    hr = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    gcb.gc_autotune(hr, 1)
+    gcb.gc_set_tuning(hr, local_max_pairs=0)  # this handle is the region recount
+    cur = keys
+    out = {}
+    for tag, frac, size in (("igc_10", 1.0, 10), ("igc_100", 1.0, 100), ("fdgc_10", 0.7, 10),
+                            ("fdgc_100", 0.7, 100), ("fdgc_1000", 0.7, 1000)):
+        batches = gen.batch_stream(n, cur, [size] * 6, frac, 700 + size + int(10 * frac))
+        for ins, dels in batches:
+            cur = gen.apply_batch_keys(cur, ins, dels)
+        ms = {"local": [], "region": []}
+        outs = {"local": [], "region": []}
+        paths, ups = [], 0
+        with torch.cuda.stream(stream):
+            for i, (ins, dels) in enumerate(batches):
+                ti = torch.from_numpy(np.ascontiguousarray(ins)).cuda()
+                td = torch.from_numpy(np.ascontiguousarray(dels)).cuda()
+                for form, h in (("local", hl), ("region", hr)):
+                    if flush is not None:
+                        flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    o = gcb.gc_apply_batch_device(h, ti.data_ptr(), ti.shape[0], td.data_ptr(), td.shape[0])
+                    e1.record(stream)
+                    e1.synchronize()
+                    st = gcb.gc_batch_stats(h)
+                    if i > 0:  # the first batch of each size is warm-up (capture)
+                        ms[form].append(e0.elapsed_time(e1))
+                        outs[form].append(o)
+                        if form == "local":
+                            paths.append(st["path"])
+                            ups += st["n_ins"] + st["n_del"]
+        ml, mr = statistics.mean(ms["local"]), statistics.mean(ms["region"])
+        tl = sum(ms["local"]) / 1e3
+        out[tag] = {"batch_updates": size, "ins_frac": frac, "batches_timed": len(ms["local"]),
+                    "local": {"value": ups / tl, "ms_per_batch": ml, "p99_ms": pct(ms["local"], 0.99)},
+                    "region": {"value": ups / (sum(ms["region"]) / 1e3), "ms_per_batch": mr,
+                               "p99_ms": pct(ms["region"], 0.99)},
+                    "local_over_region": mr / ml, "local_over_static_recount": static_ms / ml,
+                    "counts_equal": outs["local"] == outs["region"], "local_path_taken": all(p == 1 for p in paths)}
+    gcb.gc_close(hl)
+    gcb.gc_close(hr)
+    return out
+
+
 def c4_block(gcb, torch, stream, flush, peak, peak_kind):
     """64 independent batches (sizes log-uniform in 10..50,000, 50/50,
     degree-weighted endpoints) against one snapshot of the Chung-Lu
@@ -472,10 +525,14 @@ def gpu_arm(args):
         if not args.no_large and args.workload != "c3":
             try:
                 sp3 = BENCH["c3"]
-                n3, _, rp3, col3, b3 = make_batches(sp3, 1 + 3)
+                n3, keys3, rp3, col3, b3 = make_batches(sp3, 1 + 3)
                 r3, st_ms3, st3 = run_plain(gcb, torch, n3, rp3, col3, b3, 1, 3, stream, None)
                 s3 = summarize(r3)
                 secs3, raw3, outs3, _ = run_batched(gcb, torch, n3, rp3, col3, b3, 1, stream, None)
+                try:
+                    sec["c3_paper_batch_sizes"] = paper_regime(gcb, torch, n3, keys3, rp3, col3, stream, flush, st_ms3)
+                except Exception as e:  # pragma: no cover
+                    sec["c3_paper_batch_sizes"] = {"error": str(e)}
                 sec["c3"] = {"workload": sp3["desc"], "plain": {"value": s3["value"], "ms_per_batch": s3["ms_per_step"],
                                                                  "p99_ms": s3["p99_ms"]},
                              "batched": {"value": s3["edges"] / secs3, "ms_per_batch": 1e3 * secs3 / 3},

@@ -284,7 +284,9 @@ typedef struct {
                                id-range chunks; other pivots above c4_cta_max: a CTA cluster on a
                                dense array in L2; 0 = never */
     int64_t c4_chunk_max;   /* 0 = no upper bound */
-    int64_t reserved[3];
+    int64_t local_max_pairs; /* batches of at most this many pairs take the edge-local delta
+                                (gc_options.local_max_pairs); 0 = never */
+    int64_t reserved[2];
 } gc_tuning;
 
 int gc_get_tuning(const gc_graph *g, gc_tuning *t);
@@ -297,6 +299,11 @@ int gc_set_tuning(gc_graph *g, const gc_tuning *t);
  * the minimum kept).  The fastest set is installed and returned in *best
  * (may be NULL); *best_ms (may be NULL) receives its time.  Counts are
  * checked equal across all candidates (GC_ECUDA if not).
+ * Then the edge-local threshold: what-if batches of k edges sampled
+ * uniformly from the graph (deletions; k = 8, 32, 128, ... up to m / 4 and
+ * 2^16) are timed through the edge-local delta and through the region
+ * recount; local_max_pairs becomes the largest k at which the local form
+ * was faster (0 if never), and the two results must be equal.
  */
 int gc_autotune(gc_graph *g, int32_t reps, gc_tuning *best, float *best_ms);
 

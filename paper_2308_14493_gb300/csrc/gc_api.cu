@@ -112,7 +112,16 @@ struct gc_graph {
     Buf<int32_t> l_cost, l_own, l_pcost, l_ccnt, l_kcost, l_tpair;
     Buf<long long> l_pre, l_ppre, l_cpre, l_kpre;
     Buf<unsigned long long> l_rec;
+    Buf<long long> l_dcnt;
     long long l_cap = 0;
+    int l_t2 = -1;                       // captured with maintained triangle sums
+    // maintained triangle sums of the edge-local path: T2[x] = sum of t_e
+    // over the edges at x, valid after a static count and kept by local
+    // batches (a region batch makes it stale)
+    unsigned long long* T2 = nullptr;
+    long long* dtri2 = nullptr;          // zero between batches
+    uint32_t* visited2 = nullptr;
+    bool t2_valid = false;
     unsigned long long buf_gen = 1;      // bumped whenever a buffer moves
     // host mirror
     uint64_t F[6] = {0, 0, 0, 0, 0, 0};
@@ -243,6 +252,7 @@ __global__ void k_begin_batch(Ctl* c, const long long* desc) {
     c->lovf = 0;
     c->l_np = 0;
     c->l_need = 0;
+    c->l_nw3 = 0;
     for (int k = 0; k < 4; k++) c->l_len[k] = 0;
     for (int k = 0; k < 5; k++) c->l_tot[k] = 0;
 }
@@ -402,6 +412,7 @@ static void release_local(gc_graph* g) {
     release(g, g->l_cpre);
     release(g, g->l_kpre);
     release(g, g->l_rec);
+    release(g, g->l_dcnt);
     g->l_cap = 0;
 }
 
@@ -412,11 +423,11 @@ static int ensure_local(gc_graph* g, long long cap) {
     if (!ensure(g, g->l_cost, c) || !ensure(g, g->l_own, c) || !ensure(g, g->l_pcost, c) ||
         !ensure(g, g->l_ccnt, c) || !ensure(g, g->l_kcost, c) || !ensure(g, g->l_tpair, c) ||
         !ensure(g, g->l_pre, c + 1) || !ensure(g, g->l_ppre, c + 1) || !ensure(g, g->l_cpre, c + 1) ||
-        !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c))
+        !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c) || !ensure(g, g->l_dcnt, c))
         return nomem(g, "edge-local scratch");
     // ensure() may round up; the usable capacity is the smallest array's
     size_t m = std::min({g->l_cost.cap, g->l_own.cap, g->l_pcost.cap, g->l_ccnt.cap, g->l_kcost.cap,
-                         g->l_tpair.cap, g->l_rec.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
+                         g->l_tpair.cap, g->l_rec.cap, g->l_dcnt.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
                          g->l_kpre.cap - 1});
     g->l_cap = (long long)m;
     g->buf_gen++;  // captured graphs hold the old pointers
@@ -540,16 +551,17 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
 
 // Edge-local delta: union rows of the batch endpoints V_X (full rows), then
 // the local terms, 4-cliques and 4-cycles and their closed forms.
-static int count_local(gc_graph* g, int commit, bool timed) {
+static int count_local(gc_graph* g, int commit, bool timed, bool t2) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
     k_reset_count<<<1, 32, 0, s>>>(g->ctl);
+    if (t2) CK(cudaMemsetAsync(g->visited2, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
     k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg, 1);
     g->launches += 2;
     g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
-    k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
-                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 1);
+    k_u_fill_all<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->row_start, g->deg, g->col, g->segA, g->segD, g->dstA.p,
+                                    g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
     k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     LocalArgs la;
@@ -579,8 +591,14 @@ static int count_local(gc_graph* g, int commit, bool timed) {
     la.cpre = g->l_cpre.p;
     la.kpre = g->l_kpre.p;
     la.rec = g->l_rec.p;
+    la.dcnt = g->l_dcnt.p;
+    la.T2 = t2 ? g->T2 : nullptr;
+    la.dtri2 = g->dtri2;
+    la.visited2 = g->visited2;
+    la.wlist_w = g->wlist;
     la.bsum = g->bsum.p;
     la.cap = g->l_cap;
+    la.n = std::max(g->n, 1);
     la.sms = g->sms;
     g->launches += enqueue_local(la, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
                                  timed ? g->ev[5] : nullptr, commit);
@@ -627,7 +645,8 @@ static int enqueue_segments(gc_graph* g, bool clear) {
 //   commit:     apply G <- G \ D u A (else an independent what-if batch)
 //   timed:      record the stage events (event-record nodes in the graph)
 //   local:      the edge-local delta instead of the region recount
-static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed, bool local = false) {
+static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed, bool local = false,
+                         bool t2 = false) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
     k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc);
@@ -663,7 +682,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     }
     CKL();
     if (timed) CK(record_stage(g->ev[2], s));
-    int rc = local ? count_local(g, commit ? 1 : 0, timed) : count_region(g, commit ? 0 : 2, false, timed);
+    int rc = local ? count_local(g, commit ? 1 : 0, timed, t2) : count_region(g, commit ? 0 : 2, false, timed);
     if (rc) return rc;
     if (commit) {
         rc = enqueue_commit(g);
@@ -799,7 +818,7 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
 // Capture the per-batch launch sequence (batch from the run cursor) into
 // *exec; timed: with the stage events as event-record nodes.
 static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool timed, cudaGraphExec_t* exec,
-                         int* launches, bool local = false) {
+                         int* launches, bool local = false, bool t2 = false) {
     cudaStream_t s = g->s;
     if (*exec) {
         cudaGraphExecDestroy(*exec);
@@ -809,7 +828,7 @@ static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool time
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const int lsave = g->launches;
     g->launches = 0;
-    int rc = enqueue_batch(g, shape_nk, commit, timed, local);
+    int rc = enqueue_batch(g, shape_nk, commit, timed, local, t2);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     *launches = g->launches;
     g->launches = lsave;
@@ -862,12 +881,15 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         int* ex_commit = local ? &g->l_commit : &g->p_commit;
         unsigned long long* ex_gen = local ? &g->l_gen : &g->p_gen;
         int* ex_launches = local ? &g->l_launches : &g->p_launches;
-        if (!*ex || *ex_nk != shape_nk || *ex_commit != commit || *ex_gen != g->buf_gen) {
-            rc = capture_batch(g, shape_nk, commit != 0, true, ex, ex_launches, local);
+        const bool t2 = local && g->t2_valid;
+        if (!*ex || *ex_nk != shape_nk || *ex_commit != commit || *ex_gen != g->buf_gen ||
+            (local && g->l_t2 != (int)t2)) {
+            rc = capture_batch(g, shape_nk, commit != 0, true, ex, ex_launches, local, t2);
             if (rc) return rc;
             *ex_nk = shape_nk;
             *ex_commit = commit;
             *ex_gen = g->buf_gen;
+            if (local) g->l_t2 = (int)t2;
         }
         g->h_desc[0] = (long long)d_ins;
         g->h_desc[1] = (long long)d_del;
@@ -890,8 +912,9 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         }
         if (!(local && g->h_ctl->lovf)) break;
         // the local scratch was too small and nothing was applied: grow it
-        // once to what the batch needed, else take the region path
-        if (attempt == 0) {
+        // to what the batch needed (each of the two bound checks can report
+        // its own need), else take the region path
+        if (attempt < 2) {
             long long need = g->h_ctl->l_need;
             rc = ensure_local(g, need + need / 4 + 1024);
             if (rc) return rc;
@@ -922,6 +945,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         stage_times(g, 0, 7);
     }
     g->st.path = local ? 1 : 0;
+    if (commit && !local) g->t2_valid = false;  // the region pass does not keep the triangle sums
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
         for (int i = 0; i < 2; i++) g->F3[i] = c.F3[i];
@@ -937,11 +961,12 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
 // Batched form: k batches whose pairs are in device memory, described by
 // h_batches[k][4] = {ins_off, n_ins, del_off, n_del} (in pairs, relative to
 // d_ins / d_del).  One captured graph per batch shape, replayed k times.
-static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t* d_del, const long long* h_batches,
+static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t* d_del, const long long* h_batches,
                                 int k, int independent, uint64_t* out) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = g->s;
     const bool commit = !independent;
+    if (commit) g->t2_valid = false;  // region passes do not keep the triangle sums
     long long max_nk = 0, max_ins = 0, sum_ins = 0, raw_ins = 0, raw_del = 0;
     for (int i = 0; i < k; i++) {
         long long ni = h_batches[4 * i + 1], nd = h_batches[4 * i + 3];
@@ -1049,13 +1074,21 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
     CK(cudaEventRecord(g->ev[2], s));
     rc = count_region(g, 1, set_F, true);
     if (rc) return rc;
+    // the static pass also gives the triangle sums of the edge-local path
+    CK(cudaMemsetAsync(g->T2, 0, 8 * (size_t)std::max(g->n, 1), s));
+    k_t2_from_static<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p,
+                                                   g->T2);
+    g->launches++;
+    CKL();
     rc = read_ctl(g);
     if (rc) return rc;
+    g->t2_valid = true;
     if (out)
         for (int i = 0; i < 6; i++) out[i] = (uint64_t)g->h_ctl->Ca[i];
-    if (set_F)
+    if (set_F) {
         for (int i = 0; i < 6; i++) g->F[i] = (uint64_t)g->h_ctl->Ca[i];
         for (int i = 0; i < 2; i++) g->F3[i] = (uint64_t)g->h_ctl->C3a[i];
+    }
     // a static count leaves its stage times in the stats record
     stage_times(g, 2, 6);
     if (cudaEventElapsedTime(&g->st.ms_device, g->ev[2], g->ev[6]) != cudaSuccess) cudaGetLastError();
@@ -1084,6 +1117,9 @@ static void destroy(gc_graph* g) {
     dfree(g, g->segA);
     dfree(g, g->segD);
     dfree(g, g->visited);
+    dfree(g, g->visited2);
+    dfree(g, g->T2);
+    dfree(g, g->dtri2);
     release(g, g->U_col);
     release(g, g->tpack);
     release(g, g->keys);
@@ -1148,6 +1184,12 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     g->segA = (int2*)dalloc(g, sizeof(int2) * nn);
     g->segD = (int2*)dalloc(g, sizeof(int2) * nn);
     g->visited = (uint32_t*)dalloc(g, 4 * ((nn + 31) / 32 + 1));
+    g->visited2 = (uint32_t*)dalloc(g, 4 * ((nn + 31) / 32 + 1));
+    g->T2 = (unsigned long long*)dalloc(g, 8 * nn);
+    g->dtri2 = (long long*)dalloc(g, 8 * nn);
+    if (!g->visited2 || !g->T2 || !g->dtri2) return nomem(g, "triangle sums");
+    CK(cudaMemsetAsync(g->dtri2, 0, 8 * nn, s));
+    CK(cudaMemsetAsync(g->T2, 0, 8 * nn, s));
     if (!g->perm || !g->iperm || !g->deg || !g->cap || !g->wlist || !g->U_deg || !g->U_split || !g->da || !g->db ||
         !g->row_start || !g->U_off || !g->U_wt || !g->ctl || !g->segA || !g->segD || !g->visited)
         return nomem(g, "graph state");
@@ -1522,10 +1564,18 @@ static int grow_vertices(gc_graph* g, long long k) {
               grow((void**)&g->U_off, 8, nn + 1, 0, false) && grow((void**)&g->U_wt, 8, nn, 0, false) &&
               grow((void**)&g->segA, sizeof(int2), nn, 0, false) && grow((void**)&g->segD, sizeof(int2), nn, 0, false) &&
               grow((void**)&g->visited, 4, (nn + 31) / 32 + 1, 0, false) &&
+              grow((void**)&g->visited2, 4, (nn + 31) / 32 + 1, 0, false) &&
+              grow((void**)&g->T2, 8, nn, old_nn, true) && grow((void**)&g->dtri2, 8, nn, 0, false) &&
               grow((void**)&g->bins, 4, (size_t)NBINS * nn, 0, false);
     if (!ok) return nomem(g, "vertex arrays");
     CK(cudaMemsetAsync(g->segA, 0, sizeof(int2) * nn, s));
     CK(cudaMemsetAsync(g->segD, 0, sizeof(int2) * nn, s));
+    // new vertices are isolated: no triangles
+    CK(cudaMemsetAsync(g->dtri2, 0, 8 * nn, s));
+    {
+        const size_t kept = n0 > 0 ? (size_t)n0 : 0;
+        CK(cudaMemsetAsync(g->T2 + kept, 0, 8 * (nn - kept), s));
+    }
     k_init_new_vertices<<<grid_elems(g, k), TPB, 0, s>>>(g->perm, g->iperm, g->deg, g->cap, g->row_start, n0, n1);
     CKL();
     release(g, g->dense);
@@ -1609,6 +1659,66 @@ int gc_delete_vertices(gc_graph* g, const int32_t* ids, int64_t k, uint64_t out[
     }
     // an edge between two listed vertices appears twice; normalisation collapses it
     return apply_device(g, g->pairs.p, 0, g->pairs.p, total, 1, out);
+}
+
+// A run of batches: those of at most local_max_pairs pairs take the
+// edge-local delta one at a time (in order, when the run commits), the
+// others run as captured region runs.
+static int apply_batches_device(gc_graph* g, const int32_t* d_ins, const int32_t* d_del, const long long* h_batches,
+                                int k, int independent, uint64_t* out) {
+    const long long L = g->opt.local_max_pairs;
+    int nloc = 0;
+    for (int i = 0; i < k; i++) nloc += (L > 0 && h_batches[4 * i + 1] + h_batches[4 * i + 3] <= L) ? 1 : 0;
+    if (nloc == 0) return apply_batches_region(g, d_ins, d_del, h_batches, k, independent, out);
+    auto t0 = std::chrono::steady_clock::now();
+    const int commit = independent ? 0 : 1;
+    float ms = 0.f;
+    int launches = 0, relayouts = 0;
+    std::vector<long long> sub;
+    std::vector<int> idx;
+    std::vector<uint64_t> tmp;
+    auto run_region = [&]() -> int {
+        if (idx.empty()) return GC_OK;
+        tmp.assign(6 * idx.size(), 0);
+        int rc = apply_batches_region(g, d_ins, d_del, sub.data(), (int)idx.size(), independent, tmp.data());
+        if (rc) return rc;
+        if (out)
+            for (size_t j = 0; j < idx.size(); j++)
+                for (int q = 0; q < 6; q++) out[6 * (size_t)idx[j] + q] = tmp[6 * j + q];
+        ms += g->st.ms_device;
+        launches += g->st.launches;
+        relayouts += g->st.relayouts;
+        sub.clear();
+        idx.clear();
+        return GC_OK;
+    };
+    for (int i = 0; i < k; i++) {
+        const long long* b = h_batches + 4 * (size_t)i;
+        if (!(L > 0 && b[1] + b[3] <= L)) {
+            sub.insert(sub.end(), b, b + 4);
+            idx.push_back(i);
+            continue;
+        }
+        if (commit) {
+            int rc = run_region();  // batches before this one first
+            if (rc) return rc;
+        }
+        uint64_t o[6];
+        int rc = apply_device(g, d_ins + 2 * b[0], b[1], d_del + 2 * b[2], b[3], commit, o);
+        if (rc) return rc;
+        if (out)
+            for (int q = 0; q < 6; q++) out[6 * (size_t)i + q] = o[q];
+        ms += g->st.ms_device;
+        launches += g->st.launches;
+        relayouts += g->st.relayouts;
+    }
+    int rc = run_region();
+    if (rc) return rc;
+    g->st.ms_device = ms;
+    g->st.launches = launches;
+    g->st.relayouts = relayouts;
+    g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return GC_OK;
 }
 
 int gc_apply_batches(gc_graph* g, const int32_t* const* ins, const int64_t* n_ins, const int32_t* const* del,
@@ -1710,7 +1820,7 @@ int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
     return GC_OK;
 }
 
-static void tuning_to_abi(const Tuning& t, gc_tuning* o) {
+static void tuning_to_abi(const Tuning& t, long long local_max_pairs, gc_tuning* o) {
     std::memset(o, 0, sizeof(*o));
     o->tri_warp_max = t.tri_warp_max;
     o->tri_small_max = t.tri_small_max;
@@ -1721,19 +1831,21 @@ static void tuning_to_abi(const Tuning& t, gc_tuning* o) {
     o->c4_cta_max = t.c4_cta_max;
     o->c4_chunk_min = t.c4_chunk_min >= NEVER ? 0 : t.c4_chunk_min;
     o->c4_chunk_max = t.c4_chunk_max >= NEVER ? 0 : t.c4_chunk_max;
+    o->local_max_pairs = local_max_pairs;
 }
 
 int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
-    tuning_to_abi(g->tune, t);
+    tuning_to_abi(g->tune, g->opt.local_max_pairs, t);
     return GC_OK;
 }
 
 int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
     if (t->tri_warp_max < 1 || t->tri_small_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
-        t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0 || t->c4_chunk_max < 0) {
-        g->err = "tuning: every bound must be positive (c4_chunk_min may be 0)";
+        t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0 || t->c4_chunk_max < 0 ||
+        t->local_max_pairs < 0) {
+        g->err = "tuning: every bound must be positive (c4_chunk_min and local_max_pairs may be 0)";
         return GC_EINVAL;
     }
     Tuning n;
@@ -1748,6 +1860,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     n.c4_chunk_max = t->c4_chunk_max == 0 ? NEVER : t->c4_chunk_max;
     if (n.c4_chunk_min < NEVER && !ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     g->tune = n;
+    g->opt.local_max_pairs = (int32_t)std::min<int64_t>(t->local_max_pairs, INT32_MAX);
     return GC_OK;
 }
 
@@ -1760,6 +1873,74 @@ static int time_static(gc_graph* g, int reps, float* ms, uint64_t out[6]) {
         best = std::min(best, g->st.ms_device);
     }
     *ms = best;
+    return GC_OK;
+}
+
+// k edges drawn uniformly (with repetition) from the current graph, as
+// external-id pairs: draw i picks directed entry r = h(seed, i) mod 2m
+// through the degree prefix sums cum (splitmix64 of the draw index).
+__global__ void k_sample_edges(const long long* __restrict__ cum, int n, const long long* __restrict__ row_start,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ iperm,
+                               unsigned long long seed, int k, int32_t* __restrict__ pairs) {
+    const long long m2 = cum[n];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const long long r = (long long)(z % (unsigned long long)m2);
+        long long lo = 0, hi = n;  // last u with cum[u] <= r
+        while (hi - lo > 1) {
+            const long long mid = (lo + hi) >> 1;
+            if (cum[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        const int32_t u = (int32_t)lo;
+        const int32_t v = col[row_start[u] + (r - cum[u])];
+        pairs[2 * i] = iperm[u];
+        pairs[2 * i + 1] = iperm[v];
+    }
+}
+
+// The edge-local threshold by measurement (see gc_autotune).
+static int calibrate_local(gc_graph* g, int reps) {
+    const int32_t saved = g->opt.local_max_pairs;
+    if (g->m < 64 || g->n < 2) {
+        g->opt.local_max_pairs = 0;
+        return GC_OK;
+    }
+    cudaStream_t s = g->s;
+    const long long kmax = std::min<long long>(g->m / 4, 1LL << 16);
+    if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(kmax, 8))) return nomem(g, "calibration pairs");
+    // degree prefix sums (the union-graph offsets are free between batches)
+    g->launches += scan_i32_to_i64(g->deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), nullptr, s);
+    long long thr = 0;
+    for (long long k = 8; k <= kmax; k *= 4) {
+        k_sample_edges<<<grid_elems(g, k), TPB, 0, s>>>(g->U_off, g->n, g->row_start, g->col, g->iperm,
+                                                        0x5DEECE66Dull + (unsigned long long)k, (int)k, g->pairs.p);
+        CKL();
+        float best[2] = {1e30f, 1e30f};
+        uint64_t res[2][6];
+        for (int form = 0; form < 2; form++) {
+            g->opt.local_max_pairs = form == 0 ? (int32_t)k : 0;
+            for (int r = 0; r < std::max(reps, 1) + 1; r++) {  // the first run captures
+                int rc = apply_device(g, g->pairs.p, 0, g->pairs.p, k, 0, res[form]);
+                if (rc) {
+                    g->opt.local_max_pairs = saved;
+                    return rc;
+                }
+                if (r > 0) best[form] = std::min(best[form], g->st.ms_device);
+            }
+        }
+        if (std::memcmp(res[0], res[1], sizeof(res[0])) != 0) {
+            g->opt.local_max_pairs = saved;
+            g->err = "autotune: the edge-local and region results differ";
+            return GC_ECUDA;
+        }
+        if (best[0] < best[1]) thr = k;
+        else break;
+    }
+    g->opt.local_max_pairs = (int32_t)thr;
     return GC_OK;
 }
 
@@ -1849,7 +2030,9 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
         if (!moved) break;
     }
     g->tune = cur;
-    if (best) tuning_to_abi(cur, best);
+    rc = calibrate_local(g, reps);
+    if (rc) return rc;
+    if (best) tuning_to_abi(cur, g->opt.local_max_pairs, best);
     if (best_ms) *best_ms = cur_ms;
     return GC_OK;
 }

@@ -157,23 +157,20 @@ __global__ void k_commit_plan(Ctl* c, const int32_t* __restrict__ wlist, const i
     }
 }
 
+// A block per touched vertex: row \ D_u u A_u into the scratch (every
+// entry placed by binary searches, so hub rows spread over the block).
 __global__ void k_commit_merge(const Ctl* c, const int32_t* __restrict__ wlist, const int2* __restrict__ segA,
                                const int2* __restrict__ segD, const int32_t* __restrict__ dstA,
                                const int32_t* __restrict__ dstD, const int32_t* __restrict__ deg,
                                const long long* __restrict__ row_start, const int32_t* __restrict__ col,
                                const long long* __restrict__ plan_scr, uint32_t* __restrict__ scratch) {
     if (c->err || c->overflow || c->lovf) return;
-    int ns = c->lvl[0];
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < ns; i += nwarps) {
-        int32_t u = wlist[i];
-        int2 a = segA[u], d = segD[u];
-        const int32_t* dl = dstD + d.x;
-        long long nd = d.y - d.x;
-        warp_merge_row(col + row_start[u], deg[u], dstA + a.x, a.y - a.x, scratch + plan_scr[i], 0u,
-                       [&](int32_t v) { return nd == 0 || !sorted_contains(dl, nd, v); },
-                       [](int32_t) { return 0u; });
+    const int ns = c->lvl[0];
+    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+        const int32_t u = wlist[i];
+        const int2 a = segA[u], d = segD[u];
+        block_merge_row(col + row_start[u], deg[u], dstA + a.x, a.y - a.x, dstD + d.x, d.y - d.x,
+                        scratch + plan_scr[i], false, 0u, 0u, 0u);
     }
 }
 
@@ -183,16 +180,13 @@ __global__ void k_commit_write(const Ctl* c, const int32_t* __restrict__ wlist, 
                                int32_t* __restrict__ deg, int32_t* __restrict__ cap,
                                long long* __restrict__ row_start, int32_t* __restrict__ col) {
     if (c->err || c->overflow || c->lovf) return;
-    int ns = c->lvl[0];
-    int lane = threadIdx.x & 31;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < ns; i += nwarps) {
-        int32_t u = wlist[i];
-        long long dst = plan_dst[i], scr = plan_scr[i];
-        int nd = plan_deg[i];
-        for (int j = lane; j < nd; j += 32) col[dst + j] = (int32_t)scratch[scr + j];
-        if (lane == 0) {
+    const int ns = c->lvl[0];
+    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+        const int32_t u = wlist[i];
+        const long long dst = plan_dst[i], scr = plan_scr[i];
+        const int nd = plan_deg[i];
+        for (int j = threadIdx.x; j < nd; j += blockDim.x) col[dst + j] = (int32_t)scratch[scr + j];
+        if (threadIdx.x == 0) {
             deg[u] = nd;
             cap[u] = plan_cap[i];
             row_start[u] = dst;

@@ -95,6 +95,7 @@ struct Ctl {
     long long l_tot[5];              // totals: [0] triangle probes [1] records [2] 4-clique probes
                                      // [3] 4-cycle tasks [4] 4-cycle probes
     long long l_need;                // entries the largest local array needed
+    int l_nw3;                       // third vertices listed after V_X (maintained triangle sums)
     // (device-only tail: the host mirror copies the block up to here)
     unsigned long long accs[NACC][ACC_STRIPES];  // acc, striped: kernels add here, k_finalize sums
 };
@@ -220,6 +221,34 @@ __device__ __forceinline__ long long warp_merge_row(const int32_t* __restrict__ 
     }
     for (long long j = ia + lane; j < na; j += 32) out[obase + (j - ia)] = (uint32_t)ins[j] | ins_tag;
     return obase + (na - ia);
+}
+
+// Block-cooperative merge of one sorted row with sorted insertions `ins`
+// (ids absent from the row) and sorted deletions `del` (ids present in it):
+// every entry finds its output position by binary searches in the others,
+// so a long row spreads over the block.  keep_del: deletions stay, tagged
+// del_tag (else they are dropped); other row entries get row_tag,
+// insertions ins_tag.  The output is sorted by id.  Every thread of the
+// block calls it; returns the output length.
+__device__ __forceinline__ long long block_merge_row(const int32_t* __restrict__ row, long long d,
+                                                     const int32_t* __restrict__ ins, long long na,
+                                                     const int32_t* __restrict__ del, long long nd,
+                                                     uint32_t* __restrict__ out, bool keep_del, uint32_t row_tag,
+                                                     uint32_t ins_tag, uint32_t del_tag) {
+    for (long long j = threadIdx.x; j < d; j += blockDim.x) {
+        const int32_t v = row[j];
+        const long long db = lower_bound_i32(del, nd, v);
+        const bool is_del = db < nd && del[db] == v;
+        if (is_del && !keep_del) continue;
+        out[j - (keep_del ? 0 : db) + lower_bound_i32(ins, na, v)] = (uint32_t)v | (is_del ? del_tag : row_tag);
+    }
+    for (long long i = threadIdx.x; i < na; i += blockDim.x) {
+        const int32_t a = ins[i];
+        const long long rb = lower_bound_i32(row, d, a);
+        const long long db = keep_del ? 0 : lower_bound_i32(del, nd, a);
+        out[i + rb - db] = (uint32_t)a | ins_tag;
+    }
+    return d + na - (keep_del ? 0 : nd);
 }
 
 __device__ __forceinline__ bool sorted_contains(const int32_t* a, long long len, int32_t key) {

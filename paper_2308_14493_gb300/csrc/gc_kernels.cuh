@@ -54,6 +54,11 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* wlist, const uint32_t* vis
                          const int32_t* dstA, const int32_t* dstD, const long long* U_off, uint32_t* U_col,
                          int32_t* U_split, int32_t* da, int32_t* db, int all);
 
+__global__ void k_u_fill_all(const Ctl* c, const int32_t* wlist, const long long* row_start, const int32_t* deg,
+                             const int32_t* col, const int2* segA, const int2* segD, const int32_t* dstA,
+                             const int32_t* dstD, const long long* U_off, uint32_t* U_col, int32_t* U_split,
+                             int32_t* da, int32_t* db);
+
 // gc_count.cu
 __global__ void k_reset_count(Ctl* c);
 __global__ void k_zero_u64(unsigned long long* a, const long long* d_len);
@@ -117,10 +122,20 @@ struct LocalArgs {
     int32_t *cost, *own, *pcost, *ccnt, *kcost, *tpair;
     long long *pre, *ppre, *cpre, *kpre;
     unsigned long long* rec;
+    long long* dcnt;               // per-entry change of t (cap entries)
+    // maintained triangle sums (null: not valid, every edge at V_X is intersected)
+    unsigned long long* T2;        // n: sum of t_e over the edges at each vertex
+    long long* dtri2;              // n zeroed words: its change in the batch (cleared after)
+    uint32_t* visited2;            // n bits, zeroed: third vertices already listed
+    int32_t* wlist_w;              // = wlist (third vertices are appended after V_X)
     long long* bsum;               // 1024 words
     long long cap;
+    int n;                         // vertex id bound (U_off has n + 1 entries)
     int sms;
 };
+// T2 (zeroed) from a static count: sum of t_e over the edges at each vertex.
+__global__ void k_t2_from_static(const Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
+                                 const int32_t* U_split, const unsigned long long* tpack, unsigned long long* T2);
 // Enqueue the edge-local delta (after the union rows of V_X); events mark
 // the triangle stage, the 4-clique / 4-cycle stage and the closed forms.
 int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,

@@ -27,6 +27,17 @@
 // are numbered through prefix sums (an exclusive scan of per-task counts)
 // and dealt one per thread, so hub rows spread over the whole grid.
 //
+// Maintained triangle sums.  With T2[x] = sum of t_e over the edges e at x
+// (twice the triangles at x) kept for the current graph, the per-edge t of
+// the edges at V_X is not needed: TT = 1/2 sum_x T2(x) (d_x - 2) changes
+// only at V_X and at the third vertices of triangles through changed pairs;
+// P needs the degree products of the edges at V_X (a row scan) and the
+// change of sum t; D = sum C(t_e, 2) changes only on edges whose t changes,
+// and those are edges of triangles through changed pairs, found from the
+// pairs' common-neighbour records (each such triangle taken once, at its
+// smallest changed pair).  Only they need an intersection (for the old t).
+// Without valid T2 (after a region batch) every edge at V_X is intersected.
+//
 // Rows.  A vertex of V_X reads its union row from U (N(u) u A_u, entries
 // flagged FLAG_A / FLAG_B as in the region path, built over the full row).
 // Any other vertex is untouched by the batch and reads its adjacency row
@@ -90,15 +101,38 @@ __device__ __forceinline__ int row_find(const Row& r, int lo, uint32_t z) {
     return (p < r.len && vid(r.p[p]) == z) ? p : -1;
 }
 
-// last i in [0, n) with pre[i] <= t (pre non-decreasing, pre[0] = 0 <= t < pre[n])
-__device__ __forceinline__ long long locate(const long long* __restrict__ pre, long long n, long long t) {
-    long long lo = 0, hi = n;
+// last i in [lo, n) with pre[i] <= t (pre non-decreasing, pre[lo] <= t < pre[n])
+__device__ __forceinline__ long long locate(const long long* __restrict__ pre, long long n, long long t,
+                                            long long lo = 0) {
+    long long hi = n;
     while (hi - lo > 1) {
         const long long mid = (lo + hi) >> 1;
         if (pre[mid] <= t) lo = mid;
         else hi = mid;
     }
     return lo;
+}
+
+// The same for the 32 consecutive t of a warp (t non-decreasing over the
+// lanes; every lane calls it): one search for lane 0, then each lane steps
+// forward over a few task boundaries, or searches the rest when there are
+// more (runs of empty tasks).
+__device__ __forceinline__ long long locate_warp(const long long* __restrict__ pre, long long n, long long t,
+                                                 bool valid) {
+    const long long t0 = __shfl_sync(FULL, t, 0);
+    long long e = 0;
+    if ((threadIdx.x & 31) == 0) e = locate(pre, n, t0);
+    e = __shfl_sync(FULL, e, 0);
+    if (valid) {
+        for (int k = 0; e + 1 < n && pre[e + 1] <= t; k++) {
+            if (k == 4) {
+                e = locate(pre, n, t, e + 1);
+                break;
+            }
+            e++;
+        }
+    }
+    return e;
 }
 
 __device__ __forceinline__ unsigned long long pkey(uint32_t a, uint32_t b) {
@@ -136,6 +170,19 @@ __device__ __forceinline__ void acc_warp(Ctl* c, int slot, unsigned long long x)
         const int stripe = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (ACC_STRIPES - 1));
         atomicAdd(&c->accs[slot][stripe], x);
     }
+}
+
+// Position in U_col of the entry that stands for edge (x, y), x in V_X: the
+// row of the lower endpoint when both are in V_X, else x's row (the entry
+// the per-edge kernels take; the edge is in the union graph).
+__device__ __forceinline__ long long canon_pos(const LocalView& V, uint32_t x, uint32_t y) {
+    if (in_x(V.visited, y) && y < x) {
+        const uint32_t t = x;
+        x = y;
+        y = t;
+    }
+    const Row r = V.urow(x);
+    return V.U_off[x] + row_find(r, 0, y);
 }
 
 // packed common-neighbour record of a changed pair (u, v): id z, the flags of
@@ -185,26 +232,33 @@ __global__ void k_loc_check_pairs(Ctl* c, long long cap) {
 
 // ---- triangles per edge with an endpoint in V_X -----------------------------
 
-// Probes of edge (u, w) for u in V_X: the shorter of the two rows.  An edge
-// with both endpoints in V_X is taken from its lower endpoint only.
-__global__ void k_loc_tri_cost(const Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
-                               int32_t* __restrict__ cost, int32_t* __restrict__ own) {
-    if (c->l_len[0] == 0) return;
-    const int nX = c->lvl[0];
+// Owner of every union-row entry: own[e] = u for the entries of u's row (a
+// warp per vertex of V_X; a hub row is a long run of coalesced stores).
+__global__ void k_loc_owner(const Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
+                            int32_t* __restrict__ own) {
+    const int nX = c->l_len[0] ? c->lvl[0] : 0;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < nX; i += nwarps) {
-        const uint32_t u = (uint32_t)wlist[i];
-        const Row ru = V.urow(u);
-        const long long base = V.U_off[u];
-        for (int j = lane; j < ru.len; j += 32) {
-            const uint32_t w = vid(ru.p[j]);
-            int k = 0;
-            if (!(in_x(V.visited, w) && w < u)) k = min(ru.len, V.row(w).len);
-            cost[base + j] = k;
-            own[base + j] = (int32_t)u;
-        }
+        const int32_t u = wlist[i];
+        const long long b = V.U_off[u], e = V.U_off[u + 1];
+        for (long long j = b + lane; j < e; j += 32) own[j] = u;
+    }
+}
+
+// Probes of edge (u, w) for u in V_X: the shorter of the two rows.  An edge
+// with both endpoints in V_X is taken from its lower endpoint only.
+__global__ void k_loc_tri_cost(const Ctl* c, LocalView V, const int32_t* __restrict__ own,
+                               int32_t* __restrict__ cost) {
+    const long long tot = c->l_len[0];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)own[e];
+        const uint32_t w = vid(V.U_col[e]);
+        int k = 0;
+        if (!(in_x(V.visited, w) && w < u)) k = min((int)(V.U_off[u + 1] - V.U_off[u]), V.row(w).len);
+        cost[e] = k;
     }
 }
 
@@ -215,9 +269,11 @@ __global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict
     const long long n = c->l_len[0];
     if (n == 0) return;
     const long long tot = pre[n];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long e = locate(pre, n, t);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
+        const long long t = tb + (threadIdx.x & 31);
+        const long long e = locate_warp(pre, n, t, t < tot);
+        if (t >= tot) continue;
         const int k = (int)(t - pre[e]);
         const uint32_t u = (uint32_t)own[e];
         const Row ru = V.urow(u);
@@ -240,50 +296,48 @@ __global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict
 
 // ---- per-edge and per-vertex terms --------------------------------------------
 
-// The a- and b-side terms of every edge with an endpoint in V_X and of every
-// vertex of V_X, into the accumulator slots of the region path.
+// The a- and b-side terms of every edge with an endpoint in V_X (a thread
+// per entry) and of every vertex of V_X, into the accumulator slots of the
+// region path.
 __global__ void k_loc_terms(Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
-                            const unsigned long long* __restrict__ tpack, const int32_t* __restrict__ da,
-                            const int32_t* __restrict__ db) {
-    const int nX = c->l_len[0] ? c->lvl[0] : 0;
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+                            const int32_t* __restrict__ own, const unsigned long long* __restrict__ tpack,
+                            const int32_t* __restrict__ da, const int32_t* __restrict__ db) {
+    const long long tot = c->l_len[0];
+    const int nX = tot ? c->lvl[0] : 0;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned long long P[2] = {0, 0}, S[2] = {0, 0}, T[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0};
     unsigned long long T3[2] = {0, 0}, W2[2] = {0, 0};
-    for (int i = warp; i < nX; i += nwarps) {
+    for (long long i = gid; i < nX; i += stride) {
         const uint32_t u = (uint32_t)wlist[i];
+        S[0] += choose3((unsigned long long)da[u]);
+        S[1] += choose3((unsigned long long)db[u]);
+        W2[0] += choose2((unsigned long long)da[u]);
+        W2[1] += choose2((unsigned long long)db[u]);
+    }
+    for (long long e = gid; e < tot; e += stride) {
+        const uint32_t u = (uint32_t)own[e];
+        const uint32_t fe = V.U_col[e];
+        const uint32_t w = vid(fe);
+        const bool wx = in_x(V.visited, w);
+        if (wx && w < u) continue;
         const long long dau = da[u], dbu = db[u];
-        if (lane == 0) {
-            S[0] += choose3((unsigned long long)dau);
-            S[1] += choose3((unsigned long long)dbu);
-            W2[0] += choose2((unsigned long long)dau);
-            W2[1] += choose2((unsigned long long)dbu);
+        const unsigned long long t = tpack[e];
+        if (fe & FLAG_A) {
+            const long long dw = wx ? da[w] : V.deg[w], tt = (long long)(t >> 32);
+            P[0] += (unsigned long long)((dau - 1) * (dw - 1) - tt);
+            T[0] += (unsigned long long)(tt * (dau + dw - 4));
+            D[0] += choose2((unsigned long long)tt);
+            T3[0] += (unsigned long long)tt;
+            E[0] += 1;
         }
-        const Row ru = V.urow(u);
-        const long long base = V.U_off[u];
-        for (int j = lane; j < ru.len; j += 32) {
-            const uint32_t fe = ru.p[j];
-            const uint32_t w = vid(fe);
-            const bool wx = in_x(V.visited, w);
-            if (wx && w < u) continue;
-            const unsigned long long t = tpack[base + j];
-            if (fe & FLAG_A) {
-                const long long dw = wx ? da[w] : V.deg[w], tt = (long long)(t >> 32);
-                P[0] += (unsigned long long)((dau - 1) * (dw - 1) - tt);
-                T[0] += (unsigned long long)(tt * (dau + dw - 4));
-                D[0] += choose2((unsigned long long)tt);
-                T3[0] += (unsigned long long)tt;
-                E[0] += 1;
-            }
-            if (fe & FLAG_B) {
-                const long long dw = wx ? db[w] : V.deg[w], tt = (long long)(t & 0xFFFFFFFFull);
-                P[1] += (unsigned long long)((dbu - 1) * (dw - 1) - tt);
-                T[1] += (unsigned long long)(tt * (dbu + dw - 4));
-                D[1] += choose2((unsigned long long)tt);
-                T3[1] += (unsigned long long)tt;
-                E[1] += 1;
-            }
+        if (fe & FLAG_B) {
+            const long long dw = wx ? db[w] : V.deg[w], tt = (long long)(t & 0xFFFFFFFFull);
+            P[1] += (unsigned long long)((dbu - 1) * (dw - 1) - tt);
+            T[1] += (unsigned long long)(tt * (dbu + dw - 4));
+            D[1] += choose2((unsigned long long)tt);
+            T3[1] += (unsigned long long)tt;
+            E[1] += 1;
         }
     }
     for (int g = 0; g < 2; g++) {
@@ -330,9 +384,11 @@ __global__ void k_loc_common(const Ctl* c, LocalView V, const int32_t* __restric
                              unsigned long long* __restrict__ rec) {
     const long long np = c->l_len[1];
     const long long tot = c->l_len[2];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long i = locate(ppre, np, t);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
+        const long long t = tb + (threadIdx.x & 31);
+        const long long i = locate_warp(ppre, np, t, t < tot);
+        if (t >= tot) continue;
         const int k = (int)(t - ppre[i]);
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
         const Row ra = V.urow(p.a), rb = V.urow(p.b);
@@ -367,12 +423,14 @@ __global__ void k_loc_k4_cost(const Ctl* c, LocalView V, const int32_t* __restri
                               const unsigned long long* __restrict__ rec, int32_t* __restrict__ kcost) {
     const long long np = c->l_len[1];
     const long long tot = c->l_len[2];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
+        const long long t = tb + (threadIdx.x & 31);
+        const long long i = locate_warp(ppre, np, t, t < tot);
+        if (t >= tot) continue;
         const unsigned long long r = rec[t];
         int k = 0;
         if (r & T_VALID) {
-            const long long i = locate(ppre, np, t);
             const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
             if (t_flags(r, T_FU) & t_flags(r, T_FV) & p.x) {
                 const uint32_t w = (uint32_t)(r & 0xFFFFFFFFull);
@@ -394,11 +452,13 @@ __global__ void k_loc_k4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
     const long long n = c->l_len[2];
     const long long tot = n ? kpre[n] : 0;
     unsigned long long ka = 0, kb = 0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < tot;
-         s += (long long)gridDim.x * blockDim.x) {
-        const long long t = locate(kpre, n, s);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long sb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); sb < tot; sb += stride) {
+        const long long s = sb + (threadIdx.x & 31);
+        const long long t = locate_warp(kpre, n, s, s < tot);
+        const long long i = locate_warp(ppre, np, t, s < tot);
+        if (s >= tot) continue;
         const int k = (int)(s - kpre[t]);
-        const long long i = locate(ppre, np, t);
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
         const unsigned long long rw_rec = rec[t];
         const uint32_t w = (uint32_t)(rw_rec & 0xFFFFFFFFull);
@@ -469,27 +529,23 @@ __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restr
                                int32_t* __restrict__ tpair, int32_t* __restrict__ tent,
                                int32_t* __restrict__ tcost) {
     const long long np = c->l_len[1];
-    if (c->l_len[3] == 0) return;
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = warp; i < np; i += nwarps) {
-        const long long b0 = cpre[i], m = cpre[i + 1] - b0;
-        if (m == 0) continue;
+    const long long tot = c->l_len[3];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
+        const long long tau = tb + (threadIdx.x & 31);
+        const long long i = locate_warp(cpre, np, tau, tau < tot);
+        if (tau >= tot) continue;
+        const int j = (int)(tau - cpre[i]);
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
         uint32_t v, u;
         c4_orient(V, p, &v, &u);
-        const Row rv = V.urow(v);
-        const int lu = (int)(V.U_off[u + 1] - V.U_off[u]);
-        for (int j = lane; j < rv.len; j += 32) {
-            const uint32_t e = rv.p[j];
-            const uint32_t w = vid(e);
-            int k = 0;
-            if (w != u && (e & p.x)) k = min(V.row(w).len, lu);
-            tpair[b0 + j] = (int32_t)i;
-            tent[b0 + j] = j;
-            tcost[b0 + j] = k;
-        }
+        const uint32_t e = V.urow(v).p[j];
+        const uint32_t w = vid(e);
+        int k = 0;
+        if (w != u && (e & p.x)) k = min(V.row(w).len, (int)(V.U_off[u + 1] - V.U_off[u]));
+        tpair[tau] = (int32_t)i;
+        tent[tau] = j;
+        tcost[tau] = k;
     }
 }
 
@@ -500,9 +556,11 @@ __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
     const long long n = c->l_len[3];
     const long long tot = n ? tpre[n] : 0;
     unsigned long long qa = 0, qb = 0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < tot;
-         s += (long long)gridDim.x * blockDim.x) {
-        const long long tau = locate(tpre, n, s);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long sb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); sb < tot; sb += stride) {
+        const long long s = sb + (threadIdx.x & 31);
+        const long long tau = locate_warp(tpre, n, s, s < tot);
+        if (s >= tot) continue;
         const int k = (int)(s - tpre[tau]);
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, tpair[tau]);
         uint32_t v, u;
@@ -536,6 +594,175 @@ __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
     }
     acc_warp(c, 5, qa);
     acc_warp(c, 11, qb);
+}
+
+// ---- with maintained triangle sums ---------------------------------------------------
+
+// T2 from a static count (U = G, both flags on every entry; tpack holds t of
+// every out-entry).  T2 must be zero.
+__global__ void k_t2_from_static(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                                 const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                                 const unsigned long long* __restrict__ tpack, unsigned long long* __restrict__ T2) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const int32_t u = wlist[i];
+        const long long ob = U_off[u] + U_split[u], oe = U_off[u + 1];
+        unsigned long long own = 0;
+        for (long long e = ob + lane; e < oe; e += 32) {
+            const unsigned long long t = tpack[e] >> 32;
+            if (t) {
+                own += t;
+                atomicAdd(&T2[vid(U_col[e])], t);
+            }
+        }
+        own = warp_sum_u64(own);
+        if (lane == 0 && own) atomicAdd(&T2[u], own);
+    }
+}
+
+// Triangles through changed pairs, each once at its smallest changed pair:
+// delta = [in G_a] - [in G_b] goes to the change of t of its three edges
+// (dcnt, at their entries), to twice the change of the triangles at its
+// three vertices (dtri2), and to the change of sum t.  Third vertices
+// outside V_X are listed after V_X in wlist.
+__global__ void k_loc_tri_delta(Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                                const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                                const int32_t* __restrict__ dstD, const long long* __restrict__ ppre,
+                                const unsigned long long* __restrict__ rec, long long* __restrict__ dcnt,
+                                long long* __restrict__ dtri2, uint32_t* __restrict__ visited2,
+                                int32_t* __restrict__ wlist) {
+    const long long np = c->l_len[1];
+    const long long tot = c->l_len[2];
+    const int nX = c->lvl[0];
+    long long s3 = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
+        const long long t = tb + (threadIdx.x & 31);
+        const long long i = locate_warp(ppre, np, t, t < tot);
+        if (t >= tot) continue;
+        const unsigned long long r = rec[t];
+        if (!(r & T_VALID)) continue;
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+        const uint32_t w = (uint32_t)(r & 0xFFFFFFFFull);
+        const uint32_t faw = t_flags(r, T_FU), fbw = t_flags(r, T_FV);
+        const unsigned long long kp = pkey(p.a, p.b);
+        if ((faw != AB && pkey(p.a, w) < kp) || (fbw != AB && pkey(p.b, w) < kp)) continue;
+        const uint32_t f = p.x & faw & fbw;
+        const long long d = ((f & FLAG_A) ? 1 : 0) - ((f & FLAG_B) ? 1 : 0);
+        if (!d) continue;
+        atomicAdd((unsigned long long*)&dcnt[canon_pos(V, p.a, p.b)], (unsigned long long)d);
+        atomicAdd((unsigned long long*)&dcnt[canon_pos(V, p.a, w)], (unsigned long long)d);
+        atomicAdd((unsigned long long*)&dcnt[canon_pos(V, p.b, w)], (unsigned long long)d);
+        atomicAdd((unsigned long long*)&dtri2[p.a], (unsigned long long)(2 * d));
+        atomicAdd((unsigned long long*)&dtri2[p.b], (unsigned long long)(2 * d));
+        atomicAdd((unsigned long long*)&dtri2[w], (unsigned long long)(2 * d));
+        if (!in_x(V.visited, w)) {
+            const uint32_t bit = 1u << (w & 31);
+            if (!(atomicOr(&visited2[w >> 5], bit) & bit)) wlist[nX + atomicAdd(&c->l_nw3, 1)] = (int32_t)w;
+        }
+        s3 += 3 * d;
+    }
+    acc_warp(c, 16, (unsigned long long)s3);   // change of sum t (G_a slot; the G_b slot stays 0)
+    acc_warp(c, 0, (unsigned long long)(-s3)); // P = sum (d_u - 1)(d_w - 1) - sum t
+}
+
+// Intersections only for the common edges at V_X whose t changes (their old t).
+__global__ void k_loc_dcost(const Ctl* c, LocalView V, const int32_t* __restrict__ own,
+                            const long long* __restrict__ dcnt, int32_t* __restrict__ cost) {
+    const long long tot = c->l_len[0];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)own[e];
+        const uint32_t fe = V.U_col[e];
+        const uint32_t w = vid(fe);
+        int k = 0;
+        if ((fe & AB) == AB && dcnt[e] != 0 && !(in_x(V.visited, w) && w < u))
+            k = min((int)(V.U_off[u + 1] - V.U_off[u]), V.row(w).len);
+        cost[e] = k;
+    }
+}
+
+// Per-edge terms at V_X (a thread per entry): degree products (P), edge
+// counts, and C(t, 2) (D) of the edges whose t changes.
+__global__ void k_loc_eterms(Ctl* c, LocalView V, const int32_t* __restrict__ own,
+                             const unsigned long long* __restrict__ tpack, const long long* __restrict__ dcnt,
+                             const int32_t* __restrict__ da, const int32_t* __restrict__ db) {
+    const long long tot = c->l_len[0];
+    unsigned long long P[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0};
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)own[e];
+        const uint32_t fe = V.U_col[e];
+        const uint32_t w = vid(fe);
+        const bool wx = in_x(V.visited, w);
+        if (wx && w < u) continue;
+        const uint32_t f = fe & AB;
+        const long long dd = dcnt[e];
+        if (f & FLAG_A) {
+            const long long dw = wx ? da[w] : V.deg[w];
+            P[0] += (unsigned long long)(((long long)da[u] - 1) * (dw - 1));
+            E[0] += 1;
+        }
+        if (f & FLAG_B) {
+            const long long dw = wx ? db[w] : V.deg[w];
+            P[1] += (unsigned long long)(((long long)db[u] - 1) * (dw - 1));
+            E[1] += 1;
+        }
+        if (f == AB) {
+            if (dd) {
+                const long long tb = (long long)(tpack[e] & 0xFFFFFFFFull);
+                D[0] += choose2((unsigned long long)(tb + dd));
+                D[1] += choose2((unsigned long long)tb);
+            }
+        } else if (f == FLAG_A) {
+            D[0] += choose2((unsigned long long)dd);    // dd = triangles through the inserted edge
+        } else {
+            D[1] += choose2((unsigned long long)(-dd));  // -dd = triangles through the deleted edge
+        }
+    }
+    for (int g = 0; g < 2; g++) {
+        acc_warp(c, 6 * g + 0, P[g]);
+        acc_warp(c, 6 * g + 3, D[g]);
+        acc_warp(c, 12 + g, E[g]);
+    }
+}
+
+// Per-vertex terms: S and sum C(d, 2) at V_X, 2 TT = sum T2(x) (d_x - 2) at
+// V_X and at the third vertices; then T2 follows the batch (commit) and
+// the changes are cleared.
+__global__ void k_loc_vterms(Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
+                             unsigned long long* __restrict__ T2, long long* __restrict__ dtri2,
+                             const int32_t* __restrict__ da, const int32_t* __restrict__ db, int commit) {
+    const int nX = c->l_len[0] ? c->lvl[0] : 0;
+    const int nT = nX ? nX + c->l_nw3 : 0;
+    const bool apply = commit && c->err == 0 && c->active && c->lovf == 0;
+    unsigned long long S[2] = {0, 0}, W2[2] = {0, 0}, T[2] = {0, 0};
+    const int nT_r = (nT + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nT_r; i += gridDim.x * blockDim.x) {
+        if (i >= nT) continue;
+        const uint32_t x = (uint32_t)wlist[i];
+        const bool inX = i < nX;
+        const long long dxa = inX ? da[x] : V.deg[x], dxb = inX ? db[x] : V.deg[x];
+        const long long t2b = (long long)T2[x], dt = dtri2[x], t2a = t2b + dt;
+        T[0] += (unsigned long long)(t2a * (dxa - 2));
+        T[1] += (unsigned long long)(t2b * (dxb - 2));
+        if (inX) {
+            S[0] += choose3((unsigned long long)dxa);
+            S[1] += choose3((unsigned long long)dxb);
+            W2[0] += choose2((unsigned long long)dxa);
+            W2[1] += choose2((unsigned long long)dxb);
+        }
+        if (apply) T2[x] = (unsigned long long)t2a;
+        dtri2[x] = 0;
+    }
+    for (int g = 0; g < 2; g++) {
+        acc_warp(c, 6 * g + 1, S[g]);
+        acc_warp(c, 6 * g + 2, T[g]);
+        acc_warp(c, 18 + g, W2[g]);
+    }
 }
 
 // ---- closed forms on the differences -------------------------------------------------
@@ -595,25 +822,41 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
     LocalView V{a.visited, a.U_off, a.U_col, a.row_start, a.deg, a.col};
     int nl = 0;
     k_loc_check_rows<<<1, 32, 0, s>>>(a.ctl, a.cap);
-    nl++;
     if (ev_tri) record_stage(ev_tri, s);
-    // triangles of the edges at V_X, then their terms
-    k_loc_tri_cost<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.cost, a.own);
-    nl++;
-    nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
-    k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
-    k_loc_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.tpack, a.da, a.db);
+    k_loc_owner<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.own);
     nl += 2;
-    if (ev_sub) record_stage(ev_sub, s);
-    // changed pairs: common neighbours (4-cliques) and 4-cycle tasks
+    // changed pairs: common neighbours (4-cliques, triangles) and 4-cycle tasks
     k_loc_pair_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt);
     nl++;
     nl += scan_i32_to_i64(a.pcost, a.ppre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[1], s);
     nl += scan_i32_to_i64(a.ccnt, a.cpre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[3], s);
     k_loc_check_pairs<<<1, 32, 0, s>>>(a.ctl, a.cap);
     k_loc_common<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec);
+    nl += 2;
+    if (a.T2) {
+        // maintained triangle sums: intersect only the edges whose t changes
+        k_zero_u64<<<gw, tpb, 0, s>>>((unsigned long long*)a.dcnt, &a.ctl->l_len[0]);
+        k_loc_tri_delta<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.dcnt,
+                                           a.dtri2, a.visited2, a.wlist_w);
+        k_loc_dcost<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.dcnt, a.cost);
+        nl += 3;
+        nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
+        k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
+        k_loc_eterms<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.tpack, a.dcnt, a.da, a.db);
+        k_loc_vterms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.T2, a.dtri2, a.da, a.db, commit);
+        nl += 3;
+    } else {
+        // triangles of every edge at V_X, then their terms
+        k_loc_tri_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.cost);
+        nl++;
+        nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
+        k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
+        k_loc_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.own, a.tpack, a.da, a.db);
+        nl += 2;
+    }
+    if (ev_sub) record_stage(ev_sub, s);
     k_loc_k4_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kcost);
-    nl += 3;
+    nl++;
     nl += scan_i32_to_i64(a.kcost, a.kpre, &a.ctl->l_len[2], 0, a.bsum, sg, &a.ctl->l_tot[2], s);
     k_loc_k4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kpre);
     // the triangle probe offsets are free again: the 4-cycle tasks reuse them

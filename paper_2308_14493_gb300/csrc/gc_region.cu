@@ -97,6 +97,10 @@ __global__ void k_u_count(const Ctl* c, const int32_t* __restrict__ wlist, const
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < nW; i += nwarps) {
         int32_t u = wlist[i];
+        if (all) {  // the full row and the insertions
+            if (lane == 0) U_deg[u] = deg[u] + (segA[u].y - segA[u].x);
+            continue;
+        }
         const int32_t* row = col + row_start[u];
         int d = deg[u], cnt = 0;
         for (int b = 0; b < d; b += 32) {
@@ -134,6 +138,31 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const 
         __syncwarp();
         if (lane == 0) {
             U_split[u] = (int32_t)lower_bound_id(out, len, (uint32_t)u);
+            da[u] = (int32_t)(len - nd);
+            db[u] = (int32_t)(len - na);
+        }
+    }
+}
+
+// Union rows over the full adjacency (the edge-local path): a block per
+// vertex, every entry placed by binary searches (hub rows spread over the
+// block).  D entries stay with FLAG_B only, A entries get FLAG_A only.
+__global__ void k_u_fill_all(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ row_start,
+                             const int32_t* __restrict__ deg, const int32_t* __restrict__ col,
+                             const int2* __restrict__ segA, const int2* __restrict__ segD,
+                             const int32_t* __restrict__ dstA, const int32_t* __restrict__ dstD,
+                             const long long* __restrict__ U_off, uint32_t* __restrict__ U_col,
+                             int32_t* __restrict__ U_split, int32_t* __restrict__ da, int32_t* __restrict__ db) {
+    const int nW = c->nW;
+    for (int i = blockIdx.x; i < nW; i += gridDim.x) {
+        const int32_t u = wlist[i];
+        const int2 a = segA[u], d = segD[u];
+        const long long na = a.y - a.x, nd = d.y - d.x;
+        const int32_t* row = col + row_start[u];
+        const long long len = block_merge_row(row, deg[u], dstA + a.x, na, dstD + d.x, nd, U_col + U_off[u], true,
+                                              FLAG_A | FLAG_B, FLAG_A, FLAG_B);
+        if (threadIdx.x == 0) {
+            U_split[u] = (int32_t)(lower_bound_i32(row, deg[u], u + 1) + lower_bound_i32(dstA + a.x, na, u + 1));
             da[u] = (int32_t)(len - nd);
             db[u] = (int32_t)(len - na);
         }

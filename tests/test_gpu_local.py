@@ -167,3 +167,85 @@ def test_local_scratch_grows_for_a_hub(gcb):
         dels = [(0, hub), (5, hub), (2, 3)]
         _step(g, og, np.array(ins, np.int32), np.array(dels, np.int32))
         assert g.stats()["region_entries"] > (1 << 20)
+
+
+def test_local_after_region_batches_and_recount(gcb):
+    """The maintained triangle sums are valid after open and after a static
+    recount, stale after a committed region batch (the local path then
+    intersects every edge at the endpoints); every mix stays exact."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=100) as g:
+        def step(size, path, seed):
+            ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), size - size // 3, size // 3, seed)
+            r = og.apply(ins, dels)
+            assert g.apply(ins, dels) == mod64(r["F"])
+            assert g.stats()["path"] == path
+        for i, (size, path) in enumerate([(40, 1), (90, 1), (500, 0), (30, 1), (60, 1)]):
+            step(size, path, 60 + i)
+        assert g.count_static() == mod64(og.F)
+        for i in range(4):
+            step(20 + 20 * i, 1, 80 + i)
+            # what-if batches leave the sums as they are
+            ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), 7, 7, 90 + i)
+            r = oracle.fdgc_step(og.row_ptr, og.col, ins, dels, og.F, 3)
+            assert g.count_batch(ins, dels) == mod64(r["F"])
+        assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+
+
+def test_local_after_adding_vertices(gcb):
+    n, keys = gen.workload_graph("c1")
+    rp, col = gen.csr_from_keys(n, keys)
+    with gcb.Graph(n, rp, col, local_max_pairs=1 << 30) as g:
+        first = g.add_vertices(5)
+        assert first == n
+        rp2 = np.concatenate([rp, np.full(5, rp[-1], rp.dtype)])
+        og = oracle.OracleGraph(rp2, col)
+        ins = np.array([(n, 0), (n, 1), (n + 1, 0), (n + 1, n), (n + 2, 3), (0, 1)], np.int32)
+        _step(g, og, ins, NONE)
+        _step(g, og, np.array([(n + 3, n + 4), (n + 4, 0), (n + 3, 0)], np.int32), np.array([(n, 1)], np.int32))
+
+
+@pytest.mark.parametrize("independent", [False, True], ids=["sequential", "independent"])
+def test_batched_run_routes_small_batches_to_the_local_path(gcb, independent):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    sizes = [5, 2000, 40, 60, 3000, 1, 800, 10]
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 55, sequential=not independent)
+    og = oracle.OracleGraph(rp, col)
+    F0 = og.F
+    expect = []
+    for ins, dels in batches:
+        if independent:
+            expect.append(mod64(oracle.fdgc_step(rp, col, ins, dels, F0, 3)["F"]))
+        else:
+            expect.append(mod64(og.apply(ins, dels)["F"]))
+    with gcb.Graph(n, rp, col, local_max_pairs=100) as g:
+        got = g.apply_many(batches, independent=independent)
+        assert [list(map(int, o)) for o in got] == expect
+        if independent:
+            assert g.counts() == mod64(F0)
+        else:
+            assert g.counts() == expect[-1]
+            assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+
+
+def test_autotune_sets_a_local_threshold_and_keeps_counts(gcb):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col) as g:
+        tuning, _ = g.autotune(reps=1)
+        thr = tuning["local_max_pairs"]
+        assert thr >= 0 and g.tuning()["local_max_pairs"] == thr
+        for i, size in enumerate([4, 30, 300, 3000]):
+            ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), size // 2, size - size // 2, 500 + i)
+            r = og.apply(ins, dels)
+            assert g.apply(ins, dels) == mod64(r["F"])
+            assert g.stats()["path"] == (1 if size <= thr else 0)
+        g.set_tuning(local_max_pairs=0)
+        ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), 2, 2, 600)
+        r = og.apply(ins, dels)
+        assert g.apply(ins, dels) == mod64(r["F"])
+        assert g.stats()["path"] == 0

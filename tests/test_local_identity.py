@@ -116,3 +116,84 @@ def test_local_rule_on_dense_cliques():
         assert delta == [a - b for a, b in zip(_sums(n, sorted(after)), _sums(n, base))]
         delta, after = local_delta_sums(n, full, [], sorted(drop))
         assert delta == [a - b for a, b in zip(_sums(n, sorted(after)), _sums(n, full))]
+
+
+def local_delta_sums_t2(n, edges_b, ins, dels):
+    """The same delta with maintained triangle sums T2(x) = sum of t_e at x:
+    only the triangles through changed pairs are listed (once, at their
+    smallest changed pair), TT in vertex form, D on the edges whose t
+    changes; P from degree products at V_X and the change of sum t."""
+    Gb = _adj(n, edges_b)
+    eb = {(min(u, v), max(u, v)) for u, v in edges_b}
+    A = {(min(u, v), max(u, v)) for u, v in ins} - eb
+    D = {(min(u, v), max(u, v)) for u, v in dels} & eb
+    both = A & D
+    A, D = A - both, D - both
+    ea = (eb - D) | A
+    Ga = _adj(n, ea)
+    X = A | D
+    VX = {x for p in X for x in p}
+    T2b = [sum(len(Gb[x] & Gb[w]) for w in Gb[x]) for x in range(n)]
+    U = [Ga[x] | Gb[x] for x in range(n)]
+    dt = {}      # change of t per edge
+    dtri2 = {}   # change of T2 per vertex
+    for p in sorted(X):
+        a, b = p
+        for w in sorted(U[a] & U[b]):
+            es = [(min(a, w), max(a, w)), (min(b, w), max(b, w))]
+            if any(e in X and e < p for e in es):
+                continue
+            tri = [p] + es
+            d = int(all(e in ea for e in tri)) - int(all(e in eb for e in tri))
+            for e in tri:
+                dt[e] = dt.get(e, 0) + d
+            for x in (a, b, w):
+                dtri2[x] = dtri2.get(x, 0) + 2 * d
+    s3 = sum(dt.values())
+    delta = [0] * 6
+    da = [len(Ga[v]) for v in range(n)]
+    db = [len(Gb[v]) for v in range(n)]
+    at_vx = {e for e in ea | eb if e[0] in VX or e[1] in VX}
+    for e in at_vx:
+        u, w = e
+        if e in ea:
+            delta[0] += (da[u] - 1) * (da[w] - 1)
+        if e in eb:
+            delta[0] -= (db[u] - 1) * (db[w] - 1)
+        d = dt.get(e, 0)
+        if e in ea and e in eb:
+            tb = len(Gb[u] & Gb[w])
+            delta[3] += _c2(tb + d) - _c2(tb)
+        elif e in ea:
+            delta[3] += _c2(d)
+        else:
+            delta[3] -= _c2(-d)
+    delta[0] -= s3
+    tt2 = 0
+    for x in VX | set(dtri2):
+        tt2 += (T2b[x] + dtri2.get(x, 0)) * (da[x] - 2) - T2b[x] * (db[x] - 2)
+        if x in VX:
+            delta[1] += _c3(da[x]) - _c3(db[x])
+    delta[2] = tt2 // 2
+    full, _ = local_delta_sums(n, edges_b, ins, dels)   # K and Q as in the first form
+    delta[4], delta[5] = full[4], full[5]
+    T2a = [sum(len(Ga[x] & Ga[w]) for w in Ga[x]) for x in range(n)]
+    assert all(T2a[x] == T2b[x] + dtri2.get(x, 0) for x in range(n))
+    return delta, ea
+
+
+def test_triangle_sum_form_equals_full_recount():
+    rng = np.random.default_rng(77)
+    for trial in range(60):
+        n = int(rng.integers(5, 26))
+        p = float(rng.uniform(0.1, 0.8))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        all_pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+        k = int(rng.integers(1, 10))
+        pick = rng.choice(len(all_pairs), size=min(2 * k, len(all_pairs)), replace=False)
+        ins = [all_pairs[i] for i in pick[:k]]
+        dels = [all_pairs[i] for i in pick[k:]]
+        if trial % 3 == 0 and edges:
+            dels = [edges[i] for i in rng.choice(len(edges), size=min(k, len(edges)), replace=False)]
+        delta, after = local_delta_sums_t2(n, edges, ins, dels)
+        assert delta == [a - b for a, b in zip(_sums(n, sorted(after)), _sums(n, edges))], trial
