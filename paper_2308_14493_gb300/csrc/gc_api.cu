@@ -115,6 +115,8 @@ struct gc_graph {
     Buf<long long> l_dcnt;
     long long l_cap = 0;
     int l_t2 = -1;                       // captured with maintained triangle sums
+    int p_t2 = -1;                       // the same for the plain region form
+    int g_t2 = -1;                       // and for the batched region form
     // maintained triangle sums of the edge-local path: T2[x] = sum of t_e
     // over the edges at x, valid after a static count and kept by local
     // batches (a region batch makes it stale)
@@ -684,6 +686,13 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     if (timed) CK(record_stage(g->ev[2], s));
     int rc = local ? count_local(g, commit ? 1 : 0, timed, t2) : count_region(g, commit ? 0 : 2, false, timed);
     if (rc) return rc;
+    if (!local && commit && t2) {
+        // keep the triangle sums of the edge-local path
+        k_t2_from_region<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split,
+                                                       g->tpack.p, g->T2);
+        g->launches++;
+        CKL();
+    }
     if (commit) {
         rc = enqueue_commit(g);
         if (rc) return rc;
@@ -881,15 +890,17 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         int* ex_commit = local ? &g->l_commit : &g->p_commit;
         unsigned long long* ex_gen = local ? &g->l_gen : &g->p_gen;
         int* ex_launches = local ? &g->l_launches : &g->p_launches;
-        const bool t2 = local && g->t2_valid;
-        if (!*ex || *ex_nk != shape_nk || *ex_commit != commit || *ex_gen != g->buf_gen ||
-            (local && g->l_t2 != (int)t2)) {
+        // maintained triangle sums: used by the local form, kept by the
+        // region form while the local form is enabled
+        const bool t2 = g->t2_valid && (local || g->opt.local_max_pairs > 0);
+        int* ex_t2 = local ? &g->l_t2 : &g->p_t2;
+        if (!*ex || *ex_nk != shape_nk || *ex_commit != commit || *ex_gen != g->buf_gen || *ex_t2 != (int)t2) {
             rc = capture_batch(g, shape_nk, commit != 0, true, ex, ex_launches, local, t2);
             if (rc) return rc;
             *ex_nk = shape_nk;
             *ex_commit = commit;
             *ex_gen = g->buf_gen;
-            if (local) g->l_t2 = (int)t2;
+            *ex_t2 = (int)t2;
         }
         g->h_desc[0] = (long long)d_ins;
         g->h_desc[1] = (long long)d_del;
@@ -945,7 +956,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         stage_times(g, 0, 7);
     }
     g->st.path = local ? 1 : 0;
-    if (commit && !local) g->t2_valid = false;  // the region pass does not keep the triangle sums
+    if (commit && !local && g->opt.local_max_pairs <= 0) g->t2_valid = false;  // not kept without the local form
     if (commit) {
         for (int i = 0; i < 6; i++) g->F[i] = c.F[i];
         for (int i = 0; i < 2; i++) g->F3[i] = c.F3[i];
@@ -966,7 +977,9 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = g->s;
     const bool commit = !independent;
-    if (commit) g->t2_valid = false;  // region passes do not keep the triangle sums
+    // the triangle sums of the edge-local form are kept while it is enabled
+    const bool t2 = g->t2_valid && g->opt.local_max_pairs > 0;
+    if (commit && !t2) g->t2_valid = false;
     long long max_nk = 0, max_ins = 0, sum_ins = 0, raw_ins = 0, raw_del = 0;
     for (int i = 0; i < k; i++) {
         long long ni = h_batches[4 * i + 1], nd = h_batches[4 * i + 3];
@@ -1007,12 +1020,14 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     k_run_reset<<<1, 32, 0, s>>>(g->ctl);
     CKL();
     // (re)capture the per-batch graph when its shape or any buffer changed
-    if (!g->gexec || g->g_nk != shape_nk || g->g_commit != (int)commit || g->g_gen != g->buf_gen) {
-        rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches);
+    if (!g->gexec || g->g_nk != shape_nk || g->g_commit != (int)commit || g->g_gen != g->buf_gen ||
+        g->g_t2 != (int)t2) {
+        rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches, false, t2);
         if (rc) return rc;
         g->g_nk = shape_nk;
         g->g_commit = (int)commit;
         g->g_gen = g->buf_gen;
+        g->g_t2 = (int)t2;
     }
     CK(cudaEventRecord(g->e0, s));
     int done = 0;
@@ -1027,7 +1042,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
             if (rc) return rc;
             if (g->g_gen != g->buf_gen) {
                 // the adjacency moved: capture again for the remaining batches
-                rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches);
+                rc = capture_batch(g, shape_nk, commit, false, &g->gexec, &g->g_launches, false, t2);
                 if (rc) return rc;
                 g->g_gen = g->buf_gen;
             }

@@ -623,6 +623,46 @@ __global__ void k_t2_from_static(const Ctl* c, const int32_t* __restrict__ wlist
     }
 }
 
+// After a committed region batch: T2 of the vertices within one hop of the
+// batch endpoints (the only vertices whose triangles can change), from the
+// region pass's triangle counts in G_a.  Those counts are exact there: with
+// k >= 2 hops, a vertex within one hop has its whole neighbourhood inside
+// W.  A block per vertex; an in-entry (y < x) reads t from y's out-entry.
+__global__ void k_t2_from_region(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                                 const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                                 const unsigned long long* __restrict__ tpack, unsigned long long* __restrict__ T2) {
+    if (c->err || !c->active) return;
+    const int n1 = c->lvl[1];
+    __shared__ unsigned long long s_part[32];
+    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
+        const uint32_t x = (uint32_t)wlist[i];
+        const long long rb = U_off[x], re = U_off[x + 1];
+        const long long split = rb + U_split[x];
+        unsigned long long sum = 0;
+        for (long long e = rb + threadIdx.x; e < re; e += blockDim.x) {
+            const uint32_t f = U_col[e];
+            if (!(f & FLAG_A)) continue;
+            if (e >= split) {
+                sum += tpack[e] >> 32;
+            } else {
+                const uint32_t y = vid(f);
+                const long long yb = U_off[y] + U_split[y];
+                const long long q = yb + lower_bound_id(U_col + yb, U_off[y + 1] - yb, x);
+                sum += tpack[q] >> 32;
+            }
+        }
+        sum = warp_sum_u64(sum);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_part[w];
+            T2[x] = t;
+        }
+        __syncthreads();
+    }
+}
+
 // Triangles through changed pairs, each once at its smallest changed pair:
 // delta = [in G_a] - [in G_b] goes to the change of t of its three edges
 // (dcnt, at their entries), to twice the change of the triangles at its

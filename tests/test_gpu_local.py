@@ -249,3 +249,42 @@ def test_autotune_sets_a_local_threshold_and_keeps_counts(gcb):
         r = og.apply(ins, dels)
         assert g.apply(ins, dels) == mod64(r["F"])
         assert g.stats()["path"] == 0
+
+
+def test_triangle_sums_through_region_runs_and_toggles(gcb):
+    """Region batches keep the sums while the local form is enabled (plain
+    and batched runs); with it disabled they go stale, and a later local
+    batch still counts right (it intersects every edge at its endpoints)."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=50) as g:
+        def mk(size, seed):
+            return gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), size - size // 2, size // 2, seed)
+
+        def step(size, seed, path):
+            ins, dels = mk(size, seed)
+            r = og.apply(ins, dels)
+            assert g.apply(ins, dels) == mod64(r["F"])
+            assert g.stats()["path"] == path
+
+        step(400, 1, 0)
+        step(30, 2, 1)
+        # a batched run: region sub-runs between local batches
+        run = [mk(300, 3)]
+        r1 = og.apply(*run[0])
+        run.append(mk(20, 4))
+        r2 = og.apply(*run[1])
+        run.append(mk(700, 5))
+        r3 = og.apply(*run[2])
+        got = g.apply_many(run)
+        assert [list(map(int, o)) for o in got] == [mod64(r1["F"]), mod64(r2["F"]), mod64(r3["F"])]
+        step(40, 6, 1)
+        g.set_tuning(local_max_pairs=0)
+        step(20, 7, 0)
+        step(600, 8, 0)
+        g.set_tuning(local_max_pairs=50)
+        step(25, 9, 1)
+        assert g.count_static() == mod64(og.F)
+        step(35, 10, 1)
+        assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
