@@ -688,9 +688,11 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     if (rc) return rc;
     if (!local && commit && t2) {
         // keep the triangle sums of the edge-local path
+        CK(cudaMemsetAsync(g->visited2, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
+        k_t2_mark<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->visited2, g->T2);
         k_t2_from_region<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split,
-                                                       g->tpack.p, g->T2);
-        g->launches++;
+                                                       g->tpack.p, g->visited2, g->T2);
+        g->launches += 2;
         CKL();
     }
     if (commit) {

@@ -157,8 +157,11 @@ __global__ void k_commit_plan(Ctl* c, const int32_t* __restrict__ wlist, const i
     }
 }
 
-// A block per touched vertex: row \ D_u u A_u into the scratch (every
-// entry placed by binary searches, so hub rows spread over the block).
+// row \ D_u u A_u of every touched vertex into the scratch: a warp per
+// short row, a block per long one (every entry placed by binary searches,
+// so a hub row spreads over the block).
+constexpr long long LONG_ROW = 4096;
+
 __global__ void k_commit_merge(const Ctl* c, const int32_t* __restrict__ wlist, const int2* __restrict__ segA,
                                const int2* __restrict__ segD, const int32_t* __restrict__ dstA,
                                const int32_t* __restrict__ dstD, const int32_t* __restrict__ deg,
@@ -166,9 +169,22 @@ __global__ void k_commit_merge(const Ctl* c, const int32_t* __restrict__ wlist, 
                                const long long* __restrict__ plan_scr, uint32_t* __restrict__ scratch) {
     if (c->err || c->overflow || c->lovf) return;
     const int ns = c->lvl[0];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < ns; i += nwarps) {
+        const int32_t u = wlist[i];
+        const int2 a = segA[u], d = segD[u];
+        if ((long long)deg[u] + (a.y - a.x) > LONG_ROW) continue;
+        const int32_t* dl = dstD + d.x;
+        const long long nd = d.y - d.x;
+        warp_merge_row(col + row_start[u], deg[u], dstA + a.x, a.y - a.x, scratch + plan_scr[i], 0u,
+                       [&](int32_t v) { return nd == 0 || !sorted_contains(dl, nd, v); },
+                       [](int32_t) { return 0u; });
+    }
     for (int i = blockIdx.x; i < ns; i += gridDim.x) {
         const int32_t u = wlist[i];
         const int2 a = segA[u], d = segD[u];
+        if ((long long)deg[u] + (a.y - a.x) <= LONG_ROW) continue;
         block_merge_row(col + row_start[u], deg[u], dstA + a.x, a.y - a.x, dstD + d.x, d.y - d.x,
                         scratch + plan_scr[i], false, 0u, 0u, 0u);
     }
@@ -181,10 +197,26 @@ __global__ void k_commit_write(const Ctl* c, const int32_t* __restrict__ wlist, 
                                long long* __restrict__ row_start, int32_t* __restrict__ col) {
     if (c->err || c->overflow || c->lovf) return;
     const int ns = c->lvl[0];
-    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < ns; i += nwarps) {
+        const int nd = plan_deg[i];
+        if (nd > LONG_ROW) continue;
         const int32_t u = wlist[i];
         const long long dst = plan_dst[i], scr = plan_scr[i];
+        for (int j = lane; j < nd; j += 32) col[dst + j] = (int32_t)scratch[scr + j];
+        if (lane == 0) {
+            deg[u] = nd;
+            cap[u] = plan_cap[i];
+            row_start[u] = dst;
+        }
+    }
+    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
         const int nd = plan_deg[i];
+        if (nd <= LONG_ROW) continue;
+        const int32_t u = wlist[i];
+        const long long dst = plan_dst[i], scr = plan_scr[i];
         for (int j = threadIdx.x; j < nd; j += blockDim.x) col[dst + j] = (int32_t)scratch[scr + j];
         if (threadIdx.x == 0) {
             deg[u] = nd;

@@ -136,9 +136,11 @@ struct LocalArgs {
 // T2 (zeroed) from a static count: sum of t_e over the edges at each vertex.
 __global__ void k_t2_from_static(const Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
                                  const int32_t* U_split, const unsigned long long* tpack, unsigned long long* T2);
-// T2 of the vertices within one hop of a committed region batch.
+// T2 of the vertices within one hop of a committed region batch (mark, then add).
+__global__ void k_t2_mark(const Ctl* c, const int32_t* wlist, uint32_t* mark, unsigned long long* T2);
 __global__ void k_t2_from_region(const Ctl* c, const int32_t* wlist, const long long* U_off, const uint32_t* U_col,
-                                 const int32_t* U_split, const unsigned long long* tpack, unsigned long long* T2);
+                                 const int32_t* U_split, const unsigned long long* tpack, const uint32_t* mark,
+                                 unsigned long long* T2);
 // Enqueue the edge-local delta (after the union rows of V_X); events mark
 // the triangle stage, the 4-clique / 4-cycle stage and the closed forms.
 int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,

@@ -627,39 +627,44 @@ __global__ void k_t2_from_static(const Ctl* c, const int32_t* __restrict__ wlist
 // batch endpoints (the only vertices whose triangles can change), from the
 // region pass's triangle counts in G_a.  Those counts are exact there: with
 // k >= 2 hops, a vertex within one hop has its whole neighbourhood inside
-// W.  A block per vertex; an in-entry (y < x) reads t from y's out-entry.
-__global__ void k_t2_from_region(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
-                                 const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
-                                 const unsigned long long* __restrict__ tpack, unsigned long long* __restrict__ T2) {
+// W.  First the one-hop vertices are marked and their T2 cleared ...
+__global__ void k_t2_mark(const Ctl* c, const int32_t* __restrict__ wlist, uint32_t* __restrict__ mark,
+                          unsigned long long* __restrict__ T2) {
     if (c->err || !c->active) return;
     const int n1 = c->lvl[1];
-    __shared__ unsigned long long s_part[32];
-    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)wlist[i];
-        const long long rb = U_off[x], re = U_off[x + 1];
-        const long long split = rb + U_split[x];
-        unsigned long long sum = 0;
-        for (long long e = rb + threadIdx.x; e < re; e += blockDim.x) {
+        atomicOr(&mark[x >> 5], 1u << (x & 31));
+        T2[x] = 0;
+    }
+}
+
+// ... then every out-entry u -> v of U adds its t to T2 of the marked ends
+// (a warp per vertex of W: out-lists are short, hubs having the highest ids).
+__global__ void k_t2_from_region(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                                 const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                                 const unsigned long long* __restrict__ tpack, const uint32_t* __restrict__ mark,
+                                 unsigned long long* __restrict__ T2) {
+    if (c->err || !c->active) return;
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        const bool mu = in_x(mark, u);
+        unsigned long long own = 0;
+        for (long long e = U_off[u] + U_split[u] + lane; e < U_off[u + 1]; e += 32) {
             const uint32_t f = U_col[e];
             if (!(f & FLAG_A)) continue;
-            if (e >= split) {
-                sum += tpack[e] >> 32;
-            } else {
-                const uint32_t y = vid(f);
-                const long long yb = U_off[y] + U_split[y];
-                const long long q = yb + lower_bound_id(U_col + yb, U_off[y + 1] - yb, x);
-                sum += tpack[q] >> 32;
-            }
+            const unsigned long long t = tpack[e] >> 32;
+            if (!t) continue;
+            own += t;
+            const uint32_t v = vid(f);
+            if (in_x(mark, v)) atomicAdd(&T2[v], t);
         }
-        sum = warp_sum_u64(sum);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_part[w];
-            T2[x] = t;
-        }
-        __syncthreads();
+        own = warp_sum_u64(own);
+        if (lane == 0 && mu && own) atomicAdd(&T2[u], own);
     }
 }
 
