@@ -109,7 +109,7 @@ struct gc_graph {
     unsigned long long l_gen = 0;
     int l_launches = 0;
     // scratch of the edge-local path (entries each; offsets one more)
-    Buf<int32_t> l_cost, l_own, l_pcost, l_ccnt, l_kcost, l_tpair;
+    Buf<int32_t> l_cost, l_own, l_pcost, l_ccnt, l_kcost, l_tpair, l_walk;
     Buf<long long> l_pre, l_ppre, l_cpre, l_kpre;
     Buf<unsigned long long> l_rec;
     Buf<long long> l_dcnt;
@@ -409,6 +409,7 @@ static void release_local(gc_graph* g) {
     release(g, g->l_ccnt);
     release(g, g->l_kcost);
     release(g, g->l_tpair);
+    release(g, g->l_walk);
     release(g, g->l_pre);
     release(g, g->l_ppre);
     release(g, g->l_cpre);
@@ -424,12 +425,13 @@ static int ensure_local(gc_graph* g, long long cap) {
     const size_t c = (size_t)cap;
     if (!ensure(g, g->l_cost, c) || !ensure(g, g->l_own, c) || !ensure(g, g->l_pcost, c) ||
         !ensure(g, g->l_ccnt, c) || !ensure(g, g->l_kcost, c) || !ensure(g, g->l_tpair, c) ||
+        !ensure(g, g->l_walk, c) ||
         !ensure(g, g->l_pre, c + 1) || !ensure(g, g->l_ppre, c + 1) || !ensure(g, g->l_cpre, c + 1) ||
         !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c) || !ensure(g, g->l_dcnt, c))
         return nomem(g, "edge-local scratch");
     // ensure() may round up; the usable capacity is the smallest array's
     size_t m = std::min({g->l_cost.cap, g->l_own.cap, g->l_pcost.cap, g->l_ccnt.cap, g->l_kcost.cap,
-                         g->l_tpair.cap, g->l_rec.cap, g->l_dcnt.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
+                         g->l_tpair.cap, g->l_walk.cap, g->l_rec.cap, g->l_dcnt.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
                          g->l_kpre.cap - 1});
     g->l_cap = (long long)m;
     g->buf_gen++;  // captured graphs hold the old pointers
@@ -588,6 +590,7 @@ static int count_local(gc_graph* g, int commit, bool timed, bool t2) {
     la.ccnt = g->l_ccnt.p;
     la.kcost = g->l_kcost.p;
     la.tpair = g->l_tpair.p;
+    la.walk = g->l_walk.p;
     la.pre = g->l_pre.p;
     la.ppre = g->l_ppre.p;
     la.cpre = g->l_cpre.p;

@@ -119,7 +119,7 @@ struct LocalArgs {
     const int32_t* db;
     unsigned long long* tpack;     // per-entry triangle counters, zeroed
     const int32_t *srcA, *dstA, *srcD, *dstD;  // kept directed entries of the batch
-    int32_t *cost, *own, *pcost, *ccnt, *kcost, *tpair;
+    int32_t *cost, *own, *pcost, *ccnt, *kcost, *tpair, *walk;
     long long *pre, *ppre, *cpre, *kpre;
     unsigned long long* rec;
     long long* dcnt;               // per-entry change of t (cap entries)

@@ -154,14 +154,13 @@ __device__ __forceinline__ Pair pair_at(const Ctl* c, const int32_t* __restrict_
     return Pair{(uint32_t)srcD[j], (uint32_t)dstD[j], FLAG_B};
 }
 
-// For the 4-cycles through a pair, the neighbours of the endpoint with the
-// longer union row are walked and the other row is probed.
-__device__ __forceinline__ void c4_orient(const LocalView& V, const Pair& p, uint32_t* v, uint32_t* u) {
-    const int la = (int)(V.U_off[p.a + 1] - V.U_off[p.a]);
-    const int lb = (int)(V.U_off[p.b + 1] - V.U_off[p.b]);
-    const bool a_long = la > lb || (la == lb && p.a > p.b);
-    *v = a_long ? p.a : p.b;
-    *u = a_long ? p.b : p.a;
+// For the 4-cycles through a pair, the neighbours w of one endpoint v are
+// walked and each N(w) is intersected with the other endpoint's row; the
+// endpoint with the cheaper walk was chosen by k_loc_pair_cost (walk[i] = 1:
+// v = a).
+__device__ __forceinline__ void c4_orient(const Pair& p, int walk_a, uint32_t* v, uint32_t* u) {
+    *v = walk_a ? p.a : p.b;
+    *u = walk_a ? p.b : p.a;
 }
 
 __device__ __forceinline__ void acc_warp(Ctl* c, int slot, unsigned long long x) {
@@ -359,20 +358,32 @@ __global__ void k_loc_terms(Ctl* c, const int32_t* __restrict__ wlist, LocalView
 __global__ void k_loc_pair_cost(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
                                 const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                                 const int32_t* __restrict__ dstD, int32_t* __restrict__ pcost,
-                                int32_t* __restrict__ ccnt) {
+                                int32_t* __restrict__ ccnt, int32_t* __restrict__ walk) {
+    // a warp per pair slot: the 4-cycle probes of walking either endpoint,
+    // sum over its neighbours w of min(|N(w)|, |other row|)
     const long long np = c->l_len[1];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
-         i += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < np; i += nwarps) {
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
-        int k = 0, m = 0;
+        int k = 0, m = 0, wa = 0;
         if (p.a < p.b) {
-            const int la = (int)(V.U_off[p.a + 1] - V.U_off[p.a]);
-            const int lb = (int)(V.U_off[p.b + 1] - V.U_off[p.b]);
-            k = min(la, lb);
-            m = max(la, lb);
+            const Row ra = V.urow(p.a), rb = V.urow(p.b);
+            unsigned long long ca = 0, cb = 0;
+            for (int j = lane; j < ra.len; j += 32) ca += (unsigned long long)min(V.row(vid(ra.p[j])).len, rb.len);
+            for (int j = lane; j < rb.len; j += 32) cb += (unsigned long long)min(V.row(vid(rb.p[j])).len, ra.len);
+            ca = warp_sum_u64(ca);
+            cb = warp_sum_u64(cb);
+            wa = ca < cb || (ca == cb && ra.len >= rb.len);
+            k = min(ra.len, rb.len);
+            m = wa ? ra.len : rb.len;
         }
-        pcost[i] = k;
-        ccnt[i] = m;
+        if (lane == 0) {
+            pcost[i] = k;
+            ccnt[i] = m;
+            walk[i] = wa;
+        }
     }
 }
 
@@ -526,8 +537,8 @@ __global__ void k_loc_k4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
 __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
                                const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                                const int32_t* __restrict__ dstD, const long long* __restrict__ cpre,
-                               int32_t* __restrict__ tpair, int32_t* __restrict__ tent,
-                               int32_t* __restrict__ tcost) {
+                               const int32_t* __restrict__ walk, int32_t* __restrict__ tpair,
+                               int32_t* __restrict__ tent, int32_t* __restrict__ tcost) {
     const long long np = c->l_len[1];
     const long long tot = c->l_len[3];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -538,7 +549,7 @@ __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restr
         const int j = (int)(tau - cpre[i]);
         const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
         uint32_t v, u;
-        c4_orient(V, p, &v, &u);
+        c4_orient(p, walk[i], &v, &u);
         const uint32_t e = V.urow(v).p[j];
         const uint32_t w = vid(e);
         int k = 0;
@@ -551,8 +562,8 @@ __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restr
 
 __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, const int32_t* __restrict__ dstA,
                          const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
-                         const int32_t* __restrict__ tpair, const int32_t* __restrict__ tent,
-                         const long long* __restrict__ tpre) {
+                         const int32_t* __restrict__ walk, const int32_t* __restrict__ tpair,
+                         const int32_t* __restrict__ tent, const long long* __restrict__ tpre) {
     const long long n = c->l_len[3];
     const long long tot = n ? tpre[n] : 0;
     unsigned long long qa = 0, qb = 0;
@@ -562,9 +573,10 @@ __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
         const long long tau = locate_warp(tpre, n, s, s < tot);
         if (s >= tot) continue;
         const int k = (int)(s - tpre[tau]);
-        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, tpair[tau]);
+        const int pi = tpair[tau];
+        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, pi);
         uint32_t v, u;
-        c4_orient(V, p, &v, &u);
+        c4_orient(p, walk[pi], &v, &u);
         const Row rv = V.urow(v), ru = V.urow(u);
         const uint32_t ev = rv.p[tent[tau]];
         const uint32_t w = vid(ev), fvw = ev & AB;
@@ -871,7 +883,7 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
     k_loc_owner<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.own);
     nl += 2;
     // changed pairs: common neighbours (4-cliques, triangles) and 4-cycle tasks
-    k_loc_pair_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt);
+    k_loc_pair_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt, a.walk);
     nl++;
     nl += scan_i32_to_i64(a.pcost, a.ppre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[1], s);
     nl += scan_i32_to_i64(a.ccnt, a.cpre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[3], s);
@@ -905,10 +917,11 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
     nl += scan_i32_to_i64(a.kcost, a.kpre, &a.ctl->l_len[2], 0, a.bsum, sg, &a.ctl->l_tot[2], s);
     k_loc_k4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kpre);
     // the triangle probe offsets are free again: the 4-cycle tasks reuse them
-    k_loc_c4_tasks<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.cpre, a.tpair, a.own, a.cost);
+    k_loc_c4_tasks<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.cpre, a.walk, a.tpair, a.own,
+                                      a.cost);
     nl += 2;
     nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
-    k_loc_c4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.tpair, a.own, a.pre);
+    k_loc_c4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.walk, a.tpair, a.own, a.pre);
     nl++;
     if (ev_fin) record_stage(ev_fin, s);
     k_finalize_local<<<1, 32, 0, s>>>(a.ctl, commit);
