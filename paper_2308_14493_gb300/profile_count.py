@@ -1,11 +1,12 @@
 """Static count of a seeded Chung-Lu graph, repeated, for kernel profiling.
 
     python -m paper_2308_14493_gb300.profile_count --n 800000 --m 15000000 \\
-        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000]
+        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local]
 
 Opens the graph (one static count), then runs ``reps`` more static counts
 (or, with ``--batch``, ``reps`` sequential batches of that many updates, 60%
-insertions) and prints the per-stage device times of each call.  Used as the
+insertions; with ``--local`` through the edge-local delta) and prints the
+per-stage device times of each call.  Used as the
 command under ncu; it runs the library exactly as a user would.
 """
 from __future__ import annotations
@@ -34,12 +35,14 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--autotune", action="store_true", help="pick the bin boundaries first")
+    ap.add_argument("--local", action="store_true", help="batches take the edge-local delta")
     ap.add_argument("--chunk-threshold", type=int, default=0,
                     help="wedge bound above which 4-cycle pivots use the chunked shared-memory kernel")
     a = ap.parse_args()
     keys = gen.chung_lu_graph(a.n, a.m, a.gamma, a.dmax, a.seed)
     rp, col = gen.csr_from_keys(a.n, keys)
-    with gcb.Graph(a.n, rp, col, chunk_threshold=a.chunk_threshold) as g:
+    with gcb.Graph(a.n, rp, col, chunk_threshold=a.chunk_threshold,
+                   local_max_pairs=(1 << 30) if a.local else 0) as g:
         print(json.dumps({"open": g.stats()["ms_stage"]}), flush=True)
         if a.autotune:
             best, ms = g.autotune(reps=2)
@@ -48,8 +51,9 @@ def main():
             for ins, dels in gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1):
                 g.apply(ins, dels)
                 st = g.stats()
-                print(json.dumps({"batch_ms": st["ms_device"], "stage_ms": st["ms_stage"],
-                                  "region_vertices": st["region_vertices"]}), flush=True)
+                print(json.dumps({"batch_ms": st["ms_device"], "stage_ms": st["ms_stage"], "path": st["path"],
+                                  "region_vertices": st["region_vertices"], "probes": st["work_triangles"]}),
+                      flush=True)
         else:
             for _ in range(a.reps):
                 g.count_static()
