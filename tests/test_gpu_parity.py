@@ -570,18 +570,37 @@ def test_fullsize_c3_static_and_first_batch(gcb):
 
 
 @pytest.mark.slow
-def test_fullsize_c4_independent_batches(gcb):
+@pytest.mark.parametrize("local", [0, 512], ids=["region", "local_up_to_512"])
+def test_fullsize_c4_independent_batches(gcb, local):
     """Chung-Lu n=2.4M m=5M with 40k-degree hubs: independent batches on one
-    snapshot against stored oracle results."""
+    snapshot against stored oracle results (with the small ones also through
+    the edge-local delta)."""
     gold = _large_gold()["c4"]
     n, keys = gen.workload_graph("c4")
     rp, col = gen.csr_from_keys(n, keys)
     batches = gen.batch_stream(n, keys, gold["sizes"], 0.5, 4, sequential=False)
-    with open_graph(gcb, n, rp, col) as g:
+    with open_graph(gcb, n, rp, col, local_max_pairs=local) as g:
         assert g.counts() == gold["static"]
         outs = g.apply_many(batches, independent=True)
         for out, b in zip(outs, gold["batches"]):
             assert out == b["after"]
+
+
+@pytest.mark.slow
+def test_fullsize_c3_local_batches_keep_counts_of_the_graph(gcb):
+    """Chung-Lu n=1.6M m=30M: sequential batches of the paper's sizes through
+    the edge-local delta; the maintained counts equal a recount of the
+    updated graph, and a twin handle on the region form agrees batch by
+    batch."""
+    n, keys = gen.workload_graph("c3")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [10, 100, 1000, 10, 100], 0.7, 77)
+    with open_graph(gcb, n, rp, col, local_max_pairs=1 << 30) as gl, open_graph(gcb, n, rp, col) as gr:
+        for ins, dels in batches:
+            out = gl.apply(ins, dels)
+            assert gl.stats()["path"] == 1
+            assert out == gr.apply(ins, dels)
+        assert gl.count_static() == gl.counts()
 
 
 # ----------------------------------------------------------- batched form --
