@@ -140,6 +140,19 @@ int gc_counts(const gc_graph *g, uint64_t out[6]);
    counts do (F3 += C3_a - C3_b). */
 int gc_counts3(const gc_graph *g, uint64_t out[2]);
 
+/* Induced counts of all eleven 4-vertex graphs, from the maintained counts,
+   the 3-vertex counts, n and m (no device work): [0..5] the six connected
+   graphlets of gc_counts, [6] triangle + isolated vertex, [7] 2-path +
+   isolated vertex, [8] two vertex-disjoint edges, [9] one edge + two
+   isolated vertices, [10] empty; they sum to C(n, 4).  Each count is
+   128-bit (C(n, 4) passes 2^64 near n = 100,000): out[2i] holds its low
+   64 bits, out[2i + 1] its high 64 bits.  The disconnected counts follow
+   from counting, two ways, the triangles with a fourth vertex, the 2-paths
+   with a fourth vertex, the pairs of vertex-disjoint edges and the edges
+   with two more vertices (each lies in exactly one 4-set, and each induced
+   type holds a fixed number of them). */
+int gc_counts_all(const gc_graph *g, uint64_t out[22]);
+
 /*
  * Apply one batch (Algorithm 2) and return the updated counts.
  *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)

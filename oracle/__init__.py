@@ -12,10 +12,12 @@ only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 """
 from . import brute  # noqa: F401
 from .oracle import (  # noqa: F401
+    ALL_TYPES,
     GRAPHLETS,
     SUMS,
     OracleGraph,
     build,
+    counts_all,
     counts_from_sums,
     fdgc_step,
     normalize,

@@ -8,6 +8,7 @@ the CUDA library.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -115,6 +116,36 @@ def static_counts3(row_ptr, col) -> list[int]:
     if _load().or_counts3(n, _p(rp, ctypes.c_int64), _p(c, ctypes.c_int32), _p(out, ctypes.c_int64)) != 0:
         raise RuntimeError("or_counts3 failed")
     return [int(x) for x in out]
+
+
+ALL_TYPES = ("3-path", "3-star", "4-cycle", "tailed-triangle", "diamond", "4-clique",
+             "triangle+isolated", "2-path+isolated", "two-disjoint-edges", "edge+2-isolated", "empty")
+
+
+def counts_all(row_ptr, col) -> list[int]:
+    """Induced counts of all eleven 4-vertex graphs: the six connected
+    graphlets of Problem 1, then the five disconnected ones, as Python ints
+    (they exceed 64 bits).  The disconnected counts follow from counting
+    pairs (a sub-structure, a 4-set) two ways: every triangle with a fourth
+    vertex, every 2-path with a fourth vertex, every pair of vertex-disjoint
+    edges, and every edge with two more vertices lies in exactly one 4-set,
+    and each induced type holds a fixed number of each; the empty sets are
+    the rest of C(n, 4)."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    n = rp.size - 1
+    m = int(rp[-1]) // 2
+    deg = np.diff(rp)
+    g1, g2, g3, g4, g5, g6 = static_counts(row_ptr, col)
+    p2, tri = static_counts3(row_ptr, col)
+    wedges = sum(int(d) * (int(d) - 1) // 2 for d in deg)   # non-induced 2-paths
+    assert wedges == p2 + 3 * tri
+    c = math.comb
+    t_iso = tri * (n - 3) - g4 - 2 * g5 - 4 * g6
+    w_iso = wedges * (n - 3) - (2 * g1 + 3 * g2 + 4 * g3 + 5 * g4 + 8 * g5 + 12 * g6 + 3 * t_iso)
+    two = (c(m, 2) - wedges) - (g1 + 2 * g3 + g4 + 2 * g5 + 3 * g6)
+    one = m * c(n - 2, 2) - (2 * (w_iso + two) + 3 * (t_iso + g1 + g2) + 4 * (g3 + g4) + 5 * g5 + 6 * g6)
+    empty = c(n, 4) - (one + w_iso + two + t_iso + g1 + g2 + g3 + g4 + g5 + g6)
+    return [g1, g2, g3, g4, g5, g6, t_iso, w_iso, two, one, empty]
 
 
 def normalize(row_ptr, col, ins, dels):

@@ -1488,6 +1488,34 @@ int gc_counts3(const gc_graph* g, uint64_t out[2]) {
     return GC_OK;
 }
 
+int gc_counts_all(const gc_graph* g, uint64_t out[22]) {
+    if (!g || !out) return GC_EINVAL;
+    typedef unsigned __int128 u128;
+    const u128 n = (u128)(uint64_t)g->n, m = (u128)(uint64_t)g->m;
+    const u128 g1 = g->F[0], g2 = g->F[1], g3 = g->F[2], g4 = g->F[3], g5 = g->F[4], g6 = g->F[5];
+    const u128 tri = g->F3[1], wedges = (u128)g->F3[0] + 3 * (u128)g->F3[1];
+    auto c2 = [](u128 x) -> u128 { return x < 2 ? 0 : x * (x - 1) / 2; };
+    auto c4 = [](u128 x) -> u128 { return x < 4 ? 0 : x * (x - 1) / 2 * (x - 2) / 3 * (x - 3) / 4; };
+    u128 c[11];
+    c[0] = g1; c[1] = g2; c[2] = g3; c[3] = g4; c[4] = g5; c[5] = g6;
+    if (g->n < 4) {
+        for (int i = 6; i < 11; i++) c[i] = 0;
+    } else {
+        const u128 t_iso = tri * (n - 3) - g4 - 2 * g5 - 4 * g6;
+        const u128 w_iso = wedges * (n - 3) - (2 * g1 + 3 * g2 + 4 * g3 + 5 * g4 + 8 * g5 + 12 * g6 + 3 * t_iso);
+        const u128 two = (c2(m) - wedges) - (g1 + 2 * g3 + g4 + 2 * g5 + 3 * g6);
+        const u128 one = m * c2(n - 2) -
+                         (2 * (w_iso + two) + 3 * (t_iso + g1 + g2) + 4 * (g3 + g4) + 5 * g5 + 6 * g6);
+        const u128 empty = c4(n) - (one + w_iso + two + t_iso + g1 + g2 + g3 + g4 + g5 + g6);
+        c[6] = t_iso; c[7] = w_iso; c[8] = two; c[9] = one; c[10] = empty;
+    }
+    for (int i = 0; i < 11; i++) {
+        out[2 * i] = (uint64_t)c[i];
+        out[2 * i + 1] = (uint64_t)(c[i] >> 64);
+    }
+    return GC_OK;
+}
+
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;
     for (int i = 0; i < 6; i++) out[i] = g->F[i];

@@ -106,6 +106,7 @@ def load():
             lib.gc_count_static.argtypes = [P, u64p]
             lib.gc_counts.argtypes = [P, u64p]
             lib.gc_counts3.argtypes = [P, u64p]
+            lib.gc_counts_all.argtypes = [P, u64p]
             lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
             lib.gc_add_vertices.argtypes = [P, ctypes.c_int64, i32p]
             lib.gc_num_vertices.argtypes = [P]
@@ -199,6 +200,16 @@ def gc_counts(h) -> list[int]:
     out = np.zeros(6, np.uint64)
     _check(load().gc_counts(h, _ptr(out, ctypes.c_uint64)), h)
     return [int(x) for x in out]
+
+
+ALL_TYPES = GRAPHLETS + ("triangle+isolated", "2-path+isolated", "two-disjoint-edges", "edge+2-isolated", "empty")
+
+
+def gc_counts_all(h) -> list[int]:
+    """Induced counts of all eleven 4-vertex graphs (Python ints; 128-bit)."""
+    out = np.zeros(22, np.uint64)
+    _check(load().gc_counts_all(h, _ptr(out, ctypes.c_uint64)), h)
+    return [int(out[2 * i]) | (int(out[2 * i + 1]) << 64) for i in range(11)]
 
 
 def gc_counts3(h) -> list[int]:
@@ -465,6 +476,9 @@ class Graph:
 
     def counts3(self):
         return gc_counts3(self.h)
+
+    def counts_all(self):
+        return gc_counts_all(self.h)
 
     def count_static(self):
         return gc_count_static(self.h)

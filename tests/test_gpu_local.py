@@ -288,3 +288,26 @@ def test_triangle_sums_through_region_runs_and_toggles(gcb):
         assert g.count_static() == mod64(og.F)
         step(35, 10, 1)
         assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+
+
+def test_all_eleven_types_follow_the_batches(gcb):
+    """The six graphlets plus the five disconnected 4-vertex graphs, from the
+    maintained counts, after region and edge-local batches; 128-bit values
+    on a graph with millions of vertices."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=64) as g:
+        assert g.counts_all() == oracle.counts_all(rp, col)
+        for i, size in enumerate([30, 2000, 10]):
+            ins, dels = gen.random_batch(n, gen.keys_from_csr(og.row_ptr, og.col), size // 2, size - size // 2, 70 + i)
+            og.apply(ins, dels)
+            g.apply(ins, dels)
+            assert g.counts_all() == oracle.counts_all(og.row_ptr, og.col)
+    big = 3_000_000
+    edges = [(0, 1), (1, 2), (2, 0), (2, 3), (5, 6), (7, 8), (8, 9)]
+    rp, col = csr_from_edges(big, edges)
+    with gcb.Graph(big, rp, col) as g:
+        got = g.counts_all()
+        assert got == oracle.counts_all(rp, col)
+        assert got[10] > (1 << 64) and sum(got) == __import__("math").comb(big, 4)

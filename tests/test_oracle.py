@@ -413,3 +413,18 @@ def test_counts3_triangles_agree_with_the_four_vertex_sums(oracle_lib):
         tri = oracle.static_counts3(rp, col)[1]
         TT = oracle.sums_literal(rp, col)[2]
         assert TT == 3 * tri
+
+
+def test_all_eleven_types_match_the_census(oracle_lib):
+    """The disconnected types from closed forms against the census of every
+    4-subset (Problem 1's six graphlets plus the five disconnected graphs)."""
+    rng = np.random.default_rng(4411)
+    order = ["g1", "g2", "g3", "g4", "g5", "g6", "triangle+isolated", "wedge+isolated", "two-edges", "edge", "empty"]
+    for trial in range(40):
+        n = int(rng.integers(4, 22))
+        p = float(rng.uniform(0.0, 0.9))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        rp, col = csr_from_edges(n, edges)
+        h = brute.census(n, edges)
+        assert oracle.counts_all(rp, col) == [h[k] for k in order], trial
+        assert sum(oracle.counts_all(rp, col)) == math.comb(n, 4)
