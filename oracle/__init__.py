@@ -25,4 +25,5 @@ from .oracle import (  # noqa: F401
     static_counts3,
     sums_literal,
     sums_oriented,
+    vertex_counts,
 )

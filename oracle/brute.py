@@ -80,3 +80,30 @@ def graphlet3_counts(n: int, edges) -> list[int]:
     """[induced 2-paths, triangles] by the census."""
     h = census3(n, edges)
     return [h["path"], h["triangle"]]
+
+
+def vertex_census(n: int, edges) -> list[list[int]]:
+    """Per vertex, the number of induced connected 4-vertex graphlets
+    [g1..g6] that contain it: every 4-subset adds its class to each of its
+    four vertices (n <= 40)."""
+    if n > 40:
+        raise ValueError("brute force is for n <= 40")
+    adj = [[False] * n for _ in range(n)]
+    for a, b in edges:
+        adj[a][b] = adj[b][a] = True
+    idx = {c: i for i, c in enumerate(CONNECTED)}
+    out = [[0] * 6 for _ in range(n)]
+    for s in itertools.combinations(range(n), 4):
+        deg = [0, 0, 0, 0]
+        k = 0
+        for i in range(4):
+            for j in range(i + 1, 4):
+                if adj[s[i]][s[j]]:
+                    k += 1
+                    deg[i] += 1
+                    deg[j] += 1
+        c = _CLASSES[(k, tuple(sorted(deg)))]
+        if c in idx:
+            for v in s:
+                out[v][idx[c]] += 1
+    return out

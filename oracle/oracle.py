@@ -148,6 +148,79 @@ def counts_all(row_ptr, col) -> list[int]:
     return [g1, g2, g3, g4, g5, g6, t_iso, w_iso, two, one, empty]
 
 
+def vertex_counts(row_ptr, col) -> list[list[int]]:
+    """Per vertex v, the induced connected 4-vertex graphlets [g1..g6] that
+    contain v (local graphlet counts).  Plain Python over adjacency sets,
+    for graphs of a few thousand vertices.
+
+    The containment identity behind the global counts holds per vertex: a
+    4-set S holds M[H][g] copies of H if G[S] has type g, and every copy
+    spans S, so the non-induced copies of H through v are
+    N_H(v) = sum_g M[H][g] I_g(v) and the same inversion gives I(v).  The
+    non-induced copies through v, counted by v's role in them:
+      3-star   centre C(d_v,3); leaf sum_{u in N(v)} C(d_u - 1, 2)
+      3-path   end: paths v-u-w-x; middle: sum over edges vc of
+               (d_v - 1)(d_c - 1) - t_vc (the other end differs)
+      tailed triangle  tail end, attachment vertex, other triangle vertex
+      diamond  on the shared edge C(t_vu, 2); at a degree-2 corner, for the
+               triangle {v, a, b}, t_ab - 1 choices of the fourth vertex
+      4-clique, 4-cycle  by listing them."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    c = np.asarray(col, dtype=np.int64)
+    n = rp.size - 1
+    N = [set(int(x) for x in c[rp[v]:rp[v + 1]]) for v in range(n)]
+    d = [len(N[v]) for v in range(n)]
+    t = {}
+    for v in range(n):
+        for u in N[v]:
+            if u > v:
+                t[(v, u)] = t[(u, v)] = len(N[v] & N[u])
+    tri = [sum(t[(v, u)] for u in N[v]) // 2 for v in range(n)]
+    out = []
+    for v in range(n):
+        star = d[v] * (d[v] - 1) * (d[v] - 2) // 6 + sum((d[u] - 1) * (d[u] - 2) // 2 for u in N[v])
+        end = 0
+        for u in N[v]:
+            for w in N[u]:
+                if w != v:
+                    end += len(N[w] - {u, v})   # x in N(w), x != u, x != v
+        mid = sum((d[v] - 1) * (d[u] - 1) - t[(v, u)] for u in N[v])
+        tt = sum(tri[z] - t[(v, z)] for z in N[v]) + tri[v] * (d[v] - 2) + sum(t[(v, y)] * (d[y] - 2) for y in N[v])
+        dia = sum(t[(v, u)] * (t[(v, u)] - 1) // 2 for u in N[v])
+        for a in N[v]:
+            for b in N[v]:
+                if b > a and b in N[a]:
+                    dia += t[(a, b)] - 1
+        out.append([end + mid, star, tt, dia, 0, 0])
+    # 4-cliques through v, once each: z > b > a among N(v)
+    for v in range(n):
+        nb = sorted(N[v])
+        k4 = 0
+        for i, a in enumerate(nb):
+            for b in nb[i + 1:]:
+                if b in N[a]:
+                    k4 += sum(1 for z in N[a] & N[b] & N[v] if z > b)
+        out[v][4] = k4
+    # 4-cycles through v: v and its opposite corner w share >= 2 neighbours
+    for v in range(n):
+        cnt = {}
+        for a in N[v]:
+            for w in N[a]:
+                if w != v:
+                    cnt[w] = cnt.get(w, 0) + 1
+        out[v][5] = sum(x * (x - 1) // 2 for x in cnt.values())
+    res = []
+    for P, S, TT, D, K, Q in out:
+        g6 = K
+        g5 = D - 6 * K
+        g3 = Q - g5 - 3 * K
+        g4 = TT - 4 * g5 - 12 * K
+        g2 = S - g4 - 2 * g5 - 4 * K
+        g1 = P - 2 * g4 - 4 * g3 - 6 * g5 - 12 * K
+        res.append([g1, g2, g3, g4, g5, g6])
+    return res
+
+
 def normalize(row_ptr, col, ins, dels):
     """Normalised batch: (A keys, D keys, stats) or raises ValueError."""
     rp, c = _csr(row_ptr, col)

@@ -428,3 +428,31 @@ def test_all_eleven_types_match_the_census(oracle_lib):
         h = brute.census(n, edges)
         assert oracle.counts_all(rp, col) == [h[k] for k in order], trial
         assert sum(oracle.counts_all(rp, col)) == math.comb(n, 4)
+
+
+def test_vertex_counts_match_the_census(oracle_lib):
+    """Per-vertex graphlet counts against the census of every 4-subset
+    credited to its four vertices; their sum over vertices is four times
+    the global counts."""
+    rng = np.random.default_rng(909)
+    for trial in range(50):
+        n = int(rng.integers(4, 20))
+        p = float(rng.uniform(0.05, 0.95))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        rp, col = csr_from_edges(n, edges)
+        got = oracle.vertex_counts(rp, col)
+        assert got == brute.vertex_census(n, edges), trial
+        tot = [sum(r[k] for r in got) for k in range(6)]
+        assert tot == [4 * x for x in oracle.static_counts(rp, col)]
+
+
+def test_vertex_counts_of_named_graphs(oracle_lib):
+    # K4: one 4-clique through each vertex; C4: one 4-cycle; the star K_{1,3}:
+    # one 3-star through each vertex; P4: one 3-path
+    for n, edges, k in ((4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)], 5),
+                        (4, [(0, 1), (1, 2), (2, 3), (3, 0)], 2),
+                        (4, [(0, 1), (0, 2), (0, 3)], 1),
+                        (4, [(0, 1), (1, 2), (2, 3)], 0)):
+        rp, col = csr_from_edges(n, edges)
+        want = [[1 if j == k else 0 for j in range(6)] for _ in range(n)]
+        assert oracle.vertex_counts(rp, col) == want
