@@ -153,6 +153,19 @@ int gc_counts3(const gc_graph *g, uint64_t out[2]);
    type holds a fixed number of them). */
 int gc_counts_all(const gc_graph *g, uint64_t out[22]);
 
+/* Per-vertex (local) graphlet counts of the current graph: out[6 x + k] =
+   the induced connected 4-vertex graphlets of type k (order of gc_counts)
+   that contain vertex x (external ids, out holds 6 n words, host memory).
+   The containment identity of the global counts holds per vertex, so the
+   non-induced copies through each vertex, counted by its role in them,
+   invert the same way; the sum over vertices is 4 x gc_counts.  Runs a
+   static pass plus the per-vertex kernels (device scratch of about 4 bytes
+   per adjacency entry, 64 bytes per vertex, and one 4-byte counter array
+   per 4-cycle block, 2 GB at most, all freed on return); the maintained
+   counts are not changed.  gc_batch_stats().ms_device gives the device
+   time of the per-vertex kernels. */
+int gc_vertex_counts(gc_graph *g, uint64_t *out);
+
 /*
  * Apply one batch (Algorithm 2) and return the updated counts.
  *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)

@@ -1516,6 +1516,77 @@ int gc_counts_all(const gc_graph* g, uint64_t out[22]) {
     return GC_OK;
 }
 
+int gc_vertex_counts(gc_graph* g, uint64_t* out) {
+    if (!g || (!out && g->n > 0)) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    g->err.clear();
+    if (g->n == 0) return GC_OK;
+    // the union graph, per-entry t and T2 of the current graph
+    int rc = count_static(g, false, nullptr);
+    if (rc) return rc;
+    cudaStream_t s = g->s;
+    const size_t n = (size_t)g->n;
+    const long long nU = std::max<long long>(g->h_ctl->nU, 1);
+    // one dense counter array per 4-cycle block, at most 2 GB in all
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(g->sms, (2LL << 30) / (4LL * (long long)n)));
+    uint32_t* tall = (uint32_t*)dalloc(g, 4 * (size_t)nU);
+    long long* sdeg = (long long*)dalloc(g, 8 * n);
+    long long* NV = (long long*)dalloc(g, 48 * n);
+    uint32_t* cnt = (uint32_t*)dalloc(g, 4 * n * (size_t)blocks);
+    unsigned long long* dout = (unsigned long long*)dalloc(g, 48 * n);
+    auto cleanup = [&]() {
+        dfree(g, tall);
+        dfree(g, sdeg);
+        dfree(g, NV);
+        dfree(g, cnt);
+        dfree(g, dout);
+    };
+    if (!tall || !sdeg || !NV || !cnt || !dout) {
+        cleanup();
+        return nomem(g, "per-vertex counts");
+    }
+    if (cudaMemsetAsync(NV, 0, 48 * n, s) != cudaSuccess || cudaMemsetAsync(cnt, 0, 4 * n * (size_t)blocks, s) != cudaSuccess) {
+        cleanup();
+        g->err = "cudaMemsetAsync failed";
+        return GC_ECUDA;
+    }
+    VertexArgs va;
+    va.ctl = g->ctl;
+    va.wlist = g->wlist;
+    va.U_off = g->U_off;
+    va.U_col = g->U_col.p;
+    va.U_split = g->U_split;
+    va.tpack = g->tpack.p;
+    va.T2 = g->T2;
+    va.tall = tall;
+    va.sdeg = sdeg;
+    va.NV = NV;
+    va.cnt = cnt;
+    va.c4_blocks = blocks;
+    va.n = (int)n;
+    va.iperm = g->iperm;
+    va.out = dout;
+    va.sms = g->sms;
+    CK(cudaEventRecord(g->e0, s));
+    g->launches = enqueue_vertex_counts(va, s);
+    CK(cudaEventRecord(g->e1, s));
+    cudaError_t ce = cudaMemcpyAsync(out, dout, 48 * n, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    float ms = 0.f;
+    if (ce == cudaSuccess && cudaEventElapsedTime(&ms, g->e0, g->e1) == cudaSuccess) g->st.ms_device = ms;
+    cleanup();
+    if (ce != cudaSuccess) {
+        g->err = std::string("per-vertex counts: ") + cudaGetErrorString(ce);
+        return GC_ECUDA;
+    }
+    g->st.launches = g->launches;
+    return GC_OK;
+}
+
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;
     for (int i = 0; i < 6; i++) out[i] = g->F[i];

@@ -146,6 +146,27 @@ __global__ void k_t2_from_region(const Ctl* c, const int32_t* wlist, const long 
 int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,
                   int commit);
 
+// Per-vertex graphlet counts of a static pass (gc_vertex.cu).
+struct VertexArgs {
+    Ctl* ctl;
+    const int32_t* wlist;          // all vertices (c->nW = n)
+    const long long* U_off;
+    const uint32_t* U_col;
+    const int32_t* U_split;
+    const unsigned long long* tpack;
+    const unsigned long long* T2;
+    uint32_t* tall;                // nU: t of every entry
+    long long* sdeg;               // n
+    long long* NV;                 // 6 n, zeroed
+    uint32_t* cnt;                 // c4_blocks * n, zeroed
+    int c4_blocks;
+    int n;
+    const int32_t* iperm;
+    unsigned long long* out;       // 6 n, by external id
+    int sms;
+};
+int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s);
+
 // Enqueue the counting kernels (binning, triangles / 4-cliques, 4-cycles,
 // edge terms, closed forms with k_finalize(mode)); events, when given, are
 // recorded before the triangle, 4-cycle and edge-term stages.  Returns the

@@ -1,0 +1,263 @@
+// gc_vertex.cu -- per-vertex (local) graphlet counts of the current graph:
+// for every vertex v, the induced connected 4-vertex graphlets [g1..g6]
+// that contain v.
+//
+// The containment identity behind the global counts (Sec. 3, PGD's closed
+// forms) holds per vertex: a 4-set S holds M[H][g] copies of H when G[S]
+// has type g, and every copy spans S, so the non-induced copies of H
+// through v are N_H(v) = sum_g M[H][g] I_g(v) and the same inversion gives
+// I(v).  The non-induced copies through v, by v's role in them (d degrees,
+// t_e triangles per edge, tri(v) = T2[v] / 2 triangles at v,
+// s(u) = sum_{w in N(u)} (d_w - 1)):
+//   3-star   centre C(d_v, 3); leaf sum_{u in N(v)} C(d_u - 1, 2)
+//   3-path   end sum_{u in N(v)} (s(u) - (d_v - 1)) - 2 tri(v);
+//            middle sum_{u in N(v)} ((d_v - 1)(d_u - 1) - t_vu)
+//   tailed triangle  tail end sum_z (tri(z) - t_vz); attachment
+//            tri(v)(d_v - 2); other triangle vertex sum_y t_vy (d_y - 2)
+//   diamond  shared edge sum_u C(t_vu, 2); degree-2 corner: for each
+//            triangle {v, a, b}, t_ab - 1
+//   4-clique listed once (oriented), each of its four vertices credited
+//   4-cycle  counted once at its highest vertex u with opposite corner w:
+//            c_w = common lower neighbours, C(c_w, 2) cycles credit u and
+//            w, and each middle vertex a of a wedge u-a-w gets c_w - 1.
+// The input is the union graph U of a static count (both flags on every
+// entry, t of each out-entry in tpack, T2 filled).
+#include "gc_internal.cuh"
+#include "gc_kernels.cuh"
+
+namespace gcx {
+
+// t of every entry (out-entries carry it; an in-entry reads its twin).
+__global__ void k_v_tsym(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                         const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                         const unsigned long long* __restrict__ tpack, uint32_t* __restrict__ tall) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        for (long long e = U_off[u] + U_split[u] + lane; e < U_off[u + 1]; e += 32) {
+            const uint32_t t = (uint32_t)(tpack[e] >> 32);
+            const uint32_t v = vid(U_col[e]);
+            tall[e] = t;
+            const long long vb = U_off[v];
+            tall[vb + lower_bound_id(U_col + vb, U_split[v], u)] = t;
+        }
+    }
+}
+
+// s(u) = sum over the neighbours w of (d_w - 1)
+__global__ void k_v_s(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                      const uint32_t* __restrict__ U_col, long long* __restrict__ sdeg) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        long long sum = 0;
+        for (long long e = U_off[u] + lane; e < U_off[u + 1]; e += 32) {
+            const uint32_t w = vid(U_col[e]);
+            sum += U_off[w + 1] - U_off[w] - 1;
+        }
+        sum = (long long)warp_sum_u64((unsigned long long)sum);
+        if (lane == 0) sdeg[u] = sum;
+    }
+}
+
+// The row terms of each vertex: 3-path (end and middle), 3-star, tailed
+// triangle, and the shared-edge part of the diamonds.  NV[v][0..5] =
+// non-induced (P, S, TT, D, K, Q) through v.
+__global__ void k_v_terms(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                          const uint32_t* __restrict__ U_col, const uint32_t* __restrict__ tall,
+                          const long long* __restrict__ sdeg, const unsigned long long* __restrict__ T2,
+                          long long* __restrict__ NV) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t v = (uint32_t)wlist[i];
+        const long long rb = U_off[v], re = U_off[v + 1];
+        const long long d = re - rb, trv = (long long)(T2[v] / 2);
+        long long P = 0, S = 0, TT = 0, D = 0;
+        for (long long e = rb + lane; e < re; e += 32) {
+            const uint32_t u = vid(U_col[e]);
+            const long long du = U_off[u + 1] - U_off[u], t = tall[e];
+            S += (du - 1) * (du - 2) / 2;
+            P += sdeg[u] - (d - 1) + (d - 1) * (du - 1) - t;
+            TT += (long long)(T2[u] / 2) - t + t * (du - 2);
+            D += t * (t - 1) / 2;
+        }
+        P = (long long)warp_sum_u64((unsigned long long)P);
+        S = (long long)warp_sum_u64((unsigned long long)S);
+        TT = (long long)warp_sum_u64((unsigned long long)TT);
+        D = (long long)warp_sum_u64((unsigned long long)D);
+        if (lane == 0) {
+            long long* o = NV + 6 * (size_t)v;
+            o[0] += P - 2 * trv;
+            o[1] += S + d * (d - 1) * (d - 2) / 6;
+            o[2] += TT + trv * (d - 2);
+            o[3] += D;
+        }
+    }
+}
+
+// Triangles u < v < y (each once): the degree-2 corner part of the
+// diamonds (t of the opposite edge - 1 to each corner); 4-cliques
+// u < v < y < z (each once) credited to their four vertices.  A warp per
+// root u, a lane per out-edge (out-lists are short in the degree order).
+__global__ void k_v_tri_k4(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                           const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                           const uint32_t* __restrict__ tall, long long* __restrict__ NV) {
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int wi = warp; wi < nW; wi += nwarps) {
+        const uint32_t u = (uint32_t)wlist[wi];
+        const long long ob = U_off[u] + U_split[u], oe = U_off[u + 1];
+        for (long long e = ob + lane; e < oe; e += 32) {
+            const uint32_t v = vid(U_col[e]);
+            const long long vb = U_off[v] + U_split[v], ve = U_off[v + 1];
+            long long i = e + 1, j = vb;
+            long long k4u = 0;
+            while (i < oe && j < ve) {
+                const uint32_t x = vid(U_col[i]), y = vid(U_col[j]);
+                if (x < y) {
+                    i++;
+                } else if (x > y) {
+                    j++;
+                } else {
+                    // triangle (u, v, y): t of uv, uy, vy at e, i, j
+                    atomicAdd((unsigned long long*)&NV[6 * (size_t)u + 3], (unsigned long long)((long long)tall[j] - 1));
+                    atomicAdd((unsigned long long*)&NV[6 * (size_t)v + 3], (unsigned long long)((long long)tall[i] - 1));
+                    atomicAdd((unsigned long long*)&NV[6 * (size_t)y + 3], (unsigned long long)((long long)tall[e] - 1));
+                    // 4-cliques (u, v, y, z), z > y in N+(u), N+(v), N+(y)
+                    const long long yb = U_off[y] + U_split[y], ye = U_off[y + 1];
+                    long long p = i + 1, q = j + 1, r = yb, kk = 0;
+                    while (p < oe && q < ve && r < ye) {
+                        const uint32_t a = vid(U_col[p]), b = vid(U_col[q]), cc = vid(U_col[r]);
+                        const uint32_t mx = max(a, max(b, cc));
+                        if (a == mx && b == mx && cc == mx) {
+                            atomicAdd((unsigned long long*)&NV[6 * (size_t)a + 4], 1ull);
+                            kk++;
+                            p++;
+                            q++;
+                            r++;
+                        } else {
+                            if (a < mx) p++;
+                            if (b < mx) q++;
+                            if (cc < mx) r++;
+                        }
+                    }
+                    if (kk) {
+                        atomicAdd((unsigned long long*)&NV[6 * (size_t)v + 4], (unsigned long long)kk);
+                        atomicAdd((unsigned long long*)&NV[6 * (size_t)y + 4], (unsigned long long)kk);
+                        k4u += kk;
+                    }
+                    i++;
+                    j++;
+                }
+            }
+            if (k4u) atomicAdd((unsigned long long*)&NV[6 * (size_t)u + 4], (unsigned long long)k4u);
+        }
+    }
+}
+
+// 4-cycles, a block per pivot u (its highest vertex) with one dense counter
+// array of n words per block: walk 1 counts c_w over the wedges u-a-w
+// (a, w below u), walk 2 credits each middle a with c_w - 1, walk 3 takes
+// and clears c_w, crediting w and u with C(c_w, 2).
+__global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __restrict__ wlist,
+                                               const long long* __restrict__ U_off,
+                                               const uint32_t* __restrict__ U_col,
+                                               const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_all,
+                                               int n, long long* __restrict__ NV) {
+    const int nW = c->nW;
+    uint32_t* cnt = cnt_all + (size_t)blockIdx.x * (size_t)n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NWp = blockDim.x >> 5;
+    __shared__ unsigned long long s_u[32];
+    for (int pi = blockIdx.x; pi < nW; pi += gridDim.x) {
+        const uint32_t u = (uint32_t)wlist[pi];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        unsigned long long usum = 0;
+        for (int pass = 0; pass < 3; pass++) {
+            for (int j = warp; j < nlow; j += NWp) {
+                const uint32_t a = vid(U_col[rb + j]);
+                const long long ab = U_off[a], ae = U_off[a + 1];
+                long long asum = 0;
+                for (long long q = ab + lane; q < ae; q += 32) {
+                    const uint32_t w = vid(U_col[q]);
+                    if (w >= u) break;  // rows are sorted: the rest is above u
+                    if (pass == 0) {
+                        atomicAdd(&cnt[w], 1u);
+                    } else if (pass == 1) {
+                        asum += (long long)__ldcg(&cnt[w]) - 1;
+                    } else {
+                        const uint32_t old = atomicExch(&cnt[w], 0u);
+                        if (old >= 2) {
+                            const unsigned long long cy = (unsigned long long)old * (old - 1) / 2;
+                            atomicAdd((unsigned long long*)&NV[6 * (size_t)w + 5], cy);
+                            usum += cy;
+                        }
+                    }
+                }
+                if (pass == 1) {
+                    asum = (long long)warp_sum_u64((unsigned long long)asum);
+                    if (lane == 0 && asum) atomicAdd((unsigned long long*)&NV[6 * (size_t)a + 5], (unsigned long long)asum);
+                }
+            }
+            __threadfence();
+            __syncthreads();
+        }
+        usum = warp_sum_u64(usum);
+        if (lane == 0) s_u[warp] = usum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < NWp; w++) t += s_u[w];
+            if (t) atomicAdd((unsigned long long*)&NV[6 * (size_t)u + 5], t);  // other blocks credit u too
+        }
+        __syncthreads();
+    }
+}
+
+// Induced counts per vertex by the containment inversion, to external ids.
+__global__ void k_v_finalize(const long long* __restrict__ NV, int n, const int32_t* __restrict__ iperm,
+                             unsigned long long* __restrict__ out) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const long long* s = NV + 6 * (size_t)v;
+        const long long P = s[0], S = s[1], TT = s[2], D = s[3], K = s[4], Q = s[5];
+        const long long g6 = K;
+        const long long g5 = D - 6 * K;
+        const long long g3 = Q - g5 - 3 * K;
+        const long long g4 = TT - 4 * g5 - 12 * K;
+        const long long g2 = S - g4 - 2 * g5 - 4 * K;
+        const long long g1 = P - 2 * g4 - 4 * g3 - 6 * g5 - 12 * K;
+        unsigned long long* o = out + 6 * (size_t)iperm[v];
+        o[0] = (unsigned long long)g1;
+        o[1] = (unsigned long long)g2;
+        o[2] = (unsigned long long)g3;
+        o[3] = (unsigned long long)g4;
+        o[4] = (unsigned long long)g5;
+        o[5] = (unsigned long long)g6;
+    }
+}
+
+int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s) {
+    const int gw = 8 * a.sms, tpb = 256;
+    int nl = 0;
+    k_v_tsym<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.tall);
+    k_v_s<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.sdeg);
+    k_v_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.tall, a.sdeg, a.T2, a.NV);
+    k_v_tri_k4<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NV);
+    k_v_c4<<<a.c4_blocks, 1024, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n, a.NV);
+    k_v_finalize<<<(a.n + 255) / 256, 256, 0, s>>>(a.NV, a.n, a.iperm, a.out);
+    nl += 6;
+    return nl;
+}
+
+}  // namespace gcx

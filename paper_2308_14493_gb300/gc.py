@@ -107,6 +107,7 @@ def load():
             lib.gc_counts.argtypes = [P, u64p]
             lib.gc_counts3.argtypes = [P, u64p]
             lib.gc_counts_all.argtypes = [P, u64p]
+            lib.gc_vertex_counts.argtypes = [P, u64p]
             lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
             lib.gc_add_vertices.argtypes = [P, ctypes.c_int64, i32p]
             lib.gc_num_vertices.argtypes = [P]
@@ -210,6 +211,13 @@ def gc_counts_all(h) -> list[int]:
     out = np.zeros(22, np.uint64)
     _check(load().gc_counts_all(h, _ptr(out, ctypes.c_uint64)), h)
     return [int(out[2 * i]) | (int(out[2 * i + 1]) << 64) for i in range(11)]
+
+
+def gc_vertex_counts(h, n: int) -> np.ndarray:
+    """Per-vertex graphlet counts of the current graph: uint64[n, 6]."""
+    out = np.zeros((max(n, 1), 6), np.uint64)
+    _check(load().gc_vertex_counts(h, _ptr(out, ctypes.c_uint64)), h)
+    return out[:n]
 
 
 def gc_counts3(h) -> list[int]:
@@ -479,6 +487,9 @@ class Graph:
 
     def counts_all(self):
         return gc_counts_all(self.h)
+
+    def vertex_counts(self):
+        return gc_vertex_counts(self.h, self.n)
 
     def count_static(self):
         return gc_count_static(self.h)
