@@ -426,6 +426,21 @@ def paper_regime(gcb, torch, n, keys, rp, col, stream, flush, static_ms):
     return out
 
 
+def vertex_counts_line(gcb, n, rp, col):
+    """Per-vertex graphlet counts of the graph (gc_vertex_counts): device time
+    of the per-vertex kernels (after the static pass they start from) and of
+    that static pass; the sum over vertices checked against four times the
+    global counts."""
+    with gcb.Graph(n, rp, col) as g:
+        g.vertex_counts()  # warm-up
+        v = g.vertex_counts()
+        ms_v = g.stats()["ms_device"]
+        g.count_static()
+        ms_s = g.stats()["ms_device"]
+        ok = [int(x) for x in v.astype(object).sum(axis=0)] == [4 * x for x in g.counts()]
+    return {"vertices": n, "per_vertex_kernels_ms": ms_v, "static_pass_ms": ms_s, "sum_is_4x_counts": ok}
+
+
 def c4_block(gcb, torch, stream, flush, peak, peak_kind):
     """64 independent batches (sizes log-uniform in 10..50,000, 50/50,
     degree-weighted endpoints) against one snapshot of the Chung-Lu
@@ -517,6 +532,7 @@ def gpu_arm(args):
                 except Exception as e:  # pragma: no cover - reported, not hidden
                     pvb[tag] = {"error": str(e)}
             sec["c2_plain_vs_batched"] = pvb
+            sec["c2_vertex_counts"] = vertex_counts_line(gcb, n, rp, col)
         if not args.no_large:
             try:
                 sec["c4_independent"] = c4_block(gcb, torch, stream, flush, peak, peak_kind)
@@ -533,6 +549,10 @@ def gpu_arm(args):
                     sec["c3_paper_batch_sizes"] = paper_regime(gcb, torch, n3, keys3, rp3, col3, stream, flush, st_ms3)
                 except Exception as e:  # pragma: no cover
                     sec["c3_paper_batch_sizes"] = {"error": str(e)}
+                try:
+                    sec["c3_vertex_counts"] = vertex_counts_line(gcb, n3, rp3, col3)
+                except Exception as e:  # pragma: no cover
+                    sec["c3_vertex_counts"] = {"error": str(e)}
                 sec["c3"] = {"workload": sp3["desc"], "plain": {"value": s3["value"], "ms_per_batch": s3["ms_per_step"],
                                                                  "p99_ms": s3["p99_ms"]},
                              "batched": {"value": s3["edges"] / secs3, "ms_per_batch": 1e3 * secs3 / 3},
