@@ -26,4 +26,5 @@ from .oracle import (  # noqa: F401
     sums_literal,
     sums_oriented,
     vertex_counts,
+    vertex_orbits,
 )

@@ -107,3 +107,47 @@ def vertex_census(n: int, edges) -> list[list[int]]:
             for v in s:
                 out[v][idx[c]] += 1
     return out
+
+
+# orbit of a vertex inside each connected induced 4-vertex graph, by its
+# degree there (the paw's two degree-2 corners share an orbit; its degree-2
+# vertex set holds no tail): orbits 4..14 in the usual numbering of
+# 4-vertex graphlet orbits
+def _orbit(cls: str, deg: list[int], i: int) -> int:
+    d = deg[i]
+    if cls == "g1":
+        return 4 if d == 1 else 5
+    if cls == "g2":
+        return 6 if d == 1 else 7
+    if cls == "g3":
+        return 8
+    if cls == "g4":
+        return {1: 9, 2: 10, 3: 11}[d]
+    if cls == "g5":
+        return 12 if d == 2 else 13
+    return 14
+
+
+def vertex_orbit_census(n: int, edges) -> list[list[int]]:
+    """Per vertex, how many induced connected 4-vertex graphlets hold it in
+    each orbit 4..14 (11 columns), over all 4-subsets (n <= 40)."""
+    if n > 40:
+        raise ValueError("brute force is for n <= 40")
+    adj = [[False] * n for _ in range(n)]
+    for a, b in edges:
+        adj[a][b] = adj[b][a] = True
+    out = [[0] * 11 for _ in range(n)]
+    for s in itertools.combinations(range(n), 4):
+        deg = [0, 0, 0, 0]
+        k = 0
+        for i in range(4):
+            for j in range(i + 1, 4):
+                if adj[s[i]][s[j]]:
+                    k += 1
+                    deg[i] += 1
+                    deg[j] += 1
+        c = _CLASSES[(k, tuple(sorted(deg)))]
+        if c in CONNECTED:
+            for i, v in enumerate(s):
+                out[v][_orbit(c, deg, i) - 4] += 1
+    return out

@@ -148,23 +148,27 @@ def counts_all(row_ptr, col) -> list[int]:
     return [g1, g2, g3, g4, g5, g6, t_iso, w_iso, two, one, empty]
 
 
-def vertex_counts(row_ptr, col) -> list[list[int]]:
-    """Per vertex v, the induced connected 4-vertex graphlets [g1..g6] that
-    contain v (local graphlet counts).  Plain Python over adjacency sets,
-    for graphs of a few thousand vertices.
+def vertex_orbits(row_ptr, col) -> list[list[int]]:
+    """Per vertex v, how many induced connected 4-vertex graphlets hold v in
+    each orbit 4..14 (11 columns: 3-path end, middle; 3-star leaf, centre;
+    4-cycle; tailed triangle tail end, other triangle corner, attachment;
+    diamond degree-2, degree-3 corner; 4-clique).  Plain Python over
+    adjacency sets, for graphs of a few thousand vertices.
 
-    The containment identity behind the global counts holds per vertex: a
-    4-set S holds M[H][g] copies of H if G[S] has type g, and every copy
-    spans S, so the non-induced copies of H through v are
-    N_H(v) = sum_g M[H][g] I_g(v) and the same inversion gives I(v).  The
-    non-induced copies through v, counted by v's role in them:
-      3-star   centre C(d_v,3); leaf sum_{u in N(v)} C(d_u - 1, 2)
-      3-path   end: paths v-u-w-x; middle: sum over edges vc of
-               (d_v - 1)(d_c - 1) - t_vc (the other end differs)
-      tailed triangle  tail end, attachment vertex, other triangle vertex
-      diamond  on the shared edge C(t_vu, 2); at a degree-2 corner, for the
-               triangle {v, a, b}, t_ab - 1 choices of the fourth vertex
-      4-clique, 4-cycle  by listing them."""
+    The containment identity behind the global counts holds per vertex and
+    role: a 4-set S of induced type g holding v in orbit o contains a fixed
+    number of copies of each subgraph H with v in each role r, so the
+    non-induced role counts N_r(v) = sum_o M[r][o] I_o(v), and M is
+    triangular.  The role counts (d degrees, t_e triangles per edge, tri(v)
+    triangles at v, s(u) = sum_{w in N(u)} (d_w - 1)):
+      3-path end: paths v-u-w-x; middle: sum_u ((d_v-1)(d_u-1) - t_vu)
+      3-star leaf: sum_u C(d_u - 1, 2); centre: C(d_v, 3)
+      4-cycle: pairs of common neighbours of v and an opposite corner w
+      tailed triangle tail end: sum_z (tri(z) - t_vz); other corner:
+        sum_y t_vy (d_y - 2); attachment: tri(v)(d_v - 2)
+      diamond degree-2 corner: sum over triangles {v, a, b} of t_ab - 1;
+        degree-3 corner: sum_u C(t_vu, 2)
+      4-clique: cliques through v."""
     rp = np.asarray(row_ptr, dtype=np.int64)
     c = np.asarray(col, dtype=np.int64)
     n = rp.size - 1
@@ -178,47 +182,53 @@ def vertex_counts(row_ptr, col) -> list[list[int]]:
     tri = [sum(t[(v, u)] for u in N[v]) // 2 for v in range(n)]
     out = []
     for v in range(n):
-        star = d[v] * (d[v] - 1) * (d[v] - 2) // 6 + sum((d[u] - 1) * (d[u] - 2) // 2 for u in N[v])
-        end = 0
+        p_end = 0
         for u in N[v]:
             for w in N[u]:
                 if w != v:
-                    end += len(N[w] - {u, v})   # x in N(w), x != u, x != v
-        mid = sum((d[v] - 1) * (d[u] - 1) - t[(v, u)] for u in N[v])
-        tt = sum(tri[z] - t[(v, z)] for z in N[v]) + tri[v] * (d[v] - 2) + sum(t[(v, y)] * (d[y] - 2) for y in N[v])
-        dia = sum(t[(v, u)] * (t[(v, u)] - 1) // 2 for u in N[v])
-        for a in N[v]:
-            for b in N[v]:
-                if b > a and b in N[a]:
-                    dia += t[(a, b)] - 1
-        out.append([end + mid, star, tt, dia, 0, 0])
-    # 4-cliques through v, once each: z > b > a among N(v)
-    for v in range(n):
-        nb = sorted(N[v])
-        k4 = 0
-        for i, a in enumerate(nb):
-            for b in nb[i + 1:]:
-                if b in N[a]:
-                    k4 += sum(1 for z in N[a] & N[b] & N[v] if z > b)
-        out[v][4] = k4
-    # 4-cycles through v: v and its opposite corner w share >= 2 neighbours
-    for v in range(n):
+                    p_end += len(N[w] - {u, v})   # x in N(w), x != u, x != v
+        p_mid = sum((d[v] - 1) * (d[u] - 1) - t[(v, u)] for u in N[v])
+        s_leaf = sum((d[u] - 1) * (d[u] - 2) // 2 for u in N[v])
+        s_ctr = d[v] * (d[v] - 1) * (d[v] - 2) // 6
         cnt = {}
         for a in N[v]:
             for w in N[a]:
                 if w != v:
                     cnt[w] = cnt.get(w, 0) + 1
-        out[v][5] = sum(x * (x - 1) // 2 for x in cnt.values())
-    res = []
-    for P, S, TT, D, K, Q in out:
-        g6 = K
-        g5 = D - 6 * K
-        g3 = Q - g5 - 3 * K
-        g4 = TT - 4 * g5 - 12 * K
-        g2 = S - g4 - 2 * g5 - 4 * K
-        g1 = P - 2 * g4 - 4 * g3 - 6 * g5 - 12 * K
-        res.append([g1, g2, g3, g4, g5, g6])
-    return res
+        c4 = sum(x * (x - 1) // 2 for x in cnt.values())
+        tt_tail = sum(tri[z] - t[(v, z)] for z in N[v])
+        tt_oth = sum(t[(v, y)] * (d[y] - 2) for y in N[v])
+        tt_att = tri[v] * (d[v] - 2)
+        d3 = sum(t[(v, u)] * (t[(v, u)] - 1) // 2 for u in N[v])
+        d2 = 0
+        k4 = 0
+        nb = sorted(N[v])
+        for i, a in enumerate(nb):
+            for b in nb[i + 1:]:
+                if b in N[a]:
+                    d2 += t[(a, b)] - 1
+                    k4 += sum(1 for z in N[a] & N[b] & N[v] if z > b)
+        # invert the role containment (triangular)
+        o14 = k4
+        o13 = d3 - 3 * o14
+        o12 = d2 - 3 * o14
+        o11 = tt_att - 2 * o13 - 3 * o14
+        o10 = tt_oth - 2 * o12 - 2 * o13 - 6 * o14
+        o9 = tt_tail - 2 * o12 - 3 * o14
+        o8 = c4 - o12 - o13 - 3 * o14
+        o7 = s_ctr - o11 - o13 - o14
+        o6 = s_leaf - o9 - o10 - 2 * o12 - o13 - 3 * o14
+        o5 = p_mid - 2 * o8 - o10 - 2 * o11 - 2 * o12 - 4 * o13 - 6 * o14
+        o4 = p_end - 2 * o8 - 2 * o9 - o10 - 4 * o12 - 2 * o13 - 6 * o14
+        out.append([o4, o5, o6, o7, o8, o9, o10, o11, o12, o13, o14])
+    return out
+
+
+def vertex_counts(row_ptr, col) -> list[list[int]]:
+    """Per vertex v, the induced connected 4-vertex graphlets [g1..g6] that
+    contain v: the sums of its orbits per graphlet."""
+    return [[o[0] + o[1], o[2] + o[3], o[4], o[5] + o[6] + o[7], o[8] + o[9], o[10]]
+            for o in vertex_orbits(row_ptr, col)]
 
 
 def normalize(row_ptr, col, ins, dels):

@@ -456,3 +456,15 @@ def test_vertex_counts_of_named_graphs(oracle_lib):
         rp, col = csr_from_edges(n, edges)
         want = [[1 if j == k else 0 for j in range(6)] for _ in range(n)]
         assert oracle.vertex_counts(rp, col) == want
+
+
+def test_vertex_orbits_match_the_census(oracle_lib):
+    """Orbit counts per vertex (orbits 4..14) against the census of every
+    4-subset, each vertex credited with its orbit in the induced graph."""
+    rng = np.random.default_rng(1414)
+    for trial in range(50):
+        n = int(rng.integers(4, 20))
+        p = float(rng.uniform(0.05, 0.95))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        rp, col = csr_from_edges(n, edges)
+        assert oracle.vertex_orbits(rp, col) == brute.vertex_orbit_census(n, edges), trial
