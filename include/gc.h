@@ -166,6 +166,15 @@ int gc_counts_all(const gc_graph *g, uint64_t out[22]);
    time of the per-vertex kernels. */
 int gc_vertex_counts(gc_graph *g, uint64_t *out);
 
+/* The same per vertex and orbit: out[11 x + j] = the induced connected
+   4-vertex graphlets holding vertex x in orbit 4 + j (orbits 4..14: 3-path
+   end, middle; 3-star leaf, centre; 4-cycle; tailed triangle tail end,
+   other triangle corner, attachment; diamond degree-2 corner, degree-3
+   corner; 4-clique).  out holds 11 n words.  The role counts invert with
+   the triangular containment of roles in orbits; the orbits of a graphlet
+   sum to its per-vertex count. */
+int gc_vertex_orbits(gc_graph *g, uint64_t *out);
+
 /*
  * Apply one batch (Algorithm 2) and return the updated counts.
  *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)

@@ -1516,7 +1516,7 @@ int gc_counts_all(const gc_graph* g, uint64_t out[22]) {
     return GC_OK;
 }
 
-int gc_vertex_counts(gc_graph* g, uint64_t* out) {
+static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
     if (!g || (!out && g->n > 0)) return GC_EINVAL;
     if (!on_device(g)) {
         g->err = "cudaSetDevice failed";
@@ -1534,9 +1534,10 @@ int gc_vertex_counts(gc_graph* g, uint64_t* out) {
     const int blocks = (int)std::max<long long>(1, std::min<long long>(g->sms, (2LL << 30) / (4LL * (long long)n)));
     uint32_t* tall = (uint32_t*)dalloc(g, 4 * (size_t)nU);
     long long* sdeg = (long long*)dalloc(g, 8 * n);
-    long long* NV = (long long*)dalloc(g, 48 * n);
+    const int k = orbits ? 11 : 6;
+    long long* NV = (long long*)dalloc(g, 88 * n);
     uint32_t* cnt = (uint32_t*)dalloc(g, 4 * n * (size_t)blocks);
-    unsigned long long* dout = (unsigned long long*)dalloc(g, 48 * n);
+    unsigned long long* dout = (unsigned long long*)dalloc(g, 8 * (size_t)k * n);
     auto cleanup = [&]() {
         dfree(g, tall);
         dfree(g, sdeg);
@@ -1548,7 +1549,7 @@ int gc_vertex_counts(gc_graph* g, uint64_t* out) {
         cleanup();
         return nomem(g, "per-vertex counts");
     }
-    if (cudaMemsetAsync(NV, 0, 48 * n, s) != cudaSuccess || cudaMemsetAsync(cnt, 0, 4 * n * (size_t)blocks, s) != cudaSuccess) {
+    if (cudaMemsetAsync(NV, 0, 88 * n, s) != cudaSuccess || cudaMemsetAsync(cnt, 0, 4 * n * (size_t)blocks, s) != cudaSuccess) {
         cleanup();
         g->err = "cudaMemsetAsync failed";
         return GC_ECUDA;
@@ -1569,11 +1570,12 @@ int gc_vertex_counts(gc_graph* g, uint64_t* out) {
     va.n = (int)n;
     va.iperm = g->iperm;
     va.out = dout;
+    va.orbits = orbits;
     va.sms = g->sms;
     CK(cudaEventRecord(g->e0, s));
     g->launches = enqueue_vertex_counts(va, s);
     CK(cudaEventRecord(g->e1, s));
-    cudaError_t ce = cudaMemcpyAsync(out, dout, 48 * n, cudaMemcpyDeviceToHost, s);
+    cudaError_t ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * n, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce == cudaSuccess) ce = cudaGetLastError();
     float ms = 0.f;
@@ -1586,6 +1588,10 @@ int gc_vertex_counts(gc_graph* g, uint64_t* out) {
     g->st.launches = g->launches;
     return GC_OK;
 }
+
+int gc_vertex_counts(gc_graph* g, uint64_t* out) { return vertex_counts(g, out, 0); }
+
+int gc_vertex_orbits(gc_graph* g, uint64_t* out) { return vertex_counts(g, out, 1); }
 
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;

@@ -157,12 +157,13 @@ struct VertexArgs {
     const unsigned long long* T2;
     uint32_t* tall;                // nU: t of every entry
     long long* sdeg;               // n
-    long long* NV;                 // 6 n, zeroed
+    long long* NV;                 // 11 n role counts, zeroed
     uint32_t* cnt;                 // c4_blocks * n, zeroed
     int c4_blocks;
     int n;
     const int32_t* iperm;
-    unsigned long long* out;       // 6 n, by external id
+    unsigned long long* out;       // 6 n (graphlets) or 11 n (orbits), by external id
+    int orbits;
     int sms;
 };
 int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s);

@@ -108,6 +108,7 @@ def load():
             lib.gc_counts3.argtypes = [P, u64p]
             lib.gc_counts_all.argtypes = [P, u64p]
             lib.gc_vertex_counts.argtypes = [P, u64p]
+            lib.gc_vertex_orbits.argtypes = [P, u64p]
             lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
             lib.gc_add_vertices.argtypes = [P, ctypes.c_int64, i32p]
             lib.gc_num_vertices.argtypes = [P]
@@ -217,6 +218,13 @@ def gc_vertex_counts(h, n: int) -> np.ndarray:
     """Per-vertex graphlet counts of the current graph: uint64[n, 6]."""
     out = np.zeros((max(n, 1), 6), np.uint64)
     _check(load().gc_vertex_counts(h, _ptr(out, ctypes.c_uint64)), h)
+    return out[:n]
+
+
+def gc_vertex_orbits(h, n: int) -> np.ndarray:
+    """Per-vertex orbit counts (orbits 4..14) of the current graph: uint64[n, 11]."""
+    out = np.zeros((max(n, 1), 11), np.uint64)
+    _check(load().gc_vertex_orbits(h, _ptr(out, ctypes.c_uint64)), h)
     return out[:n]
 
 
@@ -490,6 +498,9 @@ class Graph:
 
     def vertex_counts(self):
         return gc_vertex_counts(self.h, self.n)
+
+    def vertex_orbits(self):
+        return gc_vertex_orbits(self.h, self.n)
 
     def count_static(self):
         return gc_count_static(self.h)

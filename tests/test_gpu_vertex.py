@@ -72,3 +72,24 @@ def test_vertex_counts_sum_to_four_times_the_counts(gcb, name):
         assert tot == [4 * x for x in g.counts()]
         deg = np.diff(rp)
         assert np.all(v[deg == 0] == 0)
+
+
+def test_vertex_orbits_random_and_planted(gcb):
+    rng = np.random.default_rng(77)
+    cases = []
+    for trial in range(15):
+        n = int(rng.integers(4, 80))
+        cases.append((n, random_graph(rng, n, float(rng.uniform(0.03, 0.8)))))
+    n = 200
+    edges = {(0, v) for v in range(1, n)} | {(a, b) for a in range(1, 12) for b in range(a + 1, 12)}
+    edges |= {(v, v + 1) for v in range(20, n - 1)} | {(a, b) for a in range(100, 108) for b in range(150, 158)}
+    cases.append((n, sorted(edges)))
+    for n, edges in cases:
+        rp, col = csr_from_edges(n, edges)
+        with gcb.Graph(n, rp, col) as g:
+            orb = g.vertex_orbits().astype(np.int64)
+            assert orb.tolist() == oracle.vertex_orbits(rp, col)
+            per = g.vertex_counts().astype(np.int64)
+            sums = np.stack([orb[:, 0] + orb[:, 1], orb[:, 2] + orb[:, 3], orb[:, 4],
+                             orb[:, 5] + orb[:, 6] + orb[:, 7], orb[:, 8] + orb[:, 9], orb[:, 10]], axis=1)
+            assert np.array_equal(per, sums)
