@@ -230,6 +230,7 @@ namespace gcx {
 // A halted run (a commit waiting for pool space) makes every later batch
 // empty and inactive.
 __global__ void k_begin_batch(Ctl* c, const long long* desc) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     const bool run = c->halt == 0;
     c->active = run ? 1 : 0;
@@ -261,6 +262,7 @@ __global__ void k_begin_batch(Ctl* c, const long long* desc) {
 
 // result of the current batch to out[cur], advance the cursor
 __global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit) {
+    pdl_enter();
     if (threadIdx.x != 0 || !c->active) return;
     for (int k = 0; k < 6; k++) out[6 * (long long)c->cur + k] = c->last_out[k];
     if (commit && !c->err && !c->lovf) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
@@ -268,6 +270,7 @@ __global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit) {
 }
 
 __global__ void k_run_reset(Ctl* c) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     c->cur = 0;
     c->halt = 0;
@@ -276,6 +279,7 @@ __global__ void k_run_reset(Ctl* c) {
 
 // restore the kept-entry counts of the batch whose commit is pending
 __global__ void k_resume_pending(Ctl* c) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     c->nA2 = c->pend_nA2;
     c->nD2 = c->pend_nD2;
@@ -285,10 +289,12 @@ __global__ void k_resume_pending(Ctl* c) {
 }
 
 __global__ void k_halt_clear(Ctl* c) {
+    pdl_enter();
     if (threadIdx.x == 0) c->halt = 0;
 }
 
 __global__ void k_commit_reset(Ctl* c, unsigned long long pool_tail, int set_pool) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     c->scratch_tail = 0;
     c->overflow = 0;
@@ -299,6 +305,7 @@ __global__ void k_commit_reset(Ctl* c, unsigned long long pool_tail, int set_poo
 // every incident edge as an (external id) pair.
 __global__ void k_vertex_degrees(const int32_t* __restrict__ ids, long long k, const int32_t* __restrict__ perm,
                                  const int32_t* __restrict__ deg, int32_t* __restrict__ vdeg) {
+    pdl_enter();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k; i += (long long)gridDim.x * blockDim.x)
         vdeg[i] = deg[perm[ids[i]]];
 }
@@ -306,6 +313,7 @@ __global__ void k_vertex_pairs(const int32_t* __restrict__ ids, long long k, con
                                const int32_t* __restrict__ iperm, const long long* __restrict__ row_start,
                                const int32_t* __restrict__ deg, const int32_t* __restrict__ col,
                                const long long* __restrict__ off, int32_t* __restrict__ pairs) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -326,6 +334,7 @@ __global__ void k_vertex_pairs(const int32_t* __restrict__ ids, long long k, con
 // capacity row: the first insertion moves it to the pool).
 __global__ void k_init_new_vertices(int32_t* perm, int32_t* iperm, int32_t* deg, int32_t* cap, long long* row_start,
                                     int n0, int n1) {
+    pdl_enter();
     for (long long i = n0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n1;
          i += (long long)gridDim.x * blockDim.x) {
         perm[i] = (int32_t)i;
@@ -337,11 +346,13 @@ __global__ void k_init_new_vertices(int32_t* perm, int32_t* iperm, int32_t* deg,
 }
 
 __global__ void k_set_F(Ctl* c) {
+    pdl_enter();
     if (threadIdx.x < 6) c->F[threadIdx.x] = (unsigned long long)c->Ca[threadIdx.x];
     if (threadIdx.x < 2) c->F3[threadIdx.x] = (unsigned long long)c->C3a[threadIdx.x];
 }
 
 __global__ void k_mark_active(Ctl* c) {
+    pdl_enter();
     if (threadIdx.x == 0) c->active = 1;
 }
 
@@ -507,14 +518,17 @@ static int ensure_desc(gc_graph* g, long long words) {
 static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
-    k_reset_count<<<1, 32, 0, s>>>(g->ctl);
+    pdl_launch(k_reset_count, dim3(1), dim3(32), 0, s, g->ctl);
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
-    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg, 0);
+    pdl_launch(k_u_count, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
+               g->segA, g->U_deg, 0);
     g->launches += 2;
-    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
-    k_u_fill<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->segD,
+    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU,
+                                   s);
+    pdl_launch(k_u_fill, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA,
+               g->segD,
                                 g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 0);
-    k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
+    pdl_launch(k_zero_u64, dim3(grid_elems(g, (long long)g->U_col.cap)), dim3(TPB), 0, s, g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     CountArgs ca;
     ca.ctl = g->ctl;
@@ -545,7 +559,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
                                     timed ? g->ev[5] : nullptr, fin);
     if (set_F) {
-        k_set_F<<<1, 32, 0, s>>>(g->ctl);
+        pdl_launch(k_set_F, dim3(1), dim3(32), 0, s, g->ctl);
         g->launches++;
     }
     if (timed) CK(record_stage(g->ev[6], s));
@@ -558,15 +572,18 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
 static int count_local(gc_graph* g, int commit, bool timed, bool t2) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
-    k_reset_count<<<1, 32, 0, s>>>(g->ctl);
+    pdl_launch(k_reset_count, dim3(1), dim3(32), 0, s, g->ctl);
     if (t2) CK(cudaMemsetAsync(g->visited2, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
-    k_u_count<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA, g->U_deg, 1);
+    pdl_launch(k_u_count, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
+               g->segA, g->U_deg, 1);
     g->launches += 2;
-    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU, s);
-    k_u_fill_all<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->row_start, g->deg, g->col, g->segA, g->segD, g->dstA.p,
+    g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU,
+                                   s);
+    pdl_launch(k_u_fill_all, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->row_start, g->deg, g->col, g->segA,
+               g->segD, g->dstA.p,
                                     g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
-    k_zero_u64<<<grid_elems(g, (long long)g->U_col.cap), TPB, 0, s>>>(g->tpack.p, &g->ctl->nU);
+    pdl_launch(k_zero_u64, dim3(grid_elems(g, (long long)g->U_col.cap)), dim3(TPB), 0, s, g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     LocalArgs la;
     la.ctl = g->ctl;
@@ -615,14 +632,15 @@ static int count_local(gc_graph* g, int commit, bool timed, bool t2) {
 static int enqueue_commit(gc_graph* g) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
-    k_commit_plan<<<grid_elems(g, std::max<long long>(g->keys.cap, 1)), TPB, 0, s>>>(
-        g->ctl, g->wlist, g->segA, g->segD, g->deg, g->cap, g->row_start, g->col_capacity, g->slack,
+    pdl_launch(k_commit_plan, dim3(grid_elems(g, std::max<long long>(g->keys.cap, 1))), dim3(TPB), 0, s, g->ctl,
+               g->wlist, g->segA, g->segD, g->deg, g->cap, g->row_start, g->col_capacity, g->slack,
         g->plan_dst.p, g->plan_cap.p, g->plan_deg.p, g->plan_scr.p);
     // the region adjacency buffer is free again and is large enough for every
     // rewritten row: use it as the merge scratch
-    k_commit_merge<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->segA, g->segD, g->dstA.p, g->dstD.p, g->deg, g->row_start,
+    pdl_launch(k_commit_merge, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->segA, g->segD, g->dstA.p, g->dstD.p,
+               g->deg, g->row_start,
                                       g->col, g->plan_scr.p, g->U_col.p);
-    k_commit_write<<<gw, TPB, 0, s>>>(g->ctl, g->wlist, g->plan_dst.p, g->plan_cap.p, g->plan_deg.p,
+    pdl_launch(k_commit_write, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->plan_dst.p, g->plan_cap.p, g->plan_deg.p,
                                       g->plan_scr.p, g->U_col.p, g->deg, g->cap, g->row_start, g->col);
     g->launches += 3;
     CKL();
@@ -632,11 +650,11 @@ static int enqueue_commit(gc_graph* g) {
 static int enqueue_segments(gc_graph* g, bool clear) {
     int ge = grid_elems(g, std::max<long long>(g->keys.cap, 1));
     if (clear) {
-        k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
-        k_batch_clear_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+        pdl_launch(k_batch_clear_segments, dim3(ge), dim3(TPB), 0, g->s, g->srcA.p, &g->ctl->nA2, g->segA);
+        pdl_launch(k_batch_clear_segments, dim3(ge), dim3(TPB), 0, g->s, g->srcD.p, &g->ctl->nD2, g->segD);
     } else {
-        k_batch_segments<<<ge, TPB, 0, g->s>>>(g->srcA.p, &g->ctl->nA2, g->segA);
-        k_batch_segments<<<ge, TPB, 0, g->s>>>(g->srcD.p, &g->ctl->nD2, g->segD);
+        pdl_launch(k_batch_segments, dim3(ge), dim3(TPB), 0, g->s, g->srcA.p, &g->ctl->nA2, g->segA);
+        pdl_launch(k_batch_segments, dim3(ge), dim3(TPB), 0, g->s, g->srcD.p, &g->ctl->nD2, g->segD);
     }
     g->launches += 2;
     CKL();
@@ -654,22 +672,24 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
                          bool t2 = false) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
-    k_begin_batch<<<1, 32, 0, s>>>(g->ctl, g->desc);
+    pdl_launch(k_begin_batch, dim3(1), dim3(32), 0, s, g->ctl, g->desc);
     g->launches++;
     const long long nkb = std::max<long long>(max_nk, 1);
     const int ge = grid_elems(g, nkb);
     if (max_nk > 0) {
-        k_batch_keys<<<grid_elems(g, nkb / 2), TPB, 0, s>>>(g->ctl, g->perm, g->n, g->S, g->keys.p);
+        pdl_launch(k_batch_keys, dim3(grid_elems(g, nkb / 2)), dim3(TPB), 0, s, g->ctl, g->perm, g->n, g->S, g->keys.p);
         g->launches++;
         g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nkb, 2 * g->S + 1, g->hist.p,
                                       radix_grid(nkb, g->sms), s);
-        k_batch_decide<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col, g->keepA.p,
+        pdl_launch(k_batch_decide, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col,
+                   g->keepA.p,
                                           g->keepD.p);
         g->launches++;
         int sg = scan_grid(nkb, g->sms);
         g->launches += scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
         g->launches += scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
-        k_batch_compact<<<ge, TPB, 0, s>>>(g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p, g->posA.p, g->posD.p,
+        pdl_launch(k_batch_compact, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p,
+                   g->posA.p, g->posD.p,
                                            g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
         g->launches++;
         int rc = enqueue_segments(g, false);
@@ -677,12 +697,13 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     }
     if (timed) CK(record_stage(g->ev[1], s));
     CK(cudaMemsetAsync(g->visited, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
-    k_bfs_sources<<<ge, TPB, 0, s>>>(g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
-    k_level_mark<<<1, 1, 0, s>>>(g->ctl, 0);
+    pdl_launch(k_bfs_sources, dim3(ge), dim3(TPB), 0, s, g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
+    pdl_launch(k_level_mark, dim3(1), dim3(1), 0, s, g->ctl, 0);
     g->launches += 2;
     for (int L = 1; L <= (local ? 0 : g->hops); L++) {
-        k_bfs_expand<<<grid_warps(g), TPB, 0, s>>>(g->ctl, L, g->row_start, g->deg, g->col, g->visited, g->wlist);
-        k_level_mark<<<1, 1, 0, s>>>(g->ctl, L);
+        pdl_launch(k_bfs_expand, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, L, g->row_start, g->deg, g->col,
+                   g->visited, g->wlist);
+        pdl_launch(k_level_mark, dim3(1), dim3(1), 0, s, g->ctl, L);
         g->launches += 2;
     }
     CKL();
@@ -692,8 +713,9 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     if (!local && commit && t2) {
         // keep the triangle sums of the edge-local path
         CK(cudaMemsetAsync(g->visited2, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
-        k_t2_mark<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->visited2, g->T2);
-        k_t2_from_region<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split,
+        pdl_launch(k_t2_mark, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited2, g->T2);
+        pdl_launch(k_t2_from_region, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, g->wlist, g->U_off, g->U_col.p,
+                   g->U_split,
                                                        g->tpack.p, g->visited2, g->T2);
         g->launches += 2;
         CKL();
@@ -707,7 +729,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
         rc = enqueue_segments(g, true);
         if (rc) return rc;
     }
-    k_end_batch<<<1, 32, 0, s>>>(g->ctl, g->out_dev.p, commit ? 1 : 0);
+    pdl_launch(k_end_batch, dim3(1), dim3(32), 0, s, g->ctl, g->out_dev.p, commit ? 1 : 0);
     g->launches++;
     CKL();
     return GC_OK;
@@ -720,7 +742,7 @@ static int relayout(gc_graph* g, long long pool_extra) {
     int n = g->n;
     long long* new_start = (long long*)dalloc(g, sizeof(long long) * (size_t)(n + 1));
     if (!new_start) return nomem(g, "row offsets");
-    k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
+    pdl_launch(k_slack_caps, dim3(grid_elems(g, n)), dim3(TPB), 0, s, g->deg, n, g->slack, g->cap);
     scan_i32_to_i64(g->cap, new_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
     long long total = 0;
     CK(cudaMemcpyAsync(&total, new_start + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -732,8 +754,8 @@ static int relayout(gc_graph* g, long long pool_extra) {
         dfree(g, new_start);
         return nomem(g, "adjacency pool");
     }
-    k_copy_rows<<<grid_warps(g), TPB, 0, s>>>(g->deg, n, g->row_start, g->col, new_start, ncol);
-    k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
+    pdl_launch(k_copy_rows, dim3(grid_warps(g)), dim3(TPB), 0, s, g->deg, n, g->row_start, g->col, new_start, ncol);
+    pdl_launch(k_commit_reset, dim3(1), dim3(32), 0, s, g->ctl, (unsigned long long)total, 1);
     CKL();
     dfree(g, g->col);
     dfree(g, g->row_start);
@@ -760,8 +782,8 @@ static int finish_pending_commit(gc_graph* g, int* relayouts) {
         int rc = relayout(g, extra);
         if (rc) return rc;
         (*relayouts)++;
-        k_resume_pending<<<1, 32, 0, g->s>>>(g->ctl);
-        k_halt_clear<<<1, 32, 0, g->s>>>(g->ctl);
+        pdl_launch(k_resume_pending, dim3(1), dim3(32), 0, g->s, g->ctl);
+        pdl_launch(k_halt_clear, dim3(1), dim3(32), 0, g->s, g->ctl);
         CKL();
         rc = enqueue_segments(g, false);
         if (rc) return rc;
@@ -777,7 +799,7 @@ static int finish_pending_commit(gc_graph* g, int* relayouts) {
     }
     int rc = enqueue_segments(g, true);
     if (rc) return rc;
-    k_halt_clear<<<1, 32, 0, g->s>>>(g->ctl);
+    pdl_launch(k_halt_clear, dim3(1), dim3(32), 0, g->s, g->ctl);
     CKL();
     return read_ctl(g);
 }
@@ -914,7 +936,7 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         g->h_desc[4] = 0;
         g->h_desc[5] = n_del;
         CK(cudaMemcpyAsync(g->desc, g->h_desc, 6 * sizeof(long long), cudaMemcpyHostToDevice, s));
-        k_run_reset<<<1, 32, 0, s>>>(g->ctl);
+        pdl_launch(k_run_reset, dim3(1), dim3(32), 0, s, g->ctl);
         CKL();
         g->launches = *ex_launches + 1;
         CK(cudaEventRecord(g->e0, s));
@@ -1022,7 +1044,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     g->h_desc[1] = (long long)d_del;
     std::memcpy(g->h_desc + 2, h_batches, sizeof(long long) * 4 * (size_t)k);
     CK(cudaMemcpyAsync(g->desc, g->h_desc, sizeof(long long) * (2 + 4 * (size_t)k), cudaMemcpyHostToDevice, s));
-    k_run_reset<<<1, 32, 0, s>>>(g->ctl);
+    pdl_launch(k_run_reset, dim3(1), dim3(32), 0, s, g->ctl);
     CKL();
     // (re)capture the per-batch graph when its shape or any buffer changed
     if (!g->gexec || g->g_nk != shape_nk || g->g_commit != (int)commit || g->g_gen != g->buf_gen ||
@@ -1087,8 +1109,8 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
     if (rc) return rc;
     g->launches = 0;
     CK(cudaMemsetAsync(g->visited, 0xFF, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
-    k_region_all<<<grid_elems(g, g->n), TPB, 0, s>>>(g->ctl, g->n, g->wlist);
-    k_mark_active<<<1, 32, 0, s>>>(g->ctl);
+    pdl_launch(k_region_all, dim3(grid_elems(g, g->n)), dim3(TPB), 0, s, g->ctl, g->n, g->wlist);
+    pdl_launch(k_mark_active, dim3(1), dim3(32), 0, s, g->ctl);
     g->launches += 2;
     CKL();
     CK(cudaEventRecord(g->ev[2], s));
@@ -1096,7 +1118,8 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
     if (rc) return rc;
     // the static pass also gives the triangle sums of the edge-local path
     CK(cudaMemsetAsync(g->T2, 0, 8 * (size_t)std::max(g->n, 1), s));
-    k_t2_from_static<<<grid_warps(g), TPB, 0, s>>>(g->ctl, g->wlist, g->U_off, g->U_col.p, g->U_split, g->tpack.p,
+    pdl_launch(k_t2_from_static, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, g->wlist, g->U_off, g->U_col.p,
+               g->U_split, g->tpack.p,
                                                    g->T2);
     g->launches++;
     CKL();
@@ -1254,17 +1277,18 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
         if (cudaMemcpyAsync(g->desc + 8, g->h_desc + 8, 2 * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) { rc = GC_ECUDA; break; }
         if (n > 0) {
-            k_degree_keys<<<grid_elems(g, n), TPB, 0, s>>>(d_rp, n, deg0, k1);
+            pdl_launch(k_degree_keys, dim3(grid_elems(g, n)), dim3(TPB), 0, s, d_rp, n, deg0, k1);
             radix_sort_u64(k1, k2, g->desc + 8, n, 32 + bitlen(maxdeg), g->hist.p, radix_grid(n, g->sms), s);
-            k_perm_from_keys<<<grid_elems(g, n), TPB, 0, s>>>(k1, n, g->perm, g->iperm, deg0, g->deg);
+            pdl_launch(k_perm_from_keys, dim3(grid_elems(g, n)), dim3(TPB), 0, s, k1, n, g->perm, g->iperm, deg0,
+                       g->deg);
         }
         if (m2 > 0) {
-            k_edge_keys<<<grid_warps(g), TPB, 0, s>>>(d_rp, d_col, n, g->perm, g->S, k1, bad);
+            pdl_launch(k_edge_keys, dim3(grid_warps(g)), dim3(TPB), 0, s, d_rp, d_col, n, g->perm, g->S, k1, bad);
             radix_sort_u64(k1, k2, g->desc + 9, m2, 2 * g->S, g->hist.p, rg, s);
         }
         if (n > 0) {
             scan_i32_to_i64(g->deg, key_off, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
-            k_slack_caps<<<grid_elems(g, n), TPB, 0, s>>>(g->deg, n, g->slack, g->cap);
+            pdl_launch(k_slack_caps, dim3(grid_elems(g, n)), dim3(TPB), 0, s, g->deg, n, g->slack, g->cap);
             scan_i32_to_i64(g->cap, g->row_start, nullptr, n, g->bsum.p, scan_grid(n, g->sms), nullptr, s);
         }
         long long total = 0;
@@ -1286,8 +1310,9 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
             break;
         }
         if (m2 > 0)
-            k_fill_from_keys<<<grid_elems(g, m2), TPB, 0, s>>>(k1, m2, n, g->S, key_off, g->row_start, g->col, bad);
-        k_commit_reset<<<1, 32, 0, s>>>(g->ctl, (unsigned long long)total, 1);
+            pdl_launch(k_fill_from_keys, dim3(grid_elems(g, m2)), dim3(TPB), 0, s, k1, m2, n, g->S, key_off,
+                       g->row_start, g->col, bad);
+        pdl_launch(k_commit_reset, dim3(1), dim3(32), 0, s, g->ctl, (unsigned long long)total, 1);
         int hbad = 0;
         if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1687,7 +1712,8 @@ static int grow_vertices(gc_graph* g, long long k) {
               grow((void**)&g->U_deg, 4, nn, 0, false) && grow((void**)&g->U_split, 4, nn, 0, false) &&
               grow((void**)&g->da, 4, nn, 0, false) && grow((void**)&g->db, 4, nn, 0, false) &&
               grow((void**)&g->U_off, 8, nn + 1, 0, false) && grow((void**)&g->U_wt, 8, nn, 0, false) &&
-              grow((void**)&g->segA, sizeof(int2), nn, 0, false) && grow((void**)&g->segD, sizeof(int2), nn, 0, false) &&
+              grow((void**)&g->segA, sizeof(int2), nn, 0, false) && grow((void**)&g->segD, sizeof(int2), nn, 0,
+                   false) &&
               grow((void**)&g->visited, 4, (nn + 31) / 32 + 1, 0, false) &&
               grow((void**)&g->visited2, 4, (nn + 31) / 32 + 1, 0, false) &&
               grow((void**)&g->T2, 8, nn, old_nn, true) && grow((void**)&g->dtri2, 8, nn, 0, false) &&
@@ -1701,7 +1727,8 @@ static int grow_vertices(gc_graph* g, long long k) {
         const size_t kept = n0 > 0 ? (size_t)n0 : 0;
         CK(cudaMemsetAsync(g->T2 + kept, 0, 8 * (nn - kept), s));
     }
-    k_init_new_vertices<<<grid_elems(g, k), TPB, 0, s>>>(g->perm, g->iperm, g->deg, g->cap, g->row_start, n0, n1);
+    pdl_launch(k_init_new_vertices, dim3(grid_elems(g, k)), dim3(TPB), 0, s, g->perm, g->iperm, g->deg, g->cap,
+               g->row_start, n0, n1);
     CKL();
     release(g, g->dense);
     if (!ensure(g, g->dense, (size_t)g->dense_clusters * (nn + 1))) return nomem(g, "4-cycle counter arrays");
@@ -1770,7 +1797,7 @@ int gc_delete_vertices(gc_graph* g, const int32_t* ids, int64_t k, uint64_t out[
     long long total = 0;
     if (k > 0) {
         CK(cudaMemcpyAsync(g->vids.p, ids, 4 * (size_t)k, cudaMemcpyHostToDevice, s));
-        k_vertex_degrees<<<grid_elems(g, k), TPB, 0, s>>>(g->vids.p, k, g->perm, g->deg, g->vdeg.p);
+        pdl_launch(k_vertex_degrees, dim3(grid_elems(g, k)), dim3(TPB), 0, s, g->vids.p, k, g->perm, g->deg, g->vdeg.p);
         CKL();
         scan_i32_to_i64(g->vdeg.p, g->voff.p, nullptr, k, g->bsum.p, scan_grid(k, g->sms), nullptr, s);
         CK(cudaMemcpyAsync(&total, g->voff.p + k, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -1778,7 +1805,8 @@ int gc_delete_vertices(gc_graph* g, const int32_t* ids, int64_t k, uint64_t out[
     }
     if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(total, 1))) return nomem(g, "vertex edges");
     if (total > 0) {
-        k_vertex_pairs<<<grid_warps(g), TPB, 0, s>>>(g->vids.p, k, g->perm, g->iperm, g->row_start, g->deg, g->col,
+        pdl_launch(k_vertex_pairs, dim3(grid_warps(g)), dim3(TPB), 0, s, g->vids.p, k, g->perm, g->iperm, g->row_start,
+                   g->deg, g->col,
                                                      g->voff.p, g->pairs.p);
         CKL();
     }
@@ -2007,6 +2035,7 @@ static int time_static(gc_graph* g, int reps, float* ms, uint64_t out[6]) {
 __global__ void k_sample_edges(const long long* __restrict__ cum, int n, const long long* __restrict__ row_start,
                                const int32_t* __restrict__ col, const int32_t* __restrict__ iperm,
                                unsigned long long seed, int k, int32_t* __restrict__ pairs) {
+    pdl_enter();
     const long long m2 = cum[n];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
         unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
@@ -2041,7 +2070,8 @@ static int calibrate_local(gc_graph* g, int reps) {
     g->launches += scan_i32_to_i64(g->deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), nullptr, s);
     long long thr = 0;
     for (long long k = 8; k <= kmax; k *= 4) {
-        k_sample_edges<<<grid_elems(g, k), TPB, 0, s>>>(g->U_off, g->n, g->row_start, g->col, g->iperm,
+        pdl_launch(k_sample_edges, dim3(grid_elems(g, k)), dim3(TPB), 0, s, g->U_off, g->n, g->row_start, g->col,
+                   g->iperm,
                                                         0x5DEECE66Dull + (unsigned long long)k, (int)k, g->pairs.p);
         CKL();
         float best[2] = {1e30f, 1e30f};

@@ -16,6 +16,7 @@
 namespace gcx {
 
 __global__ void k_batch_keys(Ctl* c, const int32_t* __restrict__ perm, int n, int S, uint64_t* __restrict__ keys) {
+    pdl_enter();
     long long ni = c->n_ins, nd = c->n_del, tot = ni + nd;
     const int32_t* ins = c->pairs_ins + 2 * c->ins_off;
     const int32_t* del = c->pairs_del + 2 * c->del_off;
@@ -40,6 +41,7 @@ __global__ void k_batch_decide(const uint64_t* __restrict__ keys, Ctl* c, int S,
                                const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
                                const int32_t* __restrict__ col, int32_t* __restrict__ keepA,
                                int32_t* __restrict__ keepD) {
+    pdl_enter();
     long long nk = c->nkeys;
     const uint64_t idmask = (1ull << S) - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nk;
@@ -80,6 +82,7 @@ __global__ void k_batch_compact(const uint64_t* __restrict__ keys, const Ctl* c,
                                 const long long* __restrict__ posA, const long long* __restrict__ posD,
                                 int32_t* __restrict__ srcA, int32_t* __restrict__ dstA,
                                 int32_t* __restrict__ srcD, int32_t* __restrict__ dstD) {
+    pdl_enter();
     long long nk = c->nkeys;
     const uint64_t idmask = (1ull << S) - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nk;
@@ -99,6 +102,7 @@ __global__ void k_batch_compact(const uint64_t* __restrict__ keys, const Ctl* c,
 
 // seg[src] = [first, last+1) of src's run in the kept, sorted entry list
 __global__ void k_batch_segments(const int32_t* __restrict__ src, const long long* d_len, int2* __restrict__ seg) {
+    pdl_enter();
     long long n = *d_len;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
@@ -113,6 +117,7 @@ __global__ void k_batch_segments(const int32_t* __restrict__ src, const long lon
 
 __global__ void k_batch_clear_segments(const int32_t* __restrict__ src, const long long* d_len,
                                        int2* __restrict__ seg) {
+    pdl_enter();
     long long n = *d_len;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x)
@@ -127,6 +132,7 @@ __global__ void k_commit_plan(Ctl* c, const int32_t* __restrict__ wlist, const i
                               long long col_capacity, float slack, long long* __restrict__ plan_dst,
                               int32_t* __restrict__ plan_cap, int32_t* __restrict__ plan_deg,
                               long long* __restrict__ plan_scr) {
+    pdl_enter();
     if (c->err || c->lovf) return;
     int ns = c->lvl[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
@@ -167,6 +173,7 @@ __global__ void k_commit_merge(const Ctl* c, const int32_t* __restrict__ wlist, 
                                const int32_t* __restrict__ dstD, const int32_t* __restrict__ deg,
                                const long long* __restrict__ row_start, const int32_t* __restrict__ col,
                                const long long* __restrict__ plan_scr, uint32_t* __restrict__ scratch) {
+    pdl_enter();
     if (c->err || c->overflow || c->lovf) return;
     const int ns = c->lvl[0];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -195,6 +202,7 @@ __global__ void k_commit_write(const Ctl* c, const int32_t* __restrict__ wlist, 
                                const long long* __restrict__ plan_scr, const uint32_t* __restrict__ scratch,
                                int32_t* __restrict__ deg, int32_t* __restrict__ cap,
                                long long* __restrict__ row_start, int32_t* __restrict__ col) {
+    pdl_enter();
     if (c->err || c->overflow || c->lovf) return;
     const int ns = c->lvl[0];
     const int lane = threadIdx.x & 31;
@@ -229,6 +237,7 @@ __global__ void k_commit_write(const Ctl* c, const int32_t* __restrict__ wlist, 
 // ---- layout ---------------------------------------------------------------
 
 __global__ void k_slack_caps(const int32_t* __restrict__ deg, int n, float slack, int32_t* __restrict__ cap) {
+    pdl_enter();
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int d = deg[v];
         int extra = (int)ceilf(slack * (float)d);
@@ -240,6 +249,7 @@ __global__ void k_slack_caps(const int32_t* __restrict__ deg, int n, float slack
 __global__ void k_copy_rows(const int32_t* __restrict__ deg, int n, const long long* __restrict__ old_start,
                             const int32_t* __restrict__ old_col, const long long* __restrict__ new_start,
                             int32_t* __restrict__ new_col) {
+    pdl_enter();
     int lane = threadIdx.x & 31;
     long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -254,6 +264,7 @@ __global__ void k_copy_rows(const int32_t* __restrict__ deg, int n, const long l
 
 __global__ void k_degree_keys(const int32_t* __restrict__ rp, int n, int32_t* __restrict__ deg0,
                               uint64_t* __restrict__ keys) {
+    pdl_enter();
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int d = rp[v + 1] - rp[v];
         deg0[v] = d;
@@ -264,6 +275,7 @@ __global__ void k_degree_keys(const int32_t* __restrict__ rp, int n, int32_t* __
 __global__ void k_perm_from_keys(const uint64_t* __restrict__ keys, int n, int32_t* __restrict__ perm,
                                  int32_t* __restrict__ iperm, const int32_t* __restrict__ deg0,
                                  int32_t* __restrict__ deg) {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t v = (int32_t)(keys[i] & 0xFFFFFFFFu);
         iperm[i] = v;
@@ -275,6 +287,7 @@ __global__ void k_perm_from_keys(const uint64_t* __restrict__ keys, int n, int32
 __global__ void k_edge_keys(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int n,
                             const int32_t* __restrict__ perm, int S, uint64_t* __restrict__ keys,
                             int* __restrict__ bad) {
+    pdl_enter();
     int lane = threadIdx.x & 31;
     long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -297,6 +310,7 @@ __global__ void k_edge_keys(const int32_t* __restrict__ rp, const int32_t* __res
 __global__ void k_fill_from_keys(const uint64_t* __restrict__ keys, long long m2, int n, int S,
                                  const long long* __restrict__ key_off, const long long* __restrict__ row_start,
                                  int32_t* __restrict__ col, int* __restrict__ bad) {
+    pdl_enter();
     const uint64_t idmask = (1ull << S) - 1;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m2;
          p += (long long)gridDim.x * blockDim.x) {
@@ -331,6 +345,7 @@ __global__ void k_export_rows(const int32_t* __restrict__ deg, int n, const long
                               const int32_t* __restrict__ col, const int32_t* __restrict__ perm,
                               const long long* __restrict__ out_off_ext, const int32_t* __restrict__ iperm,
                               int32_t* __restrict__ out_col) {
+    pdl_enter();
     // warp per internal vertex i: external id x = iperm[i]; writes external
     // neighbour ids (unsorted; sorted on the host)
     int lane = threadIdx.x & 31;
@@ -347,6 +362,7 @@ __global__ void k_export_rows(const int32_t* __restrict__ deg, int n, const long
 
 __global__ void k_ext_degrees(const int32_t* __restrict__ deg, const int32_t* __restrict__ iperm, int n,
                               int32_t* __restrict__ ext_deg) {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ext_deg[iperm[i]] = deg[i];
 }
 

@@ -51,6 +51,7 @@ namespace cg = cooperative_groups;
 namespace gcx {
 
 __global__ void k_reset_count(Ctl* c) {
+    pdl_enter();
     int t = threadIdx.x;
     if (t < NACC) c->acc[t] = 0;
     for (int i = t; i < NACC * ACC_STRIPES; i += blockDim.x) (&c->accs[0][0])[i] = 0;
@@ -60,6 +61,7 @@ __global__ void k_reset_count(Ctl* c) {
 }
 
 __global__ void k_zero_u64(unsigned long long* __restrict__ a, const long long* d_len) {
+    pdl_enter();
     long long n = *d_len;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] = 0;
@@ -113,6 +115,7 @@ __device__ __forceinline__ int find_seg(const int* pre, int k, int t) {
 __global__ void k_wedge_bound(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                               const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                               long long* __restrict__ U_wt) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -139,6 +142,7 @@ __global__ void k_wedge_bound(const Ctl* c, const int32_t* __restrict__ wlist, c
 __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                       const int32_t* __restrict__ U_split, const long long* __restrict__ U_wt,
                       int32_t* __restrict__ bins, int n, Tuning t) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(TW * 32) k_tri_warp(Ctl* c, const int32_t* __r
                                                      const uint32_t* __restrict__ U_col,
                                                      const int32_t* __restrict__ U_split,
                                                      unsigned long long* __restrict__ tpack) {
+    pdl_enter();
     __shared__ uint32_t sX[TW][32];
     __shared__ long long sNb[TW][32];
     __shared__ int sPre[TW][33];
@@ -280,6 +285,7 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
                                                   const uint32_t* __restrict__ U_col,
                                                   const int32_t* __restrict__ U_split,
                                                   unsigned long long* __restrict__ tpack) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     long long* sNb = (long long*)smem;
     unsigned long long* sTq = (unsigned long long*)(smem + (size_t)KM * 8);
@@ -383,6 +389,7 @@ __global__ void __launch_bounds__(256) k_tri_block(Ctl* c, const int32_t* __rest
 __global__ void k_tri_merge(Ctl* c, const int32_t* __restrict__ list, const long long* __restrict__ U_off,
                             const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                             unsigned long long* __restrict__ tpack) {
+    pdl_enter();
     const int cnt = c->nbin[BIN_TRI_MERGE];
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -476,6 +483,7 @@ __global__ void __launch_bounds__(256) k_c4_reg(Ctl* c, const int32_t* __restric
                                                const long long* __restrict__ U_off,
                                                const uint32_t* __restrict__ U_col,
                                                const int32_t* __restrict__ U_split) {
+    pdl_enter();
     __shared__ long long sVb[8][32];
     __shared__ uint32_t sFv[8][32];
     __shared__ int sPre[8][33];
@@ -560,6 +568,7 @@ __global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_
                                                           const long long* __restrict__ U_off,
                                                           const uint32_t* __restrict__ U_col,
                                                           const int32_t* __restrict__ U_split) {
+    pdl_enter();
     __shared__ uint32_t sKey[C4W_WARPS][C4W_SLOTS];
     __shared__ uint32_t sCnt[C4W_WARPS][C4W_SLOTS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -607,6 +616,7 @@ __global__ void __launch_bounds__(256, 4) k_c4_block(Ctl* c, const int32_t* __re
                                                  const long long* __restrict__ U_off,
                                                  const uint32_t* __restrict__ U_col,
                                                  const int32_t* __restrict__ U_split) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* keys = (uint32_t*)smem;
     uint32_t* cnts = keys + C4B_SLOTS;
@@ -747,6 +757,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                                                                 const int32_t* __restrict__ U_split,
                                                                 const long long* __restrict__ U_wt,
                                                                 unsigned long long* __restrict__ arrays, int n) {
+    pdl_enter();
     int rank = 0, ncta = 1;
     if constexpr (CLUSTER) {
         cg::cluster_group cl = cg::this_cluster();
@@ -932,6 +943,7 @@ long long c4_chunk_table_entries(long long n) {
 // straddle b * CH_R; chunks after the last entry start at the row's end.
 __global__ void k_chunk_bounds(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                                const uint32_t* __restrict__ U_col, int32_t* __restrict__ T, int TW) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1028,6 +1040,7 @@ __global__ void __launch_bounds__(CH_THREADS, 1) k_c4_chunk(Ctl* c, const int32_
                                                         const uint32_t* __restrict__ U_col,
                                                         const int32_t* __restrict__ U_split,
                                                         const int32_t* __restrict__ T, int TW) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char ch_smem[];
     int* w_pre = (int*)(ch_smem + CH_BYTES);
     long long* w_vb = (long long*)(w_pre + CH_THREADS);
@@ -1102,6 +1115,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
                                                              const int32_t* __restrict__ U_split,
                                                              unsigned long long* __restrict__ tables,
                                                              long long table_words) {
+    pdl_enter();
     unsigned long long* tab = tables + (size_t)blockIdx.x * (size_t)table_words;
     __shared__ int s_idx, s_tot;
     __shared__ unsigned long long s_wt;
@@ -1195,6 +1209,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
                              const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                              const unsigned long long* __restrict__ tpack, const int32_t* __restrict__ da,
                              const int32_t* __restrict__ db) {
+    pdl_enter();
     int nW = c->nW;
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1259,6 +1274,7 @@ __global__ void k_edge_terms(Ctl* c, const int32_t* __restrict__ wlist, const lo
 
 // mode 0: batch (F += C_a - C_b unless the batch was rejected); 1: static
 __global__ void k_finalize(Ctl* c, int mode) {
+    pdl_enter();
     // fold the striped accumulators (one warp: lane i sums slot i's copies
     // and slot i + 16's if any)
     if (blockIdx.x == 0 && threadIdx.x < NACC) {
@@ -1382,8 +1398,8 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     long long nw = a.n_alloc > 0 ? a.n_alloc : 1;
     int gb = (int)std::min<long long>((nw + 255) / 256, 8LL * sms);
     const Tuning t = effective_tuning(a);
-    k_wedge_bound<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
-    k_bin<<<gb, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
+    pdl_launch(k_wedge_bound, dim3(8 * sms), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
+    pdl_launch(k_bin, dim3(gb), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
     nl += 2;
     // The triangle kernels and the 4-cycle tiers are independent: with
     // auxiliary streams they run side by side (a fork after the binning, a
@@ -1433,8 +1449,8 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                                                                     a.U_split, a.chunk_table, TW);
         nl += 2;
     }
-    k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
-                                                        a.cta_tables, a.cta_table_words);
+    pdl_launch(k_c4_hash, dim3(a.cta_groups), dim3(C4_DENSE_THREADS), 0, s, a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col,
+               a.U_split, a.cta_tables, a.cta_table_words);
     nl += 5;
     if (par) {
         cudaEventRecord(a.join[1], sC1);
@@ -1447,8 +1463,9 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
         cudaEventRecord(a.join[0], sT);
         cudaStreamWaitEvent(s, a.join[0], 0);
     }
-    k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
-    k_finalize<<<1, 32, 0, s>>>(a.ctl, mode);
+    pdl_launch(k_edge_terms, dim3(8 * sms), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da,
+               a.db);
+    pdl_launch(k_finalize, dim3(1), dim3(32), 0, s, a.ctl, mode);
     nl += 2;
     return nl;
 }

@@ -143,6 +143,33 @@ inline cudaError_t record_stage(cudaEvent_t e, cudaStream_t s) {
 
 __device__ __forceinline__ uint32_t vid(uint32_t e) { return e & ID_MASK; }
 
+// Programmatic dependent launch: a kernel launched by pdl_launch may be
+// scheduled while the kernel before it in the stream is still running;
+// it waits here (first statement) until that kernel has finished and its
+// writes are visible, then lets the next kernel be scheduled in turn.  The
+// launch latency of a chain of small kernels is hidden this way.  Without
+// a programmatic dependency both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));

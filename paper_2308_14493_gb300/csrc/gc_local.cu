@@ -199,6 +199,7 @@ __device__ __forceinline__ uint32_t t_flags(unsigned long long r, int at) {
 // After the union rows: the entry and pair-slot scans run only if their
 // arrays fit.
 __global__ void k_loc_check_rows(Ctl* c, long long cap) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const long long np = c->nA2 + c->nD2;
     c->l_np = np;
@@ -214,6 +215,7 @@ __global__ void k_loc_check_rows(Ctl* c, long long cap) {
 
 // After the pair scans: common-neighbour records and 4-cycle tasks.
 __global__ void k_loc_check_pairs(Ctl* c, long long cap) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const bool ovf = c->l_tot[1] > cap || c->l_tot[3] > cap;
     if (ovf) {
@@ -235,6 +237,7 @@ __global__ void k_loc_check_pairs(Ctl* c, long long cap) {
 // warp per vertex of V_X; a hub row is a long run of coalesced stores).
 __global__ void k_loc_owner(const Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
                             int32_t* __restrict__ own) {
+    pdl_enter();
     const int nX = c->l_len[0] ? c->lvl[0] : 0;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -250,6 +253,7 @@ __global__ void k_loc_owner(const Ctl* c, const int32_t* __restrict__ wlist, Loc
 // with both endpoints in V_X is taken from its lower endpoint only.
 __global__ void k_loc_tri_cost(const Ctl* c, LocalView V, const int32_t* __restrict__ own,
                                int32_t* __restrict__ cost) {
+    pdl_enter();
     const long long tot = c->l_len[0];
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
@@ -265,6 +269,7 @@ __global__ void k_loc_tri_cost(const Ctl* c, LocalView V, const int32_t* __restr
 // bits G_a, low 32 G_b).
 __global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict__ pre,
                           const int32_t* __restrict__ own, unsigned long long* __restrict__ tpack) {
+    pdl_enter();
     const long long n = c->l_len[0];
     if (n == 0) return;
     const long long tot = pre[n];
@@ -301,6 +306,7 @@ __global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict
 __global__ void k_loc_terms(Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
                             const int32_t* __restrict__ own, const unsigned long long* __restrict__ tpack,
                             const int32_t* __restrict__ da, const int32_t* __restrict__ db) {
+    pdl_enter();
     const long long tot = c->l_len[0];
     const int nX = tot ? c->lvl[0] : 0;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -359,6 +365,7 @@ __global__ void k_loc_pair_cost(const Ctl* c, LocalView V, const int32_t* __rest
                                 const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                                 const int32_t* __restrict__ dstD, int32_t* __restrict__ pcost,
                                 int32_t* __restrict__ ccnt, int32_t* __restrict__ walk) {
+    pdl_enter();
     // a warp per pair slot: the 4-cycle probes of walking either endpoint,
     // sum over its neighbours w of min(|N(w)|, |other row|)
     const long long np = c->l_len[1];
@@ -393,6 +400,7 @@ __global__ void k_loc_common(const Ctl* c, LocalView V, const int32_t* __restric
                              const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                              const int32_t* __restrict__ dstD, const long long* __restrict__ ppre,
                              unsigned long long* __restrict__ rec) {
+    pdl_enter();
     const long long np = c->l_len[1];
     const long long tot = c->l_len[2];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -432,6 +440,7 @@ __global__ void k_loc_k4_cost(const Ctl* c, LocalView V, const int32_t* __restri
                               const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                               const int32_t* __restrict__ dstD, const long long* __restrict__ ppre,
                               const unsigned long long* __restrict__ rec, int32_t* __restrict__ kcost) {
+    pdl_enter();
     const long long np = c->l_len[1];
     const long long tot = c->l_len[2];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -459,6 +468,7 @@ __global__ void k_loc_k4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
                          const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
                          const long long* __restrict__ ppre, const unsigned long long* __restrict__ rec,
                          const long long* __restrict__ kpre) {
+    pdl_enter();
     const long long np = c->l_len[1];
     const long long n = c->l_len[2];
     const long long tot = n ? kpre[n] : 0;
@@ -539,6 +549,7 @@ __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restr
                                const int32_t* __restrict__ dstD, const long long* __restrict__ cpre,
                                const int32_t* __restrict__ walk, int32_t* __restrict__ tpair,
                                int32_t* __restrict__ tent, int32_t* __restrict__ tcost) {
+    pdl_enter();
     const long long np = c->l_len[1];
     const long long tot = c->l_len[3];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -564,6 +575,7 @@ __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
                          const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
                          const int32_t* __restrict__ walk, const int32_t* __restrict__ tpair,
                          const int32_t* __restrict__ tent, const long long* __restrict__ tpre) {
+    pdl_enter();
     const long long n = c->l_len[3];
     const long long tot = n ? tpre[n] : 0;
     unsigned long long qa = 0, qb = 0;
@@ -615,6 +627,7 @@ __global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, 
 __global__ void k_t2_from_static(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                                  const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                                  const unsigned long long* __restrict__ tpack, unsigned long long* __restrict__ T2) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -642,6 +655,7 @@ __global__ void k_t2_from_static(const Ctl* c, const int32_t* __restrict__ wlist
 // W.  First the one-hop vertices are marked and their T2 cleared ...
 __global__ void k_t2_mark(const Ctl* c, const int32_t* __restrict__ wlist, uint32_t* __restrict__ mark,
                           unsigned long long* __restrict__ T2) {
+    pdl_enter();
     if (c->err || !c->active) return;
     const int n1 = c->lvl[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
@@ -657,6 +671,7 @@ __global__ void k_t2_from_region(const Ctl* c, const int32_t* __restrict__ wlist
                                  const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                                  const unsigned long long* __restrict__ tpack, const uint32_t* __restrict__ mark,
                                  unsigned long long* __restrict__ T2) {
+    pdl_enter();
     if (c->err || !c->active) return;
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
@@ -691,6 +706,7 @@ __global__ void k_loc_tri_delta(Ctl* c, LocalView V, const int32_t* __restrict__
                                 const unsigned long long* __restrict__ rec, long long* __restrict__ dcnt,
                                 long long* __restrict__ dtri2, uint32_t* __restrict__ visited2,
                                 int32_t* __restrict__ wlist) {
+    pdl_enter();
     const long long np = c->l_len[1];
     const long long tot = c->l_len[2];
     const int nX = c->lvl[0];
@@ -729,6 +745,7 @@ __global__ void k_loc_tri_delta(Ctl* c, LocalView V, const int32_t* __restrict__
 // Intersections only for the common edges at V_X whose t changes (their old t).
 __global__ void k_loc_dcost(const Ctl* c, LocalView V, const int32_t* __restrict__ own,
                             const long long* __restrict__ dcnt, int32_t* __restrict__ cost) {
+    pdl_enter();
     const long long tot = c->l_len[0];
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
@@ -747,6 +764,7 @@ __global__ void k_loc_dcost(const Ctl* c, LocalView V, const int32_t* __restrict
 __global__ void k_loc_eterms(Ctl* c, LocalView V, const int32_t* __restrict__ own,
                              const unsigned long long* __restrict__ tpack, const long long* __restrict__ dcnt,
                              const int32_t* __restrict__ da, const int32_t* __restrict__ db) {
+    pdl_enter();
     const long long tot = c->l_len[0];
     unsigned long long P[2] = {0, 0}, D[2] = {0, 0}, E[2] = {0, 0};
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
@@ -793,6 +811,7 @@ __global__ void k_loc_eterms(Ctl* c, LocalView V, const int32_t* __restrict__ ow
 __global__ void k_loc_vterms(Ctl* c, const int32_t* __restrict__ wlist, LocalView V,
                              unsigned long long* __restrict__ T2, long long* __restrict__ dtri2,
                              const int32_t* __restrict__ da, const int32_t* __restrict__ db, int commit) {
+    pdl_enter();
     const int nX = c->l_len[0] ? c->lvl[0] : 0;
     const int nT = nX ? nX + c->l_nw3 : 0;
     const bool apply = commit && c->err == 0 && c->active && c->lovf == 0;
@@ -829,6 +848,7 @@ __global__ void k_loc_vterms(Ctl* c, const int32_t* __restrict__ wlist, LocalVie
 // the batch).  Ca holds the six induced deltas and sa the non-induced ones
 // (Cb, sb zero).
 __global__ void k_finalize_local(Ctl* c, int commit) {
+    pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x < NACC) {
         unsigned long long x = 0;
         for (int k = 0; k < ACC_STRIPES; k++) x += c->accs[threadIdx.x][k];
@@ -878,53 +898,58 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
     const int sg = scan_grid(a.cap, sms);
     LocalView V{a.visited, a.U_off, a.U_col, a.row_start, a.deg, a.col};
     int nl = 0;
-    k_loc_check_rows<<<1, 32, 0, s>>>(a.ctl, a.cap);
+    pdl_launch(k_loc_check_rows, dim3(1), dim3(32), 0, s, a.ctl, a.cap);
     if (ev_tri) record_stage(ev_tri, s);
-    k_loc_owner<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.own);
+    pdl_launch(k_loc_owner, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, V, a.own);
     nl += 2;
     // changed pairs: common neighbours (4-cliques, triangles) and 4-cycle tasks
-    k_loc_pair_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt, a.walk);
+    pdl_launch(k_loc_pair_cost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.pcost, a.ccnt,
+               a.walk);
     nl++;
     nl += scan_i32_to_i64(a.pcost, a.ppre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[1], s);
     nl += scan_i32_to_i64(a.ccnt, a.cpre, &a.ctl->l_len[1], 0, a.bsum, sg, &a.ctl->l_tot[3], s);
-    k_loc_check_pairs<<<1, 32, 0, s>>>(a.ctl, a.cap);
-    k_loc_common<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec);
+    pdl_launch(k_loc_check_pairs, dim3(1), dim3(32), 0, s, a.ctl, a.cap);
+    pdl_launch(k_loc_common, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec);
     nl += 2;
     if (a.T2) {
         // maintained triangle sums: intersect only the edges whose t changes
-        k_zero_u64<<<gw, tpb, 0, s>>>((unsigned long long*)a.dcnt, &a.ctl->l_len[0]);
-        k_loc_tri_delta<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.dcnt,
+        pdl_launch(k_zero_u64, dim3(gw), dim3(tpb), 0, s, (unsigned long long*)a.dcnt, &a.ctl->l_len[0]);
+        pdl_launch(k_loc_tri_delta, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec,
+                   a.dcnt,
                                            a.dtri2, a.visited2, a.wlist_w);
-        k_loc_dcost<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.dcnt, a.cost);
+        pdl_launch(k_loc_dcost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.dcnt, a.cost);
         nl += 3;
         nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
-        k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
-        k_loc_eterms<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.tpack, a.dcnt, a.da, a.db);
-        k_loc_vterms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.T2, a.dtri2, a.da, a.db, commit);
+        pdl_launch(k_loc_tri, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.pre, a.own, a.tpack);
+        pdl_launch(k_loc_eterms, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.tpack, a.dcnt, a.da, a.db);
+        pdl_launch(k_loc_vterms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, V, a.T2, a.dtri2, a.da, a.db, commit);
         nl += 3;
     } else {
         // triangles of every edge at V_X, then their terms
-        k_loc_tri_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.own, a.cost);
+        pdl_launch(k_loc_tri_cost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.cost);
         nl++;
         nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
-        k_loc_tri<<<gw, tpb, 0, s>>>(a.ctl, V, a.pre, a.own, a.tpack);
-        k_loc_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, V, a.own, a.tpack, a.da, a.db);
+        pdl_launch(k_loc_tri, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.pre, a.own, a.tpack);
+        pdl_launch(k_loc_terms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, V, a.own, a.tpack, a.da, a.db);
         nl += 2;
     }
     if (ev_sub) record_stage(ev_sub, s);
-    k_loc_k4_cost<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kcost);
+    pdl_launch(k_loc_k4_cost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec,
+               a.kcost);
     nl++;
     nl += scan_i32_to_i64(a.kcost, a.kpre, &a.ctl->l_len[2], 0, a.bsum, sg, &a.ctl->l_tot[2], s);
-    k_loc_k4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kpre);
+    pdl_launch(k_loc_k4, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.ppre, a.rec, a.kpre);
     // the triangle probe offsets are free again: the 4-cycle tasks reuse them
-    k_loc_c4_tasks<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.cpre, a.walk, a.tpair, a.own,
+    pdl_launch(k_loc_c4_tasks, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.cpre, a.walk,
+               a.tpair, a.own,
                                       a.cost);
     nl += 2;
     nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
-    k_loc_c4<<<gw, tpb, 0, s>>>(a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.walk, a.tpair, a.own, a.pre);
+    pdl_launch(k_loc_c4, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.walk, a.tpair, a.own,
+               a.pre);
     nl++;
     if (ev_fin) record_stage(ev_fin, s);
-    k_finalize_local<<<1, 32, 0, s>>>(a.ctl, commit);
+    pdl_launch(k_finalize_local, dim3(1), dim3(32), 0, s, a.ctl, commit);
     nl++;
     return nl;
 }

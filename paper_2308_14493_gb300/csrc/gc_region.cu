@@ -42,6 +42,7 @@ __device__ __forceinline__ void visit_append(bool want, int32_t v, uint32_t* vis
 
 __global__ void k_bfs_sources(Ctl* c, const int32_t* __restrict__ srcA, const int32_t* __restrict__ srcD,
                               uint32_t* __restrict__ visited, int32_t* __restrict__ wlist) {
+    pdl_enter();
     if (c->err) return;
     long long na = c->nA2, nd = c->nD2, tot = na + nd;
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -55,11 +56,12 @@ __global__ void k_bfs_sources(Ctl* c, const int32_t* __restrict__ srcA, const in
     }
 }
 
-__global__ void k_level_mark(Ctl* c, int L) { c->lvl[L] = c->nW; }
+__global__ void k_level_mark(Ctl* c, int L) { pdl_enter(); c->lvl[L] = c->nW; }
 
 __global__ void k_bfs_expand(Ctl* c, int L, const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
                              const int32_t* __restrict__ col, uint32_t* __restrict__ visited,
                              int32_t* __restrict__ wlist) {
+    pdl_enter();
     if (c->err) return;
     int fb = L >= 2 ? c->lvl[L - 2] : 0;
     int fe = c->lvl[L - 1];
@@ -80,6 +82,7 @@ __global__ void k_bfs_expand(Ctl* c, int L, const long long* __restrict__ row_st
 
 // static count: W = V
 __global__ void k_region_all(Ctl* c, int n, int32_t* __restrict__ wlist) {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wlist[i] = i;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->nW = n;
@@ -91,6 +94,7 @@ __global__ void k_u_count(const Ctl* c, const int32_t* __restrict__ wlist, const
                           const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
                           const int32_t* __restrict__ col, const int2* __restrict__ segA,
                           int32_t* __restrict__ U_deg, int all) {
+    pdl_enter();
     int nW = c->nW;
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -121,6 +125,7 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const 
                          const int32_t* __restrict__ dstD, const long long* __restrict__ U_off,
                          uint32_t* __restrict__ U_col, int32_t* __restrict__ U_split, int32_t* __restrict__ da,
                          int32_t* __restrict__ db, int all) {
+    pdl_enter();
     int nW = c->nW;
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -153,6 +158,7 @@ __global__ void k_u_fill_all(const Ctl* c, const int32_t* __restrict__ wlist, co
                              const int32_t* __restrict__ dstA, const int32_t* __restrict__ dstD,
                              const long long* __restrict__ U_off, uint32_t* __restrict__ U_col,
                              int32_t* __restrict__ U_split, int32_t* __restrict__ da, int32_t* __restrict__ db) {
+    pdl_enter();
     const int nW = c->nW;
     for (int i = blockIdx.x; i < nW; i += gridDim.x) {
         const int32_t u = wlist[i];

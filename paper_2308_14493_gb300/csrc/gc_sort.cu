@@ -25,6 +25,7 @@ __device__ __forceinline__ void chunk_of(long long n, long long& beg, long long&
 
 __global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const uint64_t* __restrict__ keys, const long long* d_count,
                                                      int shift, uint32_t* __restrict__ hist) {
+    pdl_enter();
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const uint64_t* __restrict
 // thread sums a contiguous slice, the 1024 slice sums are scanned with warp
 // shuffles (two levels), then each thread rewrites its slice.
 __global__ void __launch_bounds__(1024) k_scan_u32_one_block(uint32_t* a, int len) {
+    pdl_enter();
     __shared__ uint32_t wsum[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (len + 1023) / 1024;
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(1024) k_scan_u32_one_block(uint32_t* a, int le
 __global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                         const long long* d_count, int shift,
                                                         const uint32_t* __restrict__ offs) {
+    pdl_enter();
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[RS_WARPS][256];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -110,6 +113,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const uint64_t* __restr
 }
 
 __global__ void k_copy_u64(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, const long long* d_count) {
+    pdl_enter();
     long long n = *d_count;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = in[i];
@@ -146,6 +150,7 @@ __device__ __forceinline__ long long block_incl_scan_i64(long long x, long long*
 
 __global__ void __launch_bounds__(SC_BLOCK) k_scan_partials(const int32_t* __restrict__ in, const long long* d_len,
                                                            long long host_len, long long* __restrict__ bsum) {
+    pdl_enter();
     __shared__ long long sh[32];
     long long n = d_len ? *d_len : host_len;
     long long beg, end;
@@ -157,6 +162,7 @@ __global__ void __launch_bounds__(SC_BLOCK) k_scan_partials(const int32_t* __res
 }
 
 __global__ void __launch_bounds__(1024) k_scan_top(long long* bsum, int G) {
+    pdl_enter();
     __shared__ long long sh[32];
     // G <= 1024
     long long x = threadIdx.x < G ? bsum[threadIdx.x] : 0;
@@ -167,6 +173,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(long long* bsum, int G) {
 __global__ void __launch_bounds__(SC_BLOCK) k_scan_apply(const int32_t* __restrict__ in, long long* __restrict__ out,
                                                         const long long* d_len, long long host_len,
                                                         const long long* __restrict__ bsum, long long* total_out) {
+    pdl_enter();
     __shared__ long long sh[32];
     long long n = d_len ? *d_len : host_len;
     long long beg, end;
@@ -210,9 +217,9 @@ int radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long
     uint64_t* b = tmp;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<<<grid, RS_BLOCK, 0, s>>>(a, d_count, shift, hist);
-        k_scan_u32_one_block<<<1, 1024, 0, s>>>(hist, 256 * grid);
-        k_rs_scatter<<<grid, RS_BLOCK, 0, s>>>(a, b, d_count, shift, hist);
+        pdl_launch(k_rs_hist, dim3(grid), dim3(RS_BLOCK), 0, s, a, d_count, shift, hist);
+        pdl_launch(k_scan_u32_one_block, dim3(1), dim3(1024), 0, s, hist, 256 * grid);
+        pdl_launch(k_rs_scatter, dim3(grid), dim3(RS_BLOCK), 0, s, a, b, d_count, shift, hist);
         uint64_t* t = a;
         a = b;
         b = t;
@@ -221,7 +228,7 @@ int radix_sort_u64(uint64_t* keys, uint64_t* tmp, const long long* d_count, long
         int g = (int)((max_count + 255) / 256);
         if (g < 1) g = 1;
         if (g > 2048) g = 2048;
-        k_copy_u64<<<g, 256, 0, s>>>(a, keys, d_count);
+        pdl_launch(k_copy_u64, dim3(g), dim3(256), 0, s, a, keys, d_count);
         launches++;
     }
     return launches;
@@ -237,9 +244,9 @@ int scan_grid(long long max_len, int sms) {
 
 int scan_i32_to_i64(const int32_t* in, long long* out, const long long* d_len, long long host_len, long long* bsum,
                     int grid, long long* total_out, cudaStream_t s) {
-    k_scan_partials<<<grid, SC_BLOCK, 0, s>>>(in, d_len, host_len, bsum);
-    k_scan_top<<<1, 1024, 0, s>>>(bsum, grid);
-    k_scan_apply<<<grid, SC_BLOCK, 0, s>>>(in, out, d_len, host_len, bsum, total_out);
+    pdl_launch(k_scan_partials, dim3(grid), dim3(SC_BLOCK), 0, s, in, d_len, host_len, bsum);
+    pdl_launch(k_scan_top, dim3(1), dim3(1024), 0, s, bsum, grid);
+    pdl_launch(k_scan_apply, dim3(grid), dim3(SC_BLOCK), 0, s, in, out, d_len, host_len, bsum, total_out);
     return 3;
 }
 

@@ -36,6 +36,7 @@ enum { R_PEND, R_PMID, R_SLEAF, R_SCTR, R_C4, R_TTAIL, R_TOTH, R_TATT, R_D2, R_D
 __global__ void k_v_tsym(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                          const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                          const unsigned long long* __restrict__ tpack, uint32_t* __restrict__ tall) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -55,6 +56,7 @@ __global__ void k_v_tsym(const Ctl* c, const int32_t* __restrict__ wlist, const 
 // s(u) = sum over the neighbours w of (d_w - 1)
 __global__ void k_v_s(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                       const uint32_t* __restrict__ U_col, long long* __restrict__ sdeg) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -78,6 +80,7 @@ __global__ void k_v_terms(const Ctl* c, const int32_t* __restrict__ wlist, const
                           const uint32_t* __restrict__ U_col, const uint32_t* __restrict__ tall,
                           const long long* __restrict__ sdeg, const unsigned long long* __restrict__ T2,
                           long long* __restrict__ NV) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -124,6 +127,7 @@ __global__ void k_v_terms(const Ctl* c, const int32_t* __restrict__ wlist, const
 __global__ void k_v_tri_k4(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                            const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
                            const uint32_t* __restrict__ tall, long long* __restrict__ NV) {
+    pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -144,9 +148,12 @@ __global__ void k_v_tri_k4(const Ctl* c, const int32_t* __restrict__ wlist, cons
                     j++;
                 } else {
                     // triangle (u, v, y): t of uv, uy, vy at e, i, j
-                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)u + R_D2], (unsigned long long)((long long)tall[j] - 1));
-                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)v + R_D2], (unsigned long long)((long long)tall[i] - 1));
-                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)y + R_D2], (unsigned long long)((long long)tall[e] - 1));
+                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)u + R_D2],
+                              (unsigned long long)((long long)tall[j] - 1));
+                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)v + R_D2],
+                              (unsigned long long)((long long)tall[i] - 1));
+                    atomicAdd((unsigned long long*)&NV[NROLE * (size_t)y + R_D2],
+                              (unsigned long long)((long long)tall[e] - 1));
                     // 4-cliques (u, v, y, z), z > y in N+(u), N+(v), N+(y)
                     const long long yb = U_off[y] + U_split[y], ye = U_off[y + 1];
                     long long p = i + 1, q = j + 1, r = yb, kk = 0;
@@ -188,6 +195,7 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
                                                const uint32_t* __restrict__ U_col,
                                                const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_all,
                                                int n, long long* __restrict__ NV) {
+    pdl_enter();
     const int nW = c->nW;
     uint32_t* cnt = cnt_all + (size_t)blockIdx.x * (size_t)n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NWp = blockDim.x >> 5;
@@ -220,7 +228,8 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
                 }
                 if (pass == 1) {
                     asum = (long long)warp_sum_u64((unsigned long long)asum);
-                    if (lane == 0 && asum) atomicAdd((unsigned long long*)&NV[NROLE * (size_t)a + R_C4], (unsigned long long)asum);
+                    if (lane == 0 && asum) atomicAdd((unsigned long long*)&NV[NROLE * (size_t)a + R_C4],
+                        (unsigned long long)asum);
                 }
             }
             __threadfence();
@@ -243,6 +252,7 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
 // (k = 6).
 __global__ void k_v_finalize(const long long* __restrict__ NV, int n, const int32_t* __restrict__ iperm, int k,
                              unsigned long long* __restrict__ out) {
+    pdl_enter();
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const long long* r = NV + NROLE * (size_t)v;
         const long long o14 = r[R_K4];
@@ -274,12 +284,13 @@ __global__ void k_v_finalize(const long long* __restrict__ NV, int n, const int3
 int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s) {
     const int gw = 8 * a.sms, tpb = 256;
     int nl = 0;
-    k_v_tsym<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.tall);
-    k_v_s<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.sdeg);
-    k_v_terms<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.tall, a.sdeg, a.T2, a.NV);
-    k_v_tri_k4<<<gw, tpb, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NV);
-    k_v_c4<<<a.c4_blocks, 1024, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n, a.NV);
-    k_v_finalize<<<(a.n + 255) / 256, 256, 0, s>>>(a.NV, a.n, a.iperm, a.orbits ? 11 : 6, a.out);
+    pdl_launch(k_v_tsym, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.tall);
+    pdl_launch(k_v_s, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.sdeg);
+    pdl_launch(k_v_terms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.tall, a.sdeg, a.T2, a.NV);
+    pdl_launch(k_v_tri_k4, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NV);
+    pdl_launch(k_v_c4, dim3(a.c4_blocks), dim3(1024), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n,
+               a.NV);
+    pdl_launch(k_v_finalize, dim3((a.n + 255) / 256), dim3(256), 0, s, a.NV, a.n, a.iperm, a.orbits ? 11 : 6, a.out);
     nl += 6;
     return nl;
 }
