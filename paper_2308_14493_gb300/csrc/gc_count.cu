@@ -1449,8 +1449,8 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                                                                     a.U_split, a.chunk_table, TW);
         nl += 2;
     }
-    pdl_launch(k_c4_hash, dim3(a.cta_groups), dim3(C4_DENSE_THREADS), 0, s, a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col,
-               a.U_split, a.cta_tables, a.cta_table_words);
+    k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
+                                                        a.cta_tables, a.cta_table_words);
     nl += 5;
     if (par) {
         cudaEventRecord(a.join[1], sC1);
@@ -1463,8 +1463,7 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
         cudaEventRecord(a.join[0], sT);
         cudaStreamWaitEvent(s, a.join[0], 0);
     }
-    pdl_launch(k_edge_terms, dim3(8 * sms), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da,
-               a.db);
+    k_edge_terms<<<8 * sms, 256, 0, s>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.da, a.db);
     pdl_launch(k_finalize, dim3(1), dim3(32), 0, s, a.ctl, mode);
     nl += 2;
     return nl;
