@@ -266,6 +266,7 @@ def roofline(recs, peak, peak_kind):
     achieved = bytes_ / (sm[k] / 1e3) / 1e9 if sm[k] > 0 else None
     return {"bound": "hbm", "kernel": KERNEL_OF_STAGE[k], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
+            "frac_of_nominal_8_tbs": achieved / 8000.0 if achieved else None,
             "algorithmic_bytes": bytes_, "kernel_ms": sm[k], "traffic": None,
             "stage_ms": dict(zip(STAGES, [round(x, 4) for x in sm]))}
 
@@ -353,6 +354,21 @@ def plain_vs_batched(gcb, torch, n, rp, col, batches, W, stream, flush):
             "batched_over_plain": (normalised / secs) / sp["value"],
             "counts_equal": outs == [r["out"] for r in recs],
             "normalised_equals_raw": normalised == raw}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (x86 or Arm), for the CPU-baseline record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
 
 
 def cpu_oracle_sample(rp, col, batches, budget_s):
@@ -568,7 +584,14 @@ def gpu_arm(args):
         edges, secs, done, t_static = cpu_oracle_sample(rp, col, batches, args.cpu_seconds)
         line["cpu_baseline"] = {"value": edges / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {done} batches of the same stream, oracle Algorithm 2 step "
-                                          f"(plus {t_static:.2f} s static count at open, not timed)"}
+                                          f"(plus {t_static:.2f} s static count at open, not timed)",
+                                "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+        if not args.no_secondary:
+            # the oracle on the c1 batch (Erdos-Renyi, 400 updates) as well
+            sp1 = BENCH["c1"]
+            n1, _, rp1, col1, b1 = make_batches(sp1, 1)
+            e1, s1, d1, _ = cpu_oracle_sample(rp1, col1, b1, 5.0)
+            line["cpu_baseline"]["c1"] = {"value": e1 / s1, "unit": UNIT, "sample": f"{d1} batch of 400 updates"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
