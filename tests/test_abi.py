@@ -75,3 +75,18 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
                      col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, ctypes.byref(h))
     assert rc == binding.GC_EINVAL
     assert b"non-decreasing" in lib.gc_last_error(None)
+
+
+def test_null_handles_are_rejected():
+    """Every call that takes a handle refuses a null one without device work."""
+    import numpy as np
+
+    from paper_2308_14493_gb300 import gc as binding
+
+    lib = binding.load()
+    out = np.zeros(64, np.uint64)
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    for name in ("gc_counts", "gc_counts3", "gc_counts_all", "gc_vertex_counts", "gc_vertex_orbits",
+                 "gc_count_static"):
+        assert getattr(lib, name)(None, p) == binding.GC_EINVAL, name
+    assert lib.gc_num_edges(None) == -1
