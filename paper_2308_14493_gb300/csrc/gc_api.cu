@@ -438,8 +438,10 @@ static int ensure_local(gc_graph* g, long long cap) {
         !ensure(g, g->l_ccnt, c) || !ensure(g, g->l_kcost, c) || !ensure(g, g->l_tpair, c) ||
         !ensure(g, g->l_walk, c) ||
         !ensure(g, g->l_pre, c + 1) || !ensure(g, g->l_ppre, c + 1) || !ensure(g, g->l_cpre, c + 1) ||
-        !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c) || !ensure(g, g->l_dcnt, c))
+        !ensure(g, g->l_kpre, c + 1) || !ensure(g, g->l_rec, c) || !ensure(g, g->l_dcnt, c)) {
+        release_local(g);  // no array is left half-grown (l_cap = 0)
         return nomem(g, "edge-local scratch");
+    }
     // ensure() may round up; the usable capacity is the smallest array's
     size_t m = std::min({g->l_cost.cap, g->l_own.cap, g->l_pcost.cap, g->l_ccnt.cap, g->l_kcost.cap,
                          g->l_tpair.cap, g->l_walk.cap, g->l_rec.cap, g->l_dcnt.cap, g->l_pre.cap - 1, g->l_ppre.cap - 1, g->l_cpre.cap - 1,
@@ -908,9 +910,9 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
     // proportional to the rows the batch touches instead of a region)
     bool local = g->opt.local_max_pairs > 0 && n_ins + n_del <= (long long)g->opt.local_max_pairs;
     for (int attempt = 0;; attempt++) {
-        if (local) {
-            rc = ensure_local(g, std::max<long long>(g->l_cap, 1LL << 20));
-            if (rc) return rc;
+        if (local && ensure_local(g, std::max<long long>(g->l_cap, 1LL << 20)) != GC_OK) {
+            g->err.clear();  // no room for the local scratch: the region form does the batch
+            local = false;
         }
         cudaGraphExec_t* ex = local ? &g->lexec : &g->pexec;
         long long* ex_nk = local ? &g->l_nk : &g->p_nk;
@@ -952,11 +954,9 @@ static int apply_device(gc_graph* g, const int32_t* d_ins, long long n_ins, cons
         // the local scratch was too small and nothing was applied: grow it
         // to what the batch needed (each of the two bound checks can report
         // its own need), else take the region path
-        if (attempt < 2) {
-            long long need = g->h_ctl->l_need;
-            rc = ensure_local(g, need + need / 4 + 1024);
-            if (rc) return rc;
-        } else {
+        const long long need = g->h_ctl->l_need;
+        if (attempt >= 2 || ensure_local(g, need + need / 4 + 1024) != GC_OK) {
+            g->err.clear();
             local = false;
         }
     }
