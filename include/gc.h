@@ -334,11 +334,12 @@ int gc_set_tuning(gc_graph *g, const gc_tuning *t);
  * the minimum kept).  The fastest set is installed and returned in *best
  * (may be NULL); *best_ms (may be NULL) receives its time.  Counts are
  * checked equal across all candidates (GC_ECUDA if not).
- * Then the edge-local threshold: what-if batches of k edges sampled
- * uniformly from the graph (deletions; k = 8, 32, 128, ... up to m / 4 and
- * 2^16) are timed through the edge-local delta and through the region
- * recount; local_max_pairs becomes the largest k at which the local form
- * was faster (0 if never), and the two results must be equal.
+ * Then the edge-local threshold: what-if batches of k pairs (k = 8, 16,
+ * 32, ... up to m / 4 and 2^16; half deletions of edges sampled uniformly,
+ * half insertions between vertices drawn in proportion to degree) are
+ * timed through the edge-local delta and through the region recount;
+ * local_max_pairs becomes the largest k at which the local form was faster
+ * (0 if never), and the two results must be equal.
  */
 int gc_autotune(gc_graph *g, int32_t reps, gc_tuning *best, float *best_ms);
 

@@ -2029,28 +2029,46 @@ static int time_static(gc_graph* g, int reps, float* ms, uint64_t out[6]) {
     return GC_OK;
 }
 
-// k edges drawn uniformly (with repetition) from the current graph, as
-// external-id pairs: draw i picks directed entry r = h(seed, i) mod 2m
-// through the degree prefix sums cum (splitmix64 of the draw index).
+// splitmix64 of a draw index (Steele, Lea and Flood, OOPSLA 2014)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// the vertex owning directed entry r of the degree prefix sums cum
+__device__ __forceinline__ long long entry_owner(const long long* __restrict__ cum, int n, long long r) {
+    long long lo = 0, hi = n;  // last u with cum[u] <= r
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (cum[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// A calibration batch as external-id pairs: k deletions of edges drawn
+// uniformly (with repetition) from the current graph (draw i picks directed
+// entry h(seed, i) mod 2m), then k insertions between two vertices drawn
+// in proportion to degree (mostly non-edges, as the batch recipe's
+// insertions; a present edge is a no-op).
 __global__ void k_sample_edges(const long long* __restrict__ cum, int n, const long long* __restrict__ row_start,
                                const int32_t* __restrict__ col, const int32_t* __restrict__ iperm,
                                unsigned long long seed, int k, int32_t* __restrict__ pairs) {
     pdl_enter();
-    const long long m2 = cum[n];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        const long long r = (long long)(z % (unsigned long long)m2);
-        long long lo = 0, hi = n;  // last u with cum[u] <= r
-        while (hi - lo > 1) {
-            const long long mid = (lo + hi) >> 1;
-            if (cum[mid] <= r) lo = mid;
-            else hi = mid;
+    const unsigned long long m2 = (unsigned long long)cum[n];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * k; i += gridDim.x * blockDim.x) {
+        const long long r = (long long)(mix64(seed, (unsigned long long)i) % m2);
+        const int32_t u = (int32_t)entry_owner(cum, n, r);
+        int32_t v;
+        if (i < k) {
+            v = col[row_start[u] + (r - cum[u])];
+        } else {
+            const unsigned long long r2 = mix64(seed ^ 0x5851F42D4C957F2Dull, (unsigned long long)i) % m2;
+            v = (int32_t)entry_owner(cum, n, (long long)r2);
+            if (v == u) v = (u + 1) % n;
         }
-        const int32_t u = (int32_t)lo;
-        const int32_t v = col[row_start[u] + (r - cum[u])];
         pairs[2 * i] = iperm[u];
         pairs[2 * i + 1] = iperm[v];
     }
@@ -2066,20 +2084,22 @@ static int calibrate_local(gc_graph* g, int reps) {
     cudaStream_t s = g->s;
     const long long kmax = std::min<long long>(g->m / 4, 1LL << 16);
     if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(kmax, 8))) return nomem(g, "calibration pairs");
+    // each calibration batch: k / 2 deletions, then k / 2 insertions
     // degree prefix sums (the union-graph offsets are free between batches)
     g->launches += scan_i32_to_i64(g->deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), nullptr, s);
     long long thr = 0;
-    for (long long k = 8; k <= kmax; k *= 4) {
-        pdl_launch(k_sample_edges, dim3(grid_elems(g, k)), dim3(TPB), 0, s, g->U_off, g->n, g->row_start, g->col,
-                   g->iperm,
-                                                        0x5DEECE66Dull + (unsigned long long)k, (int)k, g->pairs.p);
+    for (long long k = 8; k <= kmax; k *= 2) {
+        const long long half = k / 2;
+        k_sample_edges<<<grid_elems(g, k), TPB, 0, s>>>(g->U_off, g->n, g->row_start, g->col, g->iperm,
+                                                        0x5DEECE66Dull + (unsigned long long)k, (int)half, g->pairs.p);
         CKL();
         float best[2] = {1e30f, 1e30f};
         uint64_t res[2][6];
         for (int form = 0; form < 2; form++) {
             g->opt.local_max_pairs = form == 0 ? (int32_t)k : 0;
             for (int r = 0; r < std::max(reps, 1) + 1; r++) {  // the first run captures
-                int rc = apply_device(g, g->pairs.p, 0, g->pairs.p, k, 0, res[form]);
+                // half deletions, half insertions (the second half of the pairs)
+                int rc = apply_device(g, g->pairs.p + 2 * half, half, g->pairs.p, half, 0, res[form]);
                 if (rc) {
                     g->opt.local_max_pairs = saved;
                     return rc;
