@@ -362,8 +362,10 @@ def cpu_model() -> str:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware"):
+                if key in ("model name", "hardware"):
                     return line.split(":", 1)[1].strip()
+                if key == "cpu part":  # Arm: the part number (0xd4f is Neoverse V2)
+                    return "Arm CPU part " + line.split(":", 1)[1].strip()
     except OSError:
         pass
     import platform
