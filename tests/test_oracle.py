@@ -468,3 +468,63 @@ def test_vertex_orbits_match_the_census(oracle_lib):
         edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
         rp, col = csr_from_edges(n, edges)
         assert oracle.vertex_orbits(rp, col) == brute.vertex_orbit_census(n, edges), trial
+
+
+def _role_counts_by_enumeration():
+    """For each connected 4-vertex graph g and each vertex orbit o in it,
+    the number of non-induced copies of each subgraph H (3-path, 3-star,
+    4-cycle, tailed triangle, diamond, 4-clique) that hold that vertex in
+    each role, found by trying every edge subset of g: the matrix the
+    per-vertex orbit inversion uses."""
+    graphs = {  # one representative of each type on vertices 0..3
+        "g1": [(0, 1), (1, 2), (2, 3)],
+        "g2": [(0, 1), (0, 2), (0, 3)],
+        "g3": [(0, 1), (1, 2), (2, 3), (3, 0)],
+        "g4": [(0, 1), (1, 2), (2, 0), (2, 3)],
+        "g5": [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)],
+        "g6": [(a, b) for a in range(4) for b in range(a + 1, 4)],
+    }
+
+    def role(edges, v):
+        deg = [0] * 4
+        for a, b in edges:
+            deg[a] += 1
+            deg[b] += 1
+        cls = brute._CLASSES.get((len(edges), tuple(sorted(deg))))
+        if cls not in brute.CONNECTED:
+            return None
+        return brute._orbit(cls, deg, v)   # the role of v in the copy = its orbit in that graph
+
+    table = {}
+    for g, edges in graphs.items():
+        for v in range(4):
+            deg = [0] * 4
+            for a, b in edges:
+                deg[a] += 1
+                deg[b] += 1
+            o = brute._orbit(g, deg, v)
+            counts = {}
+            for r in range(1, len(edges) + 1):
+                for sub in itertools.combinations(edges, r):
+                    # a copy spans all four vertices
+                    if len({x for e in sub for x in e}) != 4:
+                        continue
+                    rr = role(list(sub), v)
+                    if rr is not None:
+                        counts[rr] = counts.get(rr, 0) + 1
+            table[o] = counts
+    return table
+
+
+def test_role_containment_by_enumeration():
+    """The coefficients of the per-vertex orbit inversion, enumerated from
+    the edge subsets of each graphlet (orbit -> {role: copies})."""
+    t = _role_counts_by_enumeration()
+    assert t[14] == {4: 6, 5: 6, 6: 3, 7: 1, 8: 3, 9: 3, 10: 6, 11: 3, 12: 3, 13: 3, 14: 1}
+    assert t[13] == {4: 2, 5: 4, 6: 1, 7: 1, 8: 1, 10: 2, 11: 2, 13: 1}
+    assert t[12] == {4: 4, 5: 2, 6: 2, 8: 1, 9: 2, 10: 2, 12: 1}
+    assert t[11] == {5: 2, 7: 1, 11: 1}
+    assert t[10] == {4: 1, 5: 1, 6: 1, 10: 1}
+    assert t[9] == {4: 2, 6: 1, 9: 1}
+    assert t[8] == {4: 2, 5: 2, 8: 1}
+    assert t[7] == {7: 1} and t[6] == {6: 1} and t[5] == {5: 1} and t[4] == {4: 1}
