@@ -705,7 +705,8 @@ def serve_arm(args):
         "plain": plain, "served_saturated": sat, "served_poisson_0.8x": poi,
         "served_over_plain": sat["value"] / plain["value"],
         "generation_s": t_gen, "autotune_s": t_tune,
-        "autotuned_chunk_tier": sum(1 for t in tunings if t["c4_chunk_min"]), "clocks": clk.summary(),
+        "autotuned_chunk_tier": sum(1 for t in tunings if t["c4_chunk_min"]),
+        "local_thresholds": [t["local_max_pairs"] for t in tunings], "clocks": clk.summary(),
     }
     for h in handles:
         h.close()
