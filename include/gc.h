@@ -63,10 +63,12 @@ typedef struct {
     int32_t chunk_threshold; /* wedge bound above which a 4-cycle pivot is counted in shared memory
                                 over id-range chunks; <= 0: never (the cluster kernel takes them) */
     int32_t local_max_pairs; /* batches of at most this many pairs (as passed) to gc_apply_batch,
-                                gc_count_batch and their _device forms take the edge-local delta:
-                                the same counts from only the terms a batch can change (edges at
-                                its endpoints, 4-cliques and 4-cycles through its pairs) instead
-                                of a region recount.  0: never */
+                                gc_count_batch and their _device forms, and such batches within
+                                gc_apply_batches* runs (taken one at a time, in order), take the
+                                edge-local delta: the same counts from only the terms a batch can
+                                change (edges at its endpoints, 4-cliques and 4-cycles through its
+                                pairs) instead of a region recount.  0: never; gc_autotune sets
+                                it by measurement */
     int32_t reserved[4];
 } gc_options;
 
