@@ -151,3 +151,49 @@ def vertex_orbit_census(n: int, edges) -> list[list[int]]:
             for i, v in enumerate(s):
                 out[v][_orbit(c, deg, i) - 4] += 1
     return out
+
+
+# edge orbit (0..9) of edge {a, b} inside each connected induced 4-vertex
+# graph, by the degrees of its endpoints there: 3-path end, middle; 3-star;
+# 4-cycle; tailed triangle tail, triangle edge opposite the attachment,
+# triangle edge at the attachment; diamond outer edge, chord; 4-clique
+def _edge_orbit(cls: str, deg: list[int], a: int, b: int) -> int:
+    lo, hi = sorted((deg[a], deg[b]))
+    if cls == "g1":
+        return 0 if lo == 1 else 1
+    if cls == "g2":
+        return 2
+    if cls == "g3":
+        return 3
+    if cls == "g4":
+        return {(1, 3): 4, (2, 2): 5, (2, 3): 6}[(lo, hi)]
+    if cls == "g5":
+        return 8 if (lo, hi) == (3, 3) else 7
+    return 9
+
+
+def edge_orbit_census(n: int, edges):
+    """Per edge (u < v, sorted), how many induced connected 4-vertex
+    graphlets hold it in each edge orbit 0..9, over all 4-subsets (n <= 40).
+    Returns (sorted edge list, list of 10-entry rows)."""
+    if n > 40:
+        raise ValueError("brute force is for n <= 40")
+    adj = [[False] * n for _ in range(n)]
+    for a, b in edges:
+        adj[a][b] = adj[b][a] = True
+    keys = sorted({(min(a, b), max(a, b)) for a, b in edges})
+    row = {e: [0] * 10 for e in keys}
+    for s in itertools.combinations(range(n), 4):
+        deg = [0, 0, 0, 0]
+        present = []
+        for i in range(4):
+            for j in range(i + 1, 4):
+                if adj[s[i]][s[j]]:
+                    deg[i] += 1
+                    deg[j] += 1
+                    present.append((i, j))
+        c = _CLASSES[(len(present), tuple(sorted(deg)))]
+        if c in CONNECTED:
+            for i, j in present:
+                row[(s[i], s[j])][_edge_orbit(c, deg, i, j)] += 1
+    return keys, [row[e] for e in keys]

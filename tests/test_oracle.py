@@ -528,3 +528,103 @@ def test_role_containment_by_enumeration():
     assert t[9] == {4: 2, 6: 1, 9: 1}
     assert t[8] == {4: 2, 5: 2, 8: 1}
     assert t[7] == {7: 1} and t[6] == {6: 1} and t[5] == {5: 1} and t[4] == {4: 1}
+
+
+# ------------------------------------------------------- per-edge orbits --
+
+def test_edge_orbits_match_the_census(oracle_lib):
+    """Edge orbit counts (10 columns) against the census of every 4-subset,
+    each edge of the induced graph credited with its orbit there."""
+    rng = np.random.default_rng(2020)
+    for trial in range(60):
+        n = int(rng.integers(4, 18))
+        p = float(rng.uniform(0.05, 0.95))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        rp, col = csr_from_edges(n, edges)
+        assert oracle.edge_orbits(rp, col) == brute.edge_orbit_census(n, edges), trial
+
+
+def test_edge_orbits_of_named_graphs(oracle_lib):
+    c2 = lambda x: x * (x - 1) // 2
+    for n in range(4, 9):   # K_n: every edge lies in C(n-2, 2) 4-cliques
+        edges = list(itertools.combinations(range(n), 2))
+        rp, col = csr_from_edges(n, edges)
+        assert oracle.edge_orbits(rp, col)[1] == [[0] * 9 + [c2(n - 2)]] * len(edges)
+    for n in range(5, 10):  # C_n: each edge ends two 3-paths and is the middle of one
+        edges = [(i, (i + 1) % n) for i in range(n)]
+        rp, col = csr_from_edges(n, edges)
+        assert oracle.edge_orbits(rp, col)[1] == [[2, 1] + [0] * 8] * n
+    for a in range(1, 5):   # K_{a,b}: 3-stars at either end and (a-1)(b-1) 4-cycles
+        for b in range(1, 6):
+            edges = [(i, a + j) for i in range(a) for j in range(b)]
+            rp, col = csr_from_edges(a + b, edges)
+            want = [0, 0, c2(b - 1) + c2(a - 1), (a - 1) * (b - 1), 0, 0, 0, 0, 0, 0]
+            assert oracle.edge_orbits(rp, col)[1] == [want] * len(edges), (a, b)
+
+
+def test_edge_orbits_sum_to_the_global_counts(oracle_lib):
+    """Summed over edges, each orbit gives its graphlet count times the
+    number of its edges in that orbit (3-path 2 + 1, 3-star 3, 4-cycle 4,
+    tailed triangle 1 + 1 + 2, diamond 4 + 1, 4-clique 6); the global counts
+    come from the C oracle."""
+    rng = np.random.default_rng(3)
+    for n, p in ((120, 0.08), (60, 0.4)):
+        edges = random_graph(rng, n, p)
+        rp, col = csr_from_edges(n, edges)
+        rows = np.asarray(oracle.edge_orbits(rp, col)[1], dtype=np.int64)
+        tot = rows.sum(axis=0).tolist()
+        g1, g2, g3, g4, g5, g6 = oracle.static_counts(rp, col)
+        assert tot == [2 * g1, g1, 3 * g2, 4 * g3, g4, g4, 2 * g4, 4 * g5, g5, 6 * g6]
+
+
+def _edge_role_counts_by_enumeration():
+    """For each connected 4-vertex graph g and each edge orbit in it, the
+    number of non-induced copies of each connected subgraph holding that
+    edge in each edge role, found by trying every edge subset of g: the
+    matrix the per-edge orbit inversion uses."""
+    graphs = {
+        "g1": [(0, 1), (1, 2), (2, 3)],
+        "g2": [(0, 1), (0, 2), (0, 3)],
+        "g3": [(0, 1), (1, 2), (2, 3), (3, 0)],
+        "g4": [(0, 1), (1, 2), (2, 0), (2, 3)],
+        "g5": [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)],
+        "g6": [(a, b) for a in range(4) for b in range(a + 1, 4)],
+    }
+
+    def degs(edges):
+        d = [0] * 4
+        for a, b in edges:
+            d[a] += 1
+            d[b] += 1
+        return d
+
+    table = {}
+    for g, edges in graphs.items():
+        for e in edges:
+            o = brute._edge_orbit(g, degs(edges), *e)
+            counts = {}
+            for r in range(1, len(edges) + 1):
+                for sub in itertools.combinations(edges, r):
+                    if e not in sub or len({x for f in sub for x in f}) != 4:
+                        continue
+                    d = degs(sub)
+                    cls = brute._CLASSES.get((len(sub), tuple(sorted(d))))
+                    if cls in brute.CONNECTED:
+                        rr = brute._edge_orbit(cls, d, *e)
+                        counts[rr] = counts.get(rr, 0) + 1
+            assert table.setdefault(o, counts) == counts   # one answer per orbit
+    return table
+
+
+def test_edge_role_containment_by_enumeration():
+    """The coefficients of the per-edge orbit inversion (orbit -> {role:
+    copies}), enumerated from the edge subsets of each graphlet."""
+    t = _edge_role_counts_by_enumeration()
+    assert t[9] == {0: 4, 1: 2, 2: 2, 3: 2, 4: 2, 5: 2, 6: 4, 7: 4, 8: 1, 9: 1}
+    assert t[8] == {1: 2, 2: 2, 6: 4, 8: 1}
+    assert t[7] == {0: 3, 1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 1}
+    assert t[6] == {1: 1, 2: 1, 6: 1}
+    assert t[5] == {0: 2, 5: 1}
+    assert t[4] == {0: 2, 2: 1, 4: 1}
+    assert t[3] == {0: 2, 1: 1, 3: 1}
+    assert t[2] == {2: 1} and t[1] == {1: 1} and t[0] == {0: 1}
