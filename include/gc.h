@@ -177,6 +177,32 @@ int gc_vertex_counts(gc_graph *g, uint64_t *out);
    sum to its per-vertex count. */
 int gc_vertex_orbits(gc_graph *g, uint64_t *out);
 
+/* Per-edge (local) graphlet counts of the current graph.  Row r describes
+   the edge edges[2 r] < edges[2 r + 1] (external ids; the rows run over the
+   m = gc_num_edges(g) edges in increasing (lo, hi) order), and out[6 r + k]
+   is the number of induced connected 4-vertex graphlets of type k (order of
+   gc_counts) that contain that edge.  edges (int32[2 m], host) may be NULL;
+   out (uint64[6 m], host) may be NULL only when m = 0.  The containment
+   identity of the global counts holds per edge: the non-induced copies of
+   each connected 4-vertex subgraph through the edge, counted by the edge's
+   role in them, invert with a triangular matrix.  Summed over the edges,
+   type k gives (3, 3, 4, 4, 5, 6)[k] x gc_counts.  Runs a static pass plus
+   the per-edge kernels (device scratch of about 60 bytes per adjacency
+   entry plus the output, and one 4-byte counter array per 4-cycle block,
+   2 GB at most, all freed on return); the maintained counts are not
+   changed.  gc_batch_stats().ms_device gives the device time of the
+   per-edge kernels. */
+int gc_edge_counts(gc_graph *g, int32_t *edges, uint64_t *out);
+
+/* The same per edge orbit: out[10 r + j] = the induced connected 4-vertex
+   graphlets holding the edge of row r in edge orbit j: 0 3-path end edge,
+   1 3-path middle edge, 2 3-star edge, 3 4-cycle edge, 4 tailed-triangle
+   tail, 5 tailed-triangle edge opposite the attachment, 6 tailed-triangle
+   edge at the attachment, 7 diamond outer edge, 8 diamond chord, 9
+   4-clique edge.  out holds 10 m words; the orbits of a graphlet sum to
+   its per-edge count. */
+int gc_edge_orbits(gc_graph *g, int32_t *edges, uint64_t *out);
+
 /*
  * Apply one batch (Algorithm 2) and return the updated counts.
  *   ins   host int32[n_ins][2]: pairs to insert (may be NULL when n_ins = 0)

@@ -1597,10 +1597,10 @@ static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
     va.out = dout;
     va.orbits = orbits;
     va.sms = g->sms;
-    CK(cudaEventRecord(g->e0, s));
+    cudaError_t ce = cudaEventRecord(g->e0, s);
     g->launches = enqueue_vertex_counts(va, s);
-    CK(cudaEventRecord(g->e1, s));
-    cudaError_t ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * n, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(g->e1, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * n, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce == cudaSuccess) ce = cudaGetLastError();
     float ms = 0.f;
@@ -1617,6 +1617,106 @@ static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
 int gc_vertex_counts(gc_graph* g, uint64_t* out) { return vertex_counts(g, out, 0); }
 
 int gc_vertex_orbits(gc_graph* g, uint64_t* out) { return vertex_counts(g, out, 1); }
+
+static int edge_counts(gc_graph* g, int32_t* edges, uint64_t* out, int orbits) {
+    if (!g || (g->m > 0 && !out)) return GC_EINVAL;
+    if (!on_device(g)) {
+        g->err = "cudaSetDevice failed";
+        return GC_ECUDA;
+    }
+    g->err.clear();
+    if (g->m == 0) return GC_OK;
+    // the union graph, per-entry t and T2 of the current graph
+    int rc = count_static(g, false, nullptr);
+    if (rc) return rc;
+    cudaStream_t s = g->s;
+    const size_t n = (size_t)g->n;
+    const long long nU = g->h_ctl->nU, m = nU / 2;
+    if (nU != 2 * g->m) {
+        g->err = "per-edge counts: the union graph does not hold every edge twice";
+        return GC_ECUDA;
+    }
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(g->sms, (2LL << 30) / (4LL * (long long)n)));
+    const int sg = radix_grid(nU, g->sms);
+    const int k = orbits ? 10 : 6;
+    uint32_t* tall = (uint32_t*)dalloc(g, 4 * (size_t)nU);
+    long long* sdeg = (long long*)dalloc(g, 8 * n);
+    long long* NE = (long long*)dalloc(g, 32 * (size_t)nU);
+    unsigned long long* keys = (unsigned long long*)dalloc(g, 8 * (size_t)nU);
+    unsigned long long* ktmp = (unsigned long long*)dalloc(g, 8 * (size_t)nU);
+    uint32_t* hist = (uint32_t*)dalloc(g, 4 * 256 * (size_t)sg);
+    uint32_t* cnt = (uint32_t*)dalloc(g, 4 * n * (size_t)blocks);
+    unsigned long long* dout = (unsigned long long*)dalloc(g, 8 * (size_t)k * (size_t)m);
+    int32_t* dedges = edges ? (int32_t*)dalloc(g, 8 * (size_t)m) : nullptr;
+    auto cleanup = [&]() {
+        dfree(g, tall);
+        dfree(g, sdeg);
+        dfree(g, NE);
+        dfree(g, keys);
+        dfree(g, ktmp);
+        dfree(g, hist);
+        dfree(g, cnt);
+        dfree(g, dout);
+        if (dedges) dfree(g, dedges);
+    };
+    if (!tall || !sdeg || !NE || !keys || !ktmp || !hist || !cnt || !dout || (edges && !dedges)) {
+        cleanup();
+        return nomem(g, "per-edge counts");
+    }
+    if (cudaMemsetAsync(NE, 0, 32 * (size_t)nU, s) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, 4 * n * (size_t)blocks, s) != cudaSuccess) {
+        cleanup();
+        g->err = "cudaMemsetAsync failed";
+        return GC_ECUDA;
+    }
+    EdgeArgs ea;
+    ea.ctl = g->ctl;
+    ea.wlist = g->wlist;
+    ea.U_off = g->U_off;
+    ea.U_col = g->U_col.p;
+    ea.U_split = g->U_split;
+    ea.tpack = g->tpack.p;
+    ea.T2 = g->T2;
+    ea.tall = tall;
+    ea.sdeg = sdeg;
+    ea.NE = NE;
+    ea.keys = keys;
+    ea.keys_tmp = ktmp;
+    ea.hist = hist;
+    ea.sort_grid = sg;
+    ea.d_count = &g->ctl->nU;
+    ea.nU = nU;
+    ea.m = m;
+    ea.nb = g->S;
+    ea.cnt = cnt;
+    ea.c4_blocks = blocks;
+    ea.n = (int)n;
+    ea.iperm = g->iperm;
+    ea.out = dout;
+    ea.edges = dedges;
+    ea.orbits = orbits;
+    ea.sms = g->sms;
+    cudaError_t ce = cudaEventRecord(g->e0, s);
+    g->launches = enqueue_edge_counts(ea, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(g->e1, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * (size_t)m, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && edges) ce = cudaMemcpyAsync(edges, dedges, 8 * (size_t)m, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    float ms = 0.f;
+    if (ce == cudaSuccess && cudaEventElapsedTime(&ms, g->e0, g->e1) == cudaSuccess) g->st.ms_device = ms;
+    cleanup();
+    if (ce != cudaSuccess) {
+        g->err = std::string("per-edge counts: ") + cudaGetErrorString(ce);
+        return GC_ECUDA;
+    }
+    g->st.launches = g->launches;
+    return GC_OK;
+}
+
+int gc_edge_counts(gc_graph* g, int32_t* edges, uint64_t* out) { return edge_counts(g, edges, out, 0); }
+
+int gc_edge_orbits(gc_graph* g, int32_t* edges, uint64_t* out) { return edge_counts(g, edges, out, 1); }
 
 int gc_counts(const gc_graph* g, uint64_t out[6]) {
     if (!g || !out) return GC_EINVAL;

@@ -168,6 +168,35 @@ struct VertexArgs {
 };
 int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s);
 
+struct EdgeArgs {
+    Ctl* ctl;
+    const int32_t* wlist;          // all vertices (c->nW = n)
+    const long long* U_off;
+    const uint32_t* U_col;
+    const int32_t* U_split;
+    const unsigned long long* tpack;
+    const unsigned long long* T2;
+    uint32_t* tall;                // nU: t of every entry
+    long long* sdeg;               // n
+    long long* NE;                 // 4 nU per-entry credits, zeroed
+    unsigned long long* keys;      // nU sort keys (the first m sorted are the edges)
+    unsigned long long* keys_tmp;  // nU
+    uint32_t* hist;                // 256 sort_grid
+    int sort_grid;
+    const long long* d_count;      // device copy of nU
+    long long nU, m;
+    int nb;                        // bits of an external id
+    uint32_t* cnt;                 // c4_blocks * n, zeroed
+    int c4_blocks;
+    int n;
+    const int32_t* iperm;
+    unsigned long long* out;       // 10 m (edge orbits) or 6 m (graphlets), by external (lo, hi) order
+    int32_t* edges;                // 2 m: (lo, hi) per output row
+    int orbits;
+    int sms;
+};
+int enqueue_edge_counts(const EdgeArgs& a, cudaStream_t s);
+
 // Enqueue the counting kernels (binning, triangles / 4-cliques, 4-cycles,
 // edge terms, closed forms with k_finalize(mode)); events, when given, are
 // recorded before the triangle, 4-cycle and edge-term stages.  Returns the

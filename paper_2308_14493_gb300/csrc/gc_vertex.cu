@@ -281,6 +281,271 @@ __global__ void k_v_finalize(const long long* __restrict__ NV, int n, const int3
     }
 }
 
+// ---------------------------------------------------------------------
+// Per-edge (local) counts.  The same containment identity holds per edge
+// {u, v} and edge role, with the edge orbits 0..9 (3-path end, middle
+// edge; 3-star edge; 4-cycle edge; tailed triangle tail, triangle edge
+// opposite the attachment, triangle edge at the attachment; diamond outer
+// edge, chord; 4-clique edge).  The non-induced role counts of the edge
+// (tri(x) = T2[x] / 2, s(x) = sum_{w in N(x)} (d_w - 1)):
+//   3-path end   (s(v) - (d_u - 1) - t) + (s(u) - (d_v - 1) - t)
+//   3-path middle (d_u - 1)(d_v - 1) - t;  3-star C(d_u - 1, 2) + C(d_v - 1, 2)
+//   4-cycle      credited by the pivot walk below
+//   tail         (tri(u) - t) + (tri(v) - t);  attachment t (d_u + d_v - 4)
+//   opposite     sum over triangles {u, v, w} of d_w - 2
+//   diamond outer  sum over triangles {u, v, w} of t_uw + t_vw - 2
+//   chord C(t, 2);  4-clique credited by the clique listing
+// Credits land on either entry of the edge; the finalize adds both.
+
+enum { E_OPP, E_OUTER, E_C4, E_K4, NEROLE };
+
+// One sort key per entry: the out-entry (x < y) of an edge gets its
+// external pair (lo << nb) | hi, every in-entry the largest nb-bit pair,
+// so after the sort the first m keys are the edges in external order.
+__global__ void k_e_keys(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                         const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                         const int32_t* __restrict__ iperm, int nb, unsigned long long* __restrict__ keys) {
+    pdl_enter();
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned long long none = (1ull << (2 * nb)) - 1;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t u = (uint32_t)wlist[i];
+        const long long ob = U_off[u] + U_split[u];
+        const unsigned long long a = (unsigned long long)iperm[u];
+        for (long long e = U_off[u] + lane; e < U_off[u + 1]; e += 32) {
+            if (e < ob) {
+                keys[e] = none;
+            } else {
+                const unsigned long long b = (unsigned long long)iperm[vid(U_col[e])];
+                keys[e] = a < b ? (a << nb) | b : (b << nb) | a;
+            }
+        }
+    }
+}
+
+// Triangles u < v < y (each once) credit the opposite and diamond-outer
+// terms of their three edges; 4-cliques u < v < y < z (each once) credit
+// their six edges.  A warp per root u, a lane per out-edge e = (u, v).
+__global__ void k_e_tri_k4(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                           const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                           const uint32_t* __restrict__ tall, long long* __restrict__ NE) {
+    pdl_enter();
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int wi = warp; wi < nW; wi += nwarps) {
+        const uint32_t u = (uint32_t)wlist[wi];
+        const long long ob = U_off[u] + U_split[u], oe = U_off[u + 1];
+        const long long du = U_off[u + 1] - U_off[u];
+        for (long long e = ob + lane; e < oe; e += 32) {
+            const uint32_t v = vid(U_col[e]);
+            const long long vb = U_off[v] + U_split[v], ve = U_off[v + 1];
+            const long long dv = U_off[v + 1] - U_off[v], te = tall[e];
+            long long i = e + 1, j = vb;
+            long long opp = 0, outer = 0, k4 = 0;
+            while (i < oe && j < ve) {
+                const uint32_t x = vid(U_col[i]), y = vid(U_col[j]);
+                if (x < y) {
+                    i++;
+                } else if (x > y) {
+                    j++;
+                } else {
+                    // triangle (u, v, y): edges uv, uy, vy at e, i, j
+                    const long long dy = U_off[y + 1] - U_off[y], ti = tall[i], tj = tall[j];
+                    opp += dy - 2;
+                    outer += ti + tj - 2;
+                    atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)i + E_OPP], (unsigned long long)(dv - 2));
+                    atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)i + E_OUTER],
+                              (unsigned long long)(te + tj - 2));
+                    atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)j + E_OPP], (unsigned long long)(du - 2));
+                    atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)j + E_OUTER],
+                              (unsigned long long)(te + ti - 2));
+                    // 4-cliques (u, v, y, z), z > y: edges uz, vz, yz at p, q, r
+                    const long long yb = U_off[y] + U_split[y], ye = U_off[y + 1];
+                    long long p = i + 1, q = j + 1, r = yb, kk = 0;
+                    while (p < oe && q < ve && r < ye) {
+                        const uint32_t a = vid(U_col[p]), b = vid(U_col[q]), cc = vid(U_col[r]);
+                        const uint32_t mx = max(a, max(b, cc));
+                        if (a == mx && b == mx && cc == mx) {
+                            atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)p + E_K4], 1ull);
+                            atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)q + E_K4], 1ull);
+                            atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)r + E_K4], 1ull);
+                            kk++;
+                            p++;
+                            q++;
+                            r++;
+                        } else {
+                            if (a < mx) p++;
+                            if (b < mx) q++;
+                            if (cc < mx) r++;
+                        }
+                    }
+                    if (kk) {
+                        atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)i + E_K4], (unsigned long long)kk);
+                        atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)j + E_K4], (unsigned long long)kk);
+                        k4 += kk;
+                    }
+                    i++;
+                    j++;
+                }
+            }
+            if (opp) atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)e + E_OPP], (unsigned long long)opp);
+            if (outer) atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)e + E_OUTER], (unsigned long long)outer);
+            if (k4) atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)e + E_K4], (unsigned long long)k4);
+        }
+    }
+}
+
+// 4-cycles per edge, a block per pivot u (the highest vertex of the cycle)
+// with one dense counter array of n words per block: walk 1 counts c_w over
+// the wedges u-a-w (a, w below u); walk 2 credits each wedge's two edges
+// u-a and a-w with c_w - 1 (the cycles u-a-w-b, b another middle); walk 3
+// clears the counters.
+__global__ void __launch_bounds__(1024) k_e_c4(const Ctl* c, const int32_t* __restrict__ wlist,
+                                               const long long* __restrict__ U_off,
+                                               const uint32_t* __restrict__ U_col,
+                                               const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_all,
+                                               int n, long long* __restrict__ NE) {
+    pdl_enter();
+    const int nW = c->nW;
+    uint32_t* cnt = cnt_all + (size_t)blockIdx.x * (size_t)n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NWp = blockDim.x >> 5;
+    for (int pi = blockIdx.x; pi < nW; pi += gridDim.x) {
+        const uint32_t u = (uint32_t)wlist[pi];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        for (int pass = 0; pass < 3; pass++) {
+            for (int j = warp; j < nlow; j += NWp) {
+                const uint32_t a = vid(U_col[rb + j]);
+                const long long ab = U_off[a], ae = U_off[a + 1];
+                long long asum = 0;
+                for (long long q = ab + lane; q < ae; q += 32) {
+                    const uint32_t w = vid(U_col[q]);
+                    if (w >= u) break;  // rows are sorted: the rest is above u
+                    if (pass == 0) {
+                        atomicAdd(&cnt[w], 1u);
+                    } else if (pass == 1) {
+                        const long long x = (long long)__ldcg(&cnt[w]) - 1;
+                        if (x > 0) {
+                            atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)q + E_C4], (unsigned long long)x);
+                            asum += x;
+                        }
+                    } else {
+                        cnt[w] = 0u;
+                    }
+                }
+                if (pass == 1) {
+                    asum = (long long)warp_sum_u64((unsigned long long)asum);
+                    if (lane == 0 && asum)
+                        atomicAdd((unsigned long long*)&NE[NEROLE * (size_t)(rb + j) + E_C4], (unsigned long long)asum);
+                }
+            }
+            __threadfence();
+            __syncthreads();
+        }
+    }
+}
+
+// Orbit counts per edge by the triangular edge-role containment.  A warp
+// per vertex x, a lane per out-entry e = (x, y); the credits of the twin
+// entry (x in y's row) are added, the edge's row in the output is the rank
+// of its key among the sorted keys.  out[k row + j]: the ten edge orbits
+// (k = 10) or their sums per graphlet (k = 6); edges[2 row] = (lo, hi).
+__global__ void k_e_finalize(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
+                             const uint32_t* __restrict__ U_col, const int32_t* __restrict__ U_split,
+                             const uint32_t* __restrict__ tall, const long long* __restrict__ sdeg,
+                             const unsigned long long* __restrict__ T2, const long long* __restrict__ NE,
+                             const int32_t* __restrict__ iperm, const unsigned long long* __restrict__ skeys,
+                             int nb, long long m, int k, unsigned long long* __restrict__ out,
+                             int32_t* __restrict__ edges) {
+    pdl_enter();
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const uint32_t x = (uint32_t)wlist[i];
+        const long long dx = U_off[x + 1] - U_off[x], trx = (long long)(T2[x] / 2), sx = sdeg[x];
+        const unsigned long long ex = (unsigned long long)iperm[x];
+        for (long long e = U_off[x] + U_split[x] + lane; e < U_off[x + 1]; e += 32) {
+            const uint32_t y = vid(U_col[e]);
+            const long long yb = U_off[y];
+            const long long tw = yb + lower_bound_id(U_col + yb, U_split[y], x);
+            const long long dy = U_off[y + 1] - yb, t = tall[e];
+            const long long* ra = NE + NEROLE * (size_t)e;
+            const long long* rt = NE + NEROLE * (size_t)tw;
+            const long long n_opp = ra[E_OPP] + rt[E_OPP], n_outer = ra[E_OUTER] + rt[E_OUTER];
+            const long long n_c4 = ra[E_C4] + rt[E_C4], n_k4 = ra[E_K4] + rt[E_K4];
+            const long long n_pend = (sdeg[y] - (dx - 1) - t) + (sx - (dy - 1) - t);
+            const long long n_pmid = (dx - 1) * (dy - 1) - t;
+            const long long n_star = (dx - 1) * (dx - 2) / 2 + (dy - 1) * (dy - 2) / 2;
+            const long long n_tail = (trx - t) + ((long long)(T2[y] / 2) - t);
+            const long long n_att = t * (dx + dy - 4);
+            const long long n_chord = t * (t - 1) / 2;
+            const long long i9 = n_k4;
+            const long long i8 = n_chord - i9;
+            const long long i7 = n_outer - 4 * i9;
+            const long long i6 = n_att - 4 * i8 - i7 - 4 * i9;
+            const long long i5 = n_opp - i7 - 2 * i9;
+            const long long i4 = n_tail - i7 - 2 * i9;
+            const long long i3 = n_c4 - i7 - 2 * i9;
+            const long long i2 = n_star - i6 - i4 - 2 * i8 - i7 - 2 * i9;
+            const long long i1 = n_pmid - i3 - i6 - 2 * i8 - i7 - 2 * i9;
+            const long long i0 = n_pend - 2 * i3 - 2 * i5 - 2 * i4 - 3 * i7 - 4 * i9;
+            // rank of the key among the m sorted edge keys
+            const unsigned long long ey = (unsigned long long)iperm[y];
+            const unsigned long long lo = ex < ey ? ex : ey, hi = ex < ey ? ey : ex;
+            const unsigned long long key = (lo << nb) | hi;
+            long long a = 0, b = m;
+            while (a < b) {
+                const long long mid = (a + b) >> 1;
+                if (skeys[mid] < key) a = mid + 1;
+                else b = mid;
+            }
+            unsigned long long* o = out + (size_t)k * a;
+            if (k == 10) {
+                o[0] = (unsigned long long)i0; o[1] = (unsigned long long)i1; o[2] = (unsigned long long)i2;
+                o[3] = (unsigned long long)i3; o[4] = (unsigned long long)i4; o[5] = (unsigned long long)i5;
+                o[6] = (unsigned long long)i6; o[7] = (unsigned long long)i7; o[8] = (unsigned long long)i8;
+                o[9] = (unsigned long long)i9;
+            } else {
+                o[0] = (unsigned long long)(i0 + i1);
+                o[1] = (unsigned long long)i2;
+                o[2] = (unsigned long long)i3;
+                o[3] = (unsigned long long)(i4 + i5 + i6);
+                o[4] = (unsigned long long)(i7 + i8);
+                o[5] = (unsigned long long)i9;
+            }
+            if (edges) {
+                edges[2 * a] = (int32_t)lo;
+                edges[2 * a + 1] = (int32_t)hi;
+            }
+        }
+    }
+}
+
+int enqueue_edge_counts(const EdgeArgs& a, cudaStream_t s) {
+    const int gw = 8 * a.sms, tpb = 256;
+    int nl = 0;
+    pdl_launch(k_v_tsym, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tpack, a.tall);
+    pdl_launch(k_v_s, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.sdeg);
+    pdl_launch(k_e_keys, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.iperm, a.nb,
+               a.keys);
+    nl += 3;
+    nl += radix_sort_u64((uint64_t*)a.keys, (uint64_t*)a.keys_tmp, a.d_count, a.nU, 2 * a.nb, a.hist, a.sort_grid, s);
+    pdl_launch(k_e_tri_k4, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NE);
+    pdl_launch(k_e_c4, dim3(a.c4_blocks), dim3(1024), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n,
+               a.NE);
+    pdl_launch(k_e_finalize, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.sdeg,
+               a.T2, a.NE, a.iperm, a.keys, a.nb, a.m, a.orbits ? 10 : 6, a.out, a.edges);
+    nl += 3;
+    return nl;
+}
+
 int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s) {
     const int gw = 8 * a.sms, tpb = 256;
     int nl = 0;

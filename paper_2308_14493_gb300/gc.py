@@ -109,6 +109,8 @@ def load():
             lib.gc_counts_all.argtypes = [P, u64p]
             lib.gc_vertex_counts.argtypes = [P, u64p]
             lib.gc_vertex_orbits.argtypes = [P, u64p]
+            lib.gc_edge_counts.argtypes = [P, i32p, u64p]
+            lib.gc_edge_orbits.argtypes = [P, i32p, u64p]
             lib.gc_delete_vertices.argtypes = [P, i32p, ctypes.c_int64, u64p]
             lib.gc_add_vertices.argtypes = [P, ctypes.c_int64, i32p]
             lib.gc_num_vertices.argtypes = [P]
@@ -226,6 +228,26 @@ def gc_vertex_orbits(h, n: int) -> np.ndarray:
     out = np.zeros((max(n, 1), 11), np.uint64)
     _check(load().gc_vertex_orbits(h, _ptr(out, ctypes.c_uint64)), h)
     return out[:n]
+
+
+def _edge_rows(h, fn, k: int):
+    m = gc_num_edges(h)
+    edges = np.zeros((max(m, 1), 2), np.int32)
+    out = np.zeros((max(m, 1), k), np.uint64)
+    _check(fn(h, _ptr(edges, ctypes.c_int32), _ptr(out, ctypes.c_uint64)), h)
+    return edges[:m], out[:m]
+
+
+def gc_edge_counts(h):
+    """Per-edge graphlet counts of the current graph: (int32[m, 2] edges
+    lo < hi in increasing order, uint64[m, 6])."""
+    return _edge_rows(h, load().gc_edge_counts, 6)
+
+
+def gc_edge_orbits(h):
+    """Per-edge orbit counts (edge orbits 0..9) of the current graph:
+    (int32[m, 2] edges, uint64[m, 10])."""
+    return _edge_rows(h, load().gc_edge_orbits, 10)
 
 
 def gc_counts3(h) -> list[int]:
@@ -501,6 +523,12 @@ class Graph:
 
     def vertex_orbits(self):
         return gc_vertex_orbits(self.h, self.n)
+
+    def edge_counts(self):
+        return gc_edge_counts(self.h)
+
+    def edge_orbits(self):
+        return gc_edge_orbits(self.h)
 
     def count_static(self):
         return gc_count_static(self.h)

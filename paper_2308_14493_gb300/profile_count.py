@@ -1,12 +1,13 @@
 """Static count of a seeded Chung-Lu graph, repeated, for kernel profiling.
 
     python -m paper_2308_14493_gb300.profile_count --n 800000 --m 15000000 \\
-        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local] [--vertex]
+        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local] [--vertex | --edge]
 
 Opens the graph (one static count), then runs ``reps`` more static counts
 (or, with ``--batch``, ``reps`` sequential batches of that many updates, 60%
 insertions; with ``--local`` through the edge-local delta; with ``--vertex``
-the per-vertex graphlet counts) and prints the per-stage device times of
+the per-vertex graphlet counts, with ``--edge`` the per-edge orbit counts)
+and prints the per-stage device times of
 each call.  Used as the
 command under ncu; it runs the library exactly as a user would.
 """
@@ -38,6 +39,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick the bin boundaries first")
     ap.add_argument("--local", action="store_true", help="batches take the edge-local delta")
     ap.add_argument("--vertex", action="store_true", help="per-vertex graphlet counts instead of static counts")
+    ap.add_argument("--edge", action="store_true", help="per-edge orbit counts instead of static counts")
     ap.add_argument("--chunk-threshold", type=int, default=0,
                     help="wedge bound above which 4-cycle pivots use the chunked shared-memory kernel")
     a = ap.parse_args()
@@ -49,7 +51,11 @@ def main():
         if a.autotune:
             best, ms = g.autotune(reps=2)
             print(json.dumps({"autotune_ms": ms, "tuning": best}), flush=True)
-        if a.vertex:
+        if a.edge:
+            for _ in range(a.reps):
+                e, _o = g.edge_orbits()
+                print(json.dumps({"edge_orbits_ms": g.stats()["ms_device"], "edges": int(e.shape[0])}), flush=True)
+        elif a.vertex:
             for _ in range(a.reps):
                 v = g.vertex_counts()
                 print(json.dumps({"vertex_counts_ms": g.stats()["ms_device"], "vertices": int(v.shape[0])}),

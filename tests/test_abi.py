@@ -89,4 +89,7 @@ def test_null_handles_are_rejected():
     for name in ("gc_counts", "gc_counts3", "gc_counts_all", "gc_vertex_counts", "gc_vertex_orbits",
                  "gc_count_static"):
         assert getattr(lib, name)(None, p) == binding.GC_EINVAL, name
+    e = np.zeros(8, np.int32)
+    for name in ("gc_edge_counts", "gc_edge_orbits"):
+        assert getattr(lib, name)(None, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p) == binding.GC_EINVAL
     assert lib.gc_num_edges(None) == -1
