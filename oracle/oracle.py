@@ -284,13 +284,14 @@ def edge_orbits(row_ptr, col, pairs=None):
         if v not in Nu:
             raise ValueError(f"({u}, {v}) is not an edge")
         T = Nu & Nv
-        p_end = sum(len(N(w) - {u, v}) for w in Nv - {u}) + sum(len(N(w) - {u, v}) for w in Nu - {v})
-        p_mid = sum(len(Nv - {u, x}) for x in Nu - {v})
+        Nu_v, Nv_u = Nu - {v}, Nv - {u}   # (no set of a hub is copied per neighbour below)
+        p_end = sum(len(N(w) - {u, v}) for w in Nv_u) + sum(len(N(w) - {u, v}) for w in Nu_v)
+        p_mid = sum(len(Nv_u) - (x in Nv_u) for x in Nu_v)            # y in N(v) - {u, x}
         star = math.comb(len(Nu) - 1, 2) + math.comb(len(Nv) - 1, 2)
-        cyc = sum(len((N(w) & Nu) - {v}) for w in Nv - {u})
-        tail = sum(len(N(x) & (Nu - {v})) for x in Nu - {v}) // 2 + sum(len(N(x) & (Nv - {u})) for x in Nv - {u}) // 2
+        cyc = sum(len((N(w) & Nu) - {v}) for w in Nv_u)
+        tail = sum(len(N(x) & Nu_v) for x in Nu_v) // 2 + sum(len(N(x) & Nv_u) for x in Nv_u) // 2
         opp = sum(len(N(w) - {u, v}) for w in T)
-        att = sum(len(Nu - {v, w}) + len(Nv - {u, w}) for w in T)
+        att = sum((len(Nu_v) - (w in Nu_v)) + (len(Nv_u) - (w in Nv_u)) for w in T)   # N(u) - {v, w} and N(v) - {u, w}
         outer = sum(len((Nu & N(w)) - {v}) + len((Nv & N(w)) - {u}) for w in T)
         chord = math.comb(len(T), 2)
         k4 = sum(len(N(w) & T) for w in T) // 2
