@@ -444,19 +444,29 @@ def paper_regime(gcb, torch, n, keys, rp, col, stream, flush, static_ms):
     return out
 
 
-def vertex_counts_line(gcb, n, rp, col):
-    """Per-vertex graphlet counts of the graph (gc_vertex_counts): device time
-    of the per-vertex kernels (after the static pass they start from) and of
-    that static pass; the sum over vertices checked against four times the
-    global counts."""
+def local_counts_line(gcb, n, rp, col):
+    """Per-vertex graphlet counts (gc_vertex_counts) and per-edge orbit
+    counts (gc_edge_orbits) of the graph: device time of their kernels
+    (after the static pass they start from) and of that static pass; the
+    sums over vertices and over edges checked against the global counts."""
+    per_orbit = [(0, 2), (0, 1), (1, 3), (2, 4), (3, 1), (3, 1), (3, 2), (4, 4), (4, 1), (5, 6)]
     with gcb.Graph(n, rp, col) as g:
         g.vertex_counts()  # warm-up
         v = g.vertex_counts()
         ms_v = g.stats()["ms_device"]
+        F = g.counts()
+        ok_v = [int(x) for x in v.astype(object).sum(axis=0)] == [4 * x for x in F]
+        del v
+        g.edge_orbits()  # warm-up
+        e, o = g.edge_orbits()
+        ms_e = g.stats()["ms_device"]
+        ok_e = [int(x) for x in o.astype(object).sum(axis=0)] == [k * F[j] for j, k in per_orbit]
+        m = int(e.shape[0])
+        del e, o
         g.count_static()
         ms_s = g.stats()["ms_device"]
-        ok = [int(x) for x in v.astype(object).sum(axis=0)] == [4 * x for x in g.counts()]
-    return {"vertices": n, "per_vertex_kernels_ms": ms_v, "static_pass_ms": ms_s, "sum_is_4x_counts": ok}
+    return {"vertices": n, "edges": m, "per_vertex_kernels_ms": ms_v, "per_edge_kernels_ms": ms_e,
+            "static_pass_ms": ms_s, "vertex_sums_match_counts": ok_v, "edge_sums_match_counts": ok_e}
 
 
 def c4_block(gcb, torch, stream, flush, peak, peak_kind):
@@ -550,7 +560,10 @@ def gpu_arm(args):
                 except Exception as e:  # pragma: no cover - reported, not hidden
                     pvb[tag] = {"error": str(e)}
             sec["c2_plain_vs_batched"] = pvb
-            sec["c2_vertex_counts"] = vertex_counts_line(gcb, n, rp, col)
+            try:
+                sec["c2_local_counts"] = local_counts_line(gcb, n, rp, col)
+            except Exception as e:  # pragma: no cover - reported, not hidden
+                sec["c2_local_counts"] = {"error": str(e)}
         if not args.no_large:
             try:
                 sec["c4_independent"] = c4_block(gcb, torch, stream, flush, peak, peak_kind)
@@ -568,9 +581,9 @@ def gpu_arm(args):
                 except Exception as e:  # pragma: no cover
                     sec["c3_paper_batch_sizes"] = {"error": str(e)}
                 try:
-                    sec["c3_vertex_counts"] = vertex_counts_line(gcb, n3, rp3, col3)
+                    sec["c3_local_counts"] = local_counts_line(gcb, n3, rp3, col3)
                 except Exception as e:  # pragma: no cover
-                    sec["c3_vertex_counts"] = {"error": str(e)}
+                    sec["c3_local_counts"] = {"error": str(e)}
                 sec["c3"] = {"workload": sp3["desc"], "plain": {"value": s3["value"], "ms_per_batch": s3["ms_per_step"],
                                                                  "p99_ms": s3["p99_ms"]},
                              "batched": {"value": s3["edges"] / secs3, "ms_per_batch": 1e3 * secs3 / 3},
