@@ -2,7 +2,9 @@
 against the oracle after each step: plain batches of every size (region and
 edge-local forms), what-if batches, batched runs (sequential and
 independent), vertex deletions and insertions, tuning changes and static
-recounts.  Counts must stay bit-exact throughout."""
+recounts.  Counts must stay bit-exact throughout, and (in two of the
+programs) the per-vertex and per-edge orbit counts of the final graph must
+equal the oracle's."""
 import numpy as np
 import pytest
 
@@ -87,3 +89,11 @@ def test_random_program_of_calls(gcb, seed):
         assert g.counts_all() == oracle.counts_all(og.row_ptr, og.col)
         grp, gcol = g.export_csr()
         assert np.array_equal(grp.astype(np.int64), og.row_ptr) and np.array_equal(gcol, og.col)
+        if seed > 2:   # the oracle's local counts take seconds: two programs check them
+            return
+        # local counts of the final graph (new vertices and relocated rows included)
+        assert g.vertex_orbits().astype(np.int64).tolist() == oracle.vertex_orbits(og.row_ptr, og.col)
+        edges, orb = g.edge_orbits()
+        keys, rows = oracle.edge_orbits(og.row_ptr, og.col)
+        assert edges.tolist() == [list(k) for k in keys]
+        assert orb.astype(np.int64).tolist() == rows
