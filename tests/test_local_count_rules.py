@@ -111,6 +111,59 @@ def edge_rows_by_kernel_rules(n, edges, rank):
     return sorted(t), rows
 
 
+def vertex_rows_by_kernel_rules(n, edges, rank):
+    N = _graph(n, edges)
+    d = [len(x) for x in N]
+    key = lambda a, b: (min(a, b), max(a, b))
+    t = {key(a, b): len(N[a] & N[b]) for a, b in edges}
+    tri = [sum(t[key(x, w)] for w in N[x]) // 2 for x in range(n)]
+    s = [sum(d[w] - 1 for w in N[x]) for x in range(n)]
+    d2 = [0] * n
+    k4 = [0] * n
+    tris, k4s = _cliques_and_triangles(n, N, rank)
+    for x, y, z in tris:   # each corner: t of the opposite edge - 1
+        d2[x] += t[key(y, z)] - 1
+        d2[y] += t[key(x, z)] - 1
+        d2[z] += t[key(x, y)] - 1
+    for q in k4s:
+        for x in q:
+            k4[x] += 1
+    _, c4 = _pivot_c4(n, N, rank)
+    rows = []
+    for v in range(n):
+        dv = d[v]
+        pe = sum(s[u] - (dv - 1) for u in N[v]) - 2 * tri[v]
+        pm = sum((dv - 1) * (d[u] - 1) - t[key(v, u)] for u in N[v])
+        sl = sum(math.comb(d[u] - 1, 2) for u in N[v])
+        sc = math.comb(dv, 3)
+        tl = sum(tri[u] - t[key(v, u)] for u in N[v])
+        to = sum(t[key(v, u)] * (d[u] - 2) for u in N[v])
+        ta = tri[v] * (dv - 2)
+        d3 = sum(math.comb(t[key(v, u)], 2) for u in N[v])
+        o14 = k4[v]
+        o13 = d3 - 3 * o14
+        o12 = d2[v] - 3 * o14
+        o11 = ta - 2 * o13 - 3 * o14
+        o10 = to - 2 * o12 - 2 * o13 - 6 * o14
+        o9 = tl - 2 * o12 - 3 * o14
+        o8 = c4[v] - o12 - o13 - 3 * o14
+        o7 = sc - o11 - o13 - o14
+        o6 = sl - o9 - o10 - 2 * o12 - o13 - 3 * o14
+        o5 = pm - 2 * o8 - o10 - 2 * o11 - 2 * o12 - 4 * o13 - 6 * o14
+        o4 = pe - 2 * o8 - 2 * o9 - o10 - 4 * o12 - 2 * o13 - 6 * o14
+        rows.append([o4, o5, o6, o7, o8, o9, o10, o11, o12, o13, o14])
+    return rows
+
+
+def test_vertex_kernel_rules_match_the_census():
+    rng = np.random.default_rng(505)
+    for trial in range(60):
+        n = int(rng.integers(4, 17))
+        edges = random_graph(rng, n, float(rng.uniform(0.05, 0.95)))
+        rank = [int(x) for x in rng.permutation(n)]
+        assert vertex_rows_by_kernel_rules(n, edges, rank) == brute.vertex_orbit_census(n, edges), trial
+
+
 def test_edge_kernel_rules_match_the_census():
     rng = np.random.default_rng(404)
     for trial in range(60):
