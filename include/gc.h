@@ -187,10 +187,10 @@ int gc_vertex_orbits(gc_graph *g, uint64_t *out);
    each connected 4-vertex subgraph through the edge, counted by the edge's
    role in them, invert with a triangular matrix.  Summed over the edges,
    type k gives (3, 3, 4, 4, 5, 6)[k] x gc_counts.  Runs a static pass plus
-   the per-edge kernels (device scratch of about 60 bytes per adjacency
-   entry plus the output, and one 4-byte counter array per 4-cycle block,
-   2 GB at most, all freed on return); the maintained counts are not
-   changed.  gc_batch_stats().ms_device gives the device time of the
+   the per-edge kernels (device scratch of 52 bytes per adjacency entry,
+   two per edge; 8 bytes per vertex; the device copy of the output; and one
+   4-byte counter array per 4-cycle block, 2 GB at most; all freed on
+   return); the maintained counts are not changed.  gc_batch_stats().ms_device gives the device time of the
    per-edge kernels. */
 int gc_edge_counts(gc_graph *g, int32_t *edges, uint64_t *out);
 
