@@ -349,7 +349,11 @@ typedef struct {
     int64_t c4_chunk_max;   /* 0 = no upper bound */
     int64_t local_max_pairs; /* batches of at most this many pairs take the edge-local delta
                                 (gc_options.local_max_pairs); 0 = never */
-    int64_t reserved[2];
+    int64_t local_c4_heavy_min; /* gc_vertex_* and gc_edge_*: 4-cycle pivots with w~ at least this
+                                   are walked 8 at a time by the whole GPU, each with its own
+                                   counter array in L2; the others by one CTA each on per-CTA
+                                   arrays; 0 = never (default 65536) */
+    int64_t reserved[1];
 } gc_tuning;
 
 int gc_get_tuning(const gc_graph *g, gc_tuning *t);

@@ -89,6 +89,7 @@ struct gc_graph {
     int cta_groups = 0;
     Buf<int32_t> chunk_table;            // run bounds of the chunked 4-cycle kernel
     Tuning tune = default_tuning();     // bin boundaries of the counting pass
+    long long loc_heavy_min = 65536;   // w~ from which local-count 4-cycle pivots take k_c4_group (0 = never)
     int32_t* bins = nullptr;             // NBINS * n work lists of the counting pass
     // captured batch graph and the shape it was captured for
     cudaGraphExec_t gexec = nullptr;
@@ -1541,6 +1542,32 @@ int gc_counts_all(const gc_graph* g, uint64_t out[22]) {
     return GC_OK;
 }
 
+// Scratch of the heavy 4-cycle pivots of the local counts (none when the
+// grouped walk is off); returns false when an allocation failed.
+static bool alloc_heavy(gc_graph* g, HeavyC4& h) {
+    h.heavy_min = g->loc_heavy_min;
+    h.U_wt = g->U_wt;
+    h.heavy = nullptr;
+    h.hlist = nullptr;
+    h.hcount = nullptr;
+    h.cnt_g = nullptr;
+    if (h.heavy_min <= 0) return true;
+    const size_t n = (size_t)std::max(g->n, 1);
+    h.heavy = (uint8_t*)dalloc(g, n);
+    h.hlist = (int32_t*)dalloc(g, 4 * n);
+    h.hcount = (int*)dalloc(g, 16);
+    h.cnt_g = (uint32_t*)dalloc(g, 4 * (size_t)C4G * n);
+    return h.heavy && h.hlist && h.hcount && h.cnt_g &&
+           cudaMemsetAsync(h.cnt_g, 0, 4 * (size_t)C4G * n, g->s) == cudaSuccess;
+}
+
+static void free_heavy(gc_graph* g, HeavyC4& h) {
+    if (h.heavy) dfree(g, h.heavy);
+    if (h.hlist) dfree(g, h.hlist);
+    if (h.hcount) dfree(g, h.hcount);
+    if (h.cnt_g) dfree(g, h.cnt_g);
+}
+
 static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
     if (!g || (!out && g->n > 0)) return GC_EINVAL;
     if (!on_device(g)) {
@@ -1563,14 +1590,17 @@ static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
     long long* NV = (long long*)dalloc(g, 88 * n);
     uint32_t* cnt = (uint32_t*)dalloc(g, 4 * n * (size_t)blocks);
     unsigned long long* dout = (unsigned long long*)dalloc(g, 8 * (size_t)k * n);
+    HeavyC4 hv;
+    const bool hv_ok = alloc_heavy(g, hv);
     auto cleanup = [&]() {
         dfree(g, tall);
         dfree(g, sdeg);
         dfree(g, NV);
         dfree(g, cnt);
         dfree(g, dout);
+        free_heavy(g, hv);
     };
-    if (!tall || !sdeg || !NV || !cnt || !dout) {
+    if (!tall || !sdeg || !NV || !cnt || !dout || !hv_ok) {
         cleanup();
         return nomem(g, "per-vertex counts");
     }
@@ -1597,8 +1627,10 @@ static int vertex_counts(gc_graph* g, uint64_t* out, int orbits) {
     va.out = dout;
     va.orbits = orbits;
     va.sms = g->sms;
+    va.hv = hv;
     cudaError_t ce = cudaEventRecord(g->e0, s);
     g->launches = enqueue_vertex_counts(va, s);
+    if (g->launches < 0 && ce == cudaSuccess) ce = cudaErrorUnknown;
     if (ce == cudaSuccess) ce = cudaEventRecord(g->e1, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * n, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1648,7 +1680,10 @@ static int edge_counts(gc_graph* g, int32_t* edges, uint64_t* out, int orbits) {
     uint32_t* cnt = (uint32_t*)dalloc(g, 4 * n * (size_t)blocks);
     unsigned long long* dout = (unsigned long long*)dalloc(g, 8 * (size_t)k * (size_t)m);
     int32_t* dedges = edges ? (int32_t*)dalloc(g, 8 * (size_t)m) : nullptr;
+    HeavyC4 hv;
+    const bool hv_ok = alloc_heavy(g, hv);
     auto cleanup = [&]() {
+        free_heavy(g, hv);
         dfree(g, tall);
         dfree(g, sdeg);
         dfree(g, NE);
@@ -1659,7 +1694,7 @@ static int edge_counts(gc_graph* g, int32_t* edges, uint64_t* out, int orbits) {
         dfree(g, dout);
         if (dedges) dfree(g, dedges);
     };
-    if (!tall || !sdeg || !NE || !keys || !ktmp || !hist || !cnt || !dout || (edges && !dedges)) {
+    if (!tall || !sdeg || !NE || !keys || !ktmp || !hist || !cnt || !dout || (edges && !dedges) || !hv_ok) {
         cleanup();
         return nomem(g, "per-edge counts");
     }
@@ -1696,8 +1731,10 @@ static int edge_counts(gc_graph* g, int32_t* edges, uint64_t* out, int orbits) {
     ea.edges = dedges;
     ea.orbits = orbits;
     ea.sms = g->sms;
+    ea.hv = hv;
     cudaError_t ce = cudaEventRecord(g->e0, s);
     g->launches = enqueue_edge_counts(ea, s);
+    if (g->launches < 0 && ce == cudaSuccess) ce = cudaErrorUnknown;
     if (ce == cudaSuccess) ce = cudaEventRecord(g->e1, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, 8 * (size_t)k * (size_t)m, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess && edges) ce = cudaMemcpyAsync(edges, dedges, 8 * (size_t)m, cudaMemcpyDeviceToHost, s);
@@ -2073,7 +2110,7 @@ int gc_export_csr(gc_graph* g, int32_t* row_ptr, int32_t* col) {
     return GC_OK;
 }
 
-static void tuning_to_abi(const Tuning& t, long long local_max_pairs, gc_tuning* o) {
+static void tuning_to_abi(const Tuning& t, long long local_max_pairs, long long heavy_min, gc_tuning* o) {
     std::memset(o, 0, sizeof(*o));
     o->tri_warp_max = t.tri_warp_max;
     o->tri_small_max = t.tri_small_max;
@@ -2085,11 +2122,12 @@ static void tuning_to_abi(const Tuning& t, long long local_max_pairs, gc_tuning*
     o->c4_chunk_min = t.c4_chunk_min >= NEVER ? 0 : t.c4_chunk_min;
     o->c4_chunk_max = t.c4_chunk_max >= NEVER ? 0 : t.c4_chunk_max;
     o->local_max_pairs = local_max_pairs;
+    o->local_c4_heavy_min = heavy_min;
 }
 
 int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
-    tuning_to_abi(g->tune, g->opt.local_max_pairs, t);
+    tuning_to_abi(g->tune, g->opt.local_max_pairs, g->loc_heavy_min, t);
     return GC_OK;
 }
 
@@ -2097,8 +2135,8 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
     if (t->tri_warp_max < 1 || t->tri_small_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
         t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0 || t->c4_chunk_max < 0 ||
-        t->local_max_pairs < 0) {
-        g->err = "tuning: every bound must be positive (c4_chunk_min and local_max_pairs may be 0)";
+        t->local_max_pairs < 0 || t->local_c4_heavy_min < 0) {
+        g->err = "tuning: every bound must be positive (c4_chunk_min, local_max_pairs and local_c4_heavy_min may be 0)";
         return GC_EINVAL;
     }
     Tuning n;
@@ -2114,6 +2152,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (n.c4_chunk_min < NEVER && !ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     g->tune = n;
     g->opt.local_max_pairs = (int32_t)std::min<int64_t>(t->local_max_pairs, INT32_MAX);
+    g->loc_heavy_min = t->local_c4_heavy_min;
     return GC_OK;
 }
 
@@ -2307,7 +2346,7 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     g->tune = cur;
     rc = calibrate_local(g, reps);
     if (rc) return rc;
-    if (best) tuning_to_abi(cur, g->opt.local_max_pairs, best);
+    if (best) tuning_to_abi(cur, g->opt.local_max_pairs, g->loc_heavy_min, best);
     if (best_ms) *best_ms = cur_ms;
     return GC_OK;
 }

@@ -147,6 +147,20 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
                   int commit);
 
 // Per-vertex graphlet counts of a static pass (gc_vertex.cu).
+// Heavy 4-cycle pivots of the per-vertex and per-edge counts (gc_vertex.cu):
+// pivots with w~ >= heavy_min are walked C4G at a time by the whole grid,
+// each with its own counter array in cnt_g; heavy_min = 0 leaves every
+// pivot to the per-block walk.
+constexpr int C4G = 8;
+struct HeavyC4 {
+    long long heavy_min;
+    const long long* U_wt;         // w~ per pivot (static pass)
+    uint8_t* heavy;                // n flags
+    int32_t* hlist;                // n
+    int* hcount;                   // 1
+    uint32_t* cnt_g;               // C4G * n, zeroed
+};
+
 struct VertexArgs {
     Ctl* ctl;
     const int32_t* wlist;          // all vertices (c->nW = n)
@@ -165,7 +179,9 @@ struct VertexArgs {
     unsigned long long* out;       // 6 n (graphlets) or 11 n (orbits), by external id
     int orbits;
     int sms;
+    HeavyC4 hv;
 };
+// Returns the kernels launched, or -1 on a CUDA error.
 int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s);
 
 struct EdgeArgs {
@@ -194,7 +210,9 @@ struct EdgeArgs {
     int32_t* edges;                // 2 m: (lo, hi) per output row
     int orbits;
     int sms;
+    HeavyC4 hv;
 };
+// Returns the kernels launched, or -1 on a CUDA error.
 int enqueue_edge_counts(const EdgeArgs& a, cudaStream_t s);
 
 // Enqueue the counting kernels (binning, triangles / 4-cliques, 4-cycles,

@@ -31,6 +31,8 @@ namespace gcx {
 
 // role slots of NV, in orbit order 4..14
 enum { R_PEND, R_PMID, R_SLEAF, R_SCTR, R_C4, R_TTAIL, R_TOTH, R_TATT, R_D2, R_D3, R_K4, NROLE };
+// per-entry credit slots of the per-edge counts (the two entries of an edge are added at the end)
+enum { E_OPP, E_OUTER, E_C4, E_K4, NEROLE };
 
 // t of every entry (out-entries carry it; an in-entry reads its twin).
 __global__ void k_v_tsym(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
@@ -194,7 +196,8 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
                                                const long long* __restrict__ U_off,
                                                const uint32_t* __restrict__ U_col,
                                                const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_all,
-                                               int n, long long* __restrict__ NV) {
+                                               int n, const uint8_t* __restrict__ heavy,
+                                               long long* __restrict__ NV) {
     pdl_enter();
     const int nW = c->nW;
     uint32_t* cnt = cnt_all + (size_t)blockIdx.x * (size_t)n;
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
     __shared__ unsigned long long s_u[32];
     for (int pi = blockIdx.x; pi < nW; pi += gridDim.x) {
         const uint32_t u = (uint32_t)wlist[pi];
+        if (heavy && heavy[u]) continue;  // taken by k_c4_group (same for the whole block)
         const long long rb = U_off[u];
         const int nlow = U_split[u];
         unsigned long long usum = 0;
@@ -245,6 +249,130 @@ __global__ void __launch_bounds__(1024) k_v_c4(const Ctl* c, const int32_t* __re
         }
         __syncthreads();
     }
+}
+
+// Heavy 4-cycle pivots of the local counts: w~(u) (the sum of the degrees
+// of u's lower neighbours, from the static pass) at least heavy_min.  They
+// are listed for k_c4_group and flagged so that the per-block walk skips
+// them.
+__global__ void k_c4_heavy_mark(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_wt,
+                                long long heavy_min, uint8_t* __restrict__ heavy, int32_t* __restrict__ hlist,
+                                int* __restrict__ hcount) {
+    pdl_enter();
+    const int nW = c->nW;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x) {
+        const int32_t u = wlist[i];
+        const bool h = U_wt[u] >= heavy_min;
+        heavy[u] = h ? 1 : 0;
+        if (h) hlist[atomicAdd(hcount, 1)] = u;
+    }
+}
+
+// One walk of the 4-cycle counting for up to C4G heavy pivots at once
+// (hlist[first .. first + count)), each with its own dense counter array of
+// n words (C4G arrays of 4 n bytes stay resident in L2 on graphs of a few
+// million vertices).  The whole grid shares the work: the (pivot, lower
+// neighbour a) pairs of the group are numbered and dealt to warps, the
+// lanes of a warp walk a's row below the pivot.  The three walks are three
+// launches (pass 0 count c_w, 1 credit c_w - 1, 2 clear), so the kernel
+// boundary is the only barrier between them.  EDGE: credits go to the two
+// entries of each wedge (per-edge 4-cycle role), else to the middle vertex
+// a in pass 1 and to the corners w and u with C(c_w, 2) in pass 2.
+template <bool EDGE>
+__global__ void k_c4_group(const int32_t* __restrict__ hlist, int first, int count,
+                           const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
+                           const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_g, int n, int pass,
+                           long long* __restrict__ acc) {
+    pdl_enter();
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    // lane p < count holds slot p: its pivot and the inclusive prefix of the
+    // lower-neighbour counts
+    uint32_t up = 0;
+    long long nl = 0;
+    if (lane < count) {
+        up = (uint32_t)hlist[first + lane];
+        nl = U_split[up];
+    }
+    long long incl = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const long long total = __shfl_sync(FULL, incl, 31);
+    const long long excl = incl - nl;
+    for (long long k = gwarp; k < total; k += nwarps) {
+        const int p = __popc(__ballot_sync(FULL, incl <= k));  // the slot holding pair k
+        const uint32_t u = __shfl_sync(FULL, up, p);
+        const long long j = k - __shfl_sync(FULL, excl, p);
+        uint32_t* cnt = cnt_g + (size_t)p * (size_t)n;
+        const long long ea = U_off[u] + j;  // entry (u, a)
+        const uint32_t a = vid(U_col[ea]);
+        const long long ab = U_off[a], ae = U_off[a + 1];
+        long long asum = 0;
+        unsigned long long usum = 0;
+        for (long long q = ab + lane; q < ae; q += 32) {
+            const uint32_t w = vid(U_col[q]);
+            if (w >= u) break;  // rows are sorted: the rest is above u
+            if (pass == 0) {
+                atomicAdd(&cnt[w], 1u);
+            } else if (pass == 1) {
+                const long long x = (long long)__ldcg(&cnt[w]) - 1;
+                if (x > 0) {
+                    if (EDGE) atomicAdd((unsigned long long*)&acc[NEROLE * (size_t)q + E_C4], (unsigned long long)x);
+                    asum += x;
+                }
+            } else if (EDGE) {
+                cnt[w] = 0u;
+            } else {
+                const uint32_t old = atomicExch(&cnt[w], 0u);
+                if (old >= 2) {
+                    const unsigned long long cy = (unsigned long long)old * (old - 1) / 2;
+                    atomicAdd((unsigned long long*)&acc[NROLE * (size_t)w + R_C4], cy);
+                    usum += cy;
+                }
+            }
+        }
+        if (pass == 1) {
+            asum = (long long)warp_sum_u64((unsigned long long)asum);
+            if (lane == 0 && asum) {
+                if (EDGE) atomicAdd((unsigned long long*)&acc[NEROLE * (size_t)ea + E_C4], (unsigned long long)asum);
+                else atomicAdd((unsigned long long*)&acc[NROLE * (size_t)a + R_C4], (unsigned long long)asum);
+            }
+        } else if (pass == 2 && !EDGE) {
+            usum = warp_sum_u64(usum);
+            if (lane == 0 && usum) atomicAdd((unsigned long long*)&acc[NROLE * (size_t)u + R_C4], usum);
+        }
+    }
+}
+
+// The heavy pivots: mark them, read their number back, then three launches
+// per group of C4G.  Returns the launches made, or -1 on a CUDA error.
+template <bool EDGE>
+static int enqueue_heavy_c4(const HeavyC4& h, Ctl* ctl, const int32_t* wlist, const long long* U_off,
+                            const uint32_t* U_col, const int32_t* U_split, int n, int sms, long long* acc,
+                            cudaStream_t s) {
+    if (h.heavy_min <= 0) return 0;
+    int nl = 0;
+    if (cudaMemsetAsync(h.hcount, 0, sizeof(int), s) != cudaSuccess) return -1;
+    pdl_launch(k_c4_heavy_mark, dim3(std::max(1, std::min(8 * sms, (n + 255) / 256))), dim3(256), 0, s, ctl, wlist,
+               h.U_wt, h.heavy_min, h.heavy, h.hlist, h.hcount);
+    nl++;
+    int H = 0;
+    if (cudaMemcpyAsync(&H, h.hcount, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    for (int first = 0; first < H; first += C4G) {
+        const int cnt = std::min(C4G, H - first);
+        for (int pass = 0; pass < 3; pass++) {
+            pdl_launch(k_c4_group<EDGE>, dim3(8 * sms), dim3(256), 0, s, (const int32_t*)h.hlist, first, cnt, U_off,
+                       U_col, U_split, h.cnt_g, n, pass, acc);
+            nl++;
+        }
+    }
+    return nl;
 }
 
 // Orbit counts per vertex by the triangular role containment; out[k v + j]
@@ -296,8 +424,6 @@ __global__ void k_v_finalize(const long long* __restrict__ NV, int n, const int3
 //   diamond outer  sum over triangles {u, v, w} of t_uw + t_vw - 2
 //   chord C(t, 2);  4-clique credited by the clique listing
 // Credits land on either entry of the edge; the finalize adds both.
-
-enum { E_OPP, E_OUTER, E_C4, E_K4, NEROLE };
 
 // One sort key per entry: the out-entry (x < y) of an edge gets its
 // external pair (lo << nb) | hi, every in-entry the largest nb-bit pair,
@@ -409,13 +535,15 @@ __global__ void __launch_bounds__(1024) k_e_c4(const Ctl* c, const int32_t* __re
                                                const long long* __restrict__ U_off,
                                                const uint32_t* __restrict__ U_col,
                                                const int32_t* __restrict__ U_split, uint32_t* __restrict__ cnt_all,
-                                               int n, long long* __restrict__ NE) {
+                                               int n, const uint8_t* __restrict__ heavy,
+                                               long long* __restrict__ NE) {
     pdl_enter();
     const int nW = c->nW;
     uint32_t* cnt = cnt_all + (size_t)blockIdx.x * (size_t)n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NWp = blockDim.x >> 5;
     for (int pi = blockIdx.x; pi < nW; pi += gridDim.x) {
         const uint32_t u = (uint32_t)wlist[pi];
+        if (heavy && heavy[u]) continue;  // taken by k_c4_group (same for the whole block)
         const long long rb = U_off[u];
         const int nlow = U_split[u];
         for (int pass = 0; pass < 3; pass++) {
@@ -538,8 +666,11 @@ int enqueue_edge_counts(const EdgeArgs& a, cudaStream_t s) {
     nl += 3;
     nl += radix_sort_u64((uint64_t*)a.keys, (uint64_t*)a.keys_tmp, a.d_count, a.nU, 2 * a.nb, a.hist, a.sort_grid, s);
     pdl_launch(k_e_tri_k4, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NE);
+    const int nh = enqueue_heavy_c4<true>(a.hv, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.n, a.sms, a.NE, s);
+    if (nh < 0) return -1;
+    nl += nh;
     pdl_launch(k_e_c4, dim3(a.c4_blocks), dim3(1024), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n,
-               a.NE);
+               nh > 0 ? (const uint8_t*)a.hv.heavy : nullptr, a.NE);
     pdl_launch(k_e_finalize, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.sdeg,
                a.T2, a.NE, a.iperm, a.keys, a.nb, a.m, a.orbits ? 10 : 6, a.out, a.edges);
     nl += 3;
@@ -553,8 +684,11 @@ int enqueue_vertex_counts(const VertexArgs& a, cudaStream_t s) {
     pdl_launch(k_v_s, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.sdeg);
     pdl_launch(k_v_terms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.tall, a.sdeg, a.T2, a.NV);
     pdl_launch(k_v_tri_k4, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.tall, a.NV);
+    const int nh = enqueue_heavy_c4<false>(a.hv, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.n, a.sms, a.NV, s);
+    if (nh < 0) return -1;
+    nl += nh;
     pdl_launch(k_v_c4, dim3(a.c4_blocks), dim3(1024), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.cnt, a.n,
-               a.NV);
+               nh > 0 ? (const uint8_t*)a.hv.heavy : nullptr, a.NV);
     pdl_launch(k_v_finalize, dim3((a.n + 255) / 256), dim3(256), 0, s, a.NV, a.n, a.iperm, a.orbits ? 11 : 6, a.out);
     nl += 6;
     return nl;

@@ -40,6 +40,8 @@ def main():
     ap.add_argument("--local", action="store_true", help="batches take the edge-local delta")
     ap.add_argument("--vertex", action="store_true", help="per-vertex graphlet counts instead of static counts")
     ap.add_argument("--edge", action="store_true", help="per-edge orbit counts instead of static counts")
+    ap.add_argument("--heavy-min", default="",
+                    help="with --vertex / --edge: comma-separated local_c4_heavy_min values, each timed in turn")
     ap.add_argument("--chunk-threshold", type=int, default=0,
                     help="wedge bound above which 4-cycle pivots use the chunked shared-memory kernel")
     a = ap.parse_args()
@@ -51,15 +53,23 @@ def main():
         if a.autotune:
             best, ms = g.autotune(reps=2)
             print(json.dumps({"autotune_ms": ms, "tuning": best}), flush=True)
-        if a.edge:
-            for _ in range(a.reps):
-                e, _o = g.edge_orbits()
-                print(json.dumps({"edge_orbits_ms": g.stats()["ms_device"], "edges": int(e.shape[0])}), flush=True)
-        elif a.vertex:
-            for _ in range(a.reps):
-                v = g.vertex_counts()
-                print(json.dumps({"vertex_counts_ms": g.stats()["ms_device"], "vertices": int(v.shape[0])}),
-                      flush=True)
+        heavy = [int(x) for x in a.heavy_min.split(",") if x] or [None]
+        if a.edge or a.vertex:
+            for hm, edge in [(h, ed) for ed in ([False] if a.vertex else []) + ([True] if a.edge else [])
+                             for h in heavy]:
+                if hm is not None:
+                    g.set_tuning(local_c4_heavy_min=hm)
+                for _ in range(a.reps):
+                    if edge:
+                        e, _o = g.edge_orbits()
+                        rec = {"edge_orbits_ms": g.stats()["ms_device"], "edges": int(e.shape[0])}
+                        del e, _o
+                    else:
+                        v = g.vertex_counts()
+                        rec = {"vertex_counts_ms": g.stats()["ms_device"], "vertices": int(v.shape[0])}
+                    rec["local_c4_heavy_min"] = g.tuning()["local_c4_heavy_min"]
+                    rec["launches"] = g.stats()["launches"]
+                    print(json.dumps(rec), flush=True)
         elif a.batch:
             for ins, dels in gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1):
                 g.apply(ins, dels)

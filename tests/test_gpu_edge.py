@@ -112,3 +112,20 @@ def test_edge_orbits_full_size_sample_and_sums(gcb, name):
         keys_s, rows = oracle.edge_orbits(rp, col, [tuple(edges[i]) for i in pick])
         assert [list(k) for k in keys_s] == edges[pick].tolist()
         assert orb[pick].astype(np.int64).tolist() == rows
+
+
+@pytest.mark.parametrize("heavy_min", [0, 1, 40])
+def test_edge_orbits_every_4cycle_walk(gcb, heavy_min):
+    """Per-edge counts with every pivot on the per-CTA arrays (0), every
+    pivot in the grouped L2 walk (1), and a split (40)."""
+    rng = np.random.default_rng(70 + heavy_min)
+    cases = [(n, random_graph(rng, n, float(rng.uniform(0.05, 0.7)))) for n in (12, 40, 150)]
+    n = 300
+    edges = {(0, v) for v in range(1, n)} | {(a, b) for a in range(1, 15) for b in range(a + 1, 15)}
+    edges |= {(a, b) for a in range(100, 110) for b in range(200, 210)}
+    cases.append((n, sorted(edges)))
+    for n, edges in cases:
+        rp, col = csr_from_edges(n, edges)
+        with gcb.Graph(n, rp, col) as g:
+            g.set_tuning(local_c4_heavy_min=heavy_min)
+            _check(g, rp, col)

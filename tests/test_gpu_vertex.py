@@ -93,3 +93,22 @@ def test_vertex_orbits_random_and_planted(gcb):
             sums = np.stack([orb[:, 0] + orb[:, 1], orb[:, 2] + orb[:, 3], orb[:, 4],
                              orb[:, 5] + orb[:, 6] + orb[:, 7], orb[:, 8] + orb[:, 9], orb[:, 10]], axis=1)
             assert np.array_equal(per, sums)
+
+
+@pytest.mark.parametrize("heavy_min", [0, 1, 40])
+def test_vertex_orbits_every_4cycle_walk(gcb, heavy_min):
+    """The 4-cycle walk of the local counts: every pivot on the per-CTA
+    arrays (0), every pivot with lower neighbours in the grouped L2 walk
+    (1), and a split between the two (40)."""
+    rng = np.random.default_rng(90 + heavy_min)
+    cases = [(n, random_graph(rng, n, float(rng.uniform(0.05, 0.7)))) for n in (12, 40, 150)]
+    n = 300
+    edges = {(0, v) for v in range(1, n)} | {(a, b) for a in range(1, 15) for b in range(a + 1, 15)}
+    edges |= {(a, b) for a in range(100, 110) for b in range(200, 210)}
+    cases.append((n, sorted(edges)))
+    for n, edges in cases:
+        rp, col = csr_from_edges(n, edges)
+        with gcb.Graph(n, rp, col) as g:
+            g.set_tuning(local_c4_heavy_min=heavy_min)
+            assert g.tuning()["local_c4_heavy_min"] == heavy_min
+            assert g.vertex_orbits().astype(np.int64).tolist() == oracle.vertex_orbits(rp, col)
