@@ -23,7 +23,12 @@
 //   4-clique listed once (oriented), each of its four vertices credited
 // NV[v] holds the eleven role counts in orbit order.  The input is the
 // union graph U of a static count (both flags on every entry, t of each
-// out-entry in tpack, T2 filled).
+// out-entry in tpack, T2 filled, w~ per pivot in U_wt).
+//
+// The second half of the file gives the same per edge (ten edge orbits,
+// k_e_*), and the 4-cycle walk of the heavy pivots shared by both
+// (k_c4_group: a few pivots at a time over the whole grid, their counters
+// resident in L2).
 #include "gc_internal.cuh"
 #include "gc_kernels.cuh"
 
