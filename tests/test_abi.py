@@ -93,3 +93,54 @@ def test_null_handles_are_rejected():
     for name in ("gc_edge_counts", "gc_edge_orbits"):
         assert getattr(lib, name)(None, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p) == binding.GC_EINVAL
     assert lib.gc_num_edges(None) == -1
+
+
+_CTYPES = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+           "float": ctypes.c_float, "double": ctypes.c_double}
+
+
+def declared_structs():
+    """{name: [(field, ctypes type)]} of every typedef struct in gc.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in (d.strip() for d in body.split(";")):
+            if not decl:
+                continue
+            fp = re.match(r".*\(\s*\*\s*(\w+)\s*\)\s*\(", decl)   # function pointer
+            if fp:
+                fields.append((fp.group(1), ctypes.c_void_p))
+                continue
+            if decl.startswith("void *") or decl.startswith("void*"):
+                fields.append((decl.split("*")[-1].strip(), ctypes.c_void_p))
+                continue
+            typ, rest = decl.split(None, 1)
+            for item in (x.strip() for x in rest.split(",")):
+                m = re.match(r"(\w+)(?:\[(\d+)\])?$", item)
+                base = _CTYPES[typ]
+                fields.append((m.group(1), base * int(m.group(2)) if m.group(2) else base))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """Every struct of the ABI has the same fields, in the same order, with
+    the same types and the same size in the Python binding (a drift here
+    would pass wrong values through every call that takes the struct)."""
+    from paper_2308_14493_gb300 import gc as binding
+
+    structs = declared_structs()
+    assert set(structs) == {"gc_options", "gc_stats", "gc_tuning", "gc_server_options", "gc_result"}
+    for name, fields in structs.items():
+        cls = getattr(binding, name)
+        got = [(f, t) for f, t in cls._fields_]
+        assert [f for f, _ in got] == [f for f, _ in fields], name
+        for (f, t_py), (_, t_h) in zip(got, fields):
+            assert ctypes.sizeof(t_py) == ctypes.sizeof(t_h) and getattr(t_py, "_type_", None) == getattr(
+                t_h, "_type_", None), (name, f)
+
+        class Mirror(ctypes.Structure):
+            _fields_ = fields
+
+        assert ctypes.sizeof(cls) == ctypes.sizeof(Mirror), name
