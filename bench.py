@@ -455,12 +455,14 @@ def local_counts_line(gcb, n, rp, col):
         v = g.vertex_counts()
         ms_v = g.stats()["ms_device"]
         F = g.counts()
-        ok_v = [int(x) for x in v.astype(object).sum(axis=0)] == [4 * x for x in F]
+        # column sums modulo 2^64 (numpy's uint64 sum wraps), against k x F mod 2^64
+        mask = (1 << 64) - 1
+        ok_v = [int(x) for x in v.sum(axis=0, dtype=np.uint64)] == [(4 * x) & mask for x in F]
         del v
         g.edge_orbits()  # warm-up
         e, o = g.edge_orbits()
         ms_e = g.stats()["ms_device"]
-        ok_e = [int(x) for x in o.astype(object).sum(axis=0)] == [k * F[j] for j, k in per_orbit]
+        ok_e = [int(x) for x in o.sum(axis=0, dtype=np.uint64)] == [(k * F[j]) & mask for j, k in per_orbit]
         m = int(e.shape[0])
         del e, o
         g.count_static()
