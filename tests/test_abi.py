@@ -144,3 +144,43 @@ def test_binding_structs_match_the_header():
             _fields_ = fields
 
         assert ctypes.sizeof(cls) == ctypes.sizeof(Mirror), name
+
+
+def _open_raw(n, rp, col, **opt_fields):
+    import numpy as np
+
+    from paper_2308_14493_gb300 import gc as binding
+
+    lib = binding.load()
+    opt = binding.gc_options()
+    lib.gc_default_options(ctypes.byref(opt))
+    for k, v in opt_fields.items():
+        setattr(opt, k, v)
+    h = ctypes.c_void_p()
+    rpa = None if rp is None else np.ascontiguousarray(rp, dtype=np.int32)
+    ca = None if col is None else np.ascontiguousarray(col, dtype=np.int32)
+    ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    rc = lib.gc_open(n, ptr(rpa), ptr(ca), ctypes.byref(opt), ctypes.byref(h))
+    return rc, lib.gc_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case,n,rp,col,opt,msg", [
+    ("negative n", -1, [0], [0], {}, "n must be in"),
+    ("n too large", 1 << 30, [0], [0], {}, "n must be in"),
+    ("row_ptr NULL", 3, None, [0], {}, "row_ptr is NULL"),
+    ("row_ptr[0] != 0", 2, [1, 2, 2], [0, 1], {}, "row_ptr[0] must be 0"),
+    ("odd entries", 2, [0, 1, 1], [1], {}, "even number of entries"),
+    ("col NULL", 2, [0, 1, 2], None, {}, "col is NULL"),
+    ("hops 1", 2, [0, 1, 2], [1, 0], {"region_hops": 1}, "region_hops"),
+    ("hops 9", 2, [0, 1, 2], [1, 0], {"region_hops": 9}, "region_hops"),
+    ("cluster 4", 2, [0, 1, 2], [1, 0], {"dense_cluster": 4}, "dense_cluster"),
+    ("alloc without free", 2, [0, 1, 2], [1, 0], {"alloc": 1}, "alloc and free"),
+])
+def test_open_rejects_bad_arguments_on_the_host(case, n, rp, col, opt, msg):
+    """Argument errors of gc_open are found on the host, before any device
+    call, each with its own message (so they hold without a GPU too)."""
+    from paper_2308_14493_gb300 import gc as binding
+
+    rc, err = _open_raw(n, rp, col, **opt)
+    assert rc == binding.GC_EINVAL, case
+    assert msg in err, (case, err)
