@@ -462,12 +462,16 @@ def test_vertex_orbits_match_the_census(oracle_lib):
     """Orbit counts per vertex (orbits 4..14) against the census of every
     4-subset, each vertex credited with its orbit in the induced graph."""
     rng = np.random.default_rng(1414)
+    seen = np.zeros(11, bool)
     for trial in range(50):
         n = int(rng.integers(4, 20))
         p = float(rng.uniform(0.05, 0.95))
         edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
         rp, col = csr_from_edges(n, edges)
-        assert oracle.vertex_orbits(rp, col) == brute.vertex_orbit_census(n, edges), trial
+        got = oracle.vertex_orbits(rp, col)
+        assert got == brute.vertex_orbit_census(n, edges), trial
+        seen |= np.asarray(got).max(axis=0) > 0
+    assert seen.all()   # every orbit occurs, so every term of the inversion is exercised
 
 
 def _role_counts_by_enumeration():
@@ -536,12 +540,17 @@ def test_edge_orbits_match_the_census(oracle_lib):
     """Edge orbit counts (10 columns) against the census of every 4-subset,
     each edge of the induced graph credited with its orbit there."""
     rng = np.random.default_rng(2020)
+    seen = np.zeros(10, bool)
     for trial in range(60):
         n = int(rng.integers(4, 18))
         p = float(rng.uniform(0.05, 0.95))
         edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
         rp, col = csr_from_edges(n, edges)
-        assert oracle.edge_orbits(rp, col) == brute.edge_orbit_census(n, edges), trial
+        got = oracle.edge_orbits(rp, col)
+        assert got == brute.edge_orbit_census(n, edges), trial
+        if got[1]:
+            seen |= np.asarray(got[1]).max(axis=0) > 0
+    assert seen.all()   # every edge orbit occurs, so every term of the inversion is exercised
 
 
 def test_edge_orbits_of_named_graphs(oracle_lib):
