@@ -29,7 +29,7 @@ def _graph(n, edges):
     return N
 
 
-def _pivot_c4(n, N, rank):
+def _pivot_c4(n, N, rank, c4_off=1):
     """4-cycles from their highest vertex u (in rank order): per wedge
     u-a-w (a, w below u) the credit c_w - 1, and per opposite corner the
     cycle count C(c_w, 2).  Returns (per-edge credit, per-vertex credit)."""
@@ -46,8 +46,8 @@ def _pivot_c4(n, N, rank):
             for w in N[a]:
                 if rank[w] < rank[u] and c[w] > 1:
                     for e in ((min(u, a), max(u, a)), (min(a, w), max(a, w))):
-                        edge[e] = edge.get(e, 0) + c[w] - 1
-                    vert[a] += c[w] - 1
+                        edge[e] = edge.get(e, 0) + c[w] - c4_off
+                    vert[a] += c[w] - c4_off
         for w, x in c.items():
             vert[w] += math.comb(x, 2)
             vert[u] += math.comb(x, 2)
@@ -69,7 +69,10 @@ def _cliques_and_triangles(n, N, rank):
     return tris, k4s
 
 
-def edge_rows_by_kernel_rules(n, edges, rank):
+def edge_rows_by_kernel_rules(n, edges, rank, opp_off=2, outer_off=2, c4_off=1):
+    """The per-edge rows by the kernels' rules; the offsets are the
+    constants of the opposite, diamond-outer and 4-cycle credits (the
+    planted-mistake test changes them)."""
     N = _graph(n, edges)
     d = [len(x) for x in N]
     key = lambda a, b: (min(a, b), max(a, b))
@@ -81,12 +84,12 @@ def edge_rows_by_kernel_rules(n, edges, rank):
     for x, y, z in tris:
         for (a, b), w in (((x, y), z), ((x, z), y), ((y, z), x)):
             e = key(a, b)
-            opp[e] = opp.get(e, 0) + d[w] - 2
-            outer[e] = outer.get(e, 0) + t[key(a, w)] + t[key(b, w)] - 2
+            opp[e] = opp.get(e, 0) + d[w] - opp_off
+            outer[e] = outer.get(e, 0) + t[key(a, w)] + t[key(b, w)] - outer_off
     for q in k4s:
         for a, b in itertools.combinations(q, 2):
             k4[key(a, b)] = k4.get(key(a, b), 0) + 1
-    c4, _ = _pivot_c4(n, N, rank)
+    c4, _ = _pivot_c4(n, N, rank, c4_off)
     rows = []
     for e in sorted(t):
         u, v = e
@@ -205,3 +208,15 @@ def test_pivot_cycle_credit_is_the_cycles_through_each_vertex_and_edge():
         edge, vert = _pivot_c4(n, N, rank)
         assert vert == [x // 8 for x in cyc_v], trial
         assert {e: x for e, x in edge.items() if x} == {e: x // 8 for e, x in cyc_e.items()}, trial
+
+
+def test_planted_mistakes_in_the_edge_rules_fail():
+    """Each credit constant off by one makes the census check fail on the
+    same random graphs (so the test above can tell them apart)."""
+    rng = np.random.default_rng(404)
+    graphs = []
+    for _ in range(60):
+        n = int(rng.integers(4, 17))
+        graphs.append((n, random_graph(rng, n, float(rng.uniform(0.05, 0.95))), [int(x) for x in rng.permutation(n)]))
+    for bad in ({"opp_off": 1}, {"outer_off": 1}, {"outer_off": 3}, {"c4_off": 0}):
+        assert any(edge_rows_by_kernel_rules(n, e, r, **bad) != brute.edge_orbit_census(n, e) for n, e, r in graphs), bad
