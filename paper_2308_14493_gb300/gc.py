@@ -487,7 +487,14 @@ def gc_last_error(h=None) -> str:
 
 
 class Graph:
-    """A device-resident graph with maintained graphlet counts."""
+    """A device-resident graph with maintained graphlet counts.
+
+    Each method calls the C entry point of the same name (``counts`` ->
+    ``gc_counts``, ``apply`` -> ``gc_apply_batch``, ``apply_many`` ->
+    ``gc_apply_batches``, ``edge_orbits`` -> ``gc_edge_orbits``, ...) on the
+    handle; ``with Graph(...) as g`` closes it at the end.  The local
+    counts (``vertex_*``, ``edge_*``) describe the current graph and leave
+    the maintained counts untouched."""
 
     def __init__(self, n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, **opts):
         self.n = int(n)
