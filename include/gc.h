@@ -97,7 +97,9 @@ typedef struct {
     int32_t reserved[4];
     /* device time per stage (CUDA events):
        [0] normalise  [1] region walk  [2] union graph  [3] triangles + 4-cliques
-       [4] 4-cycles   [5] edge terms + closed forms     [6] commit  [7] unused
+       [4] 4-cycles   [5] edge terms + closed forms     [6] commit
+       [7] the heavy-pivot 4-cycle kernels alone (k_c4_dense_t and, when a
+           tuning enables it, k_c4_chunk), timed on the stream they run on
        Stages 3 and 4 run side by side: each is timed from the start of the
        counting pass to its own end. */
     float ms_stage[8];
@@ -108,6 +110,12 @@ typedef struct {
     int32_t reserved2[3];
     int64_t C3a[2], C3b[2];         /* 3-vertex counts of G_a and G_b: [0] induced 2-paths
                                        (open wedges), [1] triangles */
+    /* work of the heavy-pivot 4-cycle kernels of ms_stage[7], for their own
+       roofline: the wedges they walked, and the counter updates they sent to
+       L2 (reductions that return nothing; atomics that return the old value;
+       the shared-memory counters of k_c4_chunk send none) */
+    int64_t work_wedges_heavy;
+    int64_t l2_red_heavy, l2_atom_heavy;
 } gc_stats;
 
 /* Fill *opt with the defaults. */
@@ -237,8 +245,10 @@ int gc_add_vertices(gc_graph *g, int64_t k, int32_t *first_id);
 int32_t gc_num_vertices(const gc_graph *g);
 
 /* As gc_apply_batch, with the pair arrays in device memory (int32, same
-   layout).  The caller guarantees every id is in [0, n) and no pair is a
-   self-loop; the library does not read the pairs on the host. */
+   layout).  The library does not read the pairs on the host: the
+   normalisation kernel checks every pair on the device, and a pair with an
+   id outside [0, n) or a self-loop makes the call return GC_EINVAL with the
+   graph and the counts unchanged. */
 int gc_apply_batch_device(gc_graph *g, const int32_t *d_ins, int64_t n_ins,
                           const int32_t *d_del, int64_t n_del, uint64_t out[6]);
 
@@ -278,8 +288,8 @@ int gc_apply_batches(gc_graph *g, const int32_t *const *ins, const int64_t *n_in
  *             -- its insertions are pairs d_pairs[ins_off .. ins_off+n_ins),
  *             its deletions d_pairs[del_off .. del_off+n_del)
  *   out       host uint64[k][6]
- * The caller guarantees every id is in [0, n) and no pair is a self-loop
- * (a batch that breaks this is not applied and the call returns GC_EINVAL).
+ * Every pair is checked on the device: a batch with an id outside [0, n) or
+ * a self-loop is not applied and the call returns GC_EINVAL.
  */
 int gc_apply_batches_device(gc_graph *g, const int32_t *d_pairs, const int64_t *batches, int32_t k,
                             int32_t independent, uint64_t *out);
@@ -307,7 +317,10 @@ int gc_export_csr(gc_graph *g, int32_t *row_ptr, int32_t *col);
  * already holds in device memory, using only a fixed scratch array compiled
  * into this library (about 9 MB, held on every GPU that loads the library
  * until the process exits).  It calls no cudaMalloc, cudaFree or any other
- * allocating routine.
+ * allocating routine.  It orients edges by the caller's vertex ids as given
+ * (renumbering by degree, as gc_open does, would need scratch of its own), so
+ * its 4-cycle work is bounded by m * d_max rather than by the degree-ordered
+ * bound; the counts do not depend on the order.
  *   n          vertices, 1 <= n <= GC_NOALLOC_MAX_VERTICES (n = 0 gives zeros)
  *   d_row_ptr  device int32[n+1], d_row_ptr[0] = 0, d_row_ptr[n] = nnz
  *   d_col      device int32[nnz]: a symmetric simple graph, every row sorted

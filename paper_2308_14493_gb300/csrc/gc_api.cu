@@ -87,7 +87,8 @@ struct gc_graph {
     int dense_cluster_size = 8;
     Buf<unsigned long long> cta_tables;  // hash tables of the medium 4-cycle pivots (per CTA)
     int cta_groups = 0;
-    Buf<int32_t> chunk_table;            // run bounds of the chunked 4-cycle kernel
+    Buf<unsigned char> chunk_table;      // per-CTA run bounds of the chunked 4-cycle kernel
+    long long chunk_cap = 0;             // run-bound entries per CTA in it
     Tuning tune = default_tuning();     // bin boundaries of the counting pass
     long long loc_heavy_min = 65536;   // w~ from which local-count 4-cycle pivots take k_c4_group (0 = never)
     int32_t* bins = nullptr;             // NBINS * n work lists of the counting pass
@@ -133,7 +134,8 @@ struct gc_graph {
     gc_stats st{};
     std::string err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEvent_t ev[8] = {};  // stage boundaries, see gc_stats.ms_stage
+    cudaEvent_t ev[10] = {};  // stage boundaries, see gc_stats.ms_stage; [8], [9] around the
+                              // heavy-pivot 4-cycle kernels (ms_stage[7])
     cudaStream_t aux[3] = {};   // side streams of the counting pass
     cudaEvent_t fork = nullptr, join[3] = {};
     int launches = 0;        // kernels launched by the current call
@@ -490,13 +492,14 @@ static void trim_scratch(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
 }
 
-// Run bounds of the chunked 4-cycle kernel: one int per vertex and id-range
-// chunk, allocated when a tuning first enables that tier (never for vertex
-// counts whose table would be too large: the tier then stays off).
+// Scratch of the chunked 4-cycle kernel: per CTA, the run bounds of one
+// pivot's lower neighbours (c4_chunk_cap entries for this n), allocated when
+// a tuning first enables that tier.
 static bool ensure_chunk_table(gc_graph* g) {
-    const long long te = c4_chunk_table_entries(std::max(g->n, 1));
-    if (te <= 0) return true;
-    return ensure(g, g->chunk_table, (size_t)te);
+    const long long cap = c4_chunk_cap(std::max(g->n, 1));
+    if (!ensure(g, g->chunk_table, (size_t)g->sms * c4_chunk_cta_bytes(cap))) return false;
+    g->chunk_cap = cap;
+    return true;
 }
 
 static int ensure_desc(gc_graph* g, long long words) {
@@ -551,7 +554,8 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
     ca.cta_tables = g->cta_tables.p;
     ca.cta_table_words = 2 * C4_T3;
     ca.cta_groups = g->cta_groups;
-    ca.chunk_table = g->chunk_table.p;
+    ca.chunk_scratch = g->chunk_table.p;
+    ca.chunk_cap = g->chunk_table.p ? g->chunk_cap : 0;
     ca.tune = g->tune;
     ca.sms = g->sms;
     for (int i = 0; i < 3; i++) {
@@ -559,6 +563,8 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
         ca.join[i] = g->join[i];
     }
     ca.fork = g->fork;
+    ca.ev_heavy[0] = timed ? g->ev[8] : nullptr;
+    ca.ev_heavy[1] = timed ? g->ev[9] : nullptr;
     g->launches += enqueue_counting(ca, s, timed ? g->ev[3] : nullptr, timed ? g->ev[4] : nullptr,
                                     timed ? g->ev[5] : nullptr, fin);
     if (set_F) {
@@ -826,6 +832,8 @@ static void stage_times(gc_graph* g, int lo, int hi) {
         else if (i == 5) g->st.ms_stage[5] = std::min(elapsed(g->ev[4], g->ev[6]), elapsed(g->ev[5], g->ev[6]));
         else g->st.ms_stage[i] = elapsed(g->ev[i], g->ev[i + 1]);
     }
+    // the heavy-pivot 4-cycle kernels alone, on their own stream
+    if (lo <= 4 && hi > 4) g->st.ms_stage[7] = elapsed(g->ev[8], g->ev[9]);
 }
 
 static void fill_stats(gc_graph* g, const Ctl& c) {
@@ -842,6 +850,9 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
     t.edges_b = (long long)c.acc[13];
     t.work_triangles = (long long)c.acc[14];
     t.work_wedges = (long long)c.acc[15];
+    t.work_wedges_heavy = (long long)c.acc[20];
+    t.l2_red_heavy = (long long)c.acc[21];
+    t.l2_atom_heavy = (long long)c.acc[22];
     for (int i = 0; i < 6; i++) {
         t.Ca[i] = c.Ca[i];
         t.Cb[i] = c.Cb[i];
@@ -2312,7 +2323,7 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
             default: t.c4_chunk_max = v; break;
         }
     };
-    const bool chunk_ok = c4_chunk_table_entries(std::max(g->n, 1)) > 0 && ensure_chunk_table(g);
+    const bool chunk_ok = ensure_chunk_table(g);
     for (int sweep = 0; sweep < 3; sweep++) {
         bool moved = false;
         for (int i = 8; i >= 0; i--) {

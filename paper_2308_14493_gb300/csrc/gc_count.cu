@@ -55,7 +55,7 @@ __global__ void k_reset_count(Ctl* c) {
     int t = threadIdx.x;
     if (t < NACC) c->acc[t] = 0;
     for (int i = t; i < NACC * ACC_STRIPES; i += blockDim.x) (&c->accs[0][0])[i] = 0;
-    if (t < 8) c->work[t] = 0;
+    if (t < NWORK) c->work[t] = 0;
     if (t < NBINS) c->nbin[t] = 0;
     if (t == 0) c->maxdeg = 0;
 }
@@ -141,7 +141,7 @@ __global__ void k_wedge_bound(const Ctl* c, const int32_t* __restrict__ wlist, c
 // Work bins: triangle roots by out-degree, 4-cycle pivots by w~.
 __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
                       const int32_t* __restrict__ U_split, const long long* __restrict__ U_wt,
-                      int32_t* __restrict__ bins, int n, Tuning t) {
+                      int32_t* __restrict__ bins, int n, Tuning t, long long chunk_cap) {
     pdl_enter();
     const int nW = c->nW;
     const int lane = threadIdx.x & 31;
@@ -167,10 +167,12 @@ __global__ void k_bin(Ctl* c, const int32_t* __restrict__ wlist, const long long
                 // the hash tier packs 16-bit counts: at most 2^16 - 1 lower neighbours
                 cb = wt <= t.c4_reg_max                         ? BIN_C4_REG
                      : wt <= t.c4_warp_max                      ? BIN_C4_WARP
+                     : wt <= min(t.c4_block_max, C4B_SMALL_MAX) ? BIN_C4_BSMALL
                      : wt <= t.c4_block_max                     ? BIN_C4_BLOCK
                      : (wt <= t.c4_cta_max && split < 65536)    ? BIN_C4_CTA
-                     : (wt > t.c4_chunk_min && wt <= t.c4_chunk_max) ? BIN_C4_CHUNK
-                                                                : BIN_C4_DENSE;
+                     : (wt > t.c4_chunk_min && wt <= t.c4_chunk_max &&
+                        (long long)split * (((long long)u + CH_R - 1) / CH_R + 1) <= chunk_cap) ? BIN_C4_CHUNK
+                                                                                                 : BIN_C4_DENSE;
             }
         }
 #pragma unroll 1
@@ -539,25 +541,79 @@ __global__ void __launch_bounds__(256) k_c4_reg(Ctl* c, const int32_t* __restric
     acc_add(c, 15, wedges);
 }
 
-// Walk the wedges u-v-w of pivot u for the lower neighbours v = N(u)[j],
-// j = j0, j0 + step, ...; calls fn(w, flags) for each w < u.  Warp-uniform.
+// Walk the wedges u-v-w of pivot u (w < u) for its lower neighbours
+// v = N(u)[j], calling fn(w, flags) once per wedge.  The warp takes 32
+// lower neighbours at a time and lays their rows end to end (a warp prefix
+// sum over the nonempty rows); each lane then finds its row from a bitmask
+// of row starts (one OR-reduction per 32 entries), so the loads of up to 128
+// entries of many short rows are in flight together instead of one row after
+// the other.  Entries at or above u are read and skipped.  Rows are taken in
+// groups j0 = first, first + 32 * step, ...; scratch: 32 ints, 32 int64 and
+// 32 uint32 of shared memory per warp.  Warp-uniform.
+constexpr int WF_UNROLL = 4;
 template <class Fn>
-__device__ __forceinline__ void walk_wedges(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
-                                            int32_t u, long long rb, int nlow, int j0, int step, Fn fn) {
+__device__ __forceinline__ void walk_flat(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
+                                          uint32_t u, long long rb, int nlow, int first, int step, int* cpre,
+                                          long long* cvb, uint32_t* cfv, Fn fn) {
     const int lane = threadIdx.x & 31;
-    for (int j = j0; j < nlow; j += step) {
-        uint32_t fv = U_col[rb + j];
-        uint32_t v = vid(fv);
-        long long vb = U_off[v];
-        int dv = (int)(U_off[v + 1] - vb);
-        for (int b = 0; b < dv; b += 32) {
-            int q = b + lane;
-            uint32_t e = q < dv ? U_col[vb + q] : 0xFFFFFFFFu;
-            uint32_t wv = vid(e);
-            bool ok = q < dv && wv < (uint32_t)u;
-            if (ok) fn(wv, fv & e & (FLAG_A | FLAG_B));
-            if (__ballot_sync(FULL, q < dv && wv >= (uint32_t)u)) break;  // rows are sorted
+    for (int j0 = first * 32; j0 < nlow; j0 += step * 32) {
+        const int j = j0 + lane;
+        int len = 0;
+        long long vb = 0;
+        uint32_t fv = 0;
+        if (j < nlow) {
+            fv = U_col[rb + j];
+            const uint32_t v = vid(fv);
+            vb = U_off[v];
+            len = (int)(U_off[v + 1] - vb);
         }
+        const unsigned ne = __ballot_sync(FULL, len > 0);
+        if (!ne) continue;
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        const int k = __popc(ne);
+        __syncwarp();
+        if (len > 0) {
+            const int slot = __popc(ne & lanemask_lt());
+            cpre[slot] = inc - len;
+            cvb[slot] = vb - (inc - len);
+            cfv[slot] = fv;
+        }
+        __syncwarp();
+        const int my_start = lane < k ? cpre[lane] : 0x7FFFFFFF;
+        int R = 0;  // row holding position t0 (warp-uniform)
+        for (int t0 = 0; t0 < total; t0 += 32 * WF_UNROLL) {
+            uint32_t ev[WF_UNROLL], fr[WF_UNROLL];
+#pragma unroll
+            for (int q = 0; q < WF_UNROLL; q++) {
+                const int tb = t0 + q * 32;
+                ev[q] = 0xFFFFFFFFu;
+                fr[q] = 0;
+                if (tb < total) {
+                    const unsigned bit = (my_start > tb && my_start < tb + 32) ? (1u << (my_start - tb)) : 0u;
+                    const unsigned m = __reduce_or_sync(FULL, bit);
+                    const int r = R + __popc(m & ((2u << lane) - 1u));
+                    if (tb + lane < total) {
+                        ev[q] = U_col[cvb[r] + tb + lane];
+                        fr[q] = cfv[r];
+                    }
+                    int rn = R + __popc(m);
+                    if (rn + 1 < k && cpre[rn + 1] == tb + 32) rn++;
+                    R = rn;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < WF_UNROLL; q++) {
+                const uint32_t w = vid(ev[q]);
+                if (ev[q] != 0xFFFFFFFFu && w < u) fn(w, fr[q] & ev[q] & (FLAG_A | FLAG_B));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -567,27 +623,24 @@ constexpr int C4W_SLOTS = 2 * C4_T1;
 __global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_t* __restrict__ list,
                                                           const long long* __restrict__ U_off,
                                                           const uint32_t* __restrict__ U_col,
-                                                          const int32_t* __restrict__ U_split) {
+                                                          const int32_t* __restrict__ U_split,
+                                                          const long long* __restrict__ U_wt) {
     pdl_enter();
     __shared__ uint32_t sKey[C4W_WARPS][C4W_SLOTS];
     __shared__ uint32_t sCnt[C4W_WARPS][C4W_SLOTS];
+    __shared__ int s_pre[C4W_WARPS][32];
+    __shared__ long long s_vb[C4W_WARPS][32];
+    __shared__ uint32_t s_fv[C4W_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cnt = c->nbin[BIN_C4_WARP];
     unsigned long long qa = 0, qb = 0, wedges = 0;
     uint32_t* keys = sKey[w];
     uint32_t* cnts = sCnt[w];
     for (int i = blockIdx.x * C4W_WARPS + w; i < cnt; i += gridDim.x * C4W_WARPS) {
-        int32_t u = list[i];
-        long long rb = U_off[u];
-        int nlow = U_split[u];
-        long long wt = 0;
-        for (int j = lane; j < nlow; j += 32) {
-            uint32_t v = vid(U_col[rb + j]);
-            wt += U_off[v + 1] - U_off[v];
-        }
-        wt = (long long)warp_sum_u64((unsigned long long)wt);
-        wt = __shfl_sync(FULL, wt, 0);
-        const int lg = log2_table(wt, 5, 10);
+        const uint32_t u = (uint32_t)list[i];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        const int lg = log2_table(U_wt[u], 5, 10);
         const uint32_t mask = (1u << lg) - 1;
         const int shift = 32 - lg;
         for (int s = lane; s <= (int)mask; s += 32) {
@@ -595,7 +648,7 @@ __global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_
             cnts[s] = 0;
         }
         __syncwarp();
-        walk_wedges(U_off, U_col, u, rb, nlow, 0, 1, [&](uint32_t wv, uint32_t fl) {
+        walk_flat(U_off, U_col, u, rb, nlow, 0, 1, s_pre[w], s_vb[w], s_fv[w], [&](uint32_t wv, uint32_t fl) {
             wedges++;
             if (!fl) return;
             uint32_t old = hash_add(keys, cnts, shift, mask, wv, flag_inc16(fl));
@@ -603,63 +656,6 @@ __global__ void __launch_bounds__(C4W_WARPS * 32) k_c4_warp(Ctl* c, const int32_
             if (fl & FLAG_B) qb += old & 0xFFFFu;
         });
         __syncwarp();
-    }
-    acc_add(c, 5, qa);
-    acc_add(c, 11, qb);
-    acc_add(c, 15, wedges);
-}
-
-constexpr int C4B_SLOTS = 2 * C4_T2;
-size_t c4_block_smem_bytes() { return (size_t)C4B_SLOTS * 8; }
-
-__global__ void __launch_bounds__(256, 4) k_c4_block(Ctl* c, const int32_t* __restrict__ list,
-                                                 const long long* __restrict__ U_off,
-                                                 const uint32_t* __restrict__ U_col,
-                                                 const int32_t* __restrict__ U_split) {
-    pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* keys = (uint32_t*)smem;
-    uint32_t* cnts = keys + C4B_SLOTS;
-    __shared__ int s_idx;
-    __shared__ long long s_wt;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int cnt = c->nbin[BIN_C4_BLOCK];
-    unsigned long long qa = 0, qb = 0, wedges = 0;
-    for (;;) {
-        if (tid == 0) {
-            s_idx = (int)atomicAdd(&c->work[2], 1u);
-            s_wt = 0;
-        }
-        __syncthreads();
-        const int idx = s_idx;
-        if (idx >= cnt) break;
-        int32_t u = list[idx];
-        long long rb = U_off[u];
-        int nlow = U_split[u];
-        long long wt = 0;
-        for (int j = tid; j < nlow; j += blockDim.x) {
-            uint32_t v = vid(U_col[rb + j]);
-            wt += U_off[v + 1] - U_off[v];
-        }
-        wt = (long long)warp_sum_u64((unsigned long long)wt);
-        if (lane == 0) atomicAdd((unsigned long long*)&s_wt, (unsigned long long)wt);
-        __syncthreads();
-        const int lg = log2_table(s_wt, 6, 14);
-        const uint32_t mask = (1u << lg) - 1;
-        const int shift = 32 - lg;
-        for (int s = tid; s <= (int)mask; s += blockDim.x) {
-            keys[s] = EMPTY_KEY;
-            cnts[s] = 0;
-        }
-        __syncthreads();
-        walk_wedges(U_off, U_col, u, rb, nlow, warp, nwarps, [&](uint32_t wv, uint32_t fl) {
-            wedges++;
-            if (!fl) return;
-            uint32_t old = hash_add(keys, cnts, shift, mask, wv, flag_inc16(fl));
-            if (fl & FLAG_A) qa += old >> 16;
-            if (fl & FLAG_B) qb += old & 0xFFFFu;
-        });
-        __syncthreads();
     }
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
@@ -717,6 +713,168 @@ __device__ __forceinline__ void wedge_segment_prefix(const long long* __restrict
 
 constexpr int C4D_SEG = 2048;  // lower neighbours per prefix segment
 constexpr int C4D_UNROLL = 4;
+
+// Block-wide walk over the elements of ns <= C4D_SEG rows laid end to end,
+// so every warp of the block has work however the row lengths vary.  Row j
+// has len_fn(j, &base, &flag) elements starting at U_col[base]; the prefix of
+// the lengths goes to pre[0 .. ns] (block scan), each row's start minus its
+// prefix to vbs[j] and its flag word to fvs[j].  Then each warp takes runs of
+// 32 * C4D_UNROLL consecutive elements (binary search for the run's first
+// row, then steps) and calls fn(j, p, e, f) for the element at position p of
+// row j (e = its adjacency entry, f = the row's flag word), loads of a run in
+// flight together.  Every thread of the block calls it; ends with
+// __syncthreads().  Returns the number of elements.
+template <class LenFn, class Fn>
+__device__ __forceinline__ int block_walk_rows(const uint32_t* __restrict__ U_col, int ns, int* pre, long long* vbs,
+                                               uint32_t* fvs, int* s_tot, LenFn len_fn, Fn fn) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int j = tid; j < ns; j += blockDim.x) {
+        long long b = 0;
+        uint32_t f = 0;
+        pre[j + 1] = len_fn(j, &b, &f);
+        vbs[j] = b;
+        fvs[j] = f;
+    }
+    __syncthreads();
+    // two-level scan: each warp scans a contiguous slice, then the slice totals
+    const int per = (ns + nwarps - 1) / nwarps;
+    const int b0 = warp * per, b1 = min(ns, b0 + per);
+    int carry = 0;
+    for (int b = b0; b < b1; b += 32) {
+        int x = b + lane < b1 ? pre[b + lane + 1] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b + lane < b1) pre[b + lane + 1] = x + carry;
+        carry += __shfl_sync(FULL, x, 31);
+    }
+    __shared__ int s_part[33];
+    if (lane == 0) s_part[warp + 1] = carry;
+    __syncthreads();
+    if (tid == 0) {
+        s_part[0] = 0;
+        for (int w = 1; w <= nwarps; w++) s_part[w] += s_part[w - 1];
+        pre[0] = 0;
+        *s_tot = s_part[nwarps];
+    }
+    __syncthreads();
+    for (int j = b0 + lane; j < b1; j += 32) pre[j + 1] += s_part[warp];
+    __syncthreads();
+    for (int j = tid; j < ns; j += blockDim.x) vbs[j] -= pre[j];
+    __syncthreads();
+    const int total = *s_tot;
+    for (int base = warp * 32 * C4D_UNROLL; base < total; base += nwarps * 32 * C4D_UNROLL) {
+        uint32_t e[C4D_UNROLL], f[C4D_UNROLL];
+        int jr[C4D_UNROLL];
+        int j = find_seg(pre, ns, base);
+#pragma unroll
+        for (int r = 0; r < C4D_UNROLL; r++) {
+            const int i = base + r * 32 + lane;
+            e[r] = 0xFFFFFFFFu;
+            f[r] = 0;
+            jr[r] = -1;
+            if (i < total) {
+                while (j + 1 < ns && pre[j + 1] <= i) j++;
+                e[r] = U_col[vbs[j] + i];
+                f[r] = fvs[j];
+                jr[r] = j;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < C4D_UNROLL; r++)
+            if (jr[r] >= 0) fn(jr[r], base + r * 32 + lane - pre[jr[r]], e[r], f[r]);
+    }
+    __syncthreads();
+    return total;
+}
+
+
+// Medium pivots: one block per pivot, hash table of up to 2^LG slots in
+// shared memory.  Two instances: 2^12 slots with 4 warps (several blocks per
+// SM) for the smaller wedge bounds, each warp laying 32 rows end to end
+// (walk_flat); 2^14 slots with 16 warps for the rest, the whole block laying
+// all the pivot's rows end to end (block_walk_rows), so no warp waits idle at
+// the block barrier while others walk long rows.
+constexpr int C4B_SMALL_LG = 12, C4B_SMALL_THREADS = 128;
+constexpr int C4B_BIG_LG = 14, C4B_BIG_THREADS = 512;
+template <int LG, int THREADS>
+constexpr size_t c4_block_smem() {
+    return ((size_t)8 << LG) + (size_t)(THREADS / 32) * 32 * (4 + 8 + 4);
+}
+
+template <int LG, int THREADS, int BIN, int WORK, bool BLOCKWIDE>
+__global__ void __launch_bounds__(THREADS) k_c4_block(Ctl* c, const int32_t* __restrict__ list,
+                                                      const long long* __restrict__ U_off,
+                                                      const uint32_t* __restrict__ U_col,
+                                                      const int32_t* __restrict__ U_split,
+                                                      const long long* __restrict__ U_wt) {
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* keys = (uint32_t*)smem;
+    uint32_t* cnts = keys + (1 << LG);
+    long long* w_vb = (long long*)(cnts + (1 << LG));
+    int* w_pre = (int*)(w_vb + THREADS);
+    uint32_t* w_fv = (uint32_t*)(w_pre + THREADS);
+    __shared__ int s_idx;
+    constexpr int SEG = BLOCKWIDE ? C4D_SEG : 1;
+    __shared__ int s_pre[SEG + 1], s_tot;
+    __shared__ long long s_vb[SEG];
+    __shared__ uint32_t s_fv[SEG];
+    const int tid = threadIdx.x, warp = tid >> 5, nwarps = THREADS >> 5;
+    const int cnt = c->nbin[BIN];
+    unsigned long long qa = 0, qb = 0, wedges = 0;
+    for (;;) {
+        if (tid == 0) s_idx = (int)atomicAdd(&c->work[WORK], 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= cnt) break;
+        const uint32_t u = (uint32_t)list[idx];
+        const long long rb = U_off[u];
+        const int nlow = U_split[u];
+        const int lg = log2_table(U_wt[u], 6, LG);
+        const uint32_t mask = (1u << lg) - 1;
+        const int shift = 32 - lg;
+        for (int s = tid; s <= (int)mask; s += THREADS) {
+            keys[s] = EMPTY_KEY;
+            cnts[s] = 0;
+        }
+        __syncthreads();
+        auto count = [&](uint32_t wv, uint32_t fl) {
+            wedges++;
+            if (!fl) return;
+            uint32_t old = hash_add(keys, cnts, shift, mask, wv, flag_inc16(fl));
+            if (fl & FLAG_A) qa += old >> 16;
+            if (fl & FLAG_B) qb += old & 0xFFFFu;
+        };
+        if constexpr (BLOCKWIDE) {
+            for (int s0 = 0; s0 < nlow; s0 += SEG) {
+                const int ns = min(SEG, nlow - s0);
+                block_walk_rows(
+                    U_col, ns, s_pre, s_vb, s_fv, &s_tot,
+                    [&](int j, long long* b, uint32_t* f) {
+                        const uint32_t fv = U_col[rb + s0 + j];
+                        const uint32_t v = vid(fv);
+                        *b = U_off[v];
+                        *f = fv;
+                        return (int)(U_off[v + 1] - *b);
+                    },
+                    [&](int, int, uint32_t e, uint32_t f) {
+                        const uint32_t wv = vid(e);
+                        if (wv < u) count(wv, f & e & (FLAG_A | FLAG_B));
+                    });
+            }
+        } else {
+            walk_flat(U_off, U_col, u, rb, nlow, warp, nwarps, w_pre + warp * 32, w_vb + warp * 32,
+                      w_fv + warp * 32, count);
+            __syncthreads();
+        }
+    }
+    acc_add(c, 5, qa);
+    acc_add(c, 11, qb);
+    acc_add(c, 15, wedges);
+}
 
 // Reductions in L2 that return nothing (the compiler may otherwise merge
 // them with the returning atomics of the other path).
@@ -780,17 +938,17 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
     const int NW = ncta * (int)(blockDim.x >> 5);
     const int bin = CLUSTER ? BIN_C4_DENSE : BIN_C4_CTA;
     const int cnt = c->nbin[bin];
-    unsigned long long qa = 0, qb = 0, wedges = 0;
+    unsigned long long qa = 0, qb = 0, wedges = 0, nred = 0, natom = 0;
     for (;;) {
         int idx;
         if constexpr (CLUSTER) {
             cg::cluster_group cl = cg::this_cluster();
-            if (rank == 0 && threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[3], 1u);
+            if (rank == 0 && threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[WORK_C4_DENSE], 1u);
             cl.sync();
             idx = *cl.map_shared_rank(&s_idx, 0);
             cl.sync();
         } else {
-            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[4], 1u);
+            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[WORK_C4_CTA], 1u);
             __syncthreads();
             idx = s_idx;
             __syncthreads();
@@ -887,13 +1045,16 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                             if (wide) a64[wv] = 0ull;
                             else a32[wv] = 0u;
                         } else if (sweep) {
+                            nred++;
                             if (wide) red_add_u64(&a64[wv], flag_inc(fl));
                             else red_add_u32(&a32[wv], flag_inc16(fl));
                         } else if (wide) {
+                            natom++;
                             unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
                             if (fl & FLAG_A) qa += old >> 32;
                             if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
                         } else {
+                            natom++;
                             uint32_t old = atomicAdd(&a32[wv], flag_inc16(fl));
                             if (fl & FLAG_A) qa += old >> 16;
                             if (fl & FLAG_B) qb += old & 0xFFFFu;
@@ -908,119 +1069,132 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
     acc_add(c, 15, wedges);
-}
-
-// Heavy pivots, counters in shared memory.  Shared-memory atomics are about
-// twenty times faster than L2 or distributed-shared-memory atomics, but a
-// pivot's endpoints w range over [0, u), far more ids than shared memory
-// holds.  So the id range is cut into chunks of CH_R ids (one chunk of
-// counters fills the shared array) and the pivot is counted chunk by chunk.
-// Every adjacency row is sorted, so the entries of row v inside chunk b are
-// one contiguous run [T[v][b], T[v][b+1]); the table T of these bounds is
-// built once per counting pass (k_chunk_bounds, one read of U).  For each
-// chunk, every warp takes lower neighbours 32 at a time, lays their runs
-// end to end (a warp prefix sum) and walks them with all lanes, one shared
-// atomic per wedge (the old value gives the C(c, 2) sum as in the other
-// 4-cycle kernels); then the counters are cleared.  Counters are packed
-// 16/16 bits (G_a / G_b) while every degree is below 2^16; with larger
-// degrees they are 32/32 bits in 64-bit words and each chunk is walked twice,
-// one half of its ids at a time.
-constexpr int CH_BYTES = 196608;        // counter bytes
-constexpr int CH_R = CH_BYTES / 4;      // ids per chunk (49,152)
-constexpr int CH_THREADS = 1024;
-constexpr int CH_UNROLL = 4;
-constexpr long long CH_TABLE_MAX = 2ll << 30;  // table entries the library will allocate
-
-size_t c4_chunk_smem_bytes() { return (size_t)CH_BYTES + (CH_THREADS / 32) * 32 * (4 + 8 + 4); }
-int c4_chunk_width(long long n) { return (int)((n + CH_R - 1) / CH_R) + 1; }
-long long c4_chunk_table_entries(long long n) {
-    const long long e = n * (long long)c4_chunk_width(n);
-    return e <= CH_TABLE_MAX ? e : -1;
-}
-
-// T[v][b] = first position in row v whose id is >= b * CH_R, b = 0 .. TW-1.
-// A warp per row: a position starts chunk b when the ids before and at it
-// straddle b * CH_R; chunks after the last entry start at the row's end.
-__global__ void k_chunk_bounds(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ U_off,
-                               const uint32_t* __restrict__ U_col, int32_t* __restrict__ T, int TW) {
-    pdl_enter();
-    const int nW = c->nW;
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < nW; i += nwarps) {
-        const int32_t v = wlist[i];
-        const long long rb = U_off[v];
-        const int d = (int)(U_off[v + 1] - rb);
-        int32_t* t = T + (size_t)v * TW;
-        for (int p = lane; p < d; p += 32) {
-            const int cb = (int)(vid(U_col[rb + p]) / CH_R);
-            const int ca = p == 0 ? -1 : (int)(vid(U_col[rb + p - 1]) / CH_R);
-            for (int b = ca + 1; b <= cb; b++) t[b] = p;
-        }
-        const int last = d == 0 ? -1 : (int)(vid(U_col[rb + d - 1]) / CH_R);
-        for (int b = last + 1 + lane; b < TW; b += 32) t[b] = d;
+    if (CLUSTER) {
+        acc_add(c, 20, wedges);
+        acc_add(c, 21, nred);
+        acc_add(c, 22, natom);
     }
 }
 
+// Heavy pivots, counters in shared memory.  Shared-memory atomics are about
+// twenty times faster than L2 atomics, but a pivot's endpoints w range over
+// [0, u), far more ids than shared memory holds.  So the id range is cut
+// into chunks of CH_R ids (one chunk of counters fills the shared array) and
+// the pivot is counted chunk by chunk.  Every adjacency row is sorted, so the
+// entries of a lower neighbour's row inside chunk b are one contiguous run.
+// One CTA takes one pivot at a time:
+//   phase 1  a warp per lower neighbour v = N(u)[j] reads its row once
+//            (until the first id >= u) and writes where each chunk's run
+//            starts: T[b][j] for b = 0 .. NCH (T[NCH][j] = end of the ids
+//            below u).  T lies in the CTA's own scratch, chunk-major, so
+//            phase 2 reads it coalesced.
+//   phase 2  for every chunk b: each warp takes 32 lower neighbours, lays
+//            their runs end to end (a warp prefix sum over the nonempty
+//            runs), finds each lane's run from a bitmask of run starts
+//            (one OR-reduction per 32 wedges) and increments the counter of
+//            each endpoint by a shared-memory atomic that returns the old
+//            value c (adding c accumulates sum C(c_w, 2) as in the other
+//            4-cycle kernels); then the chunk's counters are cleared.
+// Counters are packed 16/16 bits (G_a / G_b) while every degree is below
+// 2^16; with larger degrees they are 32/32 bits in 64-bit words and each
+// chunk is walked twice, one half of its ids at a time.  A pivot whose table
+// (lower neighbours x (NCH + 1)) exceeds the CTA's scratch stays in the dense
+// tier (k_bin checks it).
+constexpr int CH_THREADS = 1024;
+
+constexpr int CH_UNROLL = 4;
+size_t c4_chunk_smem_bytes() { return (size_t)CH_BYTES + (CH_THREADS / 32) * 32 * (4 + 8 + 4); }
+int c4_chunk_width(long long n) { return (int)((n + CH_R - 1) / CH_R) + 1; }
+long long c4_chunk_cap(long long n) {
+    // run-bound entries per CTA: room for lower neighbour counts up to 16,384
+    // at this graph's chunk count, between 2^16 and 2^20 entries
+    const long long e = (long long)c4_chunk_width(n) * 16384;
+    return std::min<long long>(1ll << 20, std::max<long long>(1ll << 16, e));
+}
+// bytes of one CTA's scratch: T (int32[cap]), row starts (int64[cap / 2]),
+// row flags (uint32[cap / 2])
+
 template <bool WIDE>
-__device__ __forceinline__ void chunk_pass(const long long* __restrict__ U_off, const uint32_t* __restrict__ U_col,
-                                           const int32_t* __restrict__ T, int TW, int32_t u, long long rb, int nlow,
-                                           int b, uint32_t lo_id, uint32_t hi_id, unsigned char* smem,
-                                           int* w_pre, long long* w_vb, uint32_t* w_fv, unsigned long long& qa,
-                                           unsigned long long& qb, unsigned long long& wedges, bool count_wedges) {
+__device__ __forceinline__ void chunk_walk(const uint32_t* __restrict__ U_col, const int32_t* __restrict__ T,
+                                           const long long* __restrict__ rbase, const uint32_t* __restrict__ rflag,
+                                           int nlow, int b, uint32_t u, uint32_t lo_id, uint32_t hi_id,
+                                           unsigned char* smem, int* w_pre, long long* w_vb, uint32_t* w_fv,
+                                           unsigned long long& qa, unsigned long long& qb,
+                                           unsigned long long& wedges, bool count_wedges) {
     uint32_t* cnt32 = (uint32_t*)smem;
     unsigned long long* cnt64 = (unsigned long long*)smem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    int* pre = w_pre + warp * 32;
-    long long* vbs = w_vb + warp * 32;
-    uint32_t* fvs = w_fv + warp * 32;
+    int* cpre = w_pre + warp * 32;
+    long long* cvb = w_vb + warp * 32;
+    uint32_t* cfv = w_fv + warp * 32;
+    const int32_t* Tb = T + (size_t)b * nlow;
+    const int32_t* Tn = Tb + nlow;
     for (int j0 = warp * 32; j0 < nlow; j0 += NW * 32) {
         const int j = j0 + lane;
-        int len = 0;
+        int len = 0, s = 0;
         if (j < nlow) {
-            const uint32_t fv = U_col[rb + j];
-            const uint32_t v = vid(fv);
-            const int32_t* t = T + (size_t)v * TW + b;
-            const int lo = t[0];
-            len = t[1] - lo;
-            vbs[lane] = U_off[v] + lo;
-            fvs[lane] = fv;
+            s = Tb[j];
+            len = Tn[j] - s;
         }
+        const unsigned ne = __ballot_sync(FULL, len > 0);
+        if (!ne) continue;
         int inc = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, inc, o);
             if (lane >= o) inc += y;
         }
-        pre[lane] = inc - len;  // exclusive
         const int total = __shfl_sync(FULL, inc, 31);
+        const int k = __popc(ne);
         __syncwarp();
-        int r = 0;
+        if (len > 0) {
+            // nonempty runs, compacted: run r starts at cpre[r] of the laid-out
+            // sequence; its wedge i is U_col[cvb[r] + i]
+            const int slot = __popc(ne & lanemask_lt());
+            cpre[slot] = inc - len;
+            cvb[slot] = rbase[j] + s - (inc - len);
+            cfv[slot] = rflag[j];
+        }
+        __syncwarp();
+        const int my_start = lane < k ? cpre[lane] : 0x7FFFFFFF;
+        int R = 0;  // run holding position t0 (warp-uniform)
         for (int t0 = 0; t0 < total; t0 += 32 * CH_UNROLL) {
             uint32_t ev[CH_UNROLL], fr[CH_UNROLL];
 #pragma unroll
-            for (int k = 0; k < CH_UNROLL; k++) {  // independent loads in flight
-                const int t = t0 + k * 32 + lane;
-                ev[k] = 0xFFFFFFFFu;
-                fr[k] = 0;
-                if (t < total) {
-                    while (r < 31 && pre[r + 1] <= t) r++;
-                    ev[k] = U_col[vbs[r] + (t - pre[r])];
-                    fr[k] = fvs[r];
+            for (int q = 0; q < CH_UNROLL; q++) {
+                const int tb = t0 + q * 32;
+                ev[q] = 0xFFFFFFFFu;
+                fr[q] = 0;
+                if (tb < total) {
+                    // starts of runs inside (tb, tb + 32): bit (start - tb)
+                    const unsigned bit =
+                        (my_start > tb && my_start < tb + 32) ? (1u << (my_start - tb)) : 0u;
+                    const unsigned m = __reduce_or_sync(FULL, bit);
+                    const int r = R + __popc(m & ((2u << lane) - 1u));
+                    const int t = tb + lane;
+                    if (t < total) {
+                        ev[q] = U_col[cvb[r] + t];
+                        fr[q] = cfv[r];
+                    }
+                    // run holding tb + 32: the last lane's, or the next one if
+                    // a run starts exactly there
+                    int rn = R + __popc(m);
+                    if (rn + 1 < k && cpre[rn + 1] == tb + 32) rn++;
+                    R = rn;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < CH_UNROLL; k++) {
-                const uint32_t e = ev[k];
+            for (int q = 0; q < CH_UNROLL; q++) {
+                const uint32_t e = ev[q];
+                if (e == 0xFFFFFFFFu) continue;
                 const uint32_t w = vid(e);
-                if (w >= (uint32_t)u) continue;  // the pivot's own chunk holds ids above it too
                 if (count_wedges) wedges++;
-                if (w < lo_id || w >= hi_id) continue;
-                const uint32_t fl = fr[k] & e & (FLAG_A | FLAG_B);
+                if (WIDE && (w < lo_id || w >= hi_id)) continue;
+                const uint32_t fl = fr[q] & e & (FLAG_A | FLAG_B);
                 if (!fl) continue;
                 if (WIDE) {
-                    const unsigned long long inc2 = ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
+                    const unsigned long long inc2 =
+                        ((fl & FLAG_A) ? (1ull << 32) : 0ull) | ((fl & FLAG_B) ? 1ull : 0ull);
                     const unsigned long long old = atomicAdd(&cnt64[w - lo_id], inc2);
                     if (fl & FLAG_A) qa += old >> 32;
                     if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
@@ -1039,38 +1213,70 @@ __global__ void __launch_bounds__(CH_THREADS, 1) k_c4_chunk(Ctl* c, const int32_
                                                         const long long* __restrict__ U_off,
                                                         const uint32_t* __restrict__ U_col,
                                                         const int32_t* __restrict__ U_split,
-                                                        const int32_t* __restrict__ T, int TW) {
+                                                        unsigned char* __restrict__ scratch, long long cap) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char ch_smem[];
     int* w_pre = (int*)(ch_smem + CH_BYTES);
     long long* w_vb = (long long*)(w_pre + CH_THREADS);
     uint32_t* w_fv = (uint32_t*)(w_vb + CH_THREADS);
     __shared__ int s_idx;
+    unsigned char* mine = scratch + (size_t)blockIdx.x * c4_chunk_cta_bytes(cap);
+    int32_t* T = (int32_t*)mine;
+    long long* rbase = (long long*)(mine + (size_t)cap * 4);
+    uint32_t* rflag = (uint32_t*)(mine + (size_t)cap * 4 + (size_t)(cap / 2) * 8);
     const bool wide = c->maxdeg >= 65536;
     const int cnt = c->nbin[BIN_C4_CHUNK];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
     unsigned long long qa = 0, qb = 0, wedges = 0;
     uint4* c4 = (uint4*)ch_smem;
     for (int i = threadIdx.x; i < CH_BYTES / 16; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
     for (;;) {
-        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[5], 1u);
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[WORK_C4_CHUNK], 1u);
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
         if (idx >= cnt) break;
-        const int32_t u = list[idx];
+        const uint32_t u = (uint32_t)list[idx];
         const long long rb = U_off[u];
         const int nlow = U_split[u];
         const int nch = (int)(((long long)u + CH_R - 1) / CH_R);
+        // phase 1: run starts of every lower neighbour's row, per chunk
+        for (int j = warp; j < nlow; j += NW) {
+            const uint32_t fv = U_col[rb + j];
+            const uint32_t v = vid(fv);
+            const long long vb = U_off[v];
+            const int d = (int)(U_off[v + 1] - vb);
+            if (lane == 0) {
+                rbase[j] = vb;
+                rflag[j] = fv;
+            }
+            int prev = -1;  // chunk of the entry before this step's first
+            for (int q0 = 0;; q0 += 32) {
+                const int q = q0 + lane;
+                int cb = nch;  // past the row, or an id >= u: the end of the runs
+                if (q < d) {
+                    const uint32_t w = vid(U_col[vb + q]);
+                    if (w < u) cb = (int)(w / CH_R);
+                }
+                int ca = __shfl_up_sync(FULL, cb, 1);
+                if (lane == 0) ca = prev;
+                for (int bb = ca + 1; bb <= cb; bb++) T[(size_t)bb * nlow + j] = q;
+                prev = __shfl_sync(FULL, cb, 31);
+                if (prev == nch) break;  // every chunk bound is written
+            }
+        }
+        __syncthreads();
+        // phase 2: chunk by chunk
         for (int b = 0; b < nch; b++) {
             const int halves = wide ? 2 : 1;
             for (int h = 0; h < halves; h++) {
                 const uint32_t span = wide ? CH_R / 2 : CH_R;
                 const uint32_t lo_id = (uint32_t)b * CH_R + h * span;
-                const uint32_t hi_id = min(lo_id + span, (uint32_t)u);
+                const uint32_t hi_id = min(lo_id + span, u);
                 if (lo_id >= hi_id) continue;
-                if (wide) chunk_pass<true>(U_off, U_col, T, TW, u, rb, nlow, b, lo_id, hi_id, ch_smem, w_pre, w_vb,
+                if (wide) chunk_walk<true>(U_col, T, rbase, rflag, nlow, b, u, lo_id, hi_id, ch_smem, w_pre, w_vb,
                                            w_fv, qa, qb, wedges, h == 0);
-                else chunk_pass<false>(U_off, U_col, T, TW, u, rb, nlow, b, lo_id, hi_id, ch_smem, w_pre, w_vb,
+                else chunk_walk<false>(U_col, T, rbase, rflag, nlow, b, u, lo_id, hi_id, ch_smem, w_pre, w_vb,
                                        w_fv, qa, qb, wedges, true);
                 __syncthreads();
                 // clear the counters this chunk used (16-byte granules)
@@ -1083,6 +1289,7 @@ __global__ void __launch_bounds__(CH_THREADS, 1) k_c4_chunk(Ctl* c, const int32_
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
     acc_add(c, 15, wedges);
+    acc_add(c, 20, wedges);
 }
 
 // Open-addressing insert into a table in global memory.  A slot holds
@@ -1127,7 +1334,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
     unsigned long long qa = 0, qb = 0, wedges = 0;
     for (;;) {
         if (tid == 0) {
-            s_idx = (int)atomicAdd(&c->work[4], 1u);
+            s_idx = (int)atomicAdd(&c->work[WORK_C4_CTA], 1u);
             s_wt = 0;
         }
         __syncthreads();
@@ -1329,11 +1536,16 @@ __global__ void k_finalize(Ctl* c, int mode) {
 namespace gcx {
 
 void count_setup_attributes() {
-    cudaFuncSetAttribute(k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tri_block<TRI_KM, BIN_TRI_BLOCK, WORK_TRI_BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tri_block_smem<TRI_KM>());
-    cudaFuncSetAttribute(k_tri_block<TRI_KS, BIN_TRI_SMALL, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tri_block<TRI_KS, BIN_TRI_SMALL, WORK_TRI_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tri_block_smem<TRI_KS>());
-    cudaFuncSetAttribute(k_c4_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_block_smem_bytes());
+    cudaFuncSetAttribute(k_c4_block<C4B_SMALL_LG, C4B_SMALL_THREADS, BIN_C4_BSMALL, WORK_C4_BSMALL, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)c4_block_smem<C4B_SMALL_LG, C4B_SMALL_THREADS>());
+    cudaFuncSetAttribute(k_c4_block<C4B_BIG_LG, C4B_BIG_THREADS, BIN_C4_BLOCK, WORK_C4_BLOCK, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)c4_block_smem<C4B_BIG_LG, C4B_BIG_THREADS>());
     cudaFuncSetAttribute(k_c4_dense_t<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_c4_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c4_chunk_smem_bytes());
 }
@@ -1383,7 +1595,7 @@ Tuning effective_tuning(const CountArgs& a) {
     t.c4_warp_max = std::max(t.c4_reg_max, std::min(t.c4_warp_max, C4_T1));
     t.c4_block_max = std::max(t.c4_warp_max, std::min(t.c4_block_max, C4_T2));
     t.c4_cta_max = std::max<long long>(t.c4_block_max, std::min<long long>(t.c4_cta_max, a.cta_table_words / 2));
-    if (!a.chunk_table || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
+    if (!a.chunk_scratch || a.chunk_cap <= 0 || t.c4_chunk_min <= 0) t.c4_chunk_min = NEVER;
     t.c4_chunk_min = std::max<long long>(t.c4_chunk_min, t.c4_cta_max);
     if (t.c4_chunk_max <= 0) t.c4_chunk_max = NEVER;
     if (t.c4_chunk_max <= t.c4_chunk_min) t.c4_chunk_min = NEVER;  // empty chunked bin
@@ -1399,7 +1611,8 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
     int gb = (int)std::min<long long>((nw + 255) / 256, 8LL * sms);
     const Tuning t = effective_tuning(a);
     pdl_launch(k_wedge_bound, dim3(8 * sms), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_col, a.U_split, a.U_wt);
-    pdl_launch(k_bin, dim3(gb), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t);
+    pdl_launch(k_bin, dim3(gb), dim3(256), 0, s, a.ctl, a.wlist, a.U_off, a.U_split, a.U_wt, a.bins, a.n_alloc, t,
+               t.c4_chunk_min < NEVER ? a.chunk_cap : 0ll);
     nl += 2;
     // The triangle kernels and the 4-cycle tiers are independent: with
     // auxiliary streams they run side by side (a fork after the binning, a
@@ -1414,17 +1627,23 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
         for (int i = 0; i < 3; i++) cudaStreamWaitEvent(a.aux[i], a.fork, 0);
     }
     k_tri_warp<<<4 * sms, TW * 32, 0, sT>>>(a.ctl, lists(BIN_TRI_WARP), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_block<TRI_KS, BIN_TRI_SMALL, 6><<<8 * sms, 256, tri_block_smem<TRI_KS>(), sT>>>(
+    k_tri_block<TRI_KS, BIN_TRI_SMALL, WORK_TRI_SMALL><<<8 * sms, 256, tri_block_smem<TRI_KS>(), sT>>>(
         a.ctl, lists(BIN_TRI_SMALL), a.U_off, a.U_col, a.U_split, a.tpack);
-    k_tri_block<TRI_KM, BIN_TRI_BLOCK, 1><<<2 * sms, 256, tri_block_smem<TRI_KM>(), sT>>>(
+    k_tri_block<TRI_KM, BIN_TRI_BLOCK, WORK_TRI_BLOCK><<<2 * sms, 256, tri_block_smem<TRI_KM>(), sT>>>(
         a.ctl, lists(BIN_TRI_BLOCK), a.U_off, a.U_col, a.U_split, a.tpack);
     k_tri_merge<<<sms, 256, 0, sT>>>(a.ctl, lists(BIN_TRI_MERGE), a.U_off, a.U_col, a.U_split, a.tpack);
     nl += 4;
     if (ev_c4) record_stage(ev_c4, sT);
     k_c4_reg<<<4 * sms, 256, 0, sC1>>>(a.ctl, lists(BIN_C4_REG), a.U_off, a.U_col, a.U_split);
-    k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, sC1>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split);
-    k_c4_block<<<sms, 256, c4_block_smem_bytes(), sC1>>>(a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col,
-                                                         a.U_split);
+    k_c4_warp<<<7 * sms, C4W_WARPS * 32, 0, sC1>>>(a.ctl, lists(BIN_C4_WARP), a.U_off, a.U_col, a.U_split,
+                                                   a.U_wt);
+    k_c4_block<C4B_SMALL_LG, C4B_SMALL_THREADS, BIN_C4_BSMALL, WORK_C4_BSMALL, false>
+        <<<6 * sms, C4B_SMALL_THREADS, c4_block_smem<C4B_SMALL_LG, C4B_SMALL_THREADS>(), sC1>>>(
+            a.ctl, lists(BIN_C4_BSMALL), a.U_off, a.U_col, a.U_split, a.U_wt);
+    k_c4_block<C4B_BIG_LG, C4B_BIG_THREADS, BIN_C4_BLOCK, WORK_C4_BLOCK, true>
+        <<<sms, C4B_BIG_THREADS, c4_block_smem<C4B_BIG_LG, C4B_BIG_THREADS>(), sC1>>>(
+            a.ctl, lists(BIN_C4_BLOCK), a.U_off, a.U_col, a.U_split, a.U_wt);
+    if (a.ev_heavy[0]) record_stage(a.ev_heavy[0], sC2);
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.dense_cluster_size * a.dense_clusters);
@@ -1443,12 +1662,11 @@ int enqueue_counting(const CountArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cud
                            (const long long*)a.U_wt, a.dense, a.n_alloc);
     }
     if (t.c4_chunk_min < NEVER) {
-        const int TW = c4_chunk_width(a.n_alloc);
-        k_chunk_bounds<<<8 * sms, 256, 0, sC2>>>(a.ctl, a.wlist, a.U_off, a.U_col, a.chunk_table, TW);
         k_c4_chunk<<<sms, CH_THREADS, c4_chunk_smem_bytes(), sC2>>>(a.ctl, lists(BIN_C4_CHUNK), a.U_off, a.U_col,
-                                                                    a.U_split, a.chunk_table, TW);
-        nl += 2;
+                                                                    a.U_split, a.chunk_scratch, a.chunk_cap);
+        nl += 1;
     }
+    if (a.ev_heavy[1]) record_stage(a.ev_heavy[1], sC2);
     k_c4_hash<<<a.cta_groups, C4_DENSE_THREADS, 0, s>>>(a.ctl, lists(BIN_C4_CTA), a.U_off, a.U_col, a.U_split,
                                                         a.cta_tables, a.cta_table_words);
     nl += 5;

@@ -37,16 +37,30 @@ enum {
     BIN_TRI_MERGE = 2,  // k > TRI_KM                      merge per out-edge
     BIN_C4_REG = 3,     // w~ <= 32                        registers (match)
     BIN_C4_WARP = 4,    // w~ <= C4_T1                     warp hash in shared memory
-    BIN_C4_BLOCK = 5,   // w~ <= C4_T2                     block hash in shared memory
+    BIN_C4_BLOCK = 5,   // C4B_SMALL_MAX < w~ <= C4_T2     block hash in shared memory
     BIN_C4_DENSE = 6,   // C4_T3 < w~ <= c4_chunk_min      cluster, shared dense counter array
     BIN_C4_CTA = 7,     // C4_T2 < w~ <= C4_T3             CTA, own hash table in global memory
     BIN_C4_CHUNK = 8,   // w~ > c4_chunk_min (off)         CTA, shared-memory counters over id-range chunks
     BIN_TRI_SMALL = 9,  // 32 < k <= TRI_KS                block per root, small shared footprint
-    NBINS = 10
+    BIN_C4_BSMALL = 10, // w~ <= C4B_SMALL_MAX             block hash in shared memory, small table
+    NBINS = 11
+};
+
+// Work counters (Ctl::work) of the kernels that take their roots or pivots
+// one at a time; kernels that run side by side need different counters.
+enum {
+    WORK_TRI_BLOCK = 1,   // k_tri_block, long out-lists
+    WORK_C4_BLOCK = 2,    // k_c4_block, large table
+    WORK_C4_DENSE = 3,    // k_c4_dense_t, clusters
+    WORK_C4_CTA = 4,      // k_c4_hash (and k_c4_dense_t without clusters)
+    WORK_C4_CHUNK = 5,    // k_c4_chunk
+    WORK_TRI_SMALL = 6,   // k_tri_block, short out-lists
+    WORK_C4_BSMALL = 7,   // k_c4_block, small table
+    NWORK = 8
 };
 
 constexpr int ACC_STRIPES = 32;  // copies of each accumulator (spreads the atomics of many warps)
-constexpr int NACC = 20;         // accumulator slots (see Ctl::acc)
+constexpr int NACC = 23;         // accumulator slots (see Ctl::acc)
 
 // Device control block: sizes produced and consumed on the device, so a
 // batch's kernels never wait for the host between stages.
@@ -62,6 +76,8 @@ struct Ctl {
                                      // [12] |E(G_a)|, [13] |E(G_b)|, [14] triangle work, [15] wedges
                                      // [16] sum of t_e in G_a (3 triangles), [17] in G_b,
                                      // [18] sum C(d,2) in G_a (2-paths), [19] in G_b
+                                     // heavy-pivot 4-cycle tier: [20] wedges, [21] L2
+                                     // reductions, [22] L2 atomics returning the old value
     unsigned long long F[6];         // maintained counts
     long long Ca[6], Cb[6];          // induced counts of G_a, G_b of the last pass
     long long sa[6], sb[6];          // their non-induced sums (TT halved)
@@ -69,7 +85,7 @@ struct Ctl {
     unsigned long long scratch_tail; // bump pointer of the commit scratch
     int overflow;                    // commit needs a re-layout
     int err;                         // GC_E* code raised on the device
-    unsigned work[8];                // dynamic work counters
+    unsigned work[NWORK];            // dynamic work counters (WORK_*)
     int nbin[NBINS];                 // sizes of the work bins (see gc_count.cu)
     int maxdeg;                      // largest union-graph degree in the region
     // batch source and sequencing (a captured batch graph reads these)
@@ -104,8 +120,11 @@ constexpr int TRI_KM = 512;
 constexpr int TRI_KS = 128;
 constexpr int C4_T1 = 512;
 constexpr int C4_T2 = 8192;
+constexpr int C4B_SMALL_MAX = 2048;  // block-hash pivots up to this bound use the small table
 constexpr long long C4_T3 = 32768;
 constexpr int C4_CLUSTER = 8;       // CTAs per cluster of the dense 4-cycle kernel
+constexpr int CH_BYTES = 196608;    // shared counter bytes of the chunked 4-cycle kernel
+constexpr int CH_R = CH_BYTES / 4;  // ids per chunk (49,152)
 
 // Bin boundaries of the counting pass (upper bounds of each tier; each at
 // most the capacity its kernel was compiled for).  Chosen per graph by the

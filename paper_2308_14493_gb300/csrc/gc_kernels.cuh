@@ -86,19 +86,26 @@ struct CountArgs {
     unsigned long long* cta_tables; // cta_groups * cta_table_words zeroed words
     long long cta_table_words;      // power of two; pivots up to half of it use the hash tier
     int cta_groups;                 // CTAs of the medium 4-cycle kernel (one table each)
-    int32_t* chunk_table;           // n_alloc * c4_chunk_width(n_alloc) run bounds of the chunked 4-cycle kernel
+    unsigned char* chunk_scratch;   // sms * c4_chunk_cta_bytes(chunk_cap): per-CTA run bounds of the chunked kernel
+    long long chunk_cap;            // run-bound entries per CTA (0: the chunked tier is off)
     Tuning tune;                    // bin boundaries (clamped to the capacities)
     int sms;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // side streams of the counting pass (or none)
     cudaEvent_t fork = nullptr;     // fork / join events for them (timing disabled)
     cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_heavy[2] = {nullptr, nullptr};  // around the heavy-pivot 4-cycle kernels, on their stream
 };
 Tuning effective_tuning(const CountArgs& a);
 // Dynamic shared-memory limits of the counting kernels (once per device).
 void count_setup_attributes();
 size_t c4_chunk_smem_bytes();
 int c4_chunk_width(long long n);                 // id-range chunks + 1
-long long c4_chunk_table_entries(long long n);   // entries of the run-bound table, -1 if too large
+long long c4_chunk_cap(long long n);             // run-bound entries per CTA for ids below n
+// bytes of one CTA's scratch of the chunked kernel: run bounds int32[cap],
+// row starts int64[cap / 2], row flags uint32[cap / 2]
+__host__ __device__ inline size_t c4_chunk_cta_bytes(long long cap) {
+    return (size_t)cap * 4 + (size_t)(cap / 2) * 12;
+}
 // Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
 // 16 if the device can co-schedule it, else 8) and the number of clusters.
 int dense_cluster_plan(int want, int sms, int* size_out);

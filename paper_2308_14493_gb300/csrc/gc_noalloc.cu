@@ -61,6 +61,12 @@ int g_sms[128] = {};     // multiprocessors per device
 // Checks the caller's CSR (sorted rows, ids in range, no self-loops,
 // symmetric) and builds the flagged union-graph view the counting kernels read:
 // every entry belongs to both graphs, so both counts equal the static count.
+// Edges are oriented by the caller's ids as they are (no degree renumbering,
+// which would need scratch of its own): a 4-cycle pivot u walks every lower
+// neighbour's row, so the wedge work is at most sum over edges of the lower
+// endpoint's degree (m * d_max) rather than the degree-ordered bound that
+// gc_count_static reaches after renumbering.  Any order gives exact counts;
+// at the 16,384-vertex cap the worst case stays small.
 __global__ void k_na_build(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int n, long long nnz,
                            Ctl* c, long long* __restrict__ U_off, uint32_t* __restrict__ U_col,
                            int32_t* __restrict__ U_split, int32_t* __restrict__ da, int32_t* __restrict__ db,
@@ -183,21 +189,26 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     if (grid > 1024) grid = 1024;
     // what must start at zero: flags, accumulators, triangle counters and the
     // 4-cycle counters (an interrupted earlier call may have left them dirty)
+    const bool stale = cudaPeekAtLastError() != cudaSuccess;
     k_na_reset<<<1, 32, 0, s>>>(ctl, bad);
-    cudaMemsetAsync(tpack, 0, 8 * (size_t)std::max<long long>(nnz, 1), s);
     // per-cluster counter arrays are laid out with an even word stride
-    cudaMemsetAsync(dense, 0, 8 * (size_t)((nn + 1) & ~1) * NA_DENSE_CLUSTERS, s);
-    cudaMemsetAsync(cta_tables, 0, 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS, s);
+    if (cudaMemsetAsync(tpack, 0, 8 * (size_t)std::max<long long>(nnz, 1), s) != cudaSuccess ||
+        cudaMemsetAsync(dense, 0, 8 * (size_t)((nn + 1) & ~1) * NA_DENSE_CLUSTERS, s) != cudaSuccess ||
+        cudaMemsetAsync(cta_tables, 0, 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS, s) != cudaSuccess)
+        return GC_ECUDA;
     k_reset_count<<<1, 32, 0, s>>>(ctl);
     k_na_build<<<grid, NA_TPB, 0, s>>>(d_row_ptr, d_col, n, nnz, ctl, U_off, U_col, U_split, da, db, wlist, bad);
     k_na_fill<<<grid, NA_TPB, 0, s>>>(d_row_ptr, d_col, n, nnz, U_col, bad);
+    // a launch that failed shows in the runtime's last error; a failure
+    // while the kernels run shows in the synchronisation's own result.  An
+    // error the caller's earlier work left pending is not read or cleared
+    // (it stays with its owner), and then launch errors are not told apart.
+    if (!stale && cudaGetLastError() != cudaSuccess) return GC_ECUDA;
     // the counting kernels index by the ids they read, so they run only on a
     // CSR that passed the checks
     int hbad = 0;
-    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return GC_ECUDA;
+    if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GC_ECUDA;
     if (hbad) return GC_EINVAL;
     CountArgs ca;
     ca.ctl = ctl;
@@ -216,16 +227,16 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     ca.dense_cluster_size = 8;
     ca.cta_tables = cta_tables;
     ca.cta_table_words = NA_TABLE_WORDS;
-    ca.chunk_table = nullptr;  // no chunked 4-cycle tier in the fixed scratch
+    ca.chunk_scratch = nullptr;  // no chunked 4-cycle tier in the fixed scratch
+    ca.chunk_cap = 0;
     ca.tune = default_tuning();
     ca.cta_groups = NA_CTA_GROUPS;
     ca.sms = sms;
     enqueue_counting(ca, s, nullptr, nullptr, nullptr, 1);
+    if (!stale && cudaGetLastError() != cudaSuccess) return GC_ECUDA;
     long long Ca[6];
-    cudaMemcpyAsync(Ca, ctl->Ca, sizeof(Ca), cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return GC_ECUDA;
+    if (cudaMemcpyAsync(Ca, ctl->Ca, sizeof(Ca), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GC_ECUDA;
     for (int i = 0; i < 6; i++) out[i] = (uint64_t)Ca[i];
     return GC_OK;
 }

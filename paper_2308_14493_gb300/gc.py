@@ -45,7 +45,9 @@ class gc_stats(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 4),
                 ("ms_stage", ctypes.c_float * 8), ("work_triangles", ctypes.c_int64),
                 ("work_wedges", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved2", ctypes.c_int32 * 3),
-                ("C3a", ctypes.c_int64 * 2), ("C3b", ctypes.c_int64 * 2)]
+                ("C3a", ctypes.c_int64 * 2), ("C3b", ctypes.c_int64 * 2),
+                ("work_wedges_heavy", ctypes.c_int64), ("l2_red_heavy", ctypes.c_int64),
+                ("l2_atom_heavy", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         out = {}

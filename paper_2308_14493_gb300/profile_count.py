@@ -1,7 +1,7 @@
 """Static count of a seeded Chung-Lu graph, repeated, for kernel profiling.
 
     python -m paper_2308_14493_gb300.profile_count --n 800000 --m 15000000 \\
-        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local] [--vertex | --edge]
+        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local] [--vertex | --edge] [--tuning JSON]
 
 Opens the graph (one static count), then runs ``reps`` more static counts
 (or, with ``--batch``, ``reps`` sequential batches of that many updates, 60%
@@ -44,6 +44,8 @@ def main():
                     help="with --vertex / --edge: comma-separated local_c4_heavy_min values, each timed in turn")
     ap.add_argument("--chunk-threshold", type=int, default=0,
                     help="wedge bound above which 4-cycle pivots use the chunked shared-memory kernel")
+    ap.add_argument("--tuning", default="", help="JSON object of bin boundaries to set after the open "
+                                                 "(e.g. '{\"c4_chunk_min\": 262144}'), applied after --autotune")
     a = ap.parse_args()
     keys = gen.chung_lu_graph(a.n, a.m, a.gamma, a.dmax, a.seed)
     rp, col = gen.csr_from_keys(a.n, keys)
@@ -53,6 +55,9 @@ def main():
         if a.autotune:
             best, ms = g.autotune(reps=2)
             print(json.dumps({"autotune_ms": ms, "tuning": best}), flush=True)
+        if a.tuning:
+            g.set_tuning(**json.loads(a.tuning))
+            print(json.dumps({"tuning": g.tuning()}), flush=True)
         heavy = [int(x) for x in a.heavy_min.split(",") if x] or [None]
         if a.edge or a.vertex:
             for hm, edge in [(h, ed) for ed in ([False] if a.vertex else []) + ([True] if a.edge else [])
@@ -82,7 +87,10 @@ def main():
                 g.count_static()
                 st = g.stats()
                 print(json.dumps({"static_ms": st["ms_device"], "stage_ms": st["ms_stage"],
-                                  "work_triangles": st["work_triangles"], "work_wedges": st["work_wedges"]}),
+                                  "work_triangles": st["work_triangles"], "work_wedges": st["work_wedges"],
+                                  "heavy_ms": st["ms_stage"][7], "work_wedges_heavy": st["work_wedges_heavy"],
+                                  "l2_red_heavy": st["l2_red_heavy"], "l2_atom_heavy": st["l2_atom_heavy"],
+                                  "counts": g.counts()}),
                       flush=True)
 
 

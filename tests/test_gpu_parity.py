@@ -143,6 +143,7 @@ TUNINGS = {
     "tri_small_block": dict(tri_warp_max=8, tri_small_max=20, tri_block_max=40),
     "c4_warp_hash": dict(c4_reg_max=1, c4_warp_max=512, c4_block_max=512, c4_cta_max=512),
     "c4_block_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=8192, c4_cta_max=8192),
+    "c4_small_block_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=2048, c4_cta_max=2048),
     "c4_cta_hash": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=32768),
     "c4_all_cluster": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=0),
     "c4_all_chunk": dict(c4_reg_max=1, c4_warp_max=1, c4_block_max=1, c4_cta_max=1, c4_chunk_min=1),
@@ -601,6 +602,71 @@ def test_fullsize_c3_local_batches_keep_counts_of_the_graph(gcb):
             assert gl.stats()["path"] == 1
             assert out == gr.apply(ins, dels)
         assert gl.count_static() == gl.counts()
+        # the oracle's count of the final edge set (Lemma 2: the maintained
+        # counts are those of the updated graph)
+        gold = _large_gold().get("c3_local_stream")
+        if gold is not None:
+            assert gold["sizes"] == [10, 100, 1000, 10, 100] and gold["seed"] == 77
+            assert gl.counts() == gold["final"]
+            assert gl.num_edges() == gold["edges"]
+
+
+def _c5_gold():
+    p = os.path.join(GOLDEN_DIR, "workloads_c5.json")
+    if not os.path.exists(p):
+        pytest.skip("workloads_c5.json not generated")
+    with open(p) as f:
+        return json.load(f)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("gi", [0, 7], ids=["n100k_m1M", "n4.8M_m69M"])
+def test_fullsize_c5_graph_static_and_batch(gcb, gi):
+    """The smallest and the largest graph of the serving workload (Chung-Lu,
+    1M and 69M edges): static count and one 100,000-update batch (70%
+    insertions) against stored oracle results, with the counts of G_a and G_b
+    and the region size."""
+    gold = _c5_gold().get(f"g{gi}")
+    if gold is None:
+        pytest.skip(f"graph {gi} of the serving workload not in workloads_c5.json")
+    p = gen.c5_graph_params()[gi]
+    assert gold["params"] == p
+    n, keys = gen.workload_graph(p)
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.batch_stream(n, keys, [100000], 0.7, 500 + gi)[0]
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == gold["static"]
+        out = g.apply(ins, dels)
+        st = g.stats()
+        assert out == gold["after"]
+        assert st["Ca"] == gold["Ca"] and st["Cb"] == gold["Cb"]
+        assert st["region_vertices"] == gold["region_vertices"]
+        assert (st["n_ins"], st["n_del"]) == (gold["n_ins"], gold["n_del"])
+        assert g.count_static() == out
+
+
+@pytest.mark.slow
+def test_fullsize_c5_stream_plain_and_served(gcb):
+    """A sequential stream of 5 batches (100..100,000 updates, log-uniform)
+    on the 1M-edge serving graph: the counts after every batch equal the
+    oracle's, through gc_apply_batch and through the request server."""
+    gold = _c5_gold().get("g0_stream")
+    if gold is None:
+        pytest.skip("stream of the serving workload not in workloads_c5.json")
+    n, keys = gen.workload_graph(gen.c5_graph_params()[0])
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, gold["sizes"], 0.7, gold["seed"])
+    expect = [s["after"] for s in gold["steps"][1:]]
+    with open_graph(gcb, n, rp, col) as g:
+        assert g.counts() == gold["steps"][0]["static"]
+        assert [g.apply(i, d) for i, d in batches] == expect
+    with open_graph(gcb, n, rp, col) as g:
+        with gcb.Server([g], slots=2) as srv:
+            tickets = [srv.submit(0, i, d) for i, d in batches]
+            res = [srv.wait(t) for t in tickets]
+        assert all(r["status"] == 0 for r in res)
+        assert [r["counts"] for r in res] == expect
+        assert g.counts() == expect[-1]
 
 
 # ----------------------------------------------------------- batched form --
