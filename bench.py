@@ -64,6 +64,11 @@ HEAVY_KERNEL = "k_c4_dense_t (heavy 4-cycle pivots; with k_c4_chunk when the tun
 # nothing, and atomics that return the old value
 PROBE_L2_RED_PER_S = 204e9
 PROBE_L2_ATOM_PER_S = 55e9
+# DRAM bytes (read + written) per wedge of the heavy-pivot kernel, from one
+# ncu capture of it on the half-size graph (n=800,000 m=15M, same generator):
+# 3.587 GB over 1.302e9 wedges;
+# None once the kernel changes
+HEAVY_DRAM_BYTES_PER_WEDGE = 3.587e9 / 1.302e9
 WORKLOADS_DESC_C4 = ("Chung-Lu n=2.4M m=5M gamma=1.8 dmax=100,000; 64 independent batches, sizes log-uniform "
                      "10..50,000, 50% ins / 50% del")
 
@@ -301,7 +306,10 @@ def heavy_roofline(recs, peak, peak_kind):
     return {"bound": "hbm", "kernel": HEAVY_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
             "frac_of_nominal_8_tbs": achieved / 8000.0 if achieved else None,
-            "algorithmic_bytes": bytes_, "wedges": wedges, "kernel_ms": ms, "traffic": None,
+            "algorithmic_bytes": bytes_, "wedges": wedges, "kernel_ms": ms,
+            "traffic": HEAVY_DRAM_BYTES_PER_WEDGE * wedges if HEAVY_DRAM_BYTES_PER_WEDGE else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the n=800,000 "
+                              "m=15M graph, per wedge, times this launch's wedges",
             "l2_atomics": {"reductions": red, "returning": atom,
                            "ops_per_s": (red + atom) / sec if sec > 0 else None,
                            "probe_red_per_s": PROBE_L2_RED_PER_S, "probe_atom_per_s": PROBE_L2_ATOM_PER_S,

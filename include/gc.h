@@ -51,7 +51,12 @@ typedef struct gc_graph gc_graph;
 /* Options for gc_open.  Zero-initialised fields take the defaults. */
 typedef struct {
     /* Device allocator callbacks (both or neither).  alloc returns device
-       memory of at least `bytes` bytes usable on `stream`, or NULL. */
+       memory of at least `bytes` bytes usable on `stream` (the handle's
+       stream), or NULL, which makes the call that needed it return
+       GC_ENOMEM with the graph and its counts unchanged; free releases a
+       pointer alloc returned, in the order of `stream`.  NULL for both: the
+       library uses cudaMallocAsync / cudaFreeAsync on its stream.  The
+       Python binding's TorchAllocator passes PyTorch's caching allocator. */
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
     void (*free)(void *ptr, void *stream, void *ctx);
     void *ctx;

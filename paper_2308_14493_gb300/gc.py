@@ -173,9 +173,64 @@ def _pairs(p):
     return a, a.shape[0]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator, through
+    the gc_options alloc / free callbacks: every buffer the library takes is
+    a block of torch's pool, allocated and released in the order of the
+    library's stream (the stream the callback receives).  ``live`` maps each
+    outstanding pointer to its size; ``fail`` set True (or ``fail_after``
+    set to a count of allocations) makes every later allocation return NULL,
+    as an exhausted pool would (the library then reports GC_ENOMEM).  Keep
+    the object alive while any handle opened with it is open."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.live: dict[int, int] = {}
+        self.allocs = 0
+        self.fail = False
+        self.fail_after: int | None = None
+        self._lock = threading.Lock()
+        self._alloc_cb = ALLOC_FN(self._alloc)
+        self._free_cb = FREE_FN(self._free)
+
+    def _alloc(self, size, stream, ctx):
+        if self.fail or (self.fail_after is not None and self.allocs >= self.fail_after):
+            return None
+        try:
+            p = self._torch.cuda.caching_allocator_alloc(int(size), self.device, int(stream or 0))
+        except Exception:  # out of memory: the library sees NULL and returns GC_ENOMEM
+            return None
+        with self._lock:
+            self.live[int(p)] = int(size)
+            self.allocs += 1
+        return p
+
+    def _free(self, ptr, stream, ctx):
+        if not ptr:
+            return
+        with self._lock:
+            self.live.pop(int(ptr), None)
+        self._torch.cuda.caching_allocator_delete(int(ptr))
+
+    def options(self, opt) -> None:
+        opt.alloc = ctypes.cast(self._alloc_cb, ctypes.c_void_p)
+        opt.free = ctypes.cast(self._free_cb, ctypes.c_void_p)
+        opt.ctx = None
+
+
 def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0,
-            chunk_threshold: int = 0, dense_cluster: int = 0, local_max_pairs: int = 0):
-    """Open a graph from a symmetric CSR; returns an opaque handle."""
+            chunk_threshold: int = 0, dense_cluster: int = 0, local_max_pairs: int = 0,
+            allocator: TorchAllocator | None = None):
+    """Open a graph from a symmetric CSR; returns an opaque handle.  With an
+    ``allocator`` (e.g. TorchAllocator) the library takes its device memory
+    through it instead of cudaMallocAsync."""
     lib = load()
     rp = _i32(row_ptr)
     c = _i32(col) if len(col) else np.zeros(1, np.int32)
@@ -187,6 +242,8 @@ def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, str
     opt.chunk_threshold = chunk_threshold
     opt.dense_cluster = dense_cluster
     opt.local_max_pairs = local_max_pairs
+    if allocator is not None:
+        allocator.options(opt)
     h = ctypes.c_void_p()
     rc = lib.gc_open(int(n), _ptr(rp), _ptr(c), ctypes.byref(opt), ctypes.byref(h))
     _check(rc, None)
@@ -500,6 +557,7 @@ class Graph:
 
     def __init__(self, n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, **opts):
         self.n = int(n)
+        self.allocator = opts.get("allocator")  # kept alive as long as the handle
         self.h = gc_open(n, row_ptr, col, region_hops, slack, **opts)
 
     def close(self):
