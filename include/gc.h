@@ -94,7 +94,9 @@ typedef struct {
     float ms_device;                /* device time of the batch (CUDA events) */
     float ms_wall;                  /* host wall time of the call */
     int32_t relayouts;              /* adjacency re-layouts the batch needed */
-    int32_t path;                   /* 0: region recount (Algorithm 2); 1: edge-local delta, for
+    int32_t path;                   /* 0: region recount (Algorithm 2); 2: a batched run whose
+                                       later batches went in pairs (gc_tuning.pair_min_share);
+                                       1: edge-local delta, for
                                        which region_vertices is |V_X| (the endpoints),
                                        region_entries their union-row entries, Ca / sums_a the
                                        six induced / non-induced deltas and Cb / sums_b zero,
@@ -371,7 +373,13 @@ typedef struct {
                                    are walked 8 at a time by the whole GPU, each with its own
                                    counter array in L2; the others by one CTA each on per-CTA
                                    arrays; 0 = never (default 65536) */
-    int64_t reserved[1];
+    int64_t pair_min_share; /* gc_apply_batches*, sequential runs: when the region pass of a run's
+                               first batch holds at least this many per mille of the graph's 2m
+                               adjacency entries, the later batches go in pairs: the first of a
+                               pair is committed without a count, the second counted over every
+                               vertex, which gives the whole graph's counts after both (the
+                               counts are the same; one pass instead of two); 0 = never
+                               (default 700) */
 } gc_tuning;
 
 int gc_get_tuning(const gc_graph *g, gc_tuning *t);

@@ -119,6 +119,13 @@ struct gc_graph {
     int l_t2 = -1;                       // captured with maintained triangle sums
     int p_t2 = -1;                       // the same for the plain region form
     int g_t2 = -1;                       // and for the batched region form
+    // the two-batch form of sequential runs: [0] commits a batch without a
+    // count, [1] counts the next one over every vertex (enqueue_batch roles)
+    cudaGraphExec_t qexec[2] = {nullptr, nullptr};
+    long long q_nk[2] = {-1, -1};
+    unsigned long long q_gen[2] = {0, 0};
+    int q_launches[2] = {0, 0};
+    long long pair_min_share = 700;      // per mille of 2m (gc_tuning.pair_min_share)
     // maintained triangle sums of the edge-local path: T2[x] = sum of t_e
     // over the edges at x, valid after a static count and kept by local
     // batches (a region batch makes it stale)
@@ -263,13 +270,33 @@ __global__ void k_begin_batch(Ctl* c, const long long* desc) {
     for (int k = 0; k < 5; k++) c->l_tot[k] = 0;
 }
 
-// result of the current batch to out[cur], advance the cursor
-__global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit) {
+// result of the current batch to out[cur], advance the cursor; the second
+// batch of a two-batch pass also writes the first one's result
+__global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit, int pair_second) {
     pdl_enter();
     if (threadIdx.x != 0 || !c->active) return;
+    if (pair_second && c->cur > 0 && !c->err)
+        for (int k = 0; k < 6; k++) out[6 * (long long)(c->cur - 1) + k] = c->prev_out[k];
     for (int k = 0; k < 6; k++) out[6 * (long long)c->cur + k] = c->last_out[k];
     if (commit && !c->err && !c->lovf) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
     c->cur++;
+}
+
+// every pair of a run in range and not a self-loop (bad = 1 otherwise)
+__global__ void k_run_pairs_check(const long long* desc, int k, int n, int* bad) {
+    pdl_enter();
+    const int32_t* ins = (const int32_t*)__ldcg(desc);
+    const int32_t* del = (const int32_t*)__ldcg(desc + 1);
+    for (int b = blockIdx.y; b < k; b += gridDim.y) {
+        const long long* d = desc + 2 + 4 * (long long)b;
+        const long long io = __ldcg(d), ni = __ldcg(d + 1), dof = __ldcg(d + 2), nd = __ldcg(d + 3);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ni + nd;
+             i += (long long)gridDim.x * blockDim.x) {
+            const int32_t* p = i < ni ? ins + 2 * (io + i) : del + 2 * (dof + i - ni);
+            const int32_t x = p[0], y = p[1];
+            if (x < 0 || y < 0 || x >= n || y >= n || x == y) atomicExch(bad, 1);
+        }
+    }
 }
 
 __global__ void k_run_reset(Ctl* c) {
@@ -457,6 +484,11 @@ static int ensure_local(gc_graph* g, long long cap) {
 // Free the scratch that the next batch re-creates on demand.
 static void trim_scratch(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
+    for (int i = 0; i < 2; i++)
+        if (g->qexec[i]) {
+            cudaGraphExecDestroy(g->qexec[i]);
+            g->qexec[i] = nullptr;
+        }
     if (g->gexec) {
         cudaGraphExecDestroy(g->gexec);
         g->gexec = nullptr;
@@ -677,8 +709,13 @@ static int enqueue_segments(gc_graph* g, bool clear) {
 //   commit:     apply G <- G \ D u A (else an independent what-if batch)
 //   timed:      record the stage events (event-record nodes in the graph)
 //   local:      the edge-local delta instead of the region recount
+// role 0: the batch as Algorithm 2 (region, recount of G_a and G_b, commit);
+// the two-batch form (sequential runs whose regions cover the graph): role 1
+// normalises and commits the first batch of a pair without counting, role 2
+// counts the second over every vertex (C_b = the whole graph after the first
+// batch, C_a = after the second) and commits it.
 static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed, bool local = false,
-                         bool t2 = false) {
+                         bool t2 = false, int role = 0) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
     pdl_launch(k_begin_batch, dim3(1), dim3(32), 0, s, g->ctl, g->desc);
@@ -709,17 +746,28 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     pdl_launch(k_bfs_sources, dim3(ge), dim3(TPB), 0, s, g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
     pdl_launch(k_level_mark, dim3(1), dim3(1), 0, s, g->ctl, 0);
     g->launches += 2;
-    for (int L = 1; L <= (local ? 0 : g->hops); L++) {
-        pdl_launch(k_bfs_expand, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, L, g->row_start, g->deg, g->col,
-                   g->visited, g->wlist);
+    if (role == 2) {
+        pdl_launch(k_region_rest, dim3(grid_elems(g, g->n)), dim3(TPB), 0, s, g->ctl, g->n, g->visited, g->wlist);
+        g->launches++;
+    }
+    for (int L = 1; L <= (local || role == 1 ? 0 : g->hops); L++) {
+        if (role == 0) {
+            pdl_launch(k_bfs_expand, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, L, g->row_start, g->deg, g->col,
+                       g->visited, g->wlist);
+            g->launches++;
+        }
         pdl_launch(k_level_mark, dim3(1), dim3(1), 0, s, g->ctl, L);
-        g->launches += 2;
+        g->launches++;
     }
     CKL();
     if (timed) CK(record_stage(g->ev[2], s));
-    int rc = local ? count_local(g, commit ? 1 : 0, timed, t2) : count_region(g, commit ? 0 : 2, false, timed);
-    if (rc) return rc;
-    if (!local && commit && t2) {
+    int rc = GC_OK;
+    if (role != 1) {
+        rc = local ? count_local(g, commit ? 1 : 0, timed, t2)
+                   : count_region(g, role == 2 ? 3 : (commit ? 0 : 2), false, timed);
+        if (rc) return rc;
+    }
+    if (!local && commit && t2 && role == 0) {
         // keep the triangle sums of the edge-local path
         CK(cudaMemsetAsync(g->visited2, 0, sizeof(uint32_t) * (size_t)((g->n + 31) / 32 + 1), s));
         pdl_launch(k_t2_mark, dim3(grid_warps(g)), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited2, g->T2);
@@ -738,7 +786,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
         rc = enqueue_segments(g, true);
         if (rc) return rc;
     }
-    pdl_launch(k_end_batch, dim3(1), dim3(32), 0, s, g->ctl, g->out_dev.p, commit ? 1 : 0);
+    pdl_launch(k_end_batch, dim3(1), dim3(32), 0, s, g->ctl, g->out_dev.p, commit ? 1 : 0, role == 2 ? 1 : 0);
     g->launches++;
     CKL();
     return GC_OK;
@@ -868,7 +916,7 @@ static void fill_stats(gc_graph* g, const Ctl& c) {
 // Capture the per-batch launch sequence (batch from the run cursor) into
 // *exec; timed: with the stage events as event-record nodes.
 static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool timed, cudaGraphExec_t* exec,
-                         int* launches, bool local = false, bool t2 = false) {
+                         int* launches, bool local = false, bool t2 = false, int role = 0) {
     cudaStream_t s = g->s;
     if (*exec) {
         cudaGraphExecDestroy(*exec);
@@ -878,7 +926,7 @@ static int capture_batch(gc_graph* g, long long shape_nk, bool commit, bool time
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const int lsave = g->launches;
     g->launches = 0;
-    int rc = enqueue_batch(g, shape_nk, commit, timed, local, t2);
+    int rc = enqueue_batch(g, shape_nk, commit, timed, local, t2, role);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     *launches = g->launches;
     g->launches = lsave;
@@ -1068,15 +1116,62 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
         g->g_gen = g->buf_gen;
         g->g_t2 = (int)t2;
     }
+    // the two-batch form: a sequential run of at least three batches whose
+    // pairs pass the device check (a bad pair makes its batch a no-op, which
+    // the pairing does not model); batch 0 runs as Algorithm 2 and its region
+    // decides whether the rest go in pairs
+    bool pair_ok = commit && k >= 3 && g->pair_min_share > 0;
+    if (pair_ok) {
+        CK(cudaMemsetAsync(g->hist.p, 0, sizeof(int), s));
+        k_run_pairs_check<<<dim3(64, (unsigned)std::min(k, 64)), TPB, 0, s>>>(g->desc, k, g->n, (int*)g->hist.p);
+        CKL();
+        int bad = 0;
+        CK(cudaMemcpyAsync(&bad, g->hist.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        pair_ok = bad == 0;
+    }
+    bool pairs = false;  // batches 1 .. k-1 go in pairs
+    int pairs_used = 0;
+    auto role_of = [&](int i) {
+        if (!pairs || i == 0) return 0;
+        if ((i - 1) % 2 == 0) return i + 1 < k ? 1 : 0;
+        return 2;
+    };
+    auto ensure_exec = [&](int role) -> int {
+        if (role == 0) return GC_OK;
+        const int q = role - 1;
+        if (!g->qexec[q] || g->q_nk[q] != shape_nk || g->q_gen[q] != g->buf_gen) {
+            int r = capture_batch(g, shape_nk, true, false, &g->qexec[q], &g->q_launches[q], false, false, role);
+            if (r) return r;
+            g->q_nk[q] = shape_nk;
+            g->q_gen[q] = g->buf_gen;
+        }
+        return GC_OK;
+    };
     CK(cudaEventRecord(g->e0, s));
     int done = 0;
+    long long launches = 0;
     while (done < k) {
-        for (int i = done; i < k; i++) CK(cudaGraphLaunch(g->gexec, s));
+        const int upto = (pair_ok && !pairs && done == 0) ? 1 : k;
+        for (int i = done; i < upto; i++) {
+            const int role = role_of(i);
+            rc = ensure_exec(role);
+            if (rc) return rc;
+            CK(cudaGraphLaunch(role == 0 ? g->gexec : g->qexec[role - 1], s));
+            launches += role == 0 ? g->g_launches : g->q_launches[role - 1];
+            pairs_used += role == 2 ? 1 : 0;
+        }
         rc = read_ctl(g);
         if (rc) return rc;
         done = g->h_ctl->cur;
+        if (pair_ok && !pairs && upto == 1 && done >= 1) {
+            // batch 0's region against the graph's adjacency entries
+            pairs = (double)g->h_ctl->nU * 1000.0 >= (double)g->pair_min_share * 2.0 * (double)g->m;
+            pair_ok = false;
+        }
         if (g->h_ctl->halt) {
-            // batch done-1 is counted but its commit waits for pool space
+            // batch done-1 is counted (or, first of a pair, only normalised)
+            // but its commit waits for pool space
             rc = finish_pending_commit(g, &relayouts);
             if (rc) return rc;
             if (g->g_gen != g->buf_gen) {
@@ -1087,6 +1182,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
             }
         }
     }
+    if (pairs_used) g->t2_valid = false;  // first batches of pairs did not keep the triangle sums
     CK(cudaEventRecord(g->e1, s));
     std::vector<unsigned long long> res((size_t)6 * std::max(k, 1));
     CK(cudaMemcpyAsync(res.data(), g->out_dev.p, sizeof(unsigned long long) * 6 * (size_t)k, cudaMemcpyDeviceToHost,
@@ -1108,7 +1204,8 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     g->st.n_del_raw = raw_del;
     g->st.ms_device = ms;
     g->st.relayouts = relayouts;
-    g->st.launches = g->g_launches * k;
+    g->st.launches = (int)launches;
+    g->st.path = pairs_used ? 2 : 0;
     for (int i = 0; i < 8; i++) g->st.ms_stage[i] = 0.f;
     g->st.num_edges = g->m;
     g->st.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1159,6 +1256,8 @@ static void destroy(gc_graph* g) {
     if (!g) return;
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    for (int i = 0; i < 2; i++)
+        if (g->qexec[i]) cudaGraphExecDestroy(g->qexec[i]);
     if (g->pexec) cudaGraphExecDestroy(g->pexec);
     if (g->lexec) cudaGraphExecDestroy(g->lexec);
     release_local(g);
@@ -1887,6 +1986,11 @@ static int grow_vertices(gc_graph* g, long long k) {
         release(g, g->chunk_table);
         if (!ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     }
+    for (int i = 0; i < 2; i++)
+        if (g->qexec[i]) {
+            cudaGraphExecDestroy(g->qexec[i]);
+            g->qexec[i] = nullptr;
+        }
     if (g->gexec) {
         cudaGraphExecDestroy(g->gexec);
         g->gexec = nullptr;
@@ -2139,6 +2243,7 @@ static void tuning_to_abi(const Tuning& t, long long local_max_pairs, long long 
 int gc_get_tuning(const gc_graph* g, gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
     tuning_to_abi(g->tune, g->opt.local_max_pairs, g->loc_heavy_min, t);
+    t->pair_min_share = g->pair_min_share;
     return GC_OK;
 }
 
@@ -2146,8 +2251,9 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     if (!g || !t) return GC_EINVAL;
     if (t->tri_warp_max < 1 || t->tri_small_max < 1 || t->tri_block_max < 1 || t->c4_reg_max < 1 || t->c4_warp_max < 1 ||
         t->c4_block_max < 1 || t->c4_cta_max < 1 || t->c4_chunk_min < 0 || t->c4_chunk_max < 0 ||
-        t->local_max_pairs < 0 || t->local_c4_heavy_min < 0) {
-        g->err = "tuning: every bound must be positive (c4_chunk_min, local_max_pairs and local_c4_heavy_min may be 0)";
+        t->local_max_pairs < 0 || t->local_c4_heavy_min < 0 || t->pair_min_share < 0) {
+        g->err = "tuning: every bound must be positive (c4_chunk_min, local_max_pairs, local_c4_heavy_min and "
+                 "pair_min_share may be 0)";
         return GC_EINVAL;
     }
     Tuning n;
@@ -2164,6 +2270,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     g->tune = n;
     g->opt.local_max_pairs = (int32_t)std::min<int64_t>(t->local_max_pairs, INT32_MAX);
     g->loc_heavy_min = t->local_c4_heavy_min;
+    g->pair_min_share = t->pair_min_share;
     return GC_OK;
 }
 
@@ -2357,7 +2464,10 @@ int gc_autotune(gc_graph* g, int32_t reps, gc_tuning* best, float* best_ms) {
     g->tune = cur;
     rc = calibrate_local(g, reps);
     if (rc) return rc;
-    if (best) tuning_to_abi(cur, g->opt.local_max_pairs, g->loc_heavy_min, best);
+    if (best) {
+        tuning_to_abi(cur, g->opt.local_max_pairs, g->loc_heavy_min, best);
+        best->pair_min_share = g->pair_min_share;
+    }
     if (best_ms) *best_ms = cur_ms;
     return GC_OK;
 }

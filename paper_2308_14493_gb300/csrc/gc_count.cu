@@ -1507,11 +1507,18 @@ __global__ void k_finalize(Ctl* c, int mode) {
         sm[0] = P; sm[1] = S; sm[2] = TT; sm[3] = D; sm[4] = K; sm[5] = Q;
     }
     // mode 0: committed batch, F += C_a - C_b; mode 2: independent batch,
-    // the result is F + C_a - C_b and F stays; mode 1: static count
+    // the result is F + C_a - C_b and F stays; mode 1: static count; mode 3:
+    // a committed batch whose pass covered every vertex, so C_a and C_b are
+    // the whole graph's counts after and before it: F = C_a, and C_b is the
+    // result of the batch before it (committed without a count of its own)
     const bool ok = c->err == 0 && c->active;
     for (int i = 0; i < 6; i++) {
         unsigned long long d = (unsigned long long)(c->Ca[i] - c->Cb[i]);
         if (mode == 0 && ok) c->F[i] += d;
+        if (mode == 3 && ok) {
+            c->prev_out[i] = (unsigned long long)c->Cb[i];
+            c->F[i] = (unsigned long long)c->Ca[i];
+        }
         c->last_out[i] = mode == 2 ? c->F[i] + d : c->F[i];
     }
     // 3-vertex graphlets from the same sums: triangles = (sum t_e) / 3,
@@ -1525,6 +1532,7 @@ __global__ void k_finalize(Ctl* c, int mode) {
     for (int i = 0; i < 2; i++) {
         unsigned long long d = (unsigned long long)(c->C3a[i] - c->C3b[i]);
         if (mode == 0 && ok) c->F3[i] += d;
+        if (mode == 3 && ok) c->F3[i] = (unsigned long long)c->C3a[i];
         c->last_out3[i] = mode == 2 ? c->F3[i] + d : c->F3[i];
     }
 }

@@ -99,6 +99,8 @@ struct Ctl {
     long long pend_nA2, pend_nD2;    // its kept directed insertion / deletion entries
     long long m_delta;               // net edges committed during a run
     unsigned long long last_out[6];  // counts after the current batch
+    unsigned long long prev_out[6];  // counts before it, when its pass counted both whole graphs
+                                     // (the two-batch form: out of the batch before it)
     // 3-vertex graphlets, [0] induced 2-path (open wedge), [1] triangle
     unsigned long long F3[2];        // maintained
     long long C3a[2], C3b[2];        // of G_a, G_b of the last pass

@@ -43,6 +43,7 @@ __global__ void k_ext_degrees(const int32_t* deg, const int32_t* iperm, int n, i
 // gc_region.cu
 __global__ void k_bfs_sources(Ctl* c, const int32_t* srcA, const int32_t* srcD, uint32_t* visited, int32_t* wlist);
 __global__ void k_level_mark(Ctl* c, int L);
+__global__ void k_region_rest(Ctl* c, int n, uint32_t* visited, int32_t* wlist);
 __global__ void k_bfs_expand(Ctl* c, int L, const long long* row_start, const int32_t* deg, const int32_t* col,
                              uint32_t* visited, int32_t* wlist);
 __global__ void k_region_all(Ctl* c, int n, int32_t* wlist);

@@ -58,6 +58,19 @@ __global__ void k_bfs_sources(Ctl* c, const int32_t* __restrict__ srcA, const in
 
 __global__ void k_level_mark(Ctl* c, int L) { pdl_enter(); c->lvl[L] = c->nW; }
 
+// The two-batch form's whole-graph pass: after the batch endpoints (level
+// 0), every other vertex joins the region, so W = V and the counts of G_a and
+// G_b are those of the whole graph after and before the batch.  An inactive
+// batch (a halted run) keeps its empty region.
+__global__ void k_region_rest(Ctl* c, int n, uint32_t* __restrict__ visited, int32_t* __restrict__ wlist) {
+    pdl_enter();
+    if (c->err || !c->active) return;
+    const long long n_r = ((long long)n + 31) & ~31ll;  // warp-uniform bound for the ballot
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n_r;
+         v += (long long)gridDim.x * blockDim.x)
+        visit_append(v < n, (int32_t)(v < n ? v : 0), visited, wlist, c);
+}
+
 __global__ void k_bfs_expand(Ctl* c, int L, const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
                              const int32_t* __restrict__ col, uint32_t* __restrict__ visited,
                              int32_t* __restrict__ wlist) {

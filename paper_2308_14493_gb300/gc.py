@@ -64,7 +64,7 @@ class gc_tuning(ctypes.Structure):
                 ("c4_reg_max", ctypes.c_int32), ("c4_warp_max", ctypes.c_int32), ("c4_block_max", ctypes.c_int32),
                 ("c4_cta_max", ctypes.c_int64), ("c4_chunk_min", ctypes.c_int64), ("c4_chunk_max", ctypes.c_int64),
                 ("local_max_pairs", ctypes.c_int64), ("local_c4_heavy_min", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 1)]
+                ("pair_min_share", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if not name.startswith("reserved")}

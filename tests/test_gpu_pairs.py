@@ -1,0 +1,160 @@
+"""The two-batch form of sequential batched runs: when batch 0's region holds
+most of the graph, the later batches go in pairs (the first committed without
+a count, the second counted over every vertex, which gives the whole graph's
+counts before and after it).  Every result must equal the oracle's Algorithm
+2 steps and the plain form, through halts for pool space, with odd and even
+run lengths, through the device API, and next to edge-local batches."""
+import numpy as np
+import pytest
+
+import oracle
+from gc_testutil import edges_from_csr
+from synth import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gcb():
+    from paper_2308_14493_gb300 import gc as binding
+
+    binding.load()
+    return binding
+
+
+def _expect(rp, col, batches):
+    og = oracle.OracleGraph(rp, col)
+    return [og.apply(i, d)["F"] for i, d in batches], og
+
+
+@pytest.mark.parametrize("k", [3, 4, 7])
+def test_pairs_equal_the_oracle_and_the_single_pass_form(gcb, k):
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [3000, 10000, 1000, 5000, 8000, 2000, 10000][:k], 0.5, 90 + k)
+    expect, og = _expect(rp, col, batches)
+    with gcb.Graph(n, rp, col) as g:
+        assert g.apply_many(batches) == expect
+        assert g.stats()["path"] == 2
+        assert g.counts() == expect[-1] and g.count_static() == expect[-1]
+        assert g.counts3() == oracle.static_counts3(og.row_ptr, og.col)
+        got = g.export_csr()
+        assert np.array_equal(got[0], og.row_ptr) and np.array_equal(got[1], og.col)
+    with gcb.Graph(n, rp, col) as g:
+        g.set_tuning(pair_min_share=0)
+        assert g.apply_many(batches) == expect
+        assert g.stats()["path"] == 0
+
+
+def test_small_regions_do_not_pair(gcb):
+    """Batches of a few pairs on a sparse graph: batch 0's region is a small
+    part of the graph, so the run stays one pass per batch."""
+    n = 20000
+    keys = gen.er_graph(n, 30000, 5)
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [3, 4, 5, 6], 0.5, 6, ins_weighting="uniform")
+    expect, _ = _expect(rp, col, batches)
+    with gcb.Graph(n, rp, col) as g:
+        assert g.apply_many(batches) == expect
+        assert g.stats()["path"] == 0
+
+
+def test_pairs_through_halts_for_pool_space(gcb):
+    """Insertions into many nearly full hub rows: commits of both kinds of
+    batch in a pair run out of pool space, the run halts, the host grows the
+    pool and finishes the pending commit, and the pairs resume."""
+    n = 3000
+    rng = np.random.default_rng(31)
+    keys = set(int(x) for x in gen.er_graph(n, 3000, 30))
+    hubs = list(range(20))
+    for h in hubs:
+        for v in rng.choice(np.arange(20, n), 500, replace=False):
+            keys.add((h << 32) | int(v))
+    keys = np.array(sorted(keys), dtype=np.uint64)
+    rp, col = gen.csr_from_keys(n, keys)
+    og = oracle.OracleGraph(rp, col)
+    batches, expect = [], []
+    for _ in range(7):
+        cur = set(int(x) for x in gen.keys_from_csr(og.row_ptr, og.col))
+        ins = []
+        for h in hubs:
+            added = 0
+            for v in rng.permutation(np.arange(20, n)):
+                kk = (h << 32) | int(v)
+                if kk not in cur:
+                    cur.add(kk)
+                    ins.append((h, int(v)))
+                    added += 1
+                    if added == 30:
+                        break
+        edges = edges_from_csr(og.row_ptr, og.col)
+        dels = np.array([edges[i] for i in rng.choice(len(edges), 20, replace=False)], np.int32)
+        ins = np.array(ins, np.int32)
+        batches.append((ins, dels))
+        expect.append(og.apply(ins, dels)["F"])
+    with gcb.Graph(n, rp, col, slack=0.05) as g:
+        g.set_tuning(pair_min_share=1)
+        assert g.apply_many(batches) == expect
+        st = g.stats()
+        assert st["path"] == 2 and st["relayouts"] >= 2
+        got = g.export_csr()
+        assert np.array_equal(got[0], og.row_ptr) and np.array_equal(got[1], og.col)
+
+
+def test_device_runs_pair_and_a_bad_pair_turns_pairing_off(gcb):
+    torch = pytest.importorskip("torch")
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    batches = gen.batch_stream(n, keys, [4000, 6000, 2000, 9000, 3000], 0.5, 71)
+    pairs, desc, off = [], [], 0
+    for ins, dels in batches:
+        desc.append((off, len(ins), off + len(ins), len(dels)))
+        pairs += [ins, dels]
+        off += len(ins) + len(dels)
+    flat = np.ascontiguousarray(np.concatenate(pairs).astype(np.int32))
+    d_pairs = torch.from_numpy(flat).cuda()
+    torch.cuda.synchronize()
+    expect, _ = _expect(rp, col, batches)
+    with gcb.Graph(n, rp, col) as g:
+        assert gcb.gc_apply_batches_device(g.h, d_pairs.data_ptr(), desc) == expect
+        assert g.stats()["path"] == 2
+    # a self-loop in batch 3: the run does not pair, and that batch is not applied
+    bad = flat.copy()
+    bad[desc[3][0]] = (bad[desc[3][0]][0], bad[desc[3][0]][0])
+    d_bad = torch.from_numpy(bad).cuda()
+    torch.cuda.synchronize()
+    with gcb.Graph(n, rp, col) as g1, gcb.Graph(n, rp, col) as g2:
+        g2.set_tuning(pair_min_share=0)
+        try:
+            r1 = gcb.gc_apply_batches_device(g1.h, d_bad.data_ptr(), desc)
+        except gcb.GCError as e:
+            r1 = e.code
+        assert g1.stats()["path"] == 0
+        try:
+            r2 = gcb.gc_apply_batches_device(g2.h, d_bad.data_ptr(), desc)
+        except gcb.GCError as e:
+            r2 = e.code
+        assert r1 == r2 and g1.counts() == g2.counts()
+
+
+def test_pairs_next_to_edge_local_batches(gcb):
+    """A run mixing region batches (paired) with small batches that take the
+    edge-local delta: the local form must not use triangle sums the unpaired
+    commits left stale."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    sizes = [5000, 4000, 6000, 20, 30, 5000, 7000, 3000, 40]
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 123)
+    expect, _ = _expect(rp, col, batches)
+    with gcb.Graph(n, rp, col, local_max_pairs=64) as g:
+        assert g.apply_many(batches) == expect
+        assert g.count_static() == expect[-1]
+        # and plain local batches afterwards
+        n2, k2 = n, gen.apply_batch_keys(keys, *batches[0])
+        for ins, dels in batches[1:]:
+            k2 = gen.apply_batch_keys(k2, ins, dels)
+        more = gen.batch_stream(n2, k2, [10, 25, 50], 0.5, 124)
+        og = oracle.OracleGraph(*gen.csr_from_keys(n2, k2))
+        for ins, dels in more:
+            assert g.apply(ins, dels) == og.apply(ins, dels)["F"]
+            assert g.stats()["path"] == 1
