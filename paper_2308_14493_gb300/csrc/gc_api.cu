@@ -121,10 +121,11 @@ struct gc_graph {
     int g_t2 = -1;                       // and for the batched region form
     // the two-batch form of sequential runs: [0] commits a batch without a
     // count, [1] counts the next one over every vertex (enqueue_batch roles)
-    cudaGraphExec_t qexec[2] = {nullptr, nullptr};
-    long long q_nk[2] = {-1, -1};
-    unsigned long long q_gen[2] = {0, 0};
-    int q_launches[2] = {0, 0};
+    // and [2] the twin pass of independent runs
+    cudaGraphExec_t qexec[3] = {nullptr, nullptr, nullptr};
+    long long q_nk[3] = {-1, -1, -1};
+    unsigned long long q_gen[3] = {0, 0, 0};
+    int q_launches[3] = {0, 0, 0};
     long long pair_min_share = 700;      // per mille of 2m (gc_tuning.pair_min_share)
     // maintained triangle sums of the edge-local path: T2[x] = sum of t_e
     // over the edges at x, valid after a static count and kept by local
@@ -270,13 +271,54 @@ __global__ void k_begin_batch(Ctl* c, const long long* desc) {
     for (int k = 0; k < 5; k++) c->l_tot[k] = 0;
 }
 
-// result of the current batch to out[cur], advance the cursor; the second
-// batch of a two-batch pass also writes the first one's result
-__global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit, int pair_second) {
+// The twin pass's batches cur and cur + 1: both pair lists (the keys kernel
+// reads four segments: insertions and deletions of each).
+__global__ void k_begin_twin(Ctl* c, const long long* desc) {
+    pdl_enter();
+    if (threadIdx.x != 0) return;
+    c->active = 1;
+    c->pairs_ins = (const int32_t*)__ldcg(desc);
+    c->pairs_del = (const int32_t*)__ldcg(desc + 1);
+    long long tot = 0;
+    for (int b = 0; b < 2; b++) {
+        const long long* d = desc + 2 + 4 * (long long)(c->cur + b);
+        c->tw_off[2 * b] = __ldcg(d);
+        c->tw_n[2 * b] = __ldcg(d + 1);
+        c->tw_off[2 * b + 1] = __ldcg(d + 2);
+        c->tw_n[2 * b + 1] = __ldcg(d + 3);
+        tot += c->tw_n[2 * b] + c->tw_n[2 * b + 1];
+    }
+    c->n_ins = c->tw_n[0] + c->tw_n[2];
+    c->n_del = c->tw_n[1] + c->tw_n[3];
+    c->ins_off = c->del_off = 0;
+    c->nkeys = 2 * tot;
+    c->nA2 = c->nD2 = 0;
+    for (int k = 0; k < 8; k++) c->st[k] = 0;
+    c->nW = 0;
+    for (int k = 0; k < MAX_HOPS + 2; k++) c->lvl[k] = 0;
+    c->nU = 0;
+    c->scratch_tail = 0;
+    c->overflow = 0;
+    c->err = 0;
+    c->lovf = 0;
+}
+
+// result of the current batch to out[cur], advance the cursor.  form 1:
+// the second batch of a two-batch pass also writes the first one's result;
+// form 2: a twin pass writes the results of batches cur and cur + 1
+__global__ void k_end_batch(Ctl* c, unsigned long long* out, int commit, int form) {
     pdl_enter();
     if (threadIdx.x != 0 || !c->active) return;
-    if (pair_second && c->cur > 0 && !c->err)
+    if (form == 1 && c->cur > 0 && !c->err)
         for (int k = 0; k < 6; k++) out[6 * (long long)(c->cur - 1) + k] = c->prev_out[k];
+    if (form == 2) {
+        for (int k = 0; k < 6; k++) {
+            out[6 * (long long)c->cur + k] = c->last_out[k];
+            out[6 * (long long)(c->cur + 1) + k] = c->prev_out[k];
+        }
+        c->cur += 2;
+        return;
+    }
     for (int k = 0; k < 6; k++) out[6 * (long long)c->cur + k] = c->last_out[k];
     if (commit && !c->err && !c->lovf) c->m_delta += c->nA2 / 2 - c->nD2 / 2;
     c->cur++;
@@ -484,7 +526,7 @@ static int ensure_local(gc_graph* g, long long cap) {
 // Free the scratch that the next batch re-creates on demand.
 static void trim_scratch(gc_graph* g) {
     if (g->s) cudaStreamSynchronize(g->s);
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 3; i++)
         if (g->qexec[i]) {
             cudaGraphExecDestroy(g->qexec[i]);
             g->qexec[i] = nullptr;
@@ -553,19 +595,26 @@ static int ensure_desc(gc_graph* g, long long words) {
 // U build + counting + closed forms.
 //   fin: k_finalize mode (0 committed batch, 1 static, 2 independent batch)
 //   set_F: a static count that initialises F; timed: record stage events
-static int count_region(gc_graph* g, int fin, bool set_F, bool timed) {
+static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin = false) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
     pdl_launch(k_reset_count, dim3(1), dim3(32), 0, s, g->ctl);
     CK(cudaMemsetAsync(g->U_deg, 0, sizeof(int32_t) * (size_t)std::max(g->n, 1), s));
-    pdl_launch(k_u_count, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
-               g->segA, g->U_deg, 0);
+    if (twin)
+        pdl_launch(k_u_count_twin, dim3(grid_elems(g, g->n)), dim3(TPB), 0, s, g->ctl, g->wlist, g->deg, g->segA,
+                   g->U_deg);
+    else
+        pdl_launch(k_u_count, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
+                   g->segA, g->U_deg, 0);
     g->launches += 2;
     g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU,
                                    s);
-    pdl_launch(k_u_fill, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col, g->segA,
-               g->segD,
-                                g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 0);
+    if (twin)
+        pdl_launch(k_u_fill_twin, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->row_start, g->deg, g->col, g->segA,
+                   g->segD, g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
+    else
+        pdl_launch(k_u_fill, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
+                   g->segA, g->segD, g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 0);
     pdl_launch(k_zero_u64, dim3(grid_elems(g, (long long)g->U_col.cap)), dim3(TPB), 0, s, g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     CountArgs ca;
@@ -713,30 +762,46 @@ static int enqueue_segments(gc_graph* g, bool clear) {
 // the two-batch form (sequential runs whose regions cover the graph): role 1
 // normalises and commits the first batch of a pair without counting, role 2
 // counts the second over every vertex (C_b = the whole graph after the first
-// batch, C_a = after the second) and commits it.
+// batch, C_a = after the second) and commits it; role 3 (independent runs):
+// the twin pass, batches cur and cur + 1 keyed together with a batch tag and
+// counted over every vertex, G_a = G with the first, G_b = G with the second
+// (no commit).
 static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed, bool local = false,
                          bool t2 = false, int role = 0) {
     cudaStream_t s = g->s;
     if (timed) CK(record_stage(g->ev[0], s));
-    pdl_launch(k_begin_batch, dim3(1), dim3(32), 0, s, g->ctl, g->desc);
+    const bool twin = role == 3;
+    if (twin) pdl_launch(k_begin_twin, dim3(1), dim3(32), 0, s, g->ctl, g->desc);
+    else pdl_launch(k_begin_batch, dim3(1), dim3(32), 0, s, g->ctl, g->desc);
     g->launches++;
     const long long nkb = std::max<long long>(max_nk, 1);
     const int ge = grid_elems(g, nkb);
     if (max_nk > 0) {
-        pdl_launch(k_batch_keys, dim3(grid_elems(g, nkb / 2)), dim3(TPB), 0, s, g->ctl, g->perm, g->n, g->S, g->keys.p);
+        if (twin)
+            pdl_launch(k_batch_keys_twin, dim3(grid_elems(g, nkb / 2)), dim3(TPB), 0, s, g->ctl, g->perm, g->n, g->S,
+                       g->keys.p);
+        else
+            pdl_launch(k_batch_keys, dim3(grid_elems(g, nkb / 2)), dim3(TPB), 0, s, g->ctl, g->perm, g->n, g->S,
+                       g->keys.p);
         g->launches++;
-        g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nkb, 2 * g->S + 1, g->hist.p,
-                                      radix_grid(nkb, g->sms), s);
-        pdl_launch(k_batch_decide, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->row_start, g->deg, g->col,
-                   g->keepA.p,
-                                          g->keepD.p);
+        g->launches += radix_sort_u64(g->keys.p, g->keys_tmp.p, &g->ctl->nkeys, nkb, 2 * g->S + (twin ? 2 : 1),
+                                      g->hist.p, radix_grid(nkb, g->sms), s);
+        if (twin)
+            pdl_launch(k_batch_decide_twin, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->row_start, g->deg,
+                       g->col, g->keepA.p, g->keepD.p);
+        else
+            pdl_launch(k_batch_decide, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->row_start, g->deg,
+                       g->col, g->keepA.p, g->keepD.p);
         g->launches++;
         int sg = scan_grid(nkb, g->sms);
         g->launches += scan_i32_to_i64(g->keepA.p, g->posA.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nA2, s);
         g->launches += scan_i32_to_i64(g->keepD.p, g->posD.p, &g->ctl->nkeys, 0, g->bsum.p, sg, &g->ctl->nD2, s);
-        pdl_launch(k_batch_compact, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p,
-                   g->posA.p, g->posD.p,
-                                           g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
+        if (twin)
+            pdl_launch(k_batch_compact_twin, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->keepA.p,
+                       g->keepD.p, g->posA.p, g->posD.p, g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
+        else
+            pdl_launch(k_batch_compact, dim3(ge), dim3(TPB), 0, s, g->keys.p, g->ctl, g->S, g->keepA.p, g->keepD.p,
+                       g->posA.p, g->posD.p, g->srcA.p, g->dstA.p, g->srcD.p, g->dstD.p);
         g->launches++;
         int rc = enqueue_segments(g, false);
         if (rc) return rc;
@@ -746,7 +811,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     pdl_launch(k_bfs_sources, dim3(ge), dim3(TPB), 0, s, g->ctl, g->srcA.p, g->srcD.p, g->visited, g->wlist);
     pdl_launch(k_level_mark, dim3(1), dim3(1), 0, s, g->ctl, 0);
     g->launches += 2;
-    if (role == 2) {
+    if (role == 2 || role == 3) {
         pdl_launch(k_region_rest, dim3(grid_elems(g, g->n)), dim3(TPB), 0, s, g->ctl, g->n, g->visited, g->wlist);
         g->launches++;
     }
@@ -764,7 +829,7 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     int rc = GC_OK;
     if (role != 1) {
         rc = local ? count_local(g, commit ? 1 : 0, timed, t2)
-                   : count_region(g, role == 2 ? 3 : (commit ? 0 : 2), false, timed);
+                   : count_region(g, role == 2 ? 3 : role == 3 ? 4 : (commit ? 0 : 2), false, timed, twin);
         if (rc) return rc;
     }
     if (!local && commit && t2 && role == 0) {
@@ -786,7 +851,8 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
         rc = enqueue_segments(g, true);
         if (rc) return rc;
     }
-    pdl_launch(k_end_batch, dim3(1), dim3(32), 0, s, g->ctl, g->out_dev.p, commit ? 1 : 0, role == 2 ? 1 : 0);
+    pdl_launch(k_end_batch, dim3(1), dim3(32), 0, s, g->ctl, g->out_dev.p, commit ? 1 : 0,
+               role == 2 ? 1 : role == 3 ? 2 : 0);
     g->launches++;
     CKL();
     return GC_OK;
@@ -1093,9 +1159,14 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
             relayouts++;
         }
     }
-    rc = plan_batch_buffers(g, shape_nk);
+    // the twin pass of independent runs keys two batches at once
+    const bool twin_ok = !commit && k >= 3 && g->pair_min_share > 0 && g->n < (1 << 29);
+    long long twin_nk = 1;
+    if (twin_ok)
+        while (twin_nk < 2 * max_nk) twin_nk <<= 1;
+    rc = plan_batch_buffers(g, twin_ok ? twin_nk : shape_nk);
     if (rc) return rc;
-    rc = plan_region_buffers(g, g->m + (commit ? sum_ins : max_ins), max_ins);
+    rc = plan_region_buffers(g, g->m + (commit ? sum_ins : (twin_ok ? 2 : 1) * max_ins), (twin_ok ? 2 : 1) * max_ins);
     if (rc) return rc;
     rc = ensure_desc(g, 2 + 4LL * k);
     if (rc) return rc;
@@ -1120,7 +1191,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     // pairs pass the device check (a bad pair makes its batch a no-op, which
     // the pairing does not model); batch 0 runs as Algorithm 2 and its region
     // decides whether the rest go in pairs
-    bool pair_ok = commit && k >= 3 && g->pair_min_share > 0;
+    bool pair_ok = (commit || twin_ok) && k >= 3 && g->pair_min_share > 0;
     if (pair_ok) {
         CK(cudaMemsetAsync(g->hist.p, 0, sizeof(int), s));
         k_run_pairs_check<<<dim3(64, (unsigned)std::min(k, 64)), TPB, 0, s>>>(g->desc, k, g->n, (int*)g->hist.p);
@@ -1134,16 +1205,17 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     int pairs_used = 0;
     auto role_of = [&](int i) {
         if (!pairs || i == 0) return 0;
-        if ((i - 1) % 2 == 0) return i + 1 < k ? 1 : 0;
-        return 2;
+        if ((i - 1) % 2 == 0) return i + 1 < k ? (commit ? 1 : 3) : 0;
+        return 2;  // (independent runs never reach this: a twin pass takes two batches)
     };
     auto ensure_exec = [&](int role) -> int {
         if (role == 0) return GC_OK;
         const int q = role - 1;
-        if (!g->qexec[q] || g->q_nk[q] != shape_nk || g->q_gen[q] != g->buf_gen) {
-            int r = capture_batch(g, shape_nk, true, false, &g->qexec[q], &g->q_launches[q], false, false, role);
+        const long long nk = role == 3 ? twin_nk : shape_nk;
+        if (!g->qexec[q] || g->q_nk[q] != nk || g->q_gen[q] != g->buf_gen) {
+            int r = capture_batch(g, nk, role != 3, false, &g->qexec[q], &g->q_launches[q], false, false, role);
             if (r) return r;
-            g->q_nk[q] = shape_nk;
+            g->q_nk[q] = nk;
             g->q_gen[q] = g->buf_gen;
         }
         return GC_OK;
@@ -1153,13 +1225,14 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     long long launches = 0;
     while (done < k) {
         const int upto = (pair_ok && !pairs && done == 0) ? 1 : k;
-        for (int i = done; i < upto; i++) {
+        for (int i = done; i < upto;) {
             const int role = role_of(i);
             rc = ensure_exec(role);
             if (rc) return rc;
             CK(cudaGraphLaunch(role == 0 ? g->gexec : g->qexec[role - 1], s));
             launches += role == 0 ? g->g_launches : g->q_launches[role - 1];
-            pairs_used += role == 2 ? 1 : 0;
+            pairs_used += (role == 2 || role == 3) ? 1 : 0;
+            i += role == 3 ? 2 : 1;
         }
         rc = read_ctl(g);
         if (rc) return rc;
@@ -1182,7 +1255,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
             }
         }
     }
-    if (pairs_used) g->t2_valid = false;  // first batches of pairs did not keep the triangle sums
+    if (pairs_used && commit) g->t2_valid = false;  // first batches of pairs did not keep the triangle sums
     CK(cudaEventRecord(g->e1, s));
     std::vector<unsigned long long> res((size_t)6 * std::max(k, 1));
     CK(cudaMemcpyAsync(res.data(), g->out_dev.p, sizeof(unsigned long long) * 6 * (size_t)k, cudaMemcpyDeviceToHost,
@@ -1256,7 +1329,7 @@ static void destroy(gc_graph* g) {
     if (!g) return;
     if (g->s) cudaStreamSynchronize(g->s);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 3; i++)
         if (g->qexec[i]) cudaGraphExecDestroy(g->qexec[i]);
     if (g->pexec) cudaGraphExecDestroy(g->pexec);
     if (g->lexec) cudaGraphExecDestroy(g->lexec);
@@ -1986,7 +2059,7 @@ static int grow_vertices(gc_graph* g, long long k) {
         release(g, g->chunk_table);
         if (!ensure_chunk_table(g)) return nomem(g, "4-cycle chunk table");
     }
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 3; i++)
         if (g->qexec[i]) {
             cudaGraphExecDestroy(g->qexec[i]);
             g->qexec[i] = nullptr;

@@ -36,6 +36,107 @@ __global__ void k_batch_keys(Ctl* c, const int32_t* __restrict__ perm, int n, in
     }
 }
 
+// ---- twin pass: two independent batches counted in one pass ---------------
+// Both batches' pairs are keyed together, each key carrying its batch's tag:
+// key = (a << (S + 2)) | (b << 2) | (tag << 1) | op.  Per vertex pair the
+// group of keys decides, for each batch alone, what Algorithm 2's
+// normalisation decides (repeats collapse, a pair in both A and D of one
+// batch drops, no-ops drop); the kept entry of the pair carries the mask of
+// the batches that insert (or delete) it, in its two low bits:
+// dst = (b << 2) | mask.  A pair cannot be kept as an insertion by one batch
+// and as a deletion by the other (one needs it absent, the other present).
+__global__ void k_batch_keys_twin(Ctl* c, const int32_t* __restrict__ perm, int n, int S,
+                                  uint64_t* __restrict__ keys) {
+    pdl_enter();
+    const long long n0 = c->tw_n[0], n1 = c->tw_n[1], n2 = c->tw_n[2], n3 = c->tw_n[3];
+    const long long tot = n0 + n1 + n2 + n3;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int seg = 0;
+        long long j = i;
+        if (j >= n0) { j -= n0; seg = 1;
+            if (j >= n1) { j -= n1; seg = 2;
+                if (j >= n2) { j -= n2; seg = 3; } } }
+        const int32_t* base = (seg & 1) ? c->pairs_del : c->pairs_ins;
+        const int32_t* p = base + 2 * (c->tw_off[seg] + j);
+        const uint64_t op = seg & 1, tag = seg >> 1;
+        const int32_t x = p[0], y = p[1];
+        if (x < 0 || y < 0 || x >= n || y >= n || x == y) {
+            atomicExch(&c->err, -1);  // checked on the host before a twin pass; never applied
+            keys[2 * i] = keys[2 * i + 1] = ~0ull;
+            continue;
+        }
+        const uint64_t a = (uint64_t)perm[x], b = (uint64_t)perm[y];
+        keys[2 * i] = (a << (S + 2)) | (b << 2) | (tag << 1) | op;
+        keys[2 * i + 1] = (b << (S + 2)) | (a << 2) | (tag << 1) | op;
+    }
+}
+
+// what the group of keys of one vertex pair starting at i keeps, per batch:
+// bit t of *ins / *del: batch t inserts / deletes it (before the existence
+// test)
+__device__ __forceinline__ void twin_group(const uint64_t* keys, long long i, long long nk, uint64_t pair, int* ins,
+                                           int* del) {
+    int hi[2] = {0, 0}, hd[2] = {0, 0};
+    for (long long j = i; j < nk && (keys[j] >> 2) == pair; j++) {
+        const int t = (int)((keys[j] >> 1) & 1);
+        if (keys[j] & 1) hd[t] = 1;
+        else hi[t] = 1;
+    }
+    *ins = (hi[0] && !hd[0] ? 1 : 0) | (hi[1] && !hd[1] ? 2 : 0);
+    *del = (hd[0] && !hi[0] ? 1 : 0) | (hd[1] && !hi[1] ? 2 : 0);
+}
+
+__global__ void k_batch_decide_twin(const uint64_t* __restrict__ keys, Ctl* c, int S,
+                                    const long long* __restrict__ row_start, const int32_t* __restrict__ deg,
+                                    const int32_t* __restrict__ col, int32_t* __restrict__ keepA,
+                                    int32_t* __restrict__ keepD) {
+    pdl_enter();
+    const long long nk = c->nkeys;
+    const uint64_t idmask = (1ull << S) - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nk;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint64_t pair = keys[i] >> 2;
+        int ka = 0, kd = 0;
+        if (keys[i] != ~0ull && (i == 0 || (keys[i - 1] >> 2) != pair)) {
+            int ins, del;
+            twin_group(keys, i, nk, pair, &ins, &del);
+            const int32_t src = (int32_t)(pair >> S), dst = (int32_t)(pair & idmask);
+            const bool exists = sorted_contains(col + row_start[src], deg[src], dst);
+            ka = (!exists && ins) ? 1 : 0;
+            kd = (exists && del) ? 1 : 0;
+        }
+        keepA[i] = ka;
+        keepD[i] = kd;
+    }
+}
+
+__global__ void k_batch_compact_twin(const uint64_t* __restrict__ keys, const Ctl* c, int S,
+                                     const int32_t* __restrict__ keepA, const int32_t* __restrict__ keepD,
+                                     const long long* __restrict__ posA, const long long* __restrict__ posD,
+                                     int32_t* __restrict__ srcA, int32_t* __restrict__ dstA,
+                                     int32_t* __restrict__ srcD, int32_t* __restrict__ dstD) {
+    pdl_enter();
+    const long long nk = c->nkeys;
+    const uint64_t idmask = (1ull << S) - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nk;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!keepA[i] && !keepD[i]) continue;
+        const uint64_t pair = keys[i] >> 2;
+        const int32_t src = (int32_t)(pair >> S), dst = (int32_t)(pair & idmask);
+        int ins, del;
+        twin_group(keys, i, nk, pair, &ins, &del);
+        if (keepA[i]) {
+            srcA[posA[i]] = src;
+            dstA[posA[i]] = (dst << 2) | ins;
+        }
+        if (keepD[i]) {
+            srcD[posD[i]] = src;
+            dstD[posD[i]] = (dst << 2) | del;
+        }
+    }
+}
+
 // keep[i]: 1 = insert entry, 2 = delete entry, 0 = dropped / not a run head
 __global__ void k_batch_decide(const uint64_t* __restrict__ keys, Ctl* c, int S,
                                const long long* __restrict__ row_start, const int32_t* __restrict__ deg,

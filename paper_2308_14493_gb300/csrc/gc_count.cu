@@ -1510,7 +1510,8 @@ __global__ void k_finalize(Ctl* c, int mode) {
     // the result is F + C_a - C_b and F stays; mode 1: static count; mode 3:
     // a committed batch whose pass covered every vertex, so C_a and C_b are
     // the whole graph's counts after and before it: F = C_a, and C_b is the
-    // result of the batch before it (committed without a count of its own)
+    // result of the batch before it (committed without a count of its own);
+    // mode 4: see below
     const bool ok = c->err == 0 && c->active;
     for (int i = 0; i < 6; i++) {
         unsigned long long d = (unsigned long long)(c->Ca[i] - c->Cb[i]);
@@ -1520,6 +1521,13 @@ __global__ void k_finalize(Ctl* c, int mode) {
             c->F[i] = (unsigned long long)c->Ca[i];
         }
         c->last_out[i] = mode == 2 ? c->F[i] + d : c->F[i];
+        // mode 4: two independent batches counted over every vertex (the
+        // twin pass): C_a and C_b are the whole graph's counts with the
+        // first and with the second batch applied; F stays
+        if (mode == 4) {
+            c->last_out[i] = (unsigned long long)c->Ca[i];
+            c->prev_out[i] = (unsigned long long)c->Cb[i];
+        }
     }
     // 3-vertex graphlets from the same sums: triangles = (sum t_e) / 3,
     // induced 2-paths = sum C(d, 2) - 3 triangles

@@ -92,6 +92,8 @@ struct Ctl {
     const int32_t* pairs_ins;        // base of the insertion pairs
     const int32_t* pairs_del;        // base of the deletion pairs
     long long ins_off, del_off;      // offsets (in pairs) of the current batch
+    long long tw_off[4], tw_n[4];    // a twin pass (two independent batches): ins / del of the
+                                     // first, ins / del of the second, offsets and sizes
     int cur;                         // index of the current batch in a run
     int active;                      // the current batch runs (no commit is pending)
     int halt;                        // a commit ran out of pool space; later batches wait

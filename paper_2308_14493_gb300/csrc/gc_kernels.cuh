@@ -44,6 +44,18 @@ __global__ void k_ext_degrees(const int32_t* deg, const int32_t* iperm, int n, i
 __global__ void k_bfs_sources(Ctl* c, const int32_t* srcA, const int32_t* srcD, uint32_t* visited, int32_t* wlist);
 __global__ void k_level_mark(Ctl* c, int L);
 __global__ void k_region_rest(Ctl* c, int n, uint32_t* visited, int32_t* wlist);
+__global__ void k_u_count_twin(const Ctl* c, const int32_t* wlist, const int32_t* deg, const int2* segA,
+                               int32_t* U_deg);
+__global__ void k_u_fill_twin(const Ctl* c, const int32_t* wlist, const long long* row_start, const int32_t* deg,
+                              const int32_t* col, const int2* segA, const int2* segD, const int32_t* dstA,
+                              const int32_t* dstD, const long long* U_off, uint32_t* U_col, int32_t* U_split,
+                              int32_t* da, int32_t* db);
+__global__ void k_batch_keys_twin(Ctl* c, const int32_t* perm, int n, int S, uint64_t* keys);
+__global__ void k_batch_decide_twin(const uint64_t* keys, Ctl* c, int S, const long long* row_start,
+                                    const int32_t* deg, const int32_t* col, int32_t* keepA, int32_t* keepD);
+__global__ void k_batch_compact_twin(const uint64_t* keys, const Ctl* c, int S, const int32_t* keepA,
+                                     const int32_t* keepD, const long long* posA, const long long* posD,
+                                     int32_t* srcA, int32_t* dstA, int32_t* srcD, int32_t* dstD);
 __global__ void k_bfs_expand(Ctl* c, int L, const long long* row_start, const int32_t* deg, const int32_t* col,
                              uint32_t* visited, int32_t* wlist);
 __global__ void k_region_all(Ctl* c, int n, int32_t* wlist);

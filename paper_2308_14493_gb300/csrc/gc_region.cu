@@ -162,6 +162,80 @@ __global__ void k_u_fill(const Ctl* c, const int32_t* __restrict__ wlist, const 
     }
 }
 
+// Twin pass (two independent batches, W = V): row u of U is N(u) plus the
+// insertions of either batch; the kept entries carry the batches' mask in
+// their two low bits (dst << 2 | mask, one entry per vertex pair, sorted).
+// A G entry loses FLAG_A (FLAG_B) if the first (second) batch deletes it; an
+// insertion has FLAG_A (FLAG_B) if the first (second) batch makes it.  Every
+// entry is placed by binary searches: a row element after the insertions
+// below it, an insertion after the row elements below it.
+__global__ void k_u_count_twin(const Ctl* c, const int32_t* __restrict__ wlist, const int32_t* __restrict__ deg,
+                               const int2* __restrict__ segA, int32_t* __restrict__ U_deg) {
+    pdl_enter();
+    const int nW = c->nW;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x) {
+        const int32_t u = wlist[i];
+        U_deg[u] = deg[u] + (segA[u].y - segA[u].x);
+    }
+}
+
+__global__ void k_u_fill_twin(const Ctl* c, const int32_t* __restrict__ wlist, const long long* __restrict__ row_start,
+                              const int32_t* __restrict__ deg, const int32_t* __restrict__ col,
+                              const int2* __restrict__ segA, const int2* __restrict__ segD,
+                              const int32_t* __restrict__ dstA, const int32_t* __restrict__ dstD,
+                              const long long* __restrict__ U_off, uint32_t* __restrict__ U_col,
+                              int32_t* __restrict__ U_split, int32_t* __restrict__ da, int32_t* __restrict__ db) {
+    pdl_enter();
+    const int nW = c->nW;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nW; i += nwarps) {
+        const int32_t u = wlist[i];
+        const int2 a = segA[u], d = segD[u];
+        const int32_t* A = dstA + a.x;
+        const int32_t* D = dstD + d.x;
+        const long long na = a.y - a.x, nd = d.y - d.x;
+        const int32_t* row = col + row_start[u];
+        const int du = deg[u];
+        uint32_t* out = U_col + U_off[u];
+        for (int p = lane; p < du; p += 32) {
+            const int32_t v = row[p];
+            uint32_t fl = FLAG_A | FLAG_B;
+            if (nd) {
+                const long long q = lower_bound_i32(D, nd, v << 2);
+                if (q < nd && (D[q] >> 2) == v) {
+                    if (D[q] & 1) fl &= ~FLAG_A;
+                    if (D[q] & 2) fl &= ~FLAG_B;
+                }
+            }
+            out[p + (na ? lower_bound_i32(A, na, v << 2) : 0)] = (uint32_t)v | fl;
+        }
+        int cA = 0, cB = 0;  // insertions into G_a / G_b minus deletions from them
+        for (long long q = lane; q < na; q += 32) {
+            const int32_t x = A[q] >> 2, m = A[q] & 3;
+            out[q + lower_bound_i32(row, du, x)] = (uint32_t)x | ((m & 1) ? FLAG_A : 0u) | ((m & 2) ? FLAG_B : 0u);
+            cA += (m & 1) ? 1 : 0;
+            cB += (m & 2) ? 1 : 0;
+        }
+        for (long long q = lane; q < nd; q += 32) {
+            cA -= (D[q] & 1) ? 1 : 0;
+            cB -= (D[q] & 2) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cA += __shfl_xor_sync(FULL, cA, o);
+            cB += __shfl_xor_sync(FULL, cB, o);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            U_split[u] = (int32_t)(lower_bound_i32(row, du, u + 1) + (na ? lower_bound_i32(A, na, (u + 1) << 2) : 0));
+            da[u] = du + cA;
+            db[u] = du + cB;
+        }
+    }
+}
+
 // Union rows over the full adjacency (the edge-local path): a block per
 // vertex, every entry placed by binary searches (hub rows spread over the
 // block).  D entries stay with FLAG_B only, A entries get FLAG_A only.

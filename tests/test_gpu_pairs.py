@@ -158,3 +158,69 @@ def test_pairs_next_to_edge_local_batches(gcb):
         for ins, dels in more:
             assert g.apply(ins, dels) == og.apply(ins, dels)["F"]
             assert g.stats()["path"] == 1
+
+
+def _dirty(rng, n, keys, base_ins, base_dels, shared):
+    """A raw batch with repeats, a pair in both A and D, a no-op insertion
+    (an existing edge) and a no-op deletion (an absent pair), plus `shared`
+    pairs that another batch of the run also carries."""
+    ins = [tuple(x) for x in base_ins] + [tuple(base_ins[0][::-1])] + [tuple(x) for x in shared]
+    dels = [tuple(x) for x in base_dels] + [tuple(base_dels[0])]
+    both = base_ins[1]
+    dels.append(tuple(both))
+    e = int(keys[rng.integers(len(keys))])
+    ins.append((e >> 32, e & 0xFFFFFFFF))
+    while True:
+        a, b = (int(x) for x in rng.integers(0, n, 2))
+        kk = (min(a, b) << 32) | max(a, b)
+        if a != b and not np.any(keys == kk):
+            dels.append((a, b))
+            break
+    return np.array(ins, np.int32), np.array(dels, np.int32)
+
+
+@pytest.mark.parametrize("k", [3, 4, 7])
+def test_twin_passes_of_independent_batches(gcb, k):
+    """Independent batches on one snapshot: batch 0 alone, then two batches
+    per pass (each with its own batch tag in the normalisation keys).  Every
+    result is the oracle's Algorithm 2 step on the snapshot, and the graph
+    and its counts stay as they were."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    rng = np.random.default_rng(200 + k)
+    base = gen.batch_stream(n, keys, [2000, 5000, 800, 9000, 3000, 1500, 6000][:k], 0.5, 210 + k,
+                            sequential=False)
+    shared = [tuple(base[0][0][j]) for j in range(5)] + [tuple(base[0][1][0])]
+    batches = [_dirty(rng, n, keys, i, d, shared if b % 2 else shared[:2]) for b, (i, d) in enumerate(base)]
+    F0 = oracle.static_counts(rp, col)
+    expect = [oracle.fdgc_step(rp, col, i, d, F0)["F"] for i, d in batches]
+    with gcb.Graph(n, rp, col) as g:
+        assert g.apply_many(batches, independent=True) == expect
+        assert g.stats()["path"] == 2
+        assert g.counts() == F0 and g.num_edges() == len(keys)
+        assert g.count_static() == F0
+    with gcb.Graph(n, rp, col) as g:
+        g.set_tuning(pair_min_share=0)
+        assert g.apply_many(batches, independent=True) == expect
+        assert g.stats()["path"] == 0
+
+
+def test_twin_passes_through_the_device_api_and_local_batches(gcb):
+    torch = pytest.importorskip("torch")
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    sizes = [3000, 12, 7000, 40, 5000, 4000, 9, 6000]
+    batches = gen.batch_stream(n, keys, sizes, 0.5, 77, sequential=False)
+    F0 = oracle.static_counts(rp, col)
+    expect = [oracle.fdgc_step(rp, col, i, d, F0)["F"] for i, d in batches]
+    pairs, desc, off = [], [], 0
+    for ins, dels in batches:
+        desc.append((off, len(ins), off + len(ins), len(dels)))
+        pairs += [ins, dels]
+        off += len(ins) + len(dels)
+    d_pairs = torch.from_numpy(np.ascontiguousarray(np.concatenate(pairs).astype(np.int32))).cuda()
+    torch.cuda.synchronize()
+    for local in (0, 64):
+        with gcb.Graph(n, rp, col, local_max_pairs=local) as g:
+            assert gcb.gc_apply_batches_device(g.h, d_pairs.data_ptr(), desc, independent=True) == expect
+            assert g.counts() == F0
