@@ -359,6 +359,34 @@ def run_batched(gcb, torch, n, rp, col, batches, warmup, stream, flush, independ
     return e0.elapsed_time(e1) / 1e3, raw, outs, st["launches"]
 
 
+def run_batched_host(gcb, torch, n, rp, col, batches, warmup, stream, flush, tuning=None):
+    """Batched form end to end through gc_apply_batches: the timed batches'
+    pairs sit in pinned host memory and are copied to the device inside the
+    call; the call returns the k x 6 counts to the host.  Device time = CUDA
+    events on the library's stream around the call.  Returns (seconds,
+    outputs, host-to-device bytes)."""
+    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
+    if tuning:
+        gcb.gc_set_tuning(h, **tuning)
+    pinned = [(torch.from_numpy(np.ascontiguousarray(i, dtype=np.int32)).pin_memory(),
+               torch.from_numpy(np.ascontiguousarray(d, dtype=np.int32)).pin_memory()) for i, d in batches]
+    host = [(a.numpy(), b.numpy()) for a, b in pinned]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        if warmup:
+            gcb.gc_apply_batches(h, host[:warmup])
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = gcb.gc_apply_batches(h, host[warmup:])
+        e1.record(stream)
+    torch.cuda.synchronize()
+    gcb.gc_close(h)
+    h2d = sum(8 * (len(i) + len(d)) for i, d in batches[warmup:])
+    return e0.elapsed_time(e1) / 1e3, outs, h2d
+
+
 def run_what_if(gcb, torch, n, rp, col, batches, stream, flush, tuning=None):
     """Plain form of independent batches: one gc_count_batch_device call per
     batch against the same snapshot, L2 flushed between calls."""
@@ -632,14 +660,25 @@ def gpu_arm(args):
                            "work_wedges": static_stats["work_wedges"],
                            "work_wedges_heavy": static_stats["work_wedges_heavy"]},
     }
-    # end to end through the public API with host (pinned) buffers
+    # end to end through the public API with host (pinned) buffers: both
+    # forms; the headline's e2e is the form the headline value is
     recs_e, _, _ = run_plain(gcb, torch, n, rp, col, batches, W, K, stream, flush, device_inputs=False)
     se = summarize(recs_e)
-    line["e2e"] = {"value": allreduce(world, float(se["edges"]), "sum") / allreduce(world, se["seconds"], "max"),
-                   "unit": UNIT, "h2d_bytes_per_step": int(statistics.mean(8 * r["n_raw"] for r in recs_e)),
-                   "d2h_bytes_per_step": 48, "p50_ms": se["p50_ms"], "p99_ms": se["p99_ms"],
-                   "api": "gc_apply_batch (host pinned pairs in, 6 uint64 counts out)",
-                   "counts_equal_device_inputs": [r["out"] for r in recs_e] == [r["out"] for r in recs]}
+    e2e_plain = {"value": allreduce(world, float(se["edges"]), "sum") / allreduce(world, se["seconds"], "max"),
+                 "unit": UNIT, "h2d_bytes_per_step": int(statistics.mean(8 * r["n_raw"] for r in recs_e)),
+                 "d2h_bytes_per_step": 48, "p50_ms": se["p50_ms"], "p99_ms": se["p99_ms"],
+                 "api": "gc_apply_batch (host pinned pairs in, 6 uint64 counts out), one call per batch",
+                 "counts_equal_device_inputs": [r["out"] for r in recs_e] == [r["out"] for r in recs]}
+    secs_e, outs_e, h2d_e = run_batched_host(gcb, torch, n, rp, col, batches, W, stream, flush,
+                                             tuning=static_stats["tuning"])
+    e2e_batched = {"value": edges_all / allreduce(world, secs_e, "max"), "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d_e / max(K, 1)), "d2h_bytes_per_step": 48,
+                   "ms_per_batch": 1e3 * secs_e / max(K, 1),
+                   "api": "gc_apply_batches (the K batches' pinned host pairs in, K x 6 uint64 counts out), one call",
+                   "counts_equal_device_inputs": outs_e == [r["out"] for r in recs]}
+    line["e2e"] = dict(e2e_batched if best == "batched" else e2e_plain)
+    line["e2e"]["plain"] = e2e_plain
+    line["e2e"]["batched"] = e2e_batched
     if not args.no_secondary and rank == 0:
         sec = {}
         # the 7,000-vertex graph: plain vs batched at both batch sizes, IGC
