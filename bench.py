@@ -480,7 +480,8 @@ def cpu_sample_worker(workload, count, budget_s):
 
 def paper_regime(gcb, torch, n, keys, rp, col, stream, flush, static_ms):
     """The paper's batch sizes (10 and 100 updates, Figs. 2-4; insert-only IGC
-    and fully dynamic FDGC with p = 0.7) and 1,000, on the n=1.6M m=30M graph:
+    and fully dynamic FDGC with p = 0.7), 1,000 and 10,000, on the n=1.6M
+    m=30M graph:
     the edge-local delta against the region recount of Algorithm 2, both
     through gc_apply_batch_device on their own handle (the two graphs take
     the same batches and stay equal), and against one full static recount."""
@@ -491,7 +492,7 @@ def paper_regime(gcb, torch, n, keys, rp, col, stream, flush, static_ms):
     cur = keys
     out = {}
     for tag, frac, size in (("igc_10", 1.0, 10), ("igc_100", 1.0, 100), ("fdgc_10", 0.7, 10),
-                            ("fdgc_100", 0.7, 100), ("fdgc_1000", 0.7, 1000)):
+                            ("fdgc_100", 0.7, 100), ("fdgc_1000", 0.7, 1000), ("fdgc_10000", 0.7, 10000)):
         batches = gen.batch_stream(n, cur, [size] * 6, frac, 700 + size + int(10 * frac))
         for ins, dels in batches:
             cur = gen.apply_batch_keys(cur, ins, dels)

@@ -5,7 +5,7 @@ Run from the repository root:
 
     python tests/golden/make_golden.py           # workloads.json (seconds)
     python tests/golden/make_golden.py --large   # workloads_large.json (tens of minutes)
-    python tests/golden/make_golden.py --large c3_local   # one part of it, merged in
+    python tests/golden/make_golden.py --large c3_local   # one part of it, merged in (also c3_local_10k)
     python tests/golden/make_golden.py --c5 g0   # workloads_c5.json, one part (g0, g7, g0_stream)
 
 Each part runs alone and is merged into its file, so parts can run as
@@ -82,6 +82,17 @@ def large_c3_local():
     return {"c3_local_stream": dict(sizes=sizes, seed=77, edges=int(cur.size), final=oracle.static_counts(rp, col))}
 
 
+def large_c3_local_10k():
+    """The c3 graph after one 10,000-update batch (70% insertions, batch seed
+    78), the size at which the edge-local delta still beats the region
+    recount there: the oracle's static count of the final edge set."""
+    n, keys = gen.workload_graph("c3")
+    ins, dels = gen.batch_stream(n, keys, [10000], 0.7, 78)[0]
+    cur = gen.apply_batch_keys(keys, ins, dels)
+    rp, col = gen.csr_from_keys(n, cur)
+    return {"c3_local_10k": dict(size=10000, seed=78, edges=int(cur.size), final=oracle.static_counts(rp, col))}
+
+
 def c5_graph(gi):
     """One graph of the serving workload: its static count and one
     100,000-update batch (70% insertions, batch seed 500 + gi) applied by the
@@ -147,6 +158,8 @@ if __name__ == "__main__":
             _merge("workloads_c5.json", res)
     elif "--large" in sys.argv and sys.argv[-1] == "c3_local":
         _merge("workloads_large.json", large_c3_local())
+    elif "--large" in sys.argv and sys.argv[-1] == "c3_local_10k":
+        _merge("workloads_large.json", large_c3_local_10k())
     elif "--large" in sys.argv:
         main_large()
     else:

@@ -611,6 +611,26 @@ def test_fullsize_c3_local_batches_keep_counts_of_the_graph(gcb):
             assert gl.num_edges() == gold["edges"]
 
 
+@pytest.mark.slow
+def test_fullsize_c3_ten_thousand_pairs_through_the_edge_local_delta(gcb):
+    """One 10,000-update batch on the 1.6M-vertex graph through the edge-local
+    delta (the autotuner keeps batches up to 16,384 pairs on it there): the
+    counts equal the oracle's count of the updated graph, and the region
+    form on a twin handle agrees."""
+    gold = _large_gold().get("c3_local_10k")
+    if gold is None:
+        pytest.skip("c3_local_10k not in workloads_large.json")
+    n, keys = gen.workload_graph("c3")
+    rp, col = gen.csr_from_keys(n, keys)
+    ins, dels = gen.batch_stream(n, keys, [gold["size"]], 0.7, gold["seed"])[0]
+    with open_graph(gcb, n, rp, col, local_max_pairs=1 << 30) as gl, open_graph(gcb, n, rp, col) as gr:
+        out = gl.apply(ins, dels)
+        assert gl.stats()["path"] == 1
+        assert out == gold["final"]
+        assert gr.apply(ins, dels) == out
+        assert gl.num_edges() == gold["edges"]
+
+
 def _c5_gold():
     p = os.path.join(GOLDEN_DIR, "workloads_c5.json")
     if not os.path.exists(p):
