@@ -595,7 +595,9 @@ static int ensure_desc(gc_graph* g, long long words) {
 // U build + counting + closed forms.
 //   fin: k_finalize mode (0 committed batch, 1 static, 2 independent batch)
 //   set_F: a static count that initialises F; timed: record stage events
-static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin = false) {
+// all: the region is every vertex (no per-entry region test in the union
+// graph); twin: the twin pass's union graph of two batches
+static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin = false, bool all = false) {
     cudaStream_t s = g->s;
     int gw = grid_warps(g);
     pdl_launch(k_reset_count, dim3(1), dim3(32), 0, s, g->ctl);
@@ -605,7 +607,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin 
                    g->U_deg);
     else
         pdl_launch(k_u_count, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
-                   g->segA, g->U_deg, 0);
+                   g->segA, g->U_deg, all ? 1 : 0);
     g->launches += 2;
     g->launches += scan_i32_to_i64(g->U_deg, g->U_off, nullptr, g->n, g->bsum.p, scan_grid(g->n, g->sms), &g->ctl->nU,
                                    s);
@@ -614,7 +616,8 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin 
                    g->segD, g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db);
     else
         pdl_launch(k_u_fill, dim3(gw), dim3(TPB), 0, s, g->ctl, g->wlist, g->visited, g->row_start, g->deg, g->col,
-                   g->segA, g->segD, g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db, 0);
+                   g->segA, g->segD, g->dstA.p, g->dstD.p, g->U_off, g->U_col.p, g->U_split, g->da, g->db,
+                   all ? 1 : 0);
     pdl_launch(k_zero_u64, dim3(grid_elems(g, (long long)g->U_col.cap)), dim3(TPB), 0, s, g->tpack.p, &g->ctl->nU);
     g->launches += 2;
     CountArgs ca;
@@ -829,7 +832,8 @@ static int enqueue_batch(gc_graph* g, long long max_nk, bool commit, bool timed,
     int rc = GC_OK;
     if (role != 1) {
         rc = local ? count_local(g, commit ? 1 : 0, timed, t2)
-                   : count_region(g, role == 2 ? 3 : role == 3 ? 4 : (commit ? 0 : 2), false, timed, twin);
+                   : count_region(g, role == 2 ? 3 : role == 3 ? 4 : (commit ? 0 : 2), false, timed, twin,
+                                  role == 2);
         if (rc) return rc;
     }
     if (!local && commit && t2 && role == 0) {
@@ -1296,7 +1300,7 @@ static int count_static(gc_graph* g, bool set_F, uint64_t out[6]) {
     g->launches += 2;
     CKL();
     CK(cudaEventRecord(g->ev[2], s));
-    rc = count_region(g, 1, set_F, true);
+    rc = count_region(g, 1, set_F, true, false, true);
     if (rc) return rc;
     // the static pass also gives the triangle sums of the edge-local path
     CK(cudaMemsetAsync(g->T2, 0, 8 * (size_t)std::max(g->n, 1), s));
