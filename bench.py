@@ -209,11 +209,17 @@ def make_batches(spec, count, rank=0, ins_frac=None, size=None):
 
 # ------------------------------------------------------------------ GPU arm --
 
-def run_plain(gcb, torch, n, rp, col, batches, warmup, steps, stream, flush, device_inputs=True):
+def run_plain(gcb, torch, n, rp, col, batches, warmup, steps, stream, flush, device_inputs=True, serial=False,
+              tuning=None):
     """Plain form: one C-ABI call per batch.  Returns per-step records.  The
-    handle's bin boundaries are autotuned once at open (untimed)."""
-    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream)
-    tuning, _ = gcb.gc_autotune(h, 2)
+    handle's bin boundaries are autotuned once at open (untimed) unless a
+    tuning is given.  serial: the counting kernels run one after another
+    (each kernel's event time is then its own)."""
+    h = gcb.gc_open(n, rp, col, stream=stream.cuda_stream, serial_count=serial)
+    if tuning:
+        gcb.gc_set_tuning(h, **tuning)
+    else:
+        tuning, _ = gcb.gc_autotune(h, 2)
     recs = []
     dev = []
     if device_inputs:
@@ -290,8 +296,9 @@ def roofline(recs, peak, peak_kind):
 
 def heavy_roofline(recs, peak, peak_kind):
     """Roofline of the dominant kernel: the heavy-pivot 4-cycle kernels,
-    timed alone by the library with CUDA events on the stream they run on
-    (gc_stats.ms_stage[7]).  Algorithmic bytes = 4 bytes per wedge they walk
+    timed by the library with CUDA events on the stream they run on
+    (gc_stats.ms_stage[7]; alone when the records come from a serial-count
+    handle).  Algorithmic bytes = 4 bytes per wedge they walk
     (one adjacency element each).  Beside the HBM roofline, the L2-atomic
     one: the counter updates they send to L2 over the time the probe rates
     would need for them."""
@@ -619,6 +626,11 @@ def gpu_arm(args):
     t_max = allreduce(world, s["seconds"], "max")
     edges_all = allreduce(world, float(s["edges"]), "sum")
     plain_value = edges_all / t_max
+    # the dominant kernel timed alone: the same batches with the counting
+    # kernels one after another (side by side, its event time also holds
+    # the wait for SMs the other kernels occupy)
+    recs_serial, _, _ = run_plain(gcb, torch, n, rp, col, batches, W, K, stream, flush, serial=True,
+                                  tuning=static_stats["tuning"])
     # batched form: the same K batches in one call (from a fresh open)
     barrier(world)
     with ClockSampler(local) as clk_b:
@@ -652,7 +664,8 @@ def gpu_arm(args):
         "batched_over_plain": batched_value / plain_value,
         "counts_equal_plain_batched": batched_equal,
         "gpu_launches": s["launches"] if best == "plain" else launches_b,
-        "roofline": heavy_roofline(recs, peak, peak_kind),
+        "roofline": heavy_roofline(recs_serial, peak, peak_kind),
+        "roofline_side_by_side": heavy_roofline(recs, peak, peak_kind),
         "clocks": clk.summary(),
         "clocks_batched": clk_b.summary(),
         "static_recount": {"ms": static_ms, "edges_per_s_if_recounting_each_batch": spec["batch"] / (static_ms / 1e3),

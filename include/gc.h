@@ -74,7 +74,11 @@ typedef struct {
                                 change (edges at its endpoints, 4-cliques and 4-cycles through its
                                 pairs) instead of a region recount.  0: never; gc_autotune sets
                                 it by measurement */
-    int32_t reserved[4];
+    int32_t serial_count;    /* 1: the counting kernels of a pass run one after another on the
+                                handle's stream instead of side by side on three side streams
+                                (slower; each kernel's own time, e.g. gc_stats.ms_stage[7], is
+                                then that of the kernel alone); 0: side by side */
+    int32_t reserved[3];
 } gc_options;
 
 /* Per-batch record of the last gc_apply_batch* call. */

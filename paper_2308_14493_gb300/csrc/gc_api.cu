@@ -643,7 +643,7 @@ static int count_region(gc_graph* g, int fin, bool set_F, bool timed, bool twin 
     ca.tune = g->tune;
     ca.sms = g->sms;
     for (int i = 0; i < 3; i++) {
-        ca.aux[i] = g->aux[i];
+        ca.aux[i] = g->opt.serial_count ? nullptr : g->aux[i];
         ca.join[i] = g->join[i];
     }
     ca.fork = g->fork;

@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
     unsigned long long* a64 = arrays + (size_t)gid * (size_t)(((long long)n + 1) & ~1ll);
     uint32_t* a32 = (uint32_t*)a64;
     const bool wide = c->maxdeg >= 65536;
-    __shared__ int s_idx, s_tot;
+    __shared__ int s_tot;
     __shared__ int s_pre[C4D_SEG + 1];
     __shared__ long long s_vb[C4D_SEG];
     __shared__ uint32_t s_fv[C4D_SEG];
@@ -939,21 +939,22 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
     const int bin = CLUSTER ? BIN_C4_DENSE : BIN_C4_CTA;
     const int cnt = c->nbin[bin];
     unsigned long long qa = 0, qb = 0, wedges = 0, nred = 0, natom = 0;
-    for (;;) {
+    // Pivot indices: the group's first thread takes the next pivot from the
+    // work counter while the current one is processed, into one of two slots
+    // (iteration t reads slot t & 1, fills slot (t + 1) & 1); the barrier at
+    // the end of each pivot publishes it, so fetching costs no barrier of
+    // its own.  A slot is refilled only after every CTA has passed the
+    // barrier that follows its last read.
+    __shared__ int s_next[2];
+    const int work_slot = CLUSTER ? WORK_C4_DENSE : WORK_C4_CTA;
+    if (rank == 0 && threadIdx.x == 0) s_next[0] = (int)atomicAdd(&c->work[work_slot], 1u);
+    group_sync<CLUSTER>();
+    for (int iter = 0;; iter++) {
         int idx;
-        if constexpr (CLUSTER) {
-            cg::cluster_group cl = cg::this_cluster();
-            if (rank == 0 && threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[WORK_C4_DENSE], 1u);
-            cl.sync();
-            idx = *cl.map_shared_rank(&s_idx, 0);
-            cl.sync();
-        } else {
-            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&c->work[WORK_C4_CTA], 1u);
-            __syncthreads();
-            idx = s_idx;
-            __syncthreads();
-        }
+        if constexpr (CLUSTER) idx = *cg::this_cluster().map_shared_rank(&s_next[iter & 1], 0);
+        else idx = s_next[iter & 1];
         if (idx >= cnt) break;
+        if (rank == 0 && threadIdx.x == 0) s_next[(iter + 1) & 1] = (int)atomicAdd(&c->work[work_slot], 1u);
         const int32_t u = list[idx];
         const long long rb = U_off[u];
         const int nlow = U_split[u];
@@ -1066,6 +1067,8 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
         }
         group_sync<CLUSTER>();
     }
+    // no CTA leaves while another may still read its shared memory
+    group_sync<CLUSTER>();
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
     acc_add(c, 15, wedges);

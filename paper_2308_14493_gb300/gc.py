@@ -31,7 +31,8 @@ class gc_options(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("region_hops", ctypes.c_int32), ("slack", ctypes.c_float),
                 ("device", ctypes.c_int32), ("dense_cluster", ctypes.c_int32), ("chunk_threshold", ctypes.c_int32),
-                ("local_max_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("local_max_pairs", ctypes.c_int32), ("serial_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class gc_stats(ctypes.Structure):
@@ -227,7 +228,7 @@ class TorchAllocator:
 
 def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, stream: int = 0,
             chunk_threshold: int = 0, dense_cluster: int = 0, local_max_pairs: int = 0,
-            allocator: TorchAllocator | None = None):
+            allocator: TorchAllocator | None = None, serial_count: bool = False):
     """Open a graph from a symmetric CSR; returns an opaque handle.  With an
     ``allocator`` (e.g. TorchAllocator) the library takes its device memory
     through it instead of cudaMallocAsync."""
@@ -242,6 +243,7 @@ def gc_open(n: int, row_ptr, col, region_hops: int = 3, slack: float = 0.25, str
     opt.chunk_threshold = chunk_threshold
     opt.dense_cluster = dense_cluster
     opt.local_max_pairs = local_max_pairs
+    opt.serial_count = 1 if serial_count else 0
     if allocator is not None:
         allocator.options(opt)
     h = ctypes.c_void_p()
