@@ -1524,6 +1524,7 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     // heaviest 4-cycle pivots and one hash table per CTA of the medium ones
     // (all kept zero between pivots)
     count_setup_attributes();
+    local_setup_attributes();
     g->bins = (int32_t*)dalloc(g, sizeof(int32_t) * (size_t)NBINS * nn);
     g->dense_clusters = dense_cluster_plan(g->opt.dense_cluster, g->sms, &g->dense_cluster_size);
     if (!g->bins || !ensure(g, g->dense, (size_t)g->dense_clusters * (nn + 1))) return nomem(g, "counting work lists");

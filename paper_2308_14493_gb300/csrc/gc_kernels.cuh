@@ -111,6 +111,7 @@ struct CountArgs {
 Tuning effective_tuning(const CountArgs& a);
 // Dynamic shared-memory limits of the counting kernels (once per device).
 void count_setup_attributes();
+void local_setup_attributes();
 size_t c4_chunk_smem_bytes();
 int c4_chunk_width(long long n);                 // id-range chunks + 1
 long long c4_chunk_cap(long long n);             // run-bound entries per CTA for ids below n

@@ -571,50 +571,135 @@ __global__ void k_loc_c4_tasks(const Ctl* c, LocalView V, const int32_t* __restr
     }
 }
 
-__global__ void k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA, const int32_t* __restrict__ dstA,
-                         const int32_t* __restrict__ srcD, const int32_t* __restrict__ dstD,
-                         const int32_t* __restrict__ walk, const int32_t* __restrict__ tpair,
-                         const int32_t* __restrict__ tent, const long long* __restrict__ tpre) {
+// Each block takes one contiguous range of the probes (numbered pair by
+// pair, then task by task).  Before walking it the block picks the pair with
+// the most probes in the range and puts the other endpoint u's union row
+// (entries with their flags) into a bucketed hash table in shared memory,
+// when that row has between LC4_ROW_MIN and LC4_ROW_MAX entries and the
+// range holds at least two probes of the pair per entry; the probes of that
+// pair that walk N(w) then look z up there instead of binary-searching u's
+// row in global memory.  Probes that walk u's row (N(w) the longer) search
+// N(w) as before.  4 slots to a bucket, linear probing over buckets, at most
+// 3/4 of the slots filled, so every lookup ends at an empty slot.
+constexpr int LC4_BUCKETS = 4096;
+constexpr int LC4_ROW_MAX = 3 * LC4_BUCKETS;
+constexpr int LC4_ROW_MIN = 64;
+constexpr uint32_t LC4_EMPTY = 0xFFFFFFFFu;  // ids stay below 2^30 - 1
+constexpr size_t LC4_SMEM = (size_t)LC4_BUCKETS * sizeof(uint4);
+constexpr int LC4_THREADS = 512;
+
+__device__ __forceinline__ uint32_t lc4_bucket(uint32_t z, int lgb) { return (z * 0x9E3779B1u) >> (32 - lgb); }
+
+__device__ __forceinline__ uint32_t lc4_find(const uint4* __restrict__ tab, int lgb, uint32_t z) {
+    const uint32_t mask = (1u << lgb) - 1;
+    uint32_t h = lc4_bucket(z, lgb);
+    for (int it = 0; it <= (int)mask; it++) {
+        const uint4 q = tab[h];
+        if (vid(q.x) == z) return q.x;
+        if (vid(q.y) == z) return q.y;
+        if (vid(q.z) == z) return q.z;
+        if (vid(q.w) == z) return q.w;
+        if (q.w == LC4_EMPTY) break;  // slots fill in order within a bucket
+        h = (h + 1) & mask;
+    }
+    return LC4_EMPTY;
+}
+
+__global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+                                                const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
+                                                const int32_t* __restrict__ dstD, const int32_t* __restrict__ walk,
+                                                const int32_t* __restrict__ tpair, const int32_t* __restrict__ tent,
+                                                const long long* __restrict__ tpre,
+                                                const long long* __restrict__ cpre) {
     pdl_enter();
+    extern __shared__ uint4 tab[];
+    __shared__ unsigned long long s_best;
+    __shared__ long long s_pair[2];
     const long long n = c->l_len[3];
     const long long tot = n ? tpre[n] : 0;
+    const long long lo = tot * blockIdx.x / gridDim.x, hi = tot * (blockIdx.x + 1) / gridDim.x;
     unsigned long long qa = 0, qb = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long sb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); sb < tot; sb += stride) {
-        const long long s = sb + (threadIdx.x & 31);
-        const long long tau = locate_warp(tpre, n, s, s < tot);
-        if (s >= tot) continue;
-        const int k = (int)(s - tpre[tau]);
-        const int pi = tpair[tau];
-        const Pair p = pair_at(c, srcA, dstA, srcD, dstD, pi);
-        uint32_t v, u;
-        c4_orient(p, walk[pi], &v, &u);
-        const Row rv = V.urow(v), ru = V.urow(u);
-        const uint32_t ev = rv.p[tent[tau]];
-        const uint32_t w = vid(ev), fvw = ev & AB;
-        const Row rw = V.row(w);
-        uint32_t z, fuz, fwz;
-        if (rw.len <= ru.len) {
-            z = vid(rw.p[k]);
-            fwz = flags_at(rw, k);
-            const int q = row_find(ru, 0, z);
-            if (q < 0) continue;
-            fuz = flags_at(ru, q);
-        } else {
-            z = vid(ru.p[k]);
-            fuz = flags_at(ru, k);
-            const int q = row_find(rw, 0, z);
-            if (q < 0) continue;
-            fwz = flags_at(rw, q);
+    if (lo < hi) {
+        // the pair with the most probes in [lo, hi) whose u row can be staged
+        if (threadIdx.x == 0) {
+            s_best = 0;
+            s_pair[0] = tpair[locate(tpre, n, lo)];
+            s_pair[1] = tpair[locate(tpre, n, hi - 1)];
         }
-        const uint32_t x = p.x;
-        if (z == v || !(fvw & fuz & fwz & x)) continue;
-        // the cycle u-v-w-z-u, counted at its smallest changed pair of graph x
-        const unsigned long long kp = pkey(p.a, p.b);
-        if ((fvw == x && pkey(v, w) < kp) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp))
-            continue;
-        if (x == FLAG_A) qa++;
-        else qb++;
+        __syncthreads();
+        for (long long i = s_pair[0] + threadIdx.x; i <= s_pair[1]; i += blockDim.x) {
+            const long long ta = cpre[i], tb = cpre[i + 1];
+            if (ta >= tb) continue;
+            const long long cnt = min(hi, tpre[tb]) - max(lo, tpre[ta]);
+            const Pair p = pair_at(c, srcA, dstA, srcD, dstD, i);
+            const uint32_t u = walk[i] ? p.b : p.a;
+            const long long len = V.U_off[u + 1] - V.U_off[u];
+            if (len < LC4_ROW_MIN || len > LC4_ROW_MAX || cnt < 2 * len) continue;
+            atomicMax(&s_best, ((unsigned long long)min(cnt, 0xFFFFFFFFll) << 32) | (unsigned long long)i);
+        }
+        __syncthreads();
+        const unsigned long long best = s_best;
+        const long long sp = best ? (long long)(uint32_t)best : -1;
+        int lgb = 0;
+        if (sp >= 0) {
+            const Pair p = pair_at(c, srcA, dstA, srcD, dstD, sp);
+            const Row ru = V.urow(walk[sp] ? p.b : p.a);
+            while ((2 << lgb) < ru.len) lgb++;  // buckets >= len / 2
+            lgb = min(lgb, 12);
+            uint32_t* slot = reinterpret_cast<uint32_t*>(tab);
+            for (int q = threadIdx.x; q < (4 << lgb); q += blockDim.x) slot[q] = LC4_EMPTY;
+            __syncthreads();
+            const uint32_t mask = (1u << lgb) - 1;
+            for (int q = threadIdx.x; q < ru.len; q += blockDim.x) {
+                const uint32_t e = ru.p[q];
+                uint32_t h = lc4_bucket(vid(e), lgb);
+                for (bool done = false; !done; h = (h + 1) & mask)
+                    for (int j = 0; j < 4 && !done; j++) done = atomicCAS(&slot[4 * h + j], LC4_EMPTY, e) == LC4_EMPTY;
+            }
+            __syncthreads();
+        }
+        for (long long sb = lo + (threadIdx.x & ~31); sb < hi; sb += blockDim.x) {
+            const long long s = sb + (threadIdx.x & 31);
+            const long long tau = locate_warp(tpre, n, s, s < hi);
+            if (s >= hi) continue;
+            const int k = (int)(s - tpre[tau]);
+            const int pi = tpair[tau];
+            const Pair p = pair_at(c, srcA, dstA, srcD, dstD, pi);
+            uint32_t v, u;
+            c4_orient(p, walk[pi], &v, &u);
+            const Row rv = V.urow(v), ru = V.urow(u);
+            const uint32_t ev = rv.p[tent[tau]];
+            const uint32_t w = vid(ev), fvw = ev & AB;
+            const Row rw = V.row(w);
+            uint32_t z, fuz, fwz;
+            if (rw.len <= ru.len) {
+                z = vid(rw.p[k]);
+                fwz = flags_at(rw, k);
+                if (pi == sp) {
+                    const uint32_t e = lc4_find(tab, lgb, z);
+                    if (e == LC4_EMPTY) continue;
+                    fuz = e & AB;
+                } else {
+                    const int q = row_find(ru, 0, z);
+                    if (q < 0) continue;
+                    fuz = flags_at(ru, q);
+                }
+            } else {
+                z = vid(ru.p[k]);
+                fuz = flags_at(ru, k);
+                const int q = row_find(rw, 0, z);
+                if (q < 0) continue;
+                fwz = flags_at(rw, q);
+            }
+            const uint32_t x = p.x;
+            if (z == v || !(fvw & fuz & fwz & x)) continue;
+            // the cycle u-v-w-z-u, counted at its smallest changed pair of graph x
+            const unsigned long long kp = pkey(p.a, p.b);
+            if ((fvw == x && pkey(v, w) < kp) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp))
+                continue;
+            if (x == FLAG_A) qa++;
+            else qb++;
+        }
     }
     acc_warp(c, 5, qa);
     acc_warp(c, 11, qb);
@@ -891,6 +976,24 @@ __global__ void k_finalize_local(Ctl* c, int commit) {
 
 // ---- launch sequence ---------------------------------------------------------------
 
+// Blocks of the 4-cycle kernel: four waves of the blocks that fit at once
+// (its staged table takes 64 KB of shared memory; three 512-thread blocks
+// share an SM), so that ranges of unequal
+// cost even out.
+static int g_loc_c4_per_sm = 0;
+
+void local_setup_attributes() {
+    cudaFuncSetAttribute(k_loc_c4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LC4_SMEM);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loc_c4, LC4_THREADS, LC4_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    g_loc_c4_per_sm = per_sm > 0 ? per_sm : 2;
+}
+
+static int loc_c4_grid(int sms) { return 4 * sms * (g_loc_c4_per_sm > 0 ? g_loc_c4_per_sm : 2); }
+
 int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,
                   int commit) {
     const int sms = a.sms;
@@ -945,8 +1048,8 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
                                       a.cost);
     nl += 2;
     nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
-    pdl_launch(k_loc_c4, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD, a.walk, a.tpair, a.own,
-               a.pre);
+    pdl_launch(k_loc_c4, dim3(loc_c4_grid(sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD,
+               a.walk, a.tpair, a.own, a.pre, a.cpre);
     nl++;
     if (ev_fin) record_stage(ev_fin, s);
     pdl_launch(k_finalize_local, dim3(1), dim3(32), 0, s, a.ctl, commit);
