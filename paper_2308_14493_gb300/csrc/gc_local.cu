@@ -135,6 +135,23 @@ __device__ __forceinline__ long long locate_warp(const long long* __restrict__ p
     return e;
 }
 
+// The task that holds probe s, searched forward from task e (pre[e] <= s <
+// pre[n]; every lane calls it with the same s and e): 32 task boundaries per
+// coalesced load, so runs of empty tasks are crossed quickly; a binary search
+// after four full windows.
+__device__ __forceinline__ long long next_task(const long long* __restrict__ pre, long long n, long long s,
+                                               long long e) {
+    for (int it = 0; it < 4; it++) {
+        const long long k = e + 1 + (threadIdx.x & 31);
+        const unsigned m = __ballot_sync(FULL, k < n && pre[k] <= s);
+        e += __popc(m);
+        if (m != FULL) return e;
+    }
+    long long r = 0;
+    if ((threadIdx.x & 31) == 0) r = locate(pre, n, s, e);
+    return __shfl_sync(FULL, r, 0);
+}
+
 __device__ __forceinline__ unsigned long long pkey(uint32_t a, uint32_t b) {
     return a < b ? ((unsigned long long)a << 32) | b : ((unsigned long long)b << 32) | a;
 }
@@ -265,36 +282,55 @@ __global__ void k_loc_tri_cost(const Ctl* c, LocalView V, const int32_t* __restr
     }
 }
 
-// One probe per thread: t_e for G_a and G_b packed into tpack[e] (high 32
-// bits G_a, low 32 G_b).
+// t_e for G_a and G_b packed into tpack[e] (high 32 bits G_a, low 32 G_b).
+// Each warp takes one contiguous slice of the probes and walks it edge by
+// edge: the edge's rows once, then its probes 32 at a time, the hits summed
+// over the warp before one atomic per edge and slice.
 __global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict__ pre,
                           const int32_t* __restrict__ own, unsigned long long* __restrict__ tpack) {
     pdl_enter();
     const long long n = c->l_len[0];
     if (n == 0) return;
     const long long tot = pre[n];
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long tb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); tb < tot; tb += stride) {
-        const long long t = tb + (threadIdx.x & 31);
-        const long long e = locate_warp(pre, n, t, t < tot);
-        if (t >= tot) continue;
-        const int k = (int)(t - pre[e]);
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long wlo = tot * gw / nw, whi = tot * (gw + 1) / nw;
+    if (wlo >= whi) return;
+    long long e = 0;
+    if (lane == 0) e = locate(pre, n, wlo);
+    e = __shfl_sync(FULL, e, 0);
+    for (long long s = wlo; s < whi;) {
+        e = next_task(pre, n, s, e);
+        const long long pe = pre[e + 1], pb = pre[e];
+        const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
+        s = min(whi, pe);
         const uint32_t u = (uint32_t)own[e];
         const Row ru = V.urow(u);
-        const uint32_t w = vid(V.U_col[e]);
-        const Row rw = V.row(w);
-        uint32_t f;
+        const Row rw = V.row(vid(V.U_col[e]));
+        unsigned ca = 0, cb = 0;
         if (ru.len <= rw.len) {
-            const uint32_t z = ru.p[k];
-            const int q = row_find(rw, 0, vid(z));
-            f = q < 0 ? 0u : (z & flags_at(rw, q));
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const uint32_t z = ru.p[k];
+                const int q = row_find(rw, 0, vid(z));
+                if (q < 0) continue;
+                const uint32_t f = z & flags_at(rw, q);
+                ca += (f & FLAG_A) != 0;
+                cb += (f & FLAG_B) != 0;
+            }
         } else {
-            const uint32_t z = rw.p[k] | rw.orf;
-            const int q = row_find(ru, 0, vid(z));
-            f = q < 0 ? 0u : (z & flags_at(ru, q));
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const uint32_t z = rw.p[k] | rw.orf;
+                const int q = row_find(ru, 0, vid(z));
+                if (q < 0) continue;
+                const uint32_t f = z & flags_at(ru, q);
+                ca += (f & FLAG_A) != 0;
+                cb += (f & FLAG_B) != 0;
+            }
         }
-        f &= AB;
-        if (f) atomicAdd(&tpack[e], ((f & FLAG_A) ? (1ull << 32) : 0ull) | ((f & FLAG_B) ? 1ull : 0ull));
+        ca = __reduce_add_sync(FULL, ca);
+        cb = __reduce_add_sync(FULL, cb);
+        if (lane == 0 && (ca | cb)) atomicAdd(&tpack[e], ((unsigned long long)ca << 32) | cb);
     }
 }
 
@@ -658,47 +694,60 @@ __global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, con
             }
             __syncthreads();
         }
-        for (long long sb = lo + (threadIdx.x & ~31); sb < hi; sb += blockDim.x) {
-            const long long s = sb + (threadIdx.x & 31);
-            const long long tau = locate_warp(tpre, n, s, s < hi);
-            if (s >= hi) continue;
-            const int k = (int)(s - tpre[tau]);
+        // each warp walks one slice of the block's range task by task: the
+        // task's pair, rows and walked entry once, then its probes 32 at a time
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+        const long long wlo = lo + (hi - lo) * wib / nwb, whi = lo + (hi - lo) * (wib + 1) / nwb;
+        long long tau = 0;
+        if (lane == 0 && wlo < whi) tau = locate(tpre, n, wlo);
+        tau = __shfl_sync(FULL, tau, 0);
+        for (long long s = wlo; s < whi;) {
+            tau = next_task(tpre, n, s, tau);
+            const long long pe = tpre[tau + 1], pb = tpre[tau];
+            const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
+            s = min(whi, pe);
             const int pi = tpair[tau];
             const Pair p = pair_at(c, srcA, dstA, srcD, dstD, pi);
             uint32_t v, u;
             c4_orient(p, walk[pi], &v, &u);
-            const Row rv = V.urow(v), ru = V.urow(u);
-            const uint32_t ev = rv.p[tent[tau]];
-            const uint32_t w = vid(ev), fvw = ev & AB;
-            const Row rw = V.row(w);
-            uint32_t z, fuz, fwz;
+            const uint32_t ev = V.urow(v).p[tent[tau]];
+            const uint32_t w = vid(ev), fvw = ev & AB, x = p.x;
+            // the cycle u-v-w-z-u is counted at its smallest changed pair of graph x
+            const unsigned long long kp = pkey(p.a, p.b);
+            if (!(fvw & x) || (fvw == x && pkey(v, w) < kp)) continue;
+            const Row ru = V.urow(u), rw = V.row(w);
+            unsigned long long q4 = 0;
             if (rw.len <= ru.len) {
-                z = vid(rw.p[k]);
-                fwz = flags_at(rw, k);
-                if (pi == sp) {
-                    const uint32_t e = lc4_find(tab, lgb, z);
-                    if (e == LC4_EMPTY) continue;
-                    fuz = e & AB;
-                } else {
-                    const int q = row_find(ru, 0, z);
-                    if (q < 0) continue;
-                    fuz = flags_at(ru, q);
+                const bool staged = pi == sp;
+                for (int k = k0 + lane; k < k1; k += 32) {
+                    const uint32_t z = vid(rw.p[k]), fwz = flags_at(rw, k);
+                    if (z == v || !(fwz & x)) continue;
+                    uint32_t fuz;
+                    if (staged) {
+                        const uint32_t e = lc4_find(tab, lgb, z);
+                        if (e == LC4_EMPTY) continue;
+                        fuz = e & AB;
+                    } else {
+                        const int q = row_find(ru, 0, z);
+                        if (q < 0) continue;
+                        fuz = flags_at(ru, q);
+                    }
+                    if (!(fuz & x) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp)) continue;
+                    q4++;
                 }
             } else {
-                z = vid(ru.p[k]);
-                fuz = flags_at(ru, k);
-                const int q = row_find(rw, 0, z);
-                if (q < 0) continue;
-                fwz = flags_at(rw, q);
+                for (int k = k0 + lane; k < k1; k += 32) {
+                    const uint32_t z = vid(ru.p[k]), fuz = flags_at(ru, k);
+                    if (z == v || !(fuz & x)) continue;
+                    const int q = row_find(rw, 0, z);
+                    if (q < 0) continue;
+                    const uint32_t fwz = flags_at(rw, q);
+                    if (!(fwz & x) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp)) continue;
+                    q4++;
+                }
             }
-            const uint32_t x = p.x;
-            if (z == v || !(fvw & fuz & fwz & x)) continue;
-            // the cycle u-v-w-z-u, counted at its smallest changed pair of graph x
-            const unsigned long long kp = pkey(p.a, p.b);
-            if ((fvw == x && pkey(v, w) < kp) || (fwz == x && pkey(w, z) < kp) || (fuz == x && pkey(u, z) < kp))
-                continue;
-            if (x == FLAG_A) qa++;
-            else qb++;
+            if (x == FLAG_A) qa += q4;
+            else qb += q4;
         }
     }
     acc_warp(c, 5, qa);
