@@ -282,58 +282,6 @@ __global__ void k_loc_tri_cost(const Ctl* c, LocalView V, const int32_t* __restr
     }
 }
 
-// t_e for G_a and G_b packed into tpack[e] (high 32 bits G_a, low 32 G_b).
-// Each warp takes one contiguous slice of the probes and walks it edge by
-// edge: the edge's rows once, then its probes 32 at a time, the hits summed
-// over the warp before one atomic per edge and slice.
-__global__ void k_loc_tri(const Ctl* c, LocalView V, const long long* __restrict__ pre,
-                          const int32_t* __restrict__ own, unsigned long long* __restrict__ tpack) {
-    pdl_enter();
-    const long long n = c->l_len[0];
-    if (n == 0) return;
-    const long long tot = pre[n];
-    const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long wlo = tot * gw / nw, whi = tot * (gw + 1) / nw;
-    if (wlo >= whi) return;
-    long long e = 0;
-    if (lane == 0) e = locate(pre, n, wlo);
-    e = __shfl_sync(FULL, e, 0);
-    for (long long s = wlo; s < whi;) {
-        e = next_task(pre, n, s, e);
-        const long long pe = pre[e + 1], pb = pre[e];
-        const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
-        s = min(whi, pe);
-        const uint32_t u = (uint32_t)own[e];
-        const Row ru = V.urow(u);
-        const Row rw = V.row(vid(V.U_col[e]));
-        unsigned ca = 0, cb = 0;
-        if (ru.len <= rw.len) {
-            for (int k = k0 + lane; k < k1; k += 32) {
-                const uint32_t z = ru.p[k];
-                const int q = row_find(rw, 0, vid(z));
-                if (q < 0) continue;
-                const uint32_t f = z & flags_at(rw, q);
-                ca += (f & FLAG_A) != 0;
-                cb += (f & FLAG_B) != 0;
-            }
-        } else {
-            for (int k = k0 + lane; k < k1; k += 32) {
-                const uint32_t z = rw.p[k] | rw.orf;
-                const int q = row_find(ru, 0, vid(z));
-                if (q < 0) continue;
-                const uint32_t f = z & flags_at(ru, q);
-                ca += (f & FLAG_A) != 0;
-                cb += (f & FLAG_B) != 0;
-            }
-        }
-        ca = __reduce_add_sync(FULL, ca);
-        cb = __reduce_add_sync(FULL, cb);
-        if (lane == 0 && (ca | cb)) atomicAdd(&tpack[e], ((unsigned long long)ca << 32) | cb);
-    }
-}
-
 // ---- per-edge and per-vertex terms --------------------------------------------
 
 // The a- and b-side terms of every edge with an endpoint in V_X (a thread
@@ -641,7 +589,27 @@ __device__ __forceinline__ uint32_t lc4_find(const uint4* __restrict__ tab, int 
     return LC4_EMPTY;
 }
 
-__global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
+// Fills the table with row r (the whole block calls it; LC4_ROW_MIN <=
+// r.len <= LC4_ROW_MAX) and returns log2 of its bucket count.
+__device__ __forceinline__ int lc4_stage(uint4* tab, const Row& r) {
+    int lgb = 0;
+    while ((2 << lgb) < r.len) lgb++;  // buckets >= len / 2
+    lgb = min(lgb, 12);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(tab);
+    for (int q = threadIdx.x; q < (4 << lgb); q += blockDim.x) slot[q] = LC4_EMPTY;
+    __syncthreads();
+    const uint32_t mask = (1u << lgb) - 1;
+    for (int q = threadIdx.x; q < r.len; q += blockDim.x) {
+        const uint32_t e = r.p[q] | r.orf;
+        uint32_t h = lc4_bucket(vid(e), lgb);
+        for (bool done = false; !done; h = (h + 1) & mask)
+            for (int j = 0; j < 4 && !done; j++) done = atomicCAS(&slot[4 * h + j], LC4_EMPTY, e) == LC4_EMPTY;
+    }
+    __syncthreads();
+    return lgb;
+}
+
+__global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, const int32_t* __restrict__ srcA,
                                                 const int32_t* __restrict__ dstA, const int32_t* __restrict__ srcD,
                                                 const int32_t* __restrict__ dstD, const int32_t* __restrict__ walk,
                                                 const int32_t* __restrict__ tpair, const int32_t* __restrict__ tent,
@@ -679,20 +647,7 @@ __global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, con
         int lgb = 0;
         if (sp >= 0) {
             const Pair p = pair_at(c, srcA, dstA, srcD, dstD, sp);
-            const Row ru = V.urow(walk[sp] ? p.b : p.a);
-            while ((2 << lgb) < ru.len) lgb++;  // buckets >= len / 2
-            lgb = min(lgb, 12);
-            uint32_t* slot = reinterpret_cast<uint32_t*>(tab);
-            for (int q = threadIdx.x; q < (4 << lgb); q += blockDim.x) slot[q] = LC4_EMPTY;
-            __syncthreads();
-            const uint32_t mask = (1u << lgb) - 1;
-            for (int q = threadIdx.x; q < ru.len; q += blockDim.x) {
-                const uint32_t e = ru.p[q];
-                uint32_t h = lc4_bucket(vid(e), lgb);
-                for (bool done = false; !done; h = (h + 1) & mask)
-                    for (int j = 0; j < 4 && !done; j++) done = atomicCAS(&slot[4 * h + j], LC4_EMPTY, e) == LC4_EMPTY;
-            }
-            __syncthreads();
+            lgb = lc4_stage(tab, V.urow(walk[sp] ? p.b : p.a));
         }
         // each warp walks one slice of the block's range task by task: the
         // task's pair, rows and walked entry once, then its probes 32 at a time
@@ -716,7 +671,7 @@ __global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, con
             const unsigned long long kp = pkey(p.a, p.b);
             if (!(fvw & x) || (fvw == x && pkey(v, w) < kp)) continue;
             const Row ru = V.urow(u), rw = V.row(w);
-            unsigned long long q4 = 0;
+            unsigned q4 = 0;
             if (rw.len <= ru.len) {
                 const bool staged = pi == sp;
                 for (int k = k0 + lane; k < k1; k += 32) {
@@ -752,6 +707,91 @@ __global__ void __launch_bounds__(LC4_THREADS) k_loc_c4(Ctl* c, LocalView V, con
     }
     acc_warp(c, 5, qa);
     acc_warp(c, 11, qb);
+}
+
+// t_e for G_a and G_b packed into tpack[e] (high 32 bits G_a, low 32 G_b).
+// The probes are numbered edge by edge, and the edges of one owner u are
+// consecutive.  Each block takes one contiguous range of the probes and
+// stages the union row of the owner with the most probes in it (of the
+// owners of its first, middle and last probe) in the shared-memory hash,
+// under the same bounds as the 4-cycle kernel; that owner's edges whose probes
+// walk N(w) look z up there.  Each warp walks one slice of the block's range
+// edge by edge: the edge's rows once, then its probes 32 at a time, the hits
+// summed over the warp before one atomic per edge and slice.
+__global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalView V,
+                                                            const long long* __restrict__ pre,
+                                                            const int32_t* __restrict__ own,
+                                                            unsigned long long* __restrict__ tpack) {
+    pdl_enter();
+    extern __shared__ uint4 tab[];
+    __shared__ int32_t s_cand[3];
+    const long long n = c->l_len[0];
+    if (n == 0) return;
+    const long long tot = pre[n];
+    const long long lo = tot * blockIdx.x / gridDim.x, hi = tot * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;
+    if (threadIdx.x < 3) {
+        const long long t = threadIdx.x == 0 ? lo : threadIdx.x == 1 ? lo + (hi - lo) / 2 : hi - 1;
+        s_cand[threadIdx.x] = own[locate(pre, n, t)];
+    }
+    __syncthreads();
+    long long su = -1, best = 0;
+    for (int j = 0; j < 3; j++) {
+        const uint32_t u = (uint32_t)s_cand[j];
+        const long long b = V.U_off[u], e = V.U_off[u + 1];
+        const long long cnt = min(hi, pre[e]) - max(lo, pre[b]);
+        if (e - b < LC4_ROW_MIN || e - b > LC4_ROW_MAX || cnt < 2 * (e - b) || cnt <= best) continue;
+        best = cnt;
+        su = u;
+    }
+    int lgb = 0;
+    if (su >= 0) lgb = lc4_stage(tab, V.urow((uint32_t)su));
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const long long wlo = lo + (hi - lo) * wib / nwb, whi = lo + (hi - lo) * (wib + 1) / nwb;
+    long long e = 0;
+    if (lane == 0 && wlo < whi) e = locate(pre, n, wlo);
+    e = __shfl_sync(FULL, e, 0);
+    for (long long s = wlo; s < whi;) {
+        e = next_task(pre, n, s, e);
+        const long long pe = pre[e + 1], pb = pre[e];
+        const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
+        s = min(whi, pe);
+        const uint32_t u = (uint32_t)own[e];
+        const Row ru = V.urow(u);
+        const Row rw = V.row(vid(V.U_col[e]));
+        unsigned ca = 0, cb = 0;
+        if (ru.len <= rw.len) {
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const uint32_t z = ru.p[k];
+                const int q = row_find(rw, 0, vid(z));
+                if (q < 0) continue;
+                const uint32_t f = z & flags_at(rw, q);
+                ca += (f & FLAG_A) != 0;
+                cb += (f & FLAG_B) != 0;
+            }
+        } else if (u == su) {
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const uint32_t z = rw.p[k] | rw.orf;
+                const uint32_t hit = lc4_find(tab, lgb, vid(z));
+                if (hit == LC4_EMPTY) continue;
+                const uint32_t f = z & hit;
+                ca += (f & FLAG_A) != 0;
+                cb += (f & FLAG_B) != 0;
+            }
+        } else {
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const uint32_t z = rw.p[k] | rw.orf;
+                const int q = row_find(ru, 0, vid(z));
+                if (q < 0) continue;
+                const uint32_t f = z & flags_at(ru, q);
+                ca += (f & FLAG_A) != 0;
+                cb += (f & FLAG_B) != 0;
+            }
+        }
+        ca = __reduce_add_sync(FULL, ca);
+        cb = __reduce_add_sync(FULL, cb);
+        if (lane == 0 && (ca | cb)) atomicAdd(&tpack[e], ((unsigned long long)ca << 32) | cb);
+    }
 }
 
 // ---- with maintained triangle sums ---------------------------------------------------
@@ -1025,23 +1065,29 @@ __global__ void k_finalize_local(Ctl* c, int commit) {
 
 // ---- launch sequence ---------------------------------------------------------------
 
-// Blocks of the 4-cycle kernel: four waves of the blocks that fit at once
-// (its staged table takes 64 KB of shared memory; three 512-thread blocks
-// share an SM), so that ranges of unequal
-// cost even out.
-static int g_loc_c4_per_sm = 0;
+// Blocks of the two kernels with a staged row: four waves of the blocks that
+// fit at once (the table takes 64 KB of shared memory; three 512-thread
+// blocks share an SM), so that ranges of unequal cost even out.
+static int g_loc_per_sm[2] = {0, 0};
 
-void local_setup_attributes() {
-    cudaFuncSetAttribute(k_loc_c4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LC4_SMEM);
+template <typename K>
+static int staged_per_sm(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LC4_SMEM);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loc_c4, LC4_THREADS, LC4_SMEM) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LC4_THREADS, LC4_SMEM) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 0;
     }
-    g_loc_c4_per_sm = per_sm > 0 ? per_sm : 2;
+    return per_sm > 0 ? per_sm : 2;
 }
 
-static int loc_c4_grid(int sms) { return 4 * sms * (g_loc_c4_per_sm > 0 ? g_loc_c4_per_sm : 2); }
+void local_setup_attributes() {
+    g_loc_per_sm[0] = staged_per_sm(k_loc_tri);
+    g_loc_per_sm[1] = staged_per_sm(k_loc_c4);
+}
+
+// kind 0: the triangle kernel, 1: the 4-cycle kernel
+static int staged_grid(int kind, int sms) { return 4 * sms * (g_loc_per_sm[kind] > 0 ? g_loc_per_sm[kind] : 2); }
 
 int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEvent_t ev_sub, cudaEvent_t ev_fin,
                   int commit) {
@@ -1072,7 +1118,8 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
         pdl_launch(k_loc_dcost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.dcnt, a.cost);
         nl += 3;
         nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
-        pdl_launch(k_loc_tri, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.pre, a.own, a.tpack);
+        pdl_launch(k_loc_tri, dim3(staged_grid(0, sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.pre, a.own,
+                   a.tpack);
         pdl_launch(k_loc_eterms, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.tpack, a.dcnt, a.da, a.db);
         pdl_launch(k_loc_vterms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, V, a.T2, a.dtri2, a.da, a.db, commit);
         nl += 3;
@@ -1081,7 +1128,8 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
         pdl_launch(k_loc_tri_cost, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.own, a.cost);
         nl++;
         nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[0], 0, a.bsum, sg, &a.ctl->l_tot[0], s);
-        pdl_launch(k_loc_tri, dim3(gw), dim3(tpb), 0, s, a.ctl, V, a.pre, a.own, a.tpack);
+        pdl_launch(k_loc_tri, dim3(staged_grid(0, sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.pre, a.own,
+                   a.tpack);
         pdl_launch(k_loc_terms, dim3(gw), dim3(tpb), 0, s, a.ctl, a.wlist, V, a.own, a.tpack, a.da, a.db);
         nl += 2;
     }
@@ -1097,7 +1145,7 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
                                       a.cost);
     nl += 2;
     nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
-    pdl_launch(k_loc_c4, dim3(loc_c4_grid(sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD,
+    pdl_launch(k_loc_c4, dim3(staged_grid(1, sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD,
                a.walk, a.tpair, a.own, a.pre, a.cpre);
     nl++;
     if (ev_fin) record_stage(ev_fin, s);
