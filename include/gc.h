@@ -397,7 +397,7 @@ int gc_set_tuning(gc_graph *g, const gc_tuning *t);
  * (may be NULL); *best_ms (may be NULL) receives its time.  Counts are
  * checked equal across all candidates (GC_ECUDA if not).
  * Then the edge-local threshold: what-if batches of k pairs (k = 8, 16,
- * 32, ... up to m / 4 and 2^16; half deletions of edges sampled uniformly,
+ * 32, ... up to m / 4 and 2^17; half deletions of edges sampled uniformly,
  * half insertions between vertices drawn in proportion to degree) are
  * timed through the edge-local delta and through the region recount;
  * local_max_pairs becomes the largest k at which the local form was faster

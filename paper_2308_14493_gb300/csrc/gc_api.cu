@@ -2417,7 +2417,7 @@ static int calibrate_local(gc_graph* g, int reps) {
         return GC_OK;
     }
     cudaStream_t s = g->s;
-    const long long kmax = std::min<long long>(g->m / 4, 1LL << 16);
+    const long long kmax = std::min<long long>(g->m / 4, 1LL << 17);
     if (!ensure(g, g->pairs, 2 * (size_t)std::max<long long>(kmax, 8))) return nomem(g, "calibration pairs");
     // each calibration batch: k / 2 deletions, then k / 2 insertions
     // degree prefix sums (the union-graph offsets are free between batches)

@@ -672,9 +672,19 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
             if (!(fvw & x) || (fvw == x && pkey(v, w) < kp)) continue;
             const Row ru = V.urow(u), rw = V.row(w);
             unsigned q4 = 0;
-            if (rw.len <= ru.len) {
-                const bool staged = pi == sp;
-                for (int k = k0 + lane; k < k1; k += 32) {
+            const bool staged = pi == sp;
+            // with u's row staged, a task whose N(w) is longer (at most four
+            // times) still walks N(w) when the task lies wholly in this
+            // block's range: its probe range [k0, k1) of u's row maps to the
+            // proportional range of N(w), so the warp slices that split the
+            // task split N(w) exactly.  A task that a block boundary cuts
+            // keeps walking u's row in both blocks, whichever pairs they stage.
+            const bool walk_w =
+                rw.len <= ru.len || (staged && pb >= lo && pe <= hi && rw.len <= 4 * ru.len);
+            if (walk_w) {
+                const int j0 = rw.len <= ru.len ? k0 : (int)((long long)k0 * rw.len / ru.len);
+                const int j1 = rw.len <= ru.len ? k1 : (int)((long long)k1 * rw.len / ru.len);
+                for (int k = j0 + lane; k < j1; k += 32) {
                     const uint32_t z = vid(rw.p[k]), fwz = flags_at(rw, k);
                     if (z == v || !(fwz & x)) continue;
                     uint32_t fuz;
@@ -760,7 +770,12 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalV
         const Row ru = V.urow(u);
         const Row rw = V.row(vid(V.U_col[e]));
         unsigned ca = 0, cb = 0;
-        if (ru.len <= rw.len) {
+        // with u's row staged, an edge whose N(w) is longer (at most four
+        // times) and whose probes lie wholly in this block's range still walks
+        // N(w), over the range proportional to its probe range of u's row (an
+        // edge that a block boundary cuts walks the same row in both blocks)
+        const bool staged = u == su;
+        if (ru.len <= rw.len && !(staged && pb >= lo && pe <= hi && rw.len <= 4 * ru.len)) {
             for (int k = k0 + lane; k < k1; k += 32) {
                 const uint32_t z = ru.p[k];
                 const int q = row_find(rw, 0, vid(z));
@@ -769,8 +784,10 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalV
                 ca += (f & FLAG_A) != 0;
                 cb += (f & FLAG_B) != 0;
             }
-        } else if (u == su) {
-            for (int k = k0 + lane; k < k1; k += 32) {
+        } else if (staged) {
+            const int j0 = rw.len < ru.len ? k0 : (int)((long long)k0 * rw.len / ru.len);
+            const int j1 = rw.len < ru.len ? k1 : (int)((long long)k1 * rw.len / ru.len);
+            for (int k = j0 + lane; k < j1; k += 32) {
                 const uint32_t z = rw.p[k] | rw.orf;
                 const uint32_t hit = lc4_find(tab, lgb, vid(z));
                 if (hit == LC4_EMPTY) continue;
