@@ -571,6 +571,13 @@ constexpr int LC4_ROW_MIN = 64;
 constexpr uint32_t LC4_EMPTY = 0xFFFFFFFFu;  // ids stay below 2^30 - 1
 constexpr size_t LC4_SMEM = (size_t)LC4_BUCKETS * sizeof(uint4);
 constexpr int LC4_THREADS = 512;
+// Probes a warp takes at a time from its block's range: about an eighth of
+// a warp's share, a multiple of 32 between 128 and 2048.
+constexpr int LC4_CHUNK = 2048;
+__device__ __forceinline__ long long lc4_chunk(long long range) {
+    const long long c = (range / (8 * (LC4_THREADS / 32)) + 31) & ~31ll;
+    return c < 128 ? 128 : c > LC4_CHUNK ? LC4_CHUNK : c;
+}
 
 __device__ __forceinline__ uint32_t lc4_bucket(uint32_t z, int lgb) { return (z * 0x9E3779B1u) >> (32 - lgb); }
 
@@ -617,7 +624,7 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
                                                 const long long* __restrict__ cpre) {
     pdl_enter();
     extern __shared__ uint4 tab[];
-    __shared__ unsigned long long s_best;
+    __shared__ unsigned long long s_best, s_chunk;
     __shared__ long long s_pair[2];
     const long long n = c->l_len[3];
     const long long tot = n ? tpre[n] : 0;
@@ -627,6 +634,7 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
         // the pair with the most probes in [lo, hi) whose u row can be staged
         if (threadIdx.x == 0) {
             s_best = 0;
+            s_chunk = (unsigned long long)lo;
             s_pair[0] = tpair[locate(tpre, n, lo)];
             s_pair[1] = tpair[locate(tpre, n, hi - 1)];
         }
@@ -649,14 +657,24 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
             const Pair p = pair_at(c, srcA, dstA, srcD, dstD, sp);
             lgb = lc4_stage(tab, V.urow(walk[sp] ? p.b : p.a));
         }
-        // each warp walks one slice of the block's range task by task: the
-        // task's pair, rows and walked entry once, then its probes 32 at a time
-        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-        const long long wlo = lo + (hi - lo) * wib / nwb, whi = lo + (hi - lo) * (wib + 1) / nwb;
+        // the warps take chunks of the block's range in turn (probe costs
+        // differ tenfold, so equal shares would leave warps idle) and walk
+        // each chunk task by task: the task's pair, rows and walked entry
+        // once, then its probes 32 at a time
+        const int lane = threadIdx.x & 31;
+        const long long chunk = lc4_chunk(hi - lo);
         long long tau = 0;
-        if (lane == 0 && wlo < whi) tau = locate(tpre, n, wlo);
+        if (lane == 0) tau = locate(tpre, n, lo);
         tau = __shfl_sync(FULL, tau, 0);
-        for (long long s = wlo; s < whi;) {
+        for (long long s = 0, whi = 0;;) {
+            if (s >= whi) {
+                long long c0 = 0;
+                if (lane == 0) c0 = (long long)atomicAdd(&s_chunk, (unsigned long long)chunk);
+                c0 = __shfl_sync(FULL, c0, 0);
+                if (c0 >= hi) break;
+                s = c0;
+                whi = min(hi, c0 + chunk);
+            }
             tau = next_task(tpre, n, s, tau);
             const long long pe = tpre[tau + 1], pb = tpre[tau];
             const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
@@ -725,9 +743,10 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
 // stages the union row of the owner with the most probes in it (of the
 // owners of its first, middle and last probe) in the shared-memory hash,
 // under the same bounds as the 4-cycle kernel; that owner's edges whose probes
-// walk N(w) look z up there.  Each warp walks one slice of the block's range
-// edge by edge: the edge's rows once, then its probes 32 at a time, the hits
-// summed over the warp before one atomic per edge and slice.
+// walk N(w) look z up there.  The warps take chunks of the block's range in
+// turn and walk each edge by edge: the edge's rows once, then its probes 32
+// at a time, the hits summed over the warp before one atomic per edge and
+// chunk.
 __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalView V,
                                                             const long long* __restrict__ pre,
                                                             const int32_t* __restrict__ own,
@@ -735,6 +754,7 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalV
     pdl_enter();
     extern __shared__ uint4 tab[];
     __shared__ int32_t s_cand[3];
+    __shared__ unsigned long long s_chunk;
     const long long n = c->l_len[0];
     if (n == 0) return;
     const long long tot = pre[n];
@@ -744,6 +764,7 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalV
         const long long t = threadIdx.x == 0 ? lo : threadIdx.x == 1 ? lo + (hi - lo) / 2 : hi - 1;
         s_cand[threadIdx.x] = own[locate(pre, n, t)];
     }
+    if (threadIdx.x == 0) s_chunk = (unsigned long long)lo;
     __syncthreads();
     long long su = -1, best = 0;
     for (int j = 0; j < 3; j++) {
@@ -756,12 +777,20 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_tri(const Ctl* c, LocalV
     }
     int lgb = 0;
     if (su >= 0) lgb = lc4_stage(tab, V.urow((uint32_t)su));
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-    const long long wlo = lo + (hi - lo) * wib / nwb, whi = lo + (hi - lo) * (wib + 1) / nwb;
+    const int lane = threadIdx.x & 31;
+    const long long chunk = lc4_chunk(hi - lo);
     long long e = 0;
-    if (lane == 0 && wlo < whi) e = locate(pre, n, wlo);
+    if (lane == 0) e = locate(pre, n, lo);
     e = __shfl_sync(FULL, e, 0);
-    for (long long s = wlo; s < whi;) {
+    for (long long s = 0, whi = 0;;) {
+        if (s >= whi) {
+            long long c0 = 0;
+            if (lane == 0) c0 = (long long)atomicAdd(&s_chunk, (unsigned long long)chunk);
+            c0 = __shfl_sync(FULL, c0, 0);
+            if (c0 >= hi) break;
+            s = c0;
+            whi = min(hi, c0 + chunk);
+        }
         e = next_task(pre, n, s, e);
         const long long pe = pre[e + 1], pb = pre[e];
         const int k0 = (int)(s - pb), k1 = (int)(min(whi, pe) - pb);
