@@ -908,6 +908,16 @@ __device__ __forceinline__ void group_sync() {
 //     and clears them;
 //   otherwise: increments that return the old value (summed on the fly),
 //     then the same wedges walked again to clear what they touched.
+// While every degree is below 2^16 (narrow layout), a wedge in both graphs
+// adds 1 to a 16-bit count of its endpoint, two endpoints to a 32-bit word,
+// so the counters of a cluster take 2 bytes per id (half of a 16/16 pair
+// per id): the L2 holds them and more of the adjacency, and random L2
+// reductions run faster on the smaller footprint (130 against 100 G/s for
+// 61 against 122 MB in all, by a probe on this GPU).  The few wedges in one
+// graph only (through a changed pair) count in separate 16/16 counters and
+// are listed; after the increments, each listed wedge adds the both-graph
+// count of its endpoint (the cross term of C(c_ab + c_x, 2)) and clears
+// its counter, before the sweep or the clearing walk.
 template <bool CLUSTER>
 __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, const int32_t* __restrict__ list,
                                                                 const long long* __restrict__ U_off,
@@ -923,10 +933,24 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
         ncta = (int)cl.num_blocks();
     }
     const int gid = blockIdx.x / ncta;
-    // per-group arrays start on 16-byte boundaries (vectorised clearing)
-    unsigned long long* a64 = arrays + (size_t)gid * (size_t)(((long long)n + 1) & ~1ll);
-    uint32_t* a32 = (uint32_t*)a64;
+    // per-group regions start on 16-byte boundaries (vectorised sweeps)
+    unsigned long long* a64 = arrays + (size_t)gid * (size_t)dense_stride(n);
     const bool wide = c->maxdeg >= 65536;
+    // Narrow layout (every degree below 2^16), in 32-bit words of the region:
+    //   cab  one 16-bit count per id of the wedges in both graphs, two ids
+    //        to a word (id w in half w & 1), 16-byte aligned;
+    //   cx   16/16 counts (G_a high, G_b low) of the wedges in one graph only;
+    //   lcount, lst  the list of those wedges (id | bit 31 for G_b) of the
+    //        pivot being counted, lcap entries (none when the region has no
+    //        room, on tiny graphs).
+    uint32_t* a32 = (uint32_t*)a64;
+    const long long words = 2 * dense_stride(n);
+    const long long off_ab = ((long long)n + 3) & ~3ll, len_ab = (((long long)n + 1) / 2 + 3) & ~3ll;
+    uint32_t* cx = a32;
+    uint32_t* cab = a32 + off_ab;
+    uint32_t* lcount = a32 + off_ab + len_ab;
+    uint32_t* lst = lcount + 4;
+    const long long lcap = min(words - (off_ab + len_ab + 4), 0x7FFFFFFFll);
     __shared__ int s_tot;
     __shared__ int s_pre[C4D_SEG + 1];
     __shared__ long long s_vb[C4D_SEG];
@@ -964,44 +988,14 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
         // coalesced: each c_w gives C(c_w, 2) and is cleared.  Smaller
         // pivots take old values and clear by walking their wedges again.
         const bool sweep = U_wt[u] * 8 > (long long)u;
-        for (int pass = 0; pass < 2; pass++) {
-            // pass 0: increments; pass 1: sweep, or clear by walking
-            if (pass == 1) {
-                group_sync<CLUSTER>();
-                if (sweep) {
-                    if (wide) {
-                        for (long long w = g; w < u; w += T) {
-                            const unsigned long long x = __ldcg(&a64[w]);
-                            if (x) {
-                                qa += choose2(x >> 32);
-                                qb += choose2(x & 0xFFFFFFFFull);
-                                a64[w] = 0ull;
-                            }
-                        }
-                    } else {
-                        // four 16/16 counters per 16-byte load; the array starts 16-byte aligned
-                        const long long q4 = ((long long)u + 3) / 4;
-                        uint4* a4 = (uint4*)a32;
-                        for (long long i = g; i < q4; i += T) {
-                            const uint4 x = __ldcg(&a4[i]);
-                            if (x.x | x.y | x.z | x.w) {
-                                const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    qa += choose2(xs[k] >> 16);
-                                    qb += choose2(xs[k] & 0xFFFFu);
-                                }
-                                a4[i] = make_uint4(0, 0, 0, 0);
-                            }
-                        }
-                    }
-                    break;
-                }
-            }
+        // One walk over the pivot's wedges.  mode 0: increments; mode 1:
+        // cross terms of the wedges of one graph only (narrow layout); mode
+        // 2: clearing what mode 0 touched.
+        auto walk = [&](int mode) {
             for (int s0 = 0; s0 < nlow; s0 += C4D_SEG) {
                 const int ns = min(C4D_SEG, nlow - s0);
-                // a single-segment pivot keeps its prefix for the clearing walk
-                if (pass == 0 || nlow > C4D_SEG)
+                // a single-segment pivot keeps its prefix for the later walks
+                if (mode == 0 || nlow > C4D_SEG)
                     wedge_segment_prefix(U_off, U_col, rb, s0, ns, s_pre, s_vb, s_fv, &s_tot);
                 const int total = s_tot;
                 // each warp takes C4D_UNROLL consecutive chunks of 32 wedges;
@@ -1037,33 +1031,118 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                     }
 #pragma unroll
                     for (int r = 0; r < C4D_UNROLL; r++) {
-                        uint32_t wv = vid(e[r]);
+                        const uint32_t wv = vid(e[r]);
                         if (wv >= (uint32_t)u) continue;
-                        uint32_t fl = f[r] & e[r] & (FLAG_A | FLAG_B);
-                        if (pass == 0) wedges++;
+                        const uint32_t fl = f[r] & e[r] & (FLAG_A | FLAG_B);
+                        if (mode == 0) wedges++;
                         if (!fl) continue;
-                        if (pass == 1) {
-                            if (wide) a64[wv] = 0ull;
-                            else a32[wv] = 0u;
-                        } else if (sweep) {
-                            nred++;
-                            if (wide) red_add_u64(&a64[wv], flag_inc(fl));
-                            else red_add_u32(&a32[wv], flag_inc16(fl));
-                        } else if (wide) {
+                        if (wide) {
+                            if (mode == 2) {
+                                a64[wv] = 0ull;
+                            } else if (sweep) {
+                                nred++;
+                                red_add_u64(&a64[wv], flag_inc(fl));
+                            } else {
+                                natom++;
+                                const unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
+                                if (fl & FLAG_A) qa += old >> 32;
+                                if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
+                            }
+                            continue;
+                        }
+                        const int sh = (int)(wv & 1u) * 16;
+                        if (fl == (FLAG_A | FLAG_B)) {
+                            if (mode == 2) {
+                                cab[wv >> 1] = 0u;
+                            } else if (mode == 0) {
+                                if (sweep) {
+                                    nred++;
+                                    red_add_u32(&cab[wv >> 1], 1u << sh);
+                                } else {
+                                    natom++;
+                                    const uint32_t c = (atomicAdd(&cab[wv >> 1], 1u << sh) >> sh) & 0xFFFFu;
+                                    qa += c;
+                                    qb += c;
+                                }
+                            }
+                        } else if (mode == 0) {
+                            // one graph only: its own count by a returning
+                            // atomic, the wedge listed for the cross term
                             natom++;
-                            unsigned long long old = atomicAdd(&a64[wv], flag_inc(fl));
-                            if (fl & FLAG_A) qa += old >> 32;
-                            if (fl & FLAG_B) qb += old & 0xFFFFFFFFull;
-                        } else {
-                            natom++;
-                            uint32_t old = atomicAdd(&a32[wv], flag_inc16(fl));
+                            const uint32_t old = atomicAdd(&cx[wv], flag_inc16(fl));
                             if (fl & FLAG_A) qa += old >> 16;
-                            if (fl & FLAG_B) qb += old & 0xFFFFu;
+                            else qb += old & 0xFFFFu;
+                            if (lcap > 0) {
+                                const uint32_t at = atomicAdd(lcount, 1u);
+                                if (at < (uint32_t)lcap) lst[at] = wv | (fl == FLAG_B ? 0x80000000u : 0u);
+                            }
+                        } else if (mode == 1) {
+                            const uint64_t c = (__ldcg(&cab[wv >> 1]) >> sh) & 0xFFFFu;
+                            if (fl & FLAG_A) qa += c;
+                            else qb += c;
+                            cx[wv] = 0u;
                         }
                     }
                 }
                 __syncthreads();  // the next segment reuses the shared arrays
             }
+        };
+        walk(0);
+        group_sync<CLUSTER>();
+        if (!wide) {
+            // c_a(w) = c_ab(w) + c_a-only(w): C(c_a, 2) = C(c_ab, 2) +
+            // C(c_a-only, 2) + c_ab(w) c_a-only(w).  The second term was summed
+            // on arrival; the cross term adds c_ab(w) once per listed wedge
+            // (the whole walk again if the list overflowed).  Without room for
+            // a list (tiny graphs) the walk always runs.
+            const uint32_t nl = lcap > 0 ? __ldcg(lcount) : 1u;
+            if (nl) {
+                if (nl <= (uint32_t)lcap) {
+                    for (long long i = g; i < (long long)nl; i += T) {
+                        const uint32_t x = __ldcg(&lst[i]);
+                        const uint32_t wv = x & 0x7FFFFFFFu;
+                        const uint64_t c = (__ldcg(&cab[wv >> 1]) >> ((wv & 1u) * 16)) & 0xFFFFu;
+                        if (x >> 31) qb += c;
+                        else qa += c;
+                        cx[wv] = 0u;
+                    }
+                } else {
+                    walk(1);
+                }
+                group_sync<CLUSTER>();  // every cross term read before the clearing
+                if (lcap > 0 && rank == 0 && threadIdx.x == 0) *lcount = 0u;
+            }
+        }
+        if (sweep) {
+            if (wide) {
+                for (long long w = g; w < u; w += T) {
+                    const unsigned long long x = __ldcg(&a64[w]);
+                    if (x) {
+                        qa += choose2(x >> 32);
+                        qb += choose2(x & 0xFFFFFFFFull);
+                        a64[w] = 0ull;
+                    }
+                }
+            } else {
+                // eight 16-bit counts per 16-byte load (the counts of ids in
+                // both graphs add to both sides)
+                const long long q4 = ((long long)u + 7) / 8;
+                uint4* a4 = (uint4*)cab;
+                for (long long i = g; i < q4; i += T) {
+                    const uint4 x = __ldcg(&a4[i]);
+                    if (x.x | x.y | x.z | x.w) {
+                        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+                        unsigned long long t = 0;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) t += choose2(xs[k] >> 16) + choose2(xs[k] & 0xFFFFu);
+                        qa += t;
+                        qb += t;
+                        a4[i] = make_uint4(0, 0, 0, 0);
+                    }
+                }
+            }
+        } else {
+            walk(2);
         }
         group_sync<CLUSTER>();
     }

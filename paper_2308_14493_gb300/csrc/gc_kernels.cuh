@@ -92,7 +92,7 @@ struct CountArgs {
     const int32_t* db;             // degree in G_b
     unsigned long long* tpack;     // per-entry triangle counters, zeroed
     int32_t* bins;                 // NBINS * n_alloc
-    unsigned long long* dense;     // dense_clusters * (n_alloc + 1) zeroed words
+    unsigned long long* dense;     // dense_clusters * dense_stride(n_alloc) zeroed words
     int n_alloc;                   // vertex id bound
     int dense_clusters;            // clusters of the heavy 4-cycle kernel
     int dense_cluster_size;        // CTAs per such cluster (8 or 16)
@@ -123,6 +123,11 @@ __host__ __device__ inline size_t c4_chunk_cta_bytes(long long cap) {
 // Cluster shape of the heavy 4-cycle kernel: CTAs per cluster (want = 0:
 // 16 if the device can co-schedule it, else 8) and the number of clusters.
 int dense_cluster_plan(int want, int sms, int* size_out);
+
+// 64-bit words of one cluster's counter region in the heavy 4-cycle kernel
+// for n vertices: an even count (16-byte aligned regions) with room for the
+// narrow layout's arrays, list counter and padding at every n.
+__host__ __device__ constexpr long long dense_stride(long long n) { return ((n + 1) & ~1ll) + 8; }
 // Device buffers of the edge-local path (gc_local.cu).  V_X = wlist[0 ..
 // lvl[0]), marked in `visited`; its union rows in U_off / U_col, degrees in
 // G_a / G_b in da / db.  The scratch arrays hold `cap` entries (the offset

@@ -48,7 +48,7 @@ constexpr size_t OFF_UCOL = al(OFF_WL + 4 * (size_t)NA_MAX_N);
 constexpr size_t OFF_TPACK = al(OFF_UCOL + 4 * (size_t)NA_MAX_E);
 constexpr size_t OFF_BINS = al(OFF_TPACK + 8 * (size_t)NA_MAX_E);
 constexpr size_t OFF_DENSE = al(OFF_BINS + 4 * (size_t)NA_MAX_N * NBINS);
-constexpr size_t OFF_CTA = al(OFF_DENSE + 8 * (size_t)NA_MAX_N * NA_DENSE_CLUSTERS);
+constexpr size_t OFF_CTA = al(OFF_DENSE + 8 * (size_t)dense_stride(NA_MAX_N) * NA_DENSE_CLUSTERS);
 constexpr size_t OFF_ERR = al(OFF_CTA + 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS);
 constexpr size_t SCRATCH_BYTES = al(OFF_ERR + 16);
 
@@ -191,9 +191,9 @@ extern "C" int gc_count_static_noalloc(int32_t n, const int32_t* d_row_ptr, cons
     // 4-cycle counters (an interrupted earlier call may have left them dirty)
     const bool stale = cudaPeekAtLastError() != cudaSuccess;
     k_na_reset<<<1, 32, 0, s>>>(ctl, bad);
-    // per-cluster counter arrays are laid out with an even word stride
+    // per-cluster counter regions of dense_stride(n) words
     if (cudaMemsetAsync(tpack, 0, 8 * (size_t)std::max<long long>(nnz, 1), s) != cudaSuccess ||
-        cudaMemsetAsync(dense, 0, 8 * (size_t)((nn + 1) & ~1) * NA_DENSE_CLUSTERS, s) != cudaSuccess ||
+        cudaMemsetAsync(dense, 0, 8 * (size_t)dense_stride(nn) * NA_DENSE_CLUSTERS, s) != cudaSuccess ||
         cudaMemsetAsync(cta_tables, 0, 8 * (size_t)NA_TABLE_WORDS * NA_CTA_GROUPS, s) != cudaSuccess)
         return GC_ECUDA;
     k_reset_count<<<1, 32, 0, s>>>(ctl);
