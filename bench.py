@@ -59,16 +59,18 @@ STAGES = ["normalise", "region", "union_graph", "triangles_k4", "four_cycles", "
 KERNEL_OF_STAGE = {3: "k_tri_warp + k_tri_block + k_tri_merge (triangles, 4-cliques)",
                    4: "k_c4_reg + k_c4_warp + k_c4_block + k_c4_dense + k_c4_hash (4-cycles)"}
 HEAVY_KERNEL = "k_c4_dense_t (heavy 4-cycle pivots; with k_c4_chunk when the tuning enables it)"
-# L2 atomic throughput of this GPU, measured by a probe kernel (random
-# 32-bit updates into arrays larger than L1, all SMs): reductions that return
-# nothing, and atomics that return the old value
-PROBE_L2_RED_PER_S = 204e9
-PROBE_L2_ATOM_PER_S = 55e9
+# L2 atomic throughput of this GPU, measured by a probe kernel: random 32-bit
+# updates from 1,024-thread CTAs on every SM into 19 per-cluster arrays of
+# 3.2 MB (61 MB in all, the footprint of the heavy-pivot kernel's counters
+# on the 1.6M-vertex graph): reductions that return nothing, and atomics
+# that return the old value
+PROBE_L2_RED_PER_S = 125e9
+PROBE_L2_ATOM_PER_S = 134.5e9
 # DRAM bytes (read + written) per wedge of the heavy-pivot kernel, from one
 # ncu capture of it on the half-size graph (n=800,000 m=15M, same generator):
-# 3.587 GB over 1.302e9 wedges;
+# 1.382 GB over 1.302e9 wedges;
 # None once the kernel changes
-HEAVY_DRAM_BYTES_PER_WEDGE = 3.587e9 / 1.302e9
+HEAVY_DRAM_BYTES_PER_WEDGE = (1.378197e9 + 3.995904e6) / 1.301926991e9
 WORKLOADS_DESC_C4 = ("Chung-Lu n=2.4M m=5M gamma=1.8 dmax=100,000; 64 independent batches, sizes log-uniform "
                      "10..50,000, 50% ins / 50% del")
 
