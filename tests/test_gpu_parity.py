@@ -170,6 +170,29 @@ def test_every_kernel_tier_alone(gcb, gname, tname):
         assert mod64(g.stats()["Ca"]) == mod64(r["Ca"])
 
 
+def test_cluster_counters_with_many_one_graph_wedges(gcb):
+    """The heavy-pivot kernel keeps one 16-bit count per id for the wedges in
+    both graphs and lists the wedges in one graph only (through a changed
+    pair) for their cross terms; a pivot with more of those than its list
+    holds (112 entries for 200 vertices) takes them by walking its wedges
+    again.  A dense 200-vertex graph with a batch changing half its edges
+    sends every pivot to that kernel, most of them past the list."""
+    n = 200
+    keys = gen.er_graph(n, 4000, 43)
+    rp, col = gen.csr_from_keys(n, keys)
+    F0 = oracle.static_counts(rp, col)
+    ins, dels = gen.random_batch(n, keys, 1000, 1000, 44)
+    r = oracle.fdgc_step(rp, col, ins, dels, F0)
+    with open_graph(gcb, n, rp, col) as g:
+        g.set_tuning(**TUNINGS["c4_all_cluster"])
+        assert g.count_static() == F0
+        assert g.count_batch(ins, dels) == r["F"]
+        assert g.counts() == F0
+        assert g.apply(ins, dels) == r["F"]
+        assert mod64(g.stats()["Ca"]) == mod64(r["Ca"])
+        assert mod64(g.stats()["Cb"]) == mod64(r["Cb"])
+
+
 def test_autotune_keeps_counts(gcb):
     n, keys = gen.workload_graph("c2")
     rp, col = gen.csr_from_keys(n, keys)
