@@ -169,6 +169,37 @@ def test_local_scratch_grows_for_a_hub(gcb):
         assert g.stats()["region_entries"] > (1 << 20)
 
 
+def test_local_batches_at_hubs_beyond_the_staged_hash(gcb):
+    """Hubs of 30,000 and 20,000 neighbours, rows longer than the
+    shared-memory hash of the local kernels (12,288 entries), so their
+    lookups search the rows in global memory; batches concentrated at the
+    hubs, with the pair of hubs inserted then deleted, match the oracle step
+    by step."""
+    n = 40000
+    rng = np.random.default_rng(7)
+    edges = set()
+    for h, k in ((0, 30000), (1, 20000)):
+        for v in rng.choice(np.arange(2, n), k, replace=False):
+            edges.add((h, int(v)))
+    for a, b in rng.integers(2, n, size=(60000, 2)):
+        if a != b:
+            edges.add((int(min(a, b)), int(max(a, b))))
+    rp, col = csr_from_edges(n, edges)
+    og = oracle.OracleGraph(rp, col)
+    with gcb.Graph(n, rp, col, local_max_pairs=ALWAYS) as g:
+        assert g.counts() == mod64(og.F)
+        for step in range(2):
+            cur = sorted(edges_from_csr(og.row_ptr, og.col))
+            hub_edges = [e for e in cur if e[0] < 2 and e[1] >= 2]
+            ins = [(int(h), int(v)) for h, v in zip(rng.integers(0, 2, 150), rng.integers(2, n, 150))]
+            ins += [(int(a), int(b)) for a, b in rng.integers(2, n, size=(50, 2)) if a != b]
+            dels = [hub_edges[i] for i in rng.choice(len(hub_edges), 100, replace=False)]
+            dels += [cur[i] for i in rng.choice(len(cur), 50, replace=False)]
+            # the pair of hubs: its 4-cycle probes look up the other hub's row
+            (ins if step == 0 else dels).append((0, 1))
+            _step(g, og, np.array(ins, np.int32), np.array(dels, np.int32))
+
+
 def test_local_after_region_batches_and_recount(gcb):
     """The maintained triangle sums are valid after open and after a static
     recount, stale after a committed region batch (the local path then
