@@ -1378,15 +1378,21 @@ __global__ void __launch_bounds__(CH_THREADS, 1) k_c4_chunk(Ctl* c, const int32_
 // (w + 1) << 32 | packed counts, 0 = empty; counts stay below 2^16 because a
 // pivot of this tier has fewer than 2^16 lower neighbours.  Returns the
 // packed counts before the increment.
+// Slot = [epoch 2 | id + 1 30 | G_a count 16 | G_b count 16].  A slot whose
+// epoch is not the current one (0: never used) is free: a pivot's keys only
+// ever turn free slots into current ones, so linear probing still stops at
+// the first free slot, and the entries of the previous pivots need no
+// clearing until the epochs wrap.
 __device__ __forceinline__ uint32_t ghash_add(unsigned long long* tab, int shift, uint32_t mask, uint32_t w,
-                                              uint32_t inc) {
+                                              uint32_t inc, uint32_t epoch) {
     uint32_t h = (w * 0x9E3779B1u) >> shift;
-    const unsigned long long key = (unsigned long long)(w + 1) << 32;
+    const unsigned long long key = (unsigned long long)((w + 1) | (epoch << 30)) << 32;
     for (;;) {
         unsigned long long cur = __ldcg(&tab[h]);  // from L2: slots change only by atomics
-        if (cur == 0ull) {
-            cur = atomicCAS(&tab[h], 0ull, key | inc);
-            if (cur == 0ull) return 0u;
+        if ((uint32_t)(cur >> 62) != epoch) {
+            const unsigned long long got = atomicCAS(&tab[h], cur, key | inc);
+            if (got == cur) return 0u;
+            cur = got;  // taken meanwhile, by a key of this pivot
         }
         if ((cur & 0xFFFFFFFF00000000ull) == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
         h = (h + 1) & mask;
@@ -1396,8 +1402,10 @@ __device__ __forceinline__ uint32_t ghash_add(unsigned long long* tab, int shift
 // Medium pivots (C4_T2 < w~ <= t3): one CTA per pivot with its own hash
 // table in global memory, sized to the pivot (twice the next power of two of
 // w~), so the tables of all CTAs stay small enough for L2.  The wedges are
-// dealt in warp-contiguous chunks as in the dense kernel; the used part of
-// the table is cleared by a vectorised fill after the pivot.
+// dealt in warp-contiguous chunks as in the dense kernel.  A CTA's pivots
+// take epochs 1, 2, 3 in turn; the part of the table those three used is
+// cleared by a vectorised fill after the third (and at the end), so the
+// tables are zero between launches.
 __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const int32_t* __restrict__ list,
                                                              const long long* __restrict__ U_off,
                                                              const uint32_t* __restrict__ U_col,
@@ -1414,6 +1422,9 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
     const int cnt = c->nbin[BIN_C4_CTA];
     unsigned long long qa = 0, qb = 0, wedges = 0;
+    uint32_t epoch = 1;
+    int lg_used = 0;  // largest table of the pivots since the last clearing
+    uint4* t4 = (uint4*)tab;
     for (;;) {
         if (tid == 0) {
             s_idx = (int)atomicAdd(&c->work[WORK_C4_CTA], 1u);
@@ -1475,18 +1486,24 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_hash(Ctl* c, const i
                     wedges++;
                     uint32_t fl = f[r] & e[r] & (FLAG_A | FLAG_B);
                     if (!fl) continue;
-                    uint32_t old = ghash_add(tab, shift, mask, wv, flag_inc16(fl));
+                    uint32_t old = ghash_add(tab, shift, mask, wv, flag_inc16(fl), epoch);
                     if (fl & FLAG_A) qa += old >> 16;
                     if (fl & FLAG_B) qb += old & 0xFFFFu;
                 }
             }
             __syncthreads();
         }
-        // clear the used part of the table
-        uint4* t4 = (uint4*)tab;
-        for (long long i = tid; i < (1ll << lg) / 2; i += blockDim.x) t4[i] = make_uint4(0, 0, 0, 0);
-        __syncthreads();
+        lg_used = max(lg_used, lg);
+        if (epoch == 3) {
+            for (long long i = tid; i < (1ll << lg_used) / 2; i += blockDim.x) t4[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            epoch = 1;
+            lg_used = 0;
+        } else {
+            epoch++;
+        }
     }
+    for (long long i = tid; i < (1ll << lg_used) / 2 && lg_used > 0; i += blockDim.x) t4[i] = make_uint4(0, 0, 0, 0);
     acc_add(c, 5, qa);
     acc_add(c, 11, qb);
     acc_add(c, 15, wedges);
