@@ -694,9 +694,9 @@ __global__ void __launch_bounds__(LC4_THREADS, 3) k_loc_c4(Ctl* c, LocalView V, 
             // with u's row staged, a task whose N(w) is longer (at most four
             // times) still walks N(w) when the task lies wholly in this
             // block's range: its probe range [k0, k1) of u's row maps to the
-            // proportional range of N(w), so the warp slices that split the
-            // task split N(w) exactly.  A task that a block boundary cuts
-            // keeps walking u's row in both blocks, whichever pairs they stage.
+            // proportional range of N(w), so the chunks that split the task
+            // split N(w) exactly.  A task that a block boundary cuts keeps
+            // walking u's row in both blocks, whichever pairs they stage.
             const bool walk_w =
                 rw.len <= ru.len || (staged && pb >= lo && pe <= hi && rw.len <= 4 * ru.len);
             if (walk_w) {
