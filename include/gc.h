@@ -382,8 +382,10 @@ typedef struct {
                                adjacency entries, the later batches go in pairs: the first of a
                                pair is committed without a count, the second counted over every
                                vertex, which gives the whole graph's counts after both (the
-                               counts are the same; one pass instead of two); 0 = never
-                               (default 700) */
+                               counts are the same; one pass instead of two).  The handle keeps
+                               the size of that first batch: a later run whose first batch is at
+                               least as large goes in pairs from its first batch.  Setting the
+                               tuning forgets it.  0 = never (default 700) */
 } gc_tuning;
 
 int gc_get_tuning(const gc_graph *g, gc_tuning *t);

@@ -127,6 +127,7 @@ struct gc_graph {
     unsigned long long q_gen[3] = {0, 0, 0};
     int q_launches[3] = {0, 0, 0};
     long long pair_min_share = 700;      // per mille of 2m (gc_tuning.pair_min_share)
+    long long pair_hint = 0;             // size of the smallest first batch of a run whose region met it (0: none)
     // maintained triangle sums of the edge-local path: T2[x] = sum of t_e
     // over the edges at x, valid after a static count and kept by local
     // batches (a region batch makes it stale)
@@ -1193,9 +1194,13 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
     }
     // the two-batch form: a sequential run of at least three batches whose
     // pairs pass the device check (a bad pair makes its batch a no-op, which
-    // the pairing does not model); batch 0 runs as Algorithm 2 and its region
-    // decides whether the rest go in pairs
+    // the pairing does not model).  Batch 0 runs as Algorithm 2 and its region
+    // decides whether the rest go in pairs; a run whose batch 0 is at least as
+    // large as the first batch of an earlier run that went in pairs starts
+    // them at batch 0 (regions grow with their endpoints, and a pair is exact
+    // whatever the region: the choice is one of speed only).
     bool pair_ok = (commit || twin_ok) && k >= 3 && g->pair_min_share > 0;
+    const long long size0 = h_batches[1] + h_batches[3];
     if (pair_ok) {
         CK(cudaMemsetAsync(g->hist.p, 0, sizeof(int), s));
         k_run_pairs_check<<<dim3(64, (unsigned)std::min(k, 64)), TPB, 0, s>>>(g->desc, k, g->n, (int*)g->hist.p);
@@ -1205,11 +1210,17 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
         CK(cudaStreamSynchronize(s));
         pair_ok = bad == 0;
     }
-    bool pairs = false;  // batches 1 .. k-1 go in pairs
+    bool pairs = false;  // batches base .. k-1 go in pairs
+    int base = 1;
+    if (pair_ok && g->pair_hint > 0 && size0 >= g->pair_hint) {
+        pairs = true;
+        base = 0;
+        pair_ok = false;
+    }
     int pairs_used = 0;
     auto role_of = [&](int i) {
-        if (!pairs || i == 0) return 0;
-        if ((i - 1) % 2 == 0) return i + 1 < k ? (commit ? 1 : 3) : 0;
+        if (!pairs || i < base) return 0;
+        if ((i - base) % 2 == 0) return i + 1 < k ? (commit ? 1 : 3) : 0;
         return 2;  // (independent runs never reach this: a twin pass takes two batches)
     };
     auto ensure_exec = [&](int role) -> int {
@@ -1245,6 +1256,7 @@ static int apply_batches_region(gc_graph* g, const int32_t* d_ins, const int32_t
             // batch 0's region against the graph's adjacency entries
             pairs = (double)g->h_ctl->nU * 1000.0 >= (double)g->pair_min_share * 2.0 * (double)g->m;
             pair_ok = false;
+            if (pairs) g->pair_hint = g->pair_hint > 0 ? std::min(g->pair_hint, size0) : size0;
         }
         if (g->h_ctl->halt) {
             // batch done-1 is counted (or, first of a pair, only normalised)
@@ -2349,6 +2361,7 @@ int gc_set_tuning(gc_graph* g, const gc_tuning* t) {
     g->opt.local_max_pairs = (int32_t)std::min<int64_t>(t->local_max_pairs, INT32_MAX);
     g->loc_heavy_min = t->local_c4_heavy_min;
     g->pair_min_share = t->pair_min_share;
+    g->pair_hint = 0;
     return GC_OK;
 }
 

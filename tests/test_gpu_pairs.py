@@ -46,6 +46,37 @@ def test_pairs_equal_the_oracle_and_the_single_pass_form(gcb, k):
         assert g.stats()["path"] == 0
 
 
+def test_later_runs_pair_from_their_first_batch(gcb):
+    """After a run whose first batch's region went in pairs, the handle
+    keeps that batch's size: a later run whose first batch is at least as
+    large pairs from batch 0 (four batches: two pairs, no batch alone),
+    with the same counts; a smaller first batch measures its region again;
+    setting the tuning forgets the size."""
+    n, keys = gen.workload_graph("c2")
+    rp, col = gen.csr_from_keys(n, keys)
+    stream = gen.batch_stream(n, keys, [5000, 4000, 3000, 8000, 6000, 7000, 5000, 500, 6000, 6000, 6000],
+                              0.5, 97)
+    runs = [stream[0:3], stream[3:7], stream[7:10], stream[10:11]]
+    expect, _ = _expect(rp, col, stream)
+    with gcb.Graph(n, rp, col) as g:
+        at = 0
+        launches, paths = [], []
+        for run in runs:
+            assert g.apply_many(run) == expect[at:at + len(run)]
+            launches.append(g.stats()["launches"])
+            paths.append(g.stats()["path"])
+            at += len(run)
+        assert paths[:3] == [2, 2, 2]
+        assert g.counts() == expect[-1] and g.count_static() == expect[-1]
+    # the second run (first batch 8,000 >= 5,000) took two passes for four
+    # batches; the same four batches from a fresh handle take three
+    with gcb.Graph(n, rp, col) as g:
+        assert g.apply_many(stream[0:3]) == expect[0:3]
+        g.set_tuning(**g.tuning())
+        assert g.apply_many(stream[3:7]) == expect[3:7]
+        assert g.stats()["launches"] > launches[1]
+
+
 def test_small_regions_do_not_pair(gcb):
     """Batches of a few pairs on a sparse graph: batch 0's region is a small
     part of the graph, so the run stays one pass per batch."""
