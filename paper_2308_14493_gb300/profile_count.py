@@ -1,15 +1,15 @@
 """Static count of a seeded Chung-Lu graph, repeated, for kernel profiling.
 
     python -m paper_2308_14493_gb300.profile_count --n 800000 --m 15000000 \\
-        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000] [--local] [--vertex | --edge] [--tuning JSON]
+        --gamma 2.3 --dmax 10000 --reps 2 [--batch 100000 [--batched]] [--local] [--vertex | --edge] [--tuning JSON]
 
 Opens the graph (one static count), then runs ``reps`` more static counts
 (or, with ``--batch``, ``reps`` sequential batches of that many updates, 60%
-insertions; with ``--local`` through the edge-local delta; with ``--vertex``
-the per-vertex graphlet counts, with ``--edge`` the per-edge orbit counts)
-and prints the per-stage device times of
-each call.  Used as the
-command under ncu; it runs the library exactly as a user would.
+insertions, one ``gc_apply_batch`` call each, or all in one batched call with
+``--batched``; with ``--local`` through the edge-local delta; with
+``--vertex`` the per-vertex graphlet counts, with ``--edge`` the per-edge
+orbit counts) and prints the per-stage device times of each call.  Used as
+the command under ncu; it runs the library exactly as a user would.
 """
 from __future__ import annotations
 
@@ -38,6 +38,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--autotune", action="store_true", help="pick the bin boundaries first")
     ap.add_argument("--local", action="store_true", help="batches take the edge-local delta")
+    ap.add_argument("--batched", action="store_true", help="with --batch: all batches in one batched call")
     ap.add_argument("--vertex", action="store_true", help="per-vertex graphlet counts instead of static counts")
     ap.add_argument("--edge", action="store_true", help="per-edge orbit counts instead of static counts")
     ap.add_argument("--heavy-min", default="",
@@ -75,6 +76,12 @@ def main():
                     rec["local_c4_heavy_min"] = g.tuning()["local_c4_heavy_min"]
                     rec["launches"] = g.stats()["launches"]
                     print(json.dumps(rec), flush=True)
+        elif a.batch and a.batched:
+            batches = gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1)
+            g.apply_many(batches)
+            st = g.stats()
+            print(json.dumps({"batches": a.reps, "run_ms": st["ms_device"], "path": st["path"],
+                              "launches": st["launches"], "counts": g.counts()}), flush=True)
         elif a.batch:
             for ins, dels in gen.batch_stream(a.n, keys, [a.batch] * a.reps, 0.6, a.seed + 1):
                 g.apply(ins, dels)
