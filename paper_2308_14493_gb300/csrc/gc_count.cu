@@ -1096,11 +1096,14 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
             // on arrival; the cross term adds c_ab(w) once per listed wedge
             // (the whole walk again if the list overflowed).  Without room for
             // a list (tiny graphs) the walk always runs.
+            // The list's entries are zeroed as they are taken: the region is
+            // read as 32/32 counters once some degree reaches 2^16.
             const uint32_t nl = lcap > 0 ? __ldcg(lcount) : 1u;
             if (nl) {
                 if (nl <= (uint32_t)lcap) {
                     for (long long i = g; i < (long long)nl; i += T) {
                         const uint32_t x = __ldcg(&lst[i]);
+                        lst[i] = 0u;
                         const uint32_t wv = x & 0x7FFFFFFFu;
                         const uint64_t c = (__ldcg(&cab[wv >> 1]) >> ((wv & 1u) * 16)) & 0xFFFFu;
                         if (x >> 31) qb += c;
@@ -1109,6 +1112,7 @@ __global__ void __launch_bounds__(C4_DENSE_THREADS, 1) k_c4_dense_t(Ctl* c, cons
                     }
                 } else {
                     walk(1);
+                    for (long long i = g; i < lcap; i += T) lst[i] = 0u;
                 }
                 group_sync<CLUSTER>();  // every cross term read before the clearing
                 if (lcap > 0 && rank == 0 && threadIdx.x == 0) *lcount = 0u;

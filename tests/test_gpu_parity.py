@@ -218,6 +218,34 @@ def _two_big_hubs():
     return n, np.array(sorted(keys), dtype=np.uint64)
 
 
+def test_cluster_counters_switch_from_16_to_32_bits(gcb):
+    """A hub one neighbour short of 2^16: the cluster kernel counts in the
+    16-bit layout (a batch leaves one-graph wedges in its lists), then a
+    batch lifts the hub past 2^16 and the same counter regions serve as
+    32/32-bit counters; every count equals the oracle."""
+    n = 70000
+    keys = set(int(k) for k in gen.er_graph(n, 40000, 47) if (int(k) >> 32) > 1)
+    for v in range(2, 65537):
+        keys.add(v)  # (0, v)
+    for v in range(2, 20002):
+        keys.add((1 << 32) | v)
+    keys = np.array(sorted(keys), dtype=np.uint64)
+    rp, col = gen.csr_from_keys(n, keys)
+    assert int(np.diff(rp).max()) == 65535
+    og = oracle.OracleGraph(rp, col)
+    rng = np.random.default_rng(48)
+    with open_graph(gcb, n, rp, col) as g:
+        g.set_tuning(**TUNINGS["c4_all_cluster"])
+        assert g.counts() == og.F
+        dels = np.array([(1, int(v)) for v in rng.choice(np.arange(2, 20002), 300, replace=False)], np.int32)
+        ins = np.array([(int(a), int(b)) for a, b in rng.integers(2, n, size=(300, 2)) if a != b], np.int32)
+        assert g.apply(ins, dels) == og.apply(ins, dels)["F"]
+        ins2 = np.array([(0, 65537), (0, 65538), (0, 65539), (1, 65540)], np.int32)
+        none = np.zeros((0, 2), np.int32)
+        assert g.apply(ins2, none) == og.apply(ins2, none)["F"]
+        assert g.count_static() == og.F
+
+
 @pytest.mark.parametrize("opts", [dict(), dict(chunk_threshold=1)], ids=["cluster", "chunked"])
 def test_hubs_beyond_16_bit_counts(gcb, opts):
     n, keys = _two_big_hubs()
