@@ -1539,7 +1539,8 @@ static int open_device(gc_graph* g, const int32_t* row_ptr, const int32_t* colh)
     local_setup_attributes();
     g->bins = (int32_t*)dalloc(g, sizeof(int32_t) * (size_t)NBINS * nn);
     g->dense_clusters = dense_cluster_plan(g->opt.dense_cluster, g->sms, &g->dense_cluster_size);
-    if (!g->bins || !ensure(g, g->dense, (size_t)g->dense_clusters * (size_t)dense_stride((long long)nn))) return nomem(g, "counting work lists");
+    if (!g->bins || !ensure(g, g->dense, (size_t)g->dense_clusters * (size_t)dense_stride((long long)nn)))
+        return nomem(g, "counting work lists");
     CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
     g->cta_groups = g->sms;
     if (!ensure(g, g->cta_tables, (size_t)g->cta_groups * 2 * C4_T3)) return nomem(g, "4-cycle hash tables");
@@ -2068,7 +2069,8 @@ static int grow_vertices(gc_graph* g, long long k) {
                g->row_start, n0, n1);
     CKL();
     release(g, g->dense);
-    if (!ensure(g, g->dense, (size_t)g->dense_clusters * (size_t)dense_stride((long long)nn))) return nomem(g, "4-cycle counter arrays");
+    if (!ensure(g, g->dense, (size_t)g->dense_clusters * (size_t)dense_stride((long long)nn)))
+        return nomem(g, "4-cycle counter arrays");
     CK(cudaMemsetAsync(g->dense.p, 0, 8 * g->dense.cap, s));
     g->n = n1;
     g->S = std::max(1, bitlen(n1 > 0 ? n1 - 1 : 0));

@@ -1206,8 +1206,8 @@ int enqueue_local(const LocalArgs& a, cudaStream_t s, cudaEvent_t ev_tri, cudaEv
                                       a.cost);
     nl += 2;
     nl += scan_i32_to_i64(a.cost, a.pre, &a.ctl->l_len[3], 0, a.bsum, sg, &a.ctl->l_tot[4], s);
-    pdl_launch(k_loc_c4, dim3(staged_grid(1, sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.srcA, a.dstA, a.srcD, a.dstD,
-               a.walk, a.tpair, a.own, a.pre, a.cpre);
+    pdl_launch(k_loc_c4, dim3(staged_grid(1, sms)), dim3(LC4_THREADS), LC4_SMEM, s, a.ctl, V, a.srcA, a.dstA, a.srcD,
+               a.dstD, a.walk, a.tpair, a.own, a.pre, a.cpre);
     nl++;
     if (ev_fin) record_stage(ev_fin, s);
     pdl_launch(k_finalize_local, dim3(1), dim3(32), 0, s, a.ctl, commit);
