@@ -68,9 +68,9 @@ PROBE_L2_RED_PER_S = 125e9
 PROBE_L2_ATOM_PER_S = 134.5e9
 # DRAM bytes (read + written) per wedge of the heavy-pivot kernel, from one
 # ncu capture of it on the half-size graph (n=800,000 m=15M, same generator):
-# 1.379 GB over 1.302e9 wedges;
+# 1.403 GB over 1.302e9 wedges;
 # None once the kernel changes
-HEAVY_DRAM_BYTES_PER_WEDGE = (1.375513e9 + 3.904e6) / 1.301926991e9
+HEAVY_DRAM_BYTES_PER_WEDGE = (1.399486e9 + 3.768832e6) / 1.301926991e9
 WORKLOADS_DESC_C4 = ("Chung-Lu n=2.4M m=5M gamma=1.8 dmax=100,000; 64 independent batches, sizes log-uniform "
                      "10..50,000, 50% ins / 50% del")
 
